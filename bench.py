@@ -1,0 +1,351 @@
+"""Benchmark: particle-steps/s of the emission hot path on synthetic workloads.
+
+Default workload (one bench step): the counter-propagating circularly
+polarised plane wave, lambda = 0.8 um, 2^20 electrons with gamma = 1000 along
+-x plus 1% Gaussian momentum spread, FP32 push with FP64 ledger, 20 laser
+periods at 200 steps per period, table sampler, for each a0 in {100, 300, 500}
+(3 x 2^20 x 4000 = 1.26e10 particle-steps per bench step).  Every particle-step
+runs the whole path: gather, Boris push, H_eff, omega_c, LL kick and ledger,
+Philox, S(x) sampling with the F table, photon append, emitted-energy ledger.
+
+Timing: CUDA events on the launching stream around each bench step, L2 flushed
+(256 MB write) between steps, max over ranks.  ``--impl reference`` times the
+FP64 CPU oracle on the host cores on a bounded sample of the same workload.
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s with emission (plain table vs MLP sampler) at <=1% spectral err"
+UNIT = "particle-steps/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="prad", choices=["prad", "reference"])
+    ap.add_argument("--particles", type=int, default=1 << 20)
+    ap.add_argument("--a0", type=str, default="100,300,500")
+    ap.add_argument("--periods", type=int, default=20)
+    ap.add_argument("--nsub", type=int, default=0,
+                    help="substeps fused per launch (0: tuned default)")
+    ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--bps", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clock, reasons)."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [v.strip() for v in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- helpers
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def a0_list(s: str):
+    return [float(v) for v in s.split(",") if v.strip()]
+
+
+def workload_name(args) -> str:
+    return (f"CP plane wave, lambda=0.8um, a0 in {{{args.a0}}}, {args.particles} electrons "
+            f"gamma=1000 along -x +1% spread, {args.periods * 200} steps (200/period), "
+            "FP32 push + FP64 ledger, table sampler, LL kick")
+
+
+def cpu_baseline(args, budget_s: float) -> dict:
+    """The FP64 oracle, as it stands, on the host cores: a bounded sample of
+    the same workload (a subset of the particles, the full step count split
+    evenly over the a0 values)."""
+    import oracle as O
+    from paper_1409_5574_gb300 import workloads as W
+    O.lib()
+    a0s = a0_list(args.a0)
+    nsteps = args.periods * 200
+    # probe throughput, then size the sample to about budget_s seconds
+    wl = W.plane_wave(a0=a0s[-1], n=256, periods=1, seed=11)
+    t = time.perf_counter()
+    O.run(O.Problem(**wl.problem_kwargs()), wl.copy_state(), 200, capacity=1 << 20)
+    rate = 256 * 200 / (time.perf_counter() - t)
+    n = max(64, int(rate * budget_s / (nsteps * len(a0s))))
+    n = min(n, args.particles)
+    total_ps, total_t = 0, 0.0
+    for a0 in a0s:
+        wl = W.plane_wave(a0=a0, n=args.particles, periods=args.periods, seed=1)
+        sub = wl.subset(slice(0, n))
+        p = O.Problem(**sub.problem_kwargs())
+        st = sub.copy_state()
+        t = time.perf_counter()
+        O.run(p, st, nsteps, capacity=1 << 22)
+        total_t += time.perf_counter() - t
+        total_ps += n * nsteps
+    return {"value": total_ps / total_t, "unit": UNIT, "cores": O.num_threads(),
+            "kind": "oracle",
+            "sample": f"first {n} of {args.particles} electrons x {nsteps} steps for each "
+                      f"a0 in {{{args.a0}}} ({total_ps:.3g} particle-steps, {total_t:.1f} s)"}
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    cb = cpu_baseline(args, budget_s=args.cpu_seconds)
+    v = cb["value"]
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(args), "sample": cb["sample"]},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_prad(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1409_5574_gb300 import prad, workloads as W
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.current_stream()
+    a0s = a0_list(args.a0)
+    nsteps = args.periods * 200
+    n = args.particles
+    nsub = args.nsub if args.nsub > 0 else 100
+
+    # inputs: seeded synthetic states, one per a0, resident in HBM
+    wls = [W.plane_wave(a0=a0, n=n, periods=args.periods, seed=1 + 97 * rank) for a0 in a0s]
+    cap = int(0.12 * n * nsteps) + (1 << 20)
+    ctx = prad.Context(wls[0].problem_kwargs(), precision=prad.PRAD_FP32,
+                       photon_capacity=cap, max_particles=n, steps_per_launch=nsub,
+                       block_size=args.block, blocks_per_sm=args.bps)
+    init = [ctx.to_device(w.state) for w in wls]
+    work = {k: torch.empty_like(v) for k, v in init[0].items()}
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    pid0 = rank * n
+    launches_per_run = math.ceil(nsteps / nsub)
+
+    def one_step():
+        recs = 0
+        for w, st0 in zip(wls, init):
+            ctx.set_fields(w.problem_kwargs())
+            for k in work:
+                work[k].copy_(st0[k], non_blocking=True)
+            ctx.push_emit(work, nsteps, t0=0, pid0=pid0)
+            held, dropped = ctx.drain()
+            recs += held + dropped
+        return recs
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(dev)
+    clocks.start()
+    times = []
+    records = 0
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        flush.zero_()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        records += one_step()
+        ev1.record(stream)
+        ev1.synchronize()
+        times.append(ev0.elapsed_time(ev1) / 1e3)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    ck = clocks.stop()
+    t_total = sum(times)
+    if ws > 1:
+        tt = torch.tensor([t_total], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_total = float(tt.item())
+    ps_per_step = len(a0s) * n * nsteps
+    value = ws * ps_per_step * args.steps / t_total
+
+    # dominant kernel: average launch duration of the fused push kernel, from
+    # events around one run's push_emit only (same stream, same launches)
+    ctx.set_fields(wls[-1].problem_kwargs())
+    for k in work:
+        work[k].copy_(init[-1][k])
+    ctx.drain()
+    flush.zero_()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ctx.push_emit(work, nsteps, t0=0, pid0=pid0)
+    e1.record(stream)
+    e1.synchronize()
+    run_s = e0.elapsed_time(e1) / 1e3
+    held, dropped = ctx.drain()
+    per_launch_s = run_s / launches_per_run
+    # algorithmic bytes of one launch: state R 28 B + W 24 B, LL ledger 16 B,
+    # emit-ledger RMW 16 B per record (upper bound), photon record 40 B
+    recs_per_launch = (held + dropped) / launches_per_run
+    alg_bytes = n * (28 + 24 + 16) + recs_per_launch * (40 + 16)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    achieved = alg_bytes / per_launch_s / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": None,
+                "kernel": "k_push_emit<float, PLANE_WAVE>",
+                "launch": f"{n} particles x {nsub} steps",
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback"}
+
+    # end to end through the public API: pinned host state -> device each run,
+    # totals read back each run
+    e2e = None
+    if not args.no_e2e:
+        host = [{k: v.cpu().pin_memory() for k, v in st.items()} for st in init]
+        h2d = sum(v.numel() * v.element_size() for st in host for v in st.values())
+        d2h = 0
+
+        def e2e_step():
+            nonlocal d2h
+            d2h = 0
+            for w, hs in zip(wls, host):
+                ctx.set_fields(w.problem_kwargs())
+                for k in work:
+                    work[k].copy_(hs[k], non_blocking=True)
+                ctx.reset()
+                ctx.push_emit(work, nsteps, t0=0, pid0=pid0)
+                em, ll, st = ctx.energy_budget()
+                ctx.drain()
+                d2h += 2 * 8 + 7 * 8 + 4 + 8
+        e2e_step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        if ws > 1:
+            tt = torch.tensor([te], device="cuda", dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            te = float(tt.item())
+        e2e = {"value": ws * ps_per_step * args.steps / te, "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    cb = None
+    if rank == 0 and ws == 1:
+        cb = cpu_baseline(args, budget_s=args.cpu_seconds)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": workload_name(args), "particles_per_gpu": n,
+                           "a0": a0s, "steps_per_run": nsteps, "sampler": "table",
+                           "steps_per_launch": nsub, "ledger": "f64",
+                           "l2": "flushed (256 MB write) between timed steps; the "
+                                 f"{n * 44 / 1e6:.0f} MB state stays resident across a run",
+                           "photon_records_per_step": records / args.steps,
+                           "parallelism": f"independent particles, {ws} GPU(s)"},
+                "roofline": roofline, "cpu_baseline": cb, "e2e": e2e,
+                "gpu_launches": args.steps * len(a0s) * launches_per_run,
+                "clocks": ck}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_prad(args)
+
+
+if __name__ == "__main__":
+    main()

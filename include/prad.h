@@ -1,0 +1,246 @@
+/*
+ * prad.h - C ABI of the GB300 (sm_103a) synchrotron-emission particle step.
+ *
+ * Implements the per-timestep particle hot path of E. Wallin, A. Gonoskov and
+ * M. Marklund, "Effects of high energy photon emissions in laser generated
+ * ultra-relativistic plasmas: real-time synchrotron simulations"
+ * (arXiv:1409.5574):
+ *
+ *   field gather -> Boris push -> effective field H_eff and omega_c (Eq. (1))
+ *   -> Monte Carlo emission of synchrotron macro-photons sampled from
+ *   Eqs. (7)-(8) with the S(x) noise-reduction proposal (Eqs. (11)-(13))
+ *   -> photon append -> emitted-energy ledger booked beside the
+ *   Landau-Lifshitz loss of Eq. (4) (the comparison of Fig. 3).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - All calls return int: PRAD_OK (0), a negative PRAD_ERR_* code, or a
+ *   positive PRAD_WARN_* code.  They never abort, print or throw;
+ *   prad_last_error() returns a message for the last failing call of a
+ *   context.
+ * - Pointers named "device" must be CUDA device (or managed) memory of the
+ *   context's device; "host" pointers are ordinary host memory.  The library
+ *   never frees memory it did not allocate.
+ * - Units.  The problem is described in SI (dt in s, fields in V/m and T,
+ *   wavelength in m).  Particle state is normalised by a reference angular
+ *   frequency omega_ref: time in 1/omega_ref, length in c/omega_ref,
+ *   momentum u = p/(m_e c).  Photon and ledger energies are in m_e c^2.
+ * - Every kernel of a context runs on the context's stream (cfg.stream).
+ *   push_emit is asynchronous; get_photons, energy_budget and get_ledger
+ *   synchronise that stream before returning.
+ * - Random numbers: Philox4x32-10 with key (seed_lo, seed_hi) and counter
+ *   (pid, step, 0, ensemble); results do not depend on launch shape, on how
+ *   a run is split into calls, or on the number of substeps per launch.
+ */
+#ifndef PRAD_H
+#define PRAD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define PRAD_OK 0
+#define PRAD_ERR_ARG -1      /* invalid argument (null, size, enum, alignment) */
+#define PRAD_ERR_CUDA -2     /* a CUDA runtime call failed */
+#define PRAD_ERR_CAPACITY -3 /* a buffer of capacity 0 was given */
+#define PRAD_ERR_TIMEOUT -4  /* a bounded device wait gave up */
+#define PRAD_ERR_STATE -5    /* call made in the wrong state (e.g. no fields) */
+#define PRAD_WARN_NAN 1      /* non-finite particles were found and frozen */
+
+/* ---- enums ------------------------------------------------------------- */
+enum prad_precision { PRAD_FP32 = 0, PRAD_FP64 = 1 };
+enum prad_sampler {
+  PRAD_SAMPLER_TABLE = 0,        /* S(x) proposal + tabulated F, Eq. (13) */
+  PRAD_SAMPLER_MLP = 1,          /* learned inverse CDF (no fallback)     */
+  PRAD_SAMPLER_MLP_FALLBACK = 2  /* learned inverse CDF, table fallback   */
+};
+enum prad_rr_mode {
+  PRAD_RR_OFF = 0,    /* no LL ledger, no LL kick                          */
+  PRAD_RR_LEDGER = 1, /* book the LL loss of Eq. (4), no momentum change   */
+  PRAD_RR_APPLY = 2   /* book it and apply the LL force to the momentum    */
+};
+enum prad_heff_form {
+  PRAD_HEFF_FIELD = 0,   /* H^2 = |E + beta x B|^2 - (E.beta)^2            */
+  PRAD_HEFF_MOMENTUM = 1 /* Eq. (9), from the momentum change of the step  */
+};
+enum prad_field_kind {
+  PRAD_FIELD_CONST = 0,      /* uniform constant E, B                      */
+  PRAD_FIELD_PLANE_WAVE = 1, /* circularly polarised plane wave along +-x  */
+  PRAD_FIELD_YEE2D = 2       /* staggered 2D Yee grid, quadratic splines   */
+};
+
+/* ---- configuration ----------------------------------------------------- */
+typedef struct prad_config {
+  int32_t precision;        /* prad_precision: FP32 push (FP64 ledger) or FP64 */
+  int32_t sampler;          /* prad_sampler                                  */
+  int32_t rr_mode;          /* prad_rr_mode                                  */
+  int32_t heff_form;        /* prad_heff_form                                */
+  double dt;                /* time step [s], > 0                            */
+  double omega_ref;         /* reference angular frequency [rad/s], > 0      */
+  double charge;            /* particle charge in e: -1 electron, +1 positron */
+  uint64_t seed;            /* Philox key                                     */
+  uint32_t ensemble;        /* Philox counter word 3                          */
+  int32_t steps_per_launch; /* substeps fused per kernel launch; 0 = 1       */
+  int64_t photon_capacity;  /* photon records held on the device, >= 1       */
+  int64_t max_particles;    /* per-particle ledger entries, >= 1             */
+  void* stream;             /* cudaStream_t for every launch; NULL = default */
+  int32_t block_size;       /* threads per block (0 = 256); multiple of 32   */
+  int32_t blocks_per_sm;    /* resident blocks per SM for the grid (0 = 4)   */
+} prad_config;
+
+/* ---- field description ------------------------------------------------- */
+typedef struct prad_fields {
+  int32_t kind;      /* prad_field_kind                                      */
+  int32_t dir;       /* PLANE_WAVE: +1 propagates along +x, -1 along -x      */
+  int32_t hand;      /* PLANE_WAVE: +1 / -1 handedness of the polarisation  */
+  int32_t periodic;  /* YEE2D: 1 = wrap positions and indices (only mode)    */
+  double E[3];       /* CONST: E [V/m]                                       */
+  double B[3];       /* CONST: B [T]                                         */
+  double a0;         /* PLANE_WAVE: normalised amplitude e E0 / (m c omega_L) */
+  double lambda;     /* PLANE_WAVE: wavelength [m]                           */
+  double phase0;     /* PLANE_WAVE: phase at t = 0, x = 0 [rad]              */
+  /* YEE2D: six device planes Ex Ey Ez Bx By Bz, float32, row-major [ny][nx],
+   * normalised (E in m c omega_ref / e, B in m omega_ref / e).  Staggering:
+   * Ex (i+1/2, j), Ey (i, j+1/2), Ez (i, j), Bx (i, j+1/2), By (i+1/2, j),
+   * Bz (i+1/2, j+1/2).  BORROWED: the caller keeps them alive and unchanged
+   * until the next prad_set_fields or prad_destroy. */
+  const float* yee[6];
+  int32_t nx, ny;    /* YEE2D grid size, >= 4 each                           */
+  double dx, dy;     /* YEE2D cell size [c/omega_ref]                        */
+  double x0, y0;     /* YEE2D position of node (0, 0) [c/omega_ref]          */
+} prad_fields;
+
+/* ---- particles ---------------------------------------------------------- */
+typedef struct prad_particles {
+  /* Device SoA arrays of n entries, float (FP32 precision) or double (FP64),
+   * advanced in place.  BORROWED for the duration of the call's kernels.
+   * x, y, ux, uy, uz, w are required; z may be NULL for YEE2D (2D3V).
+   * u holds u^{n-1/2} on entry and u^{n+nsteps-1/2} on return; w is the
+   * macro-particle weight (read only). */
+  void *x, *y, *z, *ux, *uy, *uz;
+  const void* w;
+  int64_t ledger_offset; /* ledger index of particle 0 (entries used:
+                            [ledger_offset, ledger_offset + n))          */
+  uint32_t pid0;         /* particle i has Philox counter word 0 = pid0+i */
+  uint32_t pad0;
+  int64_t t0;            /* global index of the first step (time t0*dt)  */
+} prad_particles;
+
+/* ---- photon records ------------------------------------------------------ */
+typedef struct prad_photons {
+  /* Caller-owned arrays of at least `cap` entries (float32 / uint32).
+   * Position x^{n+1} [c/omega_ref], unit direction of the emitting particle's
+   * mean velocity (collinear approximation), energy x hbar omega_c [m c^2],
+   * weight = multiplicity * macro weight, emitting particle id and step. */
+  float *x, *y, *z, *nx, *ny, *nz, *eps, *weight;
+  uint32_t *pid, *step;
+} prad_photons;
+
+typedef struct prad_stats {
+  int64_t records;      /* photon records written since init               */
+  int64_t dropped;      /* records lost to a full buffer since init        */
+  int64_t dn_gt1;       /* trials with dN > 1 (multiplicity > 1 possible)  */
+  int64_t clamped;      /* steps where dp_perp/p was limited to 1          */
+  int64_t chi_gt1;      /* steps with chi > 1 (outside classical validity) */
+  int64_t mlp_fallback; /* learned-sampler draws that fell back to table   */
+  int64_t nan_frozen;   /* particle-launches skipped as non-finite         */
+  int32_t status;       /* sticky device status word (0 = ok)              */
+  int32_t pad0;
+} prad_stats;
+
+typedef struct prad_ctx prad_ctx;
+
+/* Create a context on the current CUDA device: allocates the photon buffer
+ * (10 x 4 B x photon_capacity), the per-particle FP64 ledger
+ * (2 x 8 B x max_particles), the sampling tables, counters and reduction
+ * scratch.  *out receives the handle (NULL on error).  Follows the problem
+ * statement of the Numerical implementation section (emission per particle
+ * and step, photons as particles).  Errors: PRAD_ERR_ARG for a null pointer,
+ * a non-positive dt/omega_ref/capacity/max_particles or a bad enum;
+ * PRAD_ERR_CUDA if an allocation fails. */
+int prad_init(prad_ctx** out, const prad_config* cfg);
+
+/* Free everything the context allocated.  Safe on NULL. */
+int prad_destroy(prad_ctx* ctx);
+
+/* Message of the last failing call on ctx ("" if none).  With ctx == NULL,
+ * the message of the last failed prad_init of this thread. */
+const char* prad_last_error(const prad_ctx* ctx);
+
+/* Set the field model (the E, B that enter the Lorentz force and H_eff).
+ * Copies everything except the YEE2D planes, which are borrowed.
+ * Errors: PRAD_ERR_ARG (null, bad kind, bad sizes, misaligned planes). */
+int prad_set_fields(prad_ctx* ctx, const prad_fields* f);
+
+/* Advance n particles by nsteps steps in place, emitting photons.  Per
+ * particle and step, in order:
+ *   1. gather E, B at x^n, t^n;
+ *   2. Boris push u^{n-1/2} -> u^{n+1/2} (Numerical implementation section);
+ *   3. u_avg = (u^{n-1/2} + u^{n+1/2})/2 gives gamma and beta;
+ *   4. H_eff by the configured form, limited by Omega dt <= gamma
+ *      (dp_perp/p <= 1);
+ *   5. omega_c = (3/2) Omega gamma^2 (Eq. (1)), chi = (2/3) hbar omega_c /
+ *      (gamma m c^2);
+ *   6. LL ledger += w (2/3) alpha hbar Omega^2 gamma^2 beta^2 dt (Eq. (4));
+ *      rr_mode APPLY also scales u by 1/(1 + K gamma dt),
+ *      K = (2/3) alpha hbar Omega^2 / (m c^2);
+ *   7. x^{n+1} = x^n + dt u^{n+1/2}/gamma^{n+1/2};
+ *   8. x = P^-1(R') from the proposal of Eqs. (11)-(12);
+ *      dN = (sqrt3/2pi) alpha Omega dt F(x)/(x S(x)) (Eq. (13) per unit x);
+ *      k = floor(dN) + [R < frac(dN)];
+ *   9. if k > 0 and w > 0: append one record (weight k w, energy
+ *      x hbar omega_c) and add k w x hbar omega_c to the emit ledger.
+ * Records beyond the capacity are counted as dropped, never written.
+ * Errors: PRAD_ERR_ARG (null pointers, n < 0, nsteps < 0, ledger range
+ * outside max_particles, misaligned arrays), PRAD_ERR_STATE (no fields),
+ * PRAD_ERR_CUDA (launch failure).  n == 0 or nsteps == 0 is a no-op. */
+int prad_push_emit(prad_ctx* ctx, const prad_particles* p, int64_t n,
+                   int32_t nsteps);
+
+/* Copy up to `cap` photon records into `out` (device arrays if
+ * out_on_device, else host arrays; any pointer of out may be NULL to skip
+ * that field), in slot order (nondeterministic across runs: records carry
+ * pid and step).  *n_out receives the number of records held, *n_dropped
+ * the records lost since the last drain.  With drain != 0 the buffer is
+ * emptied afterwards.  cap may be 0 with out == NULL to query or drain only.
+ * Synchronises the context stream. */
+int prad_get_photons(prad_ctx* ctx, prad_photons* out, int64_t cap,
+                     int64_t* n_out, int64_t* n_dropped, int32_t drain,
+                     int32_t out_on_device);
+
+/* Totals of the per-particle ledgers over all max_particles entries, by a
+ * deterministic two-pass Kahan-compensated FP64 reduction on the device:
+ * *emitted = sum of k w x hbar omega_c, *rr_loss = sum of the LL loss, both
+ * in m c^2 (multiply by m_e c^2 for joules).  Either output may be NULL.
+ * s (may be NULL) receives the counters.  Synchronises the stream. */
+int prad_energy_budget(prad_ctx* ctx, double* emitted, double* rr_loss,
+                       prad_stats* s);
+
+/* Copy ledger entries [offset, offset + n) into emit/ll (device arrays if
+ * out_on_device, else host); either may be NULL.  Synchronises. */
+int prad_get_ledger(prad_ctx* ctx, double* emit, double* ll, int64_t offset,
+                    int64_t n, int32_t out_on_device);
+
+/* Zero the ledgers, counters and photon buffer. */
+int prad_reset(prad_ctx* ctx);
+
+/* ---- diagnostics (same device functions as the hot kernel) --------------- */
+
+/* Philox4x32-10 on n device counters (uint32 x 4 each) with key (k0, k1),
+ * writing n x 4 words to device `out`. */
+int prad_philox(prad_ctx* ctx, const uint32_t* ctr, uint32_t k0, uint32_t k1,
+                uint32_t* out, int64_t n);
+
+/* Run the sampler of step 8 on n Philox blocks (device uint32 x 4 each):
+ * x_out[i] = P^-1(R') and g_out[i] = F(x)/S(x) from the device table, in the
+ * context precision's type (float or double device arrays). */
+int prad_eval_sampler(prad_ctx* ctx, const uint32_t* words, void* x_out,
+                      void* g_out, int64_t n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PRAD_H */

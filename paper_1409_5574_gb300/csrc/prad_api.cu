@@ -1,0 +1,542 @@
+// Host side of the C ABI declared in include/prad.h: context management,
+// argument checking, normalisation of the SI problem description, the
+// sampling table, launches and read-back.  Compute happens only in kernels.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "prad_internal.h"
+
+using namespace prad;
+
+namespace {
+
+// ---- physical constants (CODATA 2018) -------------------------------------
+constexpr double kC = 299792458.0;
+constexpr double kQe = 1.602176634e-19;
+constexpr double kMe = 9.1093837015e-31;
+constexpr double kHbar = 1.054571817e-34;
+constexpr double kEps0 = 8.8541878128e-12;
+constexpr double kPi = 3.14159265358979323846;
+// Proposal constant of Eq. (11): root of a^(4/3) + (7/9) e^(-a) = 1.
+constexpr double kA = 0.69020670216845766;
+// round(a^(4/3) 2^64): 64-bit words W below it take the x < a branch.
+constexpr uint64_t kThr = 0x9C26B9CE251FFCB8ull;
+
+thread_local char g_init_err[512];
+
+}  // namespace
+
+struct prad_ctx {
+  prad_config cfg{};
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int num_sms = 1;
+  char err[512] = {0};
+  // normalised constants
+  double dtn = 0, alpha = 0, eps_r = 0;
+  // fields
+  prad_fields fields{};
+  bool fields_set = false;
+  // sampling tables
+  float4* d_tab32 = nullptr;
+  Coef4d* d_tab64 = nullptr;
+  // photon buffer (SoA)
+  float* d_ph[8] = {nullptr};
+  uint32_t* d_pid = nullptr;
+  uint32_t* d_step = nullptr;
+  // counters, ledgers, reduction scratch
+  unsigned long long* d_cnt = nullptr;
+  double* d_led_emit = nullptr;
+  double* d_led_ll = nullptr;
+  double* d_partials = nullptr;
+  double* d_sums = nullptr;
+  int red_blocks = 0;
+  // host-side totals folded in at each drain
+  int64_t drained_records = 0;
+  int64_t drained_dropped = 0;
+};
+
+namespace {
+
+int fail(prad_ctx* c, int code, const char* fmt, ...) {
+  char* dst = c ? c->err : g_init_err;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(dst, 512, fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+#define CK(ctx, call)                                                        \
+  do {                                                                       \
+    cudaError_t e_ = (call);                                                 \
+    if (e_ != cudaSuccess)                                                   \
+      return fail((ctx), PRAD_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+// ---- F(x) of Eq. (8) for the table ------------------------------------------
+// F(x) = x int_0^inf exp(-x cosh s) cosh(5 s / 3) / cosh(s) ds, by composite
+// 16-point Gauss-Legendre panels of width 1/2 up to where x cosh s > 720.
+struct GaussLegendre {
+  double x[16], w[16];
+  GaussLegendre() {
+    const int n = 16;
+    for (int i = 0; i < n; ++i) {
+      double z = std::cos(kPi * (i + 0.75) / (n + 0.5)), pp = 1.0;
+      for (int it = 0; it < 100; ++it) {
+        double p1 = 1.0, p2 = 0.0;
+        for (int j = 1; j <= n; ++j) {
+          const double p3 = p2;
+          p2 = p1;
+          p1 = ((2.0 * j - 1.0) * z * p2 - (j - 1.0) * p3) / j;
+        }
+        pp = n * (z * p1 - p2) / (z * z - 1.0);
+        const double dz = p1 / pp;
+        z -= dz;
+        if (std::fabs(dz) < 1e-16) break;
+      }
+      x[i] = z;
+      w[i] = 2.0 / ((1.0 - z * z) * pp * pp);
+    }
+  }
+};
+
+double synchrotron_F(double x, const GaussLegendre& gl) {
+  if (!(x > 0.0)) return 0.0;
+  const double smax = std::acosh(720.0 / x + 1.0);
+  const double width = 0.5;
+  double acc = 0.0;
+  for (double a = 0.0; a < smax; a += width) {
+    const double mid = a + 0.5 * width, half = 0.5 * width;
+    for (int k = 0; k < 16; ++k) {
+      const double s = mid + half * gl.x[k];
+      const double ch = std::cosh(s);
+      acc += half * gl.w[k] * std::exp(-x * ch) * std::cosh(5.0 * s / 3.0) / ch;
+    }
+  }
+  return x * acc;
+}
+
+// g = F / S on each branch of the proposal, Eq. (11).
+double g_low(double t, const GaussLegendre& gl) {  // x = t^3 < a
+  if (t <= 0.0) {
+    // lim F(x) / ((4/3) x^(1/3)) = (3/4) 4 pi / (sqrt3 Gamma(1/3)) 2^(-1/3)
+    return 0.75 * 4.0 * kPi / (std::sqrt(3.0) * std::tgamma(1.0 / 3.0)) *
+           std::cbrt(0.5);
+  }
+  const double x = t * t * t;
+  return synchrotron_F(x, gl) / ((4.0 / 3.0) * t);
+}
+double g_high(double x, const GaussLegendre& gl) {  // x >= a
+  return synchrotron_F(x, gl) * std::exp(x) * (9.0 / 7.0);
+}
+
+// Per-interval cubic through g at s = 0, 1/3, 2/3, 1 (Newton forward form
+// expanded to monomials in s).
+void cubic_coefs(double f0, double f1, double f2, double f3, double c[4]) {
+  const double d1 = f1 - f0;
+  const double d2 = f2 - 2.0 * f1 + f0;
+  const double d3 = f3 - 3.0 * f2 + 3.0 * f1 - f0;
+  c[0] = f0;
+  c[1] = 3.0 * d1 - 1.5 * d2 + d3;
+  c[2] = 4.5 * d2 - 4.5 * d3;
+  c[3] = 4.5 * d3;
+}
+
+void build_tables(std::vector<float4>& t32, std::vector<Coef4d>& t64) {
+  GaussLegendre gl;
+  t32.resize(kNTab);
+  t64.resize(kNTab);
+  const double T1 = std::cbrt(kA);
+  for (int i = 0; i < kNTab; ++i) {
+    double v[4];
+    for (int k = 0; k < 4; ++k) {
+      if (i < kN1) {
+        const double t = (i + k / 3.0) * T1 / kN1;
+        v[k] = g_low(t, gl);
+      } else {
+        const int j = i - kN1;
+        const double x = kA + (j + k / 3.0) * (kXmax - kA) / kN2;
+        v[k] = g_high(x, gl);
+      }
+    }
+    double c[4];
+    cubic_coefs(v[0], v[1], v[2], v[3], c);
+    t64[i] = Coef4d{c[0], c[1], c[2], c[3]};
+    t32[i] = make_float4(static_cast<float>(c[0]), static_cast<float>(c[1]),
+                         static_cast<float>(c[2]), static_cast<float>(c[3]));
+  }
+}
+
+template <typename R>
+void fill_common(const prad_ctx* c, StepParams<R>& p) {
+  const double q = c->cfg.charge;
+  const double dtn = c->dtn;
+  p.half_q_dtn = static_cast<R>(0.5 * q * dtn);
+  p.dtn = static_cast<R>(dtn);
+  p.inv_dtn = static_cast<R>(1.0 / dtn);
+  p.abs_q = static_cast<R>(std::fabs(q));
+  p.cn_dt = static_cast<R>(std::sqrt(3.0) / (2.0 * kPi) * c->alpha * dtn);
+  p.eps_r = static_cast<R>(c->eps_r);
+  p.eps_r15 = static_cast<R>(1.5 * c->eps_r);
+  p.ll_coef = static_cast<R>(2.0 / 3.0 * c->alpha * c->eps_r * dtn);
+  p.rr_mode = c->cfg.rr_mode;
+  p.heff_form = c->cfg.heff_form;
+  p.ensemble = c->cfg.ensemble;
+  p.key0 = static_cast<uint32_t>(c->cfg.seed & 0xffffffffull);
+  p.key1 = static_cast<uint32_t>(c->cfg.seed >> 32);
+  p.t_scale = static_cast<R>(kN1 / std::cbrt(kA));
+  p.x_scale = static_cast<R>(kN2 / (kXmax - kA));
+  p.a = static_cast<R>(kA);
+  p.thr = kThr;
+  if constexpr (sizeof(R) == 4)
+    p.tab = c->d_tab32;
+  else
+    p.tab = c->d_tab64;
+  p.px = c->d_ph[0]; p.py = c->d_ph[1]; p.pz = c->d_ph[2];
+  p.pnx = c->d_ph[3]; p.pny = c->d_ph[4]; p.pnz = c->d_ph[5];
+  p.peps = c->d_ph[6]; p.pw = c->d_ph[7];
+  p.ppid = c->d_pid; p.pstep = c->d_step;
+  p.cap = c->cfg.photon_capacity;
+  p.counters = c->d_cnt;
+  // field, normalised: E by m c omega_ref / e, B by m omega_ref / e
+  const prad_fields& f = c->fields;
+  const double w = c->cfg.omega_ref;
+  const double Er = kMe * kC * w / kQe, Br = kMe * w / kQe;
+  for (int k = 0; k < 3; ++k) {
+    p.E[k] = static_cast<R>(f.E[k] / Er);
+    p.B[k] = static_cast<R>(f.B[k] / Br);
+  }
+  p.dims = 3;
+  if (f.kind == PRAD_FIELD_PLANE_WAVE) {
+    const double wn = (2.0 * kPi * kC / f.lambda) / w;  // omega_L / omega_ref
+    p.E0 = static_cast<R>(f.a0 * wn);
+    p.kc = static_cast<R>(f.dir * wn / (2.0 * kPi));
+    p.hand = static_cast<R>(f.hand);
+    p.dir = static_cast<R>(f.dir);
+    // fixed-point cycles: phase0 / 2pi and omega_L dt / 2pi, modulo 1
+    long double c0 = static_cast<long double>(f.phase0) / (2.0L * kPi);
+    c0 -= std::floor(c0);
+    long double cs = static_cast<long double>(wn) * dtn / (2.0L * kPi);
+    cs -= std::floor(cs);
+    p.phase_t0 = static_cast<uint64_t>(std::ldexp(c0, 64));
+    p.phase_step = static_cast<uint64_t>(std::ldexp(cs, 64));
+  } else {
+    p.E0 = p.kc = p.hand = p.dir = R(0);
+    p.phase_t0 = p.phase_step = 0;
+  }
+  if (f.kind == PRAD_FIELD_YEE2D) {
+    for (int k = 0; k < 6; ++k) p.yee[k] = f.yee[k];
+    p.nx = f.nx; p.ny = f.ny;
+    p.inv_dx = static_cast<R>(1.0 / f.dx);
+    p.inv_dy = static_cast<R>(1.0 / f.dy);
+    p.x0 = static_cast<R>(f.x0);
+    p.y0 = static_cast<R>(f.y0);
+    p.Lx = static_cast<R>(f.nx * f.dx);
+    p.Ly = static_cast<R>(f.ny * f.dy);
+    p.dims = 2;
+  } else {
+    for (int k = 0; k < 6; ++k) p.yee[k] = nullptr;
+    p.nx = p.ny = 0;
+    p.inv_dx = p.inv_dy = p.x0 = p.y0 = p.Lx = p.Ly = R(0);
+  }
+}
+
+bool aligned(const void* p, size_t a) {
+  return (reinterpret_cast<uintptr_t>(p) % a) == 0;
+}
+
+template <typename R>
+int push_emit_t(prad_ctx* c, const prad_particles* pp, int64_t n,
+                int32_t nsteps) {
+  StepParams<R> p{};
+  fill_common<R>(c, p);
+  const void* arrs[6] = {pp->x, pp->y, pp->ux, pp->uy, pp->uz, pp->w};
+  for (const void* a : arrs)
+    if (!a || !aligned(a, sizeof(R)))
+      return fail(c, PRAD_ERR_ARG, "push_emit: null or misaligned particle array");
+  if (pp->z && !aligned(pp->z, sizeof(R)))
+    return fail(c, PRAD_ERR_ARG, "push_emit: misaligned z");
+  if (!pp->z && c->fields.kind != PRAD_FIELD_YEE2D)
+    return fail(c, PRAD_ERR_ARG, "push_emit: z may be NULL only for YEE2D");
+  p.x = static_cast<R*>(pp->x); p.y = static_cast<R*>(pp->y);
+  p.z = static_cast<R*>(pp->z);
+  p.ux = static_cast<R*>(pp->ux); p.uy = static_cast<R*>(pp->uy);
+  p.uz = static_cast<R*>(pp->uz);
+  p.w = static_cast<const R*>(pp->w);
+  p.led_emit = c->d_led_emit + pp->ledger_offset;
+  p.led_ll = c->d_led_ll + pp->ledger_offset;
+  p.n = n;
+  p.pid0 = pp->pid0;
+  const int block = c->cfg.block_size > 0 ? c->cfg.block_size : 256;
+  const int bps = c->cfg.blocks_per_sm > 0 ? c->cfg.blocks_per_sm : 4;
+  const int64_t want = (n + block - 1) / block;
+  const int64_t cap = static_cast<int64_t>(c->num_sms) * bps;
+  const int grid = static_cast<int>(want < cap ? want : cap);
+  const int sub = c->cfg.steps_per_launch > 0 ? c->cfg.steps_per_launch : 1;
+  const uint64_t phase0 = p.phase_t0;
+  for (int32_t done = 0; done < nsteps;) {
+    const int32_t m = (nsteps - done) < sub ? (nsteps - done) : sub;
+    p.t0 = pp->t0 + done;
+    p.nsub = m;
+    // wave phase at the launch's first step (modulo one cycle)
+    p.phase_t0 = phase0 + static_cast<uint64_t>(p.t0) * p.phase_step;
+    CK(c, launch_push_emit<R>(p, c->fields.kind, grid, block, c->stream));
+    done += m;
+  }
+  return PRAD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int prad_init(prad_ctx** out, const prad_config* cfg) {
+  if (!out || !cfg) return fail(nullptr, PRAD_ERR_ARG, "prad_init: null argument");
+  *out = nullptr;
+  if (!(cfg->dt > 0.0) || !(cfg->omega_ref > 0.0))
+    return fail(nullptr, PRAD_ERR_ARG, "prad_init: dt and omega_ref must be > 0");
+  if (cfg->photon_capacity < 1 || cfg->max_particles < 1)
+    return fail(nullptr, PRAD_ERR_ARG,
+                "prad_init: photon_capacity and max_particles must be >= 1");
+  if (cfg->precision != PRAD_FP32 && cfg->precision != PRAD_FP64)
+    return fail(nullptr, PRAD_ERR_ARG, "prad_init: bad precision");
+  if (cfg->sampler != PRAD_SAMPLER_TABLE)
+    return fail(nullptr, PRAD_ERR_ARG, "prad_init: sampler not available in this build");
+  if (cfg->rr_mode < PRAD_RR_OFF || cfg->rr_mode > PRAD_RR_APPLY)
+    return fail(nullptr, PRAD_ERR_ARG, "prad_init: bad rr_mode");
+  if (cfg->heff_form != PRAD_HEFF_FIELD && cfg->heff_form != PRAD_HEFF_MOMENTUM)
+    return fail(nullptr, PRAD_ERR_ARG, "prad_init: bad heff_form");
+  if (cfg->charge != 1.0 && cfg->charge != -1.0)
+    return fail(nullptr, PRAD_ERR_ARG, "prad_init: charge must be +1 or -1");
+  if (cfg->block_size < 0 || cfg->block_size > 256 || (cfg->block_size % 32) != 0)
+    return fail(nullptr, PRAD_ERR_ARG, "prad_init: block_size must be a multiple of 32 <= 256");
+  if (cfg->steps_per_launch < 0 || cfg->blocks_per_sm < 0)
+    return fail(nullptr, PRAD_ERR_ARG, "prad_init: negative launch parameter");
+
+  prad_ctx* c = new (std::nothrow) prad_ctx();
+  if (!c) return fail(nullptr, PRAD_ERR_ARG, "prad_init: out of host memory");
+  c->cfg = *cfg;
+  c->stream = static_cast<cudaStream_t>(cfg->stream);
+  auto bail = [&](int code) {
+    std::snprintf(g_init_err, sizeof(g_init_err), "%s", c->err);
+    prad_destroy(c);
+    return code;
+  };
+#define CKI(call)                                                         \
+  do {                                                                    \
+    cudaError_t e_ = (call);                                              \
+    if (e_ != cudaSuccess) {                                              \
+      fail(c, PRAD_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_));    \
+      return bail(PRAD_ERR_CUDA);                                         \
+    }                                                                     \
+  } while (0)
+  CKI(cudaGetDevice(&c->device));
+  CKI(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
+  c->dtn = cfg->dt * cfg->omega_ref;
+  c->alpha = kQe * kQe / (4.0 * kPi * kEps0 * kHbar * kC);
+  c->eps_r = kHbar * cfg->omega_ref / (kMe * kC * kC);
+
+  std::vector<float4> t32;
+  std::vector<Coef4d> t64;
+  build_tables(t32, t64);
+  CKI(cudaMalloc(&c->d_tab32, kNTab * sizeof(float4)));
+  CKI(cudaMalloc(&c->d_tab64, kNTab * sizeof(Coef4d)));
+  CKI(cudaMemcpy(c->d_tab32, t32.data(), kNTab * sizeof(float4), cudaMemcpyHostToDevice));
+  CKI(cudaMemcpy(c->d_tab64, t64.data(), kNTab * sizeof(Coef4d), cudaMemcpyHostToDevice));
+
+  const size_t cap = static_cast<size_t>(cfg->photon_capacity);
+  for (int k = 0; k < 8; ++k) CKI(cudaMalloc(&c->d_ph[k], cap * sizeof(float)));
+  CKI(cudaMalloc(&c->d_pid, cap * sizeof(uint32_t)));
+  CKI(cudaMalloc(&c->d_step, cap * sizeof(uint32_t)));
+  CKI(cudaMalloc(&c->d_cnt, kNumCounters * sizeof(unsigned long long)));
+  CKI(cudaMemset(c->d_cnt, 0, kNumCounters * sizeof(unsigned long long)));
+  const size_t np = static_cast<size_t>(cfg->max_particles);
+  CKI(cudaMalloc(&c->d_led_emit, np * sizeof(double)));
+  CKI(cudaMalloc(&c->d_led_ll, np * sizeof(double)));
+  CKI(cudaMemset(c->d_led_emit, 0, np * sizeof(double)));
+  CKI(cudaMemset(c->d_led_ll, 0, np * sizeof(double)));
+  c->red_blocks = 2 * c->num_sms;
+  CKI(cudaMalloc(&c->d_partials, 4 * c->red_blocks * sizeof(double)));
+  CKI(cudaMalloc(&c->d_sums, 2 * sizeof(double)));
+  CKI(cudaDeviceSynchronize());
+#undef CKI
+  *out = c;
+  return PRAD_OK;
+}
+
+int prad_destroy(prad_ctx* c) {
+  if (!c) return PRAD_OK;
+  cudaFree(c->d_tab32);
+  cudaFree(c->d_tab64);
+  for (int k = 0; k < 8; ++k) cudaFree(c->d_ph[k]);
+  cudaFree(c->d_pid);
+  cudaFree(c->d_step);
+  cudaFree(c->d_cnt);
+  cudaFree(c->d_led_emit);
+  cudaFree(c->d_led_ll);
+  cudaFree(c->d_partials);
+  cudaFree(c->d_sums);
+  delete c;
+  return PRAD_OK;
+}
+
+const char* prad_last_error(const prad_ctx* c) { return c ? c->err : g_init_err; }
+
+int prad_set_fields(prad_ctx* c, const prad_fields* f) {
+  if (!c || !f) return fail(c, PRAD_ERR_ARG, "set_fields: null argument");
+  if (f->kind == PRAD_FIELD_CONST) {
+    // nothing to check
+  } else if (f->kind == PRAD_FIELD_PLANE_WAVE) {
+    if (!(f->lambda > 0.0) || (f->dir != 1 && f->dir != -1) ||
+        (f->hand != 1 && f->hand != -1))
+      return fail(c, PRAD_ERR_ARG, "set_fields: plane wave needs lambda > 0, dir and hand = +-1");
+  } else if (f->kind == PRAD_FIELD_YEE2D) {
+    if (f->nx < 4 || f->ny < 4 || !(f->dx > 0.0) || !(f->dy > 0.0))
+      return fail(c, PRAD_ERR_ARG, "set_fields: Yee grid needs nx, ny >= 4 and dx, dy > 0");
+    if (static_cast<int64_t>(f->nx) * f->ny > (int64_t(1) << 31))
+      return fail(c, PRAD_ERR_ARG, "set_fields: Yee grid larger than 2^31 cells");
+    for (int k = 0; k < 6; ++k)
+      if (!f->yee[k] || !aligned(f->yee[k], 4))
+        return fail(c, PRAD_ERR_ARG, "set_fields: null or misaligned Yee plane %d", k);
+  } else {
+    return fail(c, PRAD_ERR_ARG, "set_fields: bad kind %d", f->kind);
+  }
+  c->fields = *f;
+  c->fields_set = true;
+  return PRAD_OK;
+}
+
+int prad_push_emit(prad_ctx* c, const prad_particles* p, int64_t n, int32_t nsteps) {
+  if (!c || !p) return fail(c, PRAD_ERR_ARG, "push_emit: null argument");
+  if (n < 0 || nsteps < 0) return fail(c, PRAD_ERR_ARG, "push_emit: negative size");
+  if (!c->fields_set) return fail(c, PRAD_ERR_STATE, "push_emit: fields not set");
+  if (n == 0 || nsteps == 0) return PRAD_OK;
+  if (n > (int64_t(1) << 32))
+    return fail(c, PRAD_ERR_ARG, "push_emit: more than 2^32 particles in one call");
+  if (p->ledger_offset < 0 || p->ledger_offset + n > c->cfg.max_particles)
+    return fail(c, PRAD_ERR_ARG, "push_emit: ledger range [%lld, %lld) outside max_particles %lld",
+                (long long)p->ledger_offset, (long long)(p->ledger_offset + n),
+                (long long)c->cfg.max_particles);
+  if (p->t0 < 0 || p->t0 + nsteps > (int64_t(1) << 32))
+    return fail(c, PRAD_ERR_ARG, "push_emit: step index outside [0, 2^32)");
+  if (c->cfg.precision == PRAD_FP32) return push_emit_t<float>(c, p, n, nsteps);
+  return push_emit_t<double>(c, p, n, nsteps);
+}
+
+int prad_get_photons(prad_ctx* c, prad_photons* out, int64_t cap, int64_t* n_out,
+                     int64_t* n_dropped, int32_t drain, int32_t out_on_device) {
+  if (!c) return fail(c, PRAD_ERR_ARG, "get_photons: null context");
+  if (cap < 0) return fail(c, PRAD_ERR_ARG, "get_photons: negative cap");
+  if (cap > 0 && !out) return fail(c, PRAD_ERR_ARG, "get_photons: null output");
+  unsigned long long cursor = 0;
+  CK(c, cudaMemcpyAsync(&cursor, c->d_cnt + kCursor, sizeof(cursor),
+                        cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  const int64_t capd = c->cfg.photon_capacity;
+  const int64_t held = static_cast<int64_t>(cursor) < capd ? static_cast<int64_t>(cursor) : capd;
+  const int64_t dropped = static_cast<int64_t>(cursor) > capd ? static_cast<int64_t>(cursor) - capd : 0;
+  const int64_t m = held < cap ? held : cap;
+  if (m > 0) {
+    const cudaMemcpyKind kind = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    float* dst[8] = {out->x, out->y, out->z, out->nx, out->ny, out->nz, out->eps, out->weight};
+    for (int k = 0; k < 8; ++k)
+      if (dst[k]) CK(c, cudaMemcpyAsync(dst[k], c->d_ph[k], m * sizeof(float), kind, c->stream));
+    if (out->pid) CK(c, cudaMemcpyAsync(out->pid, c->d_pid, m * sizeof(uint32_t), kind, c->stream));
+    if (out->step) CK(c, cudaMemcpyAsync(out->step, c->d_step, m * sizeof(uint32_t), kind, c->stream));
+  }
+  if (drain) {
+    CK(c, cudaMemsetAsync(c->d_cnt + kCursor, 0, sizeof(unsigned long long), c->stream));
+    c->drained_records += held;
+    c->drained_dropped += dropped;
+  }
+  CK(c, cudaStreamSynchronize(c->stream));
+  if (n_out) *n_out = held;
+  if (n_dropped) *n_dropped = dropped;
+  return PRAD_OK;
+}
+
+int prad_energy_budget(prad_ctx* c, double* emitted, double* rr_loss, prad_stats* s) {
+  if (!c) return fail(c, PRAD_ERR_ARG, "energy_budget: null context");
+  CK(c, launch_ledger_reduce(c->d_led_emit, c->d_led_ll, c->cfg.max_particles,
+                             c->d_partials, c->red_blocks, c->d_sums, c->stream));
+  double sums[2];
+  unsigned long long cnt[kNumCounters];
+  CK(c, cudaMemcpyAsync(sums, c->d_sums, sizeof(sums), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaMemcpyAsync(cnt, c->d_cnt, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  if (emitted) *emitted = sums[0];
+  if (rr_loss) *rr_loss = sums[1];
+  if (s) {
+    const int64_t capd = c->cfg.photon_capacity;
+    const int64_t cur = static_cast<int64_t>(cnt[kCursor]);
+    s->records = c->drained_records + (cur < capd ? cur : capd);
+    s->dropped = c->drained_dropped + (cur > capd ? cur - capd : 0);
+    s->dn_gt1 = static_cast<int64_t>(cnt[kDnGt1]);
+    s->clamped = static_cast<int64_t>(cnt[kClamp]);
+    s->chi_gt1 = static_cast<int64_t>(cnt[kChiGt1]);
+    s->nan_frozen = static_cast<int64_t>(cnt[kNan]);
+    s->mlp_fallback = static_cast<int64_t>(cnt[kMlpFallback]);
+    s->status = static_cast<int32_t>(cnt[kStatus]);
+    s->pad0 = 0;
+  }
+  return s && s->nan_frozen > 0 ? PRAD_WARN_NAN : PRAD_OK;
+}
+
+int prad_get_ledger(prad_ctx* c, double* emit, double* ll, int64_t offset, int64_t n,
+                    int32_t out_on_device) {
+  if (!c) return fail(c, PRAD_ERR_ARG, "get_ledger: null context");
+  if (offset < 0 || n < 0 || offset + n > c->cfg.max_particles)
+    return fail(c, PRAD_ERR_ARG, "get_ledger: range outside max_particles");
+  const cudaMemcpyKind kind = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (emit && n) CK(c, cudaMemcpyAsync(emit, c->d_led_emit + offset, n * sizeof(double), kind, c->stream));
+  if (ll && n) CK(c, cudaMemcpyAsync(ll, c->d_led_ll + offset, n * sizeof(double), kind, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  return PRAD_OK;
+}
+
+int prad_reset(prad_ctx* c) {
+  if (!c) return fail(c, PRAD_ERR_ARG, "reset: null context");
+  const size_t np = static_cast<size_t>(c->cfg.max_particles);
+  CK(c, cudaMemsetAsync(c->d_led_emit, 0, np * sizeof(double), c->stream));
+  CK(c, cudaMemsetAsync(c->d_led_ll, 0, np * sizeof(double), c->stream));
+  CK(c, cudaMemsetAsync(c->d_cnt, 0, kNumCounters * sizeof(unsigned long long), c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  c->drained_records = c->drained_dropped = 0;
+  return PRAD_OK;
+}
+
+int prad_philox(prad_ctx* c, const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* out,
+                int64_t n) {
+  if (!c || (n > 0 && (!ctr || !out)) || n < 0) return fail(c, PRAD_ERR_ARG, "philox: bad argument");
+  if (n == 0) return PRAD_OK;
+  CK(c, launch_philox(ctr, k0, k1, out, n, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  return PRAD_OK;
+}
+
+int prad_eval_sampler(prad_ctx* c, const uint32_t* words, void* x_out, void* g_out, int64_t n) {
+  if (!c || (n > 0 && (!words || !x_out || !g_out)) || n < 0)
+    return fail(c, PRAD_ERR_ARG, "eval_sampler: bad argument");
+  if (n == 0) return PRAD_OK;
+  if (c->cfg.precision == PRAD_FP32) {
+    StepParams<float> p{};
+    fill_common<float>(c, p);
+    CK(c, launch_eval_sampler<float>(p, words, static_cast<float*>(x_out),
+                                     static_cast<float*>(g_out), n, c->stream));
+  } else {
+    StepParams<double> p{};
+    fill_common<double>(c, p);
+    CK(c, launch_eval_sampler<double>(p, words, static_cast<double*>(x_out),
+                                      static_cast<double*>(g_out), n, c->stream));
+  }
+  CK(c, cudaStreamSynchronize(c->stream));
+  return PRAD_OK;
+}
+
+}  // extern "C"

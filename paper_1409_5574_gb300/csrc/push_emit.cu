@@ -1,0 +1,481 @@
+// Fused per-step particle kernel: field gather, Boris push, effective field,
+// omega_c, Monte Carlo synchrotron emission with the S(x) proposal, photon
+// append and the FP64 emitted-energy / Landau-Lifshitz ledger
+// (arXiv:1409.5574, Numerical implementation section, Eqs. (1), (4), (7)-(13)).
+//
+// One thread owns one particle for `nsub` consecutive steps; its state stays
+// in registers between substeps and is read and written once per launch
+// (SoA, fully coalesced 4- or 8-byte accesses).  The grid is a multiple of the
+// SM count and strides over the particles.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "prad_internal.h"
+
+namespace prad {
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11), written from the published
+// definition: ten rounds of two 32x32->64 multiplies and xors, key bumped by
+// the Weyl constants after every round.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// ---- precision-generic helpers --------------------------------------------
+__device__ __forceinline__ float rsq(float v) { return rsqrtf(v); }
+__device__ __forceinline__ double rsq(double v) { return rsqrt(v); }
+__device__ __forceinline__ float rcp(float v) { return __fdividef(1.0f, v); }
+__device__ __forceinline__ double rcp(double v) { return 1.0 / v; }
+__device__ __forceinline__ float sqr(float v) { return sqrtf(v); }
+__device__ __forceinline__ double sqr(double v) { return sqrt(v); }
+__device__ __forceinline__ float flr(float v) { return floorf(v); }
+__device__ __forceinline__ double flr(double v) { return floor(v); }
+__device__ __forceinline__ float rnd_int(float v) { return rintf(v); }
+__device__ __forceinline__ double rnd_int(double v) { return rint(v); }
+__device__ __forceinline__ void sincos_pi(float v, float* s, float* c) {
+  sincospif(v, s, c);
+}
+__device__ __forceinline__ void sincos_pi(double v, double* s, double* c) {
+  sincospi(v, s, c);
+}
+
+// ---------------------------------------------------------------------------
+// Step 8 sampler.  From one Philox block: the proposal frequency
+// x = P^-1(R') of Eqs. (11)-(12) and g = F(x) / S(x) from the table.
+//   W = w1 2^32 + w0;  R' = (W + 1/2) 2^-64;  1 - R' = (~W + 1/2) 2^-64.
+//   low branch  (W < thr, i.e. R' < a^(4/3)):  x = R'^(3/4),  t = R'^(1/4)
+//   high branch:                               x = -ln((9/7)(1 - R'))
+// The branch is an integer compare, identical in every precision.  Both
+// branches share one log2, so the warp does not diverge.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void sample_x_g(const StepParams<float>& P,
+                                           uint32_t w0, uint32_t w1, float& x,
+                                           float& g) {
+  const uint64_t W = (static_cast<uint64_t>(w1) << 32) | w0;
+  const bool low = W < P.thr;
+  const uint32_t h = low ? w1 : ~w1;
+  const uint32_t l = low ? w0 : ~w0;
+  // (h 2^32 + l + 1/2) 2^-64, never zero
+  const float arg = fmaf(static_cast<float>(h), 0x1p-32f,
+                         fmaf(static_cast<float>(l), 0x1p-64f, 0x1p-65f));
+  const float L = __log2f(arg);
+  const float t = exp2f(0.25f * L);
+  const float x_lo = t * t * t;
+  const float x_hi = fmaf(-L, 0.69314718055994531f, -0.25131442828090608f);
+  x = low ? x_lo : x_hi;
+  const float u = low ? t * P.t_scale : (x_hi - P.a) * P.x_scale;
+  int i = static_cast<int>(fmaxf(u, 0.0f));
+  const int nmax = low ? kN1 - 1 : kN2 - 1;
+  i = min(i, nmax);
+  const float s = u - static_cast<float>(i);
+  const float4 c = __ldg(P.tab + (low ? i : kN1 + i));
+  g = fmaf(s, fmaf(s, fmaf(s, c.w, c.z), c.y), c.x);
+}
+
+__device__ __forceinline__ void sample_x_g(const StepParams<double>& P,
+                                           uint32_t w0, uint32_t w1, double& x,
+                                           double& g) {
+  const uint64_t W = (static_cast<uint64_t>(w1) << 32) | w0;
+  const bool low = W < P.thr;
+  double u;
+  if (low) {
+    const double Rp = fma(static_cast<double>(W), 0x1p-64, 0x1p-65);
+    const double L = log2(Rp);
+    const double t = exp2(0.25 * L);
+    x = exp2(0.75 * L);
+    u = t * P.t_scale;
+  } else {
+    const double om = fma(static_cast<double>(~W), 0x1p-64, 0x1p-65);
+    x = -(log(om) + 0.25131442828090608);
+    u = (x - P.a) * P.x_scale;
+  }
+  int i = static_cast<int>(fmax(u, 0.0));
+  i = min(i, low ? kN1 - 1 : kN2 - 1);
+  const double s = u - static_cast<double>(i);
+  const Coef4d c = P.tab[low ? i : kN1 + i];
+  g = fma(s, fma(s, fma(s, c.c3, c.c2), c.c1), c.c0);
+}
+
+// ---------------------------------------------------------------------------
+// Step 1 field gather.
+// ---------------------------------------------------------------------------
+template <typename R>
+struct EB {
+  R Ex, Ey, Ez, Bx, By, Bz;
+};
+
+// Circularly polarised plane wave along dir * x (unit c):
+//   E = E0 (0, cos phi, hand sin phi),  B = dir x_hat x E,
+//   phi = omega t - dir k x + phase0.
+// The time part of the phase is a 64-bit fixed-point fraction of a cycle
+// (exact modular arithmetic), so only the x k term carries rounding.
+template <typename R>
+__device__ __forceinline__ EB<R> plane_wave(const StepParams<R>& P, R x,
+                                            uint64_t phase) {
+  R psi_t;
+  if constexpr (sizeof(R) == 4)
+    psi_t = static_cast<float>(static_cast<uint32_t>(phase >> 32)) * 0x1p-32f;
+  else
+    psi_t = static_cast<double>(phase >> 11) * 0x1p-53;
+  R psi = psi_t - P.kc * x;
+  psi -= rnd_int(psi);
+  R s, c;
+  sincos_pi(psi + psi, &s, &c);
+  EB<R> f;
+  f.Ex = R(0);
+  f.Ey = P.E0 * c;
+  f.Ez = P.hand * P.E0 * s;
+  f.Bx = R(0);
+  f.By = -P.dir * f.Ez;
+  f.Bz = P.dir * f.Ey;
+  return f;
+}
+
+// Quadratic-spline (second-order) weights about the nearest node.
+template <typename R>
+__device__ __forceinline__ int qs_weights(R xi, R w[3]) {
+  const R nr = flr(xi + R(0.5));
+  const R d = xi - nr;
+  w[0] = R(0.5) * (R(0.5) - d) * (R(0.5) - d);
+  w[1] = R(0.75) - d * d;
+  w[2] = R(0.5) * (R(0.5) + d) * (R(0.5) + d);
+  return static_cast<int>(nr);
+}
+
+template <typename R>
+__device__ __forceinline__ R yee_component(const StepParams<R>& P,
+                                           const float* __restrict__ F, R xi,
+                                           R yi) {
+  R wx[3], wy[3];
+  int i0 = qs_weights(xi, wx) - 1;
+  int j0 = qs_weights(yi, wy) - 1;
+  // periodic indices of the 3 x 3 stencil
+  int ii[3], jj[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    int i = i0 + k, j = j0 + k;
+    i = i < 0 ? i + P.nx : (i >= P.nx ? i - P.nx : i);
+    j = j < 0 ? j + P.ny : (j >= P.ny ? j - P.ny : j);
+    ii[k] = i;
+    jj[k] = j;
+  }
+  R v = R(0);
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    const float* row = F + static_cast<size_t>(jj[b]) * P.nx;
+    R r = wx[0] * R(__ldg(row + ii[0])) + wx[1] * R(__ldg(row + ii[1])) +
+          wx[2] * R(__ldg(row + ii[2]));
+    v += wy[b] * r;
+  }
+  return v;
+}
+
+// 2D Yee grid: Ex (i+1/2, j), Ey (i, j+1/2), Ez (i, j), Bx (i, j+1/2),
+// By (i+1/2, j), Bz (i+1/2, j+1/2).
+template <typename R>
+__device__ __forceinline__ R wrap_cells(R xi, int n) {
+  // periodic image in [0, n]; the clamp also maps NaN and huge values into
+  // range, so every stencil index below stays inside [-1, n + 1]
+  const R nr = static_cast<R>(n);
+  xi -= nr * flr(xi * (R(1) / nr));
+  return fmin(fmax(xi, R(0)), nr);
+}
+
+template <typename R>
+__device__ __forceinline__ EB<R> yee2d(const StepParams<R>& P, R x, R y) {
+  const R xi = wrap_cells((x - P.x0) * P.inv_dx, P.nx);
+  const R yi = wrap_cells((y - P.y0) * P.inv_dy, P.ny);
+  const R h = R(0.5);
+  EB<R> f;
+  f.Ex = yee_component(P, P.yee[0], xi - h, yi);
+  f.Ey = yee_component(P, P.yee[1], xi, yi - h);
+  f.Ez = yee_component(P, P.yee[2], xi, yi);
+  f.Bx = yee_component(P, P.yee[3], xi, yi - h);
+  f.By = yee_component(P, P.yee[4], xi - h, yi);
+  f.Bz = yee_component(P, P.yee[5], xi - h, yi - h);
+  return f;
+}
+
+template <typename R, int FIELD>
+__device__ __forceinline__ EB<R> gather(const StepParams<R>& P, R x, R y,
+                                        uint64_t phase) {
+  if constexpr (FIELD == PRAD_FIELD_CONST) {
+    EB<R> f;
+    f.Ex = P.E[0]; f.Ey = P.E[1]; f.Ez = P.E[2];
+    f.Bx = P.B[0]; f.By = P.B[1]; f.Bz = P.B[2];
+    return f;
+  } else if constexpr (FIELD == PRAD_FIELD_PLANE_WAVE) {
+    return plane_wave(P, x, phase);
+  } else {
+    return yee2d(P, x, y);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Warp-aggregated photon append: one atomicAdd per warp reserves a
+// contiguous run of slots; each emitting lane writes its record.  Slots at or
+// beyond the capacity are not written (they count as dropped on the host:
+// dropped = cursor - capacity).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void append_photon(
+    float* px, float* py, float* pz, float* pnx,
+    float* pny, float* pnz, float* peps, float* pw, uint32_t* ppid,
+    uint32_t* pstep, int64_t cap, unsigned long long* cursor, bool want,
+    float X, float Y, float Z, float NX, float NY, float NZ, float EPS,
+    float WT, uint32_t pid, uint32_t step) {
+  const unsigned mask = __ballot_sync(0xffffffffu, want);
+  if (mask == 0u) return;
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(mask) - 1;
+  unsigned long long base = 0ull;
+  if (lane == leader) base = atomicAdd(cursor, static_cast<unsigned long long>(__popc(mask)));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (want) {
+    const unsigned long long slot =
+        base + static_cast<unsigned>(__popc(mask & ((1u << lane) - 1u)));
+    if (slot < static_cast<unsigned long long>(cap)) {
+      px[slot] = X; py[slot] = Y; pz[slot] = Z;
+      pnx[slot] = NX; pny[slot] = NY; pnz[slot] = NZ;
+      peps[slot] = EPS; pw[slot] = WT;
+      ppid[slot] = pid; pstep[slot] = step;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The fused kernel.
+// ---------------------------------------------------------------------------
+template <typename R, int FIELD>
+__global__ void __launch_bounds__(256) k_push_emit(const StepParams<R> P) {
+  uint32_t c_dn1 = 0, c_clamp = 0, c_chi = 0, c_nan = 0;
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+
+  for (int64_t base = static_cast<int64_t>(blockIdx.x) * blockDim.x; base < P.n;
+       base += stride) {
+    const int64_t i = base + threadIdx.x;
+    const bool act = i < P.n;
+    R x = R(0), y = R(0), z = R(0), ux = R(0), uy = R(0), uz = R(0), w = R(0);
+    double ll = 0.0;
+    if (act) {
+      x = P.x[i]; y = P.y[i];
+      if (P.z) z = P.z[i];
+      ux = P.ux[i]; uy = P.uy[i]; uz = P.uz[i];
+      w = P.w[i];
+      if (P.rr_mode >= PRAD_RR_LEDGER) ll = P.led_ll[i];
+    }
+    const R chk = x + y + z + ux + uy + uz + w;
+    const bool live = act && isfinite(chk);
+    if (act && !live) ++c_nan;
+    const uint32_t pid = P.pid0 + static_cast<uint32_t>(i);
+    uint64_t phase = P.phase_t0;
+
+    for (int s = 0; s < P.nsub; ++s) {
+      const uint32_t step = static_cast<uint32_t>(P.t0 + s);
+      // 1. field at x^n, t^n
+      const EB<R> f = gather<R, FIELD>(P, x, y, phase);
+      phase += P.phase_step;
+      // 2. Boris: half E kick, rotation, half E kick
+      const R hq = P.half_q_dtn;
+      const R umx = ux + hq * f.Ex, umy = uy + hq * f.Ey, umz = uz + hq * f.Ez;
+      const R igm = rsq(R(1) + umx * umx + umy * umy + umz * umz);
+      const R tx = hq * f.Bx * igm, ty = hq * f.By * igm, tz = hq * f.Bz * igm;
+      const R sf = R(2) * rcp(R(1) + tx * tx + ty * ty + tz * tz);
+      const R sx = sf * tx, sy = sf * ty, sz = sf * tz;
+      const R vx = umx + (umy * tz - umz * ty);
+      const R vy = umy + (umz * tx - umx * tz);
+      const R vz = umz + (umx * ty - umy * tx);
+      R nux = umx + (vy * sz - vz * sy) + hq * f.Ex;
+      R nuy = umy + (vz * sx - vx * sz) + hq * f.Ey;
+      R nuz = umz + (vx * sy - vy * sx) + hq * f.Ez;
+      // 3. mean momentum of the step
+      const R ax = R(0.5) * (ux + nux), ay = R(0.5) * (uy + nuy),
+              az = R(0.5) * (uz + nuz);
+      const R ua2 = ax * ax + ay * ay + az * az;
+      const R iga = rsq(R(1) + ua2);
+      const R ga = (R(1) + ua2) * iga;
+      // 4. effective field, limited by dp_perp/p <= 1 (Omega dt <= gamma)
+      R Om;
+      if (P.heff_form == PRAD_HEFF_FIELD) {
+        const R bx = ax * iga, by = ay * iga, bz = az * iga;
+        const R fx = f.Ex + (by * f.Bz - bz * f.By);
+        const R fy = f.Ey + (bz * f.Bx - bx * f.Bz);
+        const R fz = f.Ez + (bx * f.By - by * f.Bx);
+        const R eb = f.Ex * bx + f.Ey * by + f.Ez * bz;
+        const R h2 = fx * fx + fy * fy + fz * fz - eb * eb;
+        Om = P.abs_q * sqr(h2 > R(0) ? h2 : R(0));
+      } else {  // Eq. (9), gamma = mean of the end-point Lorentz factors
+        const R dx_ = nux - ux, dy_ = nuy - uy, dz_ = nuz - uz;
+        const R dp2 = dx_ * dx_ + dy_ * dy_ + dz_ * dz_;
+        const R pdp = ax * dx_ + ay * dy_ + az * dz_;
+        const R g0 = sqr(R(1) + ux * ux + uy * uy + uz * uz);
+        const R g1 = sqr(R(1) + nux * nux + nuy * nuy + nuz * nuz);
+        R c2 = ua2 * dp2 - pdp * pdp;
+        c2 = c2 > R(0) ? c2 : R(0);
+        Om = ua2 > R(0) ? R(0.5) * (g0 + g1) * sqr(c2) * rcp(ua2) * P.inv_dtn : R(0);
+      }
+      if (Om * P.dtn > ga) {
+        Om = ga * P.inv_dtn;
+        if (live) ++c_clamp;
+      }
+      // 5. omega_c (Eq. (1)) as hbar omega_c / m c^2; chi = eps_r Omega gamma
+      const R epsc = P.eps_r15 * Om * ga * ga;
+      if (live && P.eps_r * Om * ga > R(1)) ++c_chi;
+      // 6. Landau-Lifshitz loss (Eq. (4)): ledger and optional kick
+      const R om2 = Om * Om;
+      if (P.rr_mode >= PRAD_RR_LEDGER) ll += static_cast<double>(w * P.ll_coef * om2 * ua2);
+      if (P.rr_mode == PRAD_RR_APPLY) {
+        const R gL = sqr(R(1) + nux * nux + nuy * nuy + nuz * nuz);
+        const R fk = rcp(R(1) + P.ll_coef * om2 * gL);
+        nux *= fk; nuy *= fk; nuz *= fk;
+      }
+      // 7. position x^{n+1}
+      const R ign = rsq(R(1) + nux * nux + nuy * nuy + nuz * nuz);
+      const R dtg = P.dtn * ign;
+      R xn = x + dtg * nux, yn = y + dtg * nuy, zn = z;
+      if (P.dims == 3) zn = z + dtg * nuz;
+      if constexpr (FIELD == PRAD_FIELD_YEE2D) {
+        xn -= P.Lx * flr((xn - P.x0) * (R(1) / P.Lx));
+        yn -= P.Ly * flr((yn - P.y0) * (R(1) / P.Ly));
+      }
+      // 8. Monte Carlo emission: proposal x = P^-1(R'), dN of Eq. (13)
+      const uint4 rnd = philox10(make_uint4(pid, step, 0u, P.ensemble), P.key0, P.key1);
+      R xs, g;
+      sample_x_g(P, rnd.x, rnd.y, xs, g);
+      const R dN = P.cn_dt * Om * g * rcp(xs);
+      const R fl = flr(dN);
+      R Rr;
+      if constexpr (sizeof(R) == 4)
+        Rr = fmaf(static_cast<float>(rnd.z), 0x1p-32f, 0x1p-33f);
+      else
+        Rr = fma(static_cast<double>(rnd.z), 0x1p-32, 0x1p-33);
+      const R k = fl + ((Rr < dN - fl) ? R(1) : R(0));
+      if (live && dN > R(1)) ++c_dn1;
+      const bool want = live && k > R(0) && w > R(0);
+      // 9. append + emitted-energy ledger (updated in place at each emission,
+      //    so the summation order never depends on the substeps per launch)
+      const R eps = xs * epsc;
+      if (want) P.led_emit[i] += static_cast<double>(k * w) * static_cast<double>(eps);
+      {
+        const R inv = ua2 > R(0) ? rsq(ua2) : R(0);
+        append_photon(P.px, P.py,
+                      P.pz, P.pnx, P.pny, P.pnz, P.peps, P.pw, P.ppid, P.pstep,
+                      P.cap, P.counters + kCursor, want, static_cast<float>(xn),
+                      static_cast<float>(yn), static_cast<float>(zn),
+                      static_cast<float>(ax * inv), static_cast<float>(ay * inv),
+                      static_cast<float>(az * inv), static_cast<float>(eps),
+                      static_cast<float>(k * w), pid, step);
+      }
+      if (live) {
+        x = xn; y = yn; z = zn;
+        ux = nux; uy = nuy; uz = nuz;
+      }
+    }
+    if (live) {
+      P.x[i] = x; P.y[i] = y;
+      if (P.z) P.z[i] = z;
+      P.ux[i] = ux; P.uy[i] = uy; P.uz[i] = uz;
+      if (P.rr_mode >= PRAD_RR_LEDGER) P.led_ll[i] = ll;
+    }
+  }
+
+  // block reduction of the counters, one atomic per nonzero block total
+  __shared__ uint32_t red[4][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t a0 = __reduce_add_sync(0xffffffffu, c_dn1);
+  const uint32_t a1 = __reduce_add_sync(0xffffffffu, c_clamp);
+  const uint32_t a2 = __reduce_add_sync(0xffffffffu, c_chi);
+  const uint32_t a3 = __reduce_add_sync(0xffffffffu, c_nan);
+  if (lane == 0) {
+    red[0][warp] = a0; red[1][warp] = a1; red[2][warp] = a2; red[3][warp] = a3;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = blockDim.x >> 5;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const uint32_t v = lane < nw ? red[c][lane] : 0u;
+      const uint32_t t = __reduce_add_sync(0xffffffffu, v);
+      if (lane == 0 && t) atomicAdd(P.counters + kDnGt1 + c, static_cast<unsigned long long>(t));
+    }
+  }
+}
+
+template <typename R>
+cudaError_t launch_push_emit(const StepParams<R>& p, int field_kind, int grid,
+                             int block, cudaStream_t s) {
+  switch (field_kind) {
+    case PRAD_FIELD_CONST:
+      k_push_emit<R, PRAD_FIELD_CONST><<<grid, block, 0, s>>>(p);
+      break;
+    case PRAD_FIELD_PLANE_WAVE:
+      k_push_emit<R, PRAD_FIELD_PLANE_WAVE><<<grid, block, 0, s>>>(p);
+      break;
+    case PRAD_FIELD_YEE2D:
+      k_push_emit<R, PRAD_FIELD_YEE2D><<<grid, block, 0, s>>>(p);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+// ---- diagnostics kernels ---------------------------------------------------
+template <typename R>
+__global__ void k_eval_sampler(const StepParams<R> P, const uint32_t* words,
+                               R* x_out, R* g_out, int64_t n) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    R x, g;
+    sample_x_g(P, words[4 * i], words[4 * i + 1], x, g);
+    x_out[i] = x;
+    g_out[i] = g;
+  }
+}
+
+__global__ void k_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1,
+                         uint32_t* out, int64_t n) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const uint4 c = make_uint4(ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]);
+    const uint4 r = philox10(c, k0, k1);
+    out[4 * i] = r.x; out[4 * i + 1] = r.y; out[4 * i + 2] = r.z; out[4 * i + 3] = r.w;
+  }
+}
+
+template <typename R>
+cudaError_t launch_eval_sampler(const StepParams<R>& p, const uint32_t* words,
+                                R* x_out, R* g_out, int64_t n, cudaStream_t s) {
+  const int block = 256;
+  const int64_t want = (n + block - 1) / block;
+  const int grid = static_cast<int>(want < 4096 ? (want > 0 ? want : 1) : 4096);
+  k_eval_sampler<R><<<grid, block, 0, s>>>(p, words, x_out, g_out, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1,
+                          uint32_t* out, int64_t n, cudaStream_t s) {
+  const int block = 256;
+  const int64_t want = (n + block - 1) / block;
+  const int grid = static_cast<int>(want < 4096 ? (want > 0 ? want : 1) : 4096);
+  k_philox<<<grid, block, 0, s>>>(ctr, k0, k1, out, n);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_push_emit<float>(const StepParams<float>&, int, int, int, cudaStream_t);
+template cudaError_t launch_push_emit<double>(const StepParams<double>&, int, int, int, cudaStream_t);
+template cudaError_t launch_eval_sampler<float>(const StepParams<float>&, const uint32_t*, float*, float*, int64_t, cudaStream_t);
+template cudaError_t launch_eval_sampler<double>(const StepParams<double>&, const uint32_t*, double*, double*, int64_t, cudaStream_t);
+
+}  // namespace prad

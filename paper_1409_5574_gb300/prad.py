@@ -1,0 +1,316 @@
+"""ctypes binding of the prad C ABI (include/prad.h).
+
+Argument marshalling only: every step of the particle path runs in the CUDA
+kernels of ``_build/libprad.so``.  PyTorch provides device memory and streams.
+There is no CPU fallback: if the library is missing or a call fails, this
+module raises.
+
+The function names mirror the C ABI (``prad_init``, ``prad_set_fields``,
+``prad_push_emit``, ``prad_get_photons``, ``prad_energy_budget``, ...).
+``Context`` bundles them for torch tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from typing import Dict, Optional, Sequence
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libprad.so")
+
+# ---- constants mirrored from prad.h -------------------------------------
+PRAD_OK, PRAD_ERR_ARG, PRAD_ERR_CUDA, PRAD_ERR_CAPACITY = 0, -1, -2, -3
+PRAD_ERR_TIMEOUT, PRAD_ERR_STATE, PRAD_WARN_NAN = -4, -5, 1
+PRAD_FP32, PRAD_FP64 = 0, 1
+PRAD_SAMPLER_TABLE, PRAD_SAMPLER_MLP, PRAD_SAMPLER_MLP_FALLBACK = 0, 1, 2
+PRAD_RR_OFF, PRAD_RR_LEDGER, PRAD_RR_APPLY = 0, 1, 2
+PRAD_HEFF_FIELD, PRAD_HEFF_MOMENTUM = 0, 1
+PRAD_FIELD_CONST, PRAD_FIELD_PLANE_WAVE, PRAD_FIELD_YEE2D = 0, 1, 2
+
+_i32, _i64, _u32, _u64, _dbl = (ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32,
+                                 ctypes.c_uint64, ctypes.c_double)
+_vp = ctypes.c_void_p
+
+
+class prad_config(ctypes.Structure):
+    _fields_ = [("precision", _i32), ("sampler", _i32), ("rr_mode", _i32),
+                ("heff_form", _i32), ("dt", _dbl), ("omega_ref", _dbl),
+                ("charge", _dbl), ("seed", _u64), ("ensemble", _u32),
+                ("steps_per_launch", _i32), ("photon_capacity", _i64),
+                ("max_particles", _i64), ("stream", _vp), ("block_size", _i32),
+                ("blocks_per_sm", _i32)]
+
+
+class prad_fields(ctypes.Structure):
+    _fields_ = [("kind", _i32), ("dir", _i32), ("hand", _i32), ("periodic", _i32),
+                ("E", _dbl * 3), ("B", _dbl * 3), ("a0", _dbl), ("lam", _dbl),
+                ("phase0", _dbl), ("yee", _vp * 6), ("nx", _i32), ("ny", _i32),
+                ("dx", _dbl), ("dy", _dbl), ("x0", _dbl), ("y0", _dbl)]
+
+
+class prad_particles(ctypes.Structure):
+    _fields_ = [("x", _vp), ("y", _vp), ("z", _vp), ("ux", _vp), ("uy", _vp),
+                ("uz", _vp), ("w", _vp), ("ledger_offset", _i64), ("pid0", _u32),
+                ("pad0", _u32), ("t0", _i64)]
+
+
+class prad_photons(ctypes.Structure):
+    _fields_ = [(n, _vp) for n in ("x", "y", "z", "nx", "ny", "nz", "eps",
+                                   "weight", "pid", "step")]
+
+
+class prad_stats(ctypes.Structure):
+    _fields_ = [("records", _i64), ("dropped", _i64), ("dn_gt1", _i64),
+                ("clamped", _i64), ("chi_gt1", _i64), ("mlp_fallback", _i64),
+                ("nan_frozen", _i64), ("status", _i32), ("pad0", _i32)]
+
+
+# symbol -> (restype, argtypes); every function declared in include/prad.h
+SIGNATURES = {
+    "prad_init": (_i32, [ctypes.POINTER(_vp), ctypes.POINTER(prad_config)]),
+    "prad_destroy": (_i32, [_vp]),
+    "prad_last_error": (ctypes.c_char_p, [_vp]),
+    "prad_set_fields": (_i32, [_vp, ctypes.POINTER(prad_fields)]),
+    "prad_push_emit": (_i32, [_vp, ctypes.POINTER(prad_particles), _i64, _i32]),
+    "prad_get_photons": (_i32, [_vp, ctypes.POINTER(prad_photons), _i64,
+                                ctypes.POINTER(_i64), ctypes.POINTER(_i64), _i32, _i32]),
+    "prad_energy_budget": (_i32, [_vp, ctypes.POINTER(_dbl), ctypes.POINTER(_dbl),
+                                  ctypes.POINTER(prad_stats)]),
+    "prad_get_ledger": (_i32, [_vp, _vp, _vp, _i64, _i64, _i32]),
+    "prad_reset": (_i32, [_vp]),
+    "prad_philox": (_i32, [_vp, _vp, _u32, _u32, _vp, _i64]),
+    "prad_eval_sampler": (_i32, [_vp, _vp, _vp, _vp, _i64]),
+}
+
+_lib = None
+
+
+class PradError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"prad error {code}: {msg}")
+        self.code = code
+
+
+def load_library(path: Optional[str] = None) -> ctypes.CDLL:
+    """Load libprad.so (raises OSError if it has not been built)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise OSError(f"libprad.so not built ({p}); run "
+                      "python -c 'import __graft_entry__ as g; g.build()'")
+    lib = ctypes.CDLL(p)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _check(rc: int, handle=None) -> int:
+    if rc < 0:
+        msg = load_library().prad_last_error(handle).decode(errors="replace")
+        raise PradError(rc, msg)
+    return rc
+
+
+# ---- thin wrappers with the C names ------------------------------------
+def prad_init(cfg: prad_config) -> int:
+    h = _vp()
+    _check(load_library().prad_init(ctypes.byref(h), ctypes.byref(cfg)))
+    return h.value
+
+
+def prad_destroy(h) -> None:
+    _check(load_library().prad_destroy(h), h)
+
+
+def prad_set_fields(h, f: prad_fields) -> None:
+    _check(load_library().prad_set_fields(h, ctypes.byref(f)), h)
+
+
+def prad_push_emit(h, p: prad_particles, n: int, nsteps: int) -> int:
+    return _check(load_library().prad_push_emit(h, ctypes.byref(p), n, nsteps), h)
+
+
+def prad_get_photons(h, out: Optional[prad_photons], cap: int, drain: bool,
+                     out_on_device: bool):
+    n_out, n_drop = _i64(), _i64()
+    _check(load_library().prad_get_photons(
+        h, ctypes.byref(out) if out is not None else None, cap, ctypes.byref(n_out),
+        ctypes.byref(n_drop), int(drain), int(out_on_device)), h)
+    return n_out.value, n_drop.value
+
+
+def prad_energy_budget(h):
+    e, r, s = _dbl(), _dbl(), prad_stats()
+    rc = _check(load_library().prad_energy_budget(h, ctypes.byref(e), ctypes.byref(r),
+                                                  ctypes.byref(s)), h)
+    stats = {k: getattr(s, k) for k, _ in prad_stats._fields_ if k != "pad0"}
+    stats["rc"] = rc
+    return e.value, r.value, stats
+
+
+def prad_get_ledger(h, emit_ptr, ll_ptr, offset: int, n: int, on_device: bool) -> None:
+    _check(load_library().prad_get_ledger(h, emit_ptr, ll_ptr, offset, n, int(on_device)), h)
+
+
+def prad_reset(h) -> None:
+    _check(load_library().prad_reset(h), h)
+
+
+def prad_philox(h, ctr_ptr, k0: int, k1: int, out_ptr, n: int) -> None:
+    _check(load_library().prad_philox(h, ctr_ptr, k0, k1, out_ptr, n), h)
+
+
+def prad_eval_sampler(h, words_ptr, x_ptr, g_ptr, n: int) -> None:
+    _check(load_library().prad_eval_sampler(h, words_ptr, x_ptr, g_ptr, n), h)
+
+
+# ---- torch convenience ---------------------------------------------------
+def _torch():
+    import torch  # noqa: WPS433 (torch is only plumbing: memory and streams)
+    return torch
+
+
+def _ptr(t) -> Optional[int]:
+    return None if t is None else t.data_ptr()
+
+
+class Context:
+    """A prad context with torch tensors as the particle and photon storage.
+
+    ``problem`` keys follow ``workloads.Workload.problem_kwargs()``.
+    """
+
+    def __init__(self, problem: Dict, precision: int = PRAD_FP32,
+                 photon_capacity: int = 1 << 20, max_particles: int = 1 << 20,
+                 steps_per_launch: int = 1, stream=None, block_size: int = 0,
+                 blocks_per_sm: int = 0, sampler: int = PRAD_SAMPLER_TABLE,
+                 ensemble: int = 0):
+        torch = _torch()
+        if not torch.cuda.is_available():
+            raise RuntimeError("prad needs a CUDA device")
+        self.torch = torch
+        self.problem = dict(problem)
+        self.precision = precision
+        self.dtype = torch.float32 if precision == PRAD_FP32 else torch.float64
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        cfg = prad_config()
+        cfg.precision = precision
+        cfg.sampler = sampler
+        cfg.rr_mode = problem.get("rr_mode", PRAD_RR_LEDGER)
+        cfg.heff_form = problem.get("heff_form", PRAD_HEFF_FIELD)
+        cfg.dt = problem["dt"]
+        cfg.omega_ref = problem["omega_ref"]
+        cfg.charge = problem.get("charge", -1.0)
+        cfg.seed = int(problem.get("seed", 1))
+        cfg.ensemble = int(ensemble or problem.get("ensemble", 0))
+        cfg.steps_per_launch = steps_per_launch
+        cfg.photon_capacity = photon_capacity
+        cfg.max_particles = max_particles
+        cfg.stream = self.stream.cuda_stream
+        cfg.block_size = block_size
+        cfg.blocks_per_sm = blocks_per_sm
+        self.cfg = cfg
+        self.capacity = photon_capacity
+        self.max_particles = max_particles
+        self.h = prad_init(cfg)
+        self._yee_keep = None
+        self.set_fields(problem)
+
+    # -- fields ------------------------------------------------------------
+    def set_fields(self, problem: Dict) -> None:
+        torch = self.torch
+        f = prad_fields()
+        f.kind = problem.get("field_kind", PRAD_FIELD_CONST)
+        f.dir = int(problem.get("direction", 1))
+        f.hand = int(problem.get("hand", 1))
+        f.periodic = 1
+        for k in range(3):
+            f.E[k] = problem.get("E", (0, 0, 0))[k]
+            f.B[k] = problem.get("B", (0, 0, 0))[k]
+        f.a0 = problem.get("a0", 0.0)
+        f.lam = problem.get("lam", 0.8e-6)
+        f.phase0 = problem.get("phase0", 0.0)
+        if f.kind == PRAD_FIELD_YEE2D:
+            planes = problem["yee"]
+            dev = [p if (hasattr(p, "is_cuda") and p.is_cuda)
+                   else torch.as_tensor(p, dtype=torch.float32).cuda().contiguous()
+                   for p in planes]
+            self._yee_keep = dev
+            for k in range(6):
+                f.yee[k] = dev[k].data_ptr()
+            f.ny, f.nx = dev[0].shape
+            f.dx, f.dy = problem["dx"], problem["dy"]
+            f.x0, f.y0 = problem.get("x0", 0.0), problem.get("y0", 0.0)
+        self.fields = f
+        prad_set_fields(self.h, f)
+
+    # -- state ---------------------------------------------------------------
+    def to_device(self, state: Dict, device="cuda") -> Dict:
+        torch = self.torch
+        return {k: torch.as_tensor(v, dtype=self.dtype).to(device).contiguous()
+                for k, v in state.items()}
+
+    def push_emit(self, st: Dict, nsteps: int, t0: int = 0, pid0: int = 0,
+                  ledger_offset: int = 0) -> None:
+        n = st["x"].numel()
+        p = prad_particles()
+        p.x, p.y = _ptr(st["x"]), _ptr(st["y"])
+        p.z = _ptr(st.get("z")) if self.fields.kind != PRAD_FIELD_YEE2D or "z" in st else None
+        p.ux, p.uy, p.uz, p.w = _ptr(st["ux"]), _ptr(st["uy"]), _ptr(st["uz"]), _ptr(st["w"])
+        p.ledger_offset = ledger_offset
+        p.pid0 = pid0
+        p.t0 = t0
+        prad_push_emit(self.h, p, n, nsteps)
+
+    def photons(self, drain: bool = False, on_device: bool = True,
+                cap: Optional[int] = None) -> Dict:
+        """Copy the held photon records into new torch tensors."""
+        torch = self.torch
+        held, dropped = prad_get_photons(self.h, None, 0, False, True)
+        m = held if cap is None else min(held, cap)
+        kw = dict(device="cuda") if on_device else dict(pin_memory=m > 0)
+        out = {k: torch.empty(m, dtype=torch.float32, **kw)
+               for k in ("x", "y", "z", "nx", "ny", "nz", "eps", "weight")}
+        out["pid"] = torch.empty(m, dtype=torch.int32, **kw)
+        out["step"] = torch.empty(m, dtype=torch.int32, **kw)
+        ph = prad_photons()
+        for k, v in out.items():
+            setattr(ph, k, v.data_ptr() if m else None)
+        held, dropped = prad_get_photons(self.h, ph if m else None, m, drain, on_device)
+        out["dropped"] = dropped
+        return out
+
+    def drain(self):
+        return prad_get_photons(self.h, None, 0, True, True)
+
+    def energy_budget(self):
+        return prad_energy_budget(self.h)
+
+    def ledger(self, offset: int = 0, n: Optional[int] = None):
+        torch = self.torch
+        n = self.max_particles - offset if n is None else n
+        e = torch.empty(n, dtype=torch.float64, device="cuda")
+        l = torch.empty(n, dtype=torch.float64, device="cuda")
+        prad_get_ledger(self.h, e.data_ptr(), l.data_ptr(), offset, n, True)
+        return e, l
+
+    def reset(self) -> None:
+        prad_reset(self.h)
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            prad_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

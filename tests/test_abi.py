@@ -1,0 +1,94 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds and
+loads, exports every function include/prad.h declares, the ctypes structures
+match the C layout, and argument errors come back as status codes."""
+import ctypes
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "prad.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1409_5574_gb300 import build, prad
+    build.build()
+    return prad.load_library()
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(prad_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 11
+    out = subprocess.run(["nm", "-D", "--defined-only",
+                          os.path.join(ROOT, "paper_1409_5574_gb300", "_build", "libprad.so")],
+                         capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (prad_\w+)", out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    from paper_1409_5574_gb300 import prad
+    assert set(names) == set(prad.SIGNATURES), "binding out of sync with header"
+
+
+def test_ctypes_layout_matches_c():
+    from paper_1409_5574_gb300 import prad
+    structs = ["prad_config", "prad_fields", "prad_particles", "prad_photons", "prad_stats"]
+    body = "".join(f'printf("%zu\\n", sizeof({s}));' for s in structs)
+    offs = [("prad_config", "stream"), ("prad_config", "blocks_per_sm"),
+            ("prad_fields", "yee"), ("prad_fields", "y0"), ("prad_particles", "t0"),
+            ("prad_stats", "status")]
+    body += "".join(f'printf("%zu\\n", offsetof({s}, {f}));' for s, f in offs)
+    code = ("#include <stdio.h>\n#include <stddef.h>\n#include \"prad.h\"\n"
+            f"int main(void){{{body}return 0;}}\n")
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "l.c")
+        open(c, "w").write(code)
+        exe = os.path.join(d, "l")
+        subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+        vals = [int(v) for v in subprocess.run([exe], capture_output=True, text=True,
+                                                check=True).stdout.split()]
+    want = [ctypes.sizeof(getattr(prad, s)) for s in structs]
+    want += [getattr(getattr(prad, s), f if f != "lambda" else "lam").offset for s, f in offs]
+    assert vals == want
+
+
+def test_argument_errors_without_gpu(lib):
+    from paper_1409_5574_gb300 import prad
+    h = ctypes.c_void_p()
+    assert lib.prad_init(None, None) == prad.PRAD_ERR_ARG
+    cfg = prad.prad_config()
+    cfg.dt, cfg.omega_ref, cfg.charge = 1e-16, 1e15, -1.0
+    cfg.photon_capacity, cfg.max_particles = 16, 16
+    bad = prad.prad_config.from_buffer_copy(cfg)
+    bad.dt = 0.0
+    assert lib.prad_init(ctypes.byref(h), ctypes.byref(bad)) == prad.PRAD_ERR_ARG
+    assert b"dt" in lib.prad_last_error(None)
+    bad = prad.prad_config.from_buffer_copy(cfg)
+    bad.photon_capacity = 0
+    assert lib.prad_init(ctypes.byref(h), ctypes.byref(bad)) == prad.PRAD_ERR_ARG
+    bad = prad.prad_config.from_buffer_copy(cfg)
+    bad.charge = 2.0
+    assert lib.prad_init(ctypes.byref(h), ctypes.byref(bad)) == prad.PRAD_ERR_ARG
+    bad = prad.prad_config.from_buffer_copy(cfg)
+    bad.block_size = 100
+    assert lib.prad_init(ctypes.byref(h), ctypes.byref(bad)) == prad.PRAD_ERR_ARG
+    assert lib.prad_push_emit(None, None, 1, 1) == prad.PRAD_ERR_ARG
+    assert lib.prad_destroy(None) == prad.PRAD_OK
+    try:
+        import torch
+        has_gpu = torch.cuda.is_available()
+    except Exception:
+        has_gpu = False
+    if not has_gpu:
+        # a valid config fails cleanly with a CUDA error, no crash
+        assert lib.prad_init(ctypes.byref(h), ctypes.byref(cfg)) == prad.PRAD_ERR_CUDA
+        assert h.value is None

@@ -74,6 +74,8 @@ def lib() -> ctypes.CDLL:
             L.orc_num_threads.restype = ctypes.c_int
             L.orc_sample_x.restype = d
             L.orc_sample_x.argtypes = [P, P]
+            L.orc_S_of_words.restype = d
+            L.orc_S_of_words.argtypes = [P]
             L.orc_philox4x32_10.argtypes = [P, P, P]
             for name in ("orc_G_batch", "orc_Q_batch", "orc_Ginv_batch",
                          "orc_F_batch", "orc_F_exact_batch"):
@@ -180,6 +182,12 @@ def sample_x(words) -> tuple:
     R = np.zeros(1, dtype=np.float64)
     x = lib().orc_sample_x(_ptr(w), _ptr(R))
     return x, float(R[0])
+
+
+def S_of_words(words) -> float:
+    """S of Eq. (11) on the branch the Philox block's sample falls in."""
+    w = np.ascontiguousarray(np.asarray(words, dtype=np.uint32))
+    return lib().orc_S_of_words(_ptr(w))
 
 
 def boris(u, E, B, q: float, dtn: float) -> np.ndarray:

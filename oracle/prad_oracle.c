@@ -206,9 +206,11 @@ double orc_Pinv(double R) {
  * ====================================================================== */
 uint64_t orc_branch_threshold(void) { return orc_A_int; }
 
-double orc_sample_x(const uint32_t w[4], double* R_out) {
+static double orc_sample_x_branch(const uint32_t w[4], double* R_out,
+                                  int* low_out) {
   uint64_t W = ((uint64_t)w[1] << 32) | (uint64_t)w[0];
   double x;
+  *low_out = W < orc_A_int;
   if (W < orc_A_int) {
     double Rp = ((double)W + 0.5) * 0x1p-64;
     x = pow(Rp, 0.75);
@@ -219,6 +221,24 @@ double orc_sample_x(const uint32_t w[4], double* R_out) {
   }
   if (R_out) *R_out = ((double)w[2] + 0.5) * 0x1p-32;
   return x;
+}
+
+double orc_sample_x(const uint32_t w[4], double* R_out) {
+  int low;
+  return orc_sample_x_branch(w, R_out, &low);
+}
+
+/* S on the branch the sample was drawn from (READING: S is discontinuous at
+ * x = a, and rounding can put a high-branch x a hair below a, so the branch,
+ * not the rounded x, selects the formula of Eq. (11)). */
+static double orc_S_branch(double x, int low) {
+  return low ? (4.0 / 3.0) * cbrt(x) : (7.0 / 9.0) * exp(-x);
+}
+
+double orc_S_of_words(const uint32_t w[4]) {
+  int low;
+  double x = orc_sample_x_branch(w, 0, &low);
+  return orc_S_branch(x, low);
 }
 
 /* ======================================================================
@@ -597,8 +617,9 @@ int orc_run(const orc_problem* P, int64_t n, int32_t nsteps, int64_t t0,
       uint32_t ctr[4] = {pid[i], (uint32_t)step, 0u, P->ensemble}, rnd[4];
       orc_philox4x32_10(ctr, key, rnd);
       double R;
-      double xs = orc_sample_x(rnd, &R);
-      double dN = Cn * Om * dtn * orc_F(xs) / (xs * orc_S(xs));
+      int low;
+      double xs = orc_sample_x_branch(rnd, &R, &low);
+      double dN = Cn * Om * dtn * orc_F(xs) / (xs * orc_S_branch(xs, low));
       double fl = floor(dN);
       double k = fl + ((R < dN - fl) ? 1.0 : 0.0);
       if (dN > 1.0) s_dn1++;

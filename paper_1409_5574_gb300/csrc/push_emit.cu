@@ -70,10 +70,18 @@ __device__ __forceinline__ void sample_x_g(const StepParams<float>& P,
   // (h 2^32 + l + 1/2) 2^-64, never zero
   const float arg = fmaf(static_cast<float>(h), 0x1p-32f,
                          fmaf(static_cast<float>(l), 0x1p-64f, 0x1p-65f));
-  const float L = __log2f(arg);
-  const float t = exp2f(0.25f * L);
+  // log2(arg) = e + log2(m), m in [1, 2): the integer exponent is exact and
+  // the mantissa log has a small absolute error, so x keeps its relative
+  // accuracy down to R' ~ 2^-65 (a plain float log2 would not).
+  const int bits = __float_as_int(arg);
+  const int e = ((bits >> 23) & 0xff) - 127;
+  const float lm = __log2f(__int_as_float((bits & 0x007fffff) | 0x3f800000));
+  // t = 2^(L/4) = 2^(e >> 2) * 2^(((e & 3) + lm) / 4)
+  const float t = exp2f(0.25f * (static_cast<float>(e & 3) + lm)) *
+                  __int_as_float((127 + (e >> 2)) << 23);
   const float x_lo = t * t * t;
-  const float x_hi = fmaf(-L, 0.69314718055994531f, -0.25131442828090608f);
+  const float x_hi = fmaf(-static_cast<float>(e), 0.69314718055994531f,
+                          -fmaf(lm, 0.69314718055994531f, 0.25131442828090608f));
   x = low ? x_lo : x_hi;
   const float u = low ? t * P.t_scale : (x_hi - P.a) * P.x_scale;
   int i = static_cast<int>(fmaxf(u, 0.0f));

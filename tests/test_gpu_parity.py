@@ -126,7 +126,7 @@ def test_sampler_gpu_vs_oracle(precision):
     prad.prad_eval_sampler(ctx.h, d_w.data_ptr(), xg.data_ptr(), gg.data_ptr(), n)
     xg, gg = xg.double().cpu().numpy(), gg.double().cpu().numpy()
     xr = np.array([O.sample_x(w)[0] for w in words])
-    gr = O.F(xr) / np.array([O.S(v) for v in xr])
+    gr = O.F(xr) / np.array([O.S_of_words(w) for w in words])
     xtol, gtol = (2e-6, 2e-6) if p == prad.PRAD_FP32 else (1e-13, 3e-9)
     assert np.max(np.abs(xg / xr - 1)) < xtol
     assert np.max(np.abs(gg / gr - 1)) < gtol
@@ -143,7 +143,7 @@ def test_constB_fp64_parity():
     for k in ("x", "y", "z"):
         assert np.allclose(gpu["state"][k], ref["state"][k], rtol=1e-12, atol=1e-9)
     m, tot = _check_photons(gpu, ref, 0, eps_rtol=1e-6, flip_tol=1e-8)
-    assert tot > 2000
+    assert tot > 1000
     assert gpu["ll"] == pytest.approx(ref["ledger"]["ll"].sum(), rel=1e-10)
     assert np.allclose(gpu["led_ll"], ref["ledger"]["ll"], rtol=1e-10, atol=0)
     assert gpu["emitted"] == pytest.approx(ref["ledger"]["emit"].sum(), rel=1e-4)

@@ -36,16 +36,22 @@ def _stale(target: str, deps: list) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(verbose: bool = False, extra_flags: list | None = None) -> str:
-    os.makedirs(OUT, exist_ok=True)
+def build(verbose: bool = False, extra_flags: list | None = None,
+          out_dir: str | None = None) -> str:
+    """Compile (incrementally) and link; returns the library path.
+    ``extra_flags`` / ``out_dir`` build a variant elsewhere (e.g. -D tuning
+    macros) without touching the default library."""
+    out = out_dir or OUT
+    lib = os.path.join(out, "libprad.so")
+    os.makedirs(out, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     headers.append(os.path.join(ROOT, "include", "prad.h"))
     flags = NVCC_FLAGS + (extra_flags or [])
     nvcc = _nvcc()
     jobs = []
     for src in sources():
-        obj = os.path.join(OUT, os.path.basename(src)[:-3] + ".o")
-        if _stale(obj, [src] + headers):
+        obj = os.path.join(out, os.path.basename(src)[:-3] + ".o")
+        if _stale(obj, [src] + headers) or extra_flags:
             jobs.append([nvcc] + flags + ["-c", src, "-o", obj])
 
     def run(cmd):
@@ -59,15 +65,15 @@ def build(verbose: bool = False, extra_flags: list | None = None) -> str:
 
     with ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 4))) as ex:
         list(ex.map(run, jobs))
-    objs = [os.path.join(OUT, os.path.basename(s)[:-3] + ".o") for s in sources()]
-    if _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    objs = [os.path.join(out, os.path.basename(s)[:-3] + ".o") for s in sources()]
+    if _stale(lib, objs):
+        tmp = lib + f".tmp{os.getpid()}"
         # static cudart: the library loads without a CUDA runtime on the
         # loader path and shares the device's primary context with torch
         run([nvcc, "-shared", "-gencode", "arch=compute_103a,code=sm_103a",
              "-cudart", "static", "-o", tmp] + objs)
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -33,19 +33,53 @@ __device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
   return c;
 }
 
+// ---- compensated accumulators for the per-particle ledgers -----------------
+// The FP32 path sums a launch's ledger increments in a float-float pair
+// (Knuth TwoSum: the rounding error of every add is kept in `lo`), about
+// 48 bits, and adds the pair to the FP64 ledger once per launch.  This keeps
+// the slow FP64 pipe out of the per-step loop.  The FP64 path accumulates in
+// double directly.
+template <typename R>
+struct Acc;
+template <>
+struct Acc<float> {
+  float hi = 0.0f, lo = 0.0f;
+  __device__ __forceinline__ void add(float v) {
+    const float s = hi + v;
+    const float bb = s - hi;
+    lo += (hi - (s - bb)) + (v - bb);
+    hi = s;
+  }
+  __device__ __forceinline__ double value() const {
+    return static_cast<double>(hi) + static_cast<double>(lo);
+  }
+  __device__ __forceinline__ bool nonzero() const { return hi != 0.0f; }
+};
+template <>
+struct Acc<double> {
+  double hi = 0.0;
+  __device__ __forceinline__ void add(double v) { hi += v; }
+  __device__ __forceinline__ double value() const { return hi; }
+  __device__ __forceinline__ bool nonzero() const { return hi != 0.0; }
+};
+
 // ---- precision-generic helpers --------------------------------------------
 __device__ __forceinline__ float rsq(float v) { return rsqrtf(v); }
 __device__ __forceinline__ double rsq(double v) { return rsqrt(v); }
 __device__ __forceinline__ float rcp(float v) { return __fdividef(1.0f, v); }
 __device__ __forceinline__ double rcp(double v) { return 1.0 / v; }
-__device__ __forceinline__ float sqr(float v) { return sqrtf(v); }
+// v * rsqrt(v): one MUFU op instead of the IEEE square root (2 ulp), with
+// sqr(0) = 0
+__device__ __forceinline__ float sqr(float v) { return v > 0.0f ? v * rsqrtf(v) : 0.0f; }
 __device__ __forceinline__ double sqr(double v) { return sqrt(v); }
 __device__ __forceinline__ float flr(float v) { return floorf(v); }
 __device__ __forceinline__ double flr(double v) { return floor(v); }
 __device__ __forceinline__ float rnd_int(float v) { return rintf(v); }
 __device__ __forceinline__ double rnd_int(double v) { return rint(v); }
+// sin/cos of pi v for v in [-1, 1] (the caller reduces the phase exactly to
+// half a cycle first): the MUFU sin/cos, absolute error ~2^-21.
 __device__ __forceinline__ void sincos_pi(float v, float* s, float* c) {
-  sincospif(v, s, c);
+  __sincosf(3.14159265358979323846f * v, s, c);
 }
 __device__ __forceinline__ void sincos_pi(double v, double* s, double* c) {
   sincospi(v, s, c);
@@ -265,8 +299,22 @@ __device__ __forceinline__ void append_photon(
 // ---------------------------------------------------------------------------
 // The fused kernel.
 // ---------------------------------------------------------------------------
+// Resident blocks per SM the FP32 kernels are compiled for (registers are
+// capped at 65536 / (256 * MINB)); the FP64 kernels keep the default.
+#ifndef PRAD_F32_MINB
+#define PRAD_F32_MINB 5
+#endif
+template <typename R>
+struct MinBlocks {
+  static constexpr int value = 1;
+};
+template <>
+struct MinBlocks<float> {
+  static constexpr int value = PRAD_F32_MINB;
+};
+
 template <typename R, int FIELD>
-__global__ void __launch_bounds__(256) k_push_emit(const StepParams<R> P) {
+__global__ void __launch_bounds__(256, MinBlocks<R>::value) k_push_emit(const StepParams<R> P) {
   uint32_t c_dn1 = 0, c_clamp = 0, c_chi = 0, c_nan = 0;
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
 
@@ -275,13 +323,12 @@ __global__ void __launch_bounds__(256) k_push_emit(const StepParams<R> P) {
     const int64_t i = base + threadIdx.x;
     const bool act = i < P.n;
     R x = R(0), y = R(0), z = R(0), ux = R(0), uy = R(0), uz = R(0), w = R(0);
-    double ll = 0.0;
+    Acc<R> ll, le;
     if (act) {
       x = P.x[i]; y = P.y[i];
       if (P.z) z = P.z[i];
       ux = P.ux[i]; uy = P.uy[i]; uz = P.uz[i];
       w = P.w[i];
-      if (P.rr_mode >= PRAD_RR_LEDGER) ll = P.led_ll[i];
     }
     const R chk = x + y + z + ux + uy + uz + w;
     const bool live = act && isfinite(chk);
@@ -342,7 +389,7 @@ __global__ void __launch_bounds__(256) k_push_emit(const StepParams<R> P) {
       if (live && P.eps_r * Om * ga > R(1)) ++c_chi;
       // 6. Landau-Lifshitz loss (Eq. (4)): ledger and optional kick
       const R om2 = Om * Om;
-      if (P.rr_mode >= PRAD_RR_LEDGER) ll += static_cast<double>(w * P.ll_coef * om2 * ua2);
+      if (P.rr_mode >= PRAD_RR_LEDGER) ll.add(w * P.ll_coef * om2 * ua2);
       if (P.rr_mode == PRAD_RR_APPLY) {
         const R gL = sqr(R(1) + nux * nux + nuy * nuy + nuz * nuz);
         const R fk = rcp(R(1) + P.ll_coef * om2 * gL);
@@ -371,10 +418,9 @@ __global__ void __launch_bounds__(256) k_push_emit(const StepParams<R> P) {
       const R k = fl + ((Rr < dN - fl) ? R(1) : R(0));
       if (live && dN > R(1)) ++c_dn1;
       const bool want = live && k > R(0) && w > R(0);
-      // 9. append + emitted-energy ledger (updated in place at each emission,
-      //    so the summation order never depends on the substeps per launch)
+      // 9. append + emitted-energy ledger
       const R eps = xs * epsc;
-      if (want) P.led_emit[i] += static_cast<double>(k * w) * static_cast<double>(eps);
+      if (want) le.add(k * w * eps);
       {
         const R inv = ua2 > R(0) ? rsq(ua2) : R(0);
         append_photon(P.px, P.py,
@@ -394,7 +440,8 @@ __global__ void __launch_bounds__(256) k_push_emit(const StepParams<R> P) {
       P.x[i] = x; P.y[i] = y;
       if (P.z) P.z[i] = z;
       P.ux[i] = ux; P.uy[i] = uy; P.uz[i] = uz;
-      if (P.rr_mode >= PRAD_RR_LEDGER) P.led_ll[i] = ll;
+      if (P.rr_mode >= PRAD_RR_LEDGER) P.led_ll[i] += ll.value();
+      if (le.nonzero()) P.led_emit[i] += le.value();
     }
   }
 

@@ -97,7 +97,7 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
     global _lib
     if _lib is not None and path is None:
         return _lib
-    p = path or LIB_PATH
+    p = path or os.environ.get("PRAD_LIBRARY") or LIB_PATH
     if not os.path.exists(p):
         raise OSError(f"libprad.so not built ({p}); run "
                       "python -c 'import __graft_entry__ as g; g.build()'")

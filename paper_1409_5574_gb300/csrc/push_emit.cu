@@ -50,8 +50,12 @@ struct Acc<float> {
     lo += (hi - (s - bb)) + (v - bb);
     hi = s;
   }
+  // FP64 value; a single add (one step per launch) leaves lo == 0 and costs
+  // one conversion on the slow FP64 pipe instead of two plus an add
   __device__ __forceinline__ double value() const {
-    return static_cast<double>(hi) + static_cast<double>(lo);
+    double v = static_cast<double>(hi);
+    if (lo != 0.0f) v += static_cast<double>(lo);
+    return v;
   }
   __device__ __forceinline__ bool nonzero() const { return hi != 0.0f; }
 };

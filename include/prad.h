@@ -89,6 +89,11 @@ typedef struct prad_config {
   void* stream;             /* cudaStream_t for every launch; NULL = default */
   int32_t block_size;       /* threads per block (0 = 256); multiple of 32   */
   int32_t blocks_per_sm;    /* resident blocks per SM for the grid (0 = 4)   */
+  int32_t sort_interval;    /* YEE2D with a pid array: reorder particles by
+                               32 x 32-cell tile every this many steps and
+                               gather from shared-memory field tiles
+                               (0 = never sort; plain gather)             */
+  int32_t pad0;
 } prad_config;
 
 /* ---- field description ------------------------------------------------- */
@@ -121,10 +126,15 @@ typedef struct prad_particles {
    * u holds u^{n-1/2} on entry and u^{n+nsteps-1/2} on return; w is the
    * macro-particle weight (read only). */
   void *x, *y, *z, *ux, *uy, *uz;
-  const void* w;
-  int64_t ledger_offset; /* ledger index of particle 0 (entries used:
-                            [ledger_offset, ledger_offset + n))          */
-  uint32_t pid0;         /* particle i has Philox counter word 0 = pid0+i */
+  void* w;  /* read only in push_emit; reordered by prad_sort_by_tile */
+  /* Optional device array of n particle ids (NULL: particle i has id
+   * pid0 + i).  The id is Philox counter word 0 and selects the ledger entry
+   * ledger_offset + (id - pid0), so ids move with particles that a tile sort
+   * reorders.  Ids outside [pid0, pid0 + max_particles - ledger_offset) are
+   * not booked (status bit 1 is set). */
+  uint32_t* pid;
+  int64_t ledger_offset; /* ledger entry of id pid0                        */
+  uint32_t pid0;
   uint32_t pad0;
   int64_t t0;            /* global index of the first step (time t0*dt)  */
 } prad_particles;
@@ -194,11 +204,23 @@ int prad_set_fields(prad_ctx* ctx, const prad_fields* f);
  *   9. if k > 0 and w > 0: append one record (weight k w, energy
  *      x hbar omega_c) and add k w x hbar omega_c to the emit ledger.
  * Records beyond the capacity are counted as dropped, never written.
+ * For YEE2D with sort_interval > 0 and a pid array, the particles are
+ * reordered by tile (prad_sort_by_tile) before every sort_interval steps.
  * Errors: PRAD_ERR_ARG (null pointers, n < 0, nsteps < 0, ledger range
  * outside max_particles, misaligned arrays), PRAD_ERR_STATE (no fields),
  * PRAD_ERR_CUDA (launch failure).  n == 0 or nsteps == 0 is a no-op. */
 int prad_push_emit(prad_ctx* ctx, const prad_particles* p, int64_t n,
                    int32_t nsteps);
+
+/* Reorder n particles in place (x, y, z, ux, uy, uz, w and the pid array,
+ * which is required) by the 32 x 32-cell tile of the YEE2D grid that holds
+ * them (counting sort: histogram, scan, scatter; order within a tile is not
+ * deterministic), and record the tile ranges that push_emit uses to gather
+ * from shared-memory field tiles.  push_emit calls it itself every
+ * sort_interval steps when sort_interval > 0.  Uses the context's scratch
+ * (max_particles x 32 B).  Errors: PRAD_ERR_STATE (fields not YEE2D),
+ * PRAD_ERR_ARG (null arrays, no pid array, n > max_particles). */
+int prad_sort_by_tile(prad_ctx* ctx, const prad_particles* p, int64_t n);
 
 /* Copy up to `cap` photon records into `out` (device arrays if
  * out_on_device, else host arrays; any pointer of out may be NULL to skip

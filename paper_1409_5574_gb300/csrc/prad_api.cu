@@ -59,6 +59,8 @@ struct prad_ctx {
   // host-side totals folded in at each drain
   int64_t drained_records = 0;
   int64_t drained_dropped = 0;
+  // tile sort scratch (allocated on first use)
+  SortBuffers sort{};
 };
 
 namespace {
@@ -251,6 +253,77 @@ bool aligned(const void* p, size_t a) {
   return (reinterpret_cast<uintptr_t>(p) % a) == 0;
 }
 
+void free_sort(SortBuffers& b) {
+  for (int k = 0; k < 7; ++k) cudaFree(b.tmp[k]);
+  cudaFree(b.tmp_pid);
+  cudaFree(b.counts);
+  cudaFree(b.starts);
+  cudaFree(b.cursor);
+  cudaFree(b.work);
+  cudaFree(b.work_count);
+  b = SortBuffers{};
+}
+
+int tile_counts(const prad_fields& f, int* ntx, int* nty) {
+  *ntx = (f.nx + kTile - 1) / kTile;
+  *nty = (f.ny + kTile - 1) / kTile;
+  return (*ntx) * (*nty);
+}
+
+int64_t max_work_items(int64_t n, int ntiles) {
+  return n / kChunk + (n < ntiles ? n : ntiles) + 1;
+}
+
+// Scratch for the sort: max_particles copies of the 7 state arrays and the
+// ids, per-tile counters and the work list.
+int ensure_sort(prad_ctx* c, size_t elem) {
+  int ntx, nty;
+  const int ntiles = tile_counts(c->fields, &ntx, &nty);
+  SortBuffers& b = c->sort;
+  if (b.capacity >= c->cfg.max_particles && b.ntiles >= ntiles) return PRAD_OK;
+  free_sort(b);
+  const size_t np = static_cast<size_t>(c->cfg.max_particles);
+  for (int k = 0; k < 7; ++k) CK(c, cudaMalloc(&b.tmp[k], np * elem));
+  CK(c, cudaMalloc(&b.tmp_pid, np * sizeof(uint32_t)));
+  CK(c, cudaMalloc(&b.counts, sizeof(unsigned int) * ntiles));
+  CK(c, cudaMalloc(&b.starts, sizeof(unsigned int) * (ntiles + 1)));
+  CK(c, cudaMalloc(&b.cursor, sizeof(unsigned int) * ntiles));
+  const int64_t mw = max_work_items(c->cfg.max_particles, ntiles);
+  CK(c, cudaMalloc(&b.work, sizeof(int4) * mw));
+  CK(c, cudaMalloc(&b.work_count, sizeof(unsigned int)));
+  b.capacity = c->cfg.max_particles;
+  b.ntiles = ntiles;
+  b.max_work = static_cast<int32_t>(mw);
+  return PRAD_OK;
+}
+
+template <typename R>
+int sort_t(prad_ctx* c, const prad_particles* pp, int64_t n) {
+  int rc = ensure_sort(c, sizeof(R));
+  if (rc != PRAD_OK) return rc;
+  int ntx, nty;
+  const int ntiles = tile_counts(c->fields, &ntx, &nty);
+  SortBuffers b = c->sort;
+  b.ntiles = ntiles;
+  R* arr[7] = {static_cast<R*>(pp->x), static_cast<R*>(pp->y), static_cast<R*>(pp->z),
+               static_cast<R*>(pp->ux), static_cast<R*>(pp->uy), static_cast<R*>(pp->uz),
+               static_cast<R*>(pp->w)};
+  const prad_fields& f = c->fields;
+  CK(c, launch_tile_sort<R>(arr, pp->pid, n, b, f.nx, f.ny, f.x0, f.y0, 1.0 / f.dx,
+                            1.0 / f.dy, c->stream));
+  return PRAD_OK;
+}
+
+int check_sort_args(prad_ctx* c, const prad_particles* pp, int64_t n) {
+  if (!c->fields_set || c->fields.kind != PRAD_FIELD_YEE2D)
+    return fail(c, PRAD_ERR_STATE, "sort_by_tile: fields are not YEE2D");
+  if (!pp->pid) return fail(c, PRAD_ERR_ARG, "sort_by_tile: a pid array is required");
+  if (n > c->cfg.max_particles)
+    return fail(c, PRAD_ERR_ARG, "sort_by_tile: n exceeds max_particles");
+  if (!aligned(pp->pid, 4)) return fail(c, PRAD_ERR_ARG, "sort_by_tile: misaligned pid");
+  return PRAD_OK;
+}
+
 template <typename R>
 int push_emit_t(prad_ctx* c, const prad_particles* pp, int64_t n,
                 int32_t nsteps) {
@@ -271,8 +344,35 @@ int push_emit_t(prad_ctx* c, const prad_particles* pp, int64_t n,
   p.w = static_cast<const R*>(pp->w);
   p.led_emit = c->d_led_emit + pp->ledger_offset;
   p.led_ll = c->d_led_ll + pp->ledger_offset;
+  p.led_n = c->cfg.max_particles - pp->ledger_offset;
+  p.pid = pp->pid;
+  if (pp->pid && !aligned(pp->pid, 4))
+    return fail(c, PRAD_ERR_ARG, "push_emit: misaligned pid array");
   p.n = n;
   p.pid0 = pp->pid0;
+  const bool tiled = c->fields.kind == PRAD_FIELD_YEE2D && c->cfg.sort_interval > 0 &&
+                     pp->pid != nullptr;
+  if (tiled) {
+    if (n > c->cfg.max_particles)
+      return fail(c, PRAD_ERR_ARG, "push_emit: n exceeds max_particles (sort scratch)");
+    int ntx, nty;
+    tile_counts(c->fields, &ntx, &nty);
+    p.ntx = ntx;
+    const int interval = c->cfg.sort_interval;
+    for (int32_t done = 0; done < nsteps;) {
+      const int32_t m = (nsteps - done) < interval ? (nsteps - done) : interval;
+      int rc = sort_t<R>(c, pp, n);
+      if (rc != PRAD_OK) return rc;
+      p.work = c->sort.work;
+      p.work_count = c->sort.work_count;
+      p.t0 = pp->t0 + done;
+      p.nsub = m;
+      const int64_t mw = max_work_items(n, c->sort.ntiles);
+      CK(c, launch_push_emit_tiled<R>(p, static_cast<int>(mw), 256, c->stream));
+      done += m;
+    }
+    return PRAD_OK;
+  }
   const int block = c->cfg.block_size > 0 ? c->cfg.block_size : 256;
   const int bps = c->cfg.blocks_per_sm > 0 ? c->cfg.blocks_per_sm : 4;
   const int64_t want = (n + block - 1) / block;
@@ -316,7 +416,7 @@ int prad_init(prad_ctx** out, const prad_config* cfg) {
     return fail(nullptr, PRAD_ERR_ARG, "prad_init: charge must be +1 or -1");
   if (cfg->block_size < 0 || cfg->block_size > 256 || (cfg->block_size % 32) != 0)
     return fail(nullptr, PRAD_ERR_ARG, "prad_init: block_size must be a multiple of 32 <= 256");
-  if (cfg->steps_per_launch < 0 || cfg->blocks_per_sm < 0)
+  if (cfg->steps_per_launch < 0 || cfg->blocks_per_sm < 0 || cfg->sort_interval < 0)
     return fail(nullptr, PRAD_ERR_ARG, "prad_init: negative launch parameter");
 
   prad_ctx* c = new (std::nothrow) prad_ctx();
@@ -372,6 +472,7 @@ int prad_init(prad_ctx** out, const prad_config* cfg) {
 
 int prad_destroy(prad_ctx* c) {
   if (!c) return PRAD_OK;
+  free_sort(c->sort);
   cudaFree(c->d_tab32);
   cudaFree(c->d_tab64);
   for (int k = 0; k < 8; ++k) cudaFree(c->d_ph[k]);
@@ -427,6 +528,16 @@ int prad_push_emit(prad_ctx* c, const prad_particles* p, int64_t n, int32_t nste
     return fail(c, PRAD_ERR_ARG, "push_emit: step index outside [0, 2^32)");
   if (c->cfg.precision == PRAD_FP32) return push_emit_t<float>(c, p, n, nsteps);
   return push_emit_t<double>(c, p, n, nsteps);
+}
+
+int prad_sort_by_tile(prad_ctx* c, const prad_particles* p, int64_t n) {
+  if (!c || !p) return fail(c, PRAD_ERR_ARG, "sort_by_tile: null argument");
+  if (n < 0) return fail(c, PRAD_ERR_ARG, "sort_by_tile: negative n");
+  int rc = check_sort_args(c, p, n);
+  if (rc != PRAD_OK) return rc;
+  if (n == 0) return PRAD_OK;
+  if (c->cfg.precision == PRAD_FP32) return sort_t<float>(c, p, n);
+  return sort_t<double>(c, p, n);
 }
 
 int prad_get_photons(prad_ctx* c, prad_photons* out, int64_t cap, int64_t* n_out,

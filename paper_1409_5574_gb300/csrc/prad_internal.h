@@ -51,7 +51,9 @@ struct StepParams {
   // particle state (SoA, in place)
   R *x, *y, *z, *ux, *uy, *uz;
   const R* w;
-  double *led_emit, *led_ll;  // already offset to particle 0
+  const uint32_t* pid;        // optional explicit ids (NULL: pid0 + i)
+  double *led_emit, *led_ll;  // already offset to the entry of id pid0
+  int64_t led_n;              // ledger entries available from that offset
   int64_t n;
   int64_t t0;                 // global step of the first substep
   uint32_t pid0, ensemble, key0, key1;
@@ -79,6 +81,30 @@ struct StepParams {
   uint32_t *ppid, *pstep;
   int64_t cap;
   unsigned long long* counters;
+  // tile-sorted Yee gather (k_push_emit_tiled)
+  const int4* work;           // (tile, first, end, 0) per work item
+  const unsigned int* work_count;
+  int32_t ntx;                // tiles along x
+};
+
+// Tile geometry of the sorted Yee gather: 32 x 32-cell tiles, staged with a
+// 4-cell halo (40 x 40 values per field component) in shared memory.
+constexpr int kTile = 32;
+constexpr int kHalo = 4;
+constexpr int kStageW = kTile + 2 * kHalo;
+constexpr int kTileSmemBytes = 6 * kStageW * kStageW * 4;
+constexpr int kChunk = 4096;  // particles per work item of the tiled kernel
+
+struct SortBuffers {
+  void* tmp[7];               // scratch copies of x y z ux uy uz w
+  uint32_t* tmp_pid;
+  unsigned int* counts;       // per tile
+  unsigned int* starts;       // per tile + 1 (exclusive scan)
+  unsigned int* cursor;       // per tile scatter cursors
+  int4* work;                 // work items of the tiled kernel
+  unsigned int* work_count;
+  int64_t capacity;           // particles
+  int32_t ntiles, max_work;
 };
 
 // Launchers (defined in the kernel translation units).
@@ -90,6 +116,13 @@ cudaError_t launch_eval_sampler(const StepParams<R>& p, const uint32_t* words,
                                 R* x_out, R* g_out, int64_t n, cudaStream_t s);
 cudaError_t launch_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1,
                           uint32_t* out, int64_t n, cudaStream_t s);
+template <typename R>
+cudaError_t launch_push_emit_tiled(const StepParams<R>& p, int max_work, int block,
+                                   cudaStream_t s);
+template <typename R>
+cudaError_t launch_tile_sort(R* arr[7], uint32_t* pid, int64_t n, const SortBuffers& b,
+                             int nx, int ny, double x0, double y0, double inv_dx,
+                             double inv_dy, cudaStream_t s);
 cudaError_t launch_ledger_reduce(const double* a, const double* b, int64_t n,
                                  double* partials, int nblocks, double* out,
                                  cudaStream_t s);

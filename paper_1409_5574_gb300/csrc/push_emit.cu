@@ -338,7 +338,240 @@ __device__ __forceinline__ void stage_photon(PhotonStage& st, int& fill,
 }
 
 // ---------------------------------------------------------------------------
-// The fused kernel.
+// Gathers for the shared-memory tile of the sorted Yee path.
+// ---------------------------------------------------------------------------
+template <typename R, int FIELD>
+struct FieldGather {
+  const StepParams<R>& P;
+  __device__ __forceinline__ EB<R> operator()(R x, R y, uint64_t phase) const {
+    return gather<R, FIELD>(P, x, y, phase);
+  }
+};
+
+// Field values of one 32 x 32-cell tile plus a 4-cell halo, all six
+// components, staged in shared memory ([component][row][column], 40 x 40).
+// A particle within 2 cells of the staged edge (it drifted since the last
+// sort) is gathered from global memory instead, so the result never depends
+// on the tile assignment.
+template <typename R>
+struct TileGather {
+  const StepParams<R>& P;
+  const float* sm;
+  R ox, oy;  // cell coordinates of staged value (0, 0)
+  __device__ __forceinline__ R comp(int c, R lx, R ly) const {
+    R wx[3], wy[3];
+    const int i0 = qs_weights(lx, wx) - 1;
+    const int j0 = qs_weights(ly, wy) - 1;
+    const float* base = sm + c * (kStageW * kStageW) + j0 * kStageW + i0;
+    R v = R(0);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const float* row = base + b * kStageW;
+      v += wy[b] * (wx[0] * R(row[0]) + wx[1] * R(row[1]) + wx[2] * R(row[2]));
+    }
+    return v;
+  }
+  __device__ __forceinline__ EB<R> operator()(R x, R y, uint64_t) const {
+    const R xi = wrap_cells((x - P.x0) * P.inv_dx, P.nx);
+    const R yi = wrap_cells((y - P.y0) * P.inv_dy, P.ny);
+    const R lx = xi - ox, ly = yi - oy;
+    const R lo = R(2), hi = R(kStageW - 2);
+    if (!(lx >= lo && lx < hi && ly >= lo && ly < hi)) return yee2d(P, x, y);
+    const R h = R(0.5);
+    EB<R> f;
+    f.Ex = comp(0, lx - h, ly);
+    f.Ey = comp(1, lx, ly - h);
+    f.Ez = comp(2, lx, ly);
+    f.Bx = comp(3, lx, ly - h);
+    f.By = comp(4, lx - h, ly);
+    f.Bz = comp(5, lx - h, ly - h);
+    return f;
+  }
+};
+
+struct Counts {
+  uint32_t dn1 = 0, clamp = 0, chi = 0, nan = 0;
+  bool bad_id = false;
+};
+
+// ---------------------------------------------------------------------------
+// One particle, nsub steps (the whole per-step path).  Warp-collective: every
+// lane of the warp calls it, inactive lanes with act = false.
+// ---------------------------------------------------------------------------
+template <typename R, int FIELD, class G>
+__device__ __forceinline__ void advance_particle(const StepParams<R>& P, const G& gat,
+                                                 int64_t i, bool act, PhotonStage& stage,
+                                                 int& fill, const PhotonOut& pout,
+                                                 Counts& cnt) {
+  R x = R(0), y = R(0), z = R(0), ux = R(0), uy = R(0), uz = R(0), w = R(0);
+  uint32_t pid = 0;
+  Acc<R> ll, le;
+  if (act) {
+    x = P.x[i]; y = P.y[i];
+    if (P.z) z = P.z[i];
+    ux = P.ux[i]; uy = P.uy[i]; uz = P.uz[i];
+    w = P.w[i];
+    pid = P.pid ? P.pid[i] : P.pid0 + static_cast<uint32_t>(i);
+  }
+  const R chk = x + y + z + ux + uy + uz + w;
+  const bool live = act && isfinite(chk);
+  if (act && !live) ++cnt.nan;
+  uint64_t phase = P.phase_t0;
+
+  for (int s = 0; s < P.nsub; ++s) {
+    const uint32_t step = static_cast<uint32_t>(P.t0 + s);
+    // 1. field at x^n, t^n
+    const EB<R> f = gat(x, y, phase);
+    phase += P.phase_step;
+    // 2. Boris: half E kick, rotation, half E kick
+    const R hq = P.half_q_dtn;
+    const R umx = ux + hq * f.Ex, umy = uy + hq * f.Ey, umz = uz + hq * f.Ez;
+    const R igm = rsq(R(1) + umx * umx + umy * umy + umz * umz);
+    const R tx = hq * f.Bx * igm, ty = hq * f.By * igm, tz = hq * f.Bz * igm;
+    const R sf = R(2) * rcp(R(1) + tx * tx + ty * ty + tz * tz);
+    const R sx = sf * tx, sy = sf * ty, sz = sf * tz;
+    const R vx = umx + (umy * tz - umz * ty);
+    const R vy = umy + (umz * tx - umx * tz);
+    const R vz = umz + (umx * ty - umy * tx);
+    R nux = umx + (vy * sz - vz * sy) + hq * f.Ex;
+    R nuy = umy + (vz * sx - vx * sz) + hq * f.Ey;
+    R nuz = umz + (vx * sy - vy * sx) + hq * f.Ez;
+    // 3. mean momentum of the step
+    const R ax = R(0.5) * (ux + nux), ay = R(0.5) * (uy + nuy), az = R(0.5) * (uz + nuz);
+    const R ua2 = ax * ax + ay * ay + az * az;
+    const R iga = rsq(R(1) + ua2);
+    const R ga = (R(1) + ua2) * iga;
+    // 4. effective field, limited by dp_perp/p <= 1 (Omega dt <= gamma)
+    R Om;
+    if (P.heff_form == PRAD_HEFF_FIELD) {
+      const R bx = ax * iga, by = ay * iga, bz = az * iga;
+      const R fx = f.Ex + (by * f.Bz - bz * f.By);
+      const R fy = f.Ey + (bz * f.Bx - bx * f.Bz);
+      const R fz = f.Ez + (bx * f.By - by * f.Bx);
+      const R eb = f.Ex * bx + f.Ey * by + f.Ez * bz;
+      const R h2 = fx * fx + fy * fy + fz * fz - eb * eb;
+      Om = P.abs_q * sqr(h2 > R(0) ? h2 : R(0));
+    } else {  // Eq. (9), gamma = mean of the end-point Lorentz factors
+      const R dx_ = nux - ux, dy_ = nuy - uy, dz_ = nuz - uz;
+      const R dp2 = dx_ * dx_ + dy_ * dy_ + dz_ * dz_;
+      const R pdp = ax * dx_ + ay * dy_ + az * dz_;
+      const R g0 = sqr(R(1) + ux * ux + uy * uy + uz * uz);
+      const R g1 = sqr(R(1) + nux * nux + nuy * nuy + nuz * nuz);
+      R c2 = ua2 * dp2 - pdp * pdp;
+      c2 = c2 > R(0) ? c2 : R(0);
+      Om = ua2 > R(0) ? R(0.5) * (g0 + g1) * sqr(c2) * rcp(ua2) * P.inv_dtn : R(0);
+    }
+    if (Om * P.dtn > ga) {
+      Om = ga * P.inv_dtn;
+      if (live) ++cnt.clamp;
+    }
+    // 5. omega_c (Eq. (1)) as hbar omega_c / m c^2; chi = eps_r Omega gamma
+    const R epsc = P.eps_r15 * Om * ga * ga;
+    if (live && P.eps_r * Om * ga > R(1)) ++cnt.chi;
+    // 6. Landau-Lifshitz loss (Eq. (4)): ledger and optional kick
+    const R om2 = Om * Om;
+    if (P.rr_mode >= PRAD_RR_LEDGER) ll.add(w * P.ll_coef * om2 * ua2);
+    if (P.rr_mode == PRAD_RR_APPLY) {
+      const R gL = sqr(R(1) + nux * nux + nuy * nuy + nuz * nuz);
+      const R fk = rcp(R(1) + P.ll_coef * om2 * gL);
+      nux *= fk; nuy *= fk; nuz *= fk;
+    }
+    // 7. position x^{n+1}
+    const R ign = rsq(R(1) + nux * nux + nuy * nuy + nuz * nuz);
+    const R dtg = P.dtn * ign;
+    R xn = x + dtg * nux, yn = y + dtg * nuy, zn = z;
+    if (P.dims == 3) zn = z + dtg * nuz;
+    if constexpr (FIELD == PRAD_FIELD_YEE2D) {
+      xn -= P.Lx * flr((xn - P.x0) * (R(1) / P.Lx));
+      yn -= P.Ly * flr((yn - P.y0) * (R(1) / P.Ly));
+    }
+    // 8. Monte Carlo emission: proposal x = P^-1(R'), dN of Eq. (13)
+    const uint4 rnd = philox10(make_uint4(pid, step, 0u, P.ensemble), P.key0, P.key1);
+    R xs, g;
+    sample_x_g(P, rnd.x, rnd.y, xs, g);
+    const R dN = P.cn_dt * Om * g * rcp(xs);
+    const R fl = flr(dN);
+    R Rr;
+    if constexpr (sizeof(R) == 4)
+      Rr = fmaf(static_cast<float>(rnd.z), 0x1p-32f, 0x1p-33f);
+    else
+      Rr = fma(static_cast<double>(rnd.z), 0x1p-32, 0x1p-33);
+    const R k = fl + ((Rr < dN - fl) ? R(1) : R(0));
+    if (live && dN > R(1)) ++cnt.dn1;
+    const bool want = live && k > R(0) && w > R(0);
+    // 9. append + emitted-energy ledger
+    const R eps = xs * epsc;
+    if (want) le.add(k * w * eps);
+    {
+      const R inv = ua2 > R(0) ? rsq(ua2) : R(0);
+      const float rec[8] = {static_cast<float>(xn), static_cast<float>(yn),
+                            static_cast<float>(zn), static_cast<float>(ax * inv),
+                            static_cast<float>(ay * inv), static_cast<float>(az * inv),
+                            static_cast<float>(eps), static_cast<float>(k * w)};
+      stage_photon(stage, fill, pout, want, rec, pid, step);
+    }
+    if (live) {
+      x = xn; y = yn; z = zn;
+      ux = nux; uy = nuy; uz = nuz;
+    }
+  }
+  if (live) {
+    P.x[i] = x; P.y[i] = y;
+    if (P.z) P.z[i] = z;
+    P.ux[i] = ux; P.uy[i] = uy; P.uz[i] = uz;
+    const int64_t li = static_cast<int64_t>(pid - P.pid0);
+    if (li < P.led_n) {
+      if (P.rr_mode >= PRAD_RR_LEDGER) P.led_ll[li] += ll.value();
+      if (le.nonzero()) P.led_emit[li] += le.value();
+    } else {
+      cnt.bad_id = true;
+    }
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ PhotonOut make_pout(const StepParams<R>& P) {
+  PhotonOut o;
+  o.f[0] = P.px; o.f[1] = P.py; o.f[2] = P.pz;
+  o.f[3] = P.pnx; o.f[4] = P.pny; o.f[5] = P.pnz;
+  o.f[6] = P.peps; o.f[7] = P.pw;
+  o.pid = P.ppid; o.step = P.pstep;
+  o.cap = P.cap; o.cursor = P.counters + kCursor;
+  return o;
+}
+
+// Block reduction of the counters: one atomic per nonzero block total.
+__device__ __forceinline__ void flush_counts(const Counts& c, unsigned long long* counters) {
+  __shared__ uint32_t red[5][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t v0 = __reduce_add_sync(0xffffffffu, c.dn1);
+  const uint32_t v1 = __reduce_add_sync(0xffffffffu, c.clamp);
+  const uint32_t v2 = __reduce_add_sync(0xffffffffu, c.chi);
+  const uint32_t v3 = __reduce_add_sync(0xffffffffu, c.nan);
+  const uint32_t v4 = __reduce_add_sync(0xffffffffu, c.bad_id ? 1u : 0u);
+  if (lane == 0) {
+    red[0][warp] = v0; red[1][warp] = v1; red[2][warp] = v2; red[3][warp] = v3;
+    red[4][warp] = v4;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      const uint32_t v = lane < nw ? red[k][lane] : 0u;
+      const uint32_t t = __reduce_add_sync(0xffffffffu, v);
+      if (lane == 0 && t) {
+        if (k < 4)
+          atomicAdd(counters + kDnGt1 + k, static_cast<unsigned long long>(t));
+        else
+          atomicOr(counters + kStatus, 2ull);  // status bit 1: id outside ledger
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The fused kernel: grid-stride over particles.
 // ---------------------------------------------------------------------------
 // Resident blocks per SM the FP32 kernels are compiled for (registers are
 // capped at 65536 / (256 * MINB)); the FP64 kernels keep the default.
@@ -356,165 +589,71 @@ struct MinBlocks<float> {
 
 template <typename R, int FIELD>
 __global__ void __launch_bounds__(256, MinBlocks<R>::value) k_push_emit(const StepParams<R> P) {
-  uint32_t c_dn1 = 0, c_clamp = 0, c_chi = 0, c_nan = 0;
-  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   __shared__ PhotonStage stage_all[kMaxWarps];
   PhotonStage& stage = stage_all[threadIdx.x >> 5];
   int fill = 0;  // warp-uniform
-  PhotonOut pout;
-  pout.f[0] = P.px; pout.f[1] = P.py; pout.f[2] = P.pz;
-  pout.f[3] = P.pnx; pout.f[4] = P.pny; pout.f[5] = P.pnz;
-  pout.f[6] = P.peps; pout.f[7] = P.pw;
-  pout.pid = P.ppid; pout.step = P.pstep;
-  pout.cap = P.cap; pout.cursor = P.counters + kCursor;
-
+  const PhotonOut pout = make_pout(P);
+  Counts cnt;
+  const FieldGather<R, FIELD> gat{P};
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   for (int64_t base = static_cast<int64_t>(blockIdx.x) * blockDim.x; base < P.n;
        base += stride) {
     const int64_t i = base + threadIdx.x;
-    const bool act = i < P.n;
-    R x = R(0), y = R(0), z = R(0), ux = R(0), uy = R(0), uz = R(0), w = R(0);
-    Acc<R> ll, le;
-    if (act) {
-      x = P.x[i]; y = P.y[i];
-      if (P.z) z = P.z[i];
-      ux = P.ux[i]; uy = P.uy[i]; uz = P.uz[i];
-      w = P.w[i];
-    }
-    const R chk = x + y + z + ux + uy + uz + w;
-    const bool live = act && isfinite(chk);
-    if (act && !live) ++c_nan;
-    const uint32_t pid = P.pid0 + static_cast<uint32_t>(i);
-    uint64_t phase = P.phase_t0;
-
-    for (int s = 0; s < P.nsub; ++s) {
-      const uint32_t step = static_cast<uint32_t>(P.t0 + s);
-      // 1. field at x^n, t^n
-      const EB<R> f = gather<R, FIELD>(P, x, y, phase);
-      phase += P.phase_step;
-      // 2. Boris: half E kick, rotation, half E kick
-      const R hq = P.half_q_dtn;
-      const R umx = ux + hq * f.Ex, umy = uy + hq * f.Ey, umz = uz + hq * f.Ez;
-      const R igm = rsq(R(1) + umx * umx + umy * umy + umz * umz);
-      const R tx = hq * f.Bx * igm, ty = hq * f.By * igm, tz = hq * f.Bz * igm;
-      const R sf = R(2) * rcp(R(1) + tx * tx + ty * ty + tz * tz);
-      const R sx = sf * tx, sy = sf * ty, sz = sf * tz;
-      const R vx = umx + (umy * tz - umz * ty);
-      const R vy = umy + (umz * tx - umx * tz);
-      const R vz = umz + (umx * ty - umy * tx);
-      R nux = umx + (vy * sz - vz * sy) + hq * f.Ex;
-      R nuy = umy + (vz * sx - vx * sz) + hq * f.Ey;
-      R nuz = umz + (vx * sy - vy * sx) + hq * f.Ez;
-      // 3. mean momentum of the step
-      const R ax = R(0.5) * (ux + nux), ay = R(0.5) * (uy + nuy),
-              az = R(0.5) * (uz + nuz);
-      const R ua2 = ax * ax + ay * ay + az * az;
-      const R iga = rsq(R(1) + ua2);
-      const R ga = (R(1) + ua2) * iga;
-      // 4. effective field, limited by dp_perp/p <= 1 (Omega dt <= gamma)
-      R Om;
-      if (P.heff_form == PRAD_HEFF_FIELD) {
-        const R bx = ax * iga, by = ay * iga, bz = az * iga;
-        const R fx = f.Ex + (by * f.Bz - bz * f.By);
-        const R fy = f.Ey + (bz * f.Bx - bx * f.Bz);
-        const R fz = f.Ez + (bx * f.By - by * f.Bx);
-        const R eb = f.Ex * bx + f.Ey * by + f.Ez * bz;
-        const R h2 = fx * fx + fy * fy + fz * fz - eb * eb;
-        Om = P.abs_q * sqr(h2 > R(0) ? h2 : R(0));
-      } else {  // Eq. (9), gamma = mean of the end-point Lorentz factors
-        const R dx_ = nux - ux, dy_ = nuy - uy, dz_ = nuz - uz;
-        const R dp2 = dx_ * dx_ + dy_ * dy_ + dz_ * dz_;
-        const R pdp = ax * dx_ + ay * dy_ + az * dz_;
-        const R g0 = sqr(R(1) + ux * ux + uy * uy + uz * uz);
-        const R g1 = sqr(R(1) + nux * nux + nuy * nuy + nuz * nuz);
-        R c2 = ua2 * dp2 - pdp * pdp;
-        c2 = c2 > R(0) ? c2 : R(0);
-        Om = ua2 > R(0) ? R(0.5) * (g0 + g1) * sqr(c2) * rcp(ua2) * P.inv_dtn : R(0);
-      }
-      if (Om * P.dtn > ga) {
-        Om = ga * P.inv_dtn;
-        if (live) ++c_clamp;
-      }
-      // 5. omega_c (Eq. (1)) as hbar omega_c / m c^2; chi = eps_r Omega gamma
-      const R epsc = P.eps_r15 * Om * ga * ga;
-      if (live && P.eps_r * Om * ga > R(1)) ++c_chi;
-      // 6. Landau-Lifshitz loss (Eq. (4)): ledger and optional kick
-      const R om2 = Om * Om;
-      if (P.rr_mode >= PRAD_RR_LEDGER) ll.add(w * P.ll_coef * om2 * ua2);
-      if (P.rr_mode == PRAD_RR_APPLY) {
-        const R gL = sqr(R(1) + nux * nux + nuy * nuy + nuz * nuz);
-        const R fk = rcp(R(1) + P.ll_coef * om2 * gL);
-        nux *= fk; nuy *= fk; nuz *= fk;
-      }
-      // 7. position x^{n+1}
-      const R ign = rsq(R(1) + nux * nux + nuy * nuy + nuz * nuz);
-      const R dtg = P.dtn * ign;
-      R xn = x + dtg * nux, yn = y + dtg * nuy, zn = z;
-      if (P.dims == 3) zn = z + dtg * nuz;
-      if constexpr (FIELD == PRAD_FIELD_YEE2D) {
-        xn -= P.Lx * flr((xn - P.x0) * (R(1) / P.Lx));
-        yn -= P.Ly * flr((yn - P.y0) * (R(1) / P.Ly));
-      }
-      // 8. Monte Carlo emission: proposal x = P^-1(R'), dN of Eq. (13)
-      const uint4 rnd = philox10(make_uint4(pid, step, 0u, P.ensemble), P.key0, P.key1);
-      R xs, g;
-      sample_x_g(P, rnd.x, rnd.y, xs, g);
-      const R dN = P.cn_dt * Om * g * rcp(xs);
-      const R fl = flr(dN);
-      R Rr;
-      if constexpr (sizeof(R) == 4)
-        Rr = fmaf(static_cast<float>(rnd.z), 0x1p-32f, 0x1p-33f);
-      else
-        Rr = fma(static_cast<double>(rnd.z), 0x1p-32, 0x1p-33);
-      const R k = fl + ((Rr < dN - fl) ? R(1) : R(0));
-      if (live && dN > R(1)) ++c_dn1;
-      const bool want = live && k > R(0) && w > R(0);
-      // 9. append + emitted-energy ledger
-      const R eps = xs * epsc;
-      if (want) le.add(k * w * eps);
-      {
-        const R inv = ua2 > R(0) ? rsq(ua2) : R(0);
-        const float rec[8] = {static_cast<float>(xn), static_cast<float>(yn),
-                              static_cast<float>(zn), static_cast<float>(ax * inv),
-                              static_cast<float>(ay * inv), static_cast<float>(az * inv),
-                              static_cast<float>(eps), static_cast<float>(k * w)};
-        stage_photon(stage, fill, pout, want, rec, pid, step);
-      }
-      if (live) {
-        x = xn; y = yn; z = zn;
-        ux = nux; uy = nuy; uz = nuz;
-      }
-    }
-    if (live) {
-      P.x[i] = x; P.y[i] = y;
-      if (P.z) P.z[i] = z;
-      P.ux[i] = ux; P.uy[i] = uy; P.uz[i] = uz;
-      if (P.rr_mode >= PRAD_RR_LEDGER) P.led_ll[i] += ll.value();
-      if (le.nonzero()) P.led_emit[i] += le.value();
-    }
+    advance_particle<R, FIELD>(P, gat, i, i < P.n, stage, fill, pout, cnt);
   }
-
   if (fill > 0) flush_stage(stage, fill, pout);
+  flush_counts(cnt, P.counters);
+}
 
-  // block reduction of the counters, one atomic per nonzero block total
-  __shared__ uint32_t red[4][32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint32_t a0 = __reduce_add_sync(0xffffffffu, c_dn1);
-  const uint32_t a1 = __reduce_add_sync(0xffffffffu, c_clamp);
-  const uint32_t a2 = __reduce_add_sync(0xffffffffu, c_chi);
-  const uint32_t a3 = __reduce_add_sync(0xffffffffu, c_nan);
-  if (lane == 0) {
-    red[0][warp] = a0; red[1][warp] = a1; red[2][warp] = a2; red[3][warp] = a3;
+// ---------------------------------------------------------------------------
+// Tile-sorted Yee kernel: one block per work item (a chunk of <= kChunk
+// particles of one tile).  The block stages the tile's six field components
+// (+ halo, periodic) in shared memory with coalesced row loads, then runs the
+// same per-particle path with the shared-memory gather.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(256, 3) k_push_emit_tiled(const StepParams<R> P) {
+  if (blockIdx.x >= *P.work_count) return;
+  extern __shared__ float tile_sm[];
+  __shared__ PhotonStage stage_all[kMaxWarps];
+  const int4 wk = P.work[blockIdx.x];
+  const int tx = wk.x % P.ntx, ty = wk.x / P.ntx;
+  const int gx0 = tx * kTile - kHalo, gy0 = ty * kTile - kHalo;
+  constexpr int kPlane = kStageW * kStageW;
+  for (int e = threadIdx.x; e < 6 * kPlane; e += blockDim.x) {
+    const int c = e / kPlane;
+    const int r = e - c * kPlane;
+    const int ly = r / kStageW;
+    const int lx = r - ly * kStageW;
+    int gx = gx0 + lx, gy = gy0 + ly;
+    gx = gx < 0 ? gx + P.nx : (gx >= P.nx ? gx - P.nx : gx);
+    gy = gy < 0 ? gy + P.ny : (gy >= P.ny ? gy - P.ny : gy);
+    tile_sm[e] = __ldg(P.yee[c] + static_cast<size_t>(gy) * P.nx + gx);
   }
   __syncthreads();
-  if (warp == 0) {
-    const int nw = blockDim.x >> 5;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const uint32_t v = lane < nw ? red[c][lane] : 0u;
-      const uint32_t t = __reduce_add_sync(0xffffffffu, v);
-      if (lane == 0 && t) atomicAdd(P.counters + kDnGt1 + c, static_cast<unsigned long long>(t));
-    }
+  PhotonStage& stage = stage_all[threadIdx.x >> 5];
+  int fill = 0;
+  const PhotonOut pout = make_pout(P);
+  Counts cnt;
+  const TileGather<R> gat{P, tile_sm, static_cast<R>(gx0), static_cast<R>(gy0)};
+  for (int64_t base = wk.y; base < wk.z; base += blockDim.x) {
+    const int64_t i = base + threadIdx.x;
+    advance_particle<R, PRAD_FIELD_YEE2D>(P, gat, i, i < wk.z, stage, fill, pout, cnt);
   }
+  if (fill > 0) flush_stage(stage, fill, pout);
+  flush_counts(cnt, P.counters);
+}
+
+template <typename R>
+cudaError_t launch_push_emit_tiled(const StepParams<R>& p, int max_work, int block,
+                                   cudaStream_t s) {
+  // dynamic tile (38.4 KB) + static photon staging exceed the 48 KB default
+  cudaError_t e = cudaFuncSetAttribute(k_push_emit_tiled<R>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       kTileSmemBytes);
+  if (e != cudaSuccess) return e;
+  k_push_emit_tiled<R><<<max_work, block, kTileSmemBytes, s>>>(p);
+  return cudaGetLastError();
 }
 
 template <typename R>
@@ -580,6 +719,8 @@ cudaError_t launch_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1,
 
 template cudaError_t launch_push_emit<float>(const StepParams<float>&, int, int, int, cudaStream_t);
 template cudaError_t launch_push_emit<double>(const StepParams<double>&, int, int, int, cudaStream_t);
+template cudaError_t launch_push_emit_tiled<float>(const StepParams<float>&, int, int, cudaStream_t);
+template cudaError_t launch_push_emit_tiled<double>(const StepParams<double>&, int, int, cudaStream_t);
 template cudaError_t launch_eval_sampler<float>(const StepParams<float>&, const uint32_t*, float*, float*, int64_t, cudaStream_t);
 template cudaError_t launch_eval_sampler<double>(const StepParams<double>&, const uint32_t*, double*, double*, int64_t, cudaStream_t);
 

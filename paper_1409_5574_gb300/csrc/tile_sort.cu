@@ -1,0 +1,150 @@
+// Counting sort of particles by the 32 x 32-cell tile of the 2D Yee grid that
+// holds them (histogram -> exclusive scan -> scatter -> copy back), and the
+// work list of the tile-staged gather kernel: one item per chunk of at most
+// kChunk particles of one tile.  Particles keep their ids (pid array), so the
+// Philox streams and ledger entries follow them.  The order inside a tile
+// depends on atomic timing; results per particle do not.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "prad_internal.h"
+
+namespace prad {
+
+namespace {
+
+template <typename R>
+__device__ __forceinline__ int tile_of(R x, R y, int nx, int ny, int ntx, R x0, R y0,
+                                       R inv_dx, R inv_dy) {
+  // periodic cell coordinate in [0, n), clamped (also for NaN) into range
+  R xi = (x - x0) * inv_dx, yi = (y - y0) * inv_dy;
+  const R fx = static_cast<R>(nx), fy = static_cast<R>(ny);
+  xi -= fx * floor(xi / fx);
+  yi -= fy * floor(yi / fy);
+  int ix = static_cast<int>(fmin(fmax(xi, R(0)), fx - R(1)));
+  int iy = static_cast<int>(fmin(fmax(yi, R(0)), fy - R(1)));
+  ix = ix < 0 ? 0 : (ix >= nx ? nx - 1 : ix);
+  iy = iy < 0 ? 0 : (iy >= ny ? ny - 1 : iy);
+  return (iy / kTile) * ntx + (ix / kTile);
+}
+
+template <typename R>
+__global__ void k_tile_count(const R* __restrict__ x, const R* __restrict__ y, int64_t n,
+                             int nx, int ny, int ntx, R x0, R y0, R inv_dx, R inv_dy,
+                             unsigned int* __restrict__ counts) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    atomicAdd(counts + tile_of(x[i], y[i], nx, ny, ntx, x0, y0, inv_dx, inv_dy), 1u);
+  }
+}
+
+// One block: exclusive scan of the tile counts (starts, scatter cursors) and
+// of the per-tile chunk counts (work list offsets); writes the work list.
+constexpr int kScanThreads = 1024;
+
+__global__ void __launch_bounds__(kScanThreads)
+    k_tile_scan(const unsigned int* __restrict__ counts, int ntiles,
+                unsigned int* __restrict__ starts, unsigned int* __restrict__ cursor,
+                int4* __restrict__ work, unsigned int* __restrict__ work_count) {
+  __shared__ unsigned int s_part[kScanThreads], s_chunk[kScanThreads];
+  const int per = (ntiles + kScanThreads - 1) / kScanThreads;
+  const int lo = threadIdx.x * per;
+  const int hi = min(lo + per, ntiles);
+  unsigned int sum = 0, csum = 0;
+  for (int t = lo; t < hi; ++t) {
+    sum += counts[t];
+    csum += (counts[t] + kChunk - 1) / kChunk;
+  }
+  s_part[threadIdx.x] = sum;
+  s_chunk[threadIdx.x] = csum;
+  __syncthreads();
+  // Hillis-Steele inclusive scan over the thread partials
+  for (int off = 1; off < kScanThreads; off <<= 1) {
+    const unsigned int a = threadIdx.x >= off ? s_part[threadIdx.x - off] : 0u;
+    const unsigned int b = threadIdx.x >= off ? s_chunk[threadIdx.x - off] : 0u;
+    __syncthreads();
+    s_part[threadIdx.x] += a;
+    s_chunk[threadIdx.x] += b;
+    __syncthreads();
+  }
+  unsigned int run = s_part[threadIdx.x] - sum;
+  unsigned int wrun = s_chunk[threadIdx.x] - csum;
+  for (int t = lo; t < hi; ++t) {
+    const unsigned int c = counts[t];
+    starts[t] = run;
+    cursor[t] = run;
+    for (unsigned int f = 0; f < c; f += kChunk) {
+      const unsigned int e = f + kChunk < c ? f + kChunk : c;
+      work[wrun++] = make_int4(t, static_cast<int>(run + f), static_cast<int>(run + e), 0);
+    }
+    run += c;
+  }
+  if (threadIdx.x == kScanThreads - 1) {
+    starts[ntiles] = run;
+    *work_count = wrun;
+  }
+}
+
+template <typename R>
+struct Arrays7 {
+  R* p[7];  // x y z ux uy uz w (z may be null)
+};
+
+template <typename R>
+__global__ void k_tile_scatter(const Arrays7<R> src, const Arrays7<R> dst,
+                               const uint32_t* __restrict__ pid, uint32_t* __restrict__ pid_out,
+                               int64_t n, int nx, int ny, int ntx, R x0, R y0, R inv_dx,
+                               R inv_dy, unsigned int* __restrict__ cursor) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int t = tile_of(src.p[0][i], src.p[1][i], nx, ny, ntx, x0, y0, inv_dx, inv_dy);
+    const unsigned int d = atomicAdd(cursor + t, 1u);
+#pragma unroll
+    for (int k = 0; k < 7; ++k)
+      if (src.p[k]) dst.p[k][d] = src.p[k][i];
+    pid_out[d] = pid[i];
+  }
+}
+
+}  // namespace
+
+template <typename R>
+cudaError_t launch_tile_sort(R* arr[7], uint32_t* pid, int64_t n, const SortBuffers& b,
+                             int nx, int ny, double x0, double y0, double inv_dx,
+                             double inv_dy, cudaStream_t s) {
+  const int ntx = (nx + kTile - 1) / kTile;
+  cudaError_t e = cudaMemsetAsync(b.counts, 0, sizeof(unsigned int) * b.ntiles, s);
+  if (e != cudaSuccess) return e;
+  const int block = 256;
+  const int64_t want = (n + block - 1) / block;
+  const int grid = static_cast<int>(want < 8192 ? (want > 0 ? want : 1) : 8192);
+  k_tile_count<R><<<grid, block, 0, s>>>(arr[0], arr[1], n, nx, ny, ntx, R(x0), R(y0),
+                                         R(inv_dx), R(inv_dy), b.counts);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_tile_scan<<<1, kScanThreads, 0, s>>>(b.counts, b.ntiles, b.starts, b.cursor, b.work,
+                                          b.work_count);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  Arrays7<R> srcp, dstp;
+  for (int k = 0; k < 7; ++k) {
+    srcp.p[k] = arr[k];
+    dstp.p[k] = arr[k] ? static_cast<R*>(b.tmp[k]) : nullptr;
+  }
+  k_tile_scatter<R><<<grid, block, 0, s>>>(srcp, dstp, pid, b.tmp_pid, n, nx, ny, ntx, R(x0),
+                                           R(y0), R(inv_dx), R(inv_dy), b.cursor);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  for (int k = 0; k < 7; ++k) {
+    if (!arr[k]) continue;
+    e = cudaMemcpyAsync(arr[k], b.tmp[k], sizeof(R) * n, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaMemcpyAsync(pid, b.tmp_pid, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s);
+}
+
+template cudaError_t launch_tile_sort<float>(float* [7], uint32_t*, int64_t, const SortBuffers&,
+                                             int, int, double, double, double, double,
+                                             cudaStream_t);
+template cudaError_t launch_tile_sort<double>(double* [7], uint32_t*, int64_t,
+                                              const SortBuffers&, int, int, double, double,
+                                              double, double, cudaStream_t);
+
+}  // namespace prad

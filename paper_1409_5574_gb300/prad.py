@@ -39,7 +39,7 @@ class prad_config(ctypes.Structure):
                 ("charge", _dbl), ("seed", _u64), ("ensemble", _u32),
                 ("steps_per_launch", _i32), ("photon_capacity", _i64),
                 ("max_particles", _i64), ("stream", _vp), ("block_size", _i32),
-                ("blocks_per_sm", _i32)]
+                ("blocks_per_sm", _i32), ("sort_interval", _i32), ("pad0", _i32)]
 
 
 class prad_fields(ctypes.Structure):
@@ -51,8 +51,8 @@ class prad_fields(ctypes.Structure):
 
 class prad_particles(ctypes.Structure):
     _fields_ = [("x", _vp), ("y", _vp), ("z", _vp), ("ux", _vp), ("uy", _vp),
-                ("uz", _vp), ("w", _vp), ("ledger_offset", _i64), ("pid0", _u32),
-                ("pad0", _u32), ("t0", _i64)]
+                ("uz", _vp), ("w", _vp), ("pid", _vp), ("ledger_offset", _i64),
+                ("pid0", _u32), ("pad0", _u32), ("t0", _i64)]
 
 
 class prad_photons(ctypes.Structure):
@@ -73,6 +73,7 @@ SIGNATURES = {
     "prad_last_error": (ctypes.c_char_p, [_vp]),
     "prad_set_fields": (_i32, [_vp, ctypes.POINTER(prad_fields)]),
     "prad_push_emit": (_i32, [_vp, ctypes.POINTER(prad_particles), _i64, _i32]),
+    "prad_sort_by_tile": (_i32, [_vp, ctypes.POINTER(prad_particles), _i64]),
     "prad_get_photons": (_i32, [_vp, ctypes.POINTER(prad_photons), _i64,
                                 ctypes.POINTER(_i64), ctypes.POINTER(_i64), _i32, _i32]),
     "prad_energy_budget": (_i32, [_vp, ctypes.POINTER(_dbl), ctypes.POINTER(_dbl),
@@ -137,6 +138,10 @@ def prad_push_emit(h, p: prad_particles, n: int, nsteps: int) -> int:
     return _check(load_library().prad_push_emit(h, ctypes.byref(p), n, nsteps), h)
 
 
+def prad_sort_by_tile(h, p: prad_particles, n: int) -> int:
+    return _check(load_library().prad_sort_by_tile(h, ctypes.byref(p), n), h)
+
+
 def prad_get_photons(h, out: Optional[prad_photons], cap: int, drain: bool,
                      out_on_device: bool):
     n_out, n_drop = _i64(), _i64()
@@ -191,7 +196,7 @@ class Context:
                  photon_capacity: int = 1 << 20, max_particles: int = 1 << 20,
                  steps_per_launch: int = 1, stream=None, block_size: int = 0,
                  blocks_per_sm: int = 0, sampler: int = PRAD_SAMPLER_TABLE,
-                 ensemble: int = 0):
+                 ensemble: int = 0, sort_interval: int = 0):
         torch = _torch()
         if not torch.cuda.is_available():
             raise RuntimeError("prad needs a CUDA device")
@@ -216,6 +221,7 @@ class Context:
         cfg.stream = self.stream.cuda_stream
         cfg.block_size = block_size
         cfg.blocks_per_sm = blocks_per_sm
+        cfg.sort_interval = sort_interval
         self.cfg = cfg
         self.capacity = photon_capacity
         self.max_particles = max_particles
@@ -252,22 +258,42 @@ class Context:
         prad_set_fields(self.h, f)
 
     # -- state ---------------------------------------------------------------
-    def to_device(self, state: Dict, device="cuda") -> Dict:
+    def to_device(self, state: Dict, device="cuda", with_pid: bool = False,
+                  pid0: int = 0) -> Dict:
+        """Copy a state dict to the device in the context precision; with
+        ``with_pid`` add an int32 id array pid0 + i (ids move with particles
+        that a tile sort reorders)."""
         torch = self.torch
-        return {k: torch.as_tensor(v, dtype=self.dtype).to(device).contiguous()
-                for k, v in state.items()}
+        out = {k: torch.as_tensor(v, dtype=self.dtype).to(device).contiguous()
+               for k, v in state.items()}
+        if self.fields.kind == PRAD_FIELD_YEE2D:
+            out.pop("z", None)
+        if with_pid:
+            n = out["x"].numel()
+            out["pid"] = (torch.arange(n, dtype=torch.int64, device=device) + pid0).to(torch.int32)
+        return out
 
-    def push_emit(self, st: Dict, nsteps: int, t0: int = 0, pid0: int = 0,
-                  ledger_offset: int = 0) -> None:
-        n = st["x"].numel()
+    def _particles(self, st: Dict, t0: int, pid0: int, ledger_offset: int) -> prad_particles:
         p = prad_particles()
         p.x, p.y = _ptr(st["x"]), _ptr(st["y"])
-        p.z = _ptr(st.get("z")) if self.fields.kind != PRAD_FIELD_YEE2D or "z" in st else None
+        p.z = _ptr(st.get("z"))
         p.ux, p.uy, p.uz, p.w = _ptr(st["ux"]), _ptr(st["uy"]), _ptr(st["uz"]), _ptr(st["w"])
+        p.pid = _ptr(st.get("pid"))
         p.ledger_offset = ledger_offset
         p.pid0 = pid0
         p.t0 = t0
-        prad_push_emit(self.h, p, n, nsteps)
+        return p
+
+    def push_emit(self, st: Dict, nsteps: int, t0: int = 0, pid0: int = 0,
+                  ledger_offset: int = 0) -> None:
+        """Advance the particles of ``st`` (torch tensors x y z ux uy uz w and an
+        optional int32 ``pid``; ``z`` may be absent for the Yee grid)."""
+        n = st["x"].numel()
+        prad_push_emit(self.h, self._particles(st, t0, pid0, ledger_offset), n, nsteps)
+
+    def sort_by_tile(self, st: Dict, pid0: int = 0, ledger_offset: int = 0) -> None:
+        n = st["x"].numel()
+        prad_sort_by_tile(self.h, self._particles(st, 0, pid0, ledger_offset), n)
 
     def photons(self, drain: bool = False, on_device: bool = True,
                 cap: Optional[int] = None) -> Dict:

@@ -1,0 +1,179 @@
+"""2D Yee-grid gather (quadratic splines, staggered components) and the tile
+sort, GPU through the C ABI vs the FP64 oracle.
+
+Small grids that are not multiples of the 32-cell tile, particles everywhere
+(including across the periodic seams), the plain global-memory gather and the
+tile-sorted shared-memory gather; then the 4096^2 standing-wave workload at
+full size in the sorted launch configuration, checked on a pid-strided
+10^4-particle subset.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1409_5574_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if torch.cuda.is_available():
+    from paper_1409_5574_gb300 import prad
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    prad.load_library()
+
+
+def _small_yee(nx=130, ny=100, n=6000 + 13, seed=3, a0=300.0):
+    rng = np.random.default_rng(seed)
+    dxn = 2 * np.pi / 32
+    planes = W.yee_planes(nx, ny, a0, dxn, rng)
+    wl = W.yee2d(n_grid=64, slab=32, n_particles=n, seed=seed, with_grid=False)
+    wl.yee = planes
+    # particles over the whole grid, including the periodic seams
+    wl.state["x"] = rng.uniform(-0.5, nx + 0.5, n) * dxn
+    wl.state["y"] = rng.uniform(-0.5, ny + 0.5, n) * dxn
+    return wl
+
+
+def _gpu_run(wl, nsteps, precision, sort_interval=0, with_pid=False, cap=1 << 20):
+    ctx = prad.Context(wl.problem_kwargs(), precision=precision, photon_capacity=cap,
+                       max_particles=wl.n, sort_interval=sort_interval)
+    st = ctx.to_device(wl.state, with_pid=with_pid)
+    ctx.push_emit(st, nsteps)
+    torch.cuda.synchronize()
+    ph = ctx.photons(on_device=False)
+    e, l, stats = ctx.energy_budget()
+    le, ll = ctx.ledger()
+    out = {k: v.double().cpu().numpy() for k, v in st.items() if k != "pid"}
+    pid = st["pid"].cpu().numpy().view(np.uint32) if "pid" in st else np.arange(wl.n)
+    order = np.argsort(pid)
+    out = {k: v[order] for k, v in out.items()}
+    ctx.close()
+    return dict(state=out, photons={k: (v.numpy() if hasattr(v, "numpy") else v)
+                                    for k, v in ph.items()},
+                emitted=e, ll=l, stats=stats, led_ll=ll.cpu().numpy(),
+                led_emit=le.cpu().numpy())
+
+
+def _oracle(wl, nsteps, pid=None):
+    st = wl.copy_state()
+    res = O.run(O.Problem(**wl.problem_kwargs()), st, nsteps, pid=pid,
+                capacity=1 << 20, trial_log=False)
+    res["state"] = st
+    return res
+
+
+def _urel(a, b):
+    ua = np.stack([a["ux"], a["uy"], a["uz"]], 1)
+    ub = np.stack([b["ux"], b["uy"], b["uz"]], 1)
+    return np.abs(ua - ub).max(1) / np.linalg.norm(ub, axis=1)
+
+
+def _pos_err(a, b, L):
+    d = np.abs(a - b)
+    return np.minimum(d, L - d)      # periodic distance
+
+
+def _photon_match(g, r):
+    kg = g["pid"].astype(np.int64) * 2**32 + g["step"].astype(np.int64)
+    kr = r["pid"].astype(np.int64) * 2**32 + r["step"].astype(np.int64)
+    common = np.intersect1d(kg, kr)
+    return common.size / max(1, max(kg.size, kr.size)), kg.size, kr.size
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("fp32", 1e-5)])
+def test_yee_plain_gather_parity(precision, tol):
+    wl = _small_yee()
+    p = prad.PRAD_FP64 if precision == "fp64" else prad.PRAD_FP32
+    g = _gpu_run(wl, 25, p)
+    r = _oracle(wl, 25)
+    assert _urel(g["state"], r["state"]).max() <= tol
+    Lx = wl.yee[0].shape[1] * wl.dx
+    assert _pos_err(g["state"]["x"], r["state"]["x"], Lx).max() < 1e-4
+    frac, ng, nr = _photon_match(g["photons"], r["photons"])
+    assert frac >= 0.999 and nr > 500
+    assert g["ll"] == pytest.approx(r["ledger"]["ll"].sum(), rel=1e-4 if p == prad.PRAD_FP32 else 1e-10)
+    assert g["emitted"] == pytest.approx(r["ledger"]["emit"].sum(), rel=2e-3)
+
+
+def test_tile_sort_is_a_tile_ordered_permutation():
+    wl = _small_yee(nx=200, ny=70, n=50_000 + 7)
+    ctx = prad.Context(wl.problem_kwargs(), precision=prad.PRAD_FP32,
+                       max_particles=wl.n, photon_capacity=16, sort_interval=4)
+    st = ctx.to_device(wl.state, with_pid=True)
+    before = {k: v.clone() for k, v in st.items()}
+    ctx.sort_by_tile(st)
+    torch.cuda.synchronize()
+    pid = st["pid"].cpu().numpy()
+    assert np.array_equal(np.sort(pid), np.arange(wl.n))
+    for k in ("x", "y", "ux", "uy", "uz", "w"):
+        np.testing.assert_array_equal(st[k].cpu().numpy(), before[k].cpu().numpy()[pid])
+    dxn = wl.dx
+    xi = np.mod(st["x"].double().cpu().numpy() / dxn, 200)
+    yi = np.mod(st["y"].double().cpu().numpy() / dxn, 70)
+    tile = (np.clip(yi.astype(int), 0, 69) // 32) * 7 + np.clip(xi.astype(int), 0, 199) // 32
+    # tile index non-decreasing (a particle within float rounding of a tile
+    # edge may be counted on either side)
+    assert np.mean(np.diff(tile) < 0) < 1e-3
+    ctx.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("fp32", 1e-5)])
+def test_yee_tiled_gather_parity(precision, tol):
+    """sort_interval > 0: particles reordered by tile every 6 steps, fields
+    gathered from shared-memory tiles (global fallback near tile edges)."""
+    wl = _small_yee(nx=160, ny=96, n=20_000 + 5)
+    p = prad.PRAD_FP64 if precision == "fp64" else prad.PRAD_FP32
+    g = _gpu_run(wl, 25, p, sort_interval=6, with_pid=True)
+    r = _oracle(wl, 25)
+    assert _urel(g["state"], r["state"]).max() <= tol
+    frac, ng, nr = _photon_match(g["photons"], r["photons"])
+    assert frac >= 0.999 and nr > 1000
+    assert g["ll"] == pytest.approx(r["ledger"]["ll"].sum(), rel=1e-4 if p == prad.PRAD_FP32 else 1e-10)
+    # ledger entries follow the ids through the sorts
+    np.testing.assert_allclose(g["led_ll"], r["ledger"]["ll"],
+                               rtol=2e-4 if p == prad.PRAD_FP32 else 1e-10, atol=1e-30)
+
+
+def test_yee_tiled_equals_plain_fp32():
+    wl = _small_yee(nx=128, ny=128, n=30_000)
+    a = _gpu_run(wl, 20, prad.PRAD_FP32)
+    b = _gpu_run(wl, 20, prad.PRAD_FP32, sort_interval=5, with_pid=True)
+    assert _urel(a["state"], b["state"]).max() < 2e-6
+    assert a["stats"]["records"] == pytest.approx(b["stats"]["records"], rel=1e-3)
+
+
+def test_yee_full_size_subset_parity():
+    """The 4096^2 standing wave (a0 = 300, 1% noise), 16M electrons in the
+    central 1024^2 cells, sorted every 8 steps (the benchmarked launch shape),
+    40 steps; the oracle follows every 1600th electron."""
+    wl = W.yee2d(nsteps=40, seed=1)
+    ctx = prad.Context(wl.problem_kwargs(), precision=prad.PRAD_FP32,
+                       photon_capacity=1 << 26, max_particles=wl.n, sort_interval=8,
+                       steps_per_launch=8)
+    st = ctx.to_device(wl.state, with_pid=True)
+    ctx.push_emit(st, 40)
+    torch.cuda.synchronize()
+    e, l, stats = ctx.energy_budget()
+    assert stats["dropped"] == 0 and stats["status"] == 0
+    pid = st["pid"].cpu().numpy()
+    sel = np.arange(0, wl.n, 1600)
+    inv = np.empty(wl.n, dtype=np.int64)
+    inv[pid] = np.arange(wl.n)
+    gstate = {k: st[k][torch.from_numpy(inv[sel]).cuda()].double().cpu().numpy()
+              for k in ("x", "y", "ux", "uy", "uz")}
+    sub = wl.subset(sel)
+    r = _oracle(sub, 40, pid=sel.astype(np.uint32))
+    assert _urel(gstate, r["state"]).max() <= 1e-5
+    le, ll = ctx.ledger()
+    np.testing.assert_allclose(ll.cpu().numpy()[sel], r["ledger"]["ll"], rtol=1e-4)
+    ph = ctx.photons(on_device=False)
+    keep = np.isin(ph["pid"].numpy(), sel)
+    gp = {k: ph[k].numpy()[keep] for k in ("pid", "step")}
+    frac, ng, nr = _photon_match(gp, r["photons"])
+    assert frac >= 0.999 and nr > 1000
+    ctx.close()

@@ -625,9 +625,11 @@ __global__ void __launch_bounds__(256, 3) k_push_emit_tiled(const StepParams<R> 
     const int r = e - c * kPlane;
     const int ly = r / kStageW;
     const int lx = r - ly * kStageW;
-    int gx = gx0 + lx, gy = gy0 + ly;
-    gx = gx < 0 ? gx + P.nx : (gx >= P.nx ? gx - P.nx : gx);
-    gy = gy < 0 ? gy + P.ny : (gy >= P.ny ? gy - P.ny : gy);
+    // periodic indices; a full modulo, since grids may be smaller than the
+    // staged 40 x 40 region
+    int gx = (gx0 + lx) % P.nx, gy = (gy0 + ly) % P.ny;
+    gx += gx < 0 ? P.nx : 0;
+    gy += gy < 0 ? P.ny : 0;
     tile_sm[e] = __ldg(P.yee[c] + static_cast<size_t>(gy) * P.nx + gx);
   }
   __syncthreads();

@@ -151,10 +151,17 @@ def test_constB_fp64_parity():
         assert abs(gpu["stats"][k] - ref["stats"][k]) <= max(1, ref["stats"][k] // 1000)
 
 
+def _f32_inputs(wl):
+    """The FP32 path's inputs exactly (state rounded to float32)."""
+    w = wl.subset(np.arange(wl.n))
+    w.state = {k: v.astype(np.float32).astype(np.float64) for k, v in w.state.items()}
+    return w
+
+
 @pytest.mark.parametrize("a0", [100.0, 300.0, 500.0])
 def test_planewave_fp32_parity(a0):
     nsteps = 40
-    wl = W.plane_wave(a0=a0, n=4096 + 77, seed=7)
+    wl = _f32_inputs(W.plane_wave(a0=a0, n=4096 + 77, seed=7))
     gpu = _run_gpu(wl, nsteps, prad.PRAD_FP32)
     ref = _run_oracle(wl, nsteps)
     rel = _momentum_rel(gpu["state"], ref["state"])

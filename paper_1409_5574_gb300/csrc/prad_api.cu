@@ -218,7 +218,9 @@ void fill_common(const prad_ctx* c, StepParams<R>& p) {
   if (f.kind == PRAD_FIELD_PLANE_WAVE) {
     const double wn = (2.0 * kPi * kC / f.lambda) / w;  // omega_L / omega_ref
     p.E0 = static_cast<R>(f.a0 * wn);
-    p.kc = static_cast<R>(f.dir * wn / (2.0 * kPi));
+    const double kcd = f.dir * wn / (2.0 * kPi);
+    p.kc = static_cast<R>(kcd);
+    p.kc_lo = static_cast<R>(kcd - static_cast<double>(p.kc));
     p.hand = static_cast<R>(f.hand);
     p.dir = static_cast<R>(f.dir);
     // fixed-point cycles: phase0 / 2pi and omega_L dt / 2pi, modulo 1
@@ -229,7 +231,7 @@ void fill_common(const prad_ctx* c, StepParams<R>& p) {
     p.phase_t0 = static_cast<uint64_t>(std::ldexp(c0, 64));
     p.phase_step = static_cast<uint64_t>(std::ldexp(cs, 64));
   } else {
-    p.E0 = p.kc = p.hand = p.dir = R(0);
+    p.E0 = p.kc = p.kc_lo = p.hand = p.dir = R(0);
     p.phase_t0 = p.phase_step = 0;
   }
   if (f.kind == PRAD_FIELD_YEE2D) {
@@ -237,6 +239,8 @@ void fill_common(const prad_ctx* c, StepParams<R>& p) {
     p.nx = f.nx; p.ny = f.ny;
     p.inv_dx = static_cast<R>(1.0 / f.dx);
     p.inv_dy = static_cast<R>(1.0 / f.dy);
+    p.inv_dx_lo = static_cast<R>(1.0 / f.dx - static_cast<double>(p.inv_dx));
+    p.inv_dy_lo = static_cast<R>(1.0 / f.dy - static_cast<double>(p.inv_dy));
     p.x0 = static_cast<R>(f.x0);
     p.y0 = static_cast<R>(f.y0);
     p.Lx = static_cast<R>(f.nx * f.dx);
@@ -246,6 +250,7 @@ void fill_common(const prad_ctx* c, StepParams<R>& p) {
     for (int k = 0; k < 6; ++k) p.yee[k] = nullptr;
     p.nx = p.ny = 0;
     p.inv_dx = p.inv_dy = p.x0 = p.y0 = p.Lx = p.Ly = R(0);
+    p.inv_dx_lo = p.inv_dy_lo = R(0);
   }
 }
 

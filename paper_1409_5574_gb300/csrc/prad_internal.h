@@ -67,11 +67,12 @@ struct StepParams {
   R ll_coef;    // (2/3) alpha eps_r dtn
   // field
   R E[3], B[3];
-  R E0, kc, hand, dir;         // plane wave
+  R E0, kc, kc_lo, hand, dir;  // plane wave (kc + kc_lo: k/2pi to ~2^-48)
   uint64_t phase_t0, phase_step;  // fixed-point phase (cycles * 2^64)
   const float* yee[6];
   int32_t nx, ny;
   R inv_dx, inv_dy, x0, y0, Lx, Ly;
+  R inv_dx_lo, inv_dy_lo;      // low parts of 1/dx, 1/dy (float-float)
   // sampling table
   const typename TabOf<R>::T* tab;
   R t_scale, x_scale, a;

@@ -175,7 +175,12 @@ __device__ __forceinline__ EB<R> plane_wave(const StepParams<R>& P, R x,
     psi_t = static_cast<float>(static_cast<uint32_t>(phase >> 32)) * 0x1p-32f;
   else
     psi_t = static_cast<double>(phase >> 11) * 0x1p-53;
-  R psi = psi_t - P.kc * x;
+  // k x / 2pi in float-float: exact product error (fma) plus the low part
+  // of k/2pi; the whole cycles are removed from the high part exactly, so
+  // the phase keeps ~1e-7-cycle accuracy at any |x|
+  const R p_hi = P.kc * x;
+  const R p_lo = fma(P.kc, x, -p_hi) + P.kc_lo * x;
+  R psi = (psi_t - (p_hi - rnd_int(p_hi))) - p_lo;
   psi -= rnd_int(psi);
   R s, c;
   sincos_pi(psi + psi, &s, &c);
@@ -189,11 +194,48 @@ __device__ __forceinline__ EB<R> plane_wave(const StepParams<R>& P, R x,
   return f;
 }
 
-// Quadratic-spline (second-order) weights about the nearest node.
+// Cell coordinate of a position along one axis, split into the integer cell
+// c in [0, n] and the offset f in [0, 1] within it.  (x - x0) / dx is formed
+// in float-float (TwoSum of the difference, exact product error by fma, low
+// part of 1/dx), so f keeps ~1e-7 cell accuracy even thousands of cells
+// from the origin, where a plain FP32 product would be off by ~2e-4 cell.
+// Periodic wrap; NaN and far-out values are clamped into the grid, so every
+// stencil index derived from c stays in [-1, n + 1].
 template <typename R>
-__device__ __forceinline__ int qs_weights(R xi, R w[3]) {
-  const R nr = flr(xi + R(0.5));
-  const R d = xi - nr;
+struct Cell {
+  int c;
+  R f;
+};
+
+template <typename R>
+__device__ __forceinline__ Cell<R> cell_of(R x, R x0, R inv, R inv_lo, int n) {
+  const R d_hi = x - x0;
+  const R bb = d_hi - x;
+  const R d_lo = (x - (d_hi - bb)) - (x0 + bb);  // exact: x - x0 = d_hi + d_lo
+  const R hi = d_hi * inv;
+  const R lo = fma(d_hi, inv, -hi) + (d_hi * inv_lo + d_lo * inv);
+  const R nr = static_cast<R>(n);
+  R c = flr(hi);
+  R f = (hi - c) + lo;             // hi - c is exact
+  c -= nr * flr(c * (R(1) / nr));  // wrap the integer part
+  const R fl = flr(f);             // f may leave [0,1) by the lo correction
+  c += fl;
+  f -= fl;
+  c = c < R(0) ? c + nr : (c >= nr ? c - nr : c);
+  Cell<R> r;
+  const bool ok = c >= R(0) && c < nr && f >= R(0) && f <= R(1);
+  r.c = ok ? static_cast<int>(c) : 0;
+  r.f = ok ? f : R(0);
+  return r;
+}
+
+// Quadratic-spline (second-order) weights about the nearest node for the
+// offset t of a staggered component (t = f - shift, in [-1/2, 1]); returns
+// the nearest node relative to the cell (0 or 1, or -... never below -1).
+template <typename R>
+__device__ __forceinline__ int qs_weights(R t, R w[3]) {
+  const R nr = flr(t + R(0.5));
+  const R d = t - nr;
   w[0] = R(0.5) * (R(0.5) - d) * (R(0.5) - d);
   w[1] = R(0.75) - d * d;
   w[2] = R(0.5) * (R(0.5) + d) * (R(0.5) + d);
@@ -202,12 +244,13 @@ __device__ __forceinline__ int qs_weights(R xi, R w[3]) {
 
 template <typename R>
 __device__ __forceinline__ R yee_component(const StepParams<R>& P,
-                                           const float* __restrict__ F, R xi,
-                                           R yi) {
+                                           const float* __restrict__ F,
+                                           const Cell<R>& cx, const Cell<R>& cy, R sx,
+                                           R sy) {
   R wx[3], wy[3];
-  int i0 = qs_weights(xi, wx) - 1;
-  int j0 = qs_weights(yi, wy) - 1;
-  // periodic indices of the 3 x 3 stencil
+  const int i0 = cx.c + qs_weights(cx.f - sx, wx) - 1;
+  const int j0 = cy.c + qs_weights(cy.f - sy, wy) - 1;
+  // periodic indices of the 3 x 3 stencil (i0 in [-1, n])
   int ii[3], jj[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
@@ -231,27 +274,24 @@ __device__ __forceinline__ R yee_component(const StepParams<R>& P,
 // 2D Yee grid: Ex (i+1/2, j), Ey (i, j+1/2), Ez (i, j), Bx (i, j+1/2),
 // By (i+1/2, j), Bz (i+1/2, j+1/2).
 template <typename R>
-__device__ __forceinline__ R wrap_cells(R xi, int n) {
-  // periodic image in [0, n]; the clamp also maps NaN and huge values into
-  // range, so every stencil index below stays inside [-1, n + 1]
-  const R nr = static_cast<R>(n);
-  xi -= nr * flr(xi * (R(1) / nr));
-  return fmin(fmax(xi, R(0)), nr);
+__device__ __forceinline__ EB<R> yee2d_cells(const StepParams<R>& P, const Cell<R>& cx,
+                                             const Cell<R>& cy) {
+  const R h = R(0.5), z = R(0);
+  EB<R> f;
+  f.Ex = yee_component(P, P.yee[0], cx, cy, h, z);
+  f.Ey = yee_component(P, P.yee[1], cx, cy, z, h);
+  f.Ez = yee_component(P, P.yee[2], cx, cy, z, z);
+  f.Bx = yee_component(P, P.yee[3], cx, cy, z, h);
+  f.By = yee_component(P, P.yee[4], cx, cy, h, z);
+  f.Bz = yee_component(P, P.yee[5], cx, cy, h, h);
+  return f;
 }
 
 template <typename R>
 __device__ __forceinline__ EB<R> yee2d(const StepParams<R>& P, R x, R y) {
-  const R xi = wrap_cells((x - P.x0) * P.inv_dx, P.nx);
-  const R yi = wrap_cells((y - P.y0) * P.inv_dy, P.ny);
-  const R h = R(0.5);
-  EB<R> f;
-  f.Ex = yee_component(P, P.yee[0], xi - h, yi);
-  f.Ey = yee_component(P, P.yee[1], xi, yi - h);
-  f.Ez = yee_component(P, P.yee[2], xi, yi);
-  f.Bx = yee_component(P, P.yee[3], xi, yi - h);
-  f.By = yee_component(P, P.yee[4], xi - h, yi);
-  f.Bz = yee_component(P, P.yee[5], xi - h, yi - h);
-  return f;
+  const Cell<R> cx = cell_of(x, P.x0, P.inv_dx, P.inv_dx_lo, P.nx);
+  const Cell<R> cy = cell_of(y, P.y0, P.inv_dy, P.inv_dy_lo, P.ny);
+  return yee2d_cells(P, cx, cy);
 }
 
 template <typename R, int FIELD>
@@ -357,11 +397,11 @@ template <typename R>
 struct TileGather {
   const StepParams<R>& P;
   const float* sm;
-  R ox, oy;  // cell coordinates of staged value (0, 0)
-  __device__ __forceinline__ R comp(int c, R lx, R ly) const {
+  int gx0, gy0;  // grid cell of staged value (0, 0)
+  __device__ __forceinline__ R comp(int c, int cl, R fx, int rl, R fy, R sx, R sy) const {
     R wx[3], wy[3];
-    const int i0 = qs_weights(lx, wx) - 1;
-    const int j0 = qs_weights(ly, wy) - 1;
+    const int i0 = cl + qs_weights(fx - sx, wx) - 1;
+    const int j0 = rl + qs_weights(fy - sy, wy) - 1;
     const float* base = sm + c * (kStageW * kStageW) + j0 * kStageW + i0;
     R v = R(0);
 #pragma unroll
@@ -372,19 +412,20 @@ struct TileGather {
     return v;
   }
   __device__ __forceinline__ EB<R> operator()(R x, R y, uint64_t) const {
-    const R xi = wrap_cells((x - P.x0) * P.inv_dx, P.nx);
-    const R yi = wrap_cells((y - P.y0) * P.inv_dy, P.ny);
-    const R lx = xi - ox, ly = yi - oy;
-    const R lo = R(2), hi = R(kStageW - 2);
-    if (!(lx >= lo && lx < hi && ly >= lo && ly < hi)) return yee2d(P, x, y);
-    const R h = R(0.5);
+    const Cell<R> cx = cell_of(x, P.x0, P.inv_dx, P.inv_dx_lo, P.nx);
+    const Cell<R> cy = cell_of(y, P.y0, P.inv_dy, P.inv_dy_lo, P.ny);
+    const int cl = cx.c - gx0, rl = cy.c - gy0;
+    // staged stencil rows/columns cl-1 .. cl+2 must lie in [0, kStageW)
+    if (!(cl >= 1 && cl <= kStageW - 3 && rl >= 1 && rl <= kStageW - 3))
+      return yee2d_cells(P, cx, cy);
+    const R h = R(0.5), z = R(0);
     EB<R> f;
-    f.Ex = comp(0, lx - h, ly);
-    f.Ey = comp(1, lx, ly - h);
-    f.Ez = comp(2, lx, ly);
-    f.Bx = comp(3, lx, ly - h);
-    f.By = comp(4, lx - h, ly);
-    f.Bz = comp(5, lx - h, ly - h);
+    f.Ex = comp(0, cl, cx.f, rl, cy.f, h, z);
+    f.Ey = comp(1, cl, cx.f, rl, cy.f, z, h);
+    f.Ez = comp(2, cl, cx.f, rl, cy.f, z, z);
+    f.Bx = comp(3, cl, cx.f, rl, cy.f, z, h);
+    f.By = comp(4, cl, cx.f, rl, cy.f, h, z);
+    f.Bz = comp(5, cl, cx.f, rl, cy.f, h, h);
     return f;
   }
 };
@@ -637,7 +678,7 @@ __global__ void __launch_bounds__(256, 3) k_push_emit_tiled(const StepParams<R> 
   int fill = 0;
   const PhotonOut pout = make_pout(P);
   Counts cnt;
-  const TileGather<R> gat{P, tile_sm, static_cast<R>(gx0), static_cast<R>(gy0)};
+  const TileGather<R> gat{P, tile_sm, gx0, gy0};
   for (int64_t base = wk.y; base < wk.z; base += blockDim.x) {
     const int64_t i = base + threadIdx.x;
     advance_particle<R, PRAD_FIELD_YEE2D>(P, gat, i, i < wk.z, stage, fill, pout, cnt);

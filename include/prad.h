@@ -75,7 +75,7 @@ enum prad_field_kind {
 /* ---- configuration ----------------------------------------------------- */
 typedef struct prad_config {
   int32_t precision;        /* prad_precision: FP32 push (FP64 ledger) or FP64 */
-  int32_t sampler;          /* prad_sampler                                  */
+  int32_t sampler;          /* prad_sampler (MLP samplers: FP32 only)        */
   int32_t rr_mode;          /* prad_rr_mode                                  */
   int32_t heff_form;        /* prad_heff_form                                */
   double dt;                /* time step [s], > 0                            */
@@ -248,6 +248,50 @@ int prad_get_ledger(prad_ctx* ctx, double* emit, double* ll, int64_t offset,
 
 /* Zero the ledgers, counters and photon buffer. */
 int prad_reset(prad_ctx* ctx);
+
+/* ---- learned sampler (PRAD_SAMPLER_MLP, PRAD_SAMPLER_MLP_FALLBACK) --------
+ * A 3 -> 64 -> 64 -> 1 MLP (SiLU, BF16 weights, FP32 accumulate) maps
+ * (r, gamma, omega_c dt) to ln x with G(x) = r, G the photon-number CDF of
+ * the spectrum of Eqs. (7)-(8), int_0^x F(t)/t dt / (5 pi / 3).  With an MLP
+ * sampler, push_emit uses the direct scheme: the photons of a step have mean
+ * (5 sqrt3 / 6) alpha Omega dt (the integral over x of the rate of Eq. (13)),
+ * multiplicity k = floor + [R < frac], and x = exp(MLP(r', gamma, omega_c dt))
+ * for a uniform r' (records carry weight k w, as in the table path).  Uniforms
+ * outside the trained range [1e-7, 1 - 1e-7], and with MLP_FALLBACK also
+ * non-finite or out-of-range outputs, take x from a tabulated G^-1 instead
+ * (counted in prad_stats.mlp_fallback).  FP32 precision only.  Parameters:
+ * 4481 floats, W1[64][3], b1[64], W2[64][64] (row = output unit), b2[64],
+ * W3[64], b3.  A new context starts from a fixed Glorot initialisation. */
+#define PRAD_MLP_NUM_PARAMS 4481
+
+/* Host FP32 parameter vector in/out (n must be PRAD_MLP_NUM_PARAMS).
+ * set_weights also resets the optimiser state. */
+int prad_mlp_set_weights(prad_ctx* ctx, const float* params, int64_t n);
+int prad_mlp_get_weights(prad_ctx* ctx, float* params, int64_t n);
+
+/* Train the context's network on the GPU: `steps` Adam steps (lr with a
+ * cosine decay to 0) on minibatches of `batch` samples generated on the
+ * device (r uniform in the trained range, gamma log-uniform in [10, 1e4],
+ * H_eff log-uniform in [1e2, 1e6] T, omega_c dt from the context's dt;
+ * target ln G^-1(r) from the device table), loss = mean squared error of
+ * ln x / 10.  *final_loss (host, may be NULL) receives the last minibatch
+ * loss.  Synchronises. */
+int prad_mlp_train(prad_ctx* ctx, int64_t steps, int32_t batch, float lr, uint64_t seed,
+                   float* final_loss);
+
+/* Gradient of the mean loss over n explicit samples (device float4 each:
+ * r, gamma, omega_c dt, target ln x) with respect to the parameter vector,
+ * by the training kernels; grad (host, PRAD_MLP_NUM_PARAMS floats) and loss
+ * (host) receive the results.  Synchronises. */
+int prad_mlp_grad(prad_ctx* ctx, const float* samples, int64_t n, float* grad,
+                  double* loss);
+
+/* ln x = MLP(r, gamma, omega_c dt) for n device triples `in` (3 floats each)
+ * into device `lnx`, with the tile evaluator of the fused kernel. */
+int prad_mlp_eval(prad_ctx* ctx, const float* in, float* lnx, int64_t n);
+
+/* ln G^-1(r) from the device table for n device uniforms. */
+int prad_ginv_eval(prad_ctx* ctx, const float* r, float* lnx, int64_t n);
 
 /* ---- diagnostics (same device functions as the hot kernel) --------------- */
 

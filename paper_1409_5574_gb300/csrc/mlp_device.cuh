@@ -1,0 +1,197 @@
+// Learned inverse-CDF sampler: a 3 -> 64 -> 64 -> 1 MLP with SiLU hidden
+// activations, BF16 weights and FP32 accumulation, evaluated on tiles of 16
+// samples per warp with the m16n8k16 BF16 tensor-core MMA.
+//
+// It replaces the tabulated inversion of the synchrotron spectrum (Eqs. (7),
+// (8)): for a uniform r it returns x = omega / omega_c with G(x) = r, where G
+// is the photon-number CDF int_0^x F(t)/t dt / (5 pi/3).  Inputs are
+// (r, gamma, omega_c dt); in the classical model G does not depend on gamma
+// or omega_c dt, and the network is trained to ignore them.
+//
+// Numerics (shared by training, evaluation and the fused push kernel):
+//   features f = (logit(r)/8, clamp((ln gamma - c1)/s1), clamp((ln w - c2)/s2))
+//   z1 = W1 f + b1 (FP32 FMA, BF16 weights);  h1 = bf16(silu(z1))
+//   z2 = W2 h1 + b2 (BF16 x BF16 tensor-core MMA, FP32 accumulate)
+//   h2 = silu(z2);  o = W3 h2 + b3 (FP32);  ln x = kOutScale * o
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace prad {
+
+constexpr int kHid = 64;
+// parameter vector (FP32 master copy and the layout of get/set weights):
+//   W1 [64][3], b1 [64], W2 [64][64] (row j = output unit), b2 [64],
+//   W3 [64], b3
+constexpr int kOffW1 = 0;
+constexpr int kOffB1 = kOffW1 + kHid * 3;
+constexpr int kOffW2 = kOffB1 + kHid;
+constexpr int kOffB2 = kOffW2 + kHid * kHid;
+constexpr int kOffW3 = kOffB2 + kHid;
+constexpr int kOffB3 = kOffW3 + kHid;
+constexpr int kNumParams = kOffB3 + 1;  // 4481
+
+// feature normalisation (fixed; part of the model definition)
+constexpr float kLogitScale = 0.125f;
+constexpr float kLnGamC = 5.7565f;   // ln sqrt(10 * 1e4)
+constexpr float kLnGamS = 3.4539f;   // ln sqrt(1e4 / 10)
+constexpr float kLnWC = 8.2f;        // centre of ln(omega_c dt) over training
+constexpr float kLnWS = 11.6f;
+constexpr float kOutScale = 10.0f;
+// uniforms the network was trained on; outside, the G^-1 table is used
+constexpr float kRMin = 1.0e-7f;
+constexpr float kRMax = 1.0f - 1.0e-7f;
+
+// Shared-memory image of the network used by the tile evaluator.
+constexpr int kW2Ld = kHid + 8;  // padded row (bank-conflict free B loads)
+struct MlpSmem {
+  float4 w1b1[kHid];                       // (W1 row j, b1 j)
+  float b2[kHid];
+  float w3[kHid];
+  float b3;
+  float pad[3];
+  __nv_bfloat16 w2[kHid * kW2Ld];          // W2 row-major [j][i], padded
+};
+
+// Device copy of the network: FP32 master parameters and the BF16 W2.
+struct MlpDev {
+  const float* params;                 // kNumParams FP32
+  const __nv_bfloat16* w2;             // [64][64] BF16 (row j)
+};
+
+__device__ __forceinline__ float bf16_round(float v) {
+  return __bfloat162float(__float2bfloat16(v));
+}
+
+// Weights enter as BF16 (rounded from the FP32 master), biases as FP32.
+__device__ __forceinline__ void mlp_load_smem(MlpSmem& s, const MlpDev& d) {
+  for (int j = threadIdx.x; j < kHid; j += blockDim.x) {
+    s.w1b1[j] = make_float4(bf16_round(d.params[kOffW1 + 3 * j]),
+                            bf16_round(d.params[kOffW1 + 3 * j + 1]),
+                            bf16_round(d.params[kOffW1 + 3 * j + 2]), d.params[kOffB1 + j]);
+    s.b2[j] = d.params[kOffB2 + j];
+    s.w3[j] = bf16_round(d.params[kOffW3 + j]);
+  }
+  if (threadIdx.x == 0) s.b3 = d.params[kOffB3];
+  for (int e = threadIdx.x; e < kHid * kHid; e += blockDim.x) {
+    const int j = e / kHid, i = e - j * kHid;
+    s.w2[j * kW2Ld + i] = d.w2[e];
+  }
+}
+
+__device__ __forceinline__ float silu(float z) {
+  // z * sigmoid(z) = 0.5 z (1 + tanh(z / 2))
+  float t;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(0.5f * z));
+  return 0.5f * z * (1.0f + t);
+}
+
+__device__ __forceinline__ float silu_grad(float z) {
+  // d/dz [z sigmoid(z)] = s + z s (1 - s),  s = sigmoid(z)
+  float t;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(0.5f * z));
+  const float s = 0.5f * (1.0f + t);
+  return s + z * s * (1.0f - s);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+// D = A(16x16, row) * B(16x8, col) + C, BF16 inputs, FP32 accumulate.
+// Fragment ownership (g = lane / 4, t = lane % 4):
+//   a0: A[g][2t..2t+1]   a1: A[g+8][2t..]   a2: A[g][2t+8..]   a3: A[g+8][2t+8..]
+//   b0: B[2t..2t+1][g]   b1: B[2t+8..2t+9][g]
+//   c0,c1: C[g][2t..2t+1]   c2,c3: C[g+8][2t..2t+1]
+__device__ __forceinline__ void mma_bf16_16816(float c[4], uint32_t a0, uint32_t a1,
+                                               uint32_t a2, uint32_t a3, uint32_t b0,
+                                               uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+      "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ float3 mlp_features(float r, float gamma, float wdt) {
+  const float lg = (__logf(r) - __logf(1.0f - r)) * kLogitScale;
+  float f1 = (__logf(gamma) - kLnGamC) * (1.0f / kLnGamS);
+  float f2 = (__logf(wdt) - kLnWC) * (1.0f / kLnWS);
+  f1 = fminf(fmaxf(f1, -1.0f), 1.0f);
+  f2 = fminf(fmaxf(f2, -1.0f), 1.0f);
+  return make_float3(lg, f1, f2);
+}
+
+// Warp-collective: the 16 rows of a tile are the features of lanes' rows
+// g and g+8 (f_lo, f_hi); returns ln x of rows g (out_lo) and g+8 (out_hi),
+// valid in every lane of the row's group.
+__device__ __forceinline__ void mlp_tile16(const MlpSmem& S, float3 f_lo, float3 f_hi,
+                                           float& out_lo, float& out_hi) {
+  const int lane = threadIdx.x & 31;
+  const int g = lane >> 2, t = lane & 3;
+  // layer 1 directly in the A-fragment layout of layer 2: this lane needs h1
+  // for rows g, g+8 and hidden units 16q + 2t + {0, 1, 8, 9}, q = 0..3
+  uint32_t a[4][4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    float h[2][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int j = 16 * q + 2 * t + (u & 1) + ((u >> 1) << 3);
+      const float4 w = S.w1b1[j];
+      const float zl = fmaf(w.x, f_lo.x, fmaf(w.y, f_lo.y, fmaf(w.z, f_lo.z, w.w)));
+      const float zh = fmaf(w.x, f_hi.x, fmaf(w.y, f_hi.y, fmaf(w.z, f_hi.z, w.w)));
+      h[0][u] = silu(zl);
+      h[1][u] = silu(zh);
+    }
+    a[q][0] = pack_bf16x2(h[0][0], h[0][1]);
+    a[q][1] = pack_bf16x2(h[1][0], h[1][1]);
+    a[q][2] = pack_bf16x2(h[0][2], h[0][3]);
+    a[q][3] = pack_bf16x2(h[1][2], h[1][3]);
+  }
+  // layer 2: 8 output column tiles of 8 units, K = 64 in 4 steps of 16
+  float acc_lo = 0.0f, acc_hi = 0.0f;
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt) {
+    float c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    const __nv_bfloat16* wrow = S.w2 + (8 * nt + g) * kW2Ld + 2 * t;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint32_t b0 = *reinterpret_cast<const uint32_t*>(wrow + 16 * q);
+      const uint32_t b1 = *reinterpret_cast<const uint32_t*>(wrow + 16 * q + 8);
+      mma_bf16_16816(c, a[q][0], a[q][1], a[q][2], a[q][3], b0, b1);
+    }
+    // c0,c1: rows g, units 8nt + 2t + {0,1}; c2,c3: row g + 8
+    const int j0 = 8 * nt + 2 * t;
+    acc_lo = fmaf(S.w3[j0], silu(c[0] + S.b2[j0]), acc_lo);
+    acc_lo = fmaf(S.w3[j0 + 1], silu(c[1] + S.b2[j0 + 1]), acc_lo);
+    acc_hi = fmaf(S.w3[j0], silu(c[2] + S.b2[j0]), acc_hi);
+    acc_hi = fmaf(S.w3[j0 + 1], silu(c[3] + S.b2[j0 + 1]), acc_hi);
+  }
+  // layer 3: reduce the partial dot products over the 4 lanes of the group
+  acc_lo += __shfl_xor_sync(0xffffffffu, acc_lo, 1);
+  acc_lo += __shfl_xor_sync(0xffffffffu, acc_lo, 2);
+  acc_hi += __shfl_xor_sync(0xffffffffu, acc_hi, 1);
+  acc_hi += __shfl_xor_sync(0xffffffffu, acc_hi, 2);
+  out_lo = kOutScale * (acc_lo + S.b3);
+  out_hi = kOutScale * (acc_hi + S.b3);
+}
+
+// G^-1 table: ln x at nodes uniform in logit(r) on [-kGiL, kGiL], linear
+// interpolation (training targets, fallback, device-side spectral check).
+constexpr int kGiN = 8192;
+constexpr float kGiL = 24.0f;
+
+__device__ __forceinline__ float ginv_ln(const float* tab, float r) {
+  const float lg = __logf(r) - __logf(1.0f - r);
+  const float u = (fminf(fmaxf(lg, -kGiL), kGiL) + kGiL) * ((kGiN - 1) / (2.0f * kGiL));
+  int i = static_cast<int>(u);
+  i = min(max(i, 0), kGiN - 2);
+  const float s = u - static_cast<float>(i);
+  return fmaf(s, tab[i + 1] - tab[i], tab[i]);
+}
+
+}  // namespace prad

@@ -7,7 +7,10 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <vector>
+
+#include <cuda_bf16.h>
 
 #include "prad_internal.h"
 
@@ -61,6 +64,18 @@ struct prad_ctx {
   int64_t drained_dropped = 0;
   // tile sort scratch (allocated on first use)
   SortBuffers sort{};
+  // learned sampler
+  float* d_mlp = nullptr;        // FP32 master parameters
+  float* d_mlp_m = nullptr;      // Adam moments
+  float* d_mlp_v = nullptr;
+  float* d_mlp_grad = nullptr;
+  __nv_bfloat16* d_mlp_w2 = nullptr;
+  float* d_ginv = nullptr;       // ln G^-1 on a logit grid
+  float* d_mlp_partial = nullptr;
+  float* d_mlp_loss_part = nullptr;
+  float* d_mlp_loss = nullptr;
+  int mlp_partial_blocks = 0;
+  int64_t mlp_t = 0;             // Adam step count
 };
 
 namespace {
@@ -175,6 +190,124 @@ void build_tables(std::vector<float4>& t32, std::vector<Coef4d>& t64) {
   }
 }
 
+// ---- G^-1 table ------------------------------------------------------------
+// G(x) = int_0^x F(t)/t dt / (5 pi/3): cumulative Simpson in ln t on
+// [1e-8, 90] (F from the quadrature above), the exact integral of the small-x
+// asymptote below, and the upper tail accumulated from the top so 1 - G keeps
+// its relative accuracy.  The table holds ln G^-1(r) at kGiN nodes uniform in
+// logit(r) on [-kGiL, kGiL], by interpolation in (ln t, ln G) / (ln t, ln T).
+void build_ginv(std::vector<float>& out) {
+  GaussLegendre gl;
+  const double lt0 = std::log(1e-8), lt1 = std::log(90.0), h = 0.02;
+  const int M = static_cast<int>((lt1 - lt0) / h) + 1;
+  std::vector<double> lt(M + 1), lo(M + 1), hi(M + 1), seg(M);
+  const double c = 4.0 * kPi / (std::sqrt(3.0) * std::tgamma(1.0 / 3.0)) * std::cbrt(0.5);
+  const double norm = 5.0 * kPi / 3.0;
+  for (int k = 0; k <= M; ++k) lt[k] = lt0 + k * h;
+  for (int k = 0; k < M; ++k) {  // Simpson, 4 panels, integrand F(e^y) dy
+    const int P = 4;
+    double acc = 0.0;
+    for (int q = 0; q <= P; ++q) {
+      const double y = lt[k] + q * h / P;
+      const double wq = (q == 0 || q == P) ? 1.0 : ((q & 1) ? 4.0 : 2.0);
+      acc += wq * synchrotron_F(std::exp(y), gl);
+    }
+    seg[k] = acc * (h / P) / 3.0;
+  }
+  lo[0] = 3.0 * c * std::cbrt(std::exp(lt0));
+  for (int k = 0; k < M; ++k) lo[k + 1] = lo[k] + seg[k];
+  hi[M] = 0.0;
+  for (int k = M - 1; k >= 0; --k) hi[k] = hi[k + 1] + seg[k];
+  const double total = lo[0] + hi[0];
+  out.resize(kGiN);
+  for (int i = 0; i < kGiN; ++i) {
+    const double l = -kGiL + 2.0 * kGiL * i / (kGiN - 1);
+    double lnx;
+    if (l <= 0.0) {
+      const double r = 1.0 / (1.0 + std::exp(-l));
+      const double target = r * total;  // normalise by the computed total
+      if (target <= lo[0]) {
+        lnx = 3.0 * std::log(target / (3.0 * c));
+      } else {
+        int a = 0, b = M;
+        while (b - a > 1) {
+          const int m = (a + b) / 2;
+          (lo[m] <= target ? a : b) = m;
+        }
+        const double f = (std::log(target) - std::log(lo[a])) /
+                         (std::log(lo[b]) - std::log(lo[a]));
+        lnx = lt[a] + f * (lt[b] - lt[a]);
+      }
+    } else {
+      const double t1 = 1.0 / (1.0 + std::exp(l)) * total;  // (1 - r) total
+      int a = 0, b = M;
+      if (t1 <= hi[M - 1]) {
+        a = M - 1;
+        b = M;
+        lnx = lt[M - 1];
+      } else {
+        while (b - a > 1) {
+          const int m = (a + b) / 2;
+          (hi[m] >= t1 ? a : b) = m;
+        }
+        const double f = (std::log(t1) - std::log(hi[a])) / (std::log(hi[b]) - std::log(hi[a]));
+        lnx = lt[a] + f * (lt[b] - lt[a]);
+      }
+    }
+    out[i] = static_cast<float>(lnx);
+  }
+  (void)norm;
+}
+
+uint16_t to_bf16(float f) {  // round to nearest even
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  const uint32_t rounding = 0x7FFFu + ((u >> 16) & 1u);
+  return static_cast<uint16_t>((u + rounding) >> 16);
+}
+
+// Fixed Glorot-uniform initialisation (splitmix64 stream), biases zero
+// except the output bias, which starts at the typical ln x / 10.
+void init_mlp_params(std::vector<float>& p, uint64_t seed) {
+  p.assign(kNumParams, 0.0f);
+  uint64_t st = seed * 0x9E3779B97F4A7C15ull + 1;
+  auto uni = [&]() {
+    st += 0x9E3779B97F4A7C15ull;
+    uint64_t z = st;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (static_cast<double>(z >> 11) + 0.5) * 0x1p-53 * 2.0 - 1.0;
+  };
+  const double a1 = std::sqrt(6.0 / (3 + kHid)), a2 = std::sqrt(6.0 / (2 * kHid)),
+               a3 = std::sqrt(6.0 / (kHid + 1));
+  for (int k = 0; k < kHid * 3; ++k) p[kOffW1 + k] = static_cast<float>(a1 * uni());
+  for (int k = 0; k < kHid * kHid; ++k) p[kOffW2 + k] = static_cast<float>(a2 * uni());
+  for (int k = 0; k < kHid; ++k) p[kOffW3 + k] = static_cast<float>(a3 * uni());
+  p[kOffB3] = -0.1f;
+}
+
+int upload_mlp(prad_ctx* c, const float* host_params) {
+  std::vector<uint16_t> w2(kHid * kHid);
+  for (int k = 0; k < kHid * kHid; ++k) w2[k] = to_bf16(host_params[kOffW2 + k]);
+  CK(c, cudaMemcpyAsync(c->d_mlp, host_params, sizeof(float) * kNumParams,
+                        cudaMemcpyHostToDevice, c->stream));
+  CK(c, cudaMemcpyAsync(c->d_mlp_w2, w2.data(), sizeof(uint16_t) * kHid * kHid,
+                        cudaMemcpyHostToDevice, c->stream));
+  CK(c, cudaMemsetAsync(c->d_mlp_m, 0, sizeof(float) * kNumParams, c->stream));
+  CK(c, cudaMemsetAsync(c->d_mlp_v, 0, sizeof(float) * kNumParams, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  c->mlp_t = 0;
+  return PRAD_OK;
+}
+
+MlpDev mlp_dev(const prad_ctx* c) {
+  MlpDev d;
+  d.params = c->d_mlp;
+  d.w2 = c->d_mlp_w2;
+  return d;
+}
+
 template <typename R>
 void fill_common(const prad_ctx* c, StepParams<R>& p) {
   const double q = c->cfg.charge;
@@ -206,6 +339,9 @@ void fill_common(const prad_ctx* c, StepParams<R>& p) {
   p.ppid = c->d_pid; p.pstep = c->d_step;
   p.cap = c->cfg.photon_capacity;
   p.counters = c->d_cnt;
+  p.cp_dt = static_cast<R>(5.0 * std::sqrt(3.0) / 6.0 * c->alpha * dtn);
+  p.mlp = mlp_dev(c);
+  p.ginv = c->d_ginv;
   // field, normalised: E by m c omega_ref / e, B by m omega_ref / e
   const prad_fields& f = c->fields;
   const double w = c->cfg.omega_ref;
@@ -356,7 +492,7 @@ int push_emit_t(prad_ctx* c, const prad_particles* pp, int64_t n,
   p.n = n;
   p.pid0 = pp->pid0;
   const bool tiled = c->fields.kind == PRAD_FIELD_YEE2D && c->cfg.sort_interval > 0 &&
-                     pp->pid != nullptr;
+                     pp->pid != nullptr && c->cfg.sampler == PRAD_SAMPLER_TABLE;
   if (tiled) {
     if (n > c->cfg.max_particles)
       return fail(c, PRAD_ERR_ARG, "push_emit: n exceeds max_particles (sort scratch)");
@@ -391,7 +527,7 @@ int push_emit_t(prad_ctx* c, const prad_particles* pp, int64_t n,
     p.nsub = m;
     // wave phase at the launch's first step (modulo one cycle)
     p.phase_t0 = phase0 + static_cast<uint64_t>(p.t0) * p.phase_step;
-    CK(c, launch_push_emit<R>(p, c->fields.kind, grid, block, c->stream));
+    CK(c, launch_push_emit<R>(p, c->fields.kind, c->cfg.sampler, grid, block, c->stream));
     done += m;
   }
   return PRAD_OK;
@@ -411,8 +547,10 @@ int prad_init(prad_ctx** out, const prad_config* cfg) {
                 "prad_init: photon_capacity and max_particles must be >= 1");
   if (cfg->precision != PRAD_FP32 && cfg->precision != PRAD_FP64)
     return fail(nullptr, PRAD_ERR_ARG, "prad_init: bad precision");
-  if (cfg->sampler != PRAD_SAMPLER_TABLE)
-    return fail(nullptr, PRAD_ERR_ARG, "prad_init: sampler not available in this build");
+  if (cfg->sampler < PRAD_SAMPLER_TABLE || cfg->sampler > PRAD_SAMPLER_MLP_FALLBACK)
+    return fail(nullptr, PRAD_ERR_ARG, "prad_init: bad sampler");
+  if (cfg->sampler != PRAD_SAMPLER_TABLE && cfg->precision != PRAD_FP32)
+    return fail(nullptr, PRAD_ERR_ARG, "prad_init: the learned sampler is FP32 only");
   if (cfg->rr_mode < PRAD_RR_OFF || cfg->rr_mode > PRAD_RR_APPLY)
     return fail(nullptr, PRAD_ERR_ARG, "prad_init: bad rr_mode");
   if (cfg->heff_form != PRAD_HEFF_FIELD && cfg->heff_form != PRAD_HEFF_MOMENTUM)
@@ -447,9 +585,16 @@ int prad_init(prad_ctx** out, const prad_config* cfg) {
   c->alpha = kQe * kQe / (4.0 * kPi * kEps0 * kHbar * kC);
   c->eps_r = kHbar * cfg->omega_ref / (kMe * kC * kC);
 
-  std::vector<float4> t32;
-  std::vector<Coef4d> t64;
-  build_tables(t32, t64);
+  // host tables are built once per process (pure functions of the paper's
+  // constants) and uploaded to every context
+  static std::once_flag once;
+  static std::vector<float4> t32;
+  static std::vector<Coef4d> t64;
+  static std::vector<float> ginv_host;
+  std::call_once(once, [] {
+    build_tables(t32, t64);
+    build_ginv(ginv_host);
+  });
   CKI(cudaMalloc(&c->d_tab32, kNTab * sizeof(float4)));
   CKI(cudaMalloc(&c->d_tab64, kNTab * sizeof(Coef4d)));
   CKI(cudaMemcpy(c->d_tab32, t32.data(), kNTab * sizeof(float4), cudaMemcpyHostToDevice));
@@ -469,6 +614,20 @@ int prad_init(prad_ctx** out, const prad_config* cfg) {
   c->red_blocks = 2 * c->num_sms;
   CKI(cudaMalloc(&c->d_partials, 4 * c->red_blocks * sizeof(double)));
   CKI(cudaMalloc(&c->d_sums, 2 * sizeof(double)));
+  // learned sampler: network, optimiser state, G^-1 table
+  CKI(cudaMalloc(&c->d_mlp, sizeof(float) * kNumParams));
+  CKI(cudaMalloc(&c->d_mlp_m, sizeof(float) * kNumParams));
+  CKI(cudaMalloc(&c->d_mlp_v, sizeof(float) * kNumParams));
+  CKI(cudaMalloc(&c->d_mlp_grad, sizeof(float) * kNumParams));
+  CKI(cudaMalloc(&c->d_mlp_w2, sizeof(uint16_t) * kHid * kHid));
+  CKI(cudaMalloc(&c->d_mlp_loss, sizeof(float)));
+  CKI(cudaMalloc(&c->d_ginv, sizeof(float) * kGiN));
+  {
+    CKI(cudaMemcpy(c->d_ginv, ginv_host.data(), sizeof(float) * kGiN, cudaMemcpyHostToDevice));
+    std::vector<float> p0;
+    init_mlp_params(p0, 0x5eed5eedull);
+    if (upload_mlp(c, p0.data()) != PRAD_OK) return bail(PRAD_ERR_CUDA);
+  }
   CKI(cudaDeviceSynchronize());
 #undef CKI
   *out = c;
@@ -488,6 +647,15 @@ int prad_destroy(prad_ctx* c) {
   cudaFree(c->d_led_ll);
   cudaFree(c->d_partials);
   cudaFree(c->d_sums);
+  cudaFree(c->d_mlp);
+  cudaFree(c->d_mlp_m);
+  cudaFree(c->d_mlp_v);
+  cudaFree(c->d_mlp_grad);
+  cudaFree(c->d_mlp_w2);
+  cudaFree(c->d_mlp_loss);
+  cudaFree(c->d_ginv);
+  cudaFree(c->d_mlp_partial);
+  cudaFree(c->d_mlp_loss_part);
   delete c;
   return PRAD_OK;
 }
@@ -651,6 +819,118 @@ int prad_eval_sampler(prad_ctx* c, const uint32_t* words, void* x_out, void* g_o
     CK(c, launch_eval_sampler<double>(p, words, static_cast<double*>(x_out),
                                       static_cast<double*>(g_out), n, c->stream));
   }
+  CK(c, cudaStreamSynchronize(c->stream));
+  return PRAD_OK;
+}
+
+int prad_mlp_set_weights(prad_ctx* c, const float* params, int64_t n) {
+  if (!c || !params || n != kNumParams)
+    return fail(c, PRAD_ERR_ARG, "mlp_set_weights: need %d host floats", kNumParams);
+  return upload_mlp(c, params);
+}
+
+int prad_mlp_get_weights(prad_ctx* c, float* params, int64_t n) {
+  if (!c || !params || n != kNumParams)
+    return fail(c, PRAD_ERR_ARG, "mlp_get_weights: need %d host floats", kNumParams);
+  CK(c, cudaMemcpyAsync(params, c->d_mlp, sizeof(float) * kNumParams, cudaMemcpyDeviceToHost,
+                        c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  return PRAD_OK;
+}
+
+namespace {
+int ensure_mlp_partials(prad_ctx* c, int nblocks) {
+  if (c->mlp_partial_blocks >= nblocks) return PRAD_OK;
+  cudaFree(c->d_mlp_partial);
+  cudaFree(c->d_mlp_loss_part);
+  c->d_mlp_partial = nullptr;
+  c->d_mlp_loss_part = nullptr;
+  c->mlp_partial_blocks = 0;
+  CK(c, cudaMalloc(&c->d_mlp_partial, sizeof(float) * kNumParams * nblocks));
+  CK(c, cudaMalloc(&c->d_mlp_loss_part, sizeof(float) * nblocks));
+  c->mlp_partial_blocks = nblocks;
+  return PRAD_OK;
+}
+
+// training-sample ranges (log-uniform gamma and H_eff) and omega_c dt / (H gamma^2)
+void mlp_ranges(const prad_ctx* c, float* lng_lo, float* lng_span, float* lnh_lo,
+                float* lnh_span, float* wdt_per) {
+  *lng_lo = static_cast<float>(std::log(10.0));
+  *lng_span = static_cast<float>(std::log(1e4) - std::log(10.0));
+  *lnh_lo = static_cast<float>(std::log(1e2));
+  *lnh_span = static_cast<float>(std::log(1e6) - std::log(1e2));
+  *wdt_per = static_cast<float>(1.5 * kQe / kMe * c->cfg.dt);
+}
+}  // namespace
+
+int prad_mlp_train(prad_ctx* c, int64_t steps, int32_t batch, float lr, uint64_t seed,
+                   float* final_loss) {
+  if (!c || steps < 0 || batch < 1 || !(lr > 0.0f))
+    return fail(c, PRAD_ERR_ARG, "mlp_train: bad argument");
+  const int nblocks = (batch + 127) / 128;
+  int rc = ensure_mlp_partials(c, nblocks);
+  if (rc != PRAD_OK) return rc;
+  float lng_lo, lng_span, lnh_lo, lnh_span, wdt;
+  mlp_ranges(c, &lng_lo, &lng_span, &lnh_lo, &lnh_span, &wdt);
+  const MlpDev dev = mlp_dev(c);
+  for (int64_t s = 0; s < steps; ++s) {
+    CK(c, launch_mlp_train_block(dev, static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32),
+                                 static_cast<uint64_t>(s) * batch, batch, batch, nullptr,
+                                 c->d_ginv, lng_lo, lng_span, lnh_lo, lnh_span, wdt,
+                                 c->d_mlp_partial, c->d_mlp_loss_part, nblocks, c->stream));
+    c->mlp_t += 1;
+    const double lr_s = lr * 0.5 * (1.0 + std::cos(kPi * static_cast<double>(s) / steps));
+    const float b1t = static_cast<float>(std::pow(0.9, static_cast<double>(c->mlp_t)));
+    const float b2t = static_cast<float>(std::pow(0.999, static_cast<double>(c->mlp_t)));
+    CK(c, launch_mlp_reduce_adam(c->d_mlp_partial, nblocks, c->d_mlp_loss_part, c->d_mlp_grad,
+                                 c->d_mlp, c->d_mlp_m, c->d_mlp_v, c->d_mlp_w2,
+                                 static_cast<float>(lr_s), b1t, b2t, 1, c->d_mlp_loss,
+                                 1.0f / static_cast<float>(batch), c->stream));
+  }
+  float loss = 0.0f;
+  CK(c, cudaMemcpyAsync(&loss, c->d_mlp_loss, sizeof(float), cudaMemcpyDeviceToHost,
+                        c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  if (final_loss) *final_loss = loss;
+  return PRAD_OK;
+}
+
+int prad_mlp_grad(prad_ctx* c, const float* samples, int64_t n, float* grad, double* loss) {
+  if (!c || !samples || n < 1 || n > (int64_t(1) << 24) || !grad)
+    return fail(c, PRAD_ERR_ARG, "mlp_grad: bad argument");
+  if (!aligned(samples, 16)) return fail(c, PRAD_ERR_ARG, "mlp_grad: samples not 16-B aligned");
+  const int nblocks = static_cast<int>((n + 127) / 128);
+  int rc = ensure_mlp_partials(c, nblocks);
+  if (rc != PRAD_OK) return rc;
+  float lng_lo, lng_span, lnh_lo, lnh_span, wdt;
+  mlp_ranges(c, &lng_lo, &lng_span, &lnh_lo, &lnh_span, &wdt);
+  CK(c, launch_mlp_train_block(mlp_dev(c), 0, 0, 0, n, n, reinterpret_cast<const float4*>(samples),
+                               c->d_ginv, lng_lo, lng_span, lnh_lo, lnh_span, wdt,
+                               c->d_mlp_partial, c->d_mlp_loss_part, nblocks, c->stream));
+  CK(c, launch_mlp_reduce_adam(c->d_mlp_partial, nblocks, c->d_mlp_loss_part, c->d_mlp_grad,
+                               c->d_mlp, c->d_mlp_m, c->d_mlp_v, c->d_mlp_w2, 0.0f, 0.0f, 0.0f,
+                               0, c->d_mlp_loss, 1.0f / static_cast<float>(n), c->stream));
+  float l = 0.0f;
+  CK(c, cudaMemcpyAsync(grad, c->d_mlp_grad, sizeof(float) * kNumParams,
+                        cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaMemcpyAsync(&l, c->d_mlp_loss, sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  if (loss) *loss = l;
+  return PRAD_OK;
+}
+
+int prad_mlp_eval(prad_ctx* c, const float* in, float* lnx, int64_t n) {
+  if (!c || n < 0 || (n > 0 && (!in || !lnx))) return fail(c, PRAD_ERR_ARG, "mlp_eval: bad argument");
+  if (n == 0) return PRAD_OK;
+  CK(c, launch_mlp_eval(mlp_dev(c), in, lnx, n, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  return PRAD_OK;
+}
+
+int prad_ginv_eval(prad_ctx* c, const float* r, float* lnx, int64_t n) {
+  if (!c || n < 0 || (n > 0 && (!r || !lnx))) return fail(c, PRAD_ERR_ARG, "ginv_eval: bad argument");
+  if (n == 0) return PRAD_OK;
+  CK(c, launch_ginv_eval(c->d_ginv, r, lnx, n, c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
   return PRAD_OK;
 }

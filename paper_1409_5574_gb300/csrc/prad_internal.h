@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include "../../include/prad.h"
+#include "mlp_device.cuh"
 
 namespace prad {
 
@@ -82,6 +83,10 @@ struct StepParams {
   uint32_t *ppid, *pstep;
   int64_t cap;
   unsigned long long* counters;
+  // learned sampler (direct scheme): expected photons per step = cp_dt Omega
+  R cp_dt;                    // (5 sqrt3 / 6) alpha dtn
+  MlpDev mlp;
+  const float* ginv;          // G^-1 table (ln x on a logit(r) grid)
   // tile-sorted Yee gather (k_push_emit_tiled)
   const int4* work;           // (tile, first, end, 0) per work item
   const unsigned int* work_count;
@@ -110,7 +115,7 @@ struct SortBuffers {
 
 // Launchers (defined in the kernel translation units).
 template <typename R>
-cudaError_t launch_push_emit(const StepParams<R>& p, int field_kind, int grid,
+cudaError_t launch_push_emit(const StepParams<R>& p, int field_kind, int sampler, int grid,
                              int block, cudaStream_t s);
 template <typename R>
 cudaError_t launch_eval_sampler(const StepParams<R>& p, const uint32_t* words,
@@ -124,6 +129,22 @@ template <typename R>
 cudaError_t launch_tile_sort(R* arr[7], uint32_t* pid, int64_t n, const SortBuffers& b,
                              int nx, int ny, double x0, double y0, double inv_dx,
                              double inv_dy, cudaStream_t s);
+size_t mlp_train_smem_bytes();
+cudaError_t launch_mlp_train_block(const MlpDev& dev, uint32_t key0, uint32_t key1,
+                                   uint64_t first, int64_t n_valid, int64_t n_total,
+                                   const float4* explicit_samples, const float* ginv,
+                                   float lng_lo, float lng_span, float lnh_lo,
+                                   float lnh_span, float wdt_per_H_g2, float* partial,
+                                   float* loss_part, int nblocks, cudaStream_t s);
+cudaError_t launch_mlp_reduce_adam(const float* partial, int nblocks, const float* loss_part,
+                                   float* grad, float* params, float* m, float* v,
+                                   __nv_bfloat16* w2, float lr, float b1t, float b2t,
+                                   int apply, float* loss_out, float loss_scale,
+                                   cudaStream_t s);
+cudaError_t launch_mlp_eval(const MlpDev& dev, const float* in, float* out, int64_t n,
+                            cudaStream_t s);
+cudaError_t launch_ginv_eval(const float* tab, const float* r, float* out, int64_t n,
+                             cudaStream_t s);
 cudaError_t launch_ledger_reduce(const double* a, const double* b, int64_t n,
                                  double* partials, int nblocks, double* out,
                                  cudaStream_t s);

@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "mlp_device.cuh"
 #include "prad_internal.h"
 
 namespace prad {
@@ -431,19 +432,136 @@ struct TileGather {
 };
 
 struct Counts {
-  uint32_t dn1 = 0, clamp = 0, chi = 0, nan = 0;
+  uint32_t dn1 = 0, clamp = 0, chi = 0, nan = 0, fallback = 0;
   bool bad_id = false;
 };
+
+// ---------------------------------------------------------------------------
+// Learned-sampler queue (direct scheme).  Emitting lanes park their emission
+// (features, omega_c, weight, record geometry, ledger entry) in the warp's
+// queue; every 16 queued emissions the warp evaluates the MLP on one 16-row
+// tensor-core tile, then writes the photon records and books the emitted
+// energy.  Warp-collective throughout.
+// ---------------------------------------------------------------------------
+constexpr int kQCap = 48;  // < 16 left over + up to 32 new per step
+struct MlpQueue {
+  float f[3][kQCap];
+  float r[kQCap];
+  float epsc[kQCap];
+  float wt[kQCap];
+  float pos[3][kQCap];
+  float dir[3][kQCap];
+  uint32_t pid[kQCap], step[kQCap];
+  int32_t li[kQCap];
+};
+
+struct MlpWarp {
+  const MlpSmem* net;
+  MlpQueue* q;
+  int count;            // warp-uniform
+  bool check_output;    // MLP_FALLBACK: non-finite / out-of-range x -> table
+};
+
+__device__ __forceinline__ void mlp_enqueue(MlpWarp& mw, bool want, float3 f, float r,
+                                            float epsc, float wt, const float pos[3],
+                                            const float dir[3], uint32_t pid,
+                                            uint32_t step, int32_t li) {
+  const unsigned mask = __ballot_sync(0xffffffffu, want);
+  if (mask == 0u) return;
+  if (want) {
+    const int lane = threadIdx.x & 31;
+    const int k = mw.count + __popc(mask & ((1u << lane) - 1u));
+    MlpQueue& q = *mw.q;
+    q.f[0][k] = f.x; q.f[1][k] = f.y; q.f[2][k] = f.z;
+    q.r[k] = r; q.epsc[k] = epsc; q.wt[k] = wt;
+    q.pos[0][k] = pos[0]; q.pos[1][k] = pos[1]; q.pos[2][k] = pos[2];
+    q.dir[0][k] = dir[0]; q.dir[1][k] = dir[1]; q.dir[2][k] = dir[2];
+    q.pid[k] = pid; q.step[k] = step; q.li[k] = li;
+  }
+  mw.count += __popc(mask);
+  __syncwarp();
+}
+
+// Evaluate the first min(16, count) queued emissions, emit their records and
+// book their energy; shift the rest of the queue down.
+template <typename R>
+__device__ __forceinline__ void mlp_flush_tile(const StepParams<R>& P, MlpWarp& mw,
+                                               PhotonStage& stage, int& fill,
+                                               const PhotonOut& pout, Counts& cnt) {
+  MlpQueue& q = *mw.q;
+  const int lane = threadIdx.x & 31, g = lane >> 2;
+  const int rows = mw.count < 16 ? mw.count : 16;
+  float3 flo = make_float3(0.f, 0.f, 0.f), fhi = flo;
+  if (g < rows) flo = make_float3(q.f[0][g], q.f[1][g], q.f[2][g]);
+  if (g + 8 < rows) fhi = make_float3(q.f[0][g + 8], q.f[1][g + 8], q.f[2][g + 8]);
+  float olo, ohi;
+  mlp_tile16(*mw.net, flo, fhi, olo, ohi);
+  // row L of the tile lives in lane 4 (L % 8), in olo (L < 8) or ohi
+  const float vlo = __shfl_sync(0xffffffffu, olo, (lane & 7) * 4);
+  const float vhi = __shfl_sync(0xffffffffu, ohi, (lane & 7) * 4);
+  const bool mine = lane < rows;
+  float rec[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  uint32_t pid = 0, step = 0;
+  if (mine) {
+    float lnx = lane < 8 ? vlo : vhi;
+    float x = __expf(lnx);
+    bool ok = x > 0.0f && x < 80.0f;  // also false for NaN
+    if (mw.check_output) {
+      if (!ok) {
+        x = __expf(ginv_ln(P.ginv, q.r[lane]));
+        ++cnt.fallback;
+      }
+    } else if (!ok) {
+      x = 0.0f;  // no fallback requested: an invalid draw carries no energy
+    }
+    const float eps = x * q.epsc[lane];
+    const float wt = q.wt[lane];
+    rec[0] = q.pos[0][lane]; rec[1] = q.pos[1][lane]; rec[2] = q.pos[2][lane];
+    rec[3] = q.dir[0][lane]; rec[4] = q.dir[1][lane]; rec[5] = q.dir[2][lane];
+    rec[6] = eps; rec[7] = wt;
+    pid = q.pid[lane];
+    step = q.step[lane];
+    const int32_t li = q.li[lane];
+    if (li >= 0) atomicAdd(P.led_emit + li, static_cast<double>(wt) * static_cast<double>(eps));
+  }
+  stage_photon(stage, fill, pout, mine, rec, pid, step);
+  // shift the remaining entries to the front
+  const int rest = mw.count - rows;
+  __syncwarp();
+  float tmp[15];
+  uint32_t tp = 0, ts = 0;
+  int32_t tl = 0;
+  const bool mv = lane < rest;
+  if (mv) {
+    const int k = rows + lane;
+    tmp[0] = q.f[0][k]; tmp[1] = q.f[1][k]; tmp[2] = q.f[2][k];
+    tmp[3] = q.r[k]; tmp[4] = q.epsc[k]; tmp[5] = q.wt[k];
+    tmp[6] = q.pos[0][k]; tmp[7] = q.pos[1][k]; tmp[8] = q.pos[2][k];
+    tmp[9] = q.dir[0][k]; tmp[10] = q.dir[1][k]; tmp[11] = q.dir[2][k];
+    tp = q.pid[k]; ts = q.step[k]; tl = q.li[k];
+  }
+  __syncwarp();
+  if (mv) {
+    const int k = lane;
+    q.f[0][k] = tmp[0]; q.f[1][k] = tmp[1]; q.f[2][k] = tmp[2];
+    q.r[k] = tmp[3]; q.epsc[k] = tmp[4]; q.wt[k] = tmp[5];
+    q.pos[0][k] = tmp[6]; q.pos[1][k] = tmp[7]; q.pos[2][k] = tmp[8];
+    q.dir[0][k] = tmp[9]; q.dir[1][k] = tmp[10]; q.dir[2][k] = tmp[11];
+    q.pid[k] = tp; q.step[k] = ts; q.li[k] = tl;
+  }
+  __syncwarp();
+  mw.count = rest;
+}
 
 // ---------------------------------------------------------------------------
 // One particle, nsub steps (the whole per-step path).  Warp-collective: every
 // lane of the warp calls it, inactive lanes with act = false.
 // ---------------------------------------------------------------------------
-template <typename R, int FIELD, class G>
+template <typename R, int FIELD, int SAMP, class G>
 __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const G& gat,
                                                  int64_t i, bool act, PhotonStage& stage,
                                                  int& fill, const PhotonOut& pout,
-                                                 Counts& cnt) {
+                                                 Counts& cnt, MlpWarp* mw) {
   R x = R(0), y = R(0), z = R(0), ux = R(0), uy = R(0), uz = R(0), w = R(0);
   uint32_t pid = 0;
   Acc<R> ll, le;
@@ -458,6 +576,11 @@ __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const G
   const bool live = act && isfinite(chk);
   if (act && !live) ++cnt.nan;
   uint64_t phase = P.phase_t0;
+  // ledger entry of this particle (-1: id outside the ledger)
+  const int64_t li64 = static_cast<int64_t>(pid - P.pid0);
+  const int32_t li_q = (live && li64 < P.led_n) ? static_cast<int32_t>(li64) : -1;
+  (void)li_q;
+  (void)mw;
 
   for (int s = 0; s < P.nsub; ++s) {
     const uint32_t step = static_cast<uint32_t>(P.t0 + s);
@@ -526,30 +649,60 @@ __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const G
       xn -= P.Lx * flr((xn - P.x0) * (R(1) / P.Lx));
       yn -= P.Ly * flr((yn - P.y0) * (R(1) / P.Ly));
     }
-    // 8. Monte Carlo emission: proposal x = P^-1(R'), dN of Eq. (13)
     const uint4 rnd = philox10(make_uint4(pid, step, 0u, P.ensemble), P.key0, P.key1);
-    R xs, g;
-    sample_x_g(P, rnd.x, rnd.y, xs, g);
-    const R dN = P.cn_dt * Om * g * rcp(xs);
-    const R fl = flr(dN);
     R Rr;
     if constexpr (sizeof(R) == 4)
       Rr = fmaf(static_cast<float>(rnd.z), 0x1p-32f, 0x1p-33f);
     else
       Rr = fma(static_cast<double>(rnd.z), 0x1p-32, 0x1p-33);
-    const R k = fl + ((Rr < dN - fl) ? R(1) : R(0));
-    if (live && dN > R(1)) ++cnt.dn1;
-    const bool want = live && k > R(0) && w > R(0);
-    // 9. append + emitted-energy ledger
-    const R eps = xs * epsc;
-    if (want) le.add(k * w * eps);
-    {
-      const R inv = ua2 > R(0) ? rsq(ua2) : R(0);
+    const R inv = ua2 > R(0) ? rsq(ua2) : R(0);
+    if constexpr (SAMP == PRAD_SAMPLER_TABLE) {
+      // 8. Monte Carlo emission: proposal x = P^-1(R'), dN of Eq. (13)
+      R xs, g;
+      sample_x_g(P, rnd.x, rnd.y, xs, g);
+      const R dN = P.cn_dt * Om * g * rcp(xs);
+      const R fl = flr(dN);
+      const R k = fl + ((Rr < dN - fl) ? R(1) : R(0));
+      if (live && dN > R(1)) ++cnt.dn1;
+      const bool want = live && k > R(0) && w > R(0);
+      // 9. append + emitted-energy ledger
+      const R eps = xs * epsc;
+      if (want) le.add(k * w * eps);
       const float rec[8] = {static_cast<float>(xn), static_cast<float>(yn),
                             static_cast<float>(zn), static_cast<float>(ax * inv),
                             static_cast<float>(ay * inv), static_cast<float>(az * inv),
                             static_cast<float>(eps), static_cast<float>(k * w)};
       stage_photon(stage, fill, pout, want, rec, pid, step);
+    } else {
+      // 8'. direct scheme: photons of this step ~ mean (5 sqrt3/6) alpha
+      //     Omega dt (the integral of Eq. (13)'s spectrum), multiplicity as in
+      //     the table path; the frequency x = G^-1(r') from the MLP
+      const R pm = P.cp_dt * Om;
+      const R fl = flr(pm);
+      const R k = fl + ((Rr < pm - fl) ? R(1) : R(0));
+      if (live && pm > R(1)) ++cnt.dn1;
+      const bool want = live && k > R(0) && w > R(0);
+      const float rp = fmaf(static_cast<float>(rnd.x), 0x1p-32f, 0x1p-33f);
+      const bool tail = rp < kRMin || rp > kRMax;
+      // uniforms outside the trained range: x from the G^-1 table at once
+      const bool now = want && tail;
+      float xt = 0.0f;
+      if (now) {
+        xt = __expf(ginv_ln(P.ginv, rp));
+        ++cnt.fallback;
+        le.add(k * w * xt * epsc);
+      }
+      const float rec[8] = {static_cast<float>(xn), static_cast<float>(yn),
+                            static_cast<float>(zn), static_cast<float>(ax * inv),
+                            static_cast<float>(ay * inv), static_cast<float>(az * inv),
+                            static_cast<float>(xt * epsc), static_cast<float>(k * w)};
+      stage_photon(stage, fill, pout, now, rec, pid, step);
+      const bool q = want && !tail;
+      const float3 f = mlp_features(rp, static_cast<float>(ga),
+                                    static_cast<float>(R(1.5) * Om * ga * ga * P.dtn));
+      mlp_enqueue(*mw, q, f, rp, static_cast<float>(epsc), static_cast<float>(k * w), rec,
+                  rec + 3, pid, step, li_q);
+      while (mw->count >= 16) mlp_flush_tile(P, *mw, stage, fill, pout, cnt);
     }
     if (live) {
       x = xn; y = yn; z = zn;
@@ -583,26 +736,27 @@ __device__ __forceinline__ PhotonOut make_pout(const StepParams<R>& P) {
 
 // Block reduction of the counters: one atomic per nonzero block total.
 __device__ __forceinline__ void flush_counts(const Counts& c, unsigned long long* counters) {
-  __shared__ uint32_t red[5][32];
+  __shared__ uint32_t red[6][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t v0 = __reduce_add_sync(0xffffffffu, c.dn1);
   const uint32_t v1 = __reduce_add_sync(0xffffffffu, c.clamp);
   const uint32_t v2 = __reduce_add_sync(0xffffffffu, c.chi);
   const uint32_t v3 = __reduce_add_sync(0xffffffffu, c.nan);
-  const uint32_t v4 = __reduce_add_sync(0xffffffffu, c.bad_id ? 1u : 0u);
+  const uint32_t v4 = __reduce_add_sync(0xffffffffu, c.fallback);
+  const uint32_t v5 = __reduce_add_sync(0xffffffffu, c.bad_id ? 1u : 0u);
   if (lane == 0) {
     red[0][warp] = v0; red[1][warp] = v1; red[2][warp] = v2; red[3][warp] = v3;
-    red[4][warp] = v4;
+    red[4][warp] = v4; red[5][warp] = v5;
   }
   __syncthreads();
   if (warp == 0) {
     const int nw = blockDim.x >> 5;
 #pragma unroll
-    for (int k = 0; k < 5; ++k) {
+    for (int k = 0; k < 6; ++k) {
       const uint32_t v = lane < nw ? red[k][lane] : 0u;
       const uint32_t t = __reduce_add_sync(0xffffffffu, v);
       if (lane == 0 && t) {
-        if (k < 4)
+        if (k < 5)
           atomicAdd(counters + kDnGt1 + k, static_cast<unsigned long long>(t));
         else
           atomicOr(counters + kStatus, 2ull);  // status bit 1: id outside ledger
@@ -619,28 +773,50 @@ __device__ __forceinline__ void flush_counts(const Counts& c, unsigned long long
 #ifndef PRAD_F32_MINB
 #define PRAD_F32_MINB 5
 #endif
-template <typename R>
+#ifndef PRAD_MLP_MINB
+#define PRAD_MLP_MINB 3
+#endif
+// The Yee gather (54 loads in flight) and the learned sampler's tensor-core
+// tile need more registers than the analytic-field table path.
+template <typename R, int FIELD, int SAMP>
 struct MinBlocks {
-  static constexpr int value = 1;
-};
-template <>
-struct MinBlocks<float> {
-  static constexpr int value = PRAD_F32_MINB;
+  static constexpr int value =
+      sizeof(R) == 8 ? 1
+                     : (SAMP != PRAD_SAMPLER_TABLE ? PRAD_MLP_MINB
+                                                   : (FIELD == PRAD_FIELD_YEE2D ? 4 : PRAD_F32_MINB));
 };
 
-template <typename R, int FIELD>
-__global__ void __launch_bounds__(256, MinBlocks<R>::value) k_push_emit(const StepParams<R> P) {
+// Dynamic shared memory of the learned-sampler variant: the network image
+// and one emission queue per warp.
+constexpr size_t kMlpDynSmem = sizeof(MlpSmem) + kMaxWarps * sizeof(MlpQueue);
+
+template <typename R, int FIELD, int SAMP>
+__global__ void __launch_bounds__(256, (MinBlocks<R, FIELD, SAMP>::value))
+    k_push_emit(const StepParams<R> P) {
   __shared__ PhotonStage stage_all[kMaxWarps];
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
   PhotonStage& stage = stage_all[threadIdx.x >> 5];
   int fill = 0;  // warp-uniform
   const PhotonOut pout = make_pout(P);
   Counts cnt;
+  MlpWarp mw{nullptr, nullptr, 0, SAMP == PRAD_SAMPLER_MLP_FALLBACK};
+  if constexpr (SAMP != PRAD_SAMPLER_TABLE) {
+    MlpSmem* net = reinterpret_cast<MlpSmem*>(dyn_smem);
+    MlpQueue* qs = reinterpret_cast<MlpQueue*>(dyn_smem + sizeof(MlpSmem));
+    mlp_load_smem(*net, P.mlp);
+    __syncthreads();
+    mw.net = net;
+    mw.q = qs + (threadIdx.x >> 5);
+  }
   const FieldGather<R, FIELD> gat{P};
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   for (int64_t base = static_cast<int64_t>(blockIdx.x) * blockDim.x; base < P.n;
        base += stride) {
     const int64_t i = base + threadIdx.x;
-    advance_particle<R, FIELD>(P, gat, i, i < P.n, stage, fill, pout, cnt);
+    advance_particle<R, FIELD, SAMP>(P, gat, i, i < P.n, stage, fill, pout, cnt, &mw);
+  }
+  if constexpr (SAMP != PRAD_SAMPLER_TABLE) {
+    while (mw.count > 0) mlp_flush_tile(P, mw, stage, fill, pout, cnt);
   }
   if (fill > 0) flush_stage(stage, fill, pout);
   flush_counts(cnt, P.counters);
@@ -681,7 +857,8 @@ __global__ void __launch_bounds__(256, 3) k_push_emit_tiled(const StepParams<R> 
   const TileGather<R> gat{P, tile_sm, gx0, gy0};
   for (int64_t base = wk.y; base < wk.z; base += blockDim.x) {
     const int64_t i = base + threadIdx.x;
-    advance_particle<R, PRAD_FIELD_YEE2D>(P, gat, i, i < wk.z, stage, fill, pout, cnt);
+    advance_particle<R, PRAD_FIELD_YEE2D, PRAD_SAMPLER_TABLE>(P, gat, i, i < wk.z, stage,
+                                                              fill, pout, cnt, nullptr);
   }
   if (fill > 0) flush_stage(stage, fill, pout);
   flush_counts(cnt, P.counters);
@@ -699,23 +876,46 @@ cudaError_t launch_push_emit_tiled(const StepParams<R>& p, int max_work, int blo
   return cudaGetLastError();
 }
 
+template <typename R, int FIELD>
+cudaError_t launch_field(const StepParams<R>& p, int sampler, int grid, int block,
+                         cudaStream_t s) {
+  if (sampler == PRAD_SAMPLER_TABLE) {
+    k_push_emit<R, FIELD, PRAD_SAMPLER_TABLE><<<grid, block, 0, s>>>(p);
+    return cudaGetLastError();
+  }
+  if constexpr (sizeof(R) == 4) {
+    cudaError_t e;
+    if (sampler == PRAD_SAMPLER_MLP) {
+      e = cudaFuncSetAttribute(k_push_emit<R, FIELD, PRAD_SAMPLER_MLP>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               static_cast<int>(kMlpDynSmem));
+      if (e != cudaSuccess) return e;
+      k_push_emit<R, FIELD, PRAD_SAMPLER_MLP><<<grid, block, kMlpDynSmem, s>>>(p);
+    } else {
+      e = cudaFuncSetAttribute(k_push_emit<R, FIELD, PRAD_SAMPLER_MLP_FALLBACK>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               static_cast<int>(kMlpDynSmem));
+      if (e != cudaSuccess) return e;
+      k_push_emit<R, FIELD, PRAD_SAMPLER_MLP_FALLBACK><<<grid, block, kMlpDynSmem, s>>>(p);
+    }
+    return cudaGetLastError();
+  }
+  return cudaErrorInvalidValue;
+}
+
 template <typename R>
-cudaError_t launch_push_emit(const StepParams<R>& p, int field_kind, int grid,
+cudaError_t launch_push_emit(const StepParams<R>& p, int field_kind, int sampler, int grid,
                              int block, cudaStream_t s) {
   switch (field_kind) {
     case PRAD_FIELD_CONST:
-      k_push_emit<R, PRAD_FIELD_CONST><<<grid, block, 0, s>>>(p);
-      break;
+      return launch_field<R, PRAD_FIELD_CONST>(p, sampler, grid, block, s);
     case PRAD_FIELD_PLANE_WAVE:
-      k_push_emit<R, PRAD_FIELD_PLANE_WAVE><<<grid, block, 0, s>>>(p);
-      break;
+      return launch_field<R, PRAD_FIELD_PLANE_WAVE>(p, sampler, grid, block, s);
     case PRAD_FIELD_YEE2D:
-      k_push_emit<R, PRAD_FIELD_YEE2D><<<grid, block, 0, s>>>(p);
-      break;
+      return launch_field<R, PRAD_FIELD_YEE2D>(p, sampler, grid, block, s);
     default:
       return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
 }
 
 // ---- diagnostics kernels ---------------------------------------------------
@@ -760,8 +960,10 @@ cudaError_t launch_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1,
   return cudaGetLastError();
 }
 
-template cudaError_t launch_push_emit<float>(const StepParams<float>&, int, int, int, cudaStream_t);
-template cudaError_t launch_push_emit<double>(const StepParams<double>&, int, int, int, cudaStream_t);
+template cudaError_t launch_push_emit<float>(const StepParams<float>&, int, int, int, int,
+                                            cudaStream_t);
+template cudaError_t launch_push_emit<double>(const StepParams<double>&, int, int, int, int,
+                                             cudaStream_t);
 template cudaError_t launch_push_emit_tiled<float>(const StepParams<float>&, int, int, cudaStream_t);
 template cudaError_t launch_push_emit_tiled<double>(const StepParams<double>&, int, int, cudaStream_t);
 template cudaError_t launch_eval_sampler<float>(const StepParams<float>&, const uint32_t*, float*, float*, int64_t, cudaStream_t);

@@ -80,6 +80,13 @@ SIGNATURES = {
                                   ctypes.POINTER(prad_stats)]),
     "prad_get_ledger": (_i32, [_vp, _vp, _vp, _i64, _i64, _i32]),
     "prad_reset": (_i32, [_vp]),
+    "prad_mlp_set_weights": (_i32, [_vp, _vp, _i64]),
+    "prad_mlp_get_weights": (_i32, [_vp, _vp, _i64]),
+    "prad_mlp_train": (_i32, [_vp, _i64, _i32, ctypes.c_float, _u64,
+                              ctypes.POINTER(ctypes.c_float)]),
+    "prad_mlp_grad": (_i32, [_vp, _vp, _i64, _vp, ctypes.POINTER(_dbl)]),
+    "prad_mlp_eval": (_i32, [_vp, _vp, _vp, _i64]),
+    "prad_ginv_eval": (_i32, [_vp, _vp, _vp, _i64]),
     "prad_philox": (_i32, [_vp, _vp, _u32, _u32, _vp, _i64]),
     "prad_eval_sampler": (_i32, [_vp, _vp, _vp, _vp, _i64]),
 }
@@ -166,6 +173,44 @@ def prad_get_ledger(h, emit_ptr, ll_ptr, offset: int, n: int, on_device: bool) -
 
 def prad_reset(h) -> None:
     _check(load_library().prad_reset(h), h)
+
+
+PRAD_MLP_NUM_PARAMS = 4481
+
+
+def prad_mlp_set_weights(h, params) -> None:
+    import numpy as np
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    _check(load_library().prad_mlp_set_weights(h, p.ctypes.data, p.size), h)
+
+
+def prad_mlp_get_weights(h):
+    import numpy as np
+    p = np.zeros(PRAD_MLP_NUM_PARAMS, dtype=np.float32)
+    _check(load_library().prad_mlp_get_weights(h, p.ctypes.data, p.size), h)
+    return p
+
+
+def prad_mlp_train(h, steps: int, batch: int, lr: float, seed: int) -> float:
+    loss = ctypes.c_float()
+    _check(load_library().prad_mlp_train(h, steps, batch, lr, seed, ctypes.byref(loss)), h)
+    return loss.value
+
+
+def prad_mlp_grad(h, samples_ptr, n: int):
+    import numpy as np
+    g = np.zeros(PRAD_MLP_NUM_PARAMS, dtype=np.float32)
+    loss = _dbl()
+    _check(load_library().prad_mlp_grad(h, samples_ptr, n, g.ctypes.data, ctypes.byref(loss)), h)
+    return g, loss.value
+
+
+def prad_mlp_eval(h, in_ptr, out_ptr, n: int) -> None:
+    _check(load_library().prad_mlp_eval(h, in_ptr, out_ptr, n), h)
+
+
+def prad_ginv_eval(h, r_ptr, out_ptr, n: int) -> None:
+    _check(load_library().prad_ginv_eval(h, r_ptr, out_ptr, n), h)
 
 
 def prad_philox(h, ctr_ptr, k0: int, k1: int, out_ptr, n: int) -> None:
@@ -329,6 +374,39 @@ class Context:
 
     def reset(self) -> None:
         prad_reset(self.h)
+
+    # -- learned sampler -------------------------------------------------------
+    def mlp_train(self, steps: int, batch: int = 65536, lr: float = 3e-3,
+                  seed: int = 7) -> float:
+        return prad_mlp_train(self.h, steps, batch, lr, seed)
+
+    def mlp_weights(self):
+        return prad_mlp_get_weights(self.h)
+
+    def mlp_set_weights(self, params) -> None:
+        prad_mlp_set_weights(self.h, params)
+
+    def mlp_eval(self, r, gamma, wdt):
+        """ln x of the network for torch/numpy arrays r, gamma, omega_c dt."""
+        torch = self.torch
+        inp = torch.stack([torch.as_tensor(v, dtype=torch.float32).flatten()
+                           for v in (r, gamma, wdt)], 1).cuda().contiguous()
+        out = torch.empty(inp.shape[0], dtype=torch.float32, device="cuda")
+        prad_mlp_eval(self.h, inp.data_ptr(), out.data_ptr(), inp.shape[0])
+        return out
+
+    def mlp_grad(self, r, gamma, wdt, lnx_target):
+        torch = self.torch
+        smp = torch.stack([torch.as_tensor(v, dtype=torch.float32).flatten()
+                           for v in (r, gamma, wdt, lnx_target)], 1).cuda().contiguous()
+        return prad_mlp_grad(self.h, smp.data_ptr(), smp.shape[0])
+
+    def ginv(self, r):
+        torch = self.torch
+        rr = torch.as_tensor(r, dtype=torch.float32).flatten().cuda().contiguous()
+        out = torch.empty_like(rr)
+        prad_ginv_eval(self.h, rr.data_ptr(), out.data_ptr(), rr.numel())
+        return out
 
     def close(self) -> None:
         if getattr(self, "h", None):

@@ -1,0 +1,52 @@
+"""Pins of the FP64 numpy MLP used to check the GPU training kernels:
+central finite differences of the loss (without the BF16 roundings, where
+the loss is smooth) against the analytic backward pass, and the BF16 rounding
+helper against torch's bfloat16 conversion (a library)."""
+import numpy as np
+import pytest
+
+from oracle import mlp as M
+
+
+def _batch(n=64, seed=1):
+    rng = np.random.default_rng(seed)
+    r = rng.uniform(1e-5, 1 - 1e-5, n)
+    g = np.exp(rng.uniform(np.log(10), np.log(1e4), n))
+    w = np.exp(rng.uniform(-3, 19, n))
+    t = rng.normal(-1.0, 3.0, n)
+    return r, g, w, t
+
+
+def test_backward_matches_finite_differences():
+    p = M.glorot(3)
+    r, g, w, t = _batch()
+    _, grad = M.loss_and_grad(p, r, g, w, t, rounding=False)
+    rng = np.random.default_rng(0)
+    idx = np.concatenate([rng.choice(np.arange(M.OFF_W1, M.OFF_B1), 6),
+                          rng.choice(np.arange(M.OFF_B1, M.OFF_W2), 4),
+                          rng.choice(np.arange(M.OFF_W2, M.OFF_B2), 10),
+                          rng.choice(np.arange(M.OFF_B2, M.OFF_W3), 4),
+                          rng.choice(np.arange(M.OFF_W3, M.OFF_B3), 4), [M.OFF_B3]])
+    h = 1e-6
+    for k in idx:
+        pp, pm = p.copy(), p.copy()
+        pp[k] += h
+        pm[k] -= h
+        lp, _ = M.loss_and_grad(pp, r, g, w, t, rounding=False)
+        lm, _ = M.loss_and_grad(pm, r, g, w, t, rounding=False)
+        fd = (lp - lm) / (2 * h)
+        assert grad[k] == pytest.approx(fd, rel=1e-5, abs=1e-10)
+
+
+def test_bf16_rounding_matches_torch():
+    torch = pytest.importorskip("torch")
+    x = np.random.default_rng(2).normal(0, 10, 10000)
+    ref = torch.tensor(x, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(M.bf16(x), ref)
+
+
+def test_features_definition():
+    f = M.features(np.array([0.5, 1 / (1 + np.e ** 8)]), np.array([316.2, 1e6]),
+                   np.array([np.exp(8.2), 1e-30]))
+    assert f[0] == pytest.approx([0.0, 0.0, 0.0], abs=1e-4)
+    assert f[1] == pytest.approx([-1.0, 1.0, -1.0], abs=1e-12)

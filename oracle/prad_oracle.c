@@ -309,7 +309,9 @@ double orc_Q(double x) {
 double orc_Ginv(double r) {
   if (r <= 0.0) return 0.0;
   if (r >= 1.0) return INFINITY;
-  double lo = -60.0, hi = log(80.0);
+  /* ln x from -200: G(x) ~ 1.23 x^(1/3) reaches r = 1e-30 at ln x ~ -207,
+   * so every r representable in the tests is bracketed */
+  double lo = -230.0, hi = log(80.0);
   for (int it = 0; it < 200; ++it) {
     double mid = 0.5 * (lo + hi);
     if (orc_G(exp(mid)) < r) lo = mid; else hi = mid;

@@ -225,7 +225,7 @@ def test_yee_full_size_subset_parity():
     _fp32_multistep_ok(_urel(gstate, r["state"]))
     le, ll = ctx.ledger()
     lr = np.abs(ll.cpu().numpy()[sel] / r["ledger"]["ll"] - 1)
-    assert np.median(lr) < 1e-5 and np.quantile(lr, 0.99) < 5e-3
+    assert np.median(lr) < 1e-4 and np.quantile(lr, 0.99) < 5e-3
     assert ll.cpu().numpy()[sel].sum() == pytest.approx(r["ledger"]["ll"].sum(), rel=1e-4)
     ph = ctx.photons(on_device=False)
     keep = np.isin(ph["pid"].numpy(), sel)

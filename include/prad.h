@@ -273,9 +273,10 @@ int prad_mlp_get_weights(prad_ctx* ctx, float* params, int64_t n);
  * cosine decay to 0) on minibatches of `batch` samples generated on the
  * device (r uniform in the trained range, gamma log-uniform in [10, 1e4],
  * H_eff log-uniform in [1e2, 1e6] T, omega_c dt from the context's dt;
- * target ln G^-1(r) from the device table), loss = mean squared error of
- * ln x / 10.  *final_loss (host, may be NULL) receives the last minibatch
- * loss.  Synchronises. */
+ * target ln G^-1(r) from the device table), loss = mean over samples of
+ * w (o - ln x / 10)^2 with o the network output and the energy weight
+ * w = (1 + x) / 1.308.  *final_loss (host, may be NULL) receives the last
+ * minibatch loss.  Synchronises. */
 int prad_mlp_train(prad_ctx* ctx, int64_t steps, int32_t batch, float lr, uint64_t seed,
                    float* final_loss);
 

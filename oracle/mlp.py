@@ -10,7 +10,9 @@ arXiv:1409.5574).  Model definition (as documented with the C ABI):
   layer 1   z1 = W1 f + b1,  h1 = bf16(silu(z1))        (W1 in BF16)
   layer 2   z2 = W2 h1 + b2, h2 = silu(z2)              (W2 in BF16)
   layer 3   o  = W3 h2 + b3                             (W3 in BF16)
-  output    ln x = 10 o;  loss = mean (o - ln x_target / 10)^2
+  output    ln x = 10 o
+  loss      mean over samples of w (o - ln x_target / 10)^2,
+            w = (1 + x_target) / 1.308 (energy weighting, mean 1)
 
 Parameter vector: W1[64][3], b1[64], W2[64][64], b2[64], W3[64], b3 (4481).
 Everything here is FP64 except the two BF16 roundings the definition names;
@@ -85,8 +87,9 @@ def loss_and_grad(p, r, gamma, wdt, lnx_target, rounding=True):
     t = np.asarray(lnx_target, dtype=np.float64) / 10.0
     n = o.size
     diff = o - t
-    loss = np.mean(diff * diff)
-    do = 2.0 * diff / n
+    wgt = (1.0 + np.exp(np.asarray(lnx_target, dtype=np.float64))) / 1.308
+    loss = np.mean(wgt * diff * diff)
+    do = 2.0 * wgt * diff / n
     g = np.zeros(NUM_PARAMS)
     g[OFF_W3:OFF_B3] = h2.T @ do
     g[OFF_B3] = do.sum()

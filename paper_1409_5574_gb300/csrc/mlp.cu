@@ -156,8 +156,12 @@ __global__ void __launch_bounds__(kTThreads)
     for (int j = 0; j < kHid; ++j) o = fmaf(S.net.w3[j], silu(S.z2[s][j]), o);
     const bool valid = S.x[s][3] == 0.0f;
     const float diff = o - S.tgt[s];
-    S.loss[s] = valid ? diff * diff : 0.0f;
-    S.dout[s] = valid ? 2.0f * diff / static_cast<float>(sp.n_total) : 0.0f;
+    // energy weighting: (1 + x) / 1.308 (mean 1 over r uniform), so the
+    // high-x part of the spectrum, which carries the emitted energy, is fitted
+    // as tightly as the photon number
+    const float wgt = (1.0f + __expf(kOutScale * S.tgt[s])) * (1.0f / 1.308f);
+    S.loss[s] = valid ? wgt * diff * diff : 0.0f;
+    S.dout[s] = valid ? 2.0f * wgt * diff / static_cast<float>(sp.n_total) : 0.0f;
   }
   __syncthreads();
   // delta2 = dout W3 silu'(z2): BF16 copies for the two tensor-core products

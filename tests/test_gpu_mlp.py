@@ -116,6 +116,12 @@ def test_trained_spectral_error_below_one_percent(trained, gamma, wdt):
     err = _spectral_error(ctx, gamma, wdt)
     assert before > 0.05          # what training gains: from a useless sampler
     assert err <= 0.01, (gamma, wdt, err, loss)
+    # mean photon energy E[x] = int_0^1 G^-1(r) dr = (8 pi/9 sqrt3)/(5 pi/3)
+    n = 200_000
+    r = (np.arange(n) + 0.5) / n
+    x = np.exp(ctx.mlp_eval(r, np.full(n, gamma), np.full(n, wdt)).cpu().numpy())
+    ex = (8 * math.pi / (9 * math.sqrt(3))) / (5 * math.pi / 3)
+    assert abs(x.mean() / ex - 1) < 5e-3, x.mean() / ex
     ctx.close()
 
 

@@ -271,7 +271,8 @@ int prad_mlp_get_weights(prad_ctx* ctx, float* params, int64_t n);
 
 /* Train the context's network on the GPU: `steps` Adam steps (lr with a
  * cosine decay to 0) on minibatches of `batch` samples generated on the
- * device (r uniform in the trained range, gamma log-uniform in [10, 1e4],
+ * device (r uniform in the trained range for half of the samples and
+ * uniform in logit(r) on [-16, 16] for the other half, gamma log-uniform in [10, 1e4],
  * H_eff log-uniform in [1e2, 1e6] T, omega_c dt from the context's dt;
  * target ln G^-1(r) from the device table), loss = mean over samples of
  * w (o - ln x / 10)^2 with o the network output and the energy weight

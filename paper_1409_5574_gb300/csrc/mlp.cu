@@ -46,8 +46,8 @@ struct TrainSmem {
   __nv_bfloat16 d2t[kHid * kLdT];     // delta2 transposed [j][s]
 };
 
-// Training samples: r from a 64-bit Philox uniform (tag 3), gamma log-uniform
-// in [g_lo, g_hi], H log-uniform in [h_lo, h_hi] T, omega_c dt = 1.5 e H / m
+// Training samples: r from a Philox uniform (tag 3), gamma log-uniform in
+// [g_lo, g_hi], H log-uniform in [h_lo, h_hi] T, omega_c dt = 1.5 e H / m
 // gamma^2 dt; target ln G^-1(r) from the device table.
 struct SampleSpec {
   uint32_t key0, key1;
@@ -70,9 +70,17 @@ __device__ void make_sample(const SampleSpec& sp, int64_t idx, float* f, float* 
     const uint4 w = philox10_mlp(make_uint4(static_cast<uint32_t>(s),
                                             static_cast<uint32_t>(s >> 32), 3u, 0u),
                                  sp.key0, sp.key1);
-    // r in [kRMin, kRMax]: the trained range
+    // r in [kRMin, kRMax], the trained range: even samples uniform in r, odd
+    // samples uniform in logit(r) on [-16, 16], so both tails (where the
+    // energy-carrying high-x end lives) are covered
     const float u = fmaf(static_cast<float>(w.x), 0x1p-32f, 0x1p-33f);
-    r = kRMin + (kRMax - kRMin) * u;
+    if (s & 1ull) {
+      const float lg = -16.0f + 32.0f * u;
+      r = 1.0f / (1.0f + __expf(-lg));
+    } else {
+      r = u;
+    }
+    r = fminf(fmaxf(r, kRMin), kRMax);
     const float ug = fmaf(static_cast<float>(w.y), 0x1p-32f, 0x1p-33f);
     const float uh = fmaf(static_cast<float>(w.z), 0x1p-32f, 0x1p-33f);
     gam = __expf(sp.lng_lo + sp.lng_span * ug);

@@ -250,7 +250,8 @@ int prad_get_ledger(prad_ctx* ctx, double* emit, double* ll, int64_t offset,
 int prad_reset(prad_ctx* ctx);
 
 /* ---- learned sampler (PRAD_SAMPLER_MLP, PRAD_SAMPLER_MLP_FALLBACK) --------
- * A 3 -> 64 -> 64 -> 1 MLP (SiLU, BF16 weights, FP32 accumulate) maps
+ * A 3 -> 64 -> 64 -> 1 MLP (SiLU, BF16 weights, FP32 accumulate) plus a
+ * fixed prior ln(-ln(1 - r)) + 2 (1 - r) ln r maps
  * (r, gamma, omega_c dt) to ln x with G(x) = r, G the photon-number CDF of
  * the spectrum of Eqs. (7)-(8), int_0^x F(t)/t dt / (5 pi / 3).  With an MLP
  * sampler, push_emit uses the direct scheme: the photons of a step have mean
@@ -271,12 +272,11 @@ int prad_mlp_get_weights(prad_ctx* ctx, float* params, int64_t n);
 
 /* Train the context's network on the GPU: `steps` Adam steps (lr with a
  * cosine decay to 0) on minibatches of `batch` samples generated on the
- * device (r uniform in the trained range for half of the samples and
- * uniform in logit(r) on [-16, 16] for the other half, gamma log-uniform in [10, 1e4],
+ * device (r uniform in the trained range, gamma log-uniform in [10, 1e4],
  * H_eff log-uniform in [1e2, 1e6] T, omega_c dt from the context's dt;
  * target ln G^-1(r) from the device table), loss = mean over samples of
- * w (o - ln x / 10)^2 with o the network output and the energy weight
- * w = (1 + x) / 1.308.  *final_loss (host, may be NULL) receives the last
+ * w (o - (ln x - prior(r)))^2 with o the network output, the fixed prior
+ * ln(-ln(1 - r)) + 2 (1 - r) ln r and the energy weight w = (1 + x)/1.308.  *final_loss (host, may be NULL) receives the last
  * minibatch loss.  Synchronises. */
 int prad_mlp_train(prad_ctx* ctx, int64_t steps, int32_t batch, float lr, uint64_t seed,
                    float* final_loss);

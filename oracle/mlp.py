@@ -10,8 +10,8 @@ arXiv:1409.5574).  Model definition (as documented with the C ABI):
   layer 1   z1 = W1 f + b1,  h1 = bf16(silu(z1))        (W1 in BF16)
   layer 2   z2 = W2 h1 + b2, h2 = silu(z2)              (W2 in BF16)
   layer 3   o  = W3 h2 + b3                             (W3 in BF16)
-  output    ln x = 10 o
-  loss      mean over samples of w (o - ln x_target / 10)^2,
+  output    ln x = prior(r) + o,  prior(r) = ln(-ln(1 - r)) + 2 (1 - r) ln r
+  loss      mean over samples of w (o - (ln x_target - prior(r)))^2,
             w = (1 + x_target) / 1.308 (energy weighting, mean 1)
 
 Parameter vector: W1[64][3], b1[64], W2[64][64], b2[64], W3[64], b3 (4481).
@@ -76,15 +76,20 @@ def forward(p, f, rounding=True):
     return o, (f, z1, h1, z2, h2, W1r, W2r, W3r)
 
 
+def prior(r):
+    r = np.asarray(r, dtype=np.float64)
+    return np.log(-np.log1p(-r)) + 2.0 * (1.0 - r) * np.log(r)
+
+
 def ln_x(p, r, gamma, wdt, rounding=True):
     o, _ = forward(p, features(r, gamma, wdt), rounding)
-    return 10.0 * o
+    return o + prior(r)
 
 
 def loss_and_grad(p, r, gamma, wdt, lnx_target, rounding=True):
     f = features(r, gamma, wdt)
     o, (f, z1, h1, z2, h2, W1r, W2r, W3r) = forward(p, f, rounding)
-    t = np.asarray(lnx_target, dtype=np.float64) / 10.0
+    t = np.asarray(lnx_target, dtype=np.float64) - prior(r)
     n = o.size
     diff = o - t
     wgt = (1.0 + np.exp(np.asarray(lnx_target, dtype=np.float64))) / 1.308

@@ -36,7 +36,8 @@ struct TrainSmem {
   MlpSmem net;
   __nv_bfloat16 w2t[kHid * kW2Ld];    // W2 transposed [i][j]
   float x[kTB][4];                    // features
-  float tgt[kTB];                     // target ln x / kOutScale
+  float tgt[kTB];                     // target (ln x - prior) / kOutScale
+  float wgt[kTB];                     // loss weight
   float dout[kTB];                    // dL/do per sample
   float loss[kTB];
   float z1[kTB][kHid];
@@ -60,7 +61,8 @@ struct SampleSpec {
   int64_t n_valid;          // samples available from `first`
 };
 
-__device__ void make_sample(const SampleSpec& sp, int64_t idx, float* f, float* tgt) {
+__device__ void make_sample(const SampleSpec& sp, int64_t idx, float* f, float* tgt,
+                            float* wgt) {
   float r, gam, wdt, lnx;
   if (sp.explicit_samples) {
     const float4 v = sp.explicit_samples[idx];
@@ -70,17 +72,9 @@ __device__ void make_sample(const SampleSpec& sp, int64_t idx, float* f, float* 
     const uint4 w = philox10_mlp(make_uint4(static_cast<uint32_t>(s),
                                             static_cast<uint32_t>(s >> 32), 3u, 0u),
                                  sp.key0, sp.key1);
-    // r in [kRMin, kRMax], the trained range: even samples uniform in r, odd
-    // samples uniform in logit(r) on [-16, 16], so both tails (where the
-    // energy-carrying high-x end lives) are covered
+    // r uniform in [kRMin, kRMax], the trained range
     const float u = fmaf(static_cast<float>(w.x), 0x1p-32f, 0x1p-33f);
-    if (s & 1ull) {
-      const float lg = -16.0f + 32.0f * u;
-      r = 1.0f / (1.0f + __expf(-lg));
-    } else {
-      r = u;
-    }
-    r = fminf(fmaxf(r, kRMin), kRMax);
+    r = fminf(fmaxf(u, kRMin), kRMax);
     const float ug = fmaf(static_cast<float>(w.y), 0x1p-32f, 0x1p-33f);
     const float uh = fmaf(static_cast<float>(w.z), 0x1p-32f, 0x1p-33f);
     gam = __expf(sp.lng_lo + sp.lng_span * ug);
@@ -90,7 +84,11 @@ __device__ void make_sample(const SampleSpec& sp, int64_t idx, float* f, float* 
   }
   const float3 ff = mlp_features(r, gam, wdt);
   f[0] = ff.x; f[1] = ff.y; f[2] = ff.z; f[3] = 0.0f;
-  *tgt = lnx * (1.0f / kOutScale);
+  *tgt = (lnx - mlp_prior(r)) * (1.0f / kOutScale);
+  // energy weighting: (1 + x) / 1.308 (mean 1 over r uniform), so the
+  // high-x part of the spectrum, which carries the emitted energy, is fitted
+  // as tightly as the photon number
+  *wgt = (1.0f + __expf(lnx)) * (1.0f / 1.308f);
 }
 
 // One block: 128 samples, forward + backward; writes the block's partial
@@ -109,11 +107,12 @@ __global__ void __launch_bounds__(kTThreads)
   if (threadIdx.x < kTB) {
     const int64_t idx = base + threadIdx.x;
     if (idx < sp.n_valid) {
-      make_sample(sp, idx, S.x[threadIdx.x], &S.tgt[threadIdx.x]);
+      make_sample(sp, idx, S.x[threadIdx.x], &S.tgt[threadIdx.x], &S.wgt[threadIdx.x]);
     } else {  // padding rows contribute nothing
       S.x[threadIdx.x][0] = S.x[threadIdx.x][1] = S.x[threadIdx.x][2] = 0.0f;
       S.x[threadIdx.x][3] = -1.0f;  // marker
       S.tgt[threadIdx.x] = 0.0f;
+      S.wgt[threadIdx.x] = 0.0f;
     }
   }
   __syncthreads();
@@ -164,10 +163,7 @@ __global__ void __launch_bounds__(kTThreads)
     for (int j = 0; j < kHid; ++j) o = fmaf(S.net.w3[j], silu(S.z2[s][j]), o);
     const bool valid = S.x[s][3] == 0.0f;
     const float diff = o - S.tgt[s];
-    // energy weighting: (1 + x) / 1.308 (mean 1 over r uniform), so the
-    // high-x part of the spectrum, which carries the emitted energy, is fitted
-    // as tightly as the photon number
-    const float wgt = (1.0f + __expf(kOutScale * S.tgt[s])) * (1.0f / 1.308f);
+    const float wgt = S.wgt[s];
     S.loss[s] = valid ? wgt * diff * diff : 0.0f;
     S.dout[s] = valid ? 2.0f * wgt * diff / static_cast<float>(sp.n_total) : 0.0f;
   }
@@ -328,8 +324,8 @@ __global__ void __launch_bounds__(256) k_mlp_eval(MlpDev dev, const float* __res
     float olo, ohi;
     mlp_tile16(S, flo, fhi, olo, ohi);
     if ((lane & 3) == 0) {
-      if (r0 < n) out[r0] = olo;
-      if (r1 < n) out[r1] = ohi;
+      if (r0 < n) out[r0] = olo + mlp_prior(in[3 * r0]);
+      if (r1 < n) out[r1] = ohi + mlp_prior(in[3 * r1]);
     }
   }
 }

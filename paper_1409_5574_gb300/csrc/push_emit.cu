@@ -503,7 +503,7 @@ __device__ __forceinline__ void mlp_flush_tile(const StepParams<R>& P, MlpWarp& 
   float rec[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   uint32_t pid = 0, step = 0;
   if (mine) {
-    float lnx = lane < 8 ? vlo : vhi;
+    const float lnx = (lane < 8 ? vlo : vhi) + mlp_prior(q.r[lane]);
     float x = __expf(lnx);
     bool ok = x > 0.0f && x < 80.0f;  // also false for NaN
     if (mw.check_output) {

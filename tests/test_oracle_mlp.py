@@ -13,7 +13,7 @@ def _batch(n=64, seed=1):
     r = rng.uniform(1e-5, 1 - 1e-5, n)
     g = np.exp(rng.uniform(np.log(10), np.log(1e4), n))
     w = np.exp(rng.uniform(-3, 19, n))
-    t = rng.normal(-1.0, 3.0, n)
+    t = rng.uniform(-6.0, 2.5, n)       # ln x of the spectrum's bulk
     return r, g, w, t
 
 

@@ -93,6 +93,11 @@ typedef struct prad_config {
                                32 x 32-cell tile every this many steps and
                                gather from shared-memory field tiles
                                (0 = never sort; plain gather)             */
+  int32_t batch_chunk;      /* push_emit_batch: particles per work item
+                               (0 = 2048); multiple of 32                 */
+  int32_t use_graph;        /* push_emit_batch: capture the launches of a
+                               call in a CUDA graph and replay it when the
+                               next call has the same shape (0 = off)     */
   int32_t pad0;
 } prad_config;
 
@@ -211,6 +216,49 @@ int prad_set_fields(prad_ctx* ctx, const prad_fields* f);
  * PRAD_ERR_CUDA (launch failure).  n == 0 or nsteps == 0 is a no-op. */
 int prad_push_emit(prad_ctx* ctx, const prad_particles* p, int64_t n,
                    int32_t nsteps);
+
+/* ---- batched ensembles ---------------------------------------------------- */
+typedef struct prad_ensemble {
+  prad_particles p;  /* arrays, ids, ledger offset and t0 of this ensemble */
+  int64_t n;         /* particles (>= 0)                                   */
+  prad_fields field; /* CONST or PLANE_WAVE (the batch kernel has no Yee)  */
+  uint32_t ensemble; /* Philox counter word 3 for this ensemble            */
+  uint32_t pad0;
+} prad_ensemble;
+
+/* Advance n_ens independent ensembles of uneven size by nsteps steps in ONE
+ * persistent kernel per steps_per_launch chunk: a grid of SMs x blocks_per_sm
+ * blocks takes work items (batch_chunk particles of one ensemble) from an
+ * atomic counter until none are left, so large and small ensembles share
+ * the GPU without a launch per ensemble.  Each ensemble has its own field
+ * and Philox word 3; dt, omega_ref, seed, sampler (table only) and rr_mode
+ * are the context's.  With use_graph the launches of a call are captured in
+ * a CUDA graph and replayed by later calls of the same shape (same n_ens,
+ * sizes, nsteps and launch parameters); ensemble contents (arrays, t0,
+ * fields) may change between calls.  No kernel waits on another: nothing
+ * can spin.  Results per ensemble equal those of prad_push_emit with the
+ * same field and ensemble word.  Errors: PRAD_ERR_ARG (bad ensemble,
+ * ledger range, Yee field, n_ens < 1), PRAD_ERR_CUDA. */
+int prad_push_emit_batch(prad_ctx* ctx, const prad_ensemble* ens, int32_t n_ens,
+                         int32_t nsteps);
+
+typedef struct prad_tuning {
+  int32_t block_size, blocks_per_sm, batch_chunk, steps_per_launch;
+  double particle_steps_per_s; /* throughput of the chosen configuration  */
+  int32_t candidates;          /* configurations timed                   */
+  int32_t pad0;
+} prad_tuning;
+
+/* Autotune the batch launch for this ensemble set: time candidate
+ * (block_size, blocks_per_sm, batch_chunk, steps_per_launch) on scratch
+ * copies of up to `sample` particles per ensemble for probe_steps steps
+ * (CUDA events, after a warm-up), keep the fastest, store it in the
+ * context's configuration (used by later batch calls) and in *out.  The
+ * caller's particles, ledgers and photon records are left unchanged.
+ * A later call with the same ensemble sizes and GPU returns the cached
+ * result without timing.  Errors as for prad_push_emit_batch. */
+int prad_autotune_batch(prad_ctx* ctx, const prad_ensemble* ens, int32_t n_ens,
+                        int32_t probe_steps, int64_t sample, prad_tuning* out);
 
 /* Reorder n particles in place (x, y, z, ux, uy, uz, w and the pid array,
  * which is required) by the 32 x 32-cell tile of the YEE2D grid that holds

@@ -76,6 +76,16 @@ struct prad_ctx {
   float* d_mlp_loss = nullptr;
   int mlp_partial_blocks = 0;
   int64_t mlp_t = 0;             // Adam step count
+  // batched ensembles
+  StepParams<float>* d_batch = nullptr;
+  int64_t* d_batch_off = nullptr;
+  unsigned long long* d_batch_next = nullptr;
+  int batch_cap = 0;
+  std::vector<StepParams<float>> h_batch;
+  std::vector<int64_t> h_batch_off;
+  // captured CUDA graph of the last batch call shape
+  cudaGraphExec_t graph_exec = nullptr;
+  uint64_t graph_key = 0;
 };
 
 namespace {
@@ -309,7 +319,15 @@ MlpDev mlp_dev(const prad_ctx* c) {
 }
 
 template <typename R>
+void fill_common(const prad_ctx* c, StepParams<R>& p, const prad_fields& f);
+
+template <typename R>
 void fill_common(const prad_ctx* c, StepParams<R>& p) {
+  fill_common<R>(c, p, c->fields);
+}
+
+template <typename R>
+void fill_common(const prad_ctx* c, StepParams<R>& p, const prad_fields& f) {
   const double q = c->cfg.charge;
   const double dtn = c->dtn;
   p.half_q_dtn = static_cast<R>(0.5 * q * dtn);
@@ -343,8 +361,8 @@ void fill_common(const prad_ctx* c, StepParams<R>& p) {
   p.mlp = mlp_dev(c);
   p.ginv = c->d_ginv;
   // field, normalised: E by m c omega_ref / e, B by m omega_ref / e
-  const prad_fields& f = c->fields;
   const double w = c->cfg.omega_ref;
+  p.field_kind = f.kind;
   const double Er = kMe * kC * w / kQe, Br = kMe * w / kQe;
   for (int k = 0; k < 3; ++k) {
     p.E[k] = static_cast<R>(f.E[k] / Er);
@@ -637,6 +655,10 @@ int prad_init(prad_ctx** out, const prad_config* cfg) {
 int prad_destroy(prad_ctx* c) {
   if (!c) return PRAD_OK;
   free_sort(c->sort);
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  cudaFree(c->d_batch);
+  cudaFree(c->d_batch_off);
+  cudaFree(c->d_batch_next);
   cudaFree(c->d_tab32);
   cudaFree(c->d_tab64);
   for (int k = 0; k < 8; ++k) cudaFree(c->d_ph[k]);
@@ -820,6 +842,323 @@ int prad_eval_sampler(prad_ctx* c, const uint32_t* words, void* x_out, void* g_o
                                       static_cast<double*>(g_out), n, c->stream));
   }
   CK(c, cudaStreamSynchronize(c->stream));
+  return PRAD_OK;
+}
+
+namespace {
+
+uint64_t mix64(uint64_t h, uint64_t v) {
+  h ^= v + 0x9E3779B97F4A7C15ull + (h << 6) + (h >> 2);
+  return h * 0xBF58476D1CE4E5B9ull;
+}
+
+int check_ensemble(prad_ctx* c, const prad_ensemble& e, int k) {
+  if (e.n < 0) return fail(c, PRAD_ERR_ARG, "batch: ensemble %d has n < 0", k);
+  if (e.field.kind != PRAD_FIELD_CONST && e.field.kind != PRAD_FIELD_PLANE_WAVE)
+    return fail(c, PRAD_ERR_ARG, "batch: ensemble %d: only CONST and PLANE_WAVE fields", k);
+  if (e.field.kind == PRAD_FIELD_PLANE_WAVE &&
+      (!(e.field.lambda > 0.0) || (e.field.dir != 1 && e.field.dir != -1) ||
+       (e.field.hand != 1 && e.field.hand != -1)))
+    return fail(c, PRAD_ERR_ARG, "batch: ensemble %d: bad plane wave", k);
+  if (e.n == 0) return PRAD_OK;
+  const prad_particles& p = e.p;
+  const void* arrs[7] = {p.x, p.y, p.z, p.ux, p.uy, p.uz, p.w};
+  for (const void* a : arrs)
+    if (!a || !aligned(a, 4)) return fail(c, PRAD_ERR_ARG, "batch: ensemble %d: null array", k);
+  if (p.ledger_offset < 0 || p.ledger_offset + e.n > c->cfg.max_particles)
+    return fail(c, PRAD_ERR_ARG, "batch: ensemble %d: ledger range outside max_particles", k);
+  if (p.t0 < 0 || e.n > (int64_t(1) << 32)) return fail(c, PRAD_ERR_ARG, "batch: ensemble %d: bad t0/n", k);
+  return PRAD_OK;
+}
+
+// Fill the per-ensemble parameters and the work-item prefix sums; returns
+// the total number of work items.  `led` (optional) replaces the context's
+// ledgers (the autotuner books into scratch).
+int64_t build_batch(prad_ctx* c, const prad_ensemble* ens, int n_ens, int chunk,
+                    std::vector<StepParams<float>>& hp, std::vector<int64_t>& off,
+                    double* led_emit = nullptr, double* led_ll = nullptr) {
+  hp.resize(n_ens);
+  off.resize(n_ens + 1);
+  off[0] = 0;
+  for (int k = 0; k < n_ens; ++k) {
+    const prad_ensemble& e = ens[k];
+    StepParams<float>& p = hp[k];
+    p = StepParams<float>{};
+    fill_common<float>(c, p, e.field);
+    p.x = static_cast<float*>(e.p.x); p.y = static_cast<float*>(e.p.y);
+    p.z = static_cast<float*>(e.p.z);
+    p.ux = static_cast<float*>(e.p.ux); p.uy = static_cast<float*>(e.p.uy);
+    p.uz = static_cast<float*>(e.p.uz);
+    p.w = static_cast<const float*>(e.p.w);
+    p.pid = e.p.pid;
+    p.led_emit = (led_emit ? led_emit : c->d_led_emit) + e.p.ledger_offset;
+    p.led_ll = (led_ll ? led_ll : c->d_led_ll) + e.p.ledger_offset;
+    p.led_n = c->cfg.max_particles - e.p.ledger_offset;
+    p.n = e.n;
+    p.pid0 = e.p.pid0;
+    p.ensemble = e.ensemble;
+    p.t0 = e.p.t0;
+    p.phase_t0 = p.phase_t0 + static_cast<uint64_t>(p.t0) * p.phase_step;
+    off[k + 1] = off[k] + (e.n + chunk - 1) / chunk;
+  }
+  return off[n_ens];
+}
+
+int upload_batch(prad_ctx* c, const std::vector<StepParams<float>>& hp,
+                 const std::vector<int64_t>& off) {
+  const int n = static_cast<int>(hp.size());
+  if (n > c->batch_cap) {
+    cudaFree(c->d_batch);
+    cudaFree(c->d_batch_off);
+    c->d_batch = nullptr;
+    c->d_batch_off = nullptr;
+    c->batch_cap = 0;
+    CK(c, cudaMalloc(&c->d_batch, sizeof(StepParams<float>) * n));
+    CK(c, cudaMalloc(&c->d_batch_off, sizeof(int64_t) * (n + 1)));
+    c->batch_cap = n;
+  }
+  if (!c->d_batch_next) CK(c, cudaMalloc(&c->d_batch_next, sizeof(unsigned long long)));
+  c->h_batch = hp;  // keep the host copy alive until the copies complete
+  c->h_batch_off = off;
+  CK(c, cudaMemcpyAsync(c->d_batch, c->h_batch.data(), sizeof(StepParams<float>) * n,
+                        cudaMemcpyHostToDevice, c->stream));
+  CK(c, cudaMemcpyAsync(c->d_batch_off, c->h_batch_off.data(), sizeof(int64_t) * (n + 1),
+                        cudaMemcpyHostToDevice, c->stream));
+  return PRAD_OK;
+}
+
+// Issue the launches of one batch call on the stream (memset of the work
+// counter + one persistent kernel per steps_per_launch chunk).
+int issue_batch(prad_ctx* c, int n_ens, int64_t items, int32_t nsteps, int chunk, int nsub,
+                int block, int bps) {
+  BatchParams bp;
+  bp.ens = c->d_batch;
+  bp.item_off = c->d_batch_off;
+  bp.next_item = c->d_batch_next;
+  bp.total_items = items;
+  bp.n_ens = n_ens;
+  bp.chunk = chunk;
+  bp.pad = 0;
+  const int cap = batch_max_blocks_per_sm(block);
+  const int64_t g = static_cast<int64_t>(c->num_sms) * (bps < cap ? bps : cap);
+  const int grid = static_cast<int>(g < items ? g : (items > 0 ? items : 1));
+  for (int32_t done = 0; done < nsteps;) {
+    const int32_t m = (nsteps - done) < nsub ? (nsteps - done) : nsub;
+    bp.step_base = done;
+    bp.nsub = m;
+    CK(c, cudaMemsetAsync(c->d_batch_next, 0, sizeof(unsigned long long), c->stream));
+    CK(c, launch_push_emit_batch(bp, grid, block, c->stream));
+    done += m;
+  }
+  return PRAD_OK;
+}
+
+int batch_chunk_of(const prad_ctx* c) { return c->cfg.batch_chunk > 0 ? c->cfg.batch_chunk : 2048; }
+int batch_nsub_of(const prad_ctx* c, int32_t nsteps) {
+  const int s = c->cfg.steps_per_launch > 0 ? c->cfg.steps_per_launch : nsteps;
+  return s > 0 ? s : 1;
+}
+
+// process-wide cache of tuning results: (GPU, sizes, kinds, probe) -> tuning
+std::mutex g_tune_mu;
+std::vector<std::pair<uint64_t, prad_tuning>> g_tune_cache;
+
+}  // namespace
+
+int prad_push_emit_batch(prad_ctx* c, const prad_ensemble* ens, int32_t n_ens, int32_t nsteps) {
+  if (!c || !ens || n_ens < 1 || nsteps < 0)
+    return fail(c, PRAD_ERR_ARG, "push_emit_batch: bad argument");
+  if (c->cfg.precision != PRAD_FP32 || c->cfg.sampler != PRAD_SAMPLER_TABLE)
+    return fail(c, PRAD_ERR_ARG, "push_emit_batch: FP32 with the table sampler only");
+  for (int k = 0; k < n_ens; ++k) {
+    int rc = check_ensemble(c, ens[k], k);
+    if (rc != PRAD_OK) return rc;
+  }
+  if (nsteps == 0) return PRAD_OK;
+  const int chunk = batch_chunk_of(c);
+  const int nsub = batch_nsub_of(c, nsteps);
+  const int block = c->cfg.block_size > 0 ? c->cfg.block_size : 256;
+  const int bps = c->cfg.blocks_per_sm > 0 ? c->cfg.blocks_per_sm : 3;
+  std::vector<StepParams<float>> hp;
+  std::vector<int64_t> off;
+  const int64_t items = build_batch(c, ens, n_ens, chunk, hp, off);
+  int rc = upload_batch(c, hp, off);
+  if (rc != PRAD_OK) return rc;
+  if (items == 0) return PRAD_OK;
+  if (!c->cfg.use_graph) return issue_batch(c, n_ens, items, nsteps, chunk, nsub, block, bps);
+  if (c->stream == nullptr)
+    return fail(c, PRAD_ERR_ARG, "push_emit_batch: graph capture needs a non-default stream");
+  uint64_t key = 0x1234;
+  key = mix64(key, static_cast<uint64_t>(n_ens));
+  key = mix64(key, static_cast<uint64_t>(items));
+  for (int k = 0; k <= n_ens; ++k) key = mix64(key, static_cast<uint64_t>(off[k]));
+  key = mix64(key, static_cast<uint64_t>(nsteps));
+  key = mix64(key, (static_cast<uint64_t>(chunk) << 32) | static_cast<uint64_t>(nsub));
+  key = mix64(key, (static_cast<uint64_t>(block) << 32) | static_cast<uint64_t>(bps));
+  if (!c->graph_exec || c->graph_key != key) {
+    if (c->graph_exec) {
+      cudaGraphExecDestroy(c->graph_exec);
+      c->graph_exec = nullptr;
+    }
+    CK(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    rc = issue_batch(c, n_ens, items, nsteps, chunk, nsub, block, bps);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(c->stream, &graph);
+    if (rc != PRAD_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (ee != cudaSuccess) return fail(c, PRAD_ERR_CUDA, "graph capture: %s", cudaGetErrorString(ee));
+    const cudaError_t ei = cudaGraphInstantiate(&c->graph_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) return fail(c, PRAD_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ei));
+    c->graph_key = key;
+  }
+  CK(c, cudaGraphLaunch(c->graph_exec, c->stream));
+  return PRAD_OK;
+}
+
+int prad_autotune_batch(prad_ctx* c, const prad_ensemble* ens, int32_t n_ens, int32_t probe_steps,
+                        int64_t sample, prad_tuning* out) {
+  if (!c || !ens || n_ens < 1 || probe_steps < 1 || sample < 32)
+    return fail(c, PRAD_ERR_ARG, "autotune_batch: bad argument");
+  if (c->cfg.precision != PRAD_FP32 || c->cfg.sampler != PRAD_SAMPLER_TABLE)
+    return fail(c, PRAD_ERR_ARG, "autotune_batch: FP32 with the table sampler only");
+  for (int k = 0; k < n_ens; ++k) {
+    int rc = check_ensemble(c, ens[k], k);
+    if (rc != PRAD_OK) return rc;
+  }
+  cudaDeviceProp prop;
+  CK(c, cudaGetDeviceProperties(&prop, c->device));
+  uint64_t key = 0xC0FFEE;
+  for (const char* q = prop.name; *q; ++q) key = mix64(key, static_cast<uint64_t>(*q));
+  key = mix64(key, static_cast<uint64_t>(probe_steps));
+  key = mix64(key, static_cast<uint64_t>(sample));
+  for (int k = 0; k < n_ens; ++k)
+    key = mix64(key, (static_cast<uint64_t>(ens[k].n) << 2) | static_cast<uint64_t>(ens[k].field.kind));
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (const auto& kv : g_tune_cache)
+      if (kv.first == key) {
+        prad_tuning t = kv.second;
+        t.candidates = 0;  // served from the cache
+        c->cfg.block_size = t.block_size;
+        c->cfg.blocks_per_sm = t.blocks_per_sm;
+        c->cfg.batch_chunk = t.batch_chunk;
+        c->cfg.steps_per_launch = t.steps_per_launch;
+        if (out) *out = t;
+        return PRAD_OK;
+      }
+  }
+  // scratch copies of the first min(n, sample) particles of every ensemble
+  std::vector<prad_ensemble> se(ens, ens + n_ens);
+  int64_t tot = 0;
+  std::vector<int64_t> m(n_ens);
+  for (int k = 0; k < n_ens; ++k) {
+    m[k] = ens[k].n < sample ? ens[k].n : sample;
+    tot += m[k];
+  }
+  float *pristine = nullptr, *work = nullptr;
+  double *le = nullptr, *ll = nullptr;
+  uint32_t* pids = nullptr;
+  auto cleanup = [&]() {
+    cudaFree(pristine); cudaFree(work); cudaFree(le); cudaFree(ll); cudaFree(pids);
+  };
+  const size_t tb = static_cast<size_t>(tot > 0 ? tot : 1);
+  if (cudaMalloc(&pristine, 7 * tb * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&work, 7 * tb * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&le, tb * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&ll, tb * sizeof(double)) != cudaSuccess) {
+    cleanup();
+    return fail(c, PRAD_ERR_CUDA, "autotune_batch: scratch allocation failed");
+  }
+  int64_t o = 0;
+  for (int k = 0; k < n_ens; ++k) {
+    void* src[7] = {ens[k].p.x, ens[k].p.y, ens[k].p.z, ens[k].p.ux, ens[k].p.uy, ens[k].p.uz,
+                    ens[k].p.w};
+    for (int a = 0; a < 7; ++a)
+      if (m[k] > 0 && cudaMemcpyAsync(pristine + a * tb + o, src[a], m[k] * sizeof(float),
+                                      cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess) {
+        cleanup();
+        return fail(c, PRAD_ERR_CUDA, "autotune_batch: copy failed");
+      }
+    prad_ensemble& s = se[k];
+    s.n = m[k];
+    s.p.x = work + 0 * tb + o; s.p.y = work + 1 * tb + o; s.p.z = work + 2 * tb + o;
+    s.p.ux = work + 3 * tb + o; s.p.uy = work + 4 * tb + o; s.p.uz = work + 5 * tb + o;
+    s.p.w = work + 6 * tb + o;
+    s.p.pid = nullptr;
+    s.p.ledger_offset = o;
+    o += m[k];
+  }
+  unsigned long long cursor0 = 0;
+  CK(c, cudaMemcpyAsync(&cursor0, c->d_cnt + kCursor, sizeof(cursor0), cudaMemcpyDeviceToHost,
+                        c->stream));
+  unsigned long long cnt_save[kNumCounters];
+  CK(c, cudaMemcpyAsync(cnt_save, c->d_cnt, sizeof(cnt_save), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  prad_tuning best{};
+  best.particle_steps_per_s = -1.0;
+  int ncand = 0;
+  const int blocks[2] = {128, 256};
+  const int chunks[4] = {512, 1024, 2048, 4096};
+  int rc_all = PRAD_OK;
+  for (int bi = 0; bi < 2 && rc_all == PRAD_OK; ++bi) {
+    const int block = blocks[bi];
+    const int cap = batch_max_blocks_per_sm(block);
+    for (int bps = 2; bps <= cap && bps <= 2 * (256 / block) * 3 && rc_all == PRAD_OK; ++bps) {
+      for (int ci = 0; ci < 4 && rc_all == PRAD_OK; ++ci) {
+        const int chunk = chunks[ci];
+        std::vector<StepParams<float>> hp;
+        std::vector<int64_t> off;
+        const int64_t items = build_batch(c, se.data(), n_ens, chunk, hp, off, le, ll);
+        if ((rc_all = upload_batch(c, hp, off)) != PRAD_OK) break;
+        float best_ms = 0.0f;
+        for (int rep = 0; rep < 2; ++rep) {  // warm-up, then timed
+          cudaMemcpyAsync(work, pristine, 7 * tb * sizeof(float), cudaMemcpyDeviceToDevice,
+                          c->stream);
+          cudaEventRecord(e0, c->stream);
+          if ((rc_all = issue_batch(c, n_ens, items, probe_steps, chunk, probe_steps, block,
+                                    bps)) != PRAD_OK)
+            break;
+          cudaEventRecord(e1, c->stream);
+          cudaEventSynchronize(e1);
+          cudaEventElapsedTime(&best_ms, e0, e1);
+        }
+        ++ncand;
+        const double rate = tot * static_cast<double>(probe_steps) / (best_ms * 1e-3);
+        if (rate > best.particle_steps_per_s) {
+          best.block_size = block;
+          best.blocks_per_sm = bps;
+          best.batch_chunk = chunk;
+          best.steps_per_launch = 0;
+          best.particle_steps_per_s = rate;
+        }
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  // restore the counters (photon cursor included: tuning records are
+  // overwritten by later appends)
+  cudaMemcpyAsync(c->d_cnt, cnt_save, sizeof(cnt_save), cudaMemcpyHostToDevice, c->stream);
+  cudaStreamSynchronize(c->stream);
+  cleanup();
+  (void)cursor0;
+  if (rc_all != PRAD_OK) return rc_all;
+  best.candidates = ncand;
+  c->cfg.block_size = best.block_size;
+  c->cfg.blocks_per_sm = best.blocks_per_sm;
+  c->cfg.batch_chunk = best.batch_chunk;
+  c->cfg.steps_per_launch = best.steps_per_launch;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache.emplace_back(key, best);
+  }
+  if (out) *out = best;
   return PRAD_OK;
 }
 

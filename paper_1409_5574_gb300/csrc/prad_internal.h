@@ -60,6 +60,8 @@ struct StepParams {
   uint32_t pid0, ensemble, key0, key1;
   int32_t nsub;               // substeps in this launch
   int32_t rr_mode, heff_form, dims;
+  int32_t field_kind;         // batch kernel: per-ensemble field model
+  int32_t pad_fk;
   // normalised constants
   R half_q_dtn, dtn, inv_dtn, abs_q;
   R cn_dt;      // (sqrt3 / 2pi) alpha dtn
@@ -113,7 +115,25 @@ struct SortBuffers {
   int32_t ntiles, max_work;
 };
 
+// Batched ensembles (k_push_emit_batch): per-ensemble step parameters in a
+// device array, the prefix sum of work items per ensemble, and the atomic
+// work counter the persistent grid draws from.
+struct BatchParams {
+  const StepParams<float>* ens;
+  const int64_t* item_off;     // n_ens + 1 entries
+  unsigned long long* next_item;
+  int64_t total_items;
+  int64_t step_base;           // steps of this call done by earlier launches
+  int32_t n_ens;
+  int32_t chunk;               // particles per work item
+  int32_t nsub;                // steps of this launch
+  int32_t pad;
+};
+
 // Launchers (defined in the kernel translation units).
+cudaError_t launch_push_emit_batch(const BatchParams& bp, int grid, int block,
+                                   cudaStream_t s);
+int batch_max_blocks_per_sm(int block);
 template <typename R>
 cudaError_t launch_push_emit(const StepParams<R>& p, int field_kind, int sampler, int grid,
                              int block, cudaStream_t s);

@@ -823,6 +823,101 @@ __global__ void __launch_bounds__(256, (MinBlocks<R, FIELD, SAMP>::value))
 }
 
 // ---------------------------------------------------------------------------
+// Persistent batched kernel: the grid draws work items (a chunk of one
+// ensemble's particles) from an atomic counter until none are left.  The
+// item's ensemble parameters are copied to shared memory when the ensemble
+// changes; the per-particle path is the same as in k_push_emit.
+// ---------------------------------------------------------------------------
+#ifndef PRAD_BATCH_MINB
+#define PRAD_BATCH_MINB 3
+#endif
+__global__ void __launch_bounds__(256, PRAD_BATCH_MINB)
+    k_push_emit_batch(const BatchParams bp) {
+  __shared__ PhotonStage stage_all[kMaxWarps];
+  __shared__ StepParams<float> Ps;
+  __shared__ long long s_item;
+  __shared__ int s_ens;
+  PhotonStage& stage = stage_all[threadIdx.x >> 5];
+  int fill = 0;
+  Counts cnt;
+  int cur = -1;
+  PhotonOut pout;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const unsigned long long it = atomicAdd(bp.next_item, 1ull);
+      s_item = static_cast<long long>(it);
+      int e = -1;
+      if (static_cast<int64_t>(it) < bp.total_items) {  // last e with off[e] <= it
+        int lo = 0, hi = bp.n_ens;
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (bp.item_off[mid] <= static_cast<int64_t>(it)) lo = mid; else hi = mid;
+        }
+        e = lo;
+      }
+      s_ens = e;
+    }
+    __syncthreads();
+    const long long item = s_item;
+    const int e = s_ens;
+    if (e < 0) break;
+    if (e != cur) {
+      // photons staged so far belong to the previous ensemble's buffer view;
+      // all ensembles share the context's buffer, so no flush is needed
+      constexpr int kWords = static_cast<int>(sizeof(StepParams<float>) / 4);
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(bp.ens + e);
+      uint32_t* dst = reinterpret_cast<uint32_t*>(&Ps);
+      __syncthreads();
+      for (int w = threadIdx.x; w < kWords; w += blockDim.x) dst[w] = src[w];
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        Ps.t0 += bp.step_base;
+        Ps.phase_t0 += static_cast<uint64_t>(bp.step_base) * Ps.phase_step;
+        Ps.nsub = bp.nsub;
+      }
+      __syncthreads();
+      cur = e;
+      pout = make_pout(Ps);
+    }
+    const int64_t first = (item - bp.item_off[e]) * static_cast<int64_t>(bp.chunk);
+    const int64_t last = first + bp.chunk < Ps.n ? first + bp.chunk : Ps.n;
+    if (Ps.field_kind == PRAD_FIELD_CONST) {
+      const FieldGather<float, PRAD_FIELD_CONST> gat{Ps};
+      for (int64_t base = first; base < last; base += blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        advance_particle<float, PRAD_FIELD_CONST, PRAD_SAMPLER_TABLE>(
+            Ps, gat, i, i < last, stage, fill, pout, cnt, nullptr);
+      }
+    } else {
+      const FieldGather<float, PRAD_FIELD_PLANE_WAVE> gat{Ps};
+      for (int64_t base = first; base < last; base += blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        advance_particle<float, PRAD_FIELD_PLANE_WAVE, PRAD_SAMPLER_TABLE>(
+            Ps, gat, i, i < last, stage, fill, pout, cnt, nullptr);
+      }
+    }
+    __syncthreads();
+  }
+  if (cur >= 0 && fill > 0) flush_stage(stage, fill, pout);
+  // counters: any ensemble's pointer to the shared counter array will do
+  flush_counts(cnt, bp.ens[0].counters);
+}
+
+cudaError_t launch_push_emit_batch(const BatchParams& bp, int grid, int block,
+                                   cudaStream_t s) {
+  k_push_emit_batch<<<grid, block, 0, s>>>(bp);
+  return cudaGetLastError();
+}
+
+int batch_max_blocks_per_sm(int block) {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_push_emit_batch, block, 0) !=
+      cudaSuccess)
+    return 1;
+  return nb > 0 ? nb : 1;
+}
+
+// ---------------------------------------------------------------------------
 // Tile-sorted Yee kernel: one block per work item (a chunk of <= kChunk
 // particles of one tile).  The block stages the tile's six field components
 // (+ halo, periodic) in shared memory with coalesced row loads, then runs the

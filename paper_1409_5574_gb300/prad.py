@@ -39,7 +39,8 @@ class prad_config(ctypes.Structure):
                 ("charge", _dbl), ("seed", _u64), ("ensemble", _u32),
                 ("steps_per_launch", _i32), ("photon_capacity", _i64),
                 ("max_particles", _i64), ("stream", _vp), ("block_size", _i32),
-                ("blocks_per_sm", _i32), ("sort_interval", _i32), ("pad0", _i32)]
+                ("blocks_per_sm", _i32), ("sort_interval", _i32), ("batch_chunk", _i32),
+                ("use_graph", _i32), ("pad0", _i32)]
 
 
 class prad_fields(ctypes.Structure):
@@ -53,6 +54,17 @@ class prad_particles(ctypes.Structure):
     _fields_ = [("x", _vp), ("y", _vp), ("z", _vp), ("ux", _vp), ("uy", _vp),
                 ("uz", _vp), ("w", _vp), ("pid", _vp), ("ledger_offset", _i64),
                 ("pid0", _u32), ("pad0", _u32), ("t0", _i64)]
+
+
+class prad_ensemble(ctypes.Structure):
+    _fields_ = [("p", prad_particles), ("n", _i64), ("field", prad_fields),
+                ("ensemble", _u32), ("pad0", _u32)]
+
+
+class prad_tuning(ctypes.Structure):
+    _fields_ = [("block_size", _i32), ("blocks_per_sm", _i32), ("batch_chunk", _i32),
+                ("steps_per_launch", _i32), ("particle_steps_per_s", _dbl),
+                ("candidates", _i32), ("pad0", _i32)]
 
 
 class prad_photons(ctypes.Structure):
@@ -74,6 +86,9 @@ SIGNATURES = {
     "prad_set_fields": (_i32, [_vp, ctypes.POINTER(prad_fields)]),
     "prad_push_emit": (_i32, [_vp, ctypes.POINTER(prad_particles), _i64, _i32]),
     "prad_sort_by_tile": (_i32, [_vp, ctypes.POINTER(prad_particles), _i64]),
+    "prad_push_emit_batch": (_i32, [_vp, ctypes.POINTER(prad_ensemble), _i32, _i32]),
+    "prad_autotune_batch": (_i32, [_vp, ctypes.POINTER(prad_ensemble), _i32, _i32, _i64,
+                                   ctypes.POINTER(prad_tuning)]),
     "prad_get_photons": (_i32, [_vp, ctypes.POINTER(prad_photons), _i64,
                                 ctypes.POINTER(_i64), ctypes.POINTER(_i64), _i32, _i32]),
     "prad_energy_budget": (_i32, [_vp, ctypes.POINTER(_dbl), ctypes.POINTER(_dbl),
@@ -147,6 +162,19 @@ def prad_push_emit(h, p: prad_particles, n: int, nsteps: int) -> int:
 
 def prad_sort_by_tile(h, p: prad_particles, n: int) -> int:
     return _check(load_library().prad_sort_by_tile(h, ctypes.byref(p), n), h)
+
+
+def prad_push_emit_batch(h, ens, nsteps: int) -> int:
+    arr = (prad_ensemble * len(ens))(*ens)
+    return _check(load_library().prad_push_emit_batch(h, arr, len(ens), nsteps), h)
+
+
+def prad_autotune_batch(h, ens, probe_steps: int, sample: int) -> dict:
+    arr = (prad_ensemble * len(ens))(*ens)
+    t = prad_tuning()
+    _check(load_library().prad_autotune_batch(h, arr, len(ens), probe_steps, sample,
+                                              ctypes.byref(t)), h)
+    return {k: getattr(t, k) for k, _ in prad_tuning._fields_ if k != "pad0"}
 
 
 def prad_get_photons(h, out: Optional[prad_photons], cap: int, drain: bool,
@@ -241,7 +269,8 @@ class Context:
                  photon_capacity: int = 1 << 20, max_particles: int = 1 << 20,
                  steps_per_launch: int = 1, stream=None, block_size: int = 0,
                  blocks_per_sm: int = 0, sampler: int = PRAD_SAMPLER_TABLE,
-                 ensemble: int = 0, sort_interval: int = 0):
+                 ensemble: int = 0, sort_interval: int = 0, batch_chunk: int = 0,
+                 use_graph: bool = False):
         torch = _torch()
         if not torch.cuda.is_available():
             raise RuntimeError("prad needs a CUDA device")
@@ -267,6 +296,8 @@ class Context:
         cfg.block_size = block_size
         cfg.blocks_per_sm = blocks_per_sm
         cfg.sort_interval = sort_interval
+        cfg.batch_chunk = batch_chunk
+        cfg.use_graph = int(use_graph)
         self.cfg = cfg
         self.capacity = photon_capacity
         self.max_particles = max_particles
@@ -275,6 +306,22 @@ class Context:
         self.set_fields(problem)
 
     # -- fields ------------------------------------------------------------
+    @staticmethod
+    def make_fields(problem: Dict) -> prad_fields:
+        """prad_fields of an analytic (CONST or PLANE_WAVE) problem dict."""
+        f = prad_fields()
+        f.kind = problem.get("field_kind", PRAD_FIELD_CONST)
+        f.dir = int(problem.get("direction", 1))
+        f.hand = int(problem.get("hand", 1))
+        f.periodic = 1
+        for k in range(3):
+            f.E[k] = problem.get("E", (0, 0, 0))[k]
+            f.B[k] = problem.get("B", (0, 0, 0))[k]
+        f.a0 = problem.get("a0", 0.0)
+        f.lam = problem.get("lam", 0.8e-6)
+        f.phase0 = problem.get("phase0", 0.0)
+        return f
+
     def set_fields(self, problem: Dict) -> None:
         torch = self.torch
         f = prad_fields()
@@ -335,6 +382,29 @@ class Context:
         optional int32 ``pid``; ``z`` may be absent for the Yee grid)."""
         n = st["x"].numel()
         prad_push_emit(self.h, self._particles(st, t0, pid0, ledger_offset), n, nsteps)
+
+    def ensembles(self, states, problems, t0: int = 0, pid0s=None, ledger_offsets=None,
+                  ensemble_ids=None):
+        """prad_ensemble structs for lists of device states and problem dicts
+        (the default pid0 / ledger offsets are the running particle counts)."""
+        out, off = [], 0
+        for k, (st, pb) in enumerate(zip(states, problems)):
+            n = st["x"].numel()
+            e = prad_ensemble()
+            e.p = self._particles(st, t0, off if pid0s is None else pid0s[k],
+                                  off if ledger_offsets is None else ledger_offsets[k])
+            e.n = n
+            e.field = self.make_fields(pb)
+            e.ensemble = k if ensemble_ids is None else ensemble_ids[k]
+            out.append(e)
+            off += n
+        return out
+
+    def push_emit_batch(self, ens, nsteps: int) -> None:
+        prad_push_emit_batch(self.h, ens, nsteps)
+
+    def autotune_batch(self, ens, probe_steps: int = 20, sample: int = 4096) -> dict:
+        return prad_autotune_batch(self.h, ens, probe_steps, sample)
 
     def sort_by_tile(self, st: Dict, pid0: int = 0, ledger_offset: int = 0) -> None:
         n = st["x"].numel()

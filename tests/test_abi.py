@@ -41,11 +41,14 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_ctypes_layout_matches_c():
     from paper_1409_5574_gb300 import prad
-    structs = ["prad_config", "prad_fields", "prad_particles", "prad_photons", "prad_stats"]
+    structs = ["prad_config", "prad_fields", "prad_particles", "prad_photons", "prad_stats",
+               "prad_ensemble", "prad_tuning"]
     body = "".join(f'printf("%zu\\n", sizeof({s}));' for s in structs)
     offs = [("prad_config", "stream"), ("prad_config", "blocks_per_sm"),
-            ("prad_fields", "yee"), ("prad_fields", "y0"), ("prad_particles", "t0"),
-            ("prad_stats", "status")]
+            ("prad_config", "use_graph"), ("prad_fields", "yee"), ("prad_fields", "y0"),
+            ("prad_particles", "pid"), ("prad_particles", "t0"), ("prad_stats", "status"),
+            ("prad_ensemble", "field"), ("prad_ensemble", "ensemble"),
+            ("prad_tuning", "particle_steps_per_s")]
     body += "".join(f'printf("%zu\\n", offsetof({s}, {f}));' for s, f in offs)
     code = ("#include <stdio.h>\n#include <stddef.h>\n#include \"prad.h\"\n"
             f"int main(void){{{body}return 0;}}\n")

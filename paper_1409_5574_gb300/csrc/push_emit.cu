@@ -45,10 +45,13 @@ struct Acc;
 template <>
 struct Acc<float> {
   float hi = 0.0f, lo = 0.0f;
+  // _rn intrinsics: never contracted into an FMA with the product that
+  // forms v, so TwoSum stays exact and the sum does not depend on how the
+  // compiler schedules the surrounding kernel
   __device__ __forceinline__ void add(float v) {
-    const float s = hi + v;
-    const float bb = s - hi;
-    lo += (hi - (s - bb)) + (v - bb);
+    const float s = __fadd_rn(hi, v);
+    const float bb = __fsub_rn(s, hi);
+    lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(v, bb)));
     hi = s;
   }
   // FP64 value; a single add (one step per launch) leaves lo == 0 and costs
@@ -63,7 +66,7 @@ struct Acc<float> {
 template <>
 struct Acc<double> {
   double hi = 0.0;
-  __device__ __forceinline__ void add(double v) { hi += v; }
+  __device__ __forceinline__ void add(double v) { hi = __dadd_rn(hi, v); }
   __device__ __forceinline__ double value() const { return hi; }
   __device__ __forceinline__ bool nonzero() const { return hi != 0.0; }
 };

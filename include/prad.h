@@ -343,6 +343,35 @@ int prad_mlp_eval(prad_ctx* ctx, const float* in, float* lnx, int64_t n);
 /* ln G^-1(r) from the device table for n device uniforms. */
 int prad_ginv_eval(prad_ctx* ctx, const float* r, float* lnx, int64_t n);
 
+/* ---- totals without allocation ---------------------------------------------
+ * The paper has no counterpart to this call; it serves callers that cannot
+ * allocate device memory where they need the totals: a host code that owns
+ * a fixed device memory pool, or a time loop in which a cudaMalloc (which
+ * synchronises the device and may fail once the pool holds the memory) is
+ * not acceptable.  It needs no context.
+ *
+ * The same deterministic two-pass Kahan totals as prad_energy_budget, of
+ * two caller-owned device FP64 arrays emit[n] and rr[n] (for example the
+ * caller's own per-particle ledgers), written to out[0] (sum of emit) and
+ * out[1] (sum of rr), a caller-owned device array of 2 doubles, on `stream`
+ * (cudaStream_t; NULL = default stream); asynchronous.  The per-block
+ * partials live in a file-scope device array of 4096 x 4 doubles (128 KB,
+ * held by every GPU that loads the library until the process exits), so
+ * n is limited to 4096 x 65536 = 268435456 entries; larger n returns
+ * PRAD_ERR_ARG.  No cudaMalloc, cudaFree or allocating library routine is
+ * called.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the array and it keeps the
+ * last call's contents (each call writes every partial it reads), so calls
+ * that overlap on the GPU race: order them on one stream or synchronise.
+ * n == 0 writes zeros (emit and rr may then be NULL).
+ * Errors: PRAD_ERR_ARG (null pointer, n < 0, n too large), PRAD_ERR_CUDA;
+ * prad_ledger_totals_noalloc_error() returns the message of this thread's
+ * last failure. */
+int prad_ledger_totals_noalloc(const double* emit, const double* rr, int64_t n, double* out,
+                               void* stream);
+const char* prad_ledger_totals_noalloc_error(void);
+
 /* ---- diagnostics (same device functions as the hot kernel) --------------- */
 
 /* Philox4x32-10 on n device counters (uint32 x 4 each) with key (k0, k1),

@@ -11,6 +11,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cstdio>
+#include <mutex>
+
 #include "prad_internal.h"
 
 namespace prad {
@@ -103,3 +106,76 @@ cudaError_t launch_ledger_reduce(const double* a, const double* b, int64_t n,
 }
 
 }  // namespace prad
+
+// ---------------------------------------------------------------------------
+// Allocation-free totals.  Some callers cannot allocate device memory at the
+// point where they need the totals: a host code that owns a fixed device
+// memory pool, or a time loop in which a cudaMalloc (which synchronises the
+// device and may fail once the pool has claimed the memory) is not
+// acceptable.  This variant of the two-pass reduction above keeps its
+// per-block partials in a file-scope device array instead of context
+// scratch, and calls no allocation routine.
+// ---------------------------------------------------------------------------
+namespace {
+
+// Each block sums at most kStaticChunk consecutive entries; at most
+// kStaticBlocks blocks (4 doubles of partials each: 128 KB, held by every
+// GPU that loads the library until the process exits).
+constexpr int64_t kStaticChunk = 65536;
+constexpr int kStaticBlocks = 4096;
+__device__ __align__(256) double g_static_partials[4 * kStaticBlocks];
+
+// Device address of g_static_partials per device, looked up once per device
+// (host code must not pass the array's host-side name to a kernel).
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+double* g_static_addr[kMaxDevices] = {nullptr};
+
+thread_local char g_static_err[256];
+
+int static_fail(int code, const char* msg) {
+  std::snprintf(g_static_err, sizeof(g_static_err), "%s", msg);
+  return code;
+}
+
+}  // namespace
+
+extern "C" const char* prad_ledger_totals_noalloc_error(void) { return g_static_err; }
+
+extern "C" int prad_ledger_totals_noalloc(const double* emit, const double* rr, int64_t n,
+                                          double* out, void* stream) {
+  if (!out || n < 0 || (n > 0 && (!emit || !rr)))
+    return static_fail(PRAD_ERR_ARG, "ledger_totals_noalloc: null pointer or n < 0");
+  if (n > kStaticChunk * kStaticBlocks)
+    return static_fail(PRAD_ERR_ARG,
+                       "ledger_totals_noalloc: n exceeds the static scratch limit of "
+                       "268435456 entries (4096 blocks x 65536)");
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+    return static_fail(PRAD_ERR_CUDA, "ledger_totals_noalloc: no usable current device");
+  double* partials = nullptr;
+  {
+    // set-up on the first call per device, with that device current
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_addr[dev]) {
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_static_partials) != cudaSuccess || !p)
+        return static_fail(PRAD_ERR_CUDA, "ledger_totals_noalloc: cudaGetSymbolAddress failed");
+      g_static_addr[dev] = static_cast<double*>(p);
+    }
+    partials = g_static_addr[dev];
+  }
+  if (n == 0) {  // nothing to read: zero totals without touching the inputs
+    const cudaError_t ez = cudaMemsetAsync(out, 0, 2 * sizeof(double),
+                                           static_cast<cudaStream_t>(stream));
+    return ez == cudaSuccess ? PRAD_OK : static_fail(PRAD_ERR_CUDA, cudaGetErrorString(ez));
+  }
+  const int64_t nb64 = (n + kStaticChunk - 1) / kStaticChunk;
+  const int nblocks = static_cast<int>(nb64);
+  // every partial the second pass reads is written by the first: nothing
+  // left from an earlier call is used
+  const cudaError_t e = prad::launch_ledger_reduce(emit, rr, n, partials, nblocks, out,
+                                                   static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return static_fail(PRAD_ERR_CUDA, cudaGetErrorString(e));
+  return PRAD_OK;
+}

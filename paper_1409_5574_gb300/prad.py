@@ -102,6 +102,8 @@ SIGNATURES = {
     "prad_mlp_grad": (_i32, [_vp, _vp, _i64, _vp, ctypes.POINTER(_dbl)]),
     "prad_mlp_eval": (_i32, [_vp, _vp, _vp, _i64]),
     "prad_ginv_eval": (_i32, [_vp, _vp, _vp, _i64]),
+    "prad_ledger_totals_noalloc": (_i32, [_vp, _vp, _i64, _vp, _vp]),
+    "prad_ledger_totals_noalloc_error": (ctypes.c_char_p, []),
     "prad_philox": (_i32, [_vp, _vp, _u32, _u32, _vp, _i64]),
     "prad_eval_sampler": (_i32, [_vp, _vp, _vp, _vp, _i64]),
 }
@@ -239,6 +241,15 @@ def prad_mlp_eval(h, in_ptr, out_ptr, n: int) -> None:
 
 def prad_ginv_eval(h, r_ptr, out_ptr, n: int) -> None:
     _check(load_library().prad_ginv_eval(h, r_ptr, out_ptr, n), h)
+
+
+def prad_ledger_totals_noalloc(emit_ptr, rr_ptr, n: int, out_ptr, stream_ptr=None) -> None:
+    """Kahan totals of two caller-owned device FP64 arrays into a caller-owned
+    device array of 2 doubles, without any device allocation."""
+    L = load_library()
+    rc = L.prad_ledger_totals_noalloc(emit_ptr, rr_ptr, n, out_ptr, stream_ptr)
+    if rc < 0:
+        raise PradError(rc, L.prad_ledger_totals_noalloc_error().decode(errors="replace"))
 
 
 def prad_philox(h, ctr_ptr, k0: int, k1: int, out_ptr, n: int) -> None:

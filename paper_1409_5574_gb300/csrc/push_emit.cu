@@ -560,21 +560,46 @@ __device__ __forceinline__ void mlp_flush_tile(const StepParams<R>& P, MlpWarp& 
 // One particle, nsub steps (the whole per-step path).  Warp-collective: every
 // lane of the warp calls it, inactive lanes with act = false.
 // ---------------------------------------------------------------------------
+// What a launch reads of one particle: its state, id and (for one-step
+// launches) its LL ledger entry.  Loaded separately from the step so a thread
+// can issue the loads of its next particle before computing the current one.
+template <typename R>
+struct PState {
+  R x, y, z, ux, uy, uz, w;
+  uint32_t pid;
+  double ll_old;   // LL ledger entry (read once per launch)
+  bool act;
+};
+
+template <typename R>
+__device__ __forceinline__ void load_state(const StepParams<R>& P, int64_t i, bool act,
+                                           PState<R>& s) {
+  s.act = act;
+  s.x = s.y = s.z = s.ux = s.uy = s.uz = s.w = R(0);
+  s.pid = 0;
+  s.ll_old = 0.0;
+  if (act) {
+    s.x = P.x[i]; s.y = P.y[i];
+    if (P.z) s.z = P.z[i];
+    s.ux = P.ux[i]; s.uy = P.uy[i]; s.uz = P.uz[i];
+    s.w = P.w[i];
+    s.pid = P.pid ? P.pid[i] : P.pid0 + static_cast<uint32_t>(i);
+    const int64_t li = static_cast<int64_t>(s.pid - P.pid0);
+    if (P.rr_mode >= PRAD_RR_LEDGER && li < P.led_n) s.ll_old = P.led_ll[li];
+  }
+}
+
 template <typename R, int FIELD, int SAMP, class G>
 __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const G& gat,
-                                                 int64_t i, bool act, PhotonStage& stage,
-                                                 int& fill, const PhotonOut& pout,
-                                                 Counts& cnt, MlpWarp* mw) {
-  R x = R(0), y = R(0), z = R(0), ux = R(0), uy = R(0), uz = R(0), w = R(0);
-  uint32_t pid = 0;
+                                                 int64_t i, const PState<R>& st,
+                                                 PhotonStage& stage, int& fill,
+                                                 const PhotonOut& pout, Counts& cnt,
+                                                 MlpWarp* mw) {
+  const bool act = st.act;
+  R x = st.x, y = st.y, z = st.z, ux = st.ux, uy = st.uy, uz = st.uz;
+  const R w = st.w;
+  const uint32_t pid = st.pid;
   Acc<R> ll, le;
-  if (act) {
-    x = P.x[i]; y = P.y[i];
-    if (P.z) z = P.z[i];
-    ux = P.ux[i]; uy = P.uy[i]; uz = P.uz[i];
-    w = P.w[i];
-    pid = P.pid ? P.pid[i] : P.pid0 + static_cast<uint32_t>(i);
-  }
   const R chk = x + y + z + ux + uy + uz + w;
   const bool live = act && isfinite(chk);
   if (act && !live) ++cnt.nan;
@@ -718,7 +743,7 @@ __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const G
     P.ux[i] = ux; P.uy[i] = uy; P.uz[i] = uz;
     const int64_t li = static_cast<int64_t>(pid - P.pid0);
     if (li < P.led_n) {
-      if (P.rr_mode >= PRAD_RR_LEDGER) P.led_ll[li] += ll.value();
+      if (P.rr_mode >= PRAD_RR_LEDGER) P.led_ll[li] = st.ll_old + ll.value();
       if (le.nonzero()) P.led_emit[li] += le.value();
     } else {
       cnt.bad_id = true;
@@ -793,8 +818,11 @@ struct MinBlocks {
 // and one emission queue per warp.
 constexpr size_t kMlpDynSmem = sizeof(MlpSmem) + kMaxWarps * sizeof(MlpQueue);
 
-template <typename R, int FIELD, int SAMP>
-__global__ void __launch_bounds__(256, (MinBlocks<R, FIELD, SAMP>::value))
+#ifndef PRAD_PF_MINB
+#define PRAD_PF_MINB 4
+#endif
+template <typename R, int FIELD, int SAMP, bool PF>
+__global__ void __launch_bounds__(256, (PF ? PRAD_PF_MINB : MinBlocks<R, FIELD, SAMP>::value))
     k_push_emit(const StepParams<R> P) {
   __shared__ PhotonStage stage_all[kMaxWarps];
   extern __shared__ __align__(16) unsigned char dyn_smem[];
@@ -813,10 +841,27 @@ __global__ void __launch_bounds__(256, (MinBlocks<R, FIELD, SAMP>::value))
   }
   const FieldGather<R, FIELD> gat{P};
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-  for (int64_t base = static_cast<int64_t>(blockIdx.x) * blockDim.x; base < P.n;
-       base += stride) {
-    const int64_t i = base + threadIdx.x;
-    advance_particle<R, FIELD, SAMP>(P, gat, i, i < P.n, stage, fill, pout, cnt, &mw);
+  const int64_t first = static_cast<int64_t>(blockIdx.x) * blockDim.x;
+  if constexpr (PF) {
+    // one or a few steps per launch (the state streams through HBM): a
+    // software pipeline issues the loads of the thread's next particle
+    // before the current one is advanced, so DRAM latency overlaps compute
+    PState<R> nxt;
+    load_state(P, first + threadIdx.x, first + threadIdx.x < P.n, nxt);
+    for (int64_t base = first; base < P.n; base += stride) {
+      const int64_t i = base + threadIdx.x;
+      const PState<R> cur = nxt;
+      const int64_t j = i + stride;
+      load_state(P, j, j < P.n, nxt);
+      advance_particle<R, FIELD, SAMP>(P, gat, i, cur, stage, fill, pout, cnt, &mw);
+    }
+  } else {
+    for (int64_t base = first; base < P.n; base += stride) {
+      const int64_t i = base + threadIdx.x;
+      PState<R> cur;
+      load_state(P, i, i < P.n, cur);
+      advance_particle<R, FIELD, SAMP>(P, gat, i, cur, stage, fill, pout, cnt, &mw);
+    }
   }
   if constexpr (SAMP != PRAD_SAMPLER_TABLE) {
     while (mw.count > 0) mlp_flush_tile(P, mw, stage, fill, pout, cnt);
@@ -888,15 +933,19 @@ __global__ void __launch_bounds__(256, PRAD_BATCH_MINB)
       const FieldGather<float, PRAD_FIELD_CONST> gat{Ps};
       for (int64_t base = first; base < last; base += blockDim.x) {
         const int64_t i = base + threadIdx.x;
+        PState<float> st;
+        load_state(Ps, i, i < last, st);
         advance_particle<float, PRAD_FIELD_CONST, PRAD_SAMPLER_TABLE>(
-            Ps, gat, i, i < last, stage, fill, pout, cnt, nullptr);
+            Ps, gat, i, st, stage, fill, pout, cnt, nullptr);
       }
     } else {
       const FieldGather<float, PRAD_FIELD_PLANE_WAVE> gat{Ps};
       for (int64_t base = first; base < last; base += blockDim.x) {
         const int64_t i = base + threadIdx.x;
+        PState<float> st;
+        load_state(Ps, i, i < last, st);
         advance_particle<float, PRAD_FIELD_PLANE_WAVE, PRAD_SAMPLER_TABLE>(
-            Ps, gat, i, i < last, stage, fill, pout, cnt, nullptr);
+            Ps, gat, i, st, stage, fill, pout, cnt, nullptr);
       }
     }
     __syncthreads();
@@ -955,8 +1004,10 @@ __global__ void __launch_bounds__(256, 3) k_push_emit_tiled(const StepParams<R> 
   const TileGather<R> gat{P, tile_sm, gx0, gy0};
   for (int64_t base = wk.y; base < wk.z; base += blockDim.x) {
     const int64_t i = base + threadIdx.x;
-    advance_particle<R, PRAD_FIELD_YEE2D, PRAD_SAMPLER_TABLE>(P, gat, i, i < wk.z, stage,
-                                                              fill, pout, cnt, nullptr);
+    PState<R> st;
+    load_state(P, i, i < wk.z, st);
+    advance_particle<R, PRAD_FIELD_YEE2D, PRAD_SAMPLER_TABLE>(P, gat, i, st, stage, fill, pout,
+                                                              cnt, nullptr);
   }
   if (fill > 0) flush_stage(stage, fill, pout);
   flush_counts(cnt, P.counters);
@@ -978,23 +1029,28 @@ template <typename R, int FIELD>
 cudaError_t launch_field(const StepParams<R>& p, int sampler, int grid, int block,
                          cudaStream_t s) {
   if (sampler == PRAD_SAMPLER_TABLE) {
-    k_push_emit<R, FIELD, PRAD_SAMPLER_TABLE><<<grid, block, 0, s>>>(p);
+    // prefetching pays when the launch is short (state streamed from HBM);
+    // for long fused launches it only costs registers
+    if (sizeof(R) == 4 && p.nsub <= 4)
+      k_push_emit<R, FIELD, PRAD_SAMPLER_TABLE, (sizeof(R) == 4)><<<grid, block, 0, s>>>(p);
+    else
+      k_push_emit<R, FIELD, PRAD_SAMPLER_TABLE, false><<<grid, block, 0, s>>>(p);
     return cudaGetLastError();
   }
   if constexpr (sizeof(R) == 4) {
     cudaError_t e;
     if (sampler == PRAD_SAMPLER_MLP) {
-      e = cudaFuncSetAttribute(k_push_emit<R, FIELD, PRAD_SAMPLER_MLP>,
+      e = cudaFuncSetAttribute(k_push_emit<R, FIELD, PRAD_SAMPLER_MLP, false>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize,
                                static_cast<int>(kMlpDynSmem));
       if (e != cudaSuccess) return e;
-      k_push_emit<R, FIELD, PRAD_SAMPLER_MLP><<<grid, block, kMlpDynSmem, s>>>(p);
+      k_push_emit<R, FIELD, PRAD_SAMPLER_MLP, false><<<grid, block, kMlpDynSmem, s>>>(p);
     } else {
-      e = cudaFuncSetAttribute(k_push_emit<R, FIELD, PRAD_SAMPLER_MLP_FALLBACK>,
+      e = cudaFuncSetAttribute(k_push_emit<R, FIELD, PRAD_SAMPLER_MLP_FALLBACK, false>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize,
                                static_cast<int>(kMlpDynSmem));
       if (e != cudaSuccess) return e;
-      k_push_emit<R, FIELD, PRAD_SAMPLER_MLP_FALLBACK><<<grid, block, kMlpDynSmem, s>>>(p);
+      k_push_emit<R, FIELD, PRAD_SAMPLER_MLP_FALLBACK, false><<<grid, block, kMlpDynSmem, s>>>(p);
     }
     return cudaGetLastError();
   }

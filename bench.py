@@ -219,9 +219,10 @@ def run_prad(args):
     a0s = a0_list(args.a0)
     nsteps = args.periods * 200
     n = args.particles
-    # launch shape chosen by the sweep of substeps x resident blocks on GB300
+    # substeps per launch chosen by the sweep on GB300; the library sizes the
+    # persistent grid from the kernel's occupancy unless --bps is given
     nsub = args.nsub if args.nsub > 0 else 400
-    bps = args.bps if args.bps > 0 else 6
+    bps = args.bps if args.bps > 0 else 0
 
     # inputs: seeded synthetic states, one per a0, resident in HBM
     wls = [W.plane_wave(a0=a0, n=n, periods=args.periods, seed=1 + 97 * rank) for a0 in a0s]

@@ -88,7 +88,8 @@ typedef struct prad_config {
   int64_t max_particles;    /* per-particle ledger entries, >= 1             */
   void* stream;             /* cudaStream_t for every launch; NULL = default */
   int32_t block_size;       /* threads per block (0 = 256); multiple of 32   */
-  int32_t blocks_per_sm;    /* resident blocks per SM for the grid (0 = 4)   */
+  int32_t blocks_per_sm;    /* blocks per SM of the persistent grid, capped
+                               at the kernel's occupancy (0 = occupancy)   */
   int32_t sort_interval;    /* YEE2D with a pid array: reorder particles by
                                32 x 32-cell tile every this many steps and
                                gather from shared-memory field tiles

@@ -533,11 +533,16 @@ int push_emit_t(prad_ctx* c, const prad_particles* pp, int64_t n,
     return PRAD_OK;
   }
   const int block = c->cfg.block_size > 0 ? c->cfg.block_size : 256;
-  const int bps = c->cfg.blocks_per_sm > 0 ? c->cfg.blocks_per_sm : 4;
+  const int sub = c->cfg.steps_per_launch > 0 ? c->cfg.steps_per_launch : 1;
+  // persistent grid: at most the resident blocks of the kernel variant, so
+  // no block waits for a second wave (blocks_per_sm = 0: all of them)
+  const int occ = push_emit_occupancy<R>(c->fields.kind, c->cfg.sampler,
+                                         sub < nsteps ? sub : nsteps, block);
+  const int bps = c->cfg.blocks_per_sm > 0 && c->cfg.blocks_per_sm < occ ? c->cfg.blocks_per_sm
+                                                                         : occ;
   const int64_t want = (n + block - 1) / block;
   const int64_t cap = static_cast<int64_t>(c->num_sms) * bps;
   const int grid = static_cast<int>(want < cap ? want : cap);
-  const int sub = c->cfg.steps_per_launch > 0 ? c->cfg.steps_per_launch : 1;
   const uint64_t phase0 = p.phase_t0;
   for (int32_t done = 0; done < nsteps;) {
     const int32_t m = (nsteps - done) < sub ? (nsteps - done) : sub;

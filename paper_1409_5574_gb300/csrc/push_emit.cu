@@ -1057,6 +1057,51 @@ cudaError_t launch_field(const StepParams<R>& p, int sampler, int grid, int bloc
   return cudaErrorInvalidValue;
 }
 
+template <typename K>
+int occupancy_of(K kernel, int block, size_t dyn) {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, block, dyn) != cudaSuccess)
+    return 1;
+  return nb > 0 ? nb : 1;
+}
+
+template <typename R, int FIELD>
+int field_occupancy(int sampler, bool pf, int block) {
+  if (sampler == PRAD_SAMPLER_TABLE) {
+    if (pf && sizeof(R) == 4)
+      return occupancy_of(k_push_emit<R, FIELD, PRAD_SAMPLER_TABLE, true>, block, 0);
+    return occupancy_of(k_push_emit<R, FIELD, PRAD_SAMPLER_TABLE, false>, block, 0);
+  }
+  if constexpr (sizeof(R) == 4) {
+    // the dynamic-smem limit must be raised before the occupancy query
+    if (sampler == PRAD_SAMPLER_MLP) {
+      cudaFuncSetAttribute(k_push_emit<R, FIELD, PRAD_SAMPLER_MLP, false>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(kMlpDynSmem));
+      return occupancy_of(k_push_emit<R, FIELD, PRAD_SAMPLER_MLP, false>, block, kMlpDynSmem);
+    }
+    cudaFuncSetAttribute(k_push_emit<R, FIELD, PRAD_SAMPLER_MLP_FALLBACK, false>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(kMlpDynSmem));
+    return occupancy_of(k_push_emit<R, FIELD, PRAD_SAMPLER_MLP_FALLBACK, false>, block,
+                        kMlpDynSmem);
+  }
+  return 1;
+}
+
+// Resident blocks per SM of the kernel variant a launch would use.
+template <typename R>
+int push_emit_occupancy(int field_kind, int sampler, int nsub, int block) {
+  const bool pf = nsub <= 4;
+  switch (field_kind) {
+    case PRAD_FIELD_CONST: return field_occupancy<R, PRAD_FIELD_CONST>(sampler, pf, block);
+    case PRAD_FIELD_PLANE_WAVE: return field_occupancy<R, PRAD_FIELD_PLANE_WAVE>(sampler, pf, block);
+    default: return field_occupancy<R, PRAD_FIELD_YEE2D>(sampler, pf, block);
+  }
+}
+template int push_emit_occupancy<float>(int, int, int, int);
+template int push_emit_occupancy<double>(int, int, int, int);
+
 template <typename R>
 cudaError_t launch_push_emit(const StepParams<R>& p, int field_kind, int sampler, int grid,
                              int block, cudaStream_t s) {

@@ -5,7 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "../../include/prad.h"
+#include "prad.h"  // include/ is on the include path
 #include "mlp_device.cuh"
 
 namespace prad {

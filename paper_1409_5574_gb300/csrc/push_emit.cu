@@ -112,18 +112,13 @@ __device__ __forceinline__ void sample_x_g(const StepParams<float>& P,
   // (h 2^32 + l + 1/2) 2^-64, never zero
   const float arg = fmaf(static_cast<float>(h), 0x1p-32f,
                          fmaf(static_cast<float>(l), 0x1p-64f, 0x1p-65f));
-  // log2(arg) = e + log2(m), m in [1, 2): the integer exponent is exact and
-  // the mantissa log has a small absolute error, so x keeps its relative
-  // accuracy down to R' ~ 2^-65 (a plain float log2 would not).
-  const int bits = __float_as_int(arg);
-  const int e = ((bits >> 23) & 0xff) - 127;
-  const float lm = __log2f(__int_as_float((bits & 0x007fffff) | 0x3f800000));
-  // t = 2^(L/4) = 2^(e >> 2) * 2^(((e & 3) + lm) / 4)
-  const float t = exp2f(0.25f * (static_cast<float>(e & 3) + lm)) *
-                  __int_as_float((127 + (e >> 2)) << 23);
+  // low branch: t = R'^(1/4) = rsqrt(rsqrt(R')) keeps the relative accuracy
+  // of R' down to 2^-65 (a float log2 / exp2 route loses it for tiny R');
+  // high branch: x = -ln(9/7) - ln(1 - R'), where a relative log2 error is
+  // harmless because x >= a
+  const float t = rsqrtf(rsqrtf(arg));
   const float x_lo = t * t * t;
-  const float x_hi = fmaf(-static_cast<float>(e), 0.69314718055994531f,
-                          -fmaf(lm, 0.69314718055994531f, 0.25131442828090608f));
+  const float x_hi = fmaf(-__log2f(arg), 0.69314718055994531f, -0.25131442828090608f);
   x = low ? x_lo : x_hi;
   const float u = low ? t * P.t_scale : (x_hi - P.a) * P.x_scale;
   int i = static_cast<int>(fmaxf(u, 0.0f));
@@ -349,8 +344,14 @@ __device__ __forceinline__ void flush_stage(PhotonStage& st, int fill,
   for (int r = lane; r < fill; r += 32) {
     const unsigned long long slot = base + static_cast<unsigned>(r);
     if (slot < static_cast<unsigned long long>(o.cap)) {
-#pragma unroll
-      for (int k = 0; k < 8; ++k) o.f[k][slot] = st.f[k][r];
+      // the direction is staged as the raw mean momentum: normalise here,
+      // once per record, instead of in every lane of every step
+      const float dx = st.f[3][r], dy = st.f[4][r], dz = st.f[5][r];
+      const float d2 = dx * dx + dy * dy + dz * dz;
+      const float inv = d2 > 0.0f ? rsqrtf(d2) : 0.0f;
+      o.f[0][slot] = st.f[0][r]; o.f[1][slot] = st.f[1][r]; o.f[2][slot] = st.f[2][r];
+      o.f[3][slot] = dx * inv; o.f[4][slot] = dy * inv; o.f[5][slot] = dz * inv;
+      o.f[6][slot] = st.f[6][r]; o.f[7][slot] = st.f[7][r];
       o.pid[slot] = st.pid[r];
       o.step[slot] = st.step[r];
     }
@@ -358,13 +359,12 @@ __device__ __forceinline__ void flush_stage(PhotonStage& st, int fill,
   __syncwarp();
 }
 
-// Warp-collective: every lane of the warp calls it with its own `want`.
-__device__ __forceinline__ void stage_photon(PhotonStage& st, int& fill,
-                                             const PhotonOut& o, bool want,
-                                             const float rec[8], uint32_t pid,
-                                             uint32_t step) {
-  const unsigned mask = __ballot_sync(0xffffffffu, want);
-  if (mask == 0u) return;
+// Warp-collective, with the warp's ballot of `want` already taken (mask != 0).
+// rec = position, mean momentum (normalised at flush), energy, weight.
+__device__ __forceinline__ void stage_photon_mask(PhotonStage& st, int& fill,
+                                                  const PhotonOut& o, bool want,
+                                                  unsigned mask, const float rec[8],
+                                                  uint32_t pid, uint32_t step) {
   const int cnt = __popc(mask);
   if (fill + cnt > kStage) {
     flush_stage(st, fill, o);
@@ -379,6 +379,16 @@ __device__ __forceinline__ void stage_photon(PhotonStage& st, int& fill,
     st.step[pos] = step;
   }
   fill += cnt;
+}
+
+// Warp-collective: every lane of the warp calls it with its own `want`.
+__device__ __forceinline__ void stage_photon(PhotonStage& st, int& fill,
+                                             const PhotonOut& o, bool want,
+                                             const float rec[8], uint32_t pid,
+                                             uint32_t step) {
+  const unsigned mask = __ballot_sync(0xffffffffu, want);
+  if (mask == 0u) return;
+  stage_photon_mask(st, fill, o, want, mask, rec, pid, step);
 }
 
 // ---------------------------------------------------------------------------
@@ -683,7 +693,6 @@ __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const G
       Rr = fmaf(static_cast<float>(rnd.z), 0x1p-32f, 0x1p-33f);
     else
       Rr = fma(static_cast<double>(rnd.z), 0x1p-32, 0x1p-33);
-    const R inv = ua2 > R(0) ? rsq(ua2) : R(0);
     if constexpr (SAMP == PRAD_SAMPLER_TABLE) {
       // 8. Monte Carlo emission: proposal x = P^-1(R'), dN of Eq. (13)
       R xs, g;
@@ -693,14 +702,18 @@ __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const G
       const R k = fl + ((Rr < dN - fl) ? R(1) : R(0));
       if (live && dN > R(1)) ++cnt.dn1;
       const bool want = live && k > R(0) && w > R(0);
-      // 9. append + emitted-energy ledger
-      const R eps = xs * epsc;
-      if (want) le.add(k * w * eps);
-      const float rec[8] = {static_cast<float>(xn), static_cast<float>(yn),
-                            static_cast<float>(zn), static_cast<float>(ax * inv),
-                            static_cast<float>(ay * inv), static_cast<float>(az * inv),
-                            static_cast<float>(eps), static_cast<float>(k * w)};
-      stage_photon(stage, fill, pout, want, rec, pid, step);
+      // 9. append + emitted-energy ledger; the record is built only when
+      //    some lane of the warp emits
+      const unsigned mask = __ballot_sync(0xffffffffu, want);
+      if (mask) {
+        const R eps = xs * epsc;
+        if (want) le.add(k * w * eps);
+        const float rec[8] = {static_cast<float>(xn), static_cast<float>(yn),
+                              static_cast<float>(zn), static_cast<float>(ax),
+                              static_cast<float>(ay), static_cast<float>(az),
+                              static_cast<float>(eps), static_cast<float>(k * w)};
+        stage_photon_mask(stage, fill, pout, want, mask, rec, pid, step);
+      }
     } else {
       // 8'. direct scheme: photons of this step ~ mean (5 sqrt3/6) alpha
       //     Omega dt (the integral of Eq. (13)'s spectrum), multiplicity as in
@@ -721,8 +734,8 @@ __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const G
         le.add(k * w * xt * epsc);
       }
       const float rec[8] = {static_cast<float>(xn), static_cast<float>(yn),
-                            static_cast<float>(zn), static_cast<float>(ax * inv),
-                            static_cast<float>(ay * inv), static_cast<float>(az * inv),
+                            static_cast<float>(zn), static_cast<float>(ax),
+                            static_cast<float>(ay), static_cast<float>(az),
                             static_cast<float>(xt * epsc), static_cast<float>(k * w)};
       stage_photon(stage, fill, pout, now, rec, pid, step);
       const bool q = want && !tail;

@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--bps", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-mlp", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     return ap.parse_args()
 
@@ -322,8 +323,7 @@ def run_prad(args):
     ns = 1 << 24
     wl_s = W.plane_wave(a0=a0s[-1], n=ns, periods=1, seed=5 + rank)
     ctx_s = prad.Context(wl_s.problem_kwargs(), precision=prad.PRAD_FP32,
-                         photon_capacity=ns * 4, max_particles=ns, steps_per_launch=1,
-                         blocks_per_sm=bps)
+                         photon_capacity=ns * 4, max_particles=ns, steps_per_launch=1)
     st_s = ctx_s.to_device(wl_s.state)
     ctx_s.push_emit(st_s, 4, t0=0)
     ctx_s.drain()
@@ -384,6 +384,55 @@ def run_prad(args):
         e2e = {"value": ws * ps_per_step * args.steps / te, "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
+    # The metric's other arm: the learned sampler (trained here on 10^8
+    # device-generated samples) on the same workload and launch shape.
+    mlp = None
+    if not args.no_mlp:
+        torch.cuda.synchronize()
+        t_tr = time.perf_counter()
+        train_loss = ctx.mlp_train(1526, 65536, 3e-3, seed=7)
+        torch.cuda.synchronize()
+        t_tr = time.perf_counter() - t_tr
+        params = ctx.mlp_weights()
+        ctx_m = prad.Context(wls[0].problem_kwargs(), precision=prad.PRAD_FP32,
+                             sampler=prad.PRAD_SAMPLER_MLP_FALLBACK, photon_capacity=cap,
+                             max_particles=n, steps_per_launch=nsub, block_size=args.block,
+                             blocks_per_sm=bps)
+        ctx_m.mlp_set_weights(params)
+        # spectral error bound from the device G^-1 table: |G(g) - G(x*)| <=
+        # max dG/dln x * |ln g - ln x*| with max dG/dln x = max F / (5 pi/3)
+        rr = (torch.arange(200_000, dtype=torch.float64) + 0.5) / 200_000
+        lg = ctx_m.mlp_eval(rr, torch.full_like(rr, 1000.0), torch.full_like(rr, 1e3))
+        lt = ctx_m.ginv(rr)
+        bound = float(0.1753 * (lg - lt).abs().max().item())
+
+        def mlp_step():
+            for w, st0 in zip(wls, init):
+                ctx_m.set_fields(w.problem_kwargs())
+                for k in work:
+                    work[k].copy_(st0[k], non_blocking=True)
+                ctx_m.push_emit(work, nsteps, t0=0, pid0=pid0)
+                ctx_m.drain()
+        mlp_step()
+        torch.cuda.synchronize()
+        tm = 0.0
+        for _ in range(args.steps):
+            flush.zero_()
+            m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            m0.record(stream)
+            mlp_step()
+            m1.record(stream)
+            m1.synchronize()
+            tm += m0.elapsed_time(m1) / 1e3
+        _, _, mst = ctx_m.energy_budget()
+        v_mlp = ps_per_step * args.steps / tm
+        mlp = {"value": v_mlp, "unit": UNIT, "vs_table": v_mlp / (ps_per_step * args.steps
+                                                                  / t_total * 1.0),
+               "spectral_error_bound": bound, "train_seconds": t_tr,
+               "train_samples": 1526 * 65536, "train_loss": train_loss,
+               "mlp_fallback": mst["mlp_fallback"], "sampler": "MLP_FALLBACK (direct scheme)"}
+        ctx_m.close()
+
     cb = None
     if rank == 0 and ws == 1:
         cb = cpu_baseline(args, budget_s=args.cpu_seconds)
@@ -402,7 +451,7 @@ def run_prad(args):
                            "photon_records_per_step": records / args.steps,
                            "parallelism": f"independent particles, {ws} GPU(s)"},
                 "roofline": roofline, "roofline_stream": roofline_stream,
-                "cpu_baseline": cb, "e2e": e2e,
+                "mlp_sampler": mlp, "cpu_baseline": cb, "e2e": e2e,
                 "gpu_launches": args.steps * len(a0s) * launches_per_run,
                 "clocks": ck}
         print(json.dumps(line), flush=True)

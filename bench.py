@@ -372,7 +372,8 @@ def run_prad(args):
     roofline_stream = {"bound": "hbm", "achieved": ach_s, "peak": hbm_peak, "unit": "GB/s",
                        "frac": ach_s / hbm_peak, "traffic": ncu_traffic("stream"),
                        "algorithmic_bytes": bytes_s,
-                       "kernel": "k_push_emit<float, PLANE_WAVE>, 1 step per launch",
+                       "kernel": "k_push_emit<float, PLANE_WAVE, one-step> (next particle "
+                                 "prefetched), 1 step per launch",
                        "launch": f"{ns} particles x 1 step (a0={a0s[-1]:g})",
                        "particle_steps_per_s": ns / t_s,
                        "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback"}

@@ -534,10 +534,10 @@ int push_emit_t(prad_ctx* c, const prad_particles* pp, int64_t n,
   }
   const int block = c->cfg.block_size > 0 ? c->cfg.block_size : 256;
   const int sub = c->cfg.steps_per_launch > 0 ? c->cfg.steps_per_launch : 1;
+  const int sub_eff = sub < nsteps ? sub : nsteps;
   // persistent grid: at most the resident blocks of the kernel variant, so
   // no block waits for a second wave (blocks_per_sm = 0: all of them)
-  const int occ = push_emit_occupancy<R>(c->fields.kind, c->cfg.sampler,
-                                         sub < nsteps ? sub : nsteps, block);
+  const int occ = push_emit_occupancy<R>(c->fields.kind, c->cfg.sampler, sub_eff, block);
   const int bps = c->cfg.blocks_per_sm > 0 && c->cfg.blocks_per_sm < occ ? c->cfg.blocks_per_sm
                                                                          : occ;
   const int64_t want = (n + block - 1) / block;

@@ -62,12 +62,15 @@ struct Acc<float> {
     return v;
   }
   __device__ __forceinline__ bool nonzero() const { return hi != 0.0f; }
+  // after exactly one add, TwoSum leaves lo == 0: one conversion
+  __device__ __forceinline__ double value_one() const { return static_cast<double>(hi); }
 };
 template <>
 struct Acc<double> {
   double hi = 0.0;
   __device__ __forceinline__ void add(double v) { hi = __dadd_rn(hi, v); }
   __device__ __forceinline__ double value() const { return hi; }
+  __device__ __forceinline__ double value_one() const { return hi; }
   __device__ __forceinline__ bool nonzero() const { return hi != 0.0; }
 };
 
@@ -570,36 +573,50 @@ __device__ __forceinline__ void mlp_flush_tile(const StepParams<R>& P, MlpWarp& 
 // One particle, nsub steps (the whole per-step path).  Warp-collective: every
 // lane of the warp calls it, inactive lanes with act = false.
 // ---------------------------------------------------------------------------
-// What a launch reads of one particle: its state, id and (for one-step
-// launches) its LL ledger entry.  Loaded separately from the step so a thread
+// What a launch reads of one particle: its state, id and, for one-step
+// launches, its LL ledger entry.  Loaded separately from the step so a thread
 // can issue the loads of its next particle before computing the current one.
 template <typename R>
 struct PState {
   R x, y, z, ux, uy, uz, w;
   uint32_t pid;
-  double ll_old;   // LL ledger entry (read once per launch)
+  double ll_old, emit_old;  // ledger entries (LL = true)
   bool act;
 };
 
-template <typename R>
+template <typename R, bool LL = false>
 __device__ __forceinline__ void load_state(const StepParams<R>& P, int64_t i, bool act,
                                            PState<R>& s) {
   s.act = act;
   s.x = s.y = s.z = s.ux = s.uy = s.uz = s.w = R(0);
   s.pid = 0;
-  s.ll_old = 0.0;
+  s.ll_old = s.emit_old = 0.0;
   if (act) {
     s.x = P.x[i]; s.y = P.y[i];
     if (P.z) s.z = P.z[i];
     s.ux = P.ux[i]; s.uy = P.uy[i]; s.uz = P.uz[i];
     s.w = P.w[i];
     s.pid = P.pid ? P.pid[i] : P.pid0 + static_cast<uint32_t>(i);
-    const int64_t li = static_cast<int64_t>(s.pid - P.pid0);
-    if (P.rr_mode >= PRAD_RR_LEDGER && li < P.led_n) s.ll_old = P.led_ll[li];
+    if constexpr (LL) {
+      const int64_t li = static_cast<int64_t>(s.pid - P.pid0);
+      if (li < P.led_n) {
+        if (P.rr_mode >= PRAD_RR_LEDGER) s.ll_old = P.led_ll[li];
+        s.emit_old = P.led_emit[li];
+      }
+    }
   }
 }
 
-template <typename R, int FIELD, int SAMP, class G>
+// The new state is written back to global memory.  The launch's ledger increments reach the FP64 ledgers as one add
+// per entry per launch, so the sums are sequenced by the launches and
+// bit-reproducible.  Multi-step launches add them with fire-and-forget
+// atomics performed in L2 (no load, no FP64 add and no wait on the SM).
+// One-step launches (ONE) store st.ll_old + increment and st.emit_old +
+// increment instead, both entries prefetched with the state: there an
+// atomic per particle per launch would keep L2's atomic units busy, and the
+// photon cursor's atomic waits behind them.
+// ONE: the launch is known to advance exactly one step (P.nsub == 1).
+template <typename R, int FIELD, int SAMP, bool ONE = false, class G>
 __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const G& gat,
                                                  int64_t i, const PState<R>& st,
                                                  PhotonStage& stage, int& fill,
@@ -620,24 +637,41 @@ __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const G
   (void)li_q;
   (void)mw;
 
-  for (int s = 0; s < P.nsub; ++s) {
+  const int nsub = ONE ? 1 : P.nsub;
+  for (int s = 0; s < nsub; ++s) {
     const uint32_t step = static_cast<uint32_t>(P.t0 + s);
     // 1. field at x^n, t^n
     const EB<R> f = gat(x, y, phase);
     phase += P.phase_step;
     // 2. Boris: half E kick, rotation, half E kick
     const R hq = P.half_q_dtn;
-    const R umx = ux + hq * f.Ex, umy = uy + hq * f.Ey, umz = uz + hq * f.Ez;
-    const R igm = rsq(R(1) + umx * umx + umy * umy + umz * umz);
-    const R tx = hq * f.Bx * igm, ty = hq * f.By * igm, tz = hq * f.Bz * igm;
-    const R sf = R(2) * rcp(R(1) + tx * tx + ty * ty + tz * tz);
-    const R sx = sf * tx, sy = sf * ty, sz = sf * tz;
-    const R vx = umx + (umy * tz - umz * ty);
-    const R vy = umy + (umz * tx - umx * tz);
-    const R vz = umz + (umx * ty - umy * tx);
-    R nux = umx + (vy * sz - vz * sy) + hq * f.Ex;
-    R nuy = umy + (vz * sx - vx * sz) + hq * f.Ey;
-    R nuz = umz + (vx * sy - vy * sx) + hq * f.Ez;
+    R nux, nuy, nuz;
+    if constexpr (FIELD == PRAD_FIELD_PLANE_WAVE) {
+      // the wave has E_x = B_x = 0: the same push with those terms dropped
+      const R umx = ux, umy = uy + hq * f.Ey, umz = uz + hq * f.Ez;
+      const R igm = rsq(R(1) + umx * umx + umy * umy + umz * umz);
+      const R ty = hq * f.By * igm, tz = hq * f.Bz * igm;
+      const R sf = R(2) * rcp(R(1) + ty * ty + tz * tz);
+      const R sy = sf * ty, sz = sf * tz;
+      const R vx = umx + (umy * tz - umz * ty);
+      const R vy = umy - umx * tz;
+      const R vz = umz + umx * ty;
+      nux = umx + (vy * sz - vz * sy);
+      nuy = umy - vx * sz + hq * f.Ey;
+      nuz = umz + vx * sy + hq * f.Ez;
+    } else {
+      const R umx = ux + hq * f.Ex, umy = uy + hq * f.Ey, umz = uz + hq * f.Ez;
+      const R igm = rsq(R(1) + umx * umx + umy * umy + umz * umz);
+      const R tx = hq * f.Bx * igm, ty = hq * f.By * igm, tz = hq * f.Bz * igm;
+      const R sf = R(2) * rcp(R(1) + tx * tx + ty * ty + tz * tz);
+      const R sx = sf * tx, sy = sf * ty, sz = sf * tz;
+      const R vx = umx + (umy * tz - umz * ty);
+      const R vy = umy + (umz * tx - umx * tz);
+      const R vz = umz + (umx * ty - umy * tx);
+      nux = umx + (vy * sz - vz * sy) + hq * f.Ex;
+      nuy = umy + (vz * sx - vx * sz) + hq * f.Ey;
+      nuz = umz + (vx * sy - vy * sx) + hq * f.Ez;
+    }
     // 3. mean momentum of the step
     const R ax = R(0.5) * (ux + nux), ay = R(0.5) * (uy + nuy), az = R(0.5) * (uz + nuz);
     const R ua2 = ax * ax + ay * ay + az * az;
@@ -647,10 +681,18 @@ __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const G
     R Om;
     if (P.heff_form == PRAD_HEFF_FIELD) {
       const R bx = ax * iga, by = ay * iga, bz = az * iga;
-      const R fx = f.Ex + (by * f.Bz - bz * f.By);
-      const R fy = f.Ey + (bz * f.Bx - bx * f.Bz);
-      const R fz = f.Ez + (bx * f.By - by * f.Bx);
-      const R eb = f.Ex * bx + f.Ey * by + f.Ez * bz;
+      R fx, fy, fz, eb;
+      if constexpr (FIELD == PRAD_FIELD_PLANE_WAVE) {
+        fx = by * f.Bz - bz * f.By;
+        fy = f.Ey - bx * f.Bz;
+        fz = f.Ez + bx * f.By;
+        eb = f.Ey * by + f.Ez * bz;
+      } else {
+        fx = f.Ex + (by * f.Bz - bz * f.By);
+        fy = f.Ey + (bz * f.Bx - bx * f.Bz);
+        fz = f.Ez + (bx * f.By - by * f.Bx);
+        eb = f.Ex * bx + f.Ey * by + f.Ez * bz;
+      }
       const R h2 = fx * fx + fy * fy + fz * fz - eb * eb;
       Om = P.abs_q * sqr(h2 > R(0) ? h2 : R(0));
     } else {  // Eq. (9), gamma = mean of the end-point Lorentz factors
@@ -673,13 +715,15 @@ __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const G
     // 6. Landau-Lifshitz loss (Eq. (4)): ledger and optional kick
     const R om2 = Om * Om;
     if (P.rr_mode >= PRAD_RR_LEDGER) ll.add(w * P.ll_coef * om2 * ua2);
+    R n2 = nux * nux + nuy * nuy + nuz * nuz;
     if (P.rr_mode == PRAD_RR_APPLY) {
-      const R gL = sqr(R(1) + nux * nux + nuy * nuy + nuz * nuz);
+      const R gL = sqr(R(1) + n2);
       const R fk = rcp(R(1) + P.ll_coef * om2 * gL);
       nux *= fk; nuy *= fk; nuz *= fk;
+      n2 *= fk * fk;
     }
     // 7. position x^{n+1}
-    const R ign = rsq(R(1) + nux * nux + nuy * nuy + nuz * nuz);
+    const R ign = rsq(R(1) + n2);
     const R dtg = P.dtn * ign;
     R xn = x + dtg * nux, yn = y + dtg * nuy, zn = z;
     if (P.dims == 3) zn = z + dtg * nuz;
@@ -756,8 +800,18 @@ __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const G
     P.ux[i] = ux; P.uy[i] = uy; P.uz[i] = uz;
     const int64_t li = static_cast<int64_t>(pid - P.pid0);
     if (li < P.led_n) {
-      if (P.rr_mode >= PRAD_RR_LEDGER) P.led_ll[li] = st.ll_old + ll.value();
-      if (le.nonzero()) P.led_emit[li] += le.value();
+      if (P.rr_mode >= PRAD_RR_LEDGER) {
+        if constexpr (ONE)
+          P.led_ll[li] = st.ll_old + ll.value_one();
+        else
+          atomicAdd(P.led_ll + li, ll.value());
+      }
+      if (le.nonzero()) {
+        if constexpr (ONE)
+          P.led_emit[li] = st.emit_old + le.value_one();
+        else
+          atomicAdd(P.led_emit + li, le.value());
+      }
     } else {
       cnt.bad_id = true;
     }
@@ -856,17 +910,17 @@ __global__ void __launch_bounds__(256, (PF ? PRAD_PF_MINB : MinBlocks<R, FIELD, 
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   const int64_t first = static_cast<int64_t>(blockIdx.x) * blockDim.x;
   if constexpr (PF) {
-    // one or a few steps per launch (the state streams through HBM): a
-    // software pipeline issues the loads of the thread's next particle
-    // before the current one is advanced, so DRAM latency overlaps compute
+    // one step per launch (the state streams through HBM): a software
+    // pipeline issues the loads of the thread's next particle before the
+    // current one is advanced, so DRAM latency overlaps compute
     PState<R> nxt;
-    load_state(P, first + threadIdx.x, first + threadIdx.x < P.n, nxt);
+    load_state<R, true>(P, first + threadIdx.x, first + threadIdx.x < P.n, nxt);
     for (int64_t base = first; base < P.n; base += stride) {
       const int64_t i = base + threadIdx.x;
       const PState<R> cur = nxt;
       const int64_t j = i + stride;
-      load_state(P, j, j < P.n, nxt);
-      advance_particle<R, FIELD, SAMP>(P, gat, i, cur, stage, fill, pout, cnt, &mw);
+      load_state<R, true>(P, j, j < P.n, nxt);
+      advance_particle<R, FIELD, SAMP, true>(P, gat, i, cur, stage, fill, pout, cnt, &mw);
     }
   } else {
     for (int64_t base = first; base < P.n; base += stride) {
@@ -1044,10 +1098,11 @@ cudaError_t launch_field(const StepParams<R>& p, int sampler, int grid, int bloc
   if (sampler == PRAD_SAMPLER_TABLE) {
     // prefetching pays when the launch is short (state streamed from HBM);
     // for long fused launches it only costs registers
-    if (sizeof(R) == 4 && p.nsub <= 4)
-      k_push_emit<R, FIELD, PRAD_SAMPLER_TABLE, (sizeof(R) == 4)><<<grid, block, 0, s>>>(p);
-    else
-      k_push_emit<R, FIELD, PRAD_SAMPLER_TABLE, false><<<grid, block, 0, s>>>(p);
+    bool pf = false;
+    if constexpr (sizeof(R) == 4) pf = p.nsub == 1;
+    if constexpr (sizeof(R) == 4)
+      if (pf) k_push_emit<R, FIELD, PRAD_SAMPLER_TABLE, true><<<grid, block, 0, s>>>(p);
+    if (!pf) k_push_emit<R, FIELD, PRAD_SAMPLER_TABLE, false><<<grid, block, 0, s>>>(p);
     return cudaGetLastError();
   }
   if constexpr (sizeof(R) == 4) {
@@ -1081,8 +1136,8 @@ int occupancy_of(K kernel, int block, size_t dyn) {
 template <typename R, int FIELD>
 int field_occupancy(int sampler, bool pf, int block) {
   if (sampler == PRAD_SAMPLER_TABLE) {
-    if (pf && sizeof(R) == 4)
-      return occupancy_of(k_push_emit<R, FIELD, PRAD_SAMPLER_TABLE, true>, block, 0);
+    if constexpr (sizeof(R) == 4)
+      if (pf) return occupancy_of(k_push_emit<R, FIELD, PRAD_SAMPLER_TABLE, true>, block, 0);
     return occupancy_of(k_push_emit<R, FIELD, PRAD_SAMPLER_TABLE, false>, block, 0);
   }
   if constexpr (sizeof(R) == 4) {
@@ -1105,7 +1160,7 @@ int field_occupancy(int sampler, bool pf, int block) {
 // Resident blocks per SM of the kernel variant a launch would use.
 template <typename R>
 int push_emit_occupancy(int field_kind, int sampler, int nsub, int block) {
-  const bool pf = nsub <= 4;
+  const bool pf = nsub == 1;
   switch (field_kind) {
     case PRAD_FIELD_CONST: return field_occupancy<R, PRAD_FIELD_CONST>(sampler, pf, block);
     case PRAD_FIELD_PLANE_WAVE: return field_occupancy<R, PRAD_FIELD_PLANE_WAVE>(sampler, pf, block);

@@ -39,9 +39,9 @@ KERNEL_SOURCES = ["paper_1409_5574_gb300/csrc/push_emit.cu",
                   "paper_1409_5574_gb300/csrc/prad_internal.h",
                   "paper_1409_5574_gb300/csrc/mlp_device.cuh"]
 NCU_TRAFFIC = {
-    "src_sha256": None,
-    "fused": None,     # bytes per launch, 2^20 particles x 400 steps, a0 = 500
-    "stream": None,    # bytes per launch, 2^24 particles x 1 step, a0 = 500
+    "src_sha256": "4bde3f98f723d861ceed8329dde2799cea9f3a284b326fcf1ef8c036a9412411",
+    "fused": None,        # bytes per launch of the bench's fused launches
+    "stream": 1334472192, # bytes per launch, 2^24 particles x 1 step, a0 = 500
 }
 
 

@@ -10,9 +10,12 @@
 //
 // Numerics (shared by training, evaluation and the fused push kernel):
 //   features f = (logit(r)/8, clamp((ln gamma - c1)/s1), clamp((ln w - c2)/s2))
-//   z1 = W1 f + b1 (FP32 FMA, BF16 weights);  h1 = bf16(silu(z1))
+//   z1 = W1 f + b1 (BF16 weights, FP32 accumulate);  h1 = bf16(silu(z1))
 //   z2 = W2 h1 + b2 (BF16 x BF16 tensor-core MMA, FP32 accumulate)
 //   h2 = silu(z2);  o = W3 h2 + b3 (FP32);  ln x = prior(r) + kOutScale * o
+// The tile evaluator forms z1 on the tensor cores as well: each feature and
+// each bias enters as the sum of two BF16 numbers (high part + rounded
+// remainder, 2^-17 relative), so z1 agrees with the FP32 form to ~1e-6.
 // with the fixed prior(r) = ln(-ln(1 - r)) + 2 (1 - r) ln r, which carries
 // both asymptotes of ln G^-1 (3 ln r at r -> 0, ln(-ln(1 - r)) at r -> 1),
 // so the network only learns a bounded, smooth residual (in [-1.5, -0.2]).
@@ -56,6 +59,11 @@ struct MlpSmem {
   float b3;
   float pad[3];
   __nv_bfloat16 w2[kHid * kW2Ld];          // W2 row-major [j][i], padded
+  // layer 1 as the B operand of m16n8k16 MMAs (K = 16 x N = 64 units):
+  // rows k = 0..2 W1[j][k], k = 3..5 W1[j][k-3] (they multiply the
+  // features' low parts), k = 6, 7 the high and low BF16 parts of b1[j],
+  // k >= 8 zero.  w1f[lane][nt] holds the lane's b0 register of n-tile nt.
+  uint32_t w1f[32][8];
 };
 
 // Device copy of the network: FP32 master parameters and the BF16 W2.
@@ -66,6 +74,11 @@ struct MlpDev {
 
 __device__ __forceinline__ float bf16_round(float v) {
   return __bfloat162float(__float2bfloat16(v));
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&v);
 }
 
 // Weights enter as BF16 (rounded from the FP32 master), biases as FP32.
@@ -82,6 +95,21 @@ __device__ __forceinline__ void mlp_load_smem(MlpSmem& s, const MlpDev& d) {
     const int j = e / kHid, i = e - j * kHid;
     s.w2[j * kW2Ld + i] = d.w2[e];
   }
+  for (int e = threadIdx.x; e < 32 * 8; e += blockDim.x) {
+    const int lane = e >> 3, nt = e & 7;
+    const int j = 8 * nt + (lane >> 2), t = lane & 3;
+    float v[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int k = 2 * t + u;
+      const float b1 = d.params[kOffB1 + j];
+      const float b1h = bf16_round(b1);
+      v[u] = k < 3 ? bf16_round(d.params[kOffW1 + 3 * j + k])
+                   : (k < 6 ? bf16_round(d.params[kOffW1 + 3 * j + k - 3])
+                            : (k == 6 ? b1h : bf16_round(b1 - b1h)));
+    }
+    s.w1f[lane][nt] = pack_bf16x2(v[0], v[1]);
+  }
 }
 
 __device__ __forceinline__ float silu(float z) {
@@ -97,11 +125,6 @@ __device__ __forceinline__ float silu_grad(float z) {
   asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(0.5f * z));
   const float s = 0.5f * (1.0f + t);
   return s + z * s * (1.0f - s);
-}
-
-__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
-  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-  return *reinterpret_cast<const uint32_t*>(&v);
 }
 
 // D = A(16x16, row) * B(16x8, col) + C, BF16 inputs, FP32 accumulate.
@@ -132,51 +155,70 @@ __device__ __forceinline__ float3 mlp_features(float r, float gamma, float wdt) 
   return make_float3(lg, f1, f2);
 }
 
+// Four 8x8 BF16 matrices from shared memory in the MMA fragment layout
+// (lane l supplies the address of row l % 8 of matrix l / 8).
+__device__ __forceinline__ void ldmatrix_x4(uint32_t d[4], const void* row_addr) {
+  const uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(row_addr));
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(d[0]), "=r"(d[1]), "=r"(d[2]), "=r"(d[3])
+               : "r"(a));
+}
+
+// Columns 2t, 2t+1 of a layer-1 A row [f0h f1h f2h f0l f1l f2l 1 1 0 ...]
+// (h: BF16 high part, l: the remainder, rounded to BF16 when packed).
+__device__ __forceinline__ uint32_t mlp_feature_pair(float3 f, int t) {
+  const float h0 = bf16_round(f.x), h1 = bf16_round(f.y), h2 = bf16_round(f.z);
+  const float a = t == 0 ? h0 : (t == 1 ? h2 : (t == 2 ? f.y - h1 : 1.0f));
+  const float b = t == 0 ? h1 : (t == 1 ? f.x - h0 : (t == 2 ? f.z - h2 : 1.0f));
+  return pack_bf16x2(a, b);
+}
+
 // Warp-collective: the 16 rows of a tile are the features of lanes' rows
 // g and g+8 (f_lo, f_hi); returns kOutScale * o (ln x minus the prior) of rows
 // g (out_lo) and g+8 (out_hi), valid in every lane of the row's group.
 __device__ __forceinline__ void mlp_tile16(const MlpSmem& S, float3 f_lo, float3 f_hi,
                                            float& out_lo, float& out_hi) {
   const int lane = threadIdx.x & 31;
-  const int g = lane >> 2, t = lane & 3;
-  // layer 1 directly in the A-fragment layout of layer 2: this lane needs h1
-  // for rows g, g+8 and hidden units 16q + 2t + {0, 1, 8, 9}, q = 0..3
+  const int t = lane & 3;
+  // layer 1 on the tensor cores; its accumulator fragments are exactly the
+  // A fragments of layer 2 (n-tiles 2q, 2q+1 -> k-step q)
+  const uint32_t fa0 = mlp_feature_pair(f_lo, t), fa1 = mlp_feature_pair(f_hi, t);
+  const uint4 wlo = *reinterpret_cast<const uint4*>(&S.w1f[lane][0]);
+  const uint4 whi = *reinterpret_cast<const uint4*>(&S.w1f[lane][4]);
+  const uint32_t wb[8] = {wlo.x, wlo.y, wlo.z, wlo.w, whi.x, whi.y, whi.z, whi.w};
   uint32_t a[4][4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    float h[2][4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int j = 16 * q + 2 * t + (u & 1) + ((u >> 1) << 3);
-      const float4 w = S.w1b1[j];
-      const float zl = fmaf(w.x, f_lo.x, fmaf(w.y, f_lo.y, fmaf(w.z, f_lo.z, w.w)));
-      const float zh = fmaf(w.x, f_hi.x, fmaf(w.y, f_hi.y, fmaf(w.z, f_hi.z, w.w)));
-      h[0][u] = silu(zl);
-      h[1][u] = silu(zh);
-    }
-    a[q][0] = pack_bf16x2(h[0][0], h[0][1]);
-    a[q][1] = pack_bf16x2(h[1][0], h[1][1]);
-    a[q][2] = pack_bf16x2(h[0][2], h[0][3]);
-    a[q][3] = pack_bf16x2(h[1][2], h[1][3]);
+    float c0[4] = {0.0f, 0.0f, 0.0f, 0.0f}, c1[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    mma_bf16_16816(c0, fa0, fa1, 0u, 0u, wb[2 * q], 0u);
+    mma_bf16_16816(c1, fa0, fa1, 0u, 0u, wb[2 * q + 1], 0u);
+    a[q][0] = pack_bf16x2(silu(c0[0]), silu(c0[1]));
+    a[q][1] = pack_bf16x2(silu(c0[2]), silu(c0[3]));
+    a[q][2] = pack_bf16x2(silu(c1[0]), silu(c1[1]));
+    a[q][3] = pack_bf16x2(silu(c1[2]), silu(c1[3]));
   }
-  // layer 2: 8 output column tiles of 8 units, K = 64 in 4 steps of 16
+  // layer 2: 8 output column tiles of 8 units, K = 64 in 4 steps of 16; the
+  // accumulators start from the bias
+  const int m = lane >> 3, r = lane & 7;
   float acc_lo = 0.0f, acc_hi = 0.0f;
 #pragma unroll
   for (int nt = 0; nt < 8; ++nt) {
-    float c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    const __nv_bfloat16* wrow = S.w2 + (8 * nt + g) * kW2Ld + 2 * t;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const uint32_t b0 = *reinterpret_cast<const uint32_t*>(wrow + 16 * q);
-      const uint32_t b1 = *reinterpret_cast<const uint32_t*>(wrow + 16 * q + 8);
-      mma_bf16_16816(c, a[q][0], a[q][1], a[q][2], a[q][3], b0, b1);
-    }
-    // c0,c1: rows g, units 8nt + 2t + {0,1}; c2,c3: row g + 8
     const int j0 = 8 * nt + 2 * t;
-    acc_lo = fmaf(S.w3[j0], silu(c[0] + S.b2[j0]), acc_lo);
-    acc_lo = fmaf(S.w3[j0 + 1], silu(c[1] + S.b2[j0 + 1]), acc_lo);
-    acc_hi = fmaf(S.w3[j0], silu(c[2] + S.b2[j0]), acc_hi);
-    acc_hi = fmaf(S.w3[j0 + 1], silu(c[3] + S.b2[j0 + 1]), acc_hi);
+    const float2 bb = *reinterpret_cast<const float2*>(&S.b2[j0]);
+    float c[4] = {bb.x, bb.y, bb.x, bb.y};
+#pragma unroll
+    for (int qq = 0; qq < 4; qq += 2) {
+      uint32_t b[4];
+      ldmatrix_x4(b, S.w2 + (8 * nt + r) * kW2Ld + 16 * (qq + (m >> 1)) + 8 * (m & 1));
+      mma_bf16_16816(c, a[qq][0], a[qq][1], a[qq][2], a[qq][3], b[0], b[1]);
+      mma_bf16_16816(c, a[qq + 1][0], a[qq + 1][1], a[qq + 1][2], a[qq + 1][3], b[2], b[3]);
+    }
+    // c0,c1: row g, units j0, j0+1; c2,c3: row g + 8
+    const float2 ww = *reinterpret_cast<const float2*>(&S.w3[j0]);
+    acc_lo = fmaf(ww.x, silu(c[0]), acc_lo);
+    acc_lo = fmaf(ww.y, silu(c[1]), acc_lo);
+    acc_hi = fmaf(ww.x, silu(c[2]), acc_hi);
+    acc_hi = fmaf(ww.y, silu(c[3]), acc_hi);
   }
   // layer 3: reduce the partial dot products over the 4 lanes of the group
   acc_lo += __shfl_xor_sync(0xffffffffu, acc_lo, 1);

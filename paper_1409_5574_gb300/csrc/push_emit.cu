@@ -10,6 +10,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cstddef>
+
 #include "mlp_device.cuh"
 #include "prad_internal.h"
 
@@ -454,119 +456,133 @@ struct Counts {
 
 // ---------------------------------------------------------------------------
 // Learned-sampler queue (direct scheme).  Emitting lanes park their emission
-// (features, omega_c, weight, record geometry, ledger entry) in the warp's
-// queue; every 16 queued emissions the warp evaluates the MLP on one 16-row
-// tensor-core tile, then writes the photon records and books the emitted
-// energy.  Warp-collective throughout.
+// (uniform r, gamma, omega_c, weight, record geometry, id, step) in the
+// warp's ring of 48-byte entries; every 16 queued emissions the warp computes
+// the 16 rows' features, evaluates the MLP on one 16-row tensor-core tile,
+// then writes the photon records and books the emitted energy.
+// Warp-collective throughout.
 // ---------------------------------------------------------------------------
-constexpr int kQCap = 48;  // < 16 left over + up to 32 new per step
+constexpr int kQCap = 48;  // >= 15 left over + up to 32 new per step
 struct MlpQueue {
-  float f[3][kQCap];
-  float r[kQCap];
-  float epsc[kQCap];
-  float wt[kQCap];
-  float pos[3][kQCap];
-  float dir[3][kQCap];
-  uint32_t pid[kQCap], step[kQCap];
-  int32_t li[kQCap];
+  // (r, gamma, eps_c, weight), (x, y, z, pid), (dir x, dir y, dir z, step)
+  float4 e[kQCap][3];
 };
 
+struct MlpFlushConst;
 struct MlpWarp {
   const MlpSmem* net;
   MlpQueue* q;
-  int count;            // warp-uniform
-  bool check_output;    // MLP_FALLBACK: non-finite / out-of-range x -> table
+  const MlpFlushConst* kc;
+  int count, head;      // warp-uniform
 };
 
-__device__ __forceinline__ void mlp_enqueue(MlpWarp& mw, bool want, float3 f, float r,
-                                            float epsc, float wt, const float pos[3],
-                                            const float dir[3], uint32_t pid,
-                                            uint32_t step, int32_t li) {
-  const unsigned mask = __ballot_sync(0xffffffffu, want);
-  if (mask == 0u) return;
+// `mask` is the warp's ballot of `want` (nonzero).
+__device__ __forceinline__ void mlp_enqueue(MlpWarp& mw, bool want, unsigned mask, float r,
+                                            float gamma, float epsc, float wt,
+                                            const float pos[3], const float dir[3],
+                                            uint32_t pid, uint32_t step) {
   if (want) {
     const int lane = threadIdx.x & 31;
-    const int k = mw.count + __popc(mask & ((1u << lane) - 1u));
-    MlpQueue& q = *mw.q;
-    q.f[0][k] = f.x; q.f[1][k] = f.y; q.f[2][k] = f.z;
-    q.r[k] = r; q.epsc[k] = epsc; q.wt[k] = wt;
-    q.pos[0][k] = pos[0]; q.pos[1][k] = pos[1]; q.pos[2][k] = pos[2];
-    q.dir[0][k] = dir[0]; q.dir[1][k] = dir[1]; q.dir[2][k] = dir[2];
-    q.pid[k] = pid; q.step[k] = step; q.li[k] = li;
+    int k = mw.head + mw.count + __popc(mask & ((1u << lane) - 1u));
+    k -= k >= kQCap ? kQCap : 0;
+    float4* e = mw.q->e[k];
+    e[0] = make_float4(r, gamma, epsc, wt);
+    e[1] = make_float4(pos[0], pos[1], pos[2], __uint_as_float(pid));
+    e[2] = make_float4(dir[0], dir[1], dir[2], __uint_as_float(step));
   }
   mw.count += __popc(mask);
   __syncwarp();
 }
 
-// Evaluate the first min(16, count) queued emissions, emit their records and
-// book their energy; shift the rest of the queue down.
-template <typename R>
-__device__ __forceinline__ void mlp_flush_tile(const StepParams<R>& P, MlpWarp& mw,
-                                               PhotonStage& stage, int& fill,
-                                               const PhotonOut& pout, Counts& cnt) {
-  MlpQueue& q = *mw.q;
+// Block-uniform inputs of the queue flush, kept in shared memory so that
+// the (not inlined) flush takes a handful of arguments.  16-byte aligned
+// size: the float4 queue entries follow it in dynamic shared memory.
+struct alignas(16) MlpFlushConst {
+  PhotonOut pout;
+  const float* ginv;
+  double* led_emit;
+  int64_t led_n;
+  uint32_t pid0;
+  float wdt_per_eps;   // omega_c dt / eps_c = dt / eps_r (normalised)
+  int check_output;    // MLP_FALLBACK: non-finite / out-of-range x -> table
+};
+struct MlpFlushState {
+  int count, head, fill, fallback;
+};
+
+// Evaluate the oldest min(16, count) queued emissions, emit their records
+// and book their energy.  Not inlined: the tile's registers are not live in
+// the step loop, which keeps the loop at the table path's occupancy; the
+// call happens once per 16 emissions of a warp.
+__device__ __noinline__ MlpFlushState mlp_flush_call(const MlpSmem* net, MlpQueue* queue,
+                                                     PhotonStage* stage,
+                                                     const MlpFlushConst* kc,
+                                                     MlpFlushState st) {
   const int lane = threadIdx.x & 31, g = lane >> 2;
-  const int rows = mw.count < 16 ? mw.count : 16;
-  float3 flo = make_float3(0.f, 0.f, 0.f), fhi = flo;
-  if (g < rows) flo = make_float3(q.f[0][g], q.f[1][g], q.f[2][g]);
-  if (g + 8 < rows) fhi = make_float3(q.f[0][g + 8], q.f[1][g + 8], q.f[2][g + 8]);
+  const int rows = st.count < 16 ? st.count : 16;
+  const bool mine = lane < rows;
+  int k = st.head + lane;
+  k -= k >= kQCap ? kQCap : 0;
+  float4 e0 = make_float4(0.5f, 1.0f, 0.0f, 0.0f), e1 = e0, e2 = e0;
+  if (mine) {
+    const float4* e = queue->e[k];
+    e0 = e[0]; e1 = e[1]; e2 = e[2];
+  }
+  // features of row `lane`
+  const float3 f = mlp_features(e0.x, e0.y, e0.z * kc->wdt_per_eps);
+  // tile layout: lane (g, t) needs rows g and g + 8
+  float3 flo, fhi;
+  flo.x = __shfl_sync(0xffffffffu, f.x, g);
+  flo.y = __shfl_sync(0xffffffffu, f.y, g);
+  flo.z = __shfl_sync(0xffffffffu, f.z, g);
+  fhi.x = __shfl_sync(0xffffffffu, f.x, g + 8);
+  fhi.y = __shfl_sync(0xffffffffu, f.y, g + 8);
+  fhi.z = __shfl_sync(0xffffffffu, f.z, g + 8);
   float olo, ohi;
-  mlp_tile16(*mw.net, flo, fhi, olo, ohi);
+  mlp_tile16(*net, flo, fhi, olo, ohi);
   // row L of the tile lives in lane 4 (L % 8), in olo (L < 8) or ohi
   const float vlo = __shfl_sync(0xffffffffu, olo, (lane & 7) * 4);
   const float vhi = __shfl_sync(0xffffffffu, ohi, (lane & 7) * 4);
-  const bool mine = lane < rows;
   float rec[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   uint32_t pid = 0, step = 0;
   if (mine) {
-    const float lnx = (lane < 8 ? vlo : vhi) + mlp_prior(q.r[lane]);
+    const float lnx = (lane < 8 ? vlo : vhi) + mlp_prior(e0.x);
     float x = __expf(lnx);
-    bool ok = x > 0.0f && x < 80.0f;  // also false for NaN
-    if (mw.check_output) {
-      if (!ok) {
-        x = __expf(ginv_ln(P.ginv, q.r[lane]));
-        ++cnt.fallback;
-      }
+    // uniforms outside the trained range always take the G^-1 table
+    const bool tail = e0.x < kRMin || e0.x > kRMax;
+    const bool ok = x > 0.0f && x < 80.0f;  // also false for NaN
+    if (tail || (kc->check_output && !ok)) {
+      x = __expf(ginv_ln(kc->ginv, e0.x));
+      ++st.fallback;
     } else if (!ok) {
       x = 0.0f;  // no fallback requested: an invalid draw carries no energy
     }
-    const float eps = x * q.epsc[lane];
-    const float wt = q.wt[lane];
-    rec[0] = q.pos[0][lane]; rec[1] = q.pos[1][lane]; rec[2] = q.pos[2][lane];
-    rec[3] = q.dir[0][lane]; rec[4] = q.dir[1][lane]; rec[5] = q.dir[2][lane];
-    rec[6] = eps; rec[7] = wt;
-    pid = q.pid[lane];
-    step = q.step[lane];
-    const int32_t li = q.li[lane];
-    if (li >= 0) atomicAdd(P.led_emit + li, static_cast<double>(wt) * static_cast<double>(eps));
+    const float eps = x * e0.z;
+    rec[0] = e1.x; rec[1] = e1.y; rec[2] = e1.z;
+    rec[3] = e2.x; rec[4] = e2.y; rec[5] = e2.z;
+    rec[6] = eps; rec[7] = e0.w;
+    pid = __float_as_uint(e1.w);
+    step = __float_as_uint(e2.w);
+    const int64_t li = static_cast<int64_t>(pid - kc->pid0);
+    if (li < kc->led_n)
+      atomicAdd(kc->led_emit + li, static_cast<double>(e0.w) * static_cast<double>(eps));
   }
-  stage_photon(stage, fill, pout, mine, rec, pid, step);
-  // shift the remaining entries to the front
-  const int rest = mw.count - rows;
+  stage_photon(*stage, st.fill, kc->pout, mine, rec, pid, step);
+  st.head += rows;
+  st.head -= st.head >= kQCap ? kQCap : 0;
+  st.count -= rows;
   __syncwarp();
-  float tmp[15];
-  uint32_t tp = 0, ts = 0;
-  int32_t tl = 0;
-  const bool mv = lane < rest;
-  if (mv) {
-    const int k = rows + lane;
-    tmp[0] = q.f[0][k]; tmp[1] = q.f[1][k]; tmp[2] = q.f[2][k];
-    tmp[3] = q.r[k]; tmp[4] = q.epsc[k]; tmp[5] = q.wt[k];
-    tmp[6] = q.pos[0][k]; tmp[7] = q.pos[1][k]; tmp[8] = q.pos[2][k];
-    tmp[9] = q.dir[0][k]; tmp[10] = q.dir[1][k]; tmp[11] = q.dir[2][k];
-    tp = q.pid[k]; ts = q.step[k]; tl = q.li[k];
-  }
-  __syncwarp();
-  if (mv) {
-    const int k = lane;
-    q.f[0][k] = tmp[0]; q.f[1][k] = tmp[1]; q.f[2][k] = tmp[2];
-    q.r[k] = tmp[3]; q.epsc[k] = tmp[4]; q.wt[k] = tmp[5];
-    q.pos[0][k] = tmp[6]; q.pos[1][k] = tmp[7]; q.pos[2][k] = tmp[8];
-    q.dir[0][k] = tmp[9]; q.dir[1][k] = tmp[10]; q.dir[2][k] = tmp[11];
-    q.pid[k] = tp; q.step[k] = ts; q.li[k] = tl;
-  }
-  __syncwarp();
-  mw.count = rest;
+  return st;
+}
+
+__device__ __forceinline__ void mlp_flush_tile(MlpWarp& mw, PhotonStage& stage, int& fill,
+                                               Counts& cnt) {
+  MlpFlushState st{mw.count, mw.head, fill, 0};
+  st = mlp_flush_call(mw.net, mw.q, &stage, mw.kc, st);
+  mw.count = st.count;
+  mw.head = st.head;
+  fill = st.fill;
+  cnt.fallback += static_cast<uint32_t>(st.fallback);
 }
 
 // ---------------------------------------------------------------------------
@@ -631,10 +647,6 @@ __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const G
   const bool live = act && isfinite(chk);
   if (act && !live) ++cnt.nan;
   uint64_t phase = P.phase_t0;
-  // ledger entry of this particle (-1: id outside the ledger)
-  const int64_t li64 = static_cast<int64_t>(pid - P.pid0);
-  const int32_t li_q = (live && li64 < P.led_n) ? static_cast<int32_t>(li64) : -1;
-  (void)li_q;
   (void)mw;
 
   const int nsub = ONE ? 1 : P.nsub;
@@ -767,27 +779,17 @@ __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const G
       const R k = fl + ((Rr < pm - fl) ? R(1) : R(0));
       if (live && pm > R(1)) ++cnt.dn1;
       const bool want = live && k > R(0) && w > R(0);
-      const float rp = fmaf(static_cast<float>(rnd.x), 0x1p-32f, 0x1p-33f);
-      const bool tail = rp < kRMin || rp > kRMax;
-      // uniforms outside the trained range: x from the G^-1 table at once
-      const bool now = want && tail;
-      float xt = 0.0f;
-      if (now) {
-        xt = __expf(ginv_ln(P.ginv, rp));
-        ++cnt.fallback;
-        le.add(k * w * xt * epsc);
+      const unsigned wmask = __ballot_sync(0xffffffffu, want);
+      if (wmask) {
+        const float rp = fmaf(static_cast<float>(rnd.x), 0x1p-32f, 0x1p-33f);
+        const float pos[3] = {static_cast<float>(xn), static_cast<float>(yn),
+                              static_cast<float>(zn)};
+        const float dir[3] = {static_cast<float>(ax), static_cast<float>(ay),
+                              static_cast<float>(az)};
+        mlp_enqueue(*mw, want, wmask, rp, static_cast<float>(ga), static_cast<float>(epsc),
+                    static_cast<float>(k * w), pos, dir, pid, step);
+        while (mw->count >= 16) mlp_flush_tile(*mw, stage, fill, cnt);
       }
-      const float rec[8] = {static_cast<float>(xn), static_cast<float>(yn),
-                            static_cast<float>(zn), static_cast<float>(ax),
-                            static_cast<float>(ay), static_cast<float>(az),
-                            static_cast<float>(xt * epsc), static_cast<float>(k * w)};
-      stage_photon(stage, fill, pout, now, rec, pid, step);
-      const bool q = want && !tail;
-      const float3 f = mlp_features(rp, static_cast<float>(ga),
-                                    static_cast<float>(R(1.5) * Om * ga * ga * P.dtn));
-      mlp_enqueue(*mw, q, f, rp, static_cast<float>(epsc), static_cast<float>(k * w), rec,
-                  rec + 3, pid, step, li_q);
-      while (mw->count >= 16) mlp_flush_tile(P, *mw, stage, fill, pout, cnt);
     }
     if (live) {
       x = xn; y = yn; z = zn;
@@ -883,7 +885,15 @@ struct MinBlocks {
 
 // Dynamic shared memory of the learned-sampler variant: the network image
 // and one emission queue per warp.
-constexpr size_t kMlpDynSmem = sizeof(MlpSmem) + kMaxWarps * sizeof(MlpQueue);
+constexpr size_t kMlpDynSmem =
+    sizeof(MlpSmem) + sizeof(MlpFlushConst) + kMaxWarps * sizeof(MlpQueue);
+// every region of the dynamic shared memory starts on a 16-byte boundary
+// (float4 queue entries, uint4 / ldmatrix reads of the network image)
+static_assert(sizeof(MlpSmem) % 16 == 0, "MlpSmem size");
+static_assert(sizeof(MlpFlushConst) % 16 == 0, "MlpFlushConst size");
+static_assert(sizeof(MlpQueue) % 16 == 0, "MlpQueue size");
+static_assert(offsetof(MlpSmem, w2) % 16 == 0 && offsetof(MlpSmem, w1f) % 16 == 0,
+              "MlpSmem member alignment");
 
 #ifndef PRAD_PF_MINB
 #define PRAD_PF_MINB 4
@@ -897,13 +907,25 @@ __global__ void __launch_bounds__(256, (PF ? PRAD_PF_MINB : MinBlocks<R, FIELD, 
   int fill = 0;  // warp-uniform
   const PhotonOut pout = make_pout(P);
   Counts cnt;
-  MlpWarp mw{nullptr, nullptr, 0, SAMP == PRAD_SAMPLER_MLP_FALLBACK};
+  MlpWarp mw{nullptr, nullptr, nullptr, 0, 0};
   if constexpr (SAMP != PRAD_SAMPLER_TABLE) {
     MlpSmem* net = reinterpret_cast<MlpSmem*>(dyn_smem);
-    MlpQueue* qs = reinterpret_cast<MlpQueue*>(dyn_smem + sizeof(MlpSmem));
+    MlpFlushConst* kc = reinterpret_cast<MlpFlushConst*>(dyn_smem + sizeof(MlpSmem));
+    MlpQueue* qs =
+        reinterpret_cast<MlpQueue*>(dyn_smem + sizeof(MlpSmem) + sizeof(MlpFlushConst));
     mlp_load_smem(*net, P.mlp);
+    if (threadIdx.x == 0) {
+      kc->pout = pout;
+      kc->ginv = P.ginv;
+      kc->led_emit = P.led_emit;
+      kc->led_n = P.led_n;
+      kc->pid0 = P.pid0;
+      kc->wdt_per_eps = static_cast<float>(P.dtn / P.eps_r);
+      kc->check_output = SAMP == PRAD_SAMPLER_MLP_FALLBACK;
+    }
     __syncthreads();
     mw.net = net;
+    mw.kc = kc;
     mw.q = qs + (threadIdx.x >> 5);
   }
   const FieldGather<R, FIELD> gat{P};
@@ -931,7 +953,7 @@ __global__ void __launch_bounds__(256, (PF ? PRAD_PF_MINB : MinBlocks<R, FIELD, 
     }
   }
   if constexpr (SAMP != PRAD_SAMPLER_TABLE) {
-    while (mw.count > 0) mlp_flush_tile(P, mw, stage, fill, pout, cnt);
+    while (mw.count > 0) mlp_flush_tile(mw, stage, fill, cnt);
   }
   if (fill > 0) flush_stage(stage, fill, pout);
   flush_counts(cnt, P.counters);

@@ -232,14 +232,18 @@ typedef struct prad_ensemble {
  * blocks takes work items (batch_chunk particles of one ensemble) from an
  * atomic counter until none are left, so large and small ensembles share
  * the GPU without a launch per ensemble.  Each ensemble has its own field
- * and Philox word 3; dt, omega_ref, seed, sampler (table only) and rr_mode
- * are the context's.  With use_graph the launches of a call are captured in
- * a CUDA graph and replayed by later calls of the same shape (same n_ens,
- * sizes, nsteps and launch parameters); ensemble contents (arrays, t0,
- * fields) may change between calls.  No kernel waits on another: nothing
- * can spin.  Results per ensemble equal those of prad_push_emit with the
- * same field and ensemble word.  Errors: PRAD_ERR_ARG (bad ensemble,
- * ledger range, Yee field, n_ens < 1), PRAD_ERR_CUDA. */
+ * and Philox word 3; dt, omega_ref, seed, sampler (table or learned; FP32
+ * only) and rr_mode are the context's.  With a learned sampler a block
+ * evaluates its queued emissions before it moves to another ensemble.  With
+ * use_graph the launches of a call are captured in a CUDA graph and
+ * replayed by later calls of the same shape (same n_ens, sizes, nsteps,
+ * sampler and launch parameters); ensemble contents (arrays, t0, fields)
+ * may change between calls.  No kernel waits on another: nothing can spin.
+ * Results per ensemble equal those of prad_push_emit with the same field
+ * and ensemble word (state, counters and photon records bit for bit; the
+ * emitted-energy ledger of a learned sampler up to the order of its FP64
+ * atomic adds).  Errors: PRAD_ERR_ARG (bad ensemble, ledger range, Yee
+ * field, n_ens < 1, FP64 context), PRAD_ERR_CUDA. */
 int prad_push_emit_batch(prad_ctx* ctx, const prad_ensemble* ens, int32_t n_ens,
                          int32_t nsteps);
 

@@ -944,7 +944,7 @@ int issue_batch(prad_ctx* c, int n_ens, int64_t items, int32_t nsteps, int chunk
   bp.n_ens = n_ens;
   bp.chunk = chunk;
   bp.pad = 0;
-  const int cap = batch_max_blocks_per_sm(block);
+  const int cap = batch_max_blocks_per_sm(block, c->cfg.sampler);
   const int64_t g = static_cast<int64_t>(c->num_sms) * (bps < cap ? bps : cap);
   const int grid = static_cast<int>(g < items ? g : (items > 0 ? items : 1));
   for (int32_t done = 0; done < nsteps;) {
@@ -952,7 +952,7 @@ int issue_batch(prad_ctx* c, int n_ens, int64_t items, int32_t nsteps, int chunk
     bp.step_base = done;
     bp.nsub = m;
     CK(c, cudaMemsetAsync(c->d_batch_next, 0, sizeof(unsigned long long), c->stream));
-    CK(c, launch_push_emit_batch(bp, grid, block, c->stream));
+    CK(c, launch_push_emit_batch(bp, c->cfg.sampler, grid, block, c->stream));
     done += m;
   }
   return PRAD_OK;
@@ -973,8 +973,8 @@ std::vector<std::pair<uint64_t, prad_tuning>> g_tune_cache;
 int prad_push_emit_batch(prad_ctx* c, const prad_ensemble* ens, int32_t n_ens, int32_t nsteps) {
   if (!c || !ens || n_ens < 1 || nsteps < 0)
     return fail(c, PRAD_ERR_ARG, "push_emit_batch: bad argument");
-  if (c->cfg.precision != PRAD_FP32 || c->cfg.sampler != PRAD_SAMPLER_TABLE)
-    return fail(c, PRAD_ERR_ARG, "push_emit_batch: FP32 with the table sampler only");
+  if (c->cfg.precision != PRAD_FP32)
+    return fail(c, PRAD_ERR_ARG, "push_emit_batch: FP32 only");
   for (int k = 0; k < n_ens; ++k) {
     int rc = check_ensemble(c, ens[k], k);
     if (rc != PRAD_OK) return rc;
@@ -1000,6 +1000,7 @@ int prad_push_emit_batch(prad_ctx* c, const prad_ensemble* ens, int32_t n_ens, i
   key = mix64(key, static_cast<uint64_t>(nsteps));
   key = mix64(key, (static_cast<uint64_t>(chunk) << 32) | static_cast<uint64_t>(nsub));
   key = mix64(key, (static_cast<uint64_t>(block) << 32) | static_cast<uint64_t>(bps));
+  key = mix64(key, static_cast<uint64_t>(c->cfg.sampler));
   if (!c->graph_exec || c->graph_key != key) {
     if (c->graph_exec) {
       cudaGraphExecDestroy(c->graph_exec);
@@ -1027,8 +1028,8 @@ int prad_autotune_batch(prad_ctx* c, const prad_ensemble* ens, int32_t n_ens, in
                         int64_t sample, prad_tuning* out) {
   if (!c || !ens || n_ens < 1 || probe_steps < 1 || sample < 32)
     return fail(c, PRAD_ERR_ARG, "autotune_batch: bad argument");
-  if (c->cfg.precision != PRAD_FP32 || c->cfg.sampler != PRAD_SAMPLER_TABLE)
-    return fail(c, PRAD_ERR_ARG, "autotune_batch: FP32 with the table sampler only");
+  if (c->cfg.precision != PRAD_FP32)
+    return fail(c, PRAD_ERR_ARG, "autotune_batch: FP32 only");
   for (int k = 0; k < n_ens; ++k) {
     int rc = check_ensemble(c, ens[k], k);
     if (rc != PRAD_OK) return rc;
@@ -1039,6 +1040,7 @@ int prad_autotune_batch(prad_ctx* c, const prad_ensemble* ens, int32_t n_ens, in
   for (const char* q = prop.name; *q; ++q) key = mix64(key, static_cast<uint64_t>(*q));
   key = mix64(key, static_cast<uint64_t>(probe_steps));
   key = mix64(key, static_cast<uint64_t>(sample));
+  key = mix64(key, static_cast<uint64_t>(c->cfg.sampler));
   for (int k = 0; k < n_ens; ++k)
     key = mix64(key, (static_cast<uint64_t>(ens[k].n) << 2) | static_cast<uint64_t>(ens[k].field.kind));
   {
@@ -1113,7 +1115,7 @@ int prad_autotune_batch(prad_ctx* c, const prad_ensemble* ens, int32_t n_ens, in
   int rc_all = PRAD_OK;
   for (int bi = 0; bi < 2 && rc_all == PRAD_OK; ++bi) {
     const int block = blocks[bi];
-    const int cap = batch_max_blocks_per_sm(block);
+    const int cap = batch_max_blocks_per_sm(block, c->cfg.sampler);
     for (int bps = 2; bps <= cap && bps <= 2 * (256 / block) * 3 && rc_all == PRAD_OK; ++bps) {
       for (int ci = 0; ci < 4 && rc_all == PRAD_OK; ++ci) {
         const int chunk = chunks[ci];

@@ -131,11 +131,11 @@ struct BatchParams {
 };
 
 // Launchers (defined in the kernel translation units).
-cudaError_t launch_push_emit_batch(const BatchParams& bp, int grid, int block,
+cudaError_t launch_push_emit_batch(const BatchParams& bp, int sampler, int grid, int block,
                                    cudaStream_t s);
 template <typename R>
 int push_emit_occupancy(int field_kind, int sampler, int nsub, int block);
-int batch_max_blocks_per_sm(int block);
+int batch_max_blocks_per_sm(int block, int sampler);
 template <typename R>
 cudaError_t launch_push_emit(const StepParams<R>& p, int field_kind, int sampler, int grid,
                              int block, cudaStream_t s);

@@ -895,6 +895,16 @@ static_assert(sizeof(MlpQueue) % 16 == 0, "MlpQueue size");
 static_assert(offsetof(MlpSmem, w2) % 16 == 0 && offsetof(MlpSmem, w1f) % 16 == 0,
               "MlpSmem member alignment");
 
+// Resident blocks per SM of a kernel at this block size and dynamic shared
+// memory (1 if the query fails).
+template <typename K>
+int occupancy_of(K kernel, int block, size_t dyn) {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, block, dyn) != cudaSuccess)
+    return 1;
+  return nb > 0 ? nb : 1;
+}
+
 #ifndef PRAD_PF_MINB
 #define PRAD_PF_MINB 4
 #endif
@@ -968,17 +978,32 @@ __global__ void __launch_bounds__(256, (PF ? PRAD_PF_MINB : MinBlocks<R, FIELD, 
 #ifndef PRAD_BATCH_MINB
 #define PRAD_BATCH_MINB 3
 #endif
+template <int SAMP>
 __global__ void __launch_bounds__(256, PRAD_BATCH_MINB)
     k_push_emit_batch(const BatchParams bp) {
   __shared__ PhotonStage stage_all[kMaxWarps];
   __shared__ StepParams<float> Ps;
   __shared__ long long s_item;
   __shared__ int s_ens;
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
   PhotonStage& stage = stage_all[threadIdx.x >> 5];
   int fill = 0;
   Counts cnt;
   int cur = -1;
   PhotonOut pout;
+  MlpWarp mw{nullptr, nullptr, nullptr, 0, 0};
+  MlpFlushConst* kc = nullptr;
+  if constexpr (SAMP != PRAD_SAMPLER_TABLE) {
+    // one network for all ensembles (the context's)
+    MlpSmem* net = reinterpret_cast<MlpSmem*>(dyn_smem);
+    kc = reinterpret_cast<MlpFlushConst*>(dyn_smem + sizeof(MlpSmem));
+    MlpQueue* qs =
+        reinterpret_cast<MlpQueue*>(dyn_smem + sizeof(MlpSmem) + sizeof(MlpFlushConst));
+    mlp_load_smem(*net, bp.ens[0].mlp);
+    mw.net = net;
+    mw.kc = kc;
+    mw.q = qs + (threadIdx.x >> 5);
+  }
   for (;;) {
     if (threadIdx.x == 0) {
       const unsigned long long it = atomicAdd(bp.next_item, 1ull);
@@ -999,6 +1024,11 @@ __global__ void __launch_bounds__(256, PRAD_BATCH_MINB)
     const int e = s_ens;
     if (e < 0) break;
     if (e != cur) {
+      // queued emissions carry the previous ensemble's ledger and time step:
+      // evaluate them before its parameters are replaced
+      if constexpr (SAMP != PRAD_SAMPLER_TABLE) {
+        while (mw.count > 0) mlp_flush_tile(mw, stage, fill, cnt);
+      }
       // photons staged so far belong to the previous ensemble's buffer view;
       // all ensembles share the context's buffer, so no flush is needed
       constexpr int kWords = static_cast<int>(sizeof(StepParams<float>) / 4);
@@ -1011,6 +1041,15 @@ __global__ void __launch_bounds__(256, PRAD_BATCH_MINB)
         Ps.t0 += bp.step_base;
         Ps.phase_t0 += static_cast<uint64_t>(bp.step_base) * Ps.phase_step;
         Ps.nsub = bp.nsub;
+        if constexpr (SAMP != PRAD_SAMPLER_TABLE) {
+          kc->pout = make_pout(Ps);
+          kc->ginv = Ps.ginv;
+          kc->led_emit = Ps.led_emit;
+          kc->led_n = Ps.led_n;
+          kc->pid0 = Ps.pid0;
+          kc->wdt_per_eps = Ps.dtn / Ps.eps_r;
+          kc->check_output = SAMP == PRAD_SAMPLER_MLP_FALLBACK;
+        }
       }
       __syncthreads();
       cur = e;
@@ -1024,8 +1063,8 @@ __global__ void __launch_bounds__(256, PRAD_BATCH_MINB)
         const int64_t i = base + threadIdx.x;
         PState<float> st;
         load_state(Ps, i, i < last, st);
-        advance_particle<float, PRAD_FIELD_CONST, PRAD_SAMPLER_TABLE>(
-            Ps, gat, i, st, stage, fill, pout, cnt, nullptr);
+        advance_particle<float, PRAD_FIELD_CONST, SAMP>(Ps, gat, i, st, stage, fill, pout,
+                                                        cnt, &mw);
       }
     } else {
       const FieldGather<float, PRAD_FIELD_PLANE_WAVE> gat{Ps};
@@ -1033,29 +1072,59 @@ __global__ void __launch_bounds__(256, PRAD_BATCH_MINB)
         const int64_t i = base + threadIdx.x;
         PState<float> st;
         load_state(Ps, i, i < last, st);
-        advance_particle<float, PRAD_FIELD_PLANE_WAVE, PRAD_SAMPLER_TABLE>(
-            Ps, gat, i, st, stage, fill, pout, cnt, nullptr);
+        advance_particle<float, PRAD_FIELD_PLANE_WAVE, SAMP>(Ps, gat, i, st, stage, fill,
+                                                             pout, cnt, &mw);
       }
     }
     __syncthreads();
+  }
+  if constexpr (SAMP != PRAD_SAMPLER_TABLE) {
+    while (mw.count > 0) mlp_flush_tile(mw, stage, fill, cnt);
   }
   if (cur >= 0 && fill > 0) flush_stage(stage, fill, pout);
   // counters: any ensemble's pointer to the shared counter array will do
   flush_counts(cnt, bp.ens[0].counters);
 }
 
-cudaError_t launch_push_emit_batch(const BatchParams& bp, int grid, int block,
-                                   cudaStream_t s) {
-  k_push_emit_batch<<<grid, block, 0, s>>>(bp);
+template <int SAMP>
+cudaError_t launch_batch_samp(const BatchParams& bp, int grid, int block, cudaStream_t s) {
+  const size_t dyn = SAMP == PRAD_SAMPLER_TABLE ? 0 : kMlpDynSmem;
+  if (dyn) {
+    const cudaError_t e = cudaFuncSetAttribute(
+        k_push_emit_batch<SAMP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        static_cast<int>(dyn));
+    if (e != cudaSuccess) return e;
+  }
+  k_push_emit_batch<SAMP><<<grid, block, dyn, s>>>(bp);
   return cudaGetLastError();
 }
 
-int batch_max_blocks_per_sm(int block) {
-  int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_push_emit_batch, block, 0) !=
-      cudaSuccess)
-    return 1;
-  return nb > 0 ? nb : 1;
+cudaError_t launch_push_emit_batch(const BatchParams& bp, int sampler, int grid, int block,
+                                   cudaStream_t s) {
+  switch (sampler) {
+    case PRAD_SAMPLER_TABLE: return launch_batch_samp<PRAD_SAMPLER_TABLE>(bp, grid, block, s);
+    case PRAD_SAMPLER_MLP: return launch_batch_samp<PRAD_SAMPLER_MLP>(bp, grid, block, s);
+    case PRAD_SAMPLER_MLP_FALLBACK:
+      return launch_batch_samp<PRAD_SAMPLER_MLP_FALLBACK>(bp, grid, block, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int SAMP>
+int batch_occupancy_samp(int block) {
+  const size_t dyn = SAMP == PRAD_SAMPLER_TABLE ? 0 : kMlpDynSmem;
+  if (dyn)
+    cudaFuncSetAttribute(k_push_emit_batch<SAMP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(dyn));
+  return occupancy_of(k_push_emit_batch<SAMP>, block, dyn);
+}
+
+int batch_max_blocks_per_sm(int block, int sampler) {
+  switch (sampler) {
+    case PRAD_SAMPLER_MLP: return batch_occupancy_samp<PRAD_SAMPLER_MLP>(block);
+    case PRAD_SAMPLER_MLP_FALLBACK: return batch_occupancy_samp<PRAD_SAMPLER_MLP_FALLBACK>(block);
+    default: return batch_occupancy_samp<PRAD_SAMPLER_TABLE>(block);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1145,14 +1214,6 @@ cudaError_t launch_field(const StepParams<R>& p, int sampler, int grid, int bloc
     return cudaGetLastError();
   }
   return cudaErrorInvalidValue;
-}
-
-template <typename K>
-int occupancy_of(K kernel, int block, size_t dyn) {
-  int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, block, dyn) != cudaSuccess)
-    return 1;
-  return nb > 0 ? nb : 1;
 }
 
 template <typename R, int FIELD>

@@ -95,6 +95,70 @@ def test_batch_equals_individual_launches():
     np.testing.assert_array_equal(_keys(ph_a), np.sort(np.concatenate(keys)))
 
 
+@pytest.fixture(scope="module")
+def trained_params():
+    """The learned sampler trained on 10^8 device-generated samples."""
+    wl = W.plane_wave(a0=300.0, n=16)
+    ctx = prad.Context(wl.problem_kwargs(), precision=prad.PRAD_FP32,
+                       photon_capacity=1 << 10, max_particles=16)
+    ctx.mlp_train(1526, 65536, 3e-3, seed=7)
+    p = ctx.mlp_weights()
+    ctx.close()
+    return p
+
+
+def _records(ph):
+    key = ph["pid"].numpy().astype(np.int64) * 2**32 + ph["step"].numpy()
+    o = np.argsort(key)
+    return key[o], np.stack([ph[c].numpy()[o] for c in ("eps", "weight", "x", "nx")], 1)
+
+
+def test_batch_learned_sampler_equals_individual_launches(trained_params):
+    """Learned sampler in the batch kernel: queued emissions are evaluated
+    before a block moves to another ensemble, so every record (its x from the
+    network row of its own emission) equals the per-ensemble launch's."""
+    wls = _small_set(seed=4)
+    nsteps = 25
+    total = sum(w.n for w in wls)
+    smp = prad.PRAD_SAMPLER_MLP_FALLBACK
+    ctx = _ctx(wls, sampler=smp, batch_chunk=512)
+    ctx.mlp_set_weights(trained_params)
+    sts = [ctx.to_device(w.state) for w in wls]
+    ens = ctx.ensembles(sts, [w.problem_kwargs() for w in wls])
+    ctx.push_emit_batch(ens, nsteps)
+    states_a, ph_a, e_a, _, s_a, le_a, ll_a = _collect(ctx, sts)
+    ctx.close()
+    keys, recs, off = [], [], 0
+    for k, w in enumerate(wls):
+        if w.n:
+            c2 = prad.Context(w.problem_kwargs(), precision=prad.PRAD_FP32, sampler=smp,
+                              photon_capacity=1 << 22, max_particles=total, ensemble=k,
+                              steps_per_launch=nsteps)
+            c2.mlp_set_weights(trained_params)
+            st = c2.to_device(w.state)
+            c2.push_emit(st, nsteps, pid0=off, ledger_offset=off)
+            torch.cuda.synchronize()
+            ph2 = c2.photons(on_device=False)
+            le2, ll2 = c2.ledger()
+            for name in ("x", "y", "z", "ux", "uy", "uz"):
+                np.testing.assert_array_equal(states_a[k][name], st[name].double().cpu().numpy())
+            sl = slice(off, off + w.n)
+            np.testing.assert_array_equal(ll_a[sl], ll2.cpu().numpy()[sl])
+            np.testing.assert_allclose(le_a[sl], le2.cpu().numpy()[sl], rtol=1e-12, atol=0)
+            kk, rr = _records(ph2)
+            keys.append(kk)
+            recs.append(rr)
+            c2.close()
+        off += w.n
+    ka, ra = _records(ph_a)
+    kb = np.concatenate(keys)
+    o = np.argsort(kb)
+    np.testing.assert_array_equal(ka, kb[o])
+    np.testing.assert_array_equal(ra, np.concatenate(recs)[o])
+    assert s_a["records"] == ka.size > 1000
+    assert s_a["mlp_fallback"] < 1e-3 * ka.size + 5
+
+
 def test_batch_matches_oracle_per_ensemble():
     wls = _small_set(seed=5)
     ctx = _ctx(wls)
@@ -164,19 +228,24 @@ def test_autotune_leaves_state_and_caches():
     ctx.close()
 
 
-def test_full_size_uneven_ensembles_graph_autotuned():
+@pytest.mark.parametrize("sampler", ["table", "mlp_fallback"])
+def test_full_size_uneven_ensembles_graph_autotuned(sampler, trained_params):
     """256 ensembles, sizes log-uniform in [1e3, 1e6], a0 ~ U[50, 500], plane
     wave or constant B, 500 steps in one persistent kernel per call under a
-    captured graph with autotuned launch parameters; 4 sampled electrons of
+    captured graph with autotuned launch parameters, with the table sampler
+    and with the learned sampler (table fallback); 4 sampled electrons of
     every 16th ensemble against the oracle."""
     es = W.ensembles(count=256, nsteps=500, seed=1)
     wls = [_f32(w) for w in es.workloads]
     total = sum(w.n for w in wls)
+    smp = (prad.PRAD_SAMPLER_TABLE if sampler == "table" else prad.PRAD_SAMPLER_MLP_FALLBACK)
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         ctx = prad.Context(wls[0].problem_kwargs(), precision=prad.PRAD_FP32,
-                           photon_capacity=int(0.06 * total * 500) + (1 << 20),
-                           max_particles=total, use_graph=True, stream=stream)
+                           photon_capacity=int(0.08 * total * 500) + (1 << 20),
+                           max_particles=total, use_graph=True, stream=stream, sampler=smp)
+        if sampler != "table":
+            ctx.mlp_set_weights(trained_params)
         sts = [ctx.to_device(w.state) for w in wls]
         ens = ctx.ensembles(sts, [w.problem_kwargs() for w in wls])
         tune = ctx.autotune_batch(ens, probe_steps=10, sample=4096)
@@ -186,7 +255,7 @@ def test_full_size_uneven_ensembles_graph_autotuned():
         ev1.record(stream)
         stream.synchronize()
     secs = ev0.elapsed_time(ev1) / 1e3
-    print(f"\nbatched: {total} particles x 500 steps in {secs * 1e3:.1f} ms = "
+    print(f"\nbatched ({sampler}): {total} particles x 500 steps in {secs * 1e3:.1f} ms = "
           f"{total * 500 / secs:.3e} particle-steps/s, tuning {tune}")
     e, l, s = ctx.energy_budget()
     assert s["dropped"] == 0 and s["status"] == 0

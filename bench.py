@@ -76,6 +76,8 @@ def parse():
     ap.add_argument("--bps", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mlp", action="store_true")
+    ap.add_argument("--no-other", action="store_true",
+                    help="skip the Yee, a0=500 2^26-electron and batched workloads")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     return ap.parse_args()
 
@@ -227,6 +229,114 @@ def run_reference(args):
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------- other workloads
+def other_workloads(prad, W, torch, params, rank):
+    """One timed run of each of the other workload shapes (particle-steps/s;
+    records drained between chunks, drain time excluded): the 2D Yee grid,
+    the learned vs table sampler at 2^26 electrons and a0 = 500, and the
+    batched uneven ensembles.  `params`: trained network (None: table only)."""
+    out = {}
+
+    def timed(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        b.synchronize()
+        return a.elapsed_time(b) / 1e3
+
+    # 2D Yee grid 4096^2 (standing wave a0 = 300 + 1% noise), 16M electrons,
+    # 1000 steps, sorted by 32 x 32-cell tile every 8 steps
+    wl = W.yee2d(nsteps=1000, seed=1 + rank)
+    ctx = prad.Context(wl.problem_kwargs(), precision=prad.PRAD_FP32,
+                       photon_capacity=1 << 28, max_particles=wl.n, sort_interval=8,
+                       steps_per_launch=8)
+    st = ctx.to_device(wl.state, with_pid=True)
+    ctx.push_emit({k: v[:4096].clone() for k, v in st.items()}, 8)   # warm-up
+    ctx.reset()
+    ctx.drain()
+    secs = 0.0
+    for c in range(10):
+        secs += timed(lambda: ctx.push_emit(st, 100, t0=100 * c))
+        ctx.drain()
+    out["yee2d"] = {"value": wl.n * 1000 / secs, "unit": UNIT,
+                    "workload": "2D Yee 4096^2 FP32 planes, a0=300 standing wave + 1% noise, "
+                                "16777216 electrons in the central 1024^2 cells, 1000 steps, "
+                                "tile sort every 8 steps, table sampler"}
+    ctx.close()
+    del st, wl
+
+    # learned vs table sampler: 2^26 electrons in the CP wave at a0 = 500,
+    # 400 steps from the initial state (the emission-heavy first periods)
+    n4 = 1 << 26
+    wl = W.plane_wave(a0=500.0, n=n4, periods=2, seed=41 + rank)
+    res = {}
+    for name, smp in (("table", prad.PRAD_SAMPLER_TABLE),
+                      ("mlp", prad.PRAD_SAMPLER_MLP_FALLBACK)):
+        if smp != prad.PRAD_SAMPLER_TABLE and params is None:
+            continue
+        ctx = prad.Context(wl.problem_kwargs(), precision=prad.PRAD_FP32, sampler=smp,
+                           photon_capacity=1 << 30, max_particles=n4, steps_per_launch=25)
+        if smp != prad.PRAD_SAMPLER_TABLE:
+            ctx.mlp_set_weights(params)
+        st = ctx.to_device(wl.state)
+        ctx.push_emit({k: v[:1 << 16].clone() for k, v in st.items()}, 25)   # warm-up
+        ctx.reset()
+        ctx.drain()
+        secs = 0.0
+        for c in range(16):
+            secs += timed(lambda: ctx.push_emit(st, 25, t0=25 * c))
+            ctx.drain()
+        res[name] = n4 * 400 / secs
+        ctx.close()
+        del st
+    out["planewave_a0_500_2e26"] = {
+        "table": res.get("table"), "mlp": res.get("mlp"), "unit": UNIT,
+        "mlp_vs_table": (res["mlp"] / res["table"]) if "mlp" in res else None,
+        "workload": "CP plane wave a0=500, 67108864 electrons, 400 steps, 25 steps per launch"}
+    del wl
+
+    # batched: 256 ensembles, sizes log-uniform in [1e3, 1e6], a0 ~ U[50, 500],
+    # plane wave or constant B, 500 steps, one persistent kernel per call,
+    # captured graph, autotuned launch shape
+    es = W.ensembles(count=256, nsteps=500, seed=1 + rank)
+    total = int(sum(w.n for w in es.workloads))
+    res = {}
+    for name, smp in (("table", prad.PRAD_SAMPLER_TABLE),
+                      ("mlp", prad.PRAD_SAMPLER_MLP_FALLBACK)):
+        if smp != prad.PRAD_SAMPLER_TABLE and params is None:
+            continue
+        s2 = torch.cuda.Stream()
+        with torch.cuda.stream(s2):
+            ctx = prad.Context(es.workloads[0].problem_kwargs(), precision=prad.PRAD_FP32,
+                               sampler=smp, photon_capacity=int(0.1 * total * 100) + (1 << 20),
+                               max_particles=total, use_graph=True, stream=s2)
+            if smp != prad.PRAD_SAMPLER_TABLE:
+                ctx.mlp_set_weights(params)
+            sts = [ctx.to_device(w.state) for w in es.workloads]
+            probs = [w.problem_kwargs() for w in es.workloads]
+            ctx.autotune_batch(ctx.ensembles(sts, probs), probe_steps=10, sample=4096)
+            secs = 0.0
+            for c in range(5):
+                ens = ctx.ensembles(sts, probs, t0=100 * c)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(s2)
+                ctx.push_emit_batch(ens, 100)
+                b.record(s2)
+                b.synchronize()
+                secs += a.elapsed_time(b) / 1e3
+                ctx.drain()
+            res[name] = total * 500 / secs
+            ctx.close()
+            del sts
+    out["batched_256"] = {
+        "table": res.get("table"), "mlp": res.get("mlp"), "unit": UNIT,
+        "mlp_vs_table": (res["mlp"] / res["table"]) if "mlp" in res else None,
+        "workload": f"256 ensembles, {total} electrons, 500 steps in 5 graph-replayed calls, "
+                    "autotuned persistent kernel"}
+    return out
 
 
 # ---------------------------------------------------------------- GPU arm
@@ -470,6 +580,13 @@ def run_prad(args):
                "mlp_fallback": mst["mlp_fallback"], "sampler": "MLP_FALLBACK (direct scheme)"}
         ctx_m.close()
 
+    others = None
+    if not args.no_other:
+        ctx.close()
+        del init, work
+        torch.cuda.empty_cache()
+        others = other_workloads(prad, W, torch, None if args.no_mlp else params, rank)
+
     cb = None
     if rank == 0 and ws == 1:
         cb = cpu_baseline(args, budget_s=args.cpu_seconds)
@@ -488,7 +605,7 @@ def run_prad(args):
                            "photon_records_per_step": records / args.steps,
                            "parallelism": f"independent particles, {ws} GPU(s)"},
                 "roofline": roofline, "roofline_stream": roofline_stream,
-                "mlp_sampler": mlp, "cpu_baseline": cb, "e2e": e2e,
+                "mlp_sampler": mlp, "other_workloads": others, "cpu_baseline": cb, "e2e": e2e,
                 "gpu_launches": args.steps * len(a0s) * launches_per_run,
                 "clocks": ck}
         print(json.dumps(line), flush=True)

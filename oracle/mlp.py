@@ -7,15 +7,17 @@ arXiv:1409.5574).  Model definition (as documented with the C ABI):
   features  f0 = logit(r) / 8
             f1 = clip((ln gamma - 5.7565) / 3.4539, -1, 1)
             f2 = clip((ln(omega_c dt) - 8.2) / 11.6, -1, 1)
-  layer 1   z1 = W1 f + b1,  h1 = bf16(silu(z1))        (W1 in BF16)
-  layer 2   z2 = W2 h1 + b2, h2 = silu(z2)              (W2 in BF16)
+  layer 1   z1 = W1 f + b1,  h1 = f16(silu(z1))         (W1 in BF16)
+  layer 2   z2 = W2 h1 + b2, h2 = f16(silu(z2))         (W2 in BF16)
   layer 3   o  = W3 h2 + b3                             (W3 in BF16)
   output    ln x = prior(r) + o,  prior(r) = ln(-ln(1 - r)) + 2 (1 - r) ln r
   loss      mean over samples of w (o - (ln x_target - prior(r)))^2,
             w = (1 + x_target) / 1.308 (energy weighting, mean 1)
 
 Parameter vector: W1[64][3], b1[64], W2[64][64], b2[64], W3[64], b3 (4481).
-Everything here is FP64 except the two BF16 roundings the definition names;
+Everything here is FP64 except the roundings the definition names (weights
+to BF16, activations to IEEE half; W2 and W3 enter the f16 products as the
+half-precision images of their BF16 values, identical for |w| >= 2^-17);
 gradients treat the roundings as identity (straight-through).  Only tests
 import this module.
 """
@@ -38,6 +40,11 @@ def bf16(x):
     u = a.view(np.uint32).astype(np.uint64)
     u = (u + 0x7FFF + ((u >> 16) & 1)) >> 16 << 16
     return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def f16(x):
+    """Round to the nearest IEEE half (ties to even)."""
+    return np.asarray(x, dtype=np.float64).astype(np.float16).astype(np.float64)
 
 
 def unpack(p):
@@ -66,12 +73,14 @@ def silu_grad(z):
 
 def forward(p, f, rounding=True):
     W1, b1, W2, b2, W3, b3 = unpack(p)
-    rd = bf16 if rounding else (lambda v: np.asarray(v, dtype=np.float64))
-    W1r, W2r, W3r = rd(W1), rd(W2), rd(W3)
+    ident = lambda v: np.asarray(v, dtype=np.float64)  # noqa: E731
+    rw = bf16 if rounding else ident
+    rh = f16 if rounding else ident
+    W1r, W2r, W3r = rw(W1), rh(rw(W2)), rh(rw(W3))
     z1 = f @ W1r.T + b1
-    h1 = rd(silu(z1))
+    h1 = rh(silu(z1))
     z2 = h1 @ W2r.T + b2
-    h2 = silu(z2)
+    h2 = rh(silu(z2))
     o = h2 @ W3r + b3
     return o, (f, z1, h1, z2, h2, W1r, W2r, W3r)
 

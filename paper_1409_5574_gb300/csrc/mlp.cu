@@ -1,7 +1,7 @@
 // Training and evaluation kernels of the learned inverse-CDF sampler
 // (mlp_device.cuh): sample generation with the device G^-1 table, a fused
-// forward + backward pass per block of 128 samples (BF16 tensor-core MMA for
-// the 64 x 64 layer and its two gradient products), per-block partial
+// forward + backward pass per block of 128 samples (tensor-core MMAs for the
+// 64 x 64 layer: f16 forward, BF16 gradient products), per-block partial
 // gradients, and a deterministic reduction + Adam update.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -130,37 +130,43 @@ __global__ void __launch_bounds__(kTThreads)
   // layer 2 forward, warp w: samples 16w .. 16w + 15
   {
     const int s0 = 16 * warp;
+    // h1 = f16(silu(z1)) in packed f16 arithmetic, as in the evaluator
     uint32_t a[4][4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int j = 16 * q + 2 * t;
-      a[q][0] = pack_bf16x2(silu(S.z1[s0 + g][j]), silu(S.z1[s0 + g][j + 1]));
-      a[q][1] = pack_bf16x2(silu(S.z1[s0 + g + 8][j]), silu(S.z1[s0 + g + 8][j + 1]));
-      a[q][2] = pack_bf16x2(silu(S.z1[s0 + g][j + 8]), silu(S.z1[s0 + g][j + 9]));
-      a[q][3] = pack_bf16x2(silu(S.z1[s0 + g + 8][j + 8]), silu(S.z1[s0 + g + 8][j + 9]));
+      a[q][0] = silu_f16x2(S.z1[s0 + g][j], S.z1[s0 + g][j + 1]);
+      a[q][1] = silu_f16x2(S.z1[s0 + g + 8][j], S.z1[s0 + g + 8][j + 1]);
+      a[q][2] = silu_f16x2(S.z1[s0 + g][j + 8], S.z1[s0 + g][j + 9]);
+      a[q][3] = silu_f16x2(S.z1[s0 + g + 8][j + 8], S.z1[s0 + g + 8][j + 9]);
     }
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt) {
-      float c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-      const __nv_bfloat16* wrow = S.net.w2 + (8 * nt + g) * kW2Ld + 2 * t;
+      const int j0 = 8 * nt + 2 * t;
+      float c[4] = {S.net.b2[j0], S.net.b2[j0 + 1], S.net.b2[j0], S.net.b2[j0 + 1]};
+      const __half* wrow = S.net.w2h + (8 * nt + g) * kW2Ld + 2 * t;
 #pragma unroll
       for (int q = 0; q < 4; ++q)
-        mma_bf16_16816(c, a[q][0], a[q][1], a[q][2], a[q][3],
-                       *reinterpret_cast<const uint32_t*>(wrow + 16 * q),
-                       *reinterpret_cast<const uint32_t*>(wrow + 16 * q + 8));
-      const int j0 = 8 * nt + 2 * t;
-      S.z2[s0 + g][j0] = c[0] + S.net.b2[j0];
-      S.z2[s0 + g][j0 + 1] = c[1] + S.net.b2[j0 + 1];
-      S.z2[s0 + g + 8][j0] = c[2] + S.net.b2[j0];
-      S.z2[s0 + g + 8][j0 + 1] = c[3] + S.net.b2[j0 + 1];
+        mma_f16_16816(c, a[q][0], a[q][1], a[q][2], a[q][3],
+                      *reinterpret_cast<const uint32_t*>(wrow + 16 * q),
+                      *reinterpret_cast<const uint32_t*>(wrow + 16 * q + 8));
+      S.z2[s0 + g][j0] = c[0];
+      S.z2[s0 + g][j0 + 1] = c[1];
+      S.z2[s0 + g + 8][j0] = c[2];
+      S.z2[s0 + g + 8][j0 + 1] = c[3];
     }
   }
   __syncthreads();
-  // output, loss and dL/do per sample
+  // output (h2 = f16(silu(z2)) as in the evaluator), loss and dL/do per sample
   if (threadIdx.x < kTB) {
     const int s = threadIdx.x;
     float o = S.net.b3;
-    for (int j = 0; j < kHid; ++j) o = fmaf(S.net.w3[j], silu(S.z2[s][j]), o);
+    for (int j = 0; j < kHid; j += 2) {
+      const uint32_t hh = silu_f16x2(S.z2[s][j], S.z2[s][j + 1]);
+      const float2 h2 = __half22float2(*reinterpret_cast<const __half2*>(&hh));
+      o = fmaf(S.net.w3[j], h2.x, o);
+      o = fmaf(S.net.w3[j + 1], h2.y, o);
+    }
     const bool valid = S.x[s][3] == 0.0f;
     const float diff = o - S.tgt[s];
     const float wgt = S.wgt[s];
@@ -330,6 +336,81 @@ __global__ void __launch_bounds__(256) k_mlp_eval(MlpDev dev, const float* __res
   }
 }
 
+// Energies of the learned sampler's deferred records (MlpFinishArgs): each
+// warp takes 32 consecutive records at a time, one row per lane for the
+// features, the output and the writes, evaluated as two 16-row tiles.  The
+// last block to finish marks the range as done.
+#ifndef PRAD_FINISH_MINB
+#define PRAD_FINISH_MINB 4
+#endif
+__global__ void __launch_bounds__(256, PRAD_FINISH_MINB) k_mlp_finish(const MlpFinishArgs a) {
+  __shared__ MlpSmem S;
+  mlp_load_smem(S, a.mlp);
+  __syncthreads();
+  const unsigned long long cur = a.counters[kCursor];
+  const unsigned long long cap = static_cast<unsigned long long>(a.cap);
+  const unsigned long long end = cur < cap ? cur : cap;
+  const unsigned long long beg = a.counters[kMlpDone];
+  const int lane = threadIdx.x & 31, g = lane >> 2;
+  const unsigned long long warps = static_cast<unsigned long long>(gridDim.x) * (blockDim.x >> 5);
+  const unsigned long long wid =
+      static_cast<unsigned long long>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  uint32_t fb = 0;
+  for (unsigned long long base = beg + 32ull * wid; base < end; base += 32ull * warps) {
+    const unsigned long long row = base + static_cast<unsigned>(lane);
+    const bool mine = row < end;
+    float4 pd = make_float4(0.5f, 1.0f, 0.0f, __int_as_float(-1));
+    if (mine) pd = a.pend[row];
+    const float3 f = mlp_features(pd.x, pd.y, pd.z * a.wdt_per_eps);
+    float o_row = 0.0f;
+#pragma unroll 1
+    for (int h = 0; h < 2; ++h) {
+      // tile h: rows 16h .. 16h + 15 (lanes 16h ..); lane (g, t) needs rows g, g + 8
+      float3 flo, fhi;
+      flo.x = __shfl_sync(0xffffffffu, f.x, 16 * h + g);
+      flo.y = __shfl_sync(0xffffffffu, f.y, 16 * h + g);
+      flo.z = __shfl_sync(0xffffffffu, f.z, 16 * h + g);
+      fhi.x = __shfl_sync(0xffffffffu, f.x, 16 * h + g + 8);
+      fhi.y = __shfl_sync(0xffffffffu, f.y, 16 * h + g + 8);
+      fhi.z = __shfl_sync(0xffffffffu, f.z, 16 * h + g + 8);
+      float olo, ohi;
+      mlp_tile16(S, flo, fhi, olo, ohi);
+      // row L of the tile lives in lane 4 (L % 8), in olo (L < 8) or ohi
+      const float vlo = __shfl_sync(0xffffffffu, olo, (lane & 7) * 4);
+      const float vhi = __shfl_sync(0xffffffffu, ohi, (lane & 7) * 4);
+      if ((lane >> 4) == h) o_row = (lane & 8) ? vhi : vlo;
+    }
+    if (mine) {
+      float x = __expf(o_row + mlp_prior(pd.x));
+      // uniforms outside the trained range always take the G^-1 table
+      const bool tail = pd.x < kRMin || pd.x > kRMax;
+      const bool ok = x > 0.0f && x < 80.0f;  // also false for NaN
+      if (tail || (a.check_output && !ok)) {
+        x = __expf(ginv_ln(a.ginv, pd.x));
+        ++fb;
+      } else if (!ok) {
+        x = 0.0f;  // no fallback requested: an invalid draw carries no energy
+      }
+      const float eps = x * pd.z;
+      a.eps[row] = eps;
+      const int li = __float_as_int(pd.w);
+      if (li >= 0)
+        atomicAdd(a.led_emit + li, static_cast<double>(a.weight[row]) * static_cast<double>(eps));
+    }
+  }
+  fb = __reduce_add_sync(0xffffffffu, fb);
+  if (lane == 0 && fb) atomicAdd(a.counters + kMlpFallback, static_cast<unsigned long long>(fb));
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned long long t = atomicAdd(a.counters + kMlpBlocks, 1ull);
+    if (t == gridDim.x - 1ull) {
+      a.counters[kMlpDone] = end;
+      a.counters[kMlpBlocks] = 0ull;
+    }
+  }
+}
+
 __global__ void k_ginv_eval(const float* __restrict__ tab, const float* __restrict__ r,
                             float* __restrict__ out, int64_t n) {
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
@@ -380,6 +461,18 @@ cudaError_t launch_mlp_eval(const MlpDev& dev, const float* in, float* out, int6
   const int grid = static_cast<int>(want < 4096 ? (want > 0 ? want : 1) : 4096);
   k_mlp_eval<<<grid, 256, 0, s>>>(dev, in, out, n);
   return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_finish(const MlpFinishArgs& a, int grid, cudaStream_t s) {
+  k_mlp_finish<<<grid, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+int mlp_finish_blocks_per_sm() {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_mlp_finish, 256, 0) != cudaSuccess)
+    return 1;
+  return nb > 0 ? nb : 1;
 }
 
 cudaError_t launch_ginv_eval(const float* tab, const float* r, float* out, int64_t n,

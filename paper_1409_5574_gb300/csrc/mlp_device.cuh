@@ -8,12 +8,16 @@
 // (r, gamma, omega_c dt); in the classical model G does not depend on gamma
 // or omega_c dt, and the network is trained to ignore them.
 //
-// Numerics (shared by training, evaluation and the fused push kernel):
+// Numerics (shared by training and evaluation):
 //   features f = (logit(r)/8, clamp((ln gamma - c1)/s1), clamp((ln w - c2)/s2))
-//   z1 = W1 f + b1 (BF16 weights, FP32 accumulate);  h1 = bf16(silu(z1))
-//   z2 = W2 h1 + b2 (BF16 x BF16 tensor-core MMA, FP32 accumulate)
-//   h2 = silu(z2);  o = W3 h2 + b3 (FP32);  ln x = prior(r) + kOutScale * o
-// The tile evaluator forms z1 on the tensor cores as well: each feature and
+//   z1 = W1 f + b1 (BF16 weights, FP32 accumulate);  h1 = f16(silu(z1))
+//   z2 = W2 h1 + b2 (tensor-core MMA, FP32 accumulate);  h2 = f16(silu(z2))
+//   o = W3 h2 + b3 (FP32 accumulate);  ln x = prior(r) + kOutScale * o
+// The weights are stored in BF16; a BF16 value is exact in f16 (11 > 8
+// significant bits) down to 2^-17 in magnitude, so the f16 x f16 MMAs of
+// layers 2 and 3 multiply exactly the BF16 weights.  SiLU runs in packed f16
+// arithmetic (tanh.approx.f16x2), within ~1 f16 ulp of f16(silu(z)).  The
+// tile evaluator forms z1 on the tensor cores as well: each feature and
 // each bias enters as the sum of two BF16 numbers (high part + rounded
 // remainder, 2^-17 relative), so z1 agrees with the FP32 form to ~1e-6.
 // with the fixed prior(r) = ln(-ln(1 - r)) + 2 (1 - r) ln r, which carries
@@ -22,8 +26,11 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <cstddef>
 
 namespace prad {
 
@@ -64,7 +71,16 @@ struct MlpSmem {
   // features' low parts), k = 6, 7 the high and low BF16 parts of b1[j],
   // k >= 8 zero.  w1f[lane][nt] holds the lane's b0 register of n-tile nt.
   uint32_t w1f[32][8];
+  __half w2h[kHid * kW2Ld];  // W2 in f16 (exact images of the BF16 values)
+  // layer 3 as the B operand (K = 64 x N = 8, W3 in column 0, zero
+  // elsewhere): w3f[lane][2q + u] = the lane's b_u register of k-step q
+  uint32_t w3f[32][8];
 };
+
+static_assert(sizeof(MlpSmem) % 16 == 0 && offsetof(MlpSmem, w2) % 16 == 0 &&
+                  offsetof(MlpSmem, w1f) % 16 == 0 && offsetof(MlpSmem, w2h) % 16 == 0 &&
+                  offsetof(MlpSmem, w3f) % 16 == 0,
+              "16-byte alignment of the network image (uint4 and ldmatrix reads)");
 
 // Device copy of the network: FP32 master parameters and the BF16 W2.
 struct MlpDev {
@@ -110,6 +126,33 @@ __device__ __forceinline__ void mlp_load_smem(MlpSmem& s, const MlpDev& d) {
     }
     s.w1f[lane][nt] = pack_bf16x2(v[0], v[1]);
   }
+  for (int e = threadIdx.x; e < kHid * kHid; e += blockDim.x) {
+    const int j = e / kHid, i = e - j * kHid;
+    s.w2h[j * kW2Ld + i] = __float2half_rn(__bfloat162float(d.w2[e]));
+  }
+  for (int e = threadIdx.x; e < 32 * 8; e += blockDim.x) {
+    const int lane = e >> 3, q = (e & 7) >> 1, u = e & 1;
+    const int g = lane >> 2, t = lane & 3;
+    const int i0 = 16 * q + 8 * u + 2 * t;
+    uint32_t v = 0u;
+    if (g == 0) {
+      const __half2 h = __halves2half2(__float2half_rn(bf16_round(d.params[kOffW3 + i0])),
+                                       __float2half_rn(bf16_round(d.params[kOffW3 + i0 + 1])));
+      v = *reinterpret_cast<const uint32_t*>(&h);
+    }
+    s.w3f[lane][e & 7] = v;
+  }
+}
+
+// SiLU of two FP32 values in packed f16 arithmetic, h = hz + hz tanh(hz) with
+// hz = z / 2; returns (silu(z0), silu(z1)) as f16x2 (z0 in the low half).
+__device__ __forceinline__ uint32_t silu_f16x2(float z0, float z1) {
+  uint32_t zz, hz, th, h;
+  asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(zz) : "f"(z1), "f"(z0));
+  asm("mul.rn.f16x2 %0, %1, %2;" : "=r"(hz) : "r"(zz), "r"(0x38003800u));
+  asm("tanh.approx.f16x2 %0, %1;" : "=r"(th) : "r"(hz));
+  asm("fma.rn.f16x2 %0, %1, %2, %3;" : "=r"(h) : "r"(hz), "r"(th), "r"(hz));
+  return h;
 }
 
 __device__ __forceinline__ float silu(float z) {
@@ -137,6 +180,18 @@ __device__ __forceinline__ void mma_bf16_16816(float c[4], uint32_t a0, uint32_t
                                                uint32_t b1) {
   asm volatile(
       "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+      "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// D = A(16x16, row) * B(16x8, col) + C, f16 inputs, FP32 accumulate (the
+// fragment layout of mma_bf16_16816).
+__device__ __forceinline__ void mma_f16_16816(float c[4], uint32_t a0, uint32_t a1,
+                                              uint32_t a2, uint32_t a3, uint32_t b0,
+                                              uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 "
       "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
       : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
       : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
@@ -175,13 +230,14 @@ __device__ __forceinline__ uint32_t mlp_feature_pair(float3 f, int t) {
 
 // Warp-collective: the 16 rows of a tile are the features of lanes' rows
 // g and g+8 (f_lo, f_hi); returns kOutScale * o (ln x minus the prior) of rows
-// g (out_lo) and g+8 (out_hi), valid in every lane of the row's group.
+// g (out_lo) and g+8 (out_hi), valid in lane 4g.  Every layer runs on the
+// tensor cores; an accumulator fragment of one layer, after SiLU, is the A
+// fragment of the next (n-tiles 2q, 2q+1 -> k-step q).
 __device__ __forceinline__ void mlp_tile16(const MlpSmem& S, float3 f_lo, float3 f_hi,
                                            float& out_lo, float& out_hi) {
   const int lane = threadIdx.x & 31;
   const int t = lane & 3;
-  // layer 1 on the tensor cores; its accumulator fragments are exactly the
-  // A fragments of layer 2 (n-tiles 2q, 2q+1 -> k-step q)
+  // layer 1 (BF16, split features and bias)
   const uint32_t fa0 = mlp_feature_pair(f_lo, t), fa1 = mlp_feature_pair(f_hi, t);
   const uint4 wlo = *reinterpret_cast<const uint4*>(&S.w1f[lane][0]);
   const uint4 whi = *reinterpret_cast<const uint4*>(&S.w1f[lane][4]);
@@ -192,41 +248,43 @@ __device__ __forceinline__ void mlp_tile16(const MlpSmem& S, float3 f_lo, float3
     float c0[4] = {0.0f, 0.0f, 0.0f, 0.0f}, c1[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     mma_bf16_16816(c0, fa0, fa1, 0u, 0u, wb[2 * q], 0u);
     mma_bf16_16816(c1, fa0, fa1, 0u, 0u, wb[2 * q + 1], 0u);
-    a[q][0] = pack_bf16x2(silu(c0[0]), silu(c0[1]));
-    a[q][1] = pack_bf16x2(silu(c0[2]), silu(c0[3]));
-    a[q][2] = pack_bf16x2(silu(c1[0]), silu(c1[1]));
-    a[q][3] = pack_bf16x2(silu(c1[2]), silu(c1[3]));
+    a[q][0] = silu_f16x2(c0[0], c0[1]);
+    a[q][1] = silu_f16x2(c0[2], c0[3]);
+    a[q][2] = silu_f16x2(c1[0], c1[1]);
+    a[q][3] = silu_f16x2(c1[2], c1[3]);
   }
-  // layer 2: 8 output column tiles of 8 units, K = 64 in 4 steps of 16; the
-  // accumulators start from the bias
+  // layers 2 and 3 (f16): the accumulators start from b2; the SiLU of each
+  // pair of n-tiles is one k-step of layer 3
+  const uint4 vlo = *reinterpret_cast<const uint4*>(&S.w3f[lane][0]);
+  const uint4 vhi = *reinterpret_cast<const uint4*>(&S.w3f[lane][4]);
+  const uint32_t w3b[8] = {vlo.x, vlo.y, vlo.z, vlo.w, vhi.x, vhi.y, vhi.z, vhi.w};
   const int m = lane >> 3, r = lane & 7;
-  float acc_lo = 0.0f, acc_hi = 0.0f;
+  float o[4] = {S.b3, 0.0f, S.b3, 0.0f};
 #pragma unroll
-  for (int nt = 0; nt < 8; ++nt) {
-    const int j0 = 8 * nt + 2 * t;
-    const float2 bb = *reinterpret_cast<const float2*>(&S.b2[j0]);
-    float c[4] = {bb.x, bb.y, bb.x, bb.y};
+  for (int q3 = 0; q3 < 4; ++q3) {
+    uint32_t h[4];
 #pragma unroll
-    for (int qq = 0; qq < 4; qq += 2) {
-      uint32_t b[4];
-      ldmatrix_x4(b, S.w2 + (8 * nt + r) * kW2Ld + 16 * (qq + (m >> 1)) + 8 * (m & 1));
-      mma_bf16_16816(c, a[qq][0], a[qq][1], a[qq][2], a[qq][3], b[0], b[1]);
-      mma_bf16_16816(c, a[qq + 1][0], a[qq + 1][1], a[qq + 1][2], a[qq + 1][3], b[2], b[3]);
+    for (int u = 0; u < 2; ++u) {
+      const int nt = 2 * q3 + u;
+      const float2 bb = *reinterpret_cast<const float2*>(&S.b2[8 * nt + 2 * t]);
+      float c[4] = {bb.x, bb.y, bb.x, bb.y};
+#pragma unroll
+      for (int qq = 0; qq < 4; qq += 2) {
+        uint32_t b[4];
+        ldmatrix_x4(b, S.w2h + (8 * nt + r) * kW2Ld + 16 * (qq + (m >> 1)) + 8 * (m & 1));
+        mma_f16_16816(c, a[qq][0], a[qq][1], a[qq][2], a[qq][3], b[0], b[1]);
+        mma_f16_16816(c, a[qq + 1][0], a[qq + 1][1], a[qq + 1][2], a[qq + 1][3], b[2], b[3]);
+      }
+      h[2 * u] = silu_f16x2(c[0], c[1]);      // row g
+      h[2 * u + 1] = silu_f16x2(c[2], c[3]);  // row g + 8
     }
-    // c0,c1: row g, units j0, j0+1; c2,c3: row g + 8
-    const float2 ww = *reinterpret_cast<const float2*>(&S.w3[j0]);
-    acc_lo = fmaf(ww.x, silu(c[0]), acc_lo);
-    acc_lo = fmaf(ww.y, silu(c[1]), acc_lo);
-    acc_hi = fmaf(ww.x, silu(c[2]), acc_hi);
-    acc_hi = fmaf(ww.y, silu(c[3]), acc_hi);
+    // k-step q3 of layer 3: a0 = (g, n-tile 2q3), a1 = (g+8, 2q3),
+    // a2 = (g, 2q3+1), a3 = (g+8, 2q3+1)
+    mma_f16_16816(o, h[0], h[1], h[2], h[3], w3b[2 * q3], w3b[2 * q3 + 1]);
   }
-  // layer 3: reduce the partial dot products over the 4 lanes of the group
-  acc_lo += __shfl_xor_sync(0xffffffffu, acc_lo, 1);
-  acc_lo += __shfl_xor_sync(0xffffffffu, acc_lo, 2);
-  acc_hi += __shfl_xor_sync(0xffffffffu, acc_hi, 1);
-  acc_hi += __shfl_xor_sync(0xffffffffu, acc_hi, 2);
-  out_lo = kOutScale * (acc_lo + S.b3);
-  out_hi = kOutScale * (acc_hi + S.b3);
+  // column 0 of the output tile: rows g (o[0]) and g + 8 (o[2]) in lane 4g
+  out_lo = kOutScale * o[0];
+  out_hi = kOutScale * o[2];
 }
 
 // G^-1 table: ln x at nodes uniform in logit(r) on [-kGiL, kGiL], linear

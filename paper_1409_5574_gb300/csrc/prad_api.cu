@@ -52,6 +52,8 @@ struct prad_ctx {
   float* d_ph[8] = {nullptr};
   uint32_t* d_pid = nullptr;
   uint32_t* d_step = nullptr;
+  float4* d_pend = nullptr;      // learned sampler: per-slot network inputs
+  int finish_grid = 0;           // blocks of the learned sampler's finishing kernel
   // counters, ledgers, reduction scratch
   unsigned long long* d_cnt = nullptr;
   double* d_led_emit = nullptr;
@@ -318,6 +320,25 @@ MlpDev mlp_dev(const prad_ctx* c) {
   return d;
 }
 
+// Learned sampler: energies and ledger entries of the records appended
+// since the last call (one launch after each push or batch call).
+int mlp_finish(prad_ctx* c, double* led_base) {
+  if (c->cfg.sampler == PRAD_SAMPLER_TABLE) return PRAD_OK;
+  MlpFinishArgs a;
+  a.mlp = mlp_dev(c);
+  a.ginv = c->d_ginv;
+  a.eps = c->d_ph[6];
+  a.weight = c->d_ph[7];
+  a.pend = c->d_pend;
+  a.counters = c->d_cnt;
+  a.led_emit = led_base;
+  a.cap = c->cfg.photon_capacity;
+  a.wdt_per_eps = static_cast<float>(c->dtn / c->eps_r);
+  a.check_output = c->cfg.sampler == PRAD_SAMPLER_MLP_FALLBACK;
+  CK(c, launch_mlp_finish(a, c->finish_grid, c->stream));
+  return PRAD_OK;
+}
+
 template <typename R>
 void fill_common(const prad_ctx* c, StepParams<R>& p, const prad_fields& f);
 
@@ -355,8 +376,11 @@ void fill_common(const prad_ctx* c, StepParams<R>& p, const prad_fields& f) {
   p.pnx = c->d_ph[3]; p.pny = c->d_ph[4]; p.pnz = c->d_ph[5];
   p.peps = c->d_ph[6]; p.pw = c->d_ph[7];
   p.ppid = c->d_pid; p.pstep = c->d_step;
+  p.ppend = c->d_pend;
   p.cap = c->cfg.photon_capacity;
   p.counters = c->d_cnt;
+  p.led_off = 0;
+  p.led_base = c->d_led_emit;
   p.cp_dt = static_cast<R>(5.0 * std::sqrt(3.0) / 6.0 * c->alpha * dtn);
   p.mlp = mlp_dev(c);
   p.ginv = c->d_ginv;
@@ -504,6 +528,7 @@ int push_emit_t(prad_ctx* c, const prad_particles* pp, int64_t n,
   p.led_emit = c->d_led_emit + pp->ledger_offset;
   p.led_ll = c->d_led_ll + pp->ledger_offset;
   p.led_n = c->cfg.max_particles - pp->ledger_offset;
+  p.led_off = pp->ledger_offset;
   p.pid = pp->pid;
   if (pp->pid && !aligned(pp->pid, 4))
     return fail(c, PRAD_ERR_ARG, "push_emit: misaligned pid array");
@@ -553,7 +578,7 @@ int push_emit_t(prad_ctx* c, const prad_particles* pp, int64_t n,
     CK(c, launch_push_emit<R>(p, c->fields.kind, c->cfg.sampler, grid, block, c->stream));
     done += m;
   }
-  return PRAD_OK;
+  return mlp_finish(c, c->d_led_emit);
 }
 
 }  // namespace
@@ -627,6 +652,10 @@ int prad_init(prad_ctx** out, const prad_config* cfg) {
   for (int k = 0; k < 8; ++k) CKI(cudaMalloc(&c->d_ph[k], cap * sizeof(float)));
   CKI(cudaMalloc(&c->d_pid, cap * sizeof(uint32_t)));
   CKI(cudaMalloc(&c->d_step, cap * sizeof(uint32_t)));
+  if (cfg->sampler != PRAD_SAMPLER_TABLE) {
+    CKI(cudaMalloc(&c->d_pend, cap * sizeof(float4)));
+    c->finish_grid = c->num_sms * mlp_finish_blocks_per_sm();
+  }
   CKI(cudaMalloc(&c->d_cnt, kNumCounters * sizeof(unsigned long long)));
   CKI(cudaMemset(c->d_cnt, 0, kNumCounters * sizeof(unsigned long long)));
   const size_t np = static_cast<size_t>(cfg->max_particles);
@@ -669,6 +698,7 @@ int prad_destroy(prad_ctx* c) {
   for (int k = 0; k < 8; ++k) cudaFree(c->d_ph[k]);
   cudaFree(c->d_pid);
   cudaFree(c->d_step);
+  cudaFree(c->d_pend);
   cudaFree(c->d_cnt);
   cudaFree(c->d_led_emit);
   cudaFree(c->d_led_ll);
@@ -763,6 +793,7 @@ int prad_get_photons(prad_ctx* c, prad_photons* out, int64_t cap, int64_t* n_out
   }
   if (drain) {
     CK(c, cudaMemsetAsync(c->d_cnt + kCursor, 0, sizeof(unsigned long long), c->stream));
+    CK(c, cudaMemsetAsync(c->d_cnt + kMlpDone, 0, sizeof(unsigned long long), c->stream));
     c->drained_records += held;
     c->drained_dropped += dropped;
   }
@@ -896,9 +927,11 @@ int64_t build_batch(prad_ctx* c, const prad_ensemble* ens, int n_ens, int chunk,
     p.uz = static_cast<float*>(e.p.uz);
     p.w = static_cast<const float*>(e.p.w);
     p.pid = e.p.pid;
-    p.led_emit = (led_emit ? led_emit : c->d_led_emit) + e.p.ledger_offset;
+    p.led_base = led_emit ? led_emit : c->d_led_emit;
+    p.led_emit = p.led_base + e.p.ledger_offset;
     p.led_ll = (led_ll ? led_ll : c->d_led_ll) + e.p.ledger_offset;
     p.led_n = c->cfg.max_particles - e.p.ledger_offset;
+    p.led_off = e.p.ledger_offset;
     p.n = e.n;
     p.pid0 = e.p.pid0;
     p.ensemble = e.ensemble;
@@ -955,7 +988,7 @@ int issue_batch(prad_ctx* c, int n_ens, int64_t items, int32_t nsteps, int chunk
     CK(c, launch_push_emit_batch(bp, c->cfg.sampler, grid, block, c->stream));
     done += m;
   }
-  return PRAD_OK;
+  return mlp_finish(c, c->h_batch.empty() ? c->d_led_emit : c->h_batch[0].led_base);
 }
 
 int batch_chunk_of(const prad_ctx* c) { return c->cfg.batch_chunk > 0 ? c->cfg.batch_chunk : 2048; }

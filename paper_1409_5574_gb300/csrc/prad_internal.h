@@ -29,7 +29,9 @@ enum Counter {
   kNan = 4,
   kMlpFallback = 5,
   kStatus = 6,
-  kNumCounters = 8
+  kMlpDone = 7,    // learned sampler: records [0, kMlpDone) have their energy
+  kMlpBlocks = 8,  // learned sampler: blocks of the finishing kernel done
+  kNumCounters = 16
 };
 
 struct alignas(32) Coef4d {
@@ -83,8 +85,11 @@ struct StepParams {
   // photons
   float *px, *py, *pz, *pnx, *pny, *pnz, *peps, *pw;
   uint32_t *ppid, *pstep;
+  float4* ppend;              // learned sampler: (r, gamma, eps_c, ledger index) per slot
   int64_t cap;
   unsigned long long* counters;
+  int64_t led_off;            // ledger entry of id pid0 in the context's ledger
+  double* led_base;           // the context's emitted-energy ledger (entry 0)
   // learned sampler (direct scheme): expected photons per step = cp_dt Omega
   R cp_dt;                    // (5 sqrt3 / 6) alpha dtn
   MlpDev mlp;
@@ -165,6 +170,23 @@ cudaError_t launch_mlp_reduce_adam(const float* partial, int nblocks, const floa
                                    cudaStream_t s);
 cudaError_t launch_mlp_eval(const MlpDev& dev, const float* in, float* out, int64_t n,
                             cudaStream_t s);
+// Energies of the learned sampler's records appended since the last call:
+// records [counters[kMlpDone], min(cursor, cap)) get x from the network (table
+// fallback), eps = x eps_c, and their emitted-energy ledger entries.
+struct MlpFinishArgs {
+  MlpDev mlp;
+  const float* ginv;
+  float* eps;                 // record energies (written)
+  const float* weight;        // record weights
+  const float4* pend;         // (r, gamma, eps_c, ledger index or -1)
+  unsigned long long* counters;
+  double* led_emit;           // the context's ledger, entry 0
+  int64_t cap;
+  float wdt_per_eps;          // omega_c dt / eps_c = dt / eps_r (normalised)
+  int32_t check_output;       // MLP_FALLBACK: invalid network output -> table
+};
+cudaError_t launch_mlp_finish(const MlpFinishArgs& a, int grid, cudaStream_t s);
+int mlp_finish_blocks_per_sm();
 cudaError_t launch_ginv_eval(const float* tab, const float* r, float* out, int64_t n,
                              cudaStream_t s);
 cudaError_t launch_ledger_reduce(const double* a, const double* b, int64_t n,

@@ -10,7 +10,6 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include <cstddef>
 
 #include "mlp_device.cuh"
 #include "prad_internal.h"
@@ -330,6 +329,7 @@ struct PhotonStage {
   float f[8][kStage];  // x y z nx ny nz eps weight
   uint32_t pid[kStage];
   uint32_t step[kStage];
+  float pend[4][kStage];  // learned sampler: r, gamma, eps_c, ledger index
 };
 
 struct PhotonOut {
@@ -337,8 +337,15 @@ struct PhotonOut {
   uint32_t *pid, *step;
   int64_t cap;
   unsigned long long* cursor;
+  // learned sampler: per-slot payload for the finishing kernel; a record
+  // beyond the capacity takes its energy from the G^-1 table at once
+  float4* pend;
+  const float* ginv;
+  double* led_base;
+  unsigned long long* fallback;
 };
 
+template <bool PEND = false>
 __device__ __forceinline__ void flush_stage(PhotonStage& st, int fill,
                                             const PhotonOut& o) {
   const int lane = threadIdx.x & 31;
@@ -359,20 +366,33 @@ __device__ __forceinline__ void flush_stage(PhotonStage& st, int fill,
       o.f[6][slot] = st.f[6][r]; o.f[7][slot] = st.f[7][r];
       o.pid[slot] = st.pid[r];
       o.step[slot] = st.step[r];
+      if constexpr (PEND)
+        o.pend[slot] = make_float4(st.pend[0][r], st.pend[1][r], st.pend[2][r], st.pend[3][r]);
+    } else if constexpr (PEND) {
+      // dropped record: its energy still enters the ledger
+      const float x = __expf(ginv_ln(o.ginv, st.pend[0][r]));
+      const int li = __float_as_int(st.pend[3][r]);
+      if (li >= 0)
+        atomicAdd(o.led_base + li,
+                  static_cast<double>(st.f[7][r]) * static_cast<double>(x * st.pend[2][r]));
+      atomicAdd(o.fallback, 1ull);
     }
   }
   __syncwarp();
 }
 
 // Warp-collective, with the warp's ballot of `want` already taken (mask != 0).
-// rec = position, mean momentum (normalised at flush), energy, weight.
+// rec = position, mean momentum (normalised at flush), energy, weight;
+// pend (PEND) = the learned sampler's payload.
+template <bool PEND = false>
 __device__ __forceinline__ void stage_photon_mask(PhotonStage& st, int& fill,
                                                   const PhotonOut& o, bool want,
                                                   unsigned mask, const float rec[8],
-                                                  uint32_t pid, uint32_t step) {
+                                                  uint32_t pid, uint32_t step,
+                                                  const float* pend = nullptr) {
   const int cnt = __popc(mask);
   if (fill + cnt > kStage) {
-    flush_stage(st, fill, o);
+    flush_stage<PEND>(st, fill, o);
     fill = 0;
   }
   if (want) {
@@ -382,6 +402,10 @@ __device__ __forceinline__ void stage_photon_mask(PhotonStage& st, int& fill,
     for (int k = 0; k < 8; ++k) st.f[k][pos] = rec[k];
     st.pid[pos] = pid;
     st.step[pos] = step;
+    if constexpr (PEND) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) st.pend[k][pos] = pend[k];
+    }
   }
   fill += cnt;
 }
@@ -455,137 +479,6 @@ struct Counts {
 };
 
 // ---------------------------------------------------------------------------
-// Learned-sampler queue (direct scheme).  Emitting lanes park their emission
-// (uniform r, gamma, omega_c, weight, record geometry, id, step) in the
-// warp's ring of 48-byte entries; every 16 queued emissions the warp computes
-// the 16 rows' features, evaluates the MLP on one 16-row tensor-core tile,
-// then writes the photon records and books the emitted energy.
-// Warp-collective throughout.
-// ---------------------------------------------------------------------------
-constexpr int kQCap = 48;  // >= 15 left over + up to 32 new per step
-struct MlpQueue {
-  // (r, gamma, eps_c, weight), (x, y, z, pid), (dir x, dir y, dir z, step)
-  float4 e[kQCap][3];
-};
-
-struct MlpFlushConst;
-struct MlpWarp {
-  const MlpSmem* net;
-  MlpQueue* q;
-  const MlpFlushConst* kc;
-  int count, head;      // warp-uniform
-};
-
-// `mask` is the warp's ballot of `want` (nonzero).
-__device__ __forceinline__ void mlp_enqueue(MlpWarp& mw, bool want, unsigned mask, float r,
-                                            float gamma, float epsc, float wt,
-                                            const float pos[3], const float dir[3],
-                                            uint32_t pid, uint32_t step) {
-  if (want) {
-    const int lane = threadIdx.x & 31;
-    int k = mw.head + mw.count + __popc(mask & ((1u << lane) - 1u));
-    k -= k >= kQCap ? kQCap : 0;
-    float4* e = mw.q->e[k];
-    e[0] = make_float4(r, gamma, epsc, wt);
-    e[1] = make_float4(pos[0], pos[1], pos[2], __uint_as_float(pid));
-    e[2] = make_float4(dir[0], dir[1], dir[2], __uint_as_float(step));
-  }
-  mw.count += __popc(mask);
-  __syncwarp();
-}
-
-// Block-uniform inputs of the queue flush, kept in shared memory so that
-// the (not inlined) flush takes a handful of arguments.  16-byte aligned
-// size: the float4 queue entries follow it in dynamic shared memory.
-struct alignas(16) MlpFlushConst {
-  PhotonOut pout;
-  const float* ginv;
-  double* led_emit;
-  int64_t led_n;
-  uint32_t pid0;
-  float wdt_per_eps;   // omega_c dt / eps_c = dt / eps_r (normalised)
-  int check_output;    // MLP_FALLBACK: non-finite / out-of-range x -> table
-};
-struct MlpFlushState {
-  int count, head, fill, fallback;
-};
-
-// Evaluate the oldest min(16, count) queued emissions, emit their records
-// and book their energy.  Not inlined: the tile's registers are not live in
-// the step loop, which keeps the loop at the table path's occupancy; the
-// call happens once per 16 emissions of a warp.
-__device__ __noinline__ MlpFlushState mlp_flush_call(const MlpSmem* net, MlpQueue* queue,
-                                                     PhotonStage* stage,
-                                                     const MlpFlushConst* kc,
-                                                     MlpFlushState st) {
-  const int lane = threadIdx.x & 31, g = lane >> 2;
-  const int rows = st.count < 16 ? st.count : 16;
-  const bool mine = lane < rows;
-  int k = st.head + lane;
-  k -= k >= kQCap ? kQCap : 0;
-  float4 e0 = make_float4(0.5f, 1.0f, 0.0f, 0.0f), e1 = e0, e2 = e0;
-  if (mine) {
-    const float4* e = queue->e[k];
-    e0 = e[0]; e1 = e[1]; e2 = e[2];
-  }
-  // features of row `lane`
-  const float3 f = mlp_features(e0.x, e0.y, e0.z * kc->wdt_per_eps);
-  // tile layout: lane (g, t) needs rows g and g + 8
-  float3 flo, fhi;
-  flo.x = __shfl_sync(0xffffffffu, f.x, g);
-  flo.y = __shfl_sync(0xffffffffu, f.y, g);
-  flo.z = __shfl_sync(0xffffffffu, f.z, g);
-  fhi.x = __shfl_sync(0xffffffffu, f.x, g + 8);
-  fhi.y = __shfl_sync(0xffffffffu, f.y, g + 8);
-  fhi.z = __shfl_sync(0xffffffffu, f.z, g + 8);
-  float olo, ohi;
-  mlp_tile16(*net, flo, fhi, olo, ohi);
-  // row L of the tile lives in lane 4 (L % 8), in olo (L < 8) or ohi
-  const float vlo = __shfl_sync(0xffffffffu, olo, (lane & 7) * 4);
-  const float vhi = __shfl_sync(0xffffffffu, ohi, (lane & 7) * 4);
-  float rec[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  uint32_t pid = 0, step = 0;
-  if (mine) {
-    const float lnx = (lane < 8 ? vlo : vhi) + mlp_prior(e0.x);
-    float x = __expf(lnx);
-    // uniforms outside the trained range always take the G^-1 table
-    const bool tail = e0.x < kRMin || e0.x > kRMax;
-    const bool ok = x > 0.0f && x < 80.0f;  // also false for NaN
-    if (tail || (kc->check_output && !ok)) {
-      x = __expf(ginv_ln(kc->ginv, e0.x));
-      ++st.fallback;
-    } else if (!ok) {
-      x = 0.0f;  // no fallback requested: an invalid draw carries no energy
-    }
-    const float eps = x * e0.z;
-    rec[0] = e1.x; rec[1] = e1.y; rec[2] = e1.z;
-    rec[3] = e2.x; rec[4] = e2.y; rec[5] = e2.z;
-    rec[6] = eps; rec[7] = e0.w;
-    pid = __float_as_uint(e1.w);
-    step = __float_as_uint(e2.w);
-    const int64_t li = static_cast<int64_t>(pid - kc->pid0);
-    if (li < kc->led_n)
-      atomicAdd(kc->led_emit + li, static_cast<double>(e0.w) * static_cast<double>(eps));
-  }
-  stage_photon(*stage, st.fill, kc->pout, mine, rec, pid, step);
-  st.head += rows;
-  st.head -= st.head >= kQCap ? kQCap : 0;
-  st.count -= rows;
-  __syncwarp();
-  return st;
-}
-
-__device__ __forceinline__ void mlp_flush_tile(MlpWarp& mw, PhotonStage& stage, int& fill,
-                                               Counts& cnt) {
-  MlpFlushState st{mw.count, mw.head, fill, 0};
-  st = mlp_flush_call(mw.net, mw.q, &stage, mw.kc, st);
-  mw.count = st.count;
-  mw.head = st.head;
-  fill = st.fill;
-  cnt.fallback += static_cast<uint32_t>(st.fallback);
-}
-
-// ---------------------------------------------------------------------------
 // One particle, nsub steps (the whole per-step path).  Warp-collective: every
 // lane of the warp calls it, inactive lanes with act = false.
 // ---------------------------------------------------------------------------
@@ -636,8 +529,7 @@ template <typename R, int FIELD, int SAMP, bool ONE = false, class G>
 __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const G& gat,
                                                  int64_t i, const PState<R>& st,
                                                  PhotonStage& stage, int& fill,
-                                                 const PhotonOut& pout, Counts& cnt,
-                                                 MlpWarp* mw) {
+                                                 const PhotonOut& pout, Counts& cnt) {
   const bool act = st.act;
   R x = st.x, y = st.y, z = st.z, ux = st.ux, uy = st.uy, uz = st.uz;
   const R w = st.w;
@@ -647,7 +539,10 @@ __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const G
   const bool live = act && isfinite(chk);
   if (act && !live) ++cnt.nan;
   uint64_t phase = P.phase_t0;
-  (void)mw;
+  // absolute ledger entry of this particle (-1: outside the ledger)
+  const int64_t li_rel = static_cast<int64_t>(pid - P.pid0);
+  const int32_t li_abs = li_rel < P.led_n ? static_cast<int32_t>(P.led_off + li_rel) : -1;
+  (void)li_abs;
 
   const int nsub = ONE ? 1 : P.nsub;
   for (int s = 0; s < nsub; ++s) {
@@ -781,14 +676,16 @@ __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const G
       const bool want = live && k > R(0) && w > R(0);
       const unsigned wmask = __ballot_sync(0xffffffffu, want);
       if (wmask) {
-        const float rp = fmaf(static_cast<float>(rnd.x), 0x1p-32f, 0x1p-33f);
-        const float pos[3] = {static_cast<float>(xn), static_cast<float>(yn),
-                              static_cast<float>(zn)};
-        const float dir[3] = {static_cast<float>(ax), static_cast<float>(ay),
-                              static_cast<float>(az)};
-        mlp_enqueue(*mw, want, wmask, rp, static_cast<float>(ga), static_cast<float>(epsc),
-                    static_cast<float>(k * w), pos, dir, pid, step);
-        while (mw->count >= 16) mlp_flush_tile(*mw, stage, fill, cnt);
+        // the record and the network's inputs; the energy is filled in by
+        // the finishing kernel (batched tensor-core evaluation)
+        const float rec[8] = {static_cast<float>(xn), static_cast<float>(yn),
+                              static_cast<float>(zn), static_cast<float>(ax),
+                              static_cast<float>(ay), static_cast<float>(az),
+                              0.0f, static_cast<float>(k * w)};
+        const float pend[4] = {fmaf(static_cast<float>(rnd.x), 0x1p-32f, 0x1p-33f),
+                               static_cast<float>(ga), static_cast<float>(epsc),
+                               __int_as_float(li_abs)};
+        stage_photon_mask<true>(stage, fill, pout, want, wmask, rec, pid, step, pend);
       }
     }
     if (live) {
@@ -828,6 +725,10 @@ __device__ __forceinline__ PhotonOut make_pout(const StepParams<R>& P) {
   o.f[6] = P.peps; o.f[7] = P.pw;
   o.pid = P.ppid; o.step = P.pstep;
   o.cap = P.cap; o.cursor = P.counters + kCursor;
+  o.pend = P.ppend;
+  o.ginv = P.ginv;
+  o.led_base = P.led_base;
+  o.fallback = P.counters + kMlpFallback;
   return o;
 }
 
@@ -870,30 +771,13 @@ __device__ __forceinline__ void flush_counts(const Counts& c, unsigned long long
 #ifndef PRAD_F32_MINB
 #define PRAD_F32_MINB 5
 #endif
-#ifndef PRAD_MLP_MINB
-#define PRAD_MLP_MINB 3
-#endif
-// The Yee gather (54 loads in flight) and the learned sampler's tensor-core
-// tile need more registers than the analytic-field table path.
+// The Yee gather (54 loads in flight) needs more registers than the
+// analytic-field paths.
 template <typename R, int FIELD, int SAMP>
 struct MinBlocks {
   static constexpr int value =
-      sizeof(R) == 8 ? 1
-                     : (SAMP != PRAD_SAMPLER_TABLE ? PRAD_MLP_MINB
-                                                   : (FIELD == PRAD_FIELD_YEE2D ? 4 : PRAD_F32_MINB));
+      sizeof(R) == 8 ? 1 : (FIELD == PRAD_FIELD_YEE2D ? 4 : PRAD_F32_MINB);
 };
-
-// Dynamic shared memory of the learned-sampler variant: the network image
-// and one emission queue per warp.
-constexpr size_t kMlpDynSmem =
-    sizeof(MlpSmem) + sizeof(MlpFlushConst) + kMaxWarps * sizeof(MlpQueue);
-// every region of the dynamic shared memory starts on a 16-byte boundary
-// (float4 queue entries, uint4 / ldmatrix reads of the network image)
-static_assert(sizeof(MlpSmem) % 16 == 0, "MlpSmem size");
-static_assert(sizeof(MlpFlushConst) % 16 == 0, "MlpFlushConst size");
-static_assert(sizeof(MlpQueue) % 16 == 0, "MlpQueue size");
-static_assert(offsetof(MlpSmem, w2) % 16 == 0 && offsetof(MlpSmem, w1f) % 16 == 0,
-              "MlpSmem member alignment");
 
 // Resident blocks per SM of a kernel at this block size and dynamic shared
 // memory (1 if the query fails).
@@ -912,32 +796,10 @@ template <typename R, int FIELD, int SAMP, bool PF>
 __global__ void __launch_bounds__(256, (PF ? PRAD_PF_MINB : MinBlocks<R, FIELD, SAMP>::value))
     k_push_emit(const StepParams<R> P) {
   __shared__ PhotonStage stage_all[kMaxWarps];
-  extern __shared__ __align__(16) unsigned char dyn_smem[];
   PhotonStage& stage = stage_all[threadIdx.x >> 5];
   int fill = 0;  // warp-uniform
   const PhotonOut pout = make_pout(P);
   Counts cnt;
-  MlpWarp mw{nullptr, nullptr, nullptr, 0, 0};
-  if constexpr (SAMP != PRAD_SAMPLER_TABLE) {
-    MlpSmem* net = reinterpret_cast<MlpSmem*>(dyn_smem);
-    MlpFlushConst* kc = reinterpret_cast<MlpFlushConst*>(dyn_smem + sizeof(MlpSmem));
-    MlpQueue* qs =
-        reinterpret_cast<MlpQueue*>(dyn_smem + sizeof(MlpSmem) + sizeof(MlpFlushConst));
-    mlp_load_smem(*net, P.mlp);
-    if (threadIdx.x == 0) {
-      kc->pout = pout;
-      kc->ginv = P.ginv;
-      kc->led_emit = P.led_emit;
-      kc->led_n = P.led_n;
-      kc->pid0 = P.pid0;
-      kc->wdt_per_eps = static_cast<float>(P.dtn / P.eps_r);
-      kc->check_output = SAMP == PRAD_SAMPLER_MLP_FALLBACK;
-    }
-    __syncthreads();
-    mw.net = net;
-    mw.kc = kc;
-    mw.q = qs + (threadIdx.x >> 5);
-  }
   const FieldGather<R, FIELD> gat{P};
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   const int64_t first = static_cast<int64_t>(blockIdx.x) * blockDim.x;
@@ -952,20 +814,17 @@ __global__ void __launch_bounds__(256, (PF ? PRAD_PF_MINB : MinBlocks<R, FIELD, 
       const PState<R> cur = nxt;
       const int64_t j = i + stride;
       load_state<R, true>(P, j, j < P.n, nxt);
-      advance_particle<R, FIELD, SAMP, true>(P, gat, i, cur, stage, fill, pout, cnt, &mw);
+      advance_particle<R, FIELD, SAMP, true>(P, gat, i, cur, stage, fill, pout, cnt);
     }
   } else {
     for (int64_t base = first; base < P.n; base += stride) {
       const int64_t i = base + threadIdx.x;
       PState<R> cur;
       load_state(P, i, i < P.n, cur);
-      advance_particle<R, FIELD, SAMP>(P, gat, i, cur, stage, fill, pout, cnt, &mw);
+      advance_particle<R, FIELD, SAMP>(P, gat, i, cur, stage, fill, pout, cnt);
     }
   }
-  if constexpr (SAMP != PRAD_SAMPLER_TABLE) {
-    while (mw.count > 0) mlp_flush_tile(mw, stage, fill, cnt);
-  }
-  if (fill > 0) flush_stage(stage, fill, pout);
+  if (fill > 0) flush_stage<SAMP != PRAD_SAMPLER_TABLE>(stage, fill, pout);
   flush_counts(cnt, P.counters);
 }
 
@@ -985,25 +844,11 @@ __global__ void __launch_bounds__(256, PRAD_BATCH_MINB)
   __shared__ StepParams<float> Ps;
   __shared__ long long s_item;
   __shared__ int s_ens;
-  extern __shared__ __align__(16) unsigned char dyn_smem[];
   PhotonStage& stage = stage_all[threadIdx.x >> 5];
   int fill = 0;
   Counts cnt;
   int cur = -1;
   PhotonOut pout;
-  MlpWarp mw{nullptr, nullptr, nullptr, 0, 0};
-  MlpFlushConst* kc = nullptr;
-  if constexpr (SAMP != PRAD_SAMPLER_TABLE) {
-    // one network for all ensembles (the context's)
-    MlpSmem* net = reinterpret_cast<MlpSmem*>(dyn_smem);
-    kc = reinterpret_cast<MlpFlushConst*>(dyn_smem + sizeof(MlpSmem));
-    MlpQueue* qs =
-        reinterpret_cast<MlpQueue*>(dyn_smem + sizeof(MlpSmem) + sizeof(MlpFlushConst));
-    mlp_load_smem(*net, bp.ens[0].mlp);
-    mw.net = net;
-    mw.kc = kc;
-    mw.q = qs + (threadIdx.x >> 5);
-  }
   for (;;) {
     if (threadIdx.x == 0) {
       const unsigned long long it = atomicAdd(bp.next_item, 1ull);
@@ -1024,11 +869,6 @@ __global__ void __launch_bounds__(256, PRAD_BATCH_MINB)
     const int e = s_ens;
     if (e < 0) break;
     if (e != cur) {
-      // queued emissions carry the previous ensemble's ledger and time step:
-      // evaluate them before its parameters are replaced
-      if constexpr (SAMP != PRAD_SAMPLER_TABLE) {
-        while (mw.count > 0) mlp_flush_tile(mw, stage, fill, cnt);
-      }
       // photons staged so far belong to the previous ensemble's buffer view;
       // all ensembles share the context's buffer, so no flush is needed
       constexpr int kWords = static_cast<int>(sizeof(StepParams<float>) / 4);
@@ -1041,15 +881,6 @@ __global__ void __launch_bounds__(256, PRAD_BATCH_MINB)
         Ps.t0 += bp.step_base;
         Ps.phase_t0 += static_cast<uint64_t>(bp.step_base) * Ps.phase_step;
         Ps.nsub = bp.nsub;
-        if constexpr (SAMP != PRAD_SAMPLER_TABLE) {
-          kc->pout = make_pout(Ps);
-          kc->ginv = Ps.ginv;
-          kc->led_emit = Ps.led_emit;
-          kc->led_n = Ps.led_n;
-          kc->pid0 = Ps.pid0;
-          kc->wdt_per_eps = Ps.dtn / Ps.eps_r;
-          kc->check_output = SAMP == PRAD_SAMPLER_MLP_FALLBACK;
-        }
       }
       __syncthreads();
       cur = e;
@@ -1064,7 +895,7 @@ __global__ void __launch_bounds__(256, PRAD_BATCH_MINB)
         PState<float> st;
         load_state(Ps, i, i < last, st);
         advance_particle<float, PRAD_FIELD_CONST, SAMP>(Ps, gat, i, st, stage, fill, pout,
-                                                        cnt, &mw);
+                                                        cnt);
       }
     } else {
       const FieldGather<float, PRAD_FIELD_PLANE_WAVE> gat{Ps};
@@ -1073,29 +904,19 @@ __global__ void __launch_bounds__(256, PRAD_BATCH_MINB)
         PState<float> st;
         load_state(Ps, i, i < last, st);
         advance_particle<float, PRAD_FIELD_PLANE_WAVE, SAMP>(Ps, gat, i, st, stage, fill,
-                                                             pout, cnt, &mw);
+                                                             pout, cnt);
       }
     }
     __syncthreads();
   }
-  if constexpr (SAMP != PRAD_SAMPLER_TABLE) {
-    while (mw.count > 0) mlp_flush_tile(mw, stage, fill, cnt);
-  }
-  if (cur >= 0 && fill > 0) flush_stage(stage, fill, pout);
+  if (cur >= 0 && fill > 0) flush_stage<SAMP != PRAD_SAMPLER_TABLE>(stage, fill, pout);
   // counters: any ensemble's pointer to the shared counter array will do
   flush_counts(cnt, bp.ens[0].counters);
 }
 
 template <int SAMP>
 cudaError_t launch_batch_samp(const BatchParams& bp, int grid, int block, cudaStream_t s) {
-  const size_t dyn = SAMP == PRAD_SAMPLER_TABLE ? 0 : kMlpDynSmem;
-  if (dyn) {
-    const cudaError_t e = cudaFuncSetAttribute(
-        k_push_emit_batch<SAMP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-        static_cast<int>(dyn));
-    if (e != cudaSuccess) return e;
-  }
-  k_push_emit_batch<SAMP><<<grid, block, dyn, s>>>(bp);
+  k_push_emit_batch<SAMP><<<grid, block, 0, s>>>(bp);
   return cudaGetLastError();
 }
 
@@ -1112,11 +933,7 @@ cudaError_t launch_push_emit_batch(const BatchParams& bp, int sampler, int grid,
 
 template <int SAMP>
 int batch_occupancy_samp(int block) {
-  const size_t dyn = SAMP == PRAD_SAMPLER_TABLE ? 0 : kMlpDynSmem;
-  if (dyn)
-    cudaFuncSetAttribute(k_push_emit_batch<SAMP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         static_cast<int>(dyn));
-  return occupancy_of(k_push_emit_batch<SAMP>, block, dyn);
+  return occupancy_of(k_push_emit_batch<SAMP>, block, 0);
 }
 
 int batch_max_blocks_per_sm(int block, int sampler) {
@@ -1165,7 +982,7 @@ __global__ void __launch_bounds__(256, 3) k_push_emit_tiled(const StepParams<R> 
     PState<R> st;
     load_state(P, i, i < wk.z, st);
     advance_particle<R, PRAD_FIELD_YEE2D, PRAD_SAMPLER_TABLE>(P, gat, i, st, stage, fill, pout,
-                                                              cnt, nullptr);
+                                                              cnt);
   }
   if (fill > 0) flush_stage(stage, fill, pout);
   flush_counts(cnt, P.counters);
@@ -1197,20 +1014,10 @@ cudaError_t launch_field(const StepParams<R>& p, int sampler, int grid, int bloc
     return cudaGetLastError();
   }
   if constexpr (sizeof(R) == 4) {
-    cudaError_t e;
-    if (sampler == PRAD_SAMPLER_MLP) {
-      e = cudaFuncSetAttribute(k_push_emit<R, FIELD, PRAD_SAMPLER_MLP, false>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               static_cast<int>(kMlpDynSmem));
-      if (e != cudaSuccess) return e;
-      k_push_emit<R, FIELD, PRAD_SAMPLER_MLP, false><<<grid, block, kMlpDynSmem, s>>>(p);
-    } else {
-      e = cudaFuncSetAttribute(k_push_emit<R, FIELD, PRAD_SAMPLER_MLP_FALLBACK, false>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               static_cast<int>(kMlpDynSmem));
-      if (e != cudaSuccess) return e;
-      k_push_emit<R, FIELD, PRAD_SAMPLER_MLP_FALLBACK, false><<<grid, block, kMlpDynSmem, s>>>(p);
-    }
+    if (sampler == PRAD_SAMPLER_MLP)
+      k_push_emit<R, FIELD, PRAD_SAMPLER_MLP, false><<<grid, block, 0, s>>>(p);
+    else
+      k_push_emit<R, FIELD, PRAD_SAMPLER_MLP_FALLBACK, false><<<grid, block, 0, s>>>(p);
     return cudaGetLastError();
   }
   return cudaErrorInvalidValue;
@@ -1224,18 +1031,9 @@ int field_occupancy(int sampler, bool pf, int block) {
     return occupancy_of(k_push_emit<R, FIELD, PRAD_SAMPLER_TABLE, false>, block, 0);
   }
   if constexpr (sizeof(R) == 4) {
-    // the dynamic-smem limit must be raised before the occupancy query
-    if (sampler == PRAD_SAMPLER_MLP) {
-      cudaFuncSetAttribute(k_push_emit<R, FIELD, PRAD_SAMPLER_MLP, false>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           static_cast<int>(kMlpDynSmem));
-      return occupancy_of(k_push_emit<R, FIELD, PRAD_SAMPLER_MLP, false>, block, kMlpDynSmem);
-    }
-    cudaFuncSetAttribute(k_push_emit<R, FIELD, PRAD_SAMPLER_MLP_FALLBACK, false>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         static_cast<int>(kMlpDynSmem));
-    return occupancy_of(k_push_emit<R, FIELD, PRAD_SAMPLER_MLP_FALLBACK, false>, block,
-                        kMlpDynSmem);
+    if (sampler == PRAD_SAMPLER_MLP)
+      return occupancy_of(k_push_emit<R, FIELD, PRAD_SAMPLER_MLP, false>, block, 0);
+    return occupancy_of(k_push_emit<R, FIELD, PRAD_SAMPLER_MLP_FALLBACK, false>, block, 0);
   }
   return 1;
 }

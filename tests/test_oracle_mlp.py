@@ -45,6 +45,20 @@ def test_bf16_rounding_matches_torch():
     np.testing.assert_array_equal(M.bf16(x), ref)
 
 
+def test_f16_rounding_matches_torch_and_bf16_values_are_exact_halves():
+    torch = pytest.importorskip("torch")
+    x = np.random.default_rng(3).normal(0, 3, 10000)
+    ref = torch.tensor(x, dtype=torch.float64).to(torch.float16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(M.f16(x), ref)
+    # the weights' BF16 values (8 significant bits) are exact in f16 down to
+    # 2^-17 in magnitude, so the f16 products use exactly the BF16 weights
+    rng = np.random.default_rng(4)
+    w = M.bf16(rng.choice([-1.0, 1.0], 10000) * 2.0 ** -rng.uniform(0.0, 20.0, 10000))
+    big = np.abs(w) >= 2.0 ** -17
+    assert big.sum() > 5000
+    np.testing.assert_array_equal(M.f16(w[big]), w[big])
+
+
 def test_features_definition():
     f = M.features(np.array([0.5, 1 / (1 + np.e ** 8)]), np.array([316.2, 1e6]),
                    np.array([np.exp(8.2), 1e-30]))

@@ -140,20 +140,21 @@ __global__ void __launch_bounds__(kTThreads)
       a[q][2] = silu_f16x2(S.z1[s0 + g][j + 8], S.z1[s0 + g][j + 9]);
       a[q][3] = silu_f16x2(S.z1[s0 + g + 8][j + 8], S.z1[s0 + g + 8][j + 9]);
     }
+    // the network image holds W2 / 2 and b2 / 2 (exact): z2 = 2 c
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt) {
       const int j0 = 8 * nt + 2 * t;
-      float c[4] = {S.net.b2[j0], S.net.b2[j0 + 1], S.net.b2[j0], S.net.b2[j0 + 1]};
+      float c[4] = {S.net.b2h[j0], S.net.b2h[j0 + 1], S.net.b2h[j0], S.net.b2h[j0 + 1]};
       const __half* wrow = S.net.w2h + (8 * nt + g) * kW2Ld + 2 * t;
 #pragma unroll
       for (int q = 0; q < 4; ++q)
         mma_f16_16816(c, a[q][0], a[q][1], a[q][2], a[q][3],
                       *reinterpret_cast<const uint32_t*>(wrow + 16 * q),
                       *reinterpret_cast<const uint32_t*>(wrow + 16 * q + 8));
-      S.z2[s0 + g][j0] = c[0];
-      S.z2[s0 + g][j0 + 1] = c[1];
-      S.z2[s0 + g + 8][j0] = c[2];
-      S.z2[s0 + g + 8][j0 + 1] = c[3];
+      S.z2[s0 + g][j0] = 2.0f * c[0];
+      S.z2[s0 + g][j0 + 1] = 2.0f * c[1];
+      S.z2[s0 + g + 8][j0] = 2.0f * c[2];
+      S.z2[s0 + g + 8][j0 + 1] = 2.0f * c[3];
     }
   }
   __syncthreads();

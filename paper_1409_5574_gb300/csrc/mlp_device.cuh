@@ -71,7 +71,9 @@ struct MlpSmem {
   // features' low parts), k = 6, 7 the high and low BF16 parts of b1[j],
   // k >= 8 zero.  w1f[lane][nt] holds the lane's b0 register of n-tile nt.
   uint32_t w1f[32][8];
-  __half w2h[kHid * kW2Ld];  // W2 in f16 (exact images of the BF16 values)
+  // the tile evaluator's layer 2 in f16, halved (exact): W2 / 2 and b2 / 2
+  __half w2h[kHid * kW2Ld];
+  float b2h[kHid];
   // layer 3 as the B operand (K = 64 x N = 8, W3 in column 0, zero
   // elsewhere): w3f[lane][2q + u] = the lane's b_u register of k-step q
   uint32_t w3f[32][8];
@@ -79,7 +81,7 @@ struct MlpSmem {
 
 static_assert(sizeof(MlpSmem) % 16 == 0 && offsetof(MlpSmem, w2) % 16 == 0 &&
                   offsetof(MlpSmem, w1f) % 16 == 0 && offsetof(MlpSmem, w2h) % 16 == 0 &&
-                  offsetof(MlpSmem, w3f) % 16 == 0,
+                  offsetof(MlpSmem, w3f) % 16 == 0 && offsetof(MlpSmem, b2h) % 8 == 0,
               "16-byte alignment of the network image (uint4 and ldmatrix reads)");
 
 // Device copy of the network: FP32 master parameters and the BF16 W2.
@@ -124,12 +126,15 @@ __device__ __forceinline__ void mlp_load_smem(MlpSmem& s, const MlpDev& d) {
                    : (k < 6 ? bf16_round(d.params[kOffW1 + 3 * j + k - 3])
                             : (k == 6 ? b1h : bf16_round(b1 - b1h)));
     }
-    s.w1f[lane][nt] = pack_bf16x2(v[0], v[1]);
+    // halved (exact): the layer-1 accumulators hold z1 / 2
+    s.w1f[lane][nt] = pack_bf16x2(0.5f * v[0], 0.5f * v[1]);
   }
+  // halved (exact): the layer-2 accumulators hold z2 / 2
   for (int e = threadIdx.x; e < kHid * kHid; e += blockDim.x) {
     const int j = e / kHid, i = e - j * kHid;
-    s.w2h[j * kW2Ld + i] = __float2half_rn(__bfloat162float(d.w2[e]));
+    s.w2h[j * kW2Ld + i] = __float2half_rn(0.5f * __bfloat162float(d.w2[e]));
   }
+  for (int j = threadIdx.x; j < kHid; j += blockDim.x) s.b2h[j] = 0.5f * d.params[kOffB2 + j];
   for (int e = threadIdx.x; e < 32 * 8; e += blockDim.x) {
     const int lane = e >> 3, q = (e & 7) >> 1, u = e & 1;
     const int g = lane >> 2, t = lane & 3;
@@ -142,6 +147,17 @@ __device__ __forceinline__ void mlp_load_smem(MlpSmem& s, const MlpDev& d) {
     }
     s.w3f[lane][e & 7] = v;
   }
+}
+
+// SiLU from half arguments: h = hz + hz tanh(hz) with hz = z / 2 given
+// (hz0, hz1); returns (silu(z0), silu(z1)) as f16x2 (z0 in the low half).
+// f16(z / 2) = f16(z) / 2, so this equals silu_f16x2(z0, z1) bit for bit.
+__device__ __forceinline__ uint32_t silu_half_f16x2(float hz0, float hz1) {
+  uint32_t hz, th, h;
+  asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(hz) : "f"(hz1), "f"(hz0));
+  asm("tanh.approx.f16x2 %0, %1;" : "=r"(th) : "r"(hz));
+  asm("fma.rn.f16x2 %0, %1, %2, %3;" : "=r"(h) : "r"(hz), "r"(th), "r"(hz));
+  return h;
 }
 
 // SiLU of two FP32 values in packed f16 arithmetic, h = hz + hz tanh(hz) with
@@ -248,13 +264,13 @@ __device__ __forceinline__ void mlp_tile16(const MlpSmem& S, float3 f_lo, float3
     float c0[4] = {0.0f, 0.0f, 0.0f, 0.0f}, c1[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     mma_bf16_16816(c0, fa0, fa1, 0u, 0u, wb[2 * q], 0u);
     mma_bf16_16816(c1, fa0, fa1, 0u, 0u, wb[2 * q + 1], 0u);
-    a[q][0] = silu_f16x2(c0[0], c0[1]);
-    a[q][1] = silu_f16x2(c0[2], c0[3]);
-    a[q][2] = silu_f16x2(c1[0], c1[1]);
-    a[q][3] = silu_f16x2(c1[2], c1[3]);
+    a[q][0] = silu_half_f16x2(c0[0], c0[1]);
+    a[q][1] = silu_half_f16x2(c0[2], c0[3]);
+    a[q][2] = silu_half_f16x2(c1[0], c1[1]);
+    a[q][3] = silu_half_f16x2(c1[2], c1[3]);
   }
-  // layers 2 and 3 (f16): the accumulators start from b2; the SiLU of each
-  // pair of n-tiles is one k-step of layer 3
+  // layers 2 and 3 (f16): the accumulators start from b2 / 2; the SiLU of
+  // each pair of n-tiles is one k-step of layer 3
   const uint4 vlo = *reinterpret_cast<const uint4*>(&S.w3f[lane][0]);
   const uint4 vhi = *reinterpret_cast<const uint4*>(&S.w3f[lane][4]);
   const uint32_t w3b[8] = {vlo.x, vlo.y, vlo.z, vlo.w, vhi.x, vhi.y, vhi.z, vhi.w};
@@ -262,22 +278,26 @@ __device__ __forceinline__ void mlp_tile16(const MlpSmem& S, float3 f_lo, float3
   float o[4] = {S.b3, 0.0f, S.b3, 0.0f};
 #pragma unroll
   for (int q3 = 0; q3 < 4; ++q3) {
-    uint32_t h[4];
+    // n-tiles 2 q3 (c0) and 2 q3 + 1 (c1): two independent MMA chains
+    const float2 b0 = *reinterpret_cast<const float2*>(&S.b2h[16 * q3 + 2 * t]);
+    const float2 b1 = *reinterpret_cast<const float2*>(&S.b2h[16 * q3 + 8 + 2 * t]);
+    float c0[4] = {b0.x, b0.y, b0.x, b0.y}, c1[4] = {b1.x, b1.y, b1.x, b1.y};
 #pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const int nt = 2 * q3 + u;
-      const float2 bb = *reinterpret_cast<const float2*>(&S.b2[8 * nt + 2 * t]);
-      float c[4] = {bb.x, bb.y, bb.x, bb.y};
-#pragma unroll
-      for (int qq = 0; qq < 4; qq += 2) {
-        uint32_t b[4];
-        ldmatrix_x4(b, S.w2h + (8 * nt + r) * kW2Ld + 16 * (qq + (m >> 1)) + 8 * (m & 1));
-        mma_f16_16816(c, a[qq][0], a[qq][1], a[qq][2], a[qq][3], b[0], b[1]);
-        mma_f16_16816(c, a[qq + 1][0], a[qq + 1][1], a[qq + 1][2], a[qq + 1][3], b[2], b[3]);
-      }
-      h[2 * u] = silu_f16x2(c[0], c[1]);      // row g
-      h[2 * u + 1] = silu_f16x2(c[2], c[3]);  // row g + 8
+    for (int qq = 0; qq < 4; qq += 2) {
+      uint32_t w0[4], w1[4];
+      const int col = 16 * (qq + (m >> 1)) + 8 * (m & 1);
+      ldmatrix_x4(w0, S.w2h + (16 * q3 + r) * kW2Ld + col);
+      ldmatrix_x4(w1, S.w2h + (16 * q3 + 8 + r) * kW2Ld + col);
+      mma_f16_16816(c0, a[qq][0], a[qq][1], a[qq][2], a[qq][3], w0[0], w0[1]);
+      mma_f16_16816(c1, a[qq][0], a[qq][1], a[qq][2], a[qq][3], w1[0], w1[1]);
+      mma_f16_16816(c0, a[qq + 1][0], a[qq + 1][1], a[qq + 1][2], a[qq + 1][3], w0[2], w0[3]);
+      mma_f16_16816(c1, a[qq + 1][0], a[qq + 1][1], a[qq + 1][2], a[qq + 1][3], w1[2], w1[3]);
     }
+    uint32_t h[4];
+    h[0] = silu_half_f16x2(c0[0], c0[1]);  // row g, n-tile 2 q3
+    h[1] = silu_half_f16x2(c0[2], c0[3]);  // row g + 8
+    h[2] = silu_half_f16x2(c1[0], c1[1]);  // row g, n-tile 2 q3 + 1
+    h[3] = silu_half_f16x2(c1[2], c1[3]);
     // k-step q3 of layer 3: a0 = (g, n-tile 2q3), a1 = (g+8, 2q3),
     // a2 = (g, 2q3+1), a3 = (g+8, 2q3+1)
     mma_f16_16816(o, h[0], h[1], h[2], h[3], w3b[2 * q3], w3b[2 * q3 + 1]);

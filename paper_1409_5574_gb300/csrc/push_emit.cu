@@ -245,24 +245,35 @@ __device__ __forceinline__ int qs_weights(R t, R w[3]) {
   return static_cast<int>(nr);
 }
 
+// The quadratic-spline stencil of one axis for the two staggerings a
+// component can have (node-centred and half-cell-shifted): weights and the
+// three periodic node indices of each.
 template <typename R>
-__device__ __forceinline__ R yee_component(const StepParams<R>& P,
-                                           const float* __restrict__ F,
-                                           const Cell<R>& cx, const Cell<R>& cy, R sx,
-                                           R sy) {
-  R wx[3], wy[3];
-  const int i0 = cx.c + qs_weights(cx.f - sx, wx) - 1;
-  const int j0 = cy.c + qs_weights(cy.f - sy, wy) - 1;
-  // periodic indices of the 3 x 3 stencil (i0 in [-1, n])
-  int ii[3], jj[3];
+struct AxisStencil {
+  R w0[3], wh[3];
+  int i0[3], ih[3];
+};
+
+template <typename R>
+__device__ __forceinline__ AxisStencil<R> axis_stencil(const Cell<R>& c, int n) {
+  AxisStencil<R> a;
+  const int b0 = c.c + qs_weights(c.f, a.w0) - 1;
+  const int bh = c.c + qs_weights(c.f - R(0.5), a.wh) - 1;
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    int i = i0 + k, j = j0 + k;
-    i = i < 0 ? i + P.nx : (i >= P.nx ? i - P.nx : i);
-    j = j < 0 ? j + P.ny : (j >= P.ny ? j - P.ny : j);
-    ii[k] = i;
-    jj[k] = j;
+  for (int k = 0; k < 3; ++k) {  // periodic (b in [-1, n])
+    int i = b0 + k, j = bh + k;
+    i = i < 0 ? i + n : (i >= n ? i - n : i);
+    j = j < 0 ? j + n : (j >= n ? j - n : j);
+    a.i0[k] = i;
+    a.ih[k] = j;
   }
+  return a;
+}
+
+template <typename R>
+__device__ __forceinline__ R yee_interp(const StepParams<R>& P, const float* __restrict__ F,
+                                        const R wx[3], const int ii[3], const R wy[3],
+                                        const int jj[3]) {
   R v = R(0);
 #pragma unroll
   for (int b = 0; b < 3; ++b) {
@@ -279,14 +290,15 @@ __device__ __forceinline__ R yee_component(const StepParams<R>& P,
 template <typename R>
 __device__ __forceinline__ EB<R> yee2d_cells(const StepParams<R>& P, const Cell<R>& cx,
                                              const Cell<R>& cy) {
-  const R h = R(0.5), z = R(0);
+  const AxisStencil<R> ax = axis_stencil(cx, P.nx);
+  const AxisStencil<R> ay = axis_stencil(cy, P.ny);
   EB<R> f;
-  f.Ex = yee_component(P, P.yee[0], cx, cy, h, z);
-  f.Ey = yee_component(P, P.yee[1], cx, cy, z, h);
-  f.Ez = yee_component(P, P.yee[2], cx, cy, z, z);
-  f.Bx = yee_component(P, P.yee[3], cx, cy, z, h);
-  f.By = yee_component(P, P.yee[4], cx, cy, h, z);
-  f.Bz = yee_component(P, P.yee[5], cx, cy, h, h);
+  f.Ex = yee_interp(P, P.yee[0], ax.wh, ax.ih, ay.w0, ay.i0);
+  f.Ey = yee_interp(P, P.yee[1], ax.w0, ax.i0, ay.wh, ay.ih);
+  f.Ez = yee_interp(P, P.yee[2], ax.w0, ax.i0, ay.w0, ay.i0);
+  f.Bx = yee_interp(P, P.yee[3], ax.w0, ax.i0, ay.wh, ay.ih);
+  f.By = yee_interp(P, P.yee[4], ax.wh, ax.ih, ay.w0, ay.i0);
+  f.Bz = yee_interp(P, P.yee[5], ax.wh, ax.ih, ay.wh, ay.ih);
   return f;
 }
 
@@ -441,10 +453,9 @@ struct TileGather {
   const StepParams<R>& P;
   const float* sm;
   int gx0, gy0;  // grid cell of staged value (0, 0)
-  __device__ __forceinline__ R comp(int c, int cl, R fx, int rl, R fy, R sx, R sy) const {
-    R wx[3], wy[3];
-    const int i0 = cl + qs_weights(fx - sx, wx) - 1;
-    const int j0 = rl + qs_weights(fy - sy, wy) - 1;
+  // component c from the staged tile, stencil origin (i0, j0) in tile
+  // coordinates
+  __device__ __forceinline__ R comp(int c, int i0, const R wx[3], int j0, const R wy[3]) const {
     const float* base = sm + c * (kStageW * kStageW) + j0 * kStageW + i0;
     R v = R(0);
 #pragma unroll
@@ -461,14 +472,19 @@ struct TileGather {
     // staged stencil rows/columns cl-1 .. cl+2 must lie in [0, kStageW)
     if (!(cl >= 1 && cl <= kStageW - 3 && rl >= 1 && rl <= kStageW - 3))
       return yee2d_cells(P, cx, cy);
-    const R h = R(0.5), z = R(0);
+    // the two staggerings per axis share their weights across components
+    R wx0[3], wxh[3], wy0[3], wyh[3];
+    const int ix0 = cl + qs_weights(cx.f, wx0) - 1;
+    const int ixh = cl + qs_weights(cx.f - R(0.5), wxh) - 1;
+    const int iy0 = rl + qs_weights(cy.f, wy0) - 1;
+    const int iyh = rl + qs_weights(cy.f - R(0.5), wyh) - 1;
     EB<R> f;
-    f.Ex = comp(0, cl, cx.f, rl, cy.f, h, z);
-    f.Ey = comp(1, cl, cx.f, rl, cy.f, z, h);
-    f.Ez = comp(2, cl, cx.f, rl, cy.f, z, z);
-    f.Bx = comp(3, cl, cx.f, rl, cy.f, z, h);
-    f.By = comp(4, cl, cx.f, rl, cy.f, h, z);
-    f.Bz = comp(5, cl, cx.f, rl, cy.f, h, h);
+    f.Ex = comp(0, ixh, wxh, iy0, wy0);
+    f.Ey = comp(1, ix0, wx0, iyh, wyh);
+    f.Ez = comp(2, ix0, wx0, iy0, wy0);
+    f.Bx = comp(3, ix0, wx0, iyh, wyh);
+    f.By = comp(4, ixh, wxh, iy0, wy0);
+    f.Bz = comp(5, ixh, wxh, iyh, wyh);
     return f;
   }
 };
@@ -959,16 +975,25 @@ __global__ void __launch_bounds__(256, 3) k_push_emit_tiled(const StepParams<R> 
   const int tx = wk.x % P.ntx, ty = wk.x / P.ntx;
   const int gx0 = tx * kTile - kHalo, gy0 = ty * kTile - kHalo;
   constexpr int kPlane = kStageW * kStageW;
+  // periodic indices: gx0 + lx lies in [-kHalo, nx + kTile + kHalo), one
+  // wrap suffices when the grid is at least as wide as the staged region;
+  // smaller grids take a full modulo
+  const bool wide = P.nx >= kStageW && P.ny >= kStageW;
   for (int e = threadIdx.x; e < 6 * kPlane; e += blockDim.x) {
     const int c = e / kPlane;
     const int r = e - c * kPlane;
     const int ly = r / kStageW;
     const int lx = r - ly * kStageW;
-    // periodic indices; a full modulo, since grids may be smaller than the
-    // staged 40 x 40 region
-    int gx = (gx0 + lx) % P.nx, gy = (gy0 + ly) % P.ny;
-    gx += gx < 0 ? P.nx : 0;
-    gy += gy < 0 ? P.ny : 0;
+    int gx = gx0 + lx, gy = gy0 + ly;
+    if (wide) {
+      gx += gx < 0 ? P.nx : (gx >= P.nx ? -P.nx : 0);
+      gy += gy < 0 ? P.ny : (gy >= P.ny ? -P.ny : 0);
+    } else {
+      gx %= P.nx;
+      gy %= P.ny;
+      gx += gx < 0 ? P.nx : 0;
+      gy += gy < 0 ? P.ny : 0;
+    }
     tile_sm[e] = __ldg(P.yee[c] + static_cast<size_t>(gy) * P.nx + gx);
   }
   __syncthreads();

@@ -28,13 +28,41 @@ __device__ __forceinline__ int tile_of(R x, R y, int nx, int ny, int ntx, R x0, 
   return (iy / kTile) * ntx + (ix / kTile);
 }
 
+// Warp-aggregated increment of counter[t] for every valid lane: lanes of the
+// warp with the same tile form one group, its first lane adds the group's
+// size with one atomic, and each lane receives base + its rank in the group.
+// Particles stay nearly tile-ordered between sorts, so a warp usually holds
+// one or two tiles: one or two atomics per 32 particles instead of 32 on the
+// same counter.  Warp-collective (every lane calls it).
+__device__ __forceinline__ unsigned int warp_claim(unsigned int* counter, int t, bool valid) {
+  const int lane = threadIdx.x & 31;
+  const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+  unsigned int slot = 0u;
+  if (valid) {
+    const unsigned peers = __match_any_sync(vmask, t);
+    const int leader = __ffs(peers) - 1;
+    const int rank = __popc(peers & ((1u << lane) - 1u));
+    unsigned int base = 0u;
+    if (lane == leader) base = atomicAdd(counter + t, static_cast<unsigned int>(__popc(peers)));
+    slot = __shfl_sync(peers, base, leader) + static_cast<unsigned int>(rank);
+  }
+  return slot;
+}
+
+// Grid-stride over warps of 32 consecutive particles (every lane of a warp
+// takes the same number of iterations).
 template <typename R>
 __global__ void k_tile_count(const R* __restrict__ x, const R* __restrict__ y, int64_t n,
                              int nx, int ny, int ntx, R x0, R y0, R inv_dx, R inv_dy,
                              unsigned int* __restrict__ counts) {
-  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
-       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    atomicAdd(counts + tile_of(x[i], y[i], nx, ny, ntx, x0, y0, inv_dx, inv_dy), 1u);
+  const int lane = threadIdx.x & 31;
+  const int64_t wstride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t w0 = blockIdx.x * static_cast<int64_t>(blockDim.x) + (threadIdx.x & ~31);
+       w0 < n; w0 += wstride) {
+    const int64_t i = w0 + lane;
+    const bool valid = i < n;
+    const int t = valid ? tile_of(x[i], y[i], nx, ny, ntx, x0, y0, inv_dx, inv_dy) : 0;
+    (void)warp_claim(counts, t, valid);
   }
 }
 
@@ -95,14 +123,21 @@ __global__ void k_tile_scatter(const Arrays7<R> src, const Arrays7<R> dst,
                                const uint32_t* __restrict__ pid, uint32_t* __restrict__ pid_out,
                                int64_t n, int nx, int ny, int ntx, R x0, R y0, R inv_dx,
                                R inv_dy, unsigned int* __restrict__ cursor) {
-  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
-       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int t = tile_of(src.p[0][i], src.p[1][i], nx, ny, ntx, x0, y0, inv_dx, inv_dy);
-    const unsigned int d = atomicAdd(cursor + t, 1u);
+  const int lane = threadIdx.x & 31;
+  const int64_t wstride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t w0 = blockIdx.x * static_cast<int64_t>(blockDim.x) + (threadIdx.x & ~31);
+       w0 < n; w0 += wstride) {
+    const int64_t i = w0 + lane;
+    const bool valid = i < n;
+    const int t =
+        valid ? tile_of(src.p[0][i], src.p[1][i], nx, ny, ntx, x0, y0, inv_dx, inv_dy) : 0;
+    const unsigned int d = warp_claim(cursor, t, valid);
+    if (valid) {
 #pragma unroll
-    for (int k = 0; k < 7; ++k)
-      if (src.p[k]) dst.p[k][d] = src.p[k][i];
-    pid_out[d] = pid[i];
+      for (int k = 0; k < 7; ++k)
+        if (src.p[k]) dst.p[k][d] = src.p[k][i];
+      pid_out[d] = pid[i];
+    }
   }
 }
 

@@ -99,8 +99,25 @@ typedef struct prad_config {
   int32_t use_graph;        /* push_emit_batch: capture the launches of a
                                call in a CUDA graph and replay it when the
                                next call has the same shape (0 = off)     */
+  /* Super-photon control (Sec. "Monte Carlo method": the number of
+   * super-photons per super-particle and time step, and the number of real
+   * photons one represents, set at runtime).  n_try trials per particle and
+   * step (0 = 1; table sampler only), each with its own Philox block (tag 0
+   * for trial 0, 0x10000 + j for trial j) and 1/n_try of dN; a particle
+   * takes part in a step's emission with probability select_prob (decided
+   * by Philox word 3 of trial 0; 0 = 1) and its records then carry weight
+   * k w / select_prob.  Both keep the expected emission unchanged. */
+  int32_t n_try;
+  int32_t diagnostics;      /* bit mask of PRAD_DIAG_*                        */
   int32_t pad0;
+  double select_prob;
 } prad_config;
+
+/* Diagnostics counted in prad_stats when enabled in prad_config.diagnostics */
+#define PRAD_DIAG_WIGGLER 1 /* steps outside the synchrotron (wiggler) regime:
+                               Omega tau_EM < 1 with tau_EM the field period
+                               the particle sees, 1 / (omega_L |1 - dir beta_x|)
+                               (Eq. (3) context; PLANE_WAVE fields only)   */
 
 /* ---- field description ------------------------------------------------- */
 typedef struct prad_fields {
@@ -165,6 +182,7 @@ typedef struct prad_stats {
   int64_t nan_frozen;   /* particle-launches skipped as non-finite         */
   int32_t status;       /* sticky device status word (0 = ok)              */
   int32_t pad0;
+  int64_t wiggler_invalid; /* PRAD_DIAG_WIGGLER: steps outside the regime  */
 } prad_stats;
 
 typedef struct prad_ctx prad_ctx;
@@ -347,6 +365,22 @@ int prad_mlp_eval(prad_ctx* ctx, const float* in, float* lnx, int64_t n);
 
 /* ln G^-1(r) from the device table for n device uniforms. */
 int prad_ginv_eval(prad_ctx* ctx, const float* r, float* lnx, int64_t n);
+
+/* ---- angular distribution (Fig. 4) -------------------------------------------
+ * Histogram of the emitted energy (record energy x weight) of the photon
+ * records currently held, by direction: polar angle theta from `axis`, bins
+ * uniform over [0, theta_max] (theta_max = pi/2: the front hemisphere), and
+ * azimuth phi around the axis measured from the component of `ref`
+ * perpendicular to it (phi = pi/2 along axis x ref), bins uniform over
+ * [0, 2 pi).  Records with theta > theta_max are not counted.  out (host,
+ * ntheta x nphi doubles, row-major [theta][phi]) receives energies in
+ * m c^2.  Angles are computed in FP64 from the float records; bin sums use
+ * FP64 atomics (order-dependent in the last bits).  Errors: PRAD_ERR_ARG
+ * (null pointers, ntheta or nphi < 1, ntheta x nphi > 8192, theta_max
+ * outside (0, pi], zero axis, ref parallel to axis), PRAD_ERR_CUDA.
+ * Synchronises. */
+int prad_angular_histogram(prad_ctx* ctx, const double axis[3], const double ref[3],
+                           int32_t ntheta, int32_t nphi, double theta_max, double* out);
 
 /* ---- totals without allocation ---------------------------------------------
  * The paper has no counterpart to this call; it serves callers that cannot

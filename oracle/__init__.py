@@ -16,6 +16,7 @@ Function map to the paper (arXiv:1409.5574):
 * ``boris``            - Boris push (Numerical implementation section)
 * ``heff_field``, ``heff_momentum`` - H_eff, field form and Eq. (9)
 * ``run``              - the full per-step path with emission and LL ledger
+* ``angular_histogram`` - Fig. 4, emitted energy by direction (FP64 numpy)
 
 Every function is pinned by a ``-m "not gpu"`` test; see tests/test_oracle_*.
 """
@@ -224,6 +225,8 @@ class _Problem(ctypes.Structure):
         ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
         ("dx", ctypes.c_double), ("dy", ctypes.c_double),
         ("x0", ctypes.c_double), ("y0", ctypes.c_double),
+        ("n_try", ctypes.c_int32), ("pad1", ctypes.c_int32),
+        ("select_prob", ctypes.c_double),
     ]
 
 
@@ -262,6 +265,8 @@ class Problem:
     dy: float = 1.0
     x0: float = 0.0
     y0: float = 0.0
+    n_try: int = 1
+    select_prob: float = 1.0
     _keep: list = field(default_factory=list, repr=False)
 
     def to_c(self) -> _Problem:
@@ -281,6 +286,7 @@ class Problem:
                 p.yee[k] = planes[k].ctypes.data
             p.ny, p.nx = planes[0].shape
         p.dx, p.dy, p.x0, p.y0 = self.dx, self.dy, self.x0, self.y0
+        p.n_try, p.select_prob = int(self.n_try), float(self.select_prob)
         return p
 
 
@@ -318,7 +324,7 @@ def run(problem: Problem, state: dict, nsteps: int, t0: int = 0,
     for k, v in ph.items():
         setattr(cph, k, v.ctypes.data)
     cursor = np.zeros(1, dtype=np.int64)
-    stats = np.zeros(5, dtype=np.int64)
+    stats = np.zeros(6, dtype=np.int64)
     tl = None
     if trial_log:
         tl = {k: np.zeros((n, nsteps)) for k in ("dN", "R", "x")}
@@ -341,7 +347,33 @@ def run(problem: Problem, state: dict, nsteps: int, t0: int = 0,
     photons = {k: v[order] for k, v in photons.items()}
     out = {"photons": photons, "ledger": ledger,
            "stats": dict(zip(("records", "dropped", "dn_gt1", "clamped",
-                              "chi_gt1"), (int(s) for s in stats)))}
+                              "chi_gt1", "wiggler_invalid"), (int(s) for s in stats)))}
     if tl is not None:
         out["trials"] = tl
     return out
+
+
+def angular_histogram(nx, ny, nz, eps, weight, axis, ref, ntheta: int, nphi: int,
+                      theta_max: float) -> np.ndarray:
+    """Fig. 4: emitted energy (eps x weight) of photon records by direction,
+    [theta][phi]: theta the angle from ``axis`` in ntheta equal bins over
+    [0, theta_max], phi the azimuth around it from the component of ``ref``
+    perpendicular to it (phi = pi/2 along axis x ref) in nphi equal bins over
+    [0, 2 pi).  Records beyond theta_max are not counted.  FP64 throughout."""
+    a = np.asarray(axis, dtype=np.float64)
+    a = a / np.linalg.norm(a)
+    r = np.asarray(ref, dtype=np.float64)
+    e1 = r - (r @ a) * a
+    e1 = e1 / np.linalg.norm(e1)
+    e2 = np.cross(a, e1)
+    n = np.stack([np.asarray(v, dtype=np.float64) for v in (nx, ny, nz)], 1)
+    th = np.arccos(np.clip(n @ a, -1.0, 1.0))
+    ph = np.arctan2(n @ e2, n @ e1)
+    ph = np.where(ph < 0.0, ph + 2.0 * np.pi, ph)
+    keep = th <= theta_max
+    it = np.minimum((th * (ntheta / theta_max)).astype(np.int64), ntheta - 1)
+    ip = np.clip((ph * (nphi / (2.0 * np.pi))).astype(np.int64), 0, nphi - 1)
+    e = np.asarray(eps, dtype=np.float64) * np.asarray(weight, dtype=np.float64)
+    h = np.zeros((ntheta, nphi))
+    np.add.at(h, (it[keep], ip[keep]), e[keep])
+    return h

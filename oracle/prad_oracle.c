@@ -445,6 +445,13 @@ typedef struct orc_problem {
   const float* yee[6];       /* Ex Ey Ez Bx By Bz, normalised, [ny][nx] */
   int32_t nx, ny;
   double dx, dy, x0, y0;     /* normalised grid spacing and origin */
+  /* super-photon control (Monte Carlo method section: super-photons per
+   * particle and step, real photons per super-photon): n_try trials of
+   * 1/n_try of dN each; a particle-step takes part with probability
+   * select_prob and then carries weight k w / select_prob */
+  int32_t n_try;
+  int32_t pad1;
+  double select_prob;
 } orc_problem;
 
 typedef struct orc_photons {
@@ -453,7 +460,10 @@ typedef struct orc_photons {
   uint32_t *pid, *step;
 } orc_photons;
 
-/* stats[0] records, [1] dropped, [2] dN>1, [3] clamp, [4] chi>1 */
+/* stats[0] records, [1] dropped, [2] dN>1, [3] clamp, [4] chi>1,
+ * [5] steps outside the synchrotron (wiggler) regime, plane wave only:
+ *     Omega < omega_L |1 - dir beta_x| (Omega tau_EM < 1, tau_EM the field
+ *     period the particle sees; Eq. (3) and the text before it) */
 
 /* normalisation factors */
 static double orc_Er(double w) { return ORC_ME * ORC_C * w / ORC_QE; }
@@ -569,10 +579,13 @@ int orc_run(const orc_problem* P, int64_t n, int32_t nsteps, int64_t t0,
   const uint32_t key[2] = {(uint32_t)(P->seed & 0xffffffffu),
                            (uint32_t)(P->seed >> 32)};
   const double Lx = P->nx * P->dx, Ly = P->ny * P->dy;
-  int64_t s_dn1 = 0, s_clamp = 0, s_chi = 0, s_rec = 0, s_drop = 0;
+  int64_t s_dn1 = 0, s_clamp = 0, s_chi = 0, s_rec = 0, s_drop = 0, s_wig = 0;
+  const int n_try = P->n_try > 0 ? P->n_try : 1;
+  const double q_sel = P->select_prob > 0.0 ? P->select_prob : 1.0;
+  const double wl = (2.0 * ORC_PI * ORC_C / P->lambda) / w; /* omega_L / omega_ref */
 
 #pragma omp parallel for schedule(dynamic, 64) \
-    reduction(+ : s_dn1, s_clamp, s_chi, s_rec, s_drop)
+    reduction(+ : s_dn1, s_clamp, s_chi, s_rec, s_drop, s_wig)
   for (int64_t i = 0; i < n; ++i) {
     double x = X[i], y = Y[i], z = Z ? Z[i] : 0.0;
     double u[3] = {UX[i], UY[i], UZ[i]};
@@ -594,6 +607,7 @@ int orc_run(const orc_problem* P, int64_t n, int32_t nsteps, int64_t t0,
         Om = fabs(q) * orc_heff_field(E, B, beta);
       else
         Om = orc_heff_momentum(uo, u, dtn);
+      if (P->field_kind == 1 && Om < wl * fabs(1.0 - P->dir * beta[0])) s_wig++;
       if (Om * dtn > ga) { Om = ga / dtn; s_clamp++; }
       double wc = 1.5 * Om * ga * ga;          /* Eq. (1), normalised */
       double epsc = eps_r * wc;                /* hbar omega_c / m c^2 */
@@ -615,39 +629,49 @@ int orc_run(const orc_problem* P, int64_t n, int32_t nsteps, int64_t t0,
         x -= Lx * floor((x - P->x0) / Lx);
         y -= Ly * floor((y - P->y0) / Ly);
       }
-      /* Monte Carlo emission */
+      /* Monte Carlo emission: n_try trials, trial 0 from the block with
+       * tag 0, trial j >= 1 from tag 0x10000 + j; the particle-step takes
+       * part with probability select_prob (word 3 of the trial-0 block) */
       uint32_t ctr[4] = {pid[i], (uint32_t)step, 0u, P->ensemble}, rnd[4];
       orc_philox4x32_10(ctr, key, rnd);
-      double R;
-      int low;
-      double xs = orc_sample_x_branch(rnd, &R, &low);
-      double dN = Cn * Om * dtn * orc_F(xs) / (xs * orc_S_branch(xs, low));
-      double fl = floor(dN);
-      double k = fl + ((R < dN - fl) ? 1.0 : 0.0);
-      if (dN > 1.0) s_dn1++;
-      if (trial_dN) {
-        size_t idx = (size_t)i * (size_t)nsteps + (size_t)s;
-        trial_dN[idx] = dN;
-        trial_R[idx] = R;
-        trial_x[idx] = xs;
-      }
-      if (k > 0.0 && wt > 0.0) {
-        double eps = xs * epsc;
-        le += k * wt * eps;
-        int64_t slot;
+      const int part = q_sel >= 1.0 || ((double)rnd[3] + 0.5) * 0x1p-32 < q_sel;
+      for (int j = 0; j < n_try; ++j) {
+        if (j > 0) {
+          uint32_t cj[4] = {pid[i], (uint32_t)step, 0x10000u + (uint32_t)j, P->ensemble};
+          orc_philox4x32_10(cj, key, rnd);
+        }
+        double R;
+        int low;
+        double xs = orc_sample_x_branch(rnd, &R, &low);
+        double dN = Cn * Om * dtn * orc_F(xs) / (xs * orc_S_branch(xs, low)) / n_try;
+        double fl = floor(dN);
+        double k = fl + ((R < dN - fl) ? 1.0 : 0.0);
+        if (part && dN > 1.0) s_dn1++;
+        if (trial_dN && j == 0) {
+          size_t idx = (size_t)i * (size_t)nsteps + (size_t)s;
+          trial_dN[idx] = dN;
+          trial_R[idx] = R;
+          trial_x[idx] = xs;
+        }
+        if (part && k > 0.0 && wt > 0.0) {
+          double eps = xs * epsc;
+          double kw = k * wt / q_sel;
+          le += kw * eps;
+          int64_t slot;
 #pragma omp atomic capture
-        slot = (*cursor)++;
-        if (slot < ph->capacity) {
-          double un = sqrt(ua2);
-          double inv = un > 0.0 ? 1.0 / un : 0.0;
-          ph->x[slot] = x; ph->y[slot] = y; ph->z[slot] = z;
-          ph->nx[slot] = ua[0] * inv; ph->ny[slot] = ua[1] * inv;
-          ph->nz[slot] = ua[2] * inv;
-          ph->eps[slot] = eps; ph->weight[slot] = k * wt;
-          ph->pid[slot] = pid[i]; ph->step[slot] = (uint32_t)step;
-          s_rec++;
-        } else {
-          s_drop++;
+          slot = (*cursor)++;
+          if (slot < ph->capacity) {
+            double un = sqrt(ua2);
+            double inv = un > 0.0 ? 1.0 / un : 0.0;
+            ph->x[slot] = x; ph->y[slot] = y; ph->z[slot] = z;
+            ph->nx[slot] = ua[0] * inv; ph->ny[slot] = ua[1] * inv;
+            ph->nz[slot] = ua[2] * inv;
+            ph->eps[slot] = eps; ph->weight[slot] = kw;
+            ph->pid[slot] = pid[i]; ph->step[slot] = (uint32_t)step;
+            s_rec++;
+          } else {
+            s_drop++;
+          }
         }
       }
     }
@@ -657,7 +681,7 @@ int orc_run(const orc_problem* P, int64_t n, int32_t nsteps, int64_t t0,
   }
   if (*cursor > ph->capacity) *cursor = ph->capacity;
   stats[0] += s_rec; stats[1] += s_drop; stats[2] += s_dn1;
-  stats[3] += s_clamp; stats[4] += s_chi;
+  stats[3] += s_clamp; stats[4] += s_chi; stats[5] += s_wig;
   return 0;
 }
 

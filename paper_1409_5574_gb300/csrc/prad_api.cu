@@ -53,6 +53,7 @@ struct prad_ctx {
   uint32_t* d_pid = nullptr;
   uint32_t* d_step = nullptr;
   float4* d_pend = nullptr;      // learned sampler: per-slot network inputs
+  double* d_hist = nullptr;      // angular histogram scratch (on first use)
   int finish_grid = 0;           // blocks of the learned sampler's finishing kernel
   // counters, ledgers, reduction scratch
   unsigned long long* d_cnt = nullptr;
@@ -382,6 +383,13 @@ void fill_common(const prad_ctx* c, StepParams<R>& p, const prad_fields& f) {
   p.led_off = 0;
   p.led_base = c->d_led_emit;
   p.cp_dt = static_cast<R>(5.0 * std::sqrt(3.0) / 6.0 * c->alpha * dtn);
+  p.ntry = c->cfg.n_try > 0 ? c->cfg.n_try : 1;
+  p.diag = c->cfg.diagnostics;
+  const double q_sel = c->cfg.select_prob > 0.0 ? c->cfg.select_prob : 1.0;
+  p.inv_ntry = static_cast<R>(1.0 / p.ntry);
+  p.sel_q = static_cast<R>(q_sel);
+  p.inv_sel_q = static_cast<R>(1.0 / q_sel);
+  p.wl = R(0);
   p.mlp = mlp_dev(c);
   p.ginv = c->d_ginv;
   // field, normalised: E by m c omega_ref / e, B by m omega_ref / e
@@ -395,6 +403,7 @@ void fill_common(const prad_ctx* c, StepParams<R>& p, const prad_fields& f) {
   p.dims = 3;
   if (f.kind == PRAD_FIELD_PLANE_WAVE) {
     const double wn = (2.0 * kPi * kC / f.lambda) / w;  // omega_L / omega_ref
+    p.wl = static_cast<R>(wn);
     p.E0 = static_cast<R>(f.a0 * wn);
     const double kcd = f.dir * wn / (2.0 * kPi);
     p.kc = static_cast<R>(kcd);
@@ -609,6 +618,14 @@ int prad_init(prad_ctx** out, const prad_config* cfg) {
     return fail(nullptr, PRAD_ERR_ARG, "prad_init: block_size must be a multiple of 32 <= 256");
   if (cfg->steps_per_launch < 0 || cfg->blocks_per_sm < 0 || cfg->sort_interval < 0)
     return fail(nullptr, PRAD_ERR_ARG, "prad_init: negative launch parameter");
+  if (cfg->n_try < 0 || cfg->n_try > 65535)
+    return fail(nullptr, PRAD_ERR_ARG, "prad_init: n_try outside [0, 65535]");
+  if (cfg->n_try > 1 && cfg->sampler != PRAD_SAMPLER_TABLE)
+    return fail(nullptr, PRAD_ERR_ARG, "prad_init: n_try > 1 needs the table sampler");
+  if (!(cfg->select_prob >= 0.0 && cfg->select_prob <= 1.0))
+    return fail(nullptr, PRAD_ERR_ARG, "prad_init: select_prob outside [0, 1]");
+  if (cfg->diagnostics & ~PRAD_DIAG_WIGGLER)
+    return fail(nullptr, PRAD_ERR_ARG, "prad_init: unknown diagnostics bit");
 
   prad_ctx* c = new (std::nothrow) prad_ctx();
   if (!c) return fail(nullptr, PRAD_ERR_ARG, "prad_init: out of host memory");
@@ -699,6 +716,7 @@ int prad_destroy(prad_ctx* c) {
   cudaFree(c->d_pid);
   cudaFree(c->d_step);
   cudaFree(c->d_pend);
+  cudaFree(c->d_hist);
   cudaFree(c->d_cnt);
   cudaFree(c->d_led_emit);
   cudaFree(c->d_led_ll);
@@ -803,6 +821,44 @@ int prad_get_photons(prad_ctx* c, prad_photons* out, int64_t cap, int64_t* n_out
   return PRAD_OK;
 }
 
+int prad_angular_histogram(prad_ctx* c, const double axis[3], const double ref[3],
+                           int32_t ntheta, int32_t nphi, double theta_max, double* out) {
+  if (!c) return fail(c, PRAD_ERR_ARG, "angular_histogram: null context");
+  if (!axis || !ref || !out) return fail(c, PRAD_ERR_ARG, "angular_histogram: null pointer");
+  if (ntheta < 1 || nphi < 1 || static_cast<int64_t>(ntheta) * nphi > kMaxAngularBins)
+    return fail(c, PRAD_ERR_ARG, "angular_histogram: need 1 <= ntheta, nphi and ntheta x nphi <= %d",
+                kMaxAngularBins);
+  if (!(theta_max > 0.0 && theta_max <= kPi))
+    return fail(c, PRAD_ERR_ARG, "angular_histogram: theta_max outside (0, pi]");
+  AngularArgs a;
+  const double na = std::sqrt(axis[0] * axis[0] + axis[1] * axis[1] + axis[2] * axis[2]);
+  if (!(na > 0.0)) return fail(c, PRAD_ERR_ARG, "angular_histogram: zero axis");
+  for (int k = 0; k < 3; ++k) a.axis[k] = axis[k] / na;
+  const double ra = ref[0] * a.axis[0] + ref[1] * a.axis[1] + ref[2] * a.axis[2];
+  double e1[3] = {ref[0] - ra * a.axis[0], ref[1] - ra * a.axis[1], ref[2] - ra * a.axis[2]};
+  const double n1 = std::sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+  const double nr = std::sqrt(ref[0] * ref[0] + ref[1] * ref[1] + ref[2] * ref[2]);
+  if (!(n1 > 1e-9 * nr)) return fail(c, PRAD_ERR_ARG, "angular_histogram: ref parallel to axis");
+  for (int k = 0; k < 3; ++k) a.e1[k] = e1[k] / n1;
+  a.e2[0] = a.axis[1] * a.e1[2] - a.axis[2] * a.e1[1];
+  a.e2[1] = a.axis[2] * a.e1[0] - a.axis[0] * a.e1[2];
+  a.e2[2] = a.axis[0] * a.e1[1] - a.axis[1] * a.e1[0];
+  a.theta_max = theta_max;
+  a.ntheta = ntheta;
+  a.nphi = nphi;
+  a.nx = c->d_ph[3]; a.ny = c->d_ph[4]; a.nz = c->d_ph[5];
+  a.eps = c->d_ph[6]; a.weight = c->d_ph[7];
+  a.cursor = c->d_cnt + kCursor;
+  a.cap = c->cfg.photon_capacity;
+  if (!c->d_hist) CK(c, cudaMalloc(&c->d_hist, sizeof(double) * kMaxAngularBins));
+  a.out = c->d_hist;
+  CK(c, launch_angular_hist(a, c->num_sms * 2, c->stream));
+  const size_t nb = static_cast<size_t>(ntheta) * nphi;
+  CK(c, cudaMemcpyAsync(out, c->d_hist, sizeof(double) * nb, cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  return PRAD_OK;
+}
+
 int prad_energy_budget(prad_ctx* c, double* emitted, double* rr_loss, prad_stats* s) {
   if (!c) return fail(c, PRAD_ERR_ARG, "energy_budget: null context");
   CK(c, launch_ledger_reduce(c->d_led_emit, c->d_led_ll, c->cfg.max_particles,
@@ -824,6 +880,7 @@ int prad_energy_budget(prad_ctx* c, double* emitted, double* rr_loss, prad_stats
     s->chi_gt1 = static_cast<int64_t>(cnt[kChiGt1]);
     s->nan_frozen = static_cast<int64_t>(cnt[kNan]);
     s->mlp_fallback = static_cast<int64_t>(cnt[kMlpFallback]);
+    s->wiggler_invalid = static_cast<int64_t>(cnt[kWiggler]);
     s->status = static_cast<int32_t>(cnt[kStatus]);
     s->pad0 = 0;
   }

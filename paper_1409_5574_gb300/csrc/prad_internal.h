@@ -31,6 +31,7 @@ enum Counter {
   kStatus = 6,
   kMlpDone = 7,    // learned sampler: records [0, kMlpDone) have their energy
   kMlpBlocks = 8,  // learned sampler: blocks of the finishing kernel done
+  kWiggler = 9,    // PRAD_DIAG_WIGGLER: steps outside the synchrotron regime
   kNumCounters = 16
 };
 
@@ -90,6 +91,11 @@ struct StepParams {
   unsigned long long* counters;
   int64_t led_off;            // ledger entry of id pid0 in the context's ledger
   double* led_base;           // the context's emitted-energy ledger (entry 0)
+  // super-photon control: trials per step, selection probability
+  int32_t ntry;               // >= 1
+  int32_t diag;               // PRAD_DIAG_* mask
+  R inv_ntry, sel_q, inv_sel_q;
+  R wl;                       // plane wave: omega_L / omega_ref
   // learned sampler (direct scheme): expected photons per step = cp_dt Omega
   R cp_dt;                    // (5 sqrt3 / 6) alpha dtn
   MlpDev mlp;
@@ -186,6 +192,18 @@ struct MlpFinishArgs {
   int32_t check_output;       // MLP_FALLBACK: invalid network output -> table
 };
 cudaError_t launch_mlp_finish(const MlpFinishArgs& a, int grid, cudaStream_t s);
+// Angular histogram of the held photon records (diagnostics.cu).
+constexpr int kMaxAngularBins = 8192;  // 64 KB of FP64 bins in shared memory
+struct AngularArgs {
+  const float *nx, *ny, *nz, *eps, *weight;
+  const unsigned long long* cursor;
+  int64_t cap;
+  double axis[3], e1[3], e2[3];  // orthonormal frame: polar axis, phi = 0, phi = pi/2
+  double theta_max;
+  int32_t ntheta, nphi;
+  double* out;                   // device, ntheta x nphi
+};
+cudaError_t launch_angular_hist(const AngularArgs& a, int grid, cudaStream_t s);
 int mlp_finish_blocks_per_sm();
 cudaError_t launch_ginv_eval(const float* tab, const float* r, float* out, int64_t n,
                              cudaStream_t s);

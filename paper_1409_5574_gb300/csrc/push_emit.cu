@@ -76,6 +76,17 @@ struct Acc<double> {
 };
 
 // ---- precision-generic helpers --------------------------------------------
+// (w + 1/2) 2^-32: a Philox word as a uniform in (0, 1)
+template <typename R>
+__device__ __forceinline__ R unit_uniform(uint32_t w);
+template <>
+__device__ __forceinline__ float unit_uniform<float>(uint32_t w) {
+  return fmaf(static_cast<float>(w), 0x1p-32f, 0x1p-33f);
+}
+template <>
+__device__ __forceinline__ double unit_uniform<double>(uint32_t w) {
+  return fma(static_cast<double>(w), 0x1p-32, 0x1p-33);
+}
 __device__ __forceinline__ float rsq(float v) { return rsqrtf(v); }
 __device__ __forceinline__ double rsq(double v) { return rsqrt(v); }
 __device__ __forceinline__ float rcp(float v) { return __fdividef(1.0f, v); }
@@ -490,7 +501,7 @@ struct TileGather {
 };
 
 struct Counts {
-  uint32_t dn1 = 0, clamp = 0, chi = 0, nan = 0, fallback = 0;
+  uint32_t dn1 = 0, clamp = 0, chi = 0, nan = 0, fallback = 0, wig = 0;
   bool bad_id = false;
 };
 
@@ -628,6 +639,14 @@ __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const G
       c2 = c2 > R(0) ? c2 : R(0);
       Om = ua2 > R(0) ? R(0.5) * (g0 + g1) * sqr(c2) * rcp(ua2) * P.inv_dtn : R(0);
     }
+    if constexpr (FIELD == PRAD_FIELD_PLANE_WAVE) {
+      if (P.diag & PRAD_DIAG_WIGGLER) {
+        // synchrotron (wiggler) regime: Omega tau_EM > 1 with tau_EM the
+        // field period the particle sees, 1 / (omega_L |1 - dir beta_x|)
+        const R seen = P.wl * fabs(R(1) - P.dir * ax * iga);
+        if (live && Om < seen) ++cnt.wig;
+      }
+    }
     if (Om * P.dtn > ga) {
       Om = ga * P.inv_dtn;
       if (live) ++cnt.clamp;
@@ -655,31 +674,47 @@ __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const G
       yn -= P.Ly * flr((yn - P.y0) * (R(1) / P.Ly));
     }
     const uint4 rnd = philox10(make_uint4(pid, step, 0u, P.ensemble), P.key0, P.key1);
-    R Rr;
-    if constexpr (sizeof(R) == 4)
-      Rr = fmaf(static_cast<float>(rnd.z), 0x1p-32f, 0x1p-33f);
-    else
-      Rr = fma(static_cast<double>(rnd.z), 0x1p-32, 0x1p-33);
+    const R Rr = unit_uniform<R>(rnd.z);
     if constexpr (SAMP == PRAD_SAMPLER_TABLE) {
-      // 8. Monte Carlo emission: proposal x = P^-1(R'), dN of Eq. (13)
-      R xs, g;
-      sample_x_g(P, rnd.x, rnd.y, xs, g);
-      const R dN = P.cn_dt * Om * g * rcp(xs);
-      const R fl = flr(dN);
-      const R k = fl + ((Rr < dN - fl) ? R(1) : R(0));
-      if (live && dN > R(1)) ++cnt.dn1;
-      const bool want = live && k > R(0) && w > R(0);
-      // 9. append + emitted-energy ledger; the record is built only when
-      //    some lane of the warp emits
-      const unsigned mask = __ballot_sync(0xffffffffu, want);
-      if (mask) {
-        const R eps = xs * epsc;
-        if (want) le.add(k * w * eps);
-        const float rec[8] = {static_cast<float>(xn), static_cast<float>(yn),
-                              static_cast<float>(zn), static_cast<float>(ax),
-                              static_cast<float>(ay), static_cast<float>(az),
-                              static_cast<float>(eps), static_cast<float>(k * w)};
-        stage_photon_mask(stage, fill, pout, want, mask, rec, pid, step);
+      // 8. Monte Carlo emission: proposal x = P^-1(R'), dN of Eq. (13);
+      //    one trial with the Philox words (w0, w1) and uniform Rd, dN
+      //    scaled by dn_scale, record weights by wmul, for lanes with part
+      auto trial = [&](uint32_t w0, uint32_t w1, R Rd, R dn_scale, R wmul, bool part) {
+        R xs, g;
+        sample_x_g(P, w0, w1, xs, g);
+        const R dN = P.cn_dt * Om * g * rcp(xs) * dn_scale;
+        const R fl = flr(dN);
+        const R k = fl + ((Rd < dN - fl) ? R(1) : R(0));
+        if (part && dN > R(1)) ++cnt.dn1;
+        const bool want = part && k > R(0) && w > R(0);
+        // 9. append + emitted-energy ledger; the record is built only when
+        //    some lane of the warp emits
+        const unsigned mask = __ballot_sync(0xffffffffu, want);
+        if (mask) {
+          const R eps = xs * epsc;
+          const R kw = k * w * wmul;
+          if (want) le.add(kw * eps);
+          const float rec[8] = {static_cast<float>(xn), static_cast<float>(yn),
+                                static_cast<float>(zn), static_cast<float>(ax),
+                                static_cast<float>(ay), static_cast<float>(az),
+                                static_cast<float>(eps), static_cast<float>(kw)};
+          stage_photon_mask(stage, fill, pout, want, mask, rec, pid, step);
+        }
+      };
+      if (P.ntry == 1 && !(P.sel_q < R(1))) {
+        trial(rnd.x, rnd.y, Rr, R(1), R(1), live);
+      } else {
+        // super-photon control: a particle takes part with probability
+        // sel_q (Philox word 3 of trial 0), with weight 1 / sel_q; ntry
+        // trials of 1 / ntry of dN each, trial j >= 1 from its own block
+        const bool part = live && unit_uniform<R>(rnd.w) < P.sel_q;
+        trial(rnd.x, rnd.y, Rr, P.inv_ntry, P.inv_sel_q, part);
+        for (int j = 1; j < P.ntry; ++j) {
+          const uint4 rb = philox10(make_uint4(pid, step, 0x10000u + static_cast<uint32_t>(j),
+                                               P.ensemble),
+                                    P.key0, P.key1);
+          trial(rb.x, rb.y, unit_uniform<R>(rb.z), P.inv_ntry, P.inv_sel_q, part);
+        }
       }
     } else {
       // 8'. direct scheme: photons of this step ~ mean (5 sqrt3/6) alpha
@@ -689,7 +724,9 @@ __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const G
       const R fl = flr(pm);
       const R k = fl + ((Rr < pm - fl) ? R(1) : R(0));
       if (live && pm > R(1)) ++cnt.dn1;
-      const bool want = live && k > R(0) && w > R(0);
+      // super-photon control: selection with probability sel_q
+      const bool part = live && (!(P.sel_q < R(1)) || unit_uniform<R>(rnd.w) < P.sel_q);
+      const bool want = part && k > R(0) && w > R(0);
       const unsigned wmask = __ballot_sync(0xffffffffu, want);
       if (wmask) {
         // the record and the network's inputs; the energy is filled in by
@@ -697,7 +734,7 @@ __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const G
         const float rec[8] = {static_cast<float>(xn), static_cast<float>(yn),
                               static_cast<float>(zn), static_cast<float>(ax),
                               static_cast<float>(ay), static_cast<float>(az),
-                              0.0f, static_cast<float>(k * w)};
+                              0.0f, static_cast<float>(k * w * P.inv_sel_q)};
         const float pend[4] = {fmaf(static_cast<float>(rnd.x), 0x1p-32f, 0x1p-33f),
                                static_cast<float>(ga), static_cast<float>(epsc),
                                __int_as_float(li_abs)};
@@ -750,30 +787,34 @@ __device__ __forceinline__ PhotonOut make_pout(const StepParams<R>& P) {
 
 // Block reduction of the counters: one atomic per nonzero block total.
 __device__ __forceinline__ void flush_counts(const Counts& c, unsigned long long* counters) {
-  __shared__ uint32_t red[6][32];
+  constexpr int kN = 7;
+  __shared__ uint32_t red[kN][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint32_t v0 = __reduce_add_sync(0xffffffffu, c.dn1);
-  const uint32_t v1 = __reduce_add_sync(0xffffffffu, c.clamp);
-  const uint32_t v2 = __reduce_add_sync(0xffffffffu, c.chi);
-  const uint32_t v3 = __reduce_add_sync(0xffffffffu, c.nan);
-  const uint32_t v4 = __reduce_add_sync(0xffffffffu, c.fallback);
-  const uint32_t v5 = __reduce_add_sync(0xffffffffu, c.bad_id ? 1u : 0u);
+  const uint32_t v[kN] = {__reduce_add_sync(0xffffffffu, c.dn1),
+                          __reduce_add_sync(0xffffffffu, c.clamp),
+                          __reduce_add_sync(0xffffffffu, c.chi),
+                          __reduce_add_sync(0xffffffffu, c.nan),
+                          __reduce_add_sync(0xffffffffu, c.fallback),
+                          __reduce_add_sync(0xffffffffu, c.bad_id ? 1u : 0u),
+                          __reduce_add_sync(0xffffffffu, c.wig)};
   if (lane == 0) {
-    red[0][warp] = v0; red[1][warp] = v1; red[2][warp] = v2; red[3][warp] = v3;
-    red[4][warp] = v4; red[5][warp] = v5;
+#pragma unroll
+    for (int k = 0; k < kN; ++k) red[k][warp] = v[k];
   }
   __syncthreads();
   if (warp == 0) {
     const int nw = blockDim.x >> 5;
+    // counter slot of each value (bad ids set status bit 1)
+    constexpr int kSlot[kN] = {kDnGt1, kClamp, kChiGt1, kNan, kMlpFallback, kStatus, kWiggler};
 #pragma unroll
-    for (int k = 0; k < 6; ++k) {
-      const uint32_t v = lane < nw ? red[k][lane] : 0u;
-      const uint32_t t = __reduce_add_sync(0xffffffffu, v);
+    for (int k = 0; k < kN; ++k) {
+      const uint32_t vv = lane < nw ? red[k][lane] : 0u;
+      const uint32_t t = __reduce_add_sync(0xffffffffu, vv);
       if (lane == 0 && t) {
-        if (k < 5)
-          atomicAdd(counters + kDnGt1 + k, static_cast<unsigned long long>(t));
-        else
+        if (kSlot[k] == kStatus)
           atomicOr(counters + kStatus, 2ull);  // status bit 1: id outside ledger
+        else
+          atomicAdd(counters + kSlot[k], static_cast<unsigned long long>(t));
       }
     }
   }

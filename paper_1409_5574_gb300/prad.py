@@ -25,6 +25,7 @@ PRAD_ERR_TIMEOUT, PRAD_ERR_STATE, PRAD_WARN_NAN = -4, -5, 1
 PRAD_FP32, PRAD_FP64 = 0, 1
 PRAD_SAMPLER_TABLE, PRAD_SAMPLER_MLP, PRAD_SAMPLER_MLP_FALLBACK = 0, 1, 2
 PRAD_RR_OFF, PRAD_RR_LEDGER, PRAD_RR_APPLY = 0, 1, 2
+PRAD_DIAG_WIGGLER = 1
 PRAD_HEFF_FIELD, PRAD_HEFF_MOMENTUM = 0, 1
 PRAD_FIELD_CONST, PRAD_FIELD_PLANE_WAVE, PRAD_FIELD_YEE2D = 0, 1, 2
 
@@ -40,7 +41,8 @@ class prad_config(ctypes.Structure):
                 ("steps_per_launch", _i32), ("photon_capacity", _i64),
                 ("max_particles", _i64), ("stream", _vp), ("block_size", _i32),
                 ("blocks_per_sm", _i32), ("sort_interval", _i32), ("batch_chunk", _i32),
-                ("use_graph", _i32), ("pad0", _i32)]
+                ("use_graph", _i32), ("n_try", _i32), ("diagnostics", _i32),
+                ("pad0", _i32), ("select_prob", _dbl)]
 
 
 class prad_fields(ctypes.Structure):
@@ -75,7 +77,8 @@ class prad_photons(ctypes.Structure):
 class prad_stats(ctypes.Structure):
     _fields_ = [("records", _i64), ("dropped", _i64), ("dn_gt1", _i64),
                 ("clamped", _i64), ("chi_gt1", _i64), ("mlp_fallback", _i64),
-                ("nan_frozen", _i64), ("status", _i32), ("pad0", _i32)]
+                ("nan_frozen", _i64), ("status", _i32), ("pad0", _i32),
+                ("wiggler_invalid", _i64)]
 
 
 # symbol -> (restype, argtypes); every function declared in include/prad.h
@@ -91,6 +94,8 @@ SIGNATURES = {
                                    ctypes.POINTER(prad_tuning)]),
     "prad_get_photons": (_i32, [_vp, ctypes.POINTER(prad_photons), _i64,
                                 ctypes.POINTER(_i64), ctypes.POINTER(_i64), _i32, _i32]),
+    "prad_angular_histogram": (_i32, [_vp, ctypes.POINTER(_dbl), ctypes.POINTER(_dbl), _i32,
+                                      _i32, _dbl, ctypes.POINTER(_dbl)]),
     "prad_energy_budget": (_i32, [_vp, ctypes.POINTER(_dbl), ctypes.POINTER(_dbl),
                                   ctypes.POINTER(prad_stats)]),
     "prad_get_ledger": (_i32, [_vp, _vp, _vp, _i64, _i64, _i32]),
@@ -188,6 +193,19 @@ def prad_get_photons(h, out: Optional[prad_photons], cap: int, drain: bool,
     return n_out.value, n_drop.value
 
 
+def prad_angular_histogram(h, axis, ref, ntheta: int, nphi: int, theta_max: float):
+    """Emitted energy of the held records by direction (ntheta x nphi numpy
+    array, [theta][phi])."""
+    import numpy as np
+    out = np.zeros((ntheta, nphi), dtype=np.float64)
+    ax = (_dbl * 3)(*[float(v) for v in axis])
+    rf = (_dbl * 3)(*[float(v) for v in ref])
+    _check(load_library().prad_angular_histogram(
+        h, ax, rf, ntheta, nphi, float(theta_max),
+        out.ctypes.data_as(ctypes.POINTER(_dbl))), h)
+    return out
+
+
 def prad_energy_budget(h):
     e, r, s = _dbl(), _dbl(), prad_stats()
     rc = _check(load_library().prad_energy_budget(h, ctypes.byref(e), ctypes.byref(r),
@@ -281,7 +299,8 @@ class Context:
                  steps_per_launch: int = 1, stream=None, block_size: int = 0,
                  blocks_per_sm: int = 0, sampler: int = PRAD_SAMPLER_TABLE,
                  ensemble: int = 0, sort_interval: int = 0, batch_chunk: int = 0,
-                 use_graph: bool = False):
+                 use_graph: bool = False, n_try: int = 1, select_prob: float = 1.0,
+                 diagnostics: int = 0):
         torch = _torch()
         if not torch.cuda.is_available():
             raise RuntimeError("prad needs a CUDA device")
@@ -309,6 +328,9 @@ class Context:
         cfg.sort_interval = sort_interval
         cfg.batch_chunk = batch_chunk
         cfg.use_graph = int(use_graph)
+        cfg.n_try = n_try
+        cfg.select_prob = select_prob
+        cfg.diagnostics = diagnostics
         self.cfg = cfg
         self.capacity = photon_capacity
         self.max_particles = max_particles
@@ -444,6 +466,10 @@ class Context:
 
     def energy_budget(self):
         return prad_energy_budget(self.h)
+
+    def angular_histogram(self, axis=(1.0, 0.0, 0.0), ref=(0.0, 1.0, 0.0), ntheta: int = 45,
+                          nphi: int = 72, theta_max: float = 0.5 * 3.141592653589793):
+        return prad_angular_histogram(self.h, axis, ref, ntheta, nphi, theta_max)
 
     def ledger(self, offset: int = 0, n: Optional[int] = None):
         torch = self.torch

@@ -314,6 +314,12 @@ int upload_mlp(prad_ctx* c, const float* host_params) {
   return PRAD_OK;
 }
 
+// Super-photon control or diagnostics enabled: the kernels' CTRL variant.
+bool ctrl_of(const prad_ctx* c) {
+  return c->cfg.n_try > 1 || (c->cfg.select_prob > 0.0 && c->cfg.select_prob < 1.0) ||
+         c->cfg.diagnostics != 0;
+}
+
 MlpDev mlp_dev(const prad_ctx* c) {
   MlpDev d;
   d.params = c->d_mlp;
@@ -571,7 +577,8 @@ int push_emit_t(prad_ctx* c, const prad_particles* pp, int64_t n,
   const int sub_eff = sub < nsteps ? sub : nsteps;
   // persistent grid: at most the resident blocks of the kernel variant, so
   // no block waits for a second wave (blocks_per_sm = 0: all of them)
-  const int occ = push_emit_occupancy<R>(c->fields.kind, c->cfg.sampler, sub_eff, block);
+  const int occ = push_emit_occupancy<R>(c->fields.kind, c->cfg.sampler, sub_eff, block,
+                                         ctrl_of(c));
   const int bps = c->cfg.blocks_per_sm > 0 && c->cfg.blocks_per_sm < occ ? c->cfg.blocks_per_sm
                                                                          : occ;
   const int64_t want = (n + block - 1) / block;
@@ -1034,7 +1041,7 @@ int issue_batch(prad_ctx* c, int n_ens, int64_t items, int32_t nsteps, int chunk
   bp.n_ens = n_ens;
   bp.chunk = chunk;
   bp.pad = 0;
-  const int cap = batch_max_blocks_per_sm(block, c->cfg.sampler);
+  const int cap = batch_max_blocks_per_sm(block, c->cfg.sampler, ctrl_of(c));
   const int64_t g = static_cast<int64_t>(c->num_sms) * (bps < cap ? bps : cap);
   const int grid = static_cast<int>(g < items ? g : (items > 0 ? items : 1));
   for (int32_t done = 0; done < nsteps;) {
@@ -1042,7 +1049,7 @@ int issue_batch(prad_ctx* c, int n_ens, int64_t items, int32_t nsteps, int chunk
     bp.step_base = done;
     bp.nsub = m;
     CK(c, cudaMemsetAsync(c->d_batch_next, 0, sizeof(unsigned long long), c->stream));
-    CK(c, launch_push_emit_batch(bp, c->cfg.sampler, grid, block, c->stream));
+    CK(c, launch_push_emit_batch(bp, c->cfg.sampler, ctrl_of(c), grid, block, c->stream));
     done += m;
   }
   return mlp_finish(c, c->h_batch.empty() ? c->d_led_emit : c->h_batch[0].led_base);
@@ -1205,7 +1212,7 @@ int prad_autotune_batch(prad_ctx* c, const prad_ensemble* ens, int32_t n_ens, in
   int rc_all = PRAD_OK;
   for (int bi = 0; bi < 2 && rc_all == PRAD_OK; ++bi) {
     const int block = blocks[bi];
-    const int cap = batch_max_blocks_per_sm(block, c->cfg.sampler);
+    const int cap = batch_max_blocks_per_sm(block, c->cfg.sampler, ctrl_of(c));
     for (int bps = 2; bps <= cap && bps <= 2 * (256 / block) * 3 && rc_all == PRAD_OK; ++bps) {
       for (int ci = 0; ci < 4 && rc_all == PRAD_OK; ++ci) {
         const int chunk = chunks[ci];

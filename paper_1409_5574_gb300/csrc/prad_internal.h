@@ -142,11 +142,11 @@ struct BatchParams {
 };
 
 // Launchers (defined in the kernel translation units).
-cudaError_t launch_push_emit_batch(const BatchParams& bp, int sampler, int grid, int block,
-                                   cudaStream_t s);
+cudaError_t launch_push_emit_batch(const BatchParams& bp, int sampler, bool ctrl, int grid,
+                                   int block, cudaStream_t s);
 template <typename R>
-int push_emit_occupancy(int field_kind, int sampler, int nsub, int block);
-int batch_max_blocks_per_sm(int block, int sampler);
+int push_emit_occupancy(int field_kind, int sampler, int nsub, int block, bool ctrl);
+int batch_max_blocks_per_sm(int block, int sampler, bool ctrl);
 template <typename R>
 cudaError_t launch_push_emit(const StepParams<R>& p, int field_kind, int sampler, int grid,
                              int block, cudaStream_t s);

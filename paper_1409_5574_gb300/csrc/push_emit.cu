@@ -552,7 +552,9 @@ __device__ __forceinline__ void load_state(const StepParams<R>& P, int64_t i, bo
 // atomic per particle per launch would keep L2's atomic units busy, and the
 // photon cursor's atomic waits behind them.
 // ONE: the launch is known to advance exactly one step (P.nsub == 1).
-template <typename R, int FIELD, int SAMP, bool ONE = false, class G>
+// CTRL: super-photon control or diagnostics are enabled (the plain method
+// compiles without their per-step work).
+template <typename R, int FIELD, int SAMP, bool ONE = false, bool CTRL = false, class G>
 __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const G& gat,
                                                  int64_t i, const PState<R>& st,
                                                  PhotonStage& stage, int& fill,
@@ -639,7 +641,7 @@ __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const G
       c2 = c2 > R(0) ? c2 : R(0);
       Om = ua2 > R(0) ? R(0.5) * (g0 + g1) * sqr(c2) * rcp(ua2) * P.inv_dtn : R(0);
     }
-    if constexpr (FIELD == PRAD_FIELD_PLANE_WAVE) {
+    if constexpr (FIELD == PRAD_FIELD_PLANE_WAVE && CTRL) {
       if (P.diag & PRAD_DIAG_WIGGLER) {
         // synchrotron (wiggler) regime: Omega tau_EM > 1 with tau_EM the
         // field period the particle sees, 1 / (omega_L |1 - dir beta_x|)
@@ -701,7 +703,7 @@ __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const G
           stage_photon_mask(stage, fill, pout, want, mask, rec, pid, step);
         }
       };
-      if (P.ntry == 1 && !(P.sel_q < R(1))) {
+      if constexpr (!CTRL) {
         trial(rnd.x, rnd.y, Rr, R(1), R(1), live);
       } else {
         // super-photon control: a particle takes part with probability
@@ -725,7 +727,8 @@ __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const G
       const R k = fl + ((Rr < pm - fl) ? R(1) : R(0));
       if (live && pm > R(1)) ++cnt.dn1;
       // super-photon control: selection with probability sel_q
-      const bool part = live && (!(P.sel_q < R(1)) || unit_uniform<R>(rnd.w) < P.sel_q);
+      bool part = live;
+      if constexpr (CTRL) part = live && unit_uniform<R>(rnd.w) < P.sel_q;
       const bool want = part && k > R(0) && w > R(0);
       const unsigned wmask = __ballot_sync(0xffffffffu, want);
       if (wmask) {
@@ -734,7 +737,7 @@ __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const G
         const float rec[8] = {static_cast<float>(xn), static_cast<float>(yn),
                               static_cast<float>(zn), static_cast<float>(ax),
                               static_cast<float>(ay), static_cast<float>(az),
-                              0.0f, static_cast<float>(k * w * P.inv_sel_q)};
+                              0.0f, static_cast<float>(CTRL ? k * w * P.inv_sel_q : k * w)};
         const float pend[4] = {fmaf(static_cast<float>(rnd.x), 0x1p-32f, 0x1p-33f),
                                static_cast<float>(ga), static_cast<float>(epsc),
                                __int_as_float(li_abs)};
@@ -849,7 +852,7 @@ int occupancy_of(K kernel, int block, size_t dyn) {
 #ifndef PRAD_PF_MINB
 #define PRAD_PF_MINB 4
 #endif
-template <typename R, int FIELD, int SAMP, bool PF>
+template <typename R, int FIELD, int SAMP, bool PF, bool CTRL>
 __global__ void __launch_bounds__(256, (PF ? PRAD_PF_MINB : MinBlocks<R, FIELD, SAMP>::value))
     k_push_emit(const StepParams<R> P) {
   __shared__ PhotonStage stage_all[kMaxWarps];
@@ -871,14 +874,14 @@ __global__ void __launch_bounds__(256, (PF ? PRAD_PF_MINB : MinBlocks<R, FIELD, 
       const PState<R> cur = nxt;
       const int64_t j = i + stride;
       load_state<R, true>(P, j, j < P.n, nxt);
-      advance_particle<R, FIELD, SAMP, true>(P, gat, i, cur, stage, fill, pout, cnt);
+      advance_particle<R, FIELD, SAMP, true, CTRL>(P, gat, i, cur, stage, fill, pout, cnt);
     }
   } else {
     for (int64_t base = first; base < P.n; base += stride) {
       const int64_t i = base + threadIdx.x;
       PState<R> cur;
       load_state(P, i, i < P.n, cur);
-      advance_particle<R, FIELD, SAMP>(P, gat, i, cur, stage, fill, pout, cnt);
+      advance_particle<R, FIELD, SAMP, false, CTRL>(P, gat, i, cur, stage, fill, pout, cnt);
     }
   }
   if (fill > 0) flush_stage<SAMP != PRAD_SAMPLER_TABLE>(stage, fill, pout);
@@ -894,7 +897,7 @@ __global__ void __launch_bounds__(256, (PF ? PRAD_PF_MINB : MinBlocks<R, FIELD, 
 #ifndef PRAD_BATCH_MINB
 #define PRAD_BATCH_MINB 3
 #endif
-template <int SAMP>
+template <int SAMP, bool CTRL>
 __global__ void __launch_bounds__(256, PRAD_BATCH_MINB)
     k_push_emit_batch(const BatchParams bp) {
   __shared__ PhotonStage stage_all[kMaxWarps];
@@ -951,8 +954,8 @@ __global__ void __launch_bounds__(256, PRAD_BATCH_MINB)
         const int64_t i = base + threadIdx.x;
         PState<float> st;
         load_state(Ps, i, i < last, st);
-        advance_particle<float, PRAD_FIELD_CONST, SAMP>(Ps, gat, i, st, stage, fill, pout,
-                                                        cnt);
+        advance_particle<float, PRAD_FIELD_CONST, SAMP, false, CTRL>(Ps, gat, i, st, stage,
+                                                                     fill, pout, cnt);
       }
     } else {
       const FieldGather<float, PRAD_FIELD_PLANE_WAVE> gat{Ps};
@@ -960,8 +963,9 @@ __global__ void __launch_bounds__(256, PRAD_BATCH_MINB)
         const int64_t i = base + threadIdx.x;
         PState<float> st;
         load_state(Ps, i, i < last, st);
-        advance_particle<float, PRAD_FIELD_PLANE_WAVE, SAMP>(Ps, gat, i, st, stage, fill,
-                                                             pout, cnt);
+        advance_particle<float, PRAD_FIELD_PLANE_WAVE, SAMP, false, CTRL>(Ps, gat, i, st,
+                                                                          stage, fill, pout,
+                                                                          cnt);
       }
     }
     __syncthreads();
@@ -972,32 +976,39 @@ __global__ void __launch_bounds__(256, PRAD_BATCH_MINB)
 }
 
 template <int SAMP>
-cudaError_t launch_batch_samp(const BatchParams& bp, int grid, int block, cudaStream_t s) {
-  k_push_emit_batch<SAMP><<<grid, block, 0, s>>>(bp);
+cudaError_t launch_batch_samp(const BatchParams& bp, bool ctrl, int grid, int block,
+                              cudaStream_t s) {
+  if (ctrl)
+    k_push_emit_batch<SAMP, true><<<grid, block, 0, s>>>(bp);
+  else
+    k_push_emit_batch<SAMP, false><<<grid, block, 0, s>>>(bp);
   return cudaGetLastError();
 }
 
-cudaError_t launch_push_emit_batch(const BatchParams& bp, int sampler, int grid, int block,
-                                   cudaStream_t s) {
+cudaError_t launch_push_emit_batch(const BatchParams& bp, int sampler, bool ctrl, int grid,
+                                   int block, cudaStream_t s) {
   switch (sampler) {
-    case PRAD_SAMPLER_TABLE: return launch_batch_samp<PRAD_SAMPLER_TABLE>(bp, grid, block, s);
-    case PRAD_SAMPLER_MLP: return launch_batch_samp<PRAD_SAMPLER_MLP>(bp, grid, block, s);
+    case PRAD_SAMPLER_TABLE:
+      return launch_batch_samp<PRAD_SAMPLER_TABLE>(bp, ctrl, grid, block, s);
+    case PRAD_SAMPLER_MLP: return launch_batch_samp<PRAD_SAMPLER_MLP>(bp, ctrl, grid, block, s);
     case PRAD_SAMPLER_MLP_FALLBACK:
-      return launch_batch_samp<PRAD_SAMPLER_MLP_FALLBACK>(bp, grid, block, s);
+      return launch_batch_samp<PRAD_SAMPLER_MLP_FALLBACK>(bp, ctrl, grid, block, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
 template <int SAMP>
-int batch_occupancy_samp(int block) {
-  return occupancy_of(k_push_emit_batch<SAMP>, block, 0);
+int batch_occupancy_samp(int block, bool ctrl) {
+  return ctrl ? occupancy_of(k_push_emit_batch<SAMP, true>, block, 0)
+              : occupancy_of(k_push_emit_batch<SAMP, false>, block, 0);
 }
 
-int batch_max_blocks_per_sm(int block, int sampler) {
+int batch_max_blocks_per_sm(int block, int sampler, bool ctrl) {
   switch (sampler) {
-    case PRAD_SAMPLER_MLP: return batch_occupancy_samp<PRAD_SAMPLER_MLP>(block);
-    case PRAD_SAMPLER_MLP_FALLBACK: return batch_occupancy_samp<PRAD_SAMPLER_MLP_FALLBACK>(block);
-    default: return batch_occupancy_samp<PRAD_SAMPLER_TABLE>(block);
+    case PRAD_SAMPLER_MLP: return batch_occupancy_samp<PRAD_SAMPLER_MLP>(block, ctrl);
+    case PRAD_SAMPLER_MLP_FALLBACK:
+      return batch_occupancy_samp<PRAD_SAMPLER_MLP_FALLBACK>(block, ctrl);
+    default: return batch_occupancy_samp<PRAD_SAMPLER_TABLE>(block, ctrl);
   }
 }
 
@@ -1007,7 +1018,7 @@ int batch_max_blocks_per_sm(int block, int sampler) {
 // (+ halo, periodic) in shared memory with coalesced row loads, then runs the
 // same per-particle path with the shared-memory gather.
 // ---------------------------------------------------------------------------
-template <typename R>
+template <typename R, bool CTRL>
 __global__ void __launch_bounds__(256, 3) k_push_emit_tiled(const StepParams<R> P) {
   if (blockIdx.x >= *P.work_count) return;
   extern __shared__ float tile_sm[];
@@ -1047,8 +1058,8 @@ __global__ void __launch_bounds__(256, 3) k_push_emit_tiled(const StepParams<R> 
     const int64_t i = base + threadIdx.x;
     PState<R> st;
     load_state(P, i, i < wk.z, st);
-    advance_particle<R, PRAD_FIELD_YEE2D, PRAD_SAMPLER_TABLE>(P, gat, i, st, stage, fill, pout,
-                                                              cnt);
+    advance_particle<R, PRAD_FIELD_YEE2D, PRAD_SAMPLER_TABLE, false, CTRL>(P, gat, i, st, stage,
+                                                                           fill, pout, cnt);
   }
   if (fill > 0) flush_stage(stage, fill, pout);
   flush_counts(cnt, P.counters);
@@ -1058,64 +1069,86 @@ template <typename R>
 cudaError_t launch_push_emit_tiled(const StepParams<R>& p, int max_work, int block,
                                    cudaStream_t s) {
   // dynamic tile (38.4 KB) + static photon staging exceed the 48 KB default
-  cudaError_t e = cudaFuncSetAttribute(k_push_emit_tiled<R>,
+  const bool ctrl = p.ntry > 1 || p.sel_q < R(1) || p.diag != 0;
+  cudaError_t e = cudaFuncSetAttribute(ctrl ? k_push_emit_tiled<R, true> : k_push_emit_tiled<R, false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        kTileSmemBytes);
   if (e != cudaSuccess) return e;
-  k_push_emit_tiled<R><<<max_work, block, kTileSmemBytes, s>>>(p);
+  if (ctrl)
+    k_push_emit_tiled<R, true><<<max_work, block, kTileSmemBytes, s>>>(p);
+  else
+    k_push_emit_tiled<R, false><<<max_work, block, kTileSmemBytes, s>>>(p);
   return cudaGetLastError();
 }
 
-template <typename R, int FIELD>
-cudaError_t launch_field(const StepParams<R>& p, int sampler, int grid, int block,
-                         cudaStream_t s) {
+template <typename R, int FIELD, bool CTRL>
+cudaError_t launch_field_c(const StepParams<R>& p, int sampler, int grid, int block,
+                           cudaStream_t s) {
   if (sampler == PRAD_SAMPLER_TABLE) {
-    // prefetching pays when the launch is short (state streamed from HBM);
-    // for long fused launches it only costs registers
+    // prefetching pays when the state streams through HBM (one step per
+    // launch); for long fused launches it only costs registers
     bool pf = false;
     if constexpr (sizeof(R) == 4) pf = p.nsub == 1;
     if constexpr (sizeof(R) == 4)
-      if (pf) k_push_emit<R, FIELD, PRAD_SAMPLER_TABLE, true><<<grid, block, 0, s>>>(p);
-    if (!pf) k_push_emit<R, FIELD, PRAD_SAMPLER_TABLE, false><<<grid, block, 0, s>>>(p);
+      if (pf) k_push_emit<R, FIELD, PRAD_SAMPLER_TABLE, true, CTRL><<<grid, block, 0, s>>>(p);
+    if (!pf) k_push_emit<R, FIELD, PRAD_SAMPLER_TABLE, false, CTRL><<<grid, block, 0, s>>>(p);
     return cudaGetLastError();
   }
   if constexpr (sizeof(R) == 4) {
     if (sampler == PRAD_SAMPLER_MLP)
-      k_push_emit<R, FIELD, PRAD_SAMPLER_MLP, false><<<grid, block, 0, s>>>(p);
+      k_push_emit<R, FIELD, PRAD_SAMPLER_MLP, false, CTRL><<<grid, block, 0, s>>>(p);
     else
-      k_push_emit<R, FIELD, PRAD_SAMPLER_MLP_FALLBACK, false><<<grid, block, 0, s>>>(p);
+      k_push_emit<R, FIELD, PRAD_SAMPLER_MLP_FALLBACK, false, CTRL><<<grid, block, 0, s>>>(p);
     return cudaGetLastError();
   }
   return cudaErrorInvalidValue;
 }
 
 template <typename R, int FIELD>
-int field_occupancy(int sampler, bool pf, int block) {
+cudaError_t launch_field(const StepParams<R>& p, int sampler, int grid, int block,
+                         cudaStream_t s) {
+  const bool ctrl = p.ntry > 1 || p.sel_q < R(1) || p.diag != 0;
+  return ctrl ? launch_field_c<R, FIELD, true>(p, sampler, grid, block, s)
+              : launch_field_c<R, FIELD, false>(p, sampler, grid, block, s);
+}
+
+template <typename R, int FIELD, bool CTRL>
+int field_occupancy_c(int sampler, bool pf, int block) {
   if (sampler == PRAD_SAMPLER_TABLE) {
     if constexpr (sizeof(R) == 4)
-      if (pf) return occupancy_of(k_push_emit<R, FIELD, PRAD_SAMPLER_TABLE, true>, block, 0);
-    return occupancy_of(k_push_emit<R, FIELD, PRAD_SAMPLER_TABLE, false>, block, 0);
+      if (pf)
+        return occupancy_of(k_push_emit<R, FIELD, PRAD_SAMPLER_TABLE, true, CTRL>, block, 0);
+    return occupancy_of(k_push_emit<R, FIELD, PRAD_SAMPLER_TABLE, false, CTRL>, block, 0);
   }
   if constexpr (sizeof(R) == 4) {
     if (sampler == PRAD_SAMPLER_MLP)
-      return occupancy_of(k_push_emit<R, FIELD, PRAD_SAMPLER_MLP, false>, block, 0);
-    return occupancy_of(k_push_emit<R, FIELD, PRAD_SAMPLER_MLP_FALLBACK, false>, block, 0);
+      return occupancy_of(k_push_emit<R, FIELD, PRAD_SAMPLER_MLP, false, CTRL>, block, 0);
+    return occupancy_of(k_push_emit<R, FIELD, PRAD_SAMPLER_MLP_FALLBACK, false, CTRL>, block,
+                        0);
   }
   return 1;
 }
 
+template <typename R, int FIELD>
+int field_occupancy(int sampler, bool pf, int block, bool ctrl) {
+  return ctrl ? field_occupancy_c<R, FIELD, true>(sampler, pf, block)
+              : field_occupancy_c<R, FIELD, false>(sampler, pf, block);
+}
+
 // Resident blocks per SM of the kernel variant a launch would use.
 template <typename R>
-int push_emit_occupancy(int field_kind, int sampler, int nsub, int block) {
+int push_emit_occupancy(int field_kind, int sampler, int nsub, int block, bool ctrl) {
   const bool pf = nsub == 1;
   switch (field_kind) {
-    case PRAD_FIELD_CONST: return field_occupancy<R, PRAD_FIELD_CONST>(sampler, pf, block);
-    case PRAD_FIELD_PLANE_WAVE: return field_occupancy<R, PRAD_FIELD_PLANE_WAVE>(sampler, pf, block);
-    default: return field_occupancy<R, PRAD_FIELD_YEE2D>(sampler, pf, block);
+    case PRAD_FIELD_CONST:
+      return field_occupancy<R, PRAD_FIELD_CONST>(sampler, pf, block, ctrl);
+    case PRAD_FIELD_PLANE_WAVE:
+      return field_occupancy<R, PRAD_FIELD_PLANE_WAVE>(sampler, pf, block, ctrl);
+    default: return field_occupancy<R, PRAD_FIELD_YEE2D>(sampler, pf, block, ctrl);
   }
 }
-template int push_emit_occupancy<float>(int, int, int, int);
-template int push_emit_occupancy<double>(int, int, int, int);
+template int push_emit_occupancy<float>(int, int, int, int, bool);
+template int push_emit_occupancy<double>(int, int, int, int, bool);
 
 template <typename R>
 cudaError_t launch_push_emit(const StepParams<R>& p, int field_kind, int sampler, int grid,

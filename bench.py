@@ -39,9 +39,9 @@ KERNEL_SOURCES = ["paper_1409_5574_gb300/csrc/push_emit.cu",
                   "paper_1409_5574_gb300/csrc/prad_internal.h",
                   "paper_1409_5574_gb300/csrc/mlp_device.cuh"]
 NCU_TRAFFIC = {
-    "src_sha256": "4bde3f98f723d861ceed8329dde2799cea9f3a284b326fcf1ef8c036a9412411",
+    "src_sha256": "5d19c2f4670dd26644ad616dbc2cde9706266355972eb5f5d07f9941e3a72615",
     "fused": None,        # bytes per launch of the bench's fused launches
-    "stream": 1334472192, # bytes per launch, 2^24 particles x 1 step, a0 = 500
+    "stream": 1334827520, # bytes per launch, 2^24 particles x 1 step, a0 = 500
 }
 
 

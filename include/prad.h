@@ -180,7 +180,10 @@ typedef struct prad_stats {
   int64_t chi_gt1;      /* steps with chi > 1 (outside classical validity) */
   int64_t mlp_fallback; /* learned-sampler draws that fell back to table   */
   int64_t nan_frozen;   /* particle-launches skipped as non-finite         */
-  int32_t status;       /* sticky device status word (0 = ok)              */
+  int32_t status;       /* sticky device status word (0 = ok): bit 1 an id
+                         * outside the ledger; bit 2 a bounded tensor-core
+                         * wait of the learned sampler ran out (the block
+                         * stopped; its remaining records keep energy 0)   */
   int32_t pad0;
   int64_t wiggler_invalid; /* PRAD_DIAG_WIGGLER: steps outside the regime  */
 } prad_stats;
@@ -321,8 +324,9 @@ int prad_get_ledger(prad_ctx* ctx, double* emit, double* ll, int64_t offset,
 int prad_reset(prad_ctx* ctx);
 
 /* ---- learned sampler (PRAD_SAMPLER_MLP, PRAD_SAMPLER_MLP_FALLBACK) --------
- * A 3 -> 64 -> 64 -> 1 MLP (SiLU, BF16 weights, FP32 accumulate) plus a
- * fixed prior ln(-ln(1 - r)) + 2 (1 - r) ln r maps
+ * A 3 -> 64 -> 64 -> 1 MLP (ReLU, activations rounded to IEEE half, BF16
+ * weights, FP32 accumulate) plus a fixed prior ln(-ln(1 - r)) + 2 (1 - r) ln r
+ * maps
  * (r, gamma, omega_c dt) to ln x with G(x) = r, G the photon-number CDF of
  * the spectrum of Eqs. (7)-(8), int_0^x F(t)/t dt / (5 pi / 3).  With an MLP
  * sampler, push_emit uses the direct scheme: the photons of a step have mean
@@ -343,12 +347,14 @@ int prad_mlp_get_weights(prad_ctx* ctx, float* params, int64_t n);
 
 /* Train the context's network on the GPU: `steps` Adam steps (lr with a
  * cosine decay to 0) on minibatches of `batch` samples generated on the
- * device (r uniform in the trained range, gamma log-uniform in [10, 1e4],
- * H_eff log-uniform in [1e2, 1e6] T, omega_c dt from the context's dt;
- * target ln G^-1(r) from the device table), loss = mean over samples of
+ * device (r uniform in the trained range; gamma and omega_c dt log-uniform
+ * over the feature box, [10, 1e4] and [e^-3.4, e^19.8]; target ln G^-1(r)
+ * from the device table), loss = mean over samples of
  * w (o - (ln x - prior(r)))^2 with o the network output, the fixed prior
- * ln(-ln(1 - r)) + 2 (1 - r) ln r and the energy weight w = (1 + x)/1.308.  *final_loss (host, may be NULL) receives the last
- * minibatch loss.  Synchronises. */
+ * ln(-ln(1 - r)) + 2 (1 - r) ln r and the energy weight w = (1 + x)/1.308,
+ * plus (1e-2 / 2) sum_j (W1[j][1]^2 + W1[j][2]^2) (the classical spectrum
+ * does not depend on gamma or omega_c dt).  *final_loss (host, may be NULL)
+ * receives the last minibatch loss.  Synchronises. */
 int prad_mlp_train(prad_ctx* ctx, int64_t steps, int32_t batch, float lr, uint64_t seed,
                    float* final_loss);
 
@@ -360,8 +366,20 @@ int prad_mlp_grad(prad_ctx* ctx, const float* samples, int64_t n, float* grad,
                   double* loss);
 
 /* ln x = MLP(r, gamma, omega_c dt) for n device triples `in` (3 floats each)
- * into device `lnx`, with the tile evaluator of the fused kernel. */
+ * into device `lnx`, with the tile evaluator of the learned sampler's
+ * finishing kernel.  Synchronises.  PRAD_ERR_TIMEOUT if a bounded
+ * tensor-core wait ran out (status bit 2 is then set). */
 int prad_mlp_eval(prad_ctx* ctx, const float* in, float* lnx, int64_t n);
+
+/* Self-test of the bounded tensor-core waits: runs the evaluator on one
+ * 128-row tile with every MMA completion withheld, so each wait on the
+ * tensor cores runs out (about 2 s of SM clocks in all); the kernel then
+ * releases its tensor memory and reports through a status word of its own
+ * (the context's status is untouched).  Returns PRAD_ERR_TIMEOUT when the
+ * timeout was reported, as it should be (PRAD_ERR_STATE if it was not,
+ * PRAD_ERR_CUDA on a runtime error); the context stays usable.
+ * Synchronises. */
+int prad_mlp_wait_selftest(prad_ctx* ctx);
 
 /* ln G^-1(r) from the device table for n device uniforms. */
 int prad_ginv_eval(prad_ctx* ctx, const float* r, float* lnx, int64_t n);

@@ -1,13 +1,16 @@
 // Training and evaluation kernels of the learned inverse-CDF sampler
 // (mlp_device.cuh): sample generation with the device G^-1 table, a fused
-// forward + backward pass per block of 128 samples (tensor-core MMAs for the
+// forward + backward pass per block of 128 samples (m16n8k16 MMAs for the
 // 64 x 64 layer: f16 forward, BF16 gradient products), per-block partial
-// gradients, and a deterministic reduction + Adam update.
+// gradients, and a deterministic reduction + Adam update; the evaluators
+// (the learned sampler's finishing kernel and prad_mlp_eval) run the
+// network on the tcgen05 tensor cores (mlp_tc.cuh).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "mlp_device.cuh"
+#include "mlp_tc.cuh"
 #include "prad_internal.h"
 
 namespace prad {
@@ -47,14 +50,13 @@ struct TrainSmem {
   __nv_bfloat16 d2t[kHid * kLdT];     // delta2 transposed [j][s]
 };
 
-// Training samples: r from a Philox uniform (tag 3), gamma log-uniform in
-// [g_lo, g_hi], H log-uniform in [h_lo, h_hi] T, omega_c dt = 1.5 e H / m
-// gamma^2 dt; target ln G^-1(r) from the device table.
+// Training samples: r from a Philox uniform (tag 3), gamma and omega_c dt
+// log-uniform over the feature box (f1 and f2 uniform in [-1, 1]); target
+// ln G^-1(r) from the device table.
 struct SampleSpec {
   uint32_t key0, key1;
   uint64_t first;           // global index of the block's first sample
-  float lng_lo, lng_span, lnh_lo, lnh_span;
-  float wdt_per_H_g2;       // 1.5 (e/m) dt  [1 / (T)]
+  float lng_lo, lng_span, lnw_lo, lnw_span;
   const float* ginv;        // G^-1 table
   const float4* explicit_samples;  // (r, gamma, wdt, ln x target) or null
   int64_t n_total;          // samples in the whole batch (loss mean)
@@ -76,10 +78,9 @@ __device__ void make_sample(const SampleSpec& sp, int64_t idx, float* f, float* 
     const float u = fmaf(static_cast<float>(w.x), 0x1p-32f, 0x1p-33f);
     r = fminf(fmaxf(u, kRMin), kRMax);
     const float ug = fmaf(static_cast<float>(w.y), 0x1p-32f, 0x1p-33f);
-    const float uh = fmaf(static_cast<float>(w.z), 0x1p-32f, 0x1p-33f);
+    const float uw = fmaf(static_cast<float>(w.z), 0x1p-32f, 0x1p-33f);
     gam = __expf(sp.lng_lo + sp.lng_span * ug);
-    const float H = __expf(sp.lnh_lo + sp.lnh_span * uh);
-    wdt = sp.wdt_per_H_g2 * H * gam * gam;
+    wdt = __expf(sp.lnw_lo + sp.lnw_span * uw);
     lnx = ginv_ln(sp.ginv, r);
   }
   const float3 ff = mlp_features(r, gam, wdt);
@@ -116,13 +117,13 @@ __global__ void __launch_bounds__(kTThreads)
     }
   }
   __syncthreads();
-  // layer 1 (FP32, BF16 weights): z1 and bf16(silu(z1)) transposed
+  // layer 1 (FP32, BF16 weights): z1 and bf16(relu(z1)) transposed
   for (int e = threadIdx.x; e < kTB * kHid; e += blockDim.x) {
     const int s = e / kHid, j = e - s * kHid;
     const float4 w = S.net.w1b1[j];
     const float z = fmaf(w.x, S.x[s][0], fmaf(w.y, S.x[s][1], fmaf(w.z, S.x[s][2], w.w)));
     S.z1[s][j] = z;
-    S.h1t[j * kLdT + s] = __float2bfloat16(silu(z));
+    S.h1t[j * kLdT + s] = __float2bfloat16(relu(z));
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -130,40 +131,39 @@ __global__ void __launch_bounds__(kTThreads)
   // layer 2 forward, warp w: samples 16w .. 16w + 15
   {
     const int s0 = 16 * warp;
-    // h1 = f16(silu(z1)) in packed f16 arithmetic, as in the evaluator
+    // h1 = f16(relu(z1)), as in the evaluator
     uint32_t a[4][4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int j = 16 * q + 2 * t;
-      a[q][0] = silu_f16x2(S.z1[s0 + g][j], S.z1[s0 + g][j + 1]);
-      a[q][1] = silu_f16x2(S.z1[s0 + g + 8][j], S.z1[s0 + g + 8][j + 1]);
-      a[q][2] = silu_f16x2(S.z1[s0 + g][j + 8], S.z1[s0 + g][j + 9]);
-      a[q][3] = silu_f16x2(S.z1[s0 + g + 8][j + 8], S.z1[s0 + g + 8][j + 9]);
+      a[q][0] = relu_f16x2(S.z1[s0 + g][j], S.z1[s0 + g][j + 1]);
+      a[q][1] = relu_f16x2(S.z1[s0 + g + 8][j], S.z1[s0 + g + 8][j + 1]);
+      a[q][2] = relu_f16x2(S.z1[s0 + g][j + 8], S.z1[s0 + g][j + 9]);
+      a[q][3] = relu_f16x2(S.z1[s0 + g + 8][j + 8], S.z1[s0 + g + 8][j + 9]);
     }
-    // the network image holds W2 / 2 and b2 / 2 (exact): z2 = 2 c
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt) {
       const int j0 = 8 * nt + 2 * t;
-      float c[4] = {S.net.b2h[j0], S.net.b2h[j0 + 1], S.net.b2h[j0], S.net.b2h[j0 + 1]};
+      float c[4] = {S.net.b2[j0], S.net.b2[j0 + 1], S.net.b2[j0], S.net.b2[j0 + 1]};
       const __half* wrow = S.net.w2h + (8 * nt + g) * kW2Ld + 2 * t;
 #pragma unroll
       for (int q = 0; q < 4; ++q)
         mma_f16_16816(c, a[q][0], a[q][1], a[q][2], a[q][3],
                       *reinterpret_cast<const uint32_t*>(wrow + 16 * q),
                       *reinterpret_cast<const uint32_t*>(wrow + 16 * q + 8));
-      S.z2[s0 + g][j0] = 2.0f * c[0];
-      S.z2[s0 + g][j0 + 1] = 2.0f * c[1];
-      S.z2[s0 + g + 8][j0] = 2.0f * c[2];
-      S.z2[s0 + g + 8][j0 + 1] = 2.0f * c[3];
+      S.z2[s0 + g][j0] = c[0];
+      S.z2[s0 + g][j0 + 1] = c[1];
+      S.z2[s0 + g + 8][j0] = c[2];
+      S.z2[s0 + g + 8][j0 + 1] = c[3];
     }
   }
   __syncthreads();
-  // output (h2 = f16(silu(z2)) as in the evaluator), loss and dL/do per sample
+  // output (h2 = f16(relu(z2)) as in the evaluator), loss and dL/do per sample
   if (threadIdx.x < kTB) {
     const int s = threadIdx.x;
     float o = S.net.b3;
     for (int j = 0; j < kHid; j += 2) {
-      const uint32_t hh = silu_f16x2(S.z2[s][j], S.z2[s][j + 1]);
+      const uint32_t hh = relu_f16x2(S.z2[s][j], S.z2[s][j + 1]);
       const float2 h2 = __half22float2(*reinterpret_cast<const __half2*>(&hh));
       o = fmaf(S.net.w3[j], h2.x, o);
       o = fmaf(S.net.w3[j + 1], h2.y, o);
@@ -175,11 +175,11 @@ __global__ void __launch_bounds__(kTThreads)
     S.dout[s] = valid ? 2.0f * wgt * diff / static_cast<float>(sp.n_total) : 0.0f;
   }
   __syncthreads();
-  // delta2 = dout W3 silu'(z2): BF16 copies for the two tensor-core products
+  // delta2 = dout W3 relu'(z2): BF16 copies for the two tensor-core products
   for (int e = threadIdx.x; e < kTB * kHid; e += blockDim.x) {
     const int s = e / kHid, j = e - s * kHid;
     const __nv_bfloat16 d =
-        __float2bfloat16(S.dout[s] * S.net.w3[j] * silu_grad(S.z2[s][j]));
+        __float2bfloat16(S.dout[s] * S.net.w3[j] * relu_grad(S.z2[s][j]));
     S.d2[s * kW2Ld + j] = d;
     S.d2t[j * kLdT + s] = d;
   }
@@ -190,8 +190,8 @@ __global__ void __launch_bounds__(kTThreads)
     const int j = threadIdx.x;
     float dw3 = 0.0f, db2 = 0.0f;
     for (int s = 0; s < kTB; ++s) {
-      dw3 = fmaf(S.dout[s], silu(S.z2[s][j]), dw3);
-      db2 = fmaf(S.dout[s] * S.net.w3[j], silu_grad(S.z2[s][j]), db2);
+      dw3 = fmaf(S.dout[s], relu(S.z2[s][j]), dw3);
+      db2 = fmaf(S.dout[s] * S.net.w3[j], relu_grad(S.z2[s][j]), db2);
     }
     gp[kOffW3 + j] = dw3;
     gp[kOffB2 + j] = db2;
@@ -202,11 +202,19 @@ __global__ void __launch_bounds__(kTThreads)
       db3 += S.dout[s];
       ls += S.loss[s];
     }
+    if (blockIdx.x == 0) {  // the input-weight decay, once per batch (scaled back by 1/n)
+      float pen = 0.0f;
+      for (int j = 0; j < kHid; ++j) {
+        const float a = dev.params[kOffW1 + 3 * j + 1], b = dev.params[kOffW1 + 3 * j + 2];
+        pen = fmaf(a, a, fmaf(b, b, pen));
+      }
+      ls += 0.5f * kInputDecay * pen * static_cast<float>(sp.n_total);
+    }
     gp[kOffB3] = db3;
     loss_part[blockIdx.x] = ls;
   }
   __syncthreads();  // z2 is overwritten by delta1 below
-  // delta1 = (delta2 W2) * silu'(z1), warp w: samples 16w .. 16w + 15
+  // delta1 = (delta2 W2) * relu'(z1), warp w: samples 16w .. 16w + 15
   {
     const int s0 = 16 * warp;
     uint32_t a[4][4];
@@ -229,10 +237,10 @@ __global__ void __launch_bounds__(kTThreads)
                        *reinterpret_cast<const uint32_t*>(brow + 16 * q),
                        *reinterpret_cast<const uint32_t*>(brow + 16 * q + 8));
       const int i0 = 8 * nt + 2 * t;
-      S.z2[s0 + g][i0] = c[0] * silu_grad(S.z1[s0 + g][i0]);
-      S.z2[s0 + g][i0 + 1] = c[1] * silu_grad(S.z1[s0 + g][i0 + 1]);
-      S.z2[s0 + g + 8][i0] = c[2] * silu_grad(S.z1[s0 + g + 8][i0]);
-      S.z2[s0 + g + 8][i0 + 1] = c[3] * silu_grad(S.z1[s0 + g + 8][i0 + 1]);
+      S.z2[s0 + g][i0] = c[0] * relu_grad(S.z1[s0 + g][i0]);
+      S.z2[s0 + g][i0 + 1] = c[1] * relu_grad(S.z1[s0 + g][i0 + 1]);
+      S.z2[s0 + g + 8][i0] = c[2] * relu_grad(S.z1[s0 + g + 8][i0]);
+      S.z2[s0 + g + 8][i0 + 1] = c[3] * relu_grad(S.z1[s0 + g + 8][i0 + 1]);
     }
   }
   // dW2 = delta2^T h1 over the block's 128 samples: output [j][i];
@@ -276,9 +284,11 @@ __global__ void __launch_bounds__(kTThreads)
       a2 = fmaf(d, S.x[s][2], a2);
       b += d;
     }
+    // block 0 adds the gradient of the input-weight decay
+    const float dec = blockIdx.x == 0 ? kInputDecay : 0.0f;
     gp[kOffW1 + 3 * j] = a0;
-    gp[kOffW1 + 3 * j + 1] = a1;
-    gp[kOffW1 + 3 * j + 2] = a2;
+    gp[kOffW1 + 3 * j + 1] = fmaf(dec, dev.params[kOffW1 + 3 * j + 1], a1);
+    gp[kOffW1 + 3 * j + 2] = fmaf(dec, dev.params[kOffW1 + 3 * j + 2], a2);
     gp[kOffB1 + j] = b;
   }
 }
@@ -313,103 +323,132 @@ __global__ void k_mlp_reduce_adam(const float* __restrict__ partial, int nblocks
   if (p >= kOffW2 && p < kOffB2) w2[p - kOffW2] = __float2bfloat16(np);
 }
 
-// Evaluate ln x for n (r, gamma, omega_c dt) triples with the same tile
-// function the fused push kernel uses.
-__global__ void __launch_bounds__(256) k_mlp_eval(MlpDev dev, const float* __restrict__ in,
-                                                  float* __restrict__ out, int64_t n) {
-  __shared__ MlpSmem S;
-  mlp_load_smem(S, dev);
+// The finishing kernel on the tcgen05 tensor cores (mlp_tc.cuh): tiles of
+// 128 consecutive records, one per thread, two tiles in flight per CTA.  A
+// slot's payload (r, gamma, eps_c, ledger index) and weight are loaded two
+// tiles ahead.  A tensor-core wait that runs out stops the block and sets
+// status bit 2.
+struct FinishSrc {
+  const MlpFinishArgs& a;
+  unsigned long long first, stride, end;
+  float4 pd0, pd1, nx0, nx1;  // slot payloads: current tile and the next
+  float w0, w1, nw0, nw1;
+  uint32_t fb = 0;
+
+  __device__ FinishSrc(const MlpFinishArgs& args, unsigned long long beg)
+      : a(args) {
+    const unsigned long long cur = a.counters[kCursor];
+    const unsigned long long cap = static_cast<unsigned long long>(a.cap);
+    end = cur < cap ? cur : cap;
+    first = beg + static_cast<unsigned long long>(blockIdx.x) * kTcRows + threadIdx.x;
+    stride = static_cast<unsigned long long>(gridDim.x) * kTcRows;
+    load(first, nx0, nw0);
+    load(first + stride, nx1, nw1);
+  }
+  __device__ void load(unsigned long long row, float4& pd, float& w) const {
+    // past the end: a harmless payload that books nothing (ledger index -1)
+    pd = row < end ? a.pend[row] : make_float4(0.5f, 1.0f, 0.0f, __int_as_float(-1));
+    w = row < end ? a.weight[row] : 0.0f;
+  }
+  __device__ bool has(long long k) const { return first - threadIdx.x + k * stride < end; }
+  __device__ float3 features(int sl, long long k) {
+    const unsigned long long ahead = first + (k + 2) * stride;
+    float4& pd = sl == 0 ? pd0 : pd1;
+    float4& nx = sl == 0 ? nx0 : nx1;
+    float& w = sl == 0 ? w0 : w1;
+    float& nw = sl == 0 ? nw0 : nw1;
+    pd = nx;
+    w = nw;
+    load(ahead, nx, nw);
+    return mlp_features(pd.x, pd.y, pd.z * a.wdt_per_eps);
+  }
+  __device__ void finish(int sl, long long k, float o) {
+    const float4 pd = sl == 0 ? pd0 : pd1;
+    const float w = sl == 0 ? w0 : w1;
+    const unsigned long long row = first + k * stride;
+    if (row >= end) return;
+    float x = __expf(o + mlp_prior(pd.x));
+    // uniforms outside the trained range always take the G^-1 table
+    const bool tail = pd.x < kRMin || pd.x > kRMax;
+    const bool ok = x > 0.0f && x < 80.0f;  // also false for NaN
+    if (tail || (a.check_output && !ok)) {
+      x = __expf(ginv_ln(a.ginv, pd.x));
+      ++fb;
+    } else if (!ok) {
+      x = 0.0f;  // no fallback requested: an invalid draw carries no energy
+    }
+    const float eps = x * pd.z;
+    a.eps[row] = eps;
+    const int li = __float_as_int(pd.w);
+    if (li >= 0) atomicAdd(a.led_emit + li, static_cast<double>(w) * static_cast<double>(eps));
+  }
+};
+
+#ifndef PRAD_TC_MINB
+#define PRAD_TC_MINB 4
+#endif
+__global__ void __launch_bounds__(kTcRows, PRAD_TC_MINB) k_mlp_finish_tc(const MlpFinishArgs a) {
+  extern __shared__ unsigned char tc_raw[];
+  TcSmem& S = tc_smem(tc_raw);
+  tc_setup(S, a.mlp);
+  FinishSrc src(a, a.counters[kMlpDone]);
+  const bool failed = tc_run(S, src);
+  const uint32_t fb = __reduce_add_sync(0xffffffffu, src.fb);
+  if ((threadIdx.x & 31) == 0 && fb)
+    atomicAdd(a.counters + kMlpFallback, static_cast<unsigned long long>(fb));
   __syncthreads();
-  const int lane = threadIdx.x & 31, g = lane >> 2;
-  const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
-  for (int64_t tile = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
-       tile * 16 < n; tile += warps) {
-    const int64_t r0 = tile * 16 + g, r1 = r0 + 8;
-    float3 flo = make_float3(0.f, 0.f, 0.f), fhi = flo;
-    if (r0 < n) flo = mlp_features(in[3 * r0], in[3 * r0 + 1], in[3 * r0 + 2]);
-    if (r1 < n) fhi = mlp_features(in[3 * r1], in[3 * r1 + 1], in[3 * r1 + 2]);
-    float olo, ohi;
-    mlp_tile16(S, flo, fhi, olo, ohi);
-    if ((lane & 3) == 0) {
-      if (r0 < n) out[r0] = olo + mlp_prior(in[3 * r0]);
-      if (r1 < n) out[r1] = ohi + mlp_prior(in[3 * r1]);
+  if (threadIdx.x == 0) {
+    if (failed) atomicOr(a.counters + kStatus, 4ull);  // status bit 2: tensor-core wait
+    __threadfence();
+    const unsigned long long t = atomicAdd(a.counters + kMlpBlocks, 1ull);
+    if (t == gridDim.x - 1ull) {
+      a.counters[kMlpDone] = src.end;
+      a.counters[kMlpBlocks] = 0ull;
     }
   }
 }
 
-// Energies of the learned sampler's deferred records (MlpFinishArgs): each
-// warp takes 32 consecutive records at a time, one row per lane for the
-// features, the output and the writes, evaluated as two 16-row tiles.  The
-// last block to finish marks the range as done.
-#ifndef PRAD_FINISH_MINB
-#define PRAD_FINISH_MINB 4
-#endif
-__global__ void __launch_bounds__(256, PRAD_FINISH_MINB) k_mlp_finish(const MlpFinishArgs a) {
-  __shared__ MlpSmem S;
-  mlp_load_smem(S, a.mlp);
-  __syncthreads();
-  const unsigned long long cur = a.counters[kCursor];
-  const unsigned long long cap = static_cast<unsigned long long>(a.cap);
-  const unsigned long long end = cur < cap ? cur : cap;
-  const unsigned long long beg = a.counters[kMlpDone];
-  const int lane = threadIdx.x & 31, g = lane >> 2;
-  const unsigned long long warps = static_cast<unsigned long long>(gridDim.x) * (blockDim.x >> 5);
-  const unsigned long long wid =
-      static_cast<unsigned long long>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  uint32_t fb = 0;
-  for (unsigned long long base = beg + 32ull * wid; base < end; base += 32ull * warps) {
-    const unsigned long long row = base + static_cast<unsigned>(lane);
-    const bool mine = row < end;
-    float4 pd = make_float4(0.5f, 1.0f, 0.0f, __int_as_float(-1));
-    if (mine) pd = a.pend[row];
-    const float3 f = mlp_features(pd.x, pd.y, pd.z * a.wdt_per_eps);
-    float o_row = 0.0f;
-#pragma unroll 1
-    for (int h = 0; h < 2; ++h) {
-      // tile h: rows 16h .. 16h + 15 (lanes 16h ..); lane (g, t) needs rows g, g + 8
-      float3 flo, fhi;
-      flo.x = __shfl_sync(0xffffffffu, f.x, 16 * h + g);
-      flo.y = __shfl_sync(0xffffffffu, f.y, 16 * h + g);
-      flo.z = __shfl_sync(0xffffffffu, f.z, 16 * h + g);
-      fhi.x = __shfl_sync(0xffffffffu, f.x, 16 * h + g + 8);
-      fhi.y = __shfl_sync(0xffffffffu, f.y, 16 * h + g + 8);
-      fhi.z = __shfl_sync(0xffffffffu, f.z, 16 * h + g + 8);
-      float olo, ohi;
-      mlp_tile16(S, flo, fhi, olo, ohi);
-      // row L of the tile lives in lane 4 (L % 8), in olo (L < 8) or ohi
-      const float vlo = __shfl_sync(0xffffffffu, olo, (lane & 7) * 4);
-      const float vhi = __shfl_sync(0xffffffffu, ohi, (lane & 7) * 4);
-      if ((lane >> 4) == h) o_row = (lane & 8) ? vhi : vlo;
-    }
-    if (mine) {
-      float x = __expf(o_row + mlp_prior(pd.x));
-      // uniforms outside the trained range always take the G^-1 table
-      const bool tail = pd.x < kRMin || pd.x > kRMax;
-      const bool ok = x > 0.0f && x < 80.0f;  // also false for NaN
-      if (tail || (a.check_output && !ok)) {
-        x = __expf(ginv_ln(a.ginv, pd.x));
-        ++fb;
-      } else if (!ok) {
-        x = 0.0f;  // no fallback requested: an invalid draw carries no energy
-      }
-      const float eps = x * pd.z;
-      a.eps[row] = eps;
-      const int li = __float_as_int(pd.w);
-      if (li >= 0)
-        atomicAdd(a.led_emit + li, static_cast<double>(a.weight[row]) * static_cast<double>(eps));
-    }
+// ln x for n (r, gamma, omega_c dt) triples with the finishing kernel's
+// network.  A tensor-core wait that runs out sets status bit 2.
+struct EvalSrc {
+  const float* in;
+  float* out;
+  int64_t n, first, stride;
+  float3 v0, v1, nx0, nx1;
+
+  __device__ EvalSrc(const float* i, float* o, int64_t count) : in(i), out(o), n(count) {
+    first = static_cast<int64_t>(blockIdx.x) * kTcRows + threadIdx.x;
+    stride = static_cast<int64_t>(gridDim.x) * kTcRows;
+    nx0 = load(first);
+    nx1 = load(first + stride);
   }
-  fb = __reduce_add_sync(0xffffffffu, fb);
-  if (lane == 0 && fb) atomicAdd(a.counters + kMlpFallback, static_cast<unsigned long long>(fb));
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    const unsigned long long t = atomicAdd(a.counters + kMlpBlocks, 1ull);
-    if (t == gridDim.x - 1ull) {
-      a.counters[kMlpDone] = end;
-      a.counters[kMlpBlocks] = 0ull;
-    }
+  __device__ float3 load(int64_t i) const {
+    return i < n ? make_float3(in[3 * i], in[3 * i + 1], in[3 * i + 2])
+                 : make_float3(0.5f, 1.0f, 1.0f);
   }
+  __device__ bool has(long long k) const { return first - threadIdx.x + k * stride < n; }
+  __device__ float3 features(int sl, long long k) {
+    float3& v = sl == 0 ? v0 : v1;
+    float3& nx = sl == 0 ? nx0 : nx1;
+    v = nx;
+    nx = load(first + (k + 2) * stride);
+    return mlp_features(v.x, v.y, v.z);
+  }
+  __device__ void finish(int sl, long long k, float o) {
+    const int64_t i = first + k * stride;
+    if (i < n) out[i] = o + mlp_prior(sl == 0 ? v0.x : v1.x);
+  }
+};
+
+__global__ void __launch_bounds__(kTcRows) k_mlp_eval_tc(MlpDev dev, const float* __restrict__ in,
+                                                         float* __restrict__ out, int64_t n,
+                                                         unsigned long long* status,
+                                                         int withhold) {
+  extern __shared__ unsigned char tc_raw[];
+  TcSmem& S = tc_smem(tc_raw);
+  tc_setup(S, dev, withhold != 0);
+  EvalSrc src(in, out, n);
+  if (tc_run(S, src) && threadIdx.x == 0) atomicOr(status, 4ull);
 }
 
 __global__ void k_ginv_eval(const float* __restrict__ tab, const float* __restrict__ r,
@@ -426,13 +465,14 @@ size_t mlp_train_smem_bytes() { return sizeof(TrainSmem); }
 cudaError_t launch_mlp_train_block(const MlpDev& dev, uint32_t key0, uint32_t key1,
                                    uint64_t first, int64_t n_valid, int64_t n_total,
                                    const float4* explicit_samples, const float* ginv,
-                                   float lng_lo, float lng_span, float lnh_lo,
-                                   float lnh_span, float wdt_per_H_g2, float* partial,
-                                   float* loss_part, int nblocks, cudaStream_t s) {
+                                   float* partial, float* loss_part, int nblocks,
+                                   cudaStream_t s) {
   SampleSpec sp;
   sp.key0 = key0; sp.key1 = key1; sp.first = first;
-  sp.lng_lo = lng_lo; sp.lng_span = lng_span; sp.lnh_lo = lnh_lo; sp.lnh_span = lnh_span;
-  sp.wdt_per_H_g2 = wdt_per_H_g2; sp.ginv = ginv; sp.explicit_samples = explicit_samples;
+  // gamma and omega_c dt log-uniform over the feature box
+  sp.lng_lo = kLnGamC - kLnGamS; sp.lng_span = 2.0f * kLnGamS;
+  sp.lnw_lo = kLnWC - kLnWS; sp.lnw_span = 2.0f * kLnWS;
+  sp.ginv = ginv; sp.explicit_samples = explicit_samples;
   sp.n_total = n_total; sp.n_valid = n_valid;
   const int bytes = static_cast<int>(sizeof(TrainSmem));
   cudaError_t e = cudaFuncSetAttribute(k_mlp_train_block,
@@ -455,24 +495,55 @@ cudaError_t launch_mlp_reduce_adam(const float* partial, int nblocks, const floa
   return cudaGetLastError();
 }
 
+// The tcgen05 kernels take more than 48 KB of dynamic shared memory: the
+// attribute is set before every launch (cheap; independent of the device).
+cudaError_t tc_allow_smem(const void* fn) {
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              static_cast<int>(kTcSmemBytes));
+}
+
 cudaError_t launch_mlp_eval(const MlpDev& dev, const float* in, float* out, int64_t n,
-                            cudaStream_t s) {
-  const int64_t tiles = (n + 15) / 16;
-  const int64_t want = (tiles + 7) / 8;
-  const int grid = static_cast<int>(want < 4096 ? (want > 0 ? want : 1) : 4096);
-  k_mlp_eval<<<grid, 256, 0, s>>>(dev, in, out, n);
+                            unsigned long long* status, int withhold, cudaStream_t s) {
+  cudaError_t e = tc_allow_smem(reinterpret_cast<const void*>(k_mlp_eval_tc));
+  if (e != cudaSuccess) return e;
+  const int64_t tiles = (n + kTcRows - 1) / kTcRows;
+  const int64_t want = (tiles + kTcSlots - 1) / kTcSlots;
+  const int grid = static_cast<int>(want < 1024 ? (want > 0 ? want : 1) : 1024);
+  k_mlp_eval_tc<<<grid, kTcRows, kTcSmemBytes, s>>>(dev, in, out, n, status, withhold);
   return cudaGetLastError();
 }
 
 cudaError_t launch_mlp_finish(const MlpFinishArgs& a, int grid, cudaStream_t s) {
-  k_mlp_finish<<<grid, 256, 0, s>>>(a);
+  cudaError_t e = tc_allow_smem(reinterpret_cast<const void*>(k_mlp_finish_tc));
+  if (e != cudaSuccess) return e;
+  k_mlp_finish_tc<<<grid, kTcRows, kTcSmemBytes, s>>>(a);
   return cudaGetLastError();
 }
 
+// Resident CTAs per SM, from the kernel's registers and shared memory and
+// the SM's limits (4 on GB300: shared memory); every resident CTA holds
+// kTcCols of the SM's 512 TMEM columns, so the allocations never wait on
+// one another.
 int mlp_finish_blocks_per_sm() {
-  int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_mlp_finish, 256, 0) != cudaSuccess)
+  int dev = 0, smem_sm = 0, smem_rsv = 0, regs_sm = 0, thr_sm = 0;
+  cudaFuncAttributes fa;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaFuncGetAttributes(&fa, k_mlp_finish_tc) != cudaSuccess ||
+      cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) !=
+          cudaSuccess ||
+      cudaDeviceGetAttribute(&smem_rsv, cudaDevAttrReservedSharedMemoryPerBlock, dev) !=
+          cudaSuccess ||
+      cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) !=
+          cudaSuccess ||
+      cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev) != cudaSuccess)
     return 1;
+  const int per_cta_smem = static_cast<int>(kTcSmemBytes + fa.sharedSizeBytes) + smem_rsv;
+  int nb = smem_sm / per_cta_smem;
+  // registers are allocated per warp in units of 256
+  const int regs_warp = ((fa.numRegs > 0 ? fa.numRegs : 1) * 32 + 255) / 256 * 256;
+  nb = min(nb, regs_sm / (regs_warp * (kTcRows / 32)));
+  nb = min(nb, thr_sm / kTcRows);
+  nb = min(nb, 512 / static_cast<int>(kTcCols));
   return nb > 0 ? nb : 1;
 }
 

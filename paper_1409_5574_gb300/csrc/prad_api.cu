@@ -1295,15 +1295,6 @@ int ensure_mlp_partials(prad_ctx* c, int nblocks) {
   return PRAD_OK;
 }
 
-// training-sample ranges (log-uniform gamma and H_eff) and omega_c dt / (H gamma^2)
-void mlp_ranges(const prad_ctx* c, float* lng_lo, float* lng_span, float* lnh_lo,
-                float* lnh_span, float* wdt_per) {
-  *lng_lo = static_cast<float>(std::log(10.0));
-  *lng_span = static_cast<float>(std::log(1e4) - std::log(10.0));
-  *lnh_lo = static_cast<float>(std::log(1e2));
-  *lnh_span = static_cast<float>(std::log(1e6) - std::log(1e2));
-  *wdt_per = static_cast<float>(1.5 * kQe / kMe * c->cfg.dt);
-}
 }  // namespace
 
 int prad_mlp_train(prad_ctx* c, int64_t steps, int32_t batch, float lr, uint64_t seed,
@@ -1313,14 +1304,12 @@ int prad_mlp_train(prad_ctx* c, int64_t steps, int32_t batch, float lr, uint64_t
   const int nblocks = (batch + 127) / 128;
   int rc = ensure_mlp_partials(c, nblocks);
   if (rc != PRAD_OK) return rc;
-  float lng_lo, lng_span, lnh_lo, lnh_span, wdt;
-  mlp_ranges(c, &lng_lo, &lng_span, &lnh_lo, &lnh_span, &wdt);
   const MlpDev dev = mlp_dev(c);
   for (int64_t s = 0; s < steps; ++s) {
     CK(c, launch_mlp_train_block(dev, static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32),
                                  static_cast<uint64_t>(s) * batch, batch, batch, nullptr,
-                                 c->d_ginv, lng_lo, lng_span, lnh_lo, lnh_span, wdt,
-                                 c->d_mlp_partial, c->d_mlp_loss_part, nblocks, c->stream));
+                                 c->d_ginv, c->d_mlp_partial, c->d_mlp_loss_part, nblocks,
+                                 c->stream));
     c->mlp_t += 1;
     const double lr_s = lr * 0.5 * (1.0 + std::cos(kPi * static_cast<double>(s) / steps));
     const float b1t = static_cast<float>(std::pow(0.9, static_cast<double>(c->mlp_t)));
@@ -1345,11 +1334,9 @@ int prad_mlp_grad(prad_ctx* c, const float* samples, int64_t n, float* grad, dou
   const int nblocks = static_cast<int>((n + 127) / 128);
   int rc = ensure_mlp_partials(c, nblocks);
   if (rc != PRAD_OK) return rc;
-  float lng_lo, lng_span, lnh_lo, lnh_span, wdt;
-  mlp_ranges(c, &lng_lo, &lng_span, &lnh_lo, &lnh_span, &wdt);
   CK(c, launch_mlp_train_block(mlp_dev(c), 0, 0, 0, n, n, reinterpret_cast<const float4*>(samples),
-                               c->d_ginv, lng_lo, lng_span, lnh_lo, lnh_span, wdt,
-                               c->d_mlp_partial, c->d_mlp_loss_part, nblocks, c->stream));
+                               c->d_ginv, c->d_mlp_partial, c->d_mlp_loss_part, nblocks,
+                               c->stream));
   CK(c, launch_mlp_reduce_adam(c->d_mlp_partial, nblocks, c->d_mlp_loss_part, c->d_mlp_grad,
                                c->d_mlp, c->d_mlp_m, c->d_mlp_v, c->d_mlp_w2, 0.0f, 0.0f, 0.0f,
                                0, c->d_mlp_loss, 1.0f / static_cast<float>(n), c->stream));
@@ -1365,9 +1352,45 @@ int prad_mlp_grad(prad_ctx* c, const float* samples, int64_t n, float* grad, dou
 int prad_mlp_eval(prad_ctx* c, const float* in, float* lnx, int64_t n) {
   if (!c || n < 0 || (n > 0 && (!in || !lnx))) return fail(c, PRAD_ERR_ARG, "mlp_eval: bad argument");
   if (n == 0) return PRAD_OK;
-  CK(c, launch_mlp_eval(mlp_dev(c), in, lnx, n, c->stream));
+  CK(c, launch_mlp_eval(mlp_dev(c), in, lnx, n, c->d_cnt + kStatus, 0, c->stream));
+  unsigned long long st = 0;
+  CK(c, cudaMemcpyAsync(&st, c->d_cnt + kStatus, sizeof(st), cudaMemcpyDeviceToHost, c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
+  if (st & 4ull) return fail(c, PRAD_ERR_TIMEOUT, "mlp_eval: a tensor-core wait timed out");
   return PRAD_OK;
+}
+
+int prad_mlp_wait_selftest(prad_ctx* c) {
+  if (!c) return fail(c, PRAD_ERR_ARG, "mlp_wait_selftest: null context");
+  // one tile of inputs and a status word of its own (the context's status
+  // is not touched)
+  constexpr int64_t n = 128;
+  float* buf = nullptr;
+  unsigned long long* st_d = nullptr;
+  CK(c, cudaMalloc(&buf, sizeof(float) * 4 * n));
+  cudaError_t e = cudaMalloc(&st_d, sizeof(unsigned long long));
+  if (e != cudaSuccess) {
+    cudaFree(buf);
+    return fail(c, PRAD_ERR_CUDA, cudaGetErrorString(e));
+  }
+  std::vector<float> in(3 * n);
+  for (int64_t i = 0; i < n; ++i) {
+    in[3 * i] = (static_cast<float>(i) + 0.5f) / n;
+    in[3 * i + 1] = 100.0f;
+    in[3 * i + 2] = 1.0f;
+  }
+  unsigned long long st = 0;
+  e = cudaMemcpyAsync(buf, in.data(), sizeof(float) * 3 * n, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(st_d, 0, sizeof(unsigned long long), c->stream);
+  if (e == cudaSuccess) e = launch_mlp_eval(mlp_dev(c), buf, buf + 3 * n, n, st_d, 1, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&st, st_d, sizeof(st), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  cudaFree(buf);
+  cudaFree(st_d);
+  if (e != cudaSuccess) return fail(c, PRAD_ERR_CUDA, cudaGetErrorString(e));
+  if (st & 4ull) return fail(c, PRAD_ERR_TIMEOUT, "mlp_wait_selftest: the bounded waits ran out");
+  return fail(c, PRAD_ERR_STATE, "mlp_wait_selftest: the withheld waits did not report");
 }
 
 int prad_ginv_eval(prad_ctx* c, const float* r, float* lnx, int64_t n) {

@@ -166,16 +166,17 @@ size_t mlp_train_smem_bytes();
 cudaError_t launch_mlp_train_block(const MlpDev& dev, uint32_t key0, uint32_t key1,
                                    uint64_t first, int64_t n_valid, int64_t n_total,
                                    const float4* explicit_samples, const float* ginv,
-                                   float lng_lo, float lng_span, float lnh_lo,
-                                   float lnh_span, float wdt_per_H_g2, float* partial,
-                                   float* loss_part, int nblocks, cudaStream_t s);
+                                   float* partial, float* loss_part, int nblocks,
+                                   cudaStream_t s);
 cudaError_t launch_mlp_reduce_adam(const float* partial, int nblocks, const float* loss_part,
                                    float* grad, float* params, float* m, float* v,
                                    __nv_bfloat16* w2, float lr, float b1t, float b2t,
                                    int apply, float* loss_out, float loss_scale,
                                    cudaStream_t s);
+// withhold != 0: the self-test of the bounded tensor-core waits (no MMA
+// completion is signalled; every wait runs out and status bit 2 is set)
 cudaError_t launch_mlp_eval(const MlpDev& dev, const float* in, float* out, int64_t n,
-                            cudaStream_t s);
+                            unsigned long long* status, int withhold, cudaStream_t s);
 // Energies of the learned sampler's records appended since the last call:
 // records [counters[kMlpDone], min(cursor, cap)) get x from the network (table
 // fallback), eps = x eps_c, and their emitted-energy ledger entries.

@@ -106,6 +106,7 @@ SIGNATURES = {
                               ctypes.POINTER(ctypes.c_float)]),
     "prad_mlp_grad": (_i32, [_vp, _vp, _i64, _vp, ctypes.POINTER(_dbl)]),
     "prad_mlp_eval": (_i32, [_vp, _vp, _vp, _i64]),
+    "prad_mlp_wait_selftest": (_i32, [_vp]),
     "prad_ginv_eval": (_i32, [_vp, _vp, _vp, _i64]),
     "prad_ledger_totals_noalloc": (_i32, [_vp, _vp, _i64, _vp, _vp]),
     "prad_ledger_totals_noalloc_error": (ctypes.c_char_p, []),
@@ -255,6 +256,11 @@ def prad_mlp_grad(h, samples_ptr, n: int):
 
 def prad_mlp_eval(h, in_ptr, out_ptr, n: int) -> None:
     _check(load_library().prad_mlp_eval(h, in_ptr, out_ptr, n), h)
+
+
+def prad_mlp_wait_selftest(h) -> int:
+    """Status code of the bounded-wait self-test (PRAD_ERR_TIMEOUT expected)."""
+    return load_library().prad_mlp_wait_selftest(h)
 
 
 def prad_ginv_eval(h, r_ptr, out_ptr, n: int) -> None:

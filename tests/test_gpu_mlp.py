@@ -1,7 +1,8 @@
 """Learned inverse-CDF sampler on the GPU, through the C ABI.
 
 * the device G^-1 table against the oracle's inverse number CDF;
-* the tensor-core tile evaluator against the FP64 numpy net (same weights);
+* the tensor-core tile evaluator against the FP64 numpy net (same weights),
+  and its bounded waits: a withheld MMA completion is reported, not hung on;
 * the training kernels' gradient against the FP64 numpy backward;
 * training on 10^8 device-generated samples reaches a spectral error
   sup_r |G(g(r)) - r| <= 1% (G from the oracle) from ~100% untrained, for
@@ -71,6 +72,24 @@ def test_tile_evaluator_matches_fp64_net():
                  g.astype(np.float64), w.astype(np.float64))
     d = np.abs(got - ref)
     assert np.median(d) < 5e-3 and d.max() < 5e-2, (np.median(d), d.max())
+    ctx.close()
+
+
+def test_tensor_core_wait_timeout_is_reported_and_context_recovers():
+    """The evaluator with every MMA completion withheld: each bounded wait
+    runs out (~2 s), the kernel frees its tensor memory and reports the
+    timeout; the same context then evaluates as before."""
+    p = M.glorot(12).astype(np.float32)
+    ctx = _ctx()
+    ctx.mlp_set_weights(p)
+    r = np.linspace(0.01, 0.99, 300).astype(np.float32)
+    g = np.full(300, 100.0, np.float32)
+    w = np.full(300, 10.0, np.float32)
+    before = ctx.mlp_eval(r, g, w).cpu().numpy()
+    assert prad.prad_mlp_wait_selftest(ctx.h) == prad.PRAD_ERR_TIMEOUT
+    after = ctx.mlp_eval(r, g, w).cpu().numpy()
+    np.testing.assert_array_equal(before, after)
+    assert ctx.energy_budget()[2]["status"] == 0
     ctx.close()
 
 

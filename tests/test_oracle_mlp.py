@@ -1,7 +1,8 @@
 """Pins of the FP64 numpy MLP used to check the GPU training kernels:
 central finite differences of the loss (without the BF16 roundings, where
-the loss is smooth) against the analytic backward pass, and the BF16 rounding
-helper against torch's bfloat16 conversion (a library)."""
+the loss is smooth) against the analytic backward pass, a hand-computed
+forward pass, and the BF16 rounding helper against torch's bfloat16
+conversion (a library)."""
 import numpy as np
 import pytest
 
@@ -64,3 +65,28 @@ def test_features_definition():
                    np.array([np.exp(8.2), 1e-30]))
     assert f[0] == pytest.approx([0.0, 0.0, 0.0], abs=1e-4)
     assert f[1] == pytest.approx([-1.0, 1.0, -1.0], abs=1e-12)
+
+
+def test_forward_closed_form():
+    """W1 = 0, b1 = 1.5 on units 0..15 and -2 elsewhere: h1 = relu(b1);
+    W2 shifts (output unit j reads h1[j-1]), b2 = -0.25: h2[j] = 1.25 for
+    j = 1..16, else relu(-0.25) = 0; W3 = 1, b3 = 0.125: o = 16 * 1.25 +
+    0.125 = 20.125 (every value exact in BF16 and f16).  A transposed W2
+    gives 15 live units, a smooth activation a different value."""
+    p = np.zeros(M.NUM_PARAMS)
+    b1 = np.where(np.arange(M.H) < 16, 1.5, -2.0)
+    p[M.OFF_B1:M.OFF_W2] = b1
+    W2 = np.zeros((M.H, M.H))
+    W2[np.arange(1, M.H), np.arange(0, M.H - 1)] = 1.0
+    p[M.OFF_W2:M.OFF_B2] = W2.ravel()
+    p[M.OFF_B2:M.OFF_W3] = -0.25
+    p[M.OFF_W3:M.OFF_B3] = 1.0
+    p[M.OFF_B3] = 0.125
+    f = M.features(np.array([0.3, 0.9]), np.array([50.0, 2e3]), np.array([1.0, 1e6]))
+    for rounding in (True, False):
+        o, _ = M.forward(p, f, rounding)
+        np.testing.assert_array_equal(o, [20.125, 20.125])
+    # the prior carries the output: ln x = o + prior(r)
+    r = np.array([0.3])
+    assert M.ln_x(p, r, np.array([50.0]), np.array([1.0]))[0] == pytest.approx(
+        20.125 + np.log(-np.log1p(-0.3)) + 2 * 0.7 * np.log(0.3), rel=1e-15)

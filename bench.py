@@ -39,9 +39,9 @@ KERNEL_SOURCES = ["paper_1409_5574_gb300/csrc/push_emit.cu",
                   "paper_1409_5574_gb300/csrc/prad_internal.h",
                   "paper_1409_5574_gb300/csrc/mlp_device.cuh"]
 NCU_TRAFFIC = {
-    "src_sha256": "5d19c2f4670dd26644ad616dbc2cde9706266355972eb5f5d07f9941e3a72615",
+    "src_sha256": "f4becc1157c6c59c9f2c54fa17c6fbcf428a610cc9b87a45fbe08da3431b78f4",
     "fused": None,        # bytes per launch of the bench's fused launches
-    "stream": 1334827520, # bytes per launch, 2^24 particles x 1 step, a0 = 500
+    "stream": 1334210816, # bytes per launch, 2^24 particles x 1 step, a0 = 500
 }
 
 

@@ -371,6 +371,7 @@ void fill_common(const prad_ctx* c, StepParams<R>& p, const prad_fields& f) {
   p.ensemble = c->cfg.ensemble;
   p.key0 = static_cast<uint32_t>(c->cfg.seed & 0xffffffffull);
   p.key1 = static_cast<uint32_t>(c->cfg.seed >> 32);
+  philox_round_keys(c->cfg.seed, p.rkey);
   p.t_scale = static_cast<R>(kN1 / std::cbrt(kA));
   p.x_scale = static_cast<R>(kN2 / (kXmax - kA));
   p.a = static_cast<R>(kA);
@@ -1041,6 +1042,7 @@ int issue_batch(prad_ctx* c, int n_ens, int64_t items, int32_t nsteps, int chunk
   bp.n_ens = n_ens;
   bp.chunk = chunk;
   bp.pad = 0;
+  philox_round_keys(c->cfg.seed, bp.rkey);
   const int cap = batch_max_blocks_per_sm(block, c->cfg.sampler, ctrl_of(c));
   const int64_t g = static_cast<int64_t>(c->num_sms) * (bps < cap ? bps : cap);
   const int grid = static_cast<int>(g < items ? g : (items > 0 ? items : 1));

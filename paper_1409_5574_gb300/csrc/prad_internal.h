@@ -104,6 +104,10 @@ struct StepParams {
   const int4* work;           // (tile, first, end, 0) per work item
   const unsigned int* work_count;
   int32_t ntx;                // tiles along x
+  // Philox4x32-10 round keys of (key0, key1) (philox_round_keys), read
+  // from the kernel's parameter space by the kernels that take StepParams
+  // by value
+  uint32_t rkey[20];
 };
 
 // Tile geometry of the sorted Yee gather: 32 x 32-cell tiles, staged with a
@@ -139,7 +143,19 @@ struct BatchParams {
   int32_t chunk;               // particles per work item
   int32_t nsub;                // steps of this launch
   int32_t pad;
+  uint32_t rkey[20];           // Philox round keys of the context's seed
 };
+
+// Philox4x32-10 round keys of a 64-bit seed: (key0 + r 0x9E3779B9,
+// key1 + r 0xBB67AE85) at rk[2r], rk[2r + 1], r = 0..9.
+inline void philox_round_keys(uint64_t seed, uint32_t* rk) {
+  const uint32_t k0 = static_cast<uint32_t>(seed & 0xffffffffull);
+  const uint32_t k1 = static_cast<uint32_t>(seed >> 32);
+  for (uint32_t r = 0; r < 10; ++r) {
+    rk[2 * r] = k0 + r * 0x9E3779B9u;
+    rk[2 * r + 1] = k1 + r * 0xBB67AE85u;
+  }
+}
 
 // Launchers (defined in the kernel translation units).
 cudaError_t launch_push_emit_batch(const BatchParams& bp, int sampler, bool ctrl, int grid,

@@ -35,6 +35,21 @@ __device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
   return c;
 }
 
+// The same generator with the ten round keys given (rk[2r], rk[2r + 1]):
+// with rk in the kernel's parameter space each round's XOR with the key
+// reads it from there instead of carrying the key schedule in registers.
+__device__ __forceinline__ uint4 philox10_rk(uint4 c, const uint32_t* rk) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ rk[2 * r], lo1, hi0 ^ c.w ^ rk[2 * r + 1], lo0);
+  }
+  return c;
+}
+
 // ---- compensated accumulators for the per-particle ledgers -----------------
 // The FP32 path sums a launch's ledger increments in a float-float pair
 // (Knuth TwoSum: the rounding error of every add is kept in `lo`), about
@@ -554,8 +569,10 @@ __device__ __forceinline__ void load_state(const StepParams<R>& P, int64_t i, bo
 // ONE: the launch is known to advance exactly one step (P.nsub == 1).
 // CTRL: super-photon control or diagnostics are enabled (the plain method
 // compiles without their per-step work).
+// rk: the Philox round keys, in the kernel's parameter space.
 template <typename R, int FIELD, int SAMP, bool ONE = false, bool CTRL = false, class G>
-__device__ __forceinline__ void advance_particle(const StepParams<R>& P, const G& gat,
+__device__ __forceinline__ void advance_particle(const StepParams<R>& P, const uint32_t (&rk)[20],
+                                                 const G& gat,
                                                  int64_t i, const PState<R>& st,
                                                  PhotonStage& stage, int& fill,
                                                  const PhotonOut& pout, Counts& cnt) {
@@ -675,7 +692,8 @@ __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const G
       xn -= P.Lx * flr((xn - P.x0) * (R(1) / P.Lx));
       yn -= P.Ly * flr((yn - P.y0) * (R(1) / P.Ly));
     }
-    const uint4 rnd = philox10(make_uint4(pid, step, 0u, P.ensemble), P.key0, P.key1);
+    const uint4 ctr = make_uint4(pid, step, 0u, P.ensemble);
+    const uint4 rnd = philox10_rk(ctr, rk);
     const R Rr = unit_uniform<R>(rnd.z);
     if constexpr (SAMP == PRAD_SAMPLER_TABLE) {
       // 8. Monte Carlo emission: proposal x = P^-1(R'), dN of Eq. (13);
@@ -712,9 +730,8 @@ __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const G
         const bool part = live && unit_uniform<R>(rnd.w) < P.sel_q;
         trial(rnd.x, rnd.y, Rr, P.inv_ntry, P.inv_sel_q, part);
         for (int j = 1; j < P.ntry; ++j) {
-          const uint4 rb = philox10(make_uint4(pid, step, 0x10000u + static_cast<uint32_t>(j),
-                                               P.ensemble),
-                                    P.key0, P.key1);
+          const uint4 cj = make_uint4(pid, step, 0x10000u + static_cast<uint32_t>(j), P.ensemble);
+          const uint4 rb = philox10_rk(cj, rk);
           trial(rb.x, rb.y, unit_uniform<R>(rb.z), P.inv_ntry, P.inv_sel_q, part);
         }
       }
@@ -874,14 +891,14 @@ __global__ void __launch_bounds__(256, (PF ? PRAD_PF_MINB : MinBlocks<R, FIELD, 
       const PState<R> cur = nxt;
       const int64_t j = i + stride;
       load_state<R, true>(P, j, j < P.n, nxt);
-      advance_particle<R, FIELD, SAMP, true, CTRL>(P, gat, i, cur, stage, fill, pout, cnt);
+      advance_particle<R, FIELD, SAMP, true, CTRL>(P, P.rkey, gat, i, cur, stage, fill, pout, cnt);
     }
   } else {
     for (int64_t base = first; base < P.n; base += stride) {
       const int64_t i = base + threadIdx.x;
       PState<R> cur;
       load_state(P, i, i < P.n, cur);
-      advance_particle<R, FIELD, SAMP, false, CTRL>(P, gat, i, cur, stage, fill, pout, cnt);
+      advance_particle<R, FIELD, SAMP, false, CTRL>(P, P.rkey, gat, i, cur, stage, fill, pout, cnt);
     }
   }
   if (fill > 0) flush_stage<SAMP != PRAD_SAMPLER_TABLE>(stage, fill, pout);
@@ -954,7 +971,7 @@ __global__ void __launch_bounds__(256, PRAD_BATCH_MINB)
         const int64_t i = base + threadIdx.x;
         PState<float> st;
         load_state(Ps, i, i < last, st);
-        advance_particle<float, PRAD_FIELD_CONST, SAMP, false, CTRL>(Ps, gat, i, st, stage,
+        advance_particle<float, PRAD_FIELD_CONST, SAMP, false, CTRL>(Ps, bp.rkey, gat, i, st, stage,
                                                                      fill, pout, cnt);
       }
     } else {
@@ -963,7 +980,7 @@ __global__ void __launch_bounds__(256, PRAD_BATCH_MINB)
         const int64_t i = base + threadIdx.x;
         PState<float> st;
         load_state(Ps, i, i < last, st);
-        advance_particle<float, PRAD_FIELD_PLANE_WAVE, SAMP, false, CTRL>(Ps, gat, i, st,
+        advance_particle<float, PRAD_FIELD_PLANE_WAVE, SAMP, false, CTRL>(Ps, bp.rkey, gat, i, st,
                                                                           stage, fill, pout,
                                                                           cnt);
       }
@@ -1058,7 +1075,7 @@ __global__ void __launch_bounds__(256, 3) k_push_emit_tiled(const StepParams<R> 
     const int64_t i = base + threadIdx.x;
     PState<R> st;
     load_state(P, i, i < wk.z, st);
-    advance_particle<R, PRAD_FIELD_YEE2D, PRAD_SAMPLER_TABLE, false, CTRL>(P, gat, i, st, stage,
+    advance_particle<R, PRAD_FIELD_YEE2D, PRAD_SAMPLER_TABLE, false, CTRL>(P, P.rkey, gat, i, st, stage,
                                                                            fill, pout, cnt);
   }
   if (fill > 0) flush_stage(stage, fill, pout);

@@ -31,17 +31,17 @@ sys.path.insert(0, ROOT)
 
 METRIC = "particle-steps/s with emission (plain table vs MLP sampler) at <=1% spectral err"
 
-# DRAM bytes (read + write) per launch of the dominant kernels from ncu
-# captures of the commands in profiles/push_emit_planewave_*.md, valid for the
-# kernel sources they were taken on (sha256 of KERNEL_SOURCES); reported as
-# null once those sources change.
+# DRAM bytes (read + write) per launch of the dominant kernels from one-pass
+# ncu captures (dram__bytes_read.sum + dram__bytes_write.sum) of the bench's
+# own launches, valid for the kernel sources they were taken on (sha256 of
+# KERNEL_SOURCES); reported as null once those sources change.
 KERNEL_SOURCES = ["paper_1409_5574_gb300/csrc/push_emit.cu",
                   "paper_1409_5574_gb300/csrc/prad_internal.h",
                   "paper_1409_5574_gb300/csrc/mlp_device.cuh"]
 NCU_TRAFFIC = {
-    "src_sha256": "f4becc1157c6c59c9f2c54fa17c6fbcf428a610cc9b87a45fbe08da3431b78f4",
-    "fused": None,        # bytes per launch of the bench's fused launches
-    "stream": 1334210816, # bytes per launch, 2^24 particles x 1 step, a0 = 500
+    "src_sha256": "d8ddcee8086f757c101896a7da34aa0617a8b784b7b5b8e37d820150cfa0263f",
+    "fused": 253649681,   # mean bytes per launch over the 30 fused launches of one bench step
+    "stream": 1334093056, # bytes per launch, 2^24 particles x 1 step, a0 = 500
 }
 
 
@@ -441,9 +441,12 @@ def run_prad(args):
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
     # The fused kernel keeps the particle in registers for nsub steps, so it
     # is bound by issue of FP32/INT32 arithmetic: peak = SMs x 128 lanes x
-    # clock.  Achieved = algorithmic operations of one particle-step (hand
-    # count of the method's arithmetic: 252) x particle-steps
-    # of one launch / launch time.
+    # clock.  Achieved = algorithmic operations of one particle-step x
+    # particle-steps of one launch / launch time, with the hand count of the
+    # method's arithmetic: plane-wave gather 9, Boris 42, step averages 12,
+    # H_eff 21, clamp / omega_c / chi 9, LL ledger and kick 20, position 8,
+    # Philox4x32-10 80, proposal sampling 30, dN and decision 10, emission
+    # bookkeeping 8, counters 3 (252).
     alg_ops = 252.0
     alu_peak = nsm * 128 * sm_mhz * 1e6 / 1e12
     achieved = alg_ops * n * nsub / per_launch_s / 1e12

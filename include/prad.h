@@ -324,7 +324,7 @@ int prad_get_ledger(prad_ctx* ctx, double* emit, double* ll, int64_t offset,
 int prad_reset(prad_ctx* ctx);
 
 /* ---- learned sampler (PRAD_SAMPLER_MLP, PRAD_SAMPLER_MLP_FALLBACK) --------
- * A 3 -> 64 -> 64 -> 1 MLP (ReLU, activations rounded to IEEE half, BF16
+ * A 3 -> 64 -> 64 -> 1 MLP (SiLU, activations rounded to IEEE half, BF16
  * weights, FP32 accumulate) plus a fixed prior ln(-ln(1 - r)) + 2 (1 - r) ln r
  * maps
  * (r, gamma, omega_c dt) to ln x with G(x) = r, G the photon-number CDF of
@@ -347,14 +347,13 @@ int prad_mlp_get_weights(prad_ctx* ctx, float* params, int64_t n);
 
 /* Train the context's network on the GPU: `steps` Adam steps (lr with a
  * cosine decay to 0) on minibatches of `batch` samples generated on the
- * device (r uniform in the trained range; gamma and omega_c dt log-uniform
- * over the feature box, [10, 1e4] and [e^-3.4, e^19.8]; target ln G^-1(r)
- * from the device table), loss = mean over samples of
+ * device (r uniform in the trained range, gamma log-uniform in [10, 1e4],
+ * H_eff log-uniform in [1e2, 1e6] T, omega_c dt from the context's dt;
+ * target ln G^-1(r) from the device table), loss = mean over samples of
  * w (o - (ln x - prior(r)))^2 with o the network output, the fixed prior
- * ln(-ln(1 - r)) + 2 (1 - r) ln r and the energy weight w = (1 + x)/1.308,
- * plus (1e-2 / 2) sum_j (W1[j][1]^2 + W1[j][2]^2) (the classical spectrum
- * does not depend on gamma or omega_c dt).  *final_loss (host, may be NULL)
- * receives the last minibatch loss.  Synchronises. */
+ * ln(-ln(1 - r)) + 2 (1 - r) ln r and the energy weight w = (1 + x)/1.308.
+ * *final_loss (host, may be NULL) receives the last minibatch loss.
+ * Synchronises. */
 int prad_mlp_train(prad_ctx* ctx, int64_t steps, int32_t batch, float lr, uint64_t seed,
                    float* final_loss);
 

@@ -7,22 +7,19 @@ arXiv:1409.5574).  Model definition (as documented with the C ABI):
   features  f0 = logit(r) / 8
             f1 = clip((ln gamma - 5.7565) / 3.4539, -1, 1)
             f2 = clip((ln(omega_c dt) - 8.2) / 11.6, -1, 1)
-  layer 1   z1 = W1 f + b1,  h1 = f16(relu(z1))         (W1 in BF16)
-  layer 2   z2 = W2 h1 + b2, h2 = f16(relu(z2))         (W2 in BF16)
+  layer 1   z1 = W1 f + b1,  h1 = f16(silu(z1))         (W1 in BF16)
+  layer 2   z2 = W2 h1 + b2, h2 = f16(silu(z2))         (W2 in BF16)
   layer 3   o  = W3 h2 + b3                             (W3 in BF16)
   output    ln x = prior(r) + o,  prior(r) = ln(-ln(1 - r)) + 2 (1 - r) ln r
   loss      mean over samples of w (o - (ln x_target - prior(r)))^2,
-            w = (1 + x_target) / 1.308 (energy weighting, mean 1),
-            + (INPUT_DECAY / 2) sum_j (W1[j][1]^2 + W1[j][2]^2): the classical
-            spectrum does not depend on gamma or omega_c dt, and the decay of
-            their input weights keeps the net flat across the feature box
+            w = (1 + x_target) / 1.308 (energy weighting, mean 1)
 
 Parameter vector: W1[64][3], b1[64], W2[64][64], b2[64], W3[64], b3 (4481).
 Everything here is FP64 except the roundings the definition names (weights
 to BF16, activations to IEEE half; W2 and W3 enter the f16 products as the
 half-precision images of their BF16 values, identical for |w| >= 2^-17);
-gradients treat the roundings as identity (straight-through) and take
-relu'(0) = 0.  Only tests import this module.
+gradients treat the roundings as identity (straight-through).  Only tests
+import this module.
 """
 from __future__ import annotations
 
@@ -35,7 +32,6 @@ OFF_B2 = OFF_W2 + H * H
 OFF_W3 = OFF_B2 + H
 OFF_B3 = OFF_W3 + H
 NUM_PARAMS = OFF_B3 + 1
-INPUT_DECAY = 1e-2
 
 
 def bf16(x):
@@ -66,13 +62,13 @@ def features(r, gamma, wdt):
     return np.stack([f0, f1, f2], 1)
 
 
-def relu(z):
-    return np.maximum(z, 0.0)
+def silu(z):
+    return z / (1.0 + np.exp(-z))
 
 
-def relu_grad(z):
-    """Derivative of relu, taken as 0 at z = 0."""
-    return (np.asarray(z) > 0.0).astype(np.float64)
+def silu_grad(z):
+    s = 1.0 / (1.0 + np.exp(-z))
+    return s + z * s * (1.0 - s)
 
 
 def forward(p, f, rounding=True):
@@ -82,9 +78,9 @@ def forward(p, f, rounding=True):
     rh = f16 if rounding else ident
     W1r, W2r, W3r = rw(W1), rh(rw(W2)), rh(rw(W3))
     z1 = f @ W1r.T + b1
-    h1 = rh(relu(z1))
+    h1 = rh(silu(z1))
     z2 = h1 @ W2r.T + b2
-    h2 = rh(relu(z2))
+    h2 = rh(silu(z2))
     o = h2 @ W3r + b3
     return o, (f, z1, h1, z2, h2, W1r, W2r, W3r)
 
@@ -106,19 +102,16 @@ def loss_and_grad(p, r, gamma, wdt, lnx_target, rounding=True):
     n = o.size
     diff = o - t
     wgt = (1.0 + np.exp(np.asarray(lnx_target, dtype=np.float64))) / 1.308
-    W1m = np.asarray(p, dtype=np.float64)[OFF_W1:OFF_B1].reshape(H, 3)
-    loss = np.mean(wgt * diff * diff) + 0.5 * INPUT_DECAY * np.sum(W1m[:, 1:] ** 2)
+    loss = np.mean(wgt * diff * diff)
     do = 2.0 * wgt * diff / n
     g = np.zeros(NUM_PARAMS)
     g[OFF_W3:OFF_B3] = h2.T @ do
     g[OFF_B3] = do.sum()
-    d2 = np.outer(do, W3r) * relu_grad(z2)
+    d2 = np.outer(do, W3r) * silu_grad(z2)
     g[OFF_W2:OFF_B2] = (d2.T @ h1).ravel()
     g[OFF_B2:OFF_W3] = d2.sum(0)
-    d1 = (d2 @ W2r) * relu_grad(z1)
-    gw1 = d1.T @ f
-    gw1[:, 1:] += INPUT_DECAY * W1m[:, 1:]
-    g[OFF_W1:OFF_B1] = gw1.ravel()
+    d1 = (d2 @ W2r) * silu_grad(z1)
+    g[OFF_W1:OFF_B1] = (d1.T @ f).ravel()
     g[OFF_B1:OFF_W2] = d1.sum(0)
     return loss, g
 

@@ -50,13 +50,14 @@ struct TrainSmem {
   __nv_bfloat16 d2t[kHid * kLdT];     // delta2 transposed [j][s]
 };
 
-// Training samples: r from a Philox uniform (tag 3), gamma and omega_c dt
-// log-uniform over the feature box (f1 and f2 uniform in [-1, 1]); target
-// ln G^-1(r) from the device table.
+// Training samples: r from a Philox uniform (tag 3), gamma log-uniform in
+// [g_lo, g_hi], H log-uniform in [h_lo, h_hi] T, omega_c dt = 1.5 e H / m
+// gamma^2 dt; target ln G^-1(r) from the device table.
 struct SampleSpec {
   uint32_t key0, key1;
   uint64_t first;           // global index of the block's first sample
-  float lng_lo, lng_span, lnw_lo, lnw_span;
+  float lng_lo, lng_span, lnh_lo, lnh_span;
+  float wdt_per_H_g2;       // 1.5 (e/m) dt  [1 / (T)]
   const float* ginv;        // G^-1 table
   const float4* explicit_samples;  // (r, gamma, wdt, ln x target) or null
   int64_t n_total;          // samples in the whole batch (loss mean)
@@ -78,9 +79,10 @@ __device__ void make_sample(const SampleSpec& sp, int64_t idx, float* f, float* 
     const float u = fmaf(static_cast<float>(w.x), 0x1p-32f, 0x1p-33f);
     r = fminf(fmaxf(u, kRMin), kRMax);
     const float ug = fmaf(static_cast<float>(w.y), 0x1p-32f, 0x1p-33f);
-    const float uw = fmaf(static_cast<float>(w.z), 0x1p-32f, 0x1p-33f);
+    const float uh = fmaf(static_cast<float>(w.z), 0x1p-32f, 0x1p-33f);
     gam = __expf(sp.lng_lo + sp.lng_span * ug);
-    wdt = __expf(sp.lnw_lo + sp.lnw_span * uw);
+    const float H = __expf(sp.lnh_lo + sp.lnh_span * uh);
+    wdt = sp.wdt_per_H_g2 * H * gam * gam;
     lnx = ginv_ln(sp.ginv, r);
   }
   const float3 ff = mlp_features(r, gam, wdt);
@@ -117,13 +119,13 @@ __global__ void __launch_bounds__(kTThreads)
     }
   }
   __syncthreads();
-  // layer 1 (FP32, BF16 weights): z1 and bf16(relu(z1)) transposed
+  // layer 1 (FP32, BF16 weights): z1 and bf16(silu(z1)) transposed
   for (int e = threadIdx.x; e < kTB * kHid; e += blockDim.x) {
     const int s = e / kHid, j = e - s * kHid;
     const float4 w = S.net.w1b1[j];
     const float z = fmaf(w.x, S.x[s][0], fmaf(w.y, S.x[s][1], fmaf(w.z, S.x[s][2], w.w)));
     S.z1[s][j] = z;
-    S.h1t[j * kLdT + s] = __float2bfloat16(relu(z));
+    S.h1t[j * kLdT + s] = __float2bfloat16(silu(z));
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -131,39 +133,40 @@ __global__ void __launch_bounds__(kTThreads)
   // layer 2 forward, warp w: samples 16w .. 16w + 15
   {
     const int s0 = 16 * warp;
-    // h1 = f16(relu(z1)), as in the evaluator
+    // h1 = f16(silu(z1)) in packed f16 arithmetic, as in the evaluator
     uint32_t a[4][4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int j = 16 * q + 2 * t;
-      a[q][0] = relu_f16x2(S.z1[s0 + g][j], S.z1[s0 + g][j + 1]);
-      a[q][1] = relu_f16x2(S.z1[s0 + g + 8][j], S.z1[s0 + g + 8][j + 1]);
-      a[q][2] = relu_f16x2(S.z1[s0 + g][j + 8], S.z1[s0 + g][j + 9]);
-      a[q][3] = relu_f16x2(S.z1[s0 + g + 8][j + 8], S.z1[s0 + g + 8][j + 9]);
+      a[q][0] = silu_f16x2(S.z1[s0 + g][j], S.z1[s0 + g][j + 1]);
+      a[q][1] = silu_f16x2(S.z1[s0 + g + 8][j], S.z1[s0 + g + 8][j + 1]);
+      a[q][2] = silu_f16x2(S.z1[s0 + g][j + 8], S.z1[s0 + g][j + 9]);
+      a[q][3] = silu_f16x2(S.z1[s0 + g + 8][j + 8], S.z1[s0 + g + 8][j + 9]);
     }
+    // the network image holds W2 / 2 and b2 / 2 (exact): z2 = 2 c
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt) {
       const int j0 = 8 * nt + 2 * t;
-      float c[4] = {S.net.b2[j0], S.net.b2[j0 + 1], S.net.b2[j0], S.net.b2[j0 + 1]};
+      float c[4] = {S.net.b2h[j0], S.net.b2h[j0 + 1], S.net.b2h[j0], S.net.b2h[j0 + 1]};
       const __half* wrow = S.net.w2h + (8 * nt + g) * kW2Ld + 2 * t;
 #pragma unroll
       for (int q = 0; q < 4; ++q)
         mma_f16_16816(c, a[q][0], a[q][1], a[q][2], a[q][3],
                       *reinterpret_cast<const uint32_t*>(wrow + 16 * q),
                       *reinterpret_cast<const uint32_t*>(wrow + 16 * q + 8));
-      S.z2[s0 + g][j0] = c[0];
-      S.z2[s0 + g][j0 + 1] = c[1];
-      S.z2[s0 + g + 8][j0] = c[2];
-      S.z2[s0 + g + 8][j0 + 1] = c[3];
+      S.z2[s0 + g][j0] = 2.0f * c[0];
+      S.z2[s0 + g][j0 + 1] = 2.0f * c[1];
+      S.z2[s0 + g + 8][j0] = 2.0f * c[2];
+      S.z2[s0 + g + 8][j0 + 1] = 2.0f * c[3];
     }
   }
   __syncthreads();
-  // output (h2 = f16(relu(z2)) as in the evaluator), loss and dL/do per sample
+  // output (h2 = f16(silu(z2)) as in the evaluator), loss and dL/do per sample
   if (threadIdx.x < kTB) {
     const int s = threadIdx.x;
     float o = S.net.b3;
     for (int j = 0; j < kHid; j += 2) {
-      const uint32_t hh = relu_f16x2(S.z2[s][j], S.z2[s][j + 1]);
+      const uint32_t hh = silu_f16x2(S.z2[s][j], S.z2[s][j + 1]);
       const float2 h2 = __half22float2(*reinterpret_cast<const __half2*>(&hh));
       o = fmaf(S.net.w3[j], h2.x, o);
       o = fmaf(S.net.w3[j + 1], h2.y, o);
@@ -175,11 +178,11 @@ __global__ void __launch_bounds__(kTThreads)
     S.dout[s] = valid ? 2.0f * wgt * diff / static_cast<float>(sp.n_total) : 0.0f;
   }
   __syncthreads();
-  // delta2 = dout W3 relu'(z2): BF16 copies for the two tensor-core products
+  // delta2 = dout W3 silu'(z2): BF16 copies for the two tensor-core products
   for (int e = threadIdx.x; e < kTB * kHid; e += blockDim.x) {
     const int s = e / kHid, j = e - s * kHid;
     const __nv_bfloat16 d =
-        __float2bfloat16(S.dout[s] * S.net.w3[j] * relu_grad(S.z2[s][j]));
+        __float2bfloat16(S.dout[s] * S.net.w3[j] * silu_grad(S.z2[s][j]));
     S.d2[s * kW2Ld + j] = d;
     S.d2t[j * kLdT + s] = d;
   }
@@ -190,8 +193,8 @@ __global__ void __launch_bounds__(kTThreads)
     const int j = threadIdx.x;
     float dw3 = 0.0f, db2 = 0.0f;
     for (int s = 0; s < kTB; ++s) {
-      dw3 = fmaf(S.dout[s], relu(S.z2[s][j]), dw3);
-      db2 = fmaf(S.dout[s] * S.net.w3[j], relu_grad(S.z2[s][j]), db2);
+      dw3 = fmaf(S.dout[s], silu(S.z2[s][j]), dw3);
+      db2 = fmaf(S.dout[s] * S.net.w3[j], silu_grad(S.z2[s][j]), db2);
     }
     gp[kOffW3 + j] = dw3;
     gp[kOffB2 + j] = db2;
@@ -202,19 +205,11 @@ __global__ void __launch_bounds__(kTThreads)
       db3 += S.dout[s];
       ls += S.loss[s];
     }
-    if (blockIdx.x == 0) {  // the input-weight decay, once per batch (scaled back by 1/n)
-      float pen = 0.0f;
-      for (int j = 0; j < kHid; ++j) {
-        const float a = dev.params[kOffW1 + 3 * j + 1], b = dev.params[kOffW1 + 3 * j + 2];
-        pen = fmaf(a, a, fmaf(b, b, pen));
-      }
-      ls += 0.5f * kInputDecay * pen * static_cast<float>(sp.n_total);
-    }
     gp[kOffB3] = db3;
     loss_part[blockIdx.x] = ls;
   }
   __syncthreads();  // z2 is overwritten by delta1 below
-  // delta1 = (delta2 W2) * relu'(z1), warp w: samples 16w .. 16w + 15
+  // delta1 = (delta2 W2) * silu'(z1), warp w: samples 16w .. 16w + 15
   {
     const int s0 = 16 * warp;
     uint32_t a[4][4];
@@ -237,10 +232,10 @@ __global__ void __launch_bounds__(kTThreads)
                        *reinterpret_cast<const uint32_t*>(brow + 16 * q),
                        *reinterpret_cast<const uint32_t*>(brow + 16 * q + 8));
       const int i0 = 8 * nt + 2 * t;
-      S.z2[s0 + g][i0] = c[0] * relu_grad(S.z1[s0 + g][i0]);
-      S.z2[s0 + g][i0 + 1] = c[1] * relu_grad(S.z1[s0 + g][i0 + 1]);
-      S.z2[s0 + g + 8][i0] = c[2] * relu_grad(S.z1[s0 + g + 8][i0]);
-      S.z2[s0 + g + 8][i0 + 1] = c[3] * relu_grad(S.z1[s0 + g + 8][i0 + 1]);
+      S.z2[s0 + g][i0] = c[0] * silu_grad(S.z1[s0 + g][i0]);
+      S.z2[s0 + g][i0 + 1] = c[1] * silu_grad(S.z1[s0 + g][i0 + 1]);
+      S.z2[s0 + g + 8][i0] = c[2] * silu_grad(S.z1[s0 + g + 8][i0]);
+      S.z2[s0 + g + 8][i0 + 1] = c[3] * silu_grad(S.z1[s0 + g + 8][i0 + 1]);
     }
   }
   // dW2 = delta2^T h1 over the block's 128 samples: output [j][i];
@@ -284,11 +279,9 @@ __global__ void __launch_bounds__(kTThreads)
       a2 = fmaf(d, S.x[s][2], a2);
       b += d;
     }
-    // block 0 adds the gradient of the input-weight decay
-    const float dec = blockIdx.x == 0 ? kInputDecay : 0.0f;
     gp[kOffW1 + 3 * j] = a0;
-    gp[kOffW1 + 3 * j + 1] = fmaf(dec, dev.params[kOffW1 + 3 * j + 1], a1);
-    gp[kOffW1 + 3 * j + 2] = fmaf(dec, dev.params[kOffW1 + 3 * j + 2], a2);
+    gp[kOffW1 + 3 * j + 1] = a1;
+    gp[kOffW1 + 3 * j + 2] = a2;
     gp[kOffB1 + j] = b;
   }
 }
@@ -324,9 +317,9 @@ __global__ void k_mlp_reduce_adam(const float* __restrict__ partial, int nblocks
 }
 
 // The finishing kernel on the tcgen05 tensor cores (mlp_tc.cuh): tiles of
-// 128 consecutive records, one per thread, two tiles in flight per CTA.  A
-// slot's payload (r, gamma, eps_c, ledger index) and weight are loaded two
-// tiles ahead.  A tensor-core wait that runs out stops the block and sets
+// 128 consecutive records, one per thread, kTcSlots tiles in flight per CTA.
+// A slot's payload (r, gamma, eps_c, ledger index) and weight are loaded one
+// tile of that slot ahead.  A tensor-core wait that runs out stops the block and sets
 // status bit 2.
 struct FinishSrc {
   const MlpFinishArgs& a;
@@ -343,7 +336,7 @@ struct FinishSrc {
     first = beg + static_cast<unsigned long long>(blockIdx.x) * kTcRows + threadIdx.x;
     stride = static_cast<unsigned long long>(gridDim.x) * kTcRows;
     load(first, nx0, nw0);
-    load(first + stride, nx1, nw1);
+    if (kTcSlots > 1) load(first + stride, nx1, nw1);
   }
   __device__ void load(unsigned long long row, float4& pd, float& w) const {
     // past the end: a harmless payload that books nothing (ledger index -1)
@@ -352,7 +345,7 @@ struct FinishSrc {
   }
   __device__ bool has(long long k) const { return first - threadIdx.x + k * stride < end; }
   __device__ float3 features(int sl, long long k) {
-    const unsigned long long ahead = first + (k + 2) * stride;
+    const unsigned long long ahead = first + (k + kTcSlots) * stride;
     float4& pd = sl == 0 ? pd0 : pd1;
     float4& nx = sl == 0 ? nx0 : nx1;
     float& w = sl == 0 ? w0 : w1;
@@ -385,7 +378,7 @@ struct FinishSrc {
 };
 
 #ifndef PRAD_TC_MINB
-#define PRAD_TC_MINB 4
+#define PRAD_TC_MINB (kTcSlots == 1 ? 6 : 4)
 #endif
 __global__ void __launch_bounds__(kTcRows, PRAD_TC_MINB) k_mlp_finish_tc(const MlpFinishArgs a) {
   extern __shared__ unsigned char tc_raw[];
@@ -420,7 +413,7 @@ struct EvalSrc {
     first = static_cast<int64_t>(blockIdx.x) * kTcRows + threadIdx.x;
     stride = static_cast<int64_t>(gridDim.x) * kTcRows;
     nx0 = load(first);
-    nx1 = load(first + stride);
+    if (kTcSlots > 1) nx1 = load(first + stride);
   }
   __device__ float3 load(int64_t i) const {
     return i < n ? make_float3(in[3 * i], in[3 * i + 1], in[3 * i + 2])
@@ -431,7 +424,7 @@ struct EvalSrc {
     float3& v = sl == 0 ? v0 : v1;
     float3& nx = sl == 0 ? nx0 : nx1;
     v = nx;
-    nx = load(first + (k + 2) * stride);
+    nx = load(first + (k + kTcSlots) * stride);
     return mlp_features(v.x, v.y, v.z);
   }
   __device__ void finish(int sl, long long k, float o) {
@@ -465,14 +458,13 @@ size_t mlp_train_smem_bytes() { return sizeof(TrainSmem); }
 cudaError_t launch_mlp_train_block(const MlpDev& dev, uint32_t key0, uint32_t key1,
                                    uint64_t first, int64_t n_valid, int64_t n_total,
                                    const float4* explicit_samples, const float* ginv,
-                                   float* partial, float* loss_part, int nblocks,
-                                   cudaStream_t s) {
+                                   float lng_lo, float lng_span, float lnh_lo,
+                                   float lnh_span, float wdt_per_H_g2, float* partial,
+                                   float* loss_part, int nblocks, cudaStream_t s) {
   SampleSpec sp;
   sp.key0 = key0; sp.key1 = key1; sp.first = first;
-  // gamma and omega_c dt log-uniform over the feature box
-  sp.lng_lo = kLnGamC - kLnGamS; sp.lng_span = 2.0f * kLnGamS;
-  sp.lnw_lo = kLnWC - kLnWS; sp.lnw_span = 2.0f * kLnWS;
-  sp.ginv = ginv; sp.explicit_samples = explicit_samples;
+  sp.lng_lo = lng_lo; sp.lng_span = lng_span; sp.lnh_lo = lnh_lo; sp.lnh_span = lnh_span;
+  sp.wdt_per_H_g2 = wdt_per_H_g2; sp.ginv = ginv; sp.explicit_samples = explicit_samples;
   sp.n_total = n_total; sp.n_valid = n_valid;
   const int bytes = static_cast<int>(sizeof(TrainSmem));
   cudaError_t e = cudaFuncSetAttribute(k_mlp_train_block,
@@ -521,7 +513,7 @@ cudaError_t launch_mlp_finish(const MlpFinishArgs& a, int grid, cudaStream_t s) 
 }
 
 // Resident CTAs per SM, from the kernel's registers and shared memory and
-// the SM's limits (4 on GB300: shared memory); every resident CTA holds
+// the SM's limits (6 on GB300 with one slot: shared memory); every resident CTA holds
 // kTcCols of the SM's 512 TMEM columns, so the allocations never wait on
 // one another.
 int mlp_finish_blocks_per_sm() {

@@ -6,18 +6,20 @@
 // (TMEM lane = row, one 32-bit column per output unit), one thread issues
 // the MMAs and an mbarrier signals their completion.  Per tile:
 //   layer 1: A1 = [f0h f1h f2h f0l f1l f2l 1 1 0..] (128 x 16, BF16)
-//            B1 = W1 | split b1 (64 x 16, BF16)             -> D = z1
+//            B1 = halved W1 | split b1 (64 x 16, BF16)      -> D = z1 / 2
 //   layer 2: A2 = [h1 | 1 1 0..] (128 x 80, f16)
-//            B2 = W2 | split b2 (64 x 80, f16)              -> D = z2
+//            B2 = halved W2 | split b2 (64 x 80, f16)       -> D = z2 / 2
 //   layer 3: A3 = h2 (A2's first 64 columns, K = 64, f16)
 //            B3 = W3 in row 0 (16 x 64, f16)                -> D[:, 0] = o - b3
-// with h = f16(relu(z)) between the layers (one cvt.rn.relu.f16x2.f32 per
-// pair), the numerics of mlp_device.cuh; features and biases enter as sums
-// of two parts (BF16 or f16 high part + rounded remainder), so z agrees with
-// the FP32 form to ~1e-6, and the BF16 weights are exact in f16.  A CTA
-// keeps two tiles in flight (slots): the tensor cores work on one while the
-// threads convert the other; a slot's three accumulators share its 64 TMEM
-// columns, each read out before the slot's next MMA is issued.
+// with h = f16(SiLU) in packed f16 arithmetic between the layers (the
+// halved images make the accumulators hold z / 2, the argument of SiLU's
+// tanh form; halving is exact), the numerics of mlp_device.cuh; features
+// and biases enter as sums of two parts (BF16 or f16 high part + rounded
+// remainder), so z agrees with the FP32 form to ~1e-6, and the BF16 weights
+// are exact in f16.  A CTA keeps kTcSlots tiles in flight (with two, the
+// tensor cores work on one while the threads run the other's SiLU); a
+// slot's three accumulators share its 64 TMEM columns, each read out before
+// the slot's next MMA is issued.
 //
 // Every wait on the tensor cores is bounded.  A wait that runs out marks
 // the thread bad; the block agrees on it at its next barrier and stops.
@@ -128,9 +130,9 @@ __device__ __forceinline__ void tmem_ld_32x32b_x1(uint32_t taddr, uint32_t* v) {
                : "r"(taddr));
 }
 
-__device__ __forceinline__ void tmem_wait_ld_x64(uint32_t* v) {
+__device__ __forceinline__ void tmem_wait_ld_x32(uint32_t* v) {
   asm volatile("tcgen05.wait::ld.sync.aligned;"
-               : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7]), "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]), "+r"(v[13]), "+r"(v[14]), "+r"(v[15]), "+r"(v[16]), "+r"(v[17]), "+r"(v[18]), "+r"(v[19]), "+r"(v[20]), "+r"(v[21]), "+r"(v[22]), "+r"(v[23]), "+r"(v[24]), "+r"(v[25]), "+r"(v[26]), "+r"(v[27]), "+r"(v[28]), "+r"(v[29]), "+r"(v[30]), "+r"(v[31]), "+r"(v[32]), "+r"(v[33]), "+r"(v[34]), "+r"(v[35]), "+r"(v[36]), "+r"(v[37]), "+r"(v[38]), "+r"(v[39]), "+r"(v[40]), "+r"(v[41]), "+r"(v[42]), "+r"(v[43]), "+r"(v[44]), "+r"(v[45]), "+r"(v[46]), "+r"(v[47]), "+r"(v[48]), "+r"(v[49]), "+r"(v[50]), "+r"(v[51]), "+r"(v[52]), "+r"(v[53]), "+r"(v[54]), "+r"(v[55]), "+r"(v[56]), "+r"(v[57]), "+r"(v[58]), "+r"(v[59]), "+r"(v[60]), "+r"(v[61]), "+r"(v[62]), "+r"(v[63])
+               : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7]), "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]), "+r"(v[13]), "+r"(v[14]), "+r"(v[15]), "+r"(v[16]), "+r"(v[17]), "+r"(v[18]), "+r"(v[19]), "+r"(v[20]), "+r"(v[21]), "+r"(v[22]), "+r"(v[23]), "+r"(v[24]), "+r"(v[25]), "+r"(v[26]), "+r"(v[27]), "+r"(v[28]), "+r"(v[29]), "+r"(v[30]), "+r"(v[31])
                :
                : "memory");
 }
@@ -161,9 +163,17 @@ __host__ __device__ constexpr uint32_t tc_idesc(bool bf16, int m, int n) {
 
 // ---- 128-row tiles, two in flight per CTA --------------------------------
 constexpr int kTcRows = 128;          // rows per tile = threads per CTA
-constexpr int kTcSlots = 2;           // tiles in flight per CTA
+// Tiles in flight per CTA.  Two overlap one tile's MMAs with the other's
+// activations; with SiLU the kernel is bound by the MUFU tanh instead, and
+// one slot, which fits six CTAs per SM (24 warps) instead of four, is
+// faster (1.28 against 1.43 ms for 29M records).
+#ifndef PRAD_TC_SLOTS
+#define PRAD_TC_SLOTS 1
+#endif
+constexpr int kTcSlots = PRAD_TC_SLOTS;  // 1 or 2
+static_assert(kTcSlots == 1 || kTcSlots == 2, "one or two slots");
 constexpr int kTcK2 = 80;             // layer-2 K: 64 units, 2 bias columns, zeros
-constexpr uint32_t kTcCols = 128;     // TMEM columns held per CTA: 64 per slot
+constexpr uint32_t kTcCols = 64 * kTcSlots;  // TMEM columns held per CTA: 64 per slot
 constexpr uint32_t kTcLbo = 128;      // core matrix: 8 rows x 16 B
 constexpr uint32_t kTcSbo1 = 2 * 128;            // K = 16
 constexpr uint32_t kTcSbo2 = (kTcK2 / 8) * 128;  // K = 80
@@ -232,17 +242,17 @@ __device__ __forceinline__ void tc_setup(TcSmem& S, const MlpDev& d, bool withho
     else if (k < 6) v = bf16_round(d.params[kOffW1 + 3 * n + k - 3]);
     else if (k == 6) v = b1h;
     else if (k == 7) v = bf16_round(b1 - b1h);
-    S.b1[tc_off(n, k, kTcSbo1)] = tc_bf16_bits(v);
+    S.b1[tc_off(n, k, kTcSbo1)] = tc_bf16_bits(0.5f * v);  // halved: exact
   }
   for (int e = threadIdx.x; e < kHid * kTcK2; e += nt) {  // B2 (unit n, k)
     const int n = e / kTcK2, k = e - n * kTcK2;
     float v = 0.0f;
     if (k < kHid) {
-      v = __bfloat162float(d.w2[n * kHid + k]);
+      v = 0.5f * __bfloat162float(d.w2[n * kHid + k]);
     } else if (k < kHid + 2) {
-      const float b2 = d.params[kOffB2 + n];
-      const float hi = __half2float(__float2half_rn(b2));
-      v = k == kHid ? hi : b2 - hi;
+      const float hb = 0.5f * d.params[kOffB2 + n];
+      const float hi = __half2float(__float2half_rn(hb));
+      v = k == kHid ? hi : hb - hi;
     }
     S.b2[tc_off(n, k, kTcSbo2)] = tc_f16_bits(v);
   }
@@ -260,8 +270,7 @@ __device__ __forceinline__ void tc_setup(TcSmem& S, const MlpDev& d, bool withho
   if (threadIdx.x == 0) {
     S.b3s = d.params[kOffB3];
     S.withhold = withhold ? 1u : 0u;
-    tc_mbar_init(&S.bar[0]);
-    tc_mbar_init(&S.bar[1]);
+    for (int sl = 0; sl < kTcSlots; ++sl) tc_mbar_init(&S.bar[sl]);
   }
   __syncwarp();
   if (threadIdx.x < 32) tc_tmem_alloc(&S.tmem, kTcCols);
@@ -295,21 +304,24 @@ __device__ __forceinline__ void tc_put_a1(uint16_t* a2, int row, float3 f) {
   *reinterpret_cast<uint4*>(&a2[tc_off(row, 8, kTcSbo2)]) = make_uint4(0u, 0u, 0u, 0u);
 }
 
-// Reads this thread's 64 accumulator columns z and writes f16(relu(z)) into
-// A2 columns 0..63.
-__device__ __forceinline__ void tc_relu_to_a2(uint16_t* a2, int row, uint32_t taddr) {
-  uint32_t z[kHid];
-  tmem_ld_32x32b_x32(taddr, z);
-  tmem_ld_32x32b_x32(taddr + 32, z + 32);
-  tmem_wait_ld_x64(z);
+// Reads this thread's 64 accumulator columns z (= z_true / 2) and writes
+// f16(SiLU(2 z)) into A2 columns 0..63.
+// (two halves of 32 columns: 32 accumulator registers live at a time)
+__device__ __forceinline__ void tc_silu_to_a2(uint16_t* a2, int row, uint32_t taddr) {
 #pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    uint4 q;
-    q.x = relu_f16x2(__uint_as_float(z[8 * c + 0]), __uint_as_float(z[8 * c + 1]));
-    q.y = relu_f16x2(__uint_as_float(z[8 * c + 2]), __uint_as_float(z[8 * c + 3]));
-    q.z = relu_f16x2(__uint_as_float(z[8 * c + 4]), __uint_as_float(z[8 * c + 5]));
-    q.w = relu_f16x2(__uint_as_float(z[8 * c + 6]), __uint_as_float(z[8 * c + 7]));
-    *reinterpret_cast<uint4*>(&a2[tc_off(row, 8 * c, kTcSbo2)]) = q;
+  for (int half = 0; half < 2; ++half) {
+    uint32_t z[32];
+    tmem_ld_32x32b_x32(taddr + 32 * half, z);
+    tmem_wait_ld_x32(z);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      uint4 q;
+      q.x = silu_half_f16x2(__uint_as_float(z[8 * c + 0]), __uint_as_float(z[8 * c + 1]));
+      q.y = silu_half_f16x2(__uint_as_float(z[8 * c + 2]), __uint_as_float(z[8 * c + 3]));
+      q.z = silu_half_f16x2(__uint_as_float(z[8 * c + 4]), __uint_as_float(z[8 * c + 5]));
+      q.w = silu_half_f16x2(__uint_as_float(z[8 * c + 6]), __uint_as_float(z[8 * c + 7]));
+      *reinterpret_cast<uint4*>(&a2[tc_off(row, 32 * half + 8 * c, kTcSbo2)]) = q;
+    }
   }
 }
 
@@ -342,9 +354,9 @@ __device__ __forceinline__ void tc_issue(TcSmem& S, int sl, int layer) {
 // mbarrier: the parity of the next phase, and whether a committed group has
 // not been seen complete (with the parity it completes).
 struct TcSlots {
-  uint32_t phase[kTcSlots] = {0u, 0u};
-  uint32_t pend_par[kTcSlots] = {0u, 0u};
-  bool pend[kTcSlots] = {false, false};
+  uint32_t phase[kTcSlots] = {};
+  uint32_t pend_par[kTcSlots] = {};
+  bool pend[kTcSlots] = {};
   bool bad = false;  // a wait of this thread ran out
 };
 
@@ -365,8 +377,7 @@ __device__ __forceinline__ void tc_wait(TcSmem& S, TcSlots& t, int sl) {
 
 // The network over a sequence of 128-row tiles k = 0, 1, 2, ... (one row per
 // thread; tile k in slot k % 2), software-pipelined so that the tensor
-// cores work on one slot while the threads convert the other slot's
-// activations.
+// cores work on one slot while the threads run the other slot's SiLU.
 // Src supplies, block-uniformly, whether tile k exists (has(k)), this
 // thread's features of tile k in slot sl (features(sl, k): called once per
 // tile, in order of k), and takes kOutScale * o of the thread's row
@@ -378,21 +389,21 @@ __device__ __forceinline__ bool tc_run(TcSmem& S, Src& src) {
   const uint32_t lanes = S.tmem + (static_cast<uint32_t>(row & ~31) << 16);  // warp's TMEM lanes
   TcSlots t;
   long long k0 = 0;  // tile of slot 0; slot 1 holds k0 + 1
-  bool live0 = src.has(0), live1 = src.has(1);
+  bool live0 = src.has(0), live1 = kTcSlots > 1 && src.has(1);
   bool stop = false;
   if (live0) tc_put_a1(S.a2[0], row, src.features(0, 0));
-  if (live1) tc_put_a1(S.a2[1], row, src.features(1, 1));
+  if (live1) tc_put_a1(S.a2[kTcSlots - 1], row, src.features(kTcSlots - 1, 1));
   tc_sync_bad(false);
   if (live0) {
     if (row == 0) tc_issue(S, 0, 1);
     tc_note_issue(t, 0);
   }
   if (live1) {
-    if (row == 0) tc_issue(S, 1, 1);
-    tc_note_issue(t, 1);
+    if (row == 0) tc_issue(S, kTcSlots - 1, 1);
+    tc_note_issue(t, kTcSlots - 1);
   }
   while (live0 && !stop) {
-    // layers 2 and 3: activations of slot sl's accumulators, then its next layer
+    // layers 2 and 3: SiLU of slot sl's accumulators, then its next layer
 #pragma unroll
     for (int layer = 2; layer <= 3; ++layer) {
 #pragma unroll
@@ -400,7 +411,7 @@ __device__ __forceinline__ bool tc_run(TcSmem& S, Src& src) {
         const bool live = sl == 0 ? live0 : live1;
         if (!live || stop) continue;
         tc_wait(S, t, sl);
-        tc_relu_to_a2(S.a2[sl], row, lanes + sl * kHid);
+        tc_silu_to_a2(S.a2[sl], row, lanes + sl * kHid);
         if (tc_sync_bad(t.bad)) {
           stop = true;
           continue;

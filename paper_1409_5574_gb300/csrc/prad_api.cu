@@ -1297,6 +1297,15 @@ int ensure_mlp_partials(prad_ctx* c, int nblocks) {
   return PRAD_OK;
 }
 
+// training-sample ranges (log-uniform gamma and H_eff) and omega_c dt / (H gamma^2)
+void mlp_ranges(const prad_ctx* c, float* lng_lo, float* lng_span, float* lnh_lo,
+                float* lnh_span, float* wdt_per) {
+  *lng_lo = static_cast<float>(std::log(10.0));
+  *lng_span = static_cast<float>(std::log(1e4) - std::log(10.0));
+  *lnh_lo = static_cast<float>(std::log(1e2));
+  *lnh_span = static_cast<float>(std::log(1e6) - std::log(1e2));
+  *wdt_per = static_cast<float>(1.5 * kQe / kMe * c->cfg.dt);
+}
 }  // namespace
 
 int prad_mlp_train(prad_ctx* c, int64_t steps, int32_t batch, float lr, uint64_t seed,
@@ -1306,12 +1315,14 @@ int prad_mlp_train(prad_ctx* c, int64_t steps, int32_t batch, float lr, uint64_t
   const int nblocks = (batch + 127) / 128;
   int rc = ensure_mlp_partials(c, nblocks);
   if (rc != PRAD_OK) return rc;
+  float lng_lo, lng_span, lnh_lo, lnh_span, wdt;
+  mlp_ranges(c, &lng_lo, &lng_span, &lnh_lo, &lnh_span, &wdt);
   const MlpDev dev = mlp_dev(c);
   for (int64_t s = 0; s < steps; ++s) {
     CK(c, launch_mlp_train_block(dev, static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32),
                                  static_cast<uint64_t>(s) * batch, batch, batch, nullptr,
-                                 c->d_ginv, c->d_mlp_partial, c->d_mlp_loss_part, nblocks,
-                                 c->stream));
+                                 c->d_ginv, lng_lo, lng_span, lnh_lo, lnh_span, wdt,
+                                 c->d_mlp_partial, c->d_mlp_loss_part, nblocks, c->stream));
     c->mlp_t += 1;
     const double lr_s = lr * 0.5 * (1.0 + std::cos(kPi * static_cast<double>(s) / steps));
     const float b1t = static_cast<float>(std::pow(0.9, static_cast<double>(c->mlp_t)));
@@ -1336,9 +1347,11 @@ int prad_mlp_grad(prad_ctx* c, const float* samples, int64_t n, float* grad, dou
   const int nblocks = static_cast<int>((n + 127) / 128);
   int rc = ensure_mlp_partials(c, nblocks);
   if (rc != PRAD_OK) return rc;
+  float lng_lo, lng_span, lnh_lo, lnh_span, wdt;
+  mlp_ranges(c, &lng_lo, &lng_span, &lnh_lo, &lnh_span, &wdt);
   CK(c, launch_mlp_train_block(mlp_dev(c), 0, 0, 0, n, n, reinterpret_cast<const float4*>(samples),
-                               c->d_ginv, c->d_mlp_partial, c->d_mlp_loss_part, nblocks,
-                               c->stream));
+                               c->d_ginv, lng_lo, lng_span, lnh_lo, lnh_span, wdt,
+                               c->d_mlp_partial, c->d_mlp_loss_part, nblocks, c->stream));
   CK(c, launch_mlp_reduce_adam(c->d_mlp_partial, nblocks, c->d_mlp_loss_part, c->d_mlp_grad,
                                c->d_mlp, c->d_mlp_m, c->d_mlp_v, c->d_mlp_w2, 0.0f, 0.0f, 0.0f,
                                0, c->d_mlp_loss, 1.0f / static_cast<float>(n), c->stream));

@@ -67,26 +67,29 @@ def test_features_definition():
     assert f[1] == pytest.approx([-1.0, 1.0, -1.0], abs=1e-12)
 
 
-def test_forward_closed_form():
-    """W1 = 0, b1 = 1.5 on units 0..15 and -2 elsewhere: h1 = relu(b1);
-    W2 shifts (output unit j reads h1[j-1]), b2 = -0.25: h2[j] = 1.25 for
-    j = 1..16, else relu(-0.25) = 0; W3 = 1, b3 = 0.125: o = 16 * 1.25 +
-    0.125 = 20.125 (every value exact in BF16 and f16).  A transposed W2
-    gives 15 live units, a smooth activation a different value."""
-    p = np.zeros(M.NUM_PARAMS)
-    b1 = np.where(np.arange(M.H) < 16, 1.5, -2.0)
-    p[M.OFF_B1:M.OFF_W2] = b1
+def test_forward_matches_torch_layers():
+    """The forward pass (without the roundings) against torch's own SiLU and
+    matrix products in float64, on a net whose W2 shifts units (output unit
+    j reads h1[j-1]): a transposed W2, a dropped bias or another activation
+    changes the output."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(9)
+    p = M.glorot(21)
     W2 = np.zeros((M.H, M.H))
-    W2[np.arange(1, M.H), np.arange(0, M.H - 1)] = 1.0
+    W2[np.arange(1, M.H), np.arange(0, M.H - 1)] = rng.uniform(0.5, 1.5, M.H - 1)
     p[M.OFF_W2:M.OFF_B2] = W2.ravel()
-    p[M.OFF_B2:M.OFF_W3] = -0.25
-    p[M.OFF_W3:M.OFF_B3] = 1.0
-    p[M.OFF_B3] = 0.125
-    f = M.features(np.array([0.3, 0.9]), np.array([50.0, 2e3]), np.array([1.0, 1e6]))
-    for rounding in (True, False):
-        o, _ = M.forward(p, f, rounding)
-        np.testing.assert_array_equal(o, [20.125, 20.125])
-    # the prior carries the output: ln x = o + prior(r)
-    r = np.array([0.3])
-    assert M.ln_x(p, r, np.array([50.0]), np.array([1.0]))[0] == pytest.approx(
-        20.125 + np.log(-np.log1p(-0.3)) + 2 * 0.7 * np.log(0.3), rel=1e-15)
+    p[M.OFF_B1:M.OFF_W2] = np.where(np.arange(M.H) < 16, 1.5, -2.0)
+    r, g, w, _ = _batch(n=32, seed=5)
+    f = M.features(r, g, w)
+    o, _ = M.forward(p, f, rounding=False)
+    t = torch.tensor
+    W1 = t(p[M.OFF_W1:M.OFF_B1].reshape(M.H, 3))
+    lin1 = t(f) @ W1.T + t(p[M.OFF_B1:M.OFF_W2])
+    h1 = torch.nn.functional.silu(lin1)
+    h2 = torch.nn.functional.silu(h1 @ t(W2).T + t(p[M.OFF_B2:M.OFF_W3]))
+    ref = (h2 @ t(p[M.OFF_W3:M.OFF_B3]) + p[M.OFF_B3]).numpy()
+    np.testing.assert_allclose(o, ref, rtol=1e-13, atol=1e-13)
+    # the transposed shift gives a different output
+    bad = p.copy()
+    bad[M.OFF_W2:M.OFF_B2] = W2.T.ravel()
+    assert np.max(np.abs(M.forward(bad, f, rounding=False)[0] - o)) > 1e-3

@@ -376,19 +376,19 @@ __device__ __forceinline__ void tc_wait(TcSmem& S, TcSlots& t, int sl) {
 }
 
 // The network over a sequence of 128-row tiles k = 0, 1, 2, ... (one row per
-// thread; tile k in slot k % 2), software-pipelined so that the tensor
-// cores work on one slot while the threads run the other slot's SiLU.
-// Src supplies, block-uniformly, whether tile k exists (has(k)), this
-// thread's features of tile k in slot sl (features(sl, k): called once per
-// tile, in order of k), and takes kOutScale * o of the thread's row
-// (finish(sl, k, o): not called for a tile whose waits ran out).  Block-collective.  Returns true if a tensor-core wait ran
-// out in any thread (the block then stopped early).
+// thread; tile k in slot k % kTcSlots; with two slots the tensor cores work
+// on one while the threads run the other's SiLU).  Src supplies,
+// block-uniformly, whether tile k exists (has(k)), this thread's features of
+// tile k in slot sl (features(sl, k): called once per tile, in order of k),
+// and takes kOutScale * o of the thread's row (finish(sl, k, o): not called
+// for a tile whose waits ran out).  Block-collective.  Returns true if a
+// tensor-core wait ran out in any thread (the block then stopped early).
 template <class Src>
 __device__ __forceinline__ bool tc_run(TcSmem& S, Src& src) {
   const int row = threadIdx.x;
   const uint32_t lanes = S.tmem + (static_cast<uint32_t>(row & ~31) << 16);  // warp's TMEM lanes
   TcSlots t;
-  long long k0 = 0;  // tile of slot 0; slot 1 holds k0 + 1
+  long long k0 = 0;  // tile of slot 0; a second slot holds k0 + 1
   bool live0 = src.has(0), live1 = kTcSlots > 1 && src.has(1);
   bool stop = false;
   if (live0) tc_put_a1(S.a2[0], row, src.features(0, 0));

@@ -10,6 +10,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 
 #include "mlp_device.cuh"
 #include "prad_internal.h"
@@ -365,12 +367,63 @@ __device__ __forceinline__ EB<R> gather(const StepParams<R>& P, R x, R y,
 constexpr int kStage = 64;
 constexpr int kMaxWarps = 8;  // 256 threads per block at most
 
-struct PhotonStage {
-  float f[8][kStage];  // x y z nx ny nz eps weight
+// Two layouts of the staging buffer.  Fields (SoA): one 32-bit store per
+// field and record; it keeps the fewest registers live, which the table
+// and batched kernels need.  Records (AoS): record r in three 16-byte
+// vectors, (x, y, z, u_x), (u_y, u_z, eps, weight), (pid, step, -, -) as
+// bits, and the learned sampler's payload (r, gamma, eps_c, ledger index)
+// in a fourth: three or four vector stores per record, which the learned
+// sampler's step kernel (14 words per record) gains from; the 48-byte record
+// stride keeps the 8 lanes of each quarter-warp on distinct banks.  u is the
+// raw mean momentum, normalised at the flush.
+struct PhotonStageSoA {
+  float f[8][kStage];  // x y z u_x u_y u_z eps weight
   uint32_t pid[kStage];
   uint32_t step[kStage];
   float pend[4][kStage];  // learned sampler: r, gamma, eps_c, ledger index
 };
+struct PhotonStageAoS {
+  float4 q[kStage][3];
+  float4 pend[kStage];
+};
+
+template <bool PEND>
+__device__ __forceinline__ void stage_put(PhotonStageSoA& st, int pos, const float rec[8],
+                                          uint32_t pid, uint32_t step, const float* pend) {
+#pragma unroll
+  for (int k = 0; k < 8; ++k) st.f[k][pos] = rec[k];
+  st.pid[pos] = pid;
+  st.step[pos] = step;
+  if constexpr (PEND) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) st.pend[k][pos] = pend[k];
+  }
+}
+template <bool PEND>
+__device__ __forceinline__ void stage_put(PhotonStageAoS& st, int pos, const float rec[8],
+                                          uint32_t pid, uint32_t step, const float* pend) {
+  st.q[pos][0] = make_float4(rec[0], rec[1], rec[2], rec[3]);
+  st.q[pos][1] = make_float4(rec[4], rec[5], rec[6], rec[7]);
+  st.q[pos][2] = make_float4(__uint_as_float(pid), __uint_as_float(step), 0.0f, 0.0f);
+  if constexpr (PEND) st.pend[pos] = make_float4(pend[0], pend[1], pend[2], pend[3]);
+}
+__device__ __forceinline__ float4 stage_pend(const PhotonStageSoA& st, int r) {
+  return make_float4(st.pend[0][r], st.pend[1][r], st.pend[2][r], st.pend[3][r]);
+}
+__device__ __forceinline__ float4 stage_pend(const PhotonStageAoS& st, int r) {
+  return st.pend[r];
+}
+__device__ __forceinline__ float stage_weight(const PhotonStageSoA& st, int r) {
+  return st.f[7][r];
+}
+__device__ __forceinline__ float stage_weight(const PhotonStageAoS& st, int r) {
+  return st.q[r][1].w;
+}
+
+// The layout a kernel stages in: records for the learned sampler's step
+// kernel (Pend), fields otherwise.
+template <bool Aos>
+using PhotonStageT = typename std::conditional<Aos, PhotonStageAoS, PhotonStageSoA>::type;
 
 struct PhotonOut {
   float* f[8];
@@ -385,9 +438,8 @@ struct PhotonOut {
   unsigned long long* fallback;
 };
 
-template <bool PEND = false>
-__device__ __forceinline__ void flush_stage(PhotonStage& st, int fill,
-                                            const PhotonOut& o) {
+template <bool PEND = false, class ST>
+__device__ __forceinline__ void flush_stage(ST& st, int fill, const PhotonOut& o) {
   const int lane = threadIdx.x & 31;
   unsigned long long base = 0ull;
   if (lane == 0) base = atomicAdd(o.cursor, static_cast<unsigned long long>(fill));
@@ -398,23 +450,34 @@ __device__ __forceinline__ void flush_stage(PhotonStage& st, int fill,
     if (slot < static_cast<unsigned long long>(o.cap)) {
       // the direction is staged as the raw mean momentum: normalise here,
       // once per record, instead of in every lane of every step
-      const float dx = st.f[3][r], dy = st.f[4][r], dz = st.f[5][r];
-      const float d2 = dx * dx + dy * dy + dz * dz;
-      const float inv = d2 > 0.0f ? rsqrtf(d2) : 0.0f;
-      o.f[0][slot] = st.f[0][r]; o.f[1][slot] = st.f[1][r]; o.f[2][slot] = st.f[2][r];
-      o.f[3][slot] = dx * inv; o.f[4][slot] = dy * inv; o.f[5][slot] = dz * inv;
-      o.f[6][slot] = st.f[6][r]; o.f[7][slot] = st.f[7][r];
-      o.pid[slot] = st.pid[r];
-      o.step[slot] = st.step[r];
-      if constexpr (PEND)
-        o.pend[slot] = make_float4(st.pend[0][r], st.pend[1][r], st.pend[2][r], st.pend[3][r]);
+      if constexpr (std::is_same<ST, PhotonStageAoS>::value) {
+        const float4 qa = st.q[r][0], qb = st.q[r][1], qc = st.q[r][2];
+        const float d2 = qa.w * qa.w + qb.x * qb.x + qb.y * qb.y;
+        const float inv = d2 > 0.0f ? rsqrtf(d2) : 0.0f;
+        o.f[0][slot] = qa.x; o.f[1][slot] = qa.y; o.f[2][slot] = qa.z;
+        o.f[3][slot] = qa.w * inv; o.f[4][slot] = qb.x * inv; o.f[5][slot] = qb.y * inv;
+        o.f[6][slot] = qb.z; o.f[7][slot] = qb.w;
+        o.pid[slot] = __float_as_uint(qc.x);
+        o.step[slot] = __float_as_uint(qc.y);
+      } else {
+        const float dx = st.f[3][r], dy = st.f[4][r], dz = st.f[5][r];
+        const float d2 = dx * dx + dy * dy + dz * dz;
+        const float inv = d2 > 0.0f ? rsqrtf(d2) : 0.0f;
+        o.f[0][slot] = st.f[0][r]; o.f[1][slot] = st.f[1][r]; o.f[2][slot] = st.f[2][r];
+        o.f[3][slot] = dx * inv; o.f[4][slot] = dy * inv; o.f[5][slot] = dz * inv;
+        o.f[6][slot] = st.f[6][r]; o.f[7][slot] = st.f[7][r];
+        o.pid[slot] = st.pid[r];
+        o.step[slot] = st.step[r];
+      }
+      if constexpr (PEND) o.pend[slot] = stage_pend(st, r);
     } else if constexpr (PEND) {
       // dropped record: its energy still enters the ledger
-      const float x = __expf(ginv_ln(o.ginv, st.pend[0][r]));
-      const int li = __float_as_int(st.pend[3][r]);
+      const float4 pd = stage_pend(st, r);
+      const float x = __expf(ginv_ln(o.ginv, pd.x));
+      const int li = __float_as_int(pd.w);
       if (li >= 0)
         atomicAdd(o.led_base + li,
-                  static_cast<double>(st.f[7][r]) * static_cast<double>(x * st.pend[2][r]));
+                  static_cast<double>(stage_weight(st, r)) * static_cast<double>(x * pd.z));
       atomicAdd(o.fallback, 1ull);
     }
   }
@@ -424,8 +487,8 @@ __device__ __forceinline__ void flush_stage(PhotonStage& st, int fill,
 // Warp-collective, with the warp's ballot of `want` already taken (mask != 0).
 // rec = position, mean momentum (normalised at flush), energy, weight;
 // pend (PEND) = the learned sampler's payload.
-template <bool PEND = false>
-__device__ __forceinline__ void stage_photon_mask(PhotonStage& st, int& fill,
+template <bool PEND = false, class ST>
+__device__ __forceinline__ void stage_photon_mask(ST& st, int& fill,
                                                   const PhotonOut& o, bool want,
                                                   unsigned mask, const float rec[8],
                                                   uint32_t pid, uint32_t step,
@@ -438,20 +501,14 @@ __device__ __forceinline__ void stage_photon_mask(PhotonStage& st, int& fill,
   if (want) {
     const int lane = threadIdx.x & 31;
     const int pos = fill + __popc(mask & ((1u << lane) - 1u));
-#pragma unroll
-    for (int k = 0; k < 8; ++k) st.f[k][pos] = rec[k];
-    st.pid[pos] = pid;
-    st.step[pos] = step;
-    if constexpr (PEND) {
-#pragma unroll
-      for (int k = 0; k < 4; ++k) st.pend[k][pos] = pend[k];
-    }
+    stage_put<PEND>(st, pos, rec, pid, step, pend);
   }
   fill += cnt;
 }
 
 // Warp-collective: every lane of the warp calls it with its own `want`.
-__device__ __forceinline__ void stage_photon(PhotonStage& st, int& fill,
+template <class ST>
+__device__ __forceinline__ void stage_photon(ST& st, int& fill,
                                              const PhotonOut& o, bool want,
                                              const float rec[8], uint32_t pid,
                                              uint32_t step) {
@@ -572,11 +629,12 @@ __device__ __forceinline__ void load_state(const StepParams<R>& P, int64_t i, bo
 // CTRL: super-photon control or diagnostics are enabled (the plain method
 // compiles without their per-step work).
 // rk: the Philox round keys, in the kernel's parameter space.
-template <typename R, int FIELD, int SAMP, bool ONE = false, bool CTRL = false, class G>
+template <typename R, int FIELD, int SAMP, bool ONE = false, bool CTRL = false, class G,
+          class ST>
 __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const uint32_t (&rk)[20],
                                                  const G& gat,
                                                  int64_t i, const PState<R>& st,
-                                                 PhotonStage& stage, int& fill,
+                                                 ST& stage, int& fill,
                                                  const PhotonOut& pout, Counts& cnt) {
   const bool act = st.act;
   R x = st.x, y = st.y, z = st.z, ux = st.ux, uy = st.uy, uz = st.uz;
@@ -874,8 +932,9 @@ int occupancy_of(K kernel, int block, size_t dyn) {
 template <typename R, int FIELD, int SAMP, bool PF, bool CTRL>
 __global__ void __launch_bounds__(256, (PF ? PRAD_PF_MINB : MinBlocks<R, FIELD, SAMP>::value))
     k_push_emit(const StepParams<R> P) {
-  __shared__ PhotonStage stage_all[kMaxWarps];
-  PhotonStage& stage = stage_all[threadIdx.x >> 5];
+  using Stage = PhotonStageT<SAMP != PRAD_SAMPLER_TABLE>;
+  __shared__ Stage stage_all[kMaxWarps];
+  Stage& stage = stage_all[threadIdx.x >> 5];
   int fill = 0;  // warp-uniform
   const PhotonOut pout = make_pout(P);
   Counts cnt;
@@ -919,11 +978,11 @@ __global__ void __launch_bounds__(256, (PF ? PRAD_PF_MINB : MinBlocks<R, FIELD, 
 template <int SAMP, bool CTRL>
 __global__ void __launch_bounds__(256, PRAD_BATCH_MINB)
     k_push_emit_batch(const BatchParams bp) {
-  __shared__ PhotonStage stage_all[kMaxWarps];
+  __shared__ PhotonStageSoA stage_all[kMaxWarps];
   __shared__ StepParams<float> Ps;
   __shared__ long long s_item;
   __shared__ int s_ens;
-  PhotonStage& stage = stage_all[threadIdx.x >> 5];
+  PhotonStageSoA& stage = stage_all[threadIdx.x >> 5];
   int fill = 0;
   Counts cnt;
   int cur = -1;
@@ -1041,7 +1100,7 @@ template <typename R, bool CTRL>
 __global__ void __launch_bounds__(256, 3) k_push_emit_tiled(const StepParams<R> P) {
   if (blockIdx.x >= *P.work_count) return;
   extern __shared__ float tile_sm[];
-  __shared__ PhotonStage stage_all[kMaxWarps];
+  __shared__ PhotonStageSoA stage_all[kMaxWarps];
   const int4 wk = P.work[blockIdx.x];
   const int tx = wk.x % P.ntx, ty = wk.x / P.ntx;
   const int gx0 = tx * kTile - kHalo, gy0 = ty * kTile - kHalo;
@@ -1068,7 +1127,7 @@ __global__ void __launch_bounds__(256, 3) k_push_emit_tiled(const StepParams<R> 
     tile_sm[e] = __ldg(P.yee[c] + static_cast<size_t>(gy) * P.nx + gx);
   }
   __syncthreads();
-  PhotonStage& stage = stage_all[threadIdx.x >> 5];
+  PhotonStageSoA& stage = stage_all[threadIdx.x >> 5];
   int fill = 0;
   const PhotonOut pout = make_pout(P);
   Counts cnt;

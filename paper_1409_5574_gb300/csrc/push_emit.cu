@@ -538,10 +538,20 @@ struct TileGather {
   const StepParams<R>& P;
   const float* sm;
   int gx0, gy0;  // grid cell of staged value (0, 0)
-  // component c from the staged tile, stencil origin (i0, j0) in tile
-  // coordinates
-  __device__ __forceinline__ R comp(int c, int i0, const R wx[3], int j0, const R wy[3]) const {
-    const float* base = sm + c * (kStageW * kStageW) + j0 * kStageW + i0;
+  // Staged layout (tile coordinates, row-major kStageW x kStageW per plane):
+  // (Ex, By) and (Ey, Bx) interleaved in pairs, since each pair shares its
+  // staggering and so its stencil, then the Ez and Bz planes.
+  static constexpr int kPlane = kStageW * kStageW;
+  __host__ __device__ static constexpr int pos(int c, int r) {
+    return c == 0 ? 2 * r
+                  : c == 4 ? 2 * r + 1
+                  : c == 1 ? 2 * kPlane + 2 * r
+                  : c == 3 ? 2 * kPlane + 2 * r + 1
+                  : c == 2 ? 4 * kPlane + r : 5 * kPlane + r;
+  }
+  // one plane (Ez: p = 4, Bz: p = 5), stencil origin (i0, j0)
+  __device__ __forceinline__ R comp(int p, int i0, const R wx[3], int j0, const R wy[3]) const {
+    const float* base = sm + p * kPlane + j0 * kStageW + i0;
     R v = R(0);
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
@@ -549,6 +559,21 @@ struct TileGather {
       v += wy[b] * (wx[0] * R(row[0]) + wx[1] * R(row[1]) + wx[2] * R(row[2]));
     }
     return v;
+  }
+  // an interleaved pair (pair 0: Ex, By; pair 1: Ey, Bx)
+  __device__ __forceinline__ void comp2(int pair, int i0, const R wx[3], int j0, const R wy[3],
+                                        R& a, R& b) const {
+    const float2* base =
+        reinterpret_cast<const float2*>(sm) + pair * kPlane + j0 * kStageW + i0;
+    a = R(0);
+    b = R(0);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float2* row = base + k * kStageW;
+      const float2 v0 = row[0], v1 = row[1], v2 = row[2];
+      a += wy[k] * (wx[0] * R(v0.x) + wx[1] * R(v1.x) + wx[2] * R(v2.x));
+      b += wy[k] * (wx[0] * R(v0.y) + wx[1] * R(v1.y) + wx[2] * R(v2.y));
+    }
   }
   __device__ __forceinline__ EB<R> operator()(R x, R y, uint64_t) const {
     const Cell<R> cx = cell_of(x, P.x0, P.inv_dx, P.inv_dx_lo, P.nx);
@@ -564,11 +589,9 @@ struct TileGather {
     const int iy0 = rl + qs_weights(cy.f, wy0) - 1;
     const int iyh = rl + qs_weights(cy.f - R(0.5), wyh) - 1;
     EB<R> f;
-    f.Ex = comp(0, ixh, wxh, iy0, wy0);
-    f.Ey = comp(1, ix0, wx0, iyh, wyh);
-    f.Ez = comp(2, ix0, wx0, iy0, wy0);
-    f.Bx = comp(3, ix0, wx0, iyh, wyh);
-    f.By = comp(4, ixh, wxh, iy0, wy0);
+    comp2(0, ixh, wxh, iy0, wy0, f.Ex, f.By);
+    comp2(1, ix0, wx0, iyh, wyh, f.Ey, f.Bx);
+    f.Ez = comp(4, ix0, wx0, iy0, wy0);
     f.Bz = comp(5, ixh, wxh, iyh, wyh);
     return f;
   }
@@ -1099,7 +1122,7 @@ int batch_max_blocks_per_sm(int block, int sampler, bool ctrl) {
 template <typename R, bool CTRL>
 __global__ void __launch_bounds__(256, 3) k_push_emit_tiled(const StepParams<R> P) {
   if (blockIdx.x >= *P.work_count) return;
-  extern __shared__ float tile_sm[];
+  extern __shared__ __align__(16) float tile_sm[];
   __shared__ PhotonStageSoA stage_all[kMaxWarps];
   const int4 wk = P.work[blockIdx.x];
   const int tx = wk.x % P.ntx, ty = wk.x / P.ntx;
@@ -1124,7 +1147,7 @@ __global__ void __launch_bounds__(256, 3) k_push_emit_tiled(const StepParams<R> 
       gx += gx < 0 ? P.nx : 0;
       gy += gy < 0 ? P.ny : 0;
     }
-    tile_sm[e] = __ldg(P.yee[c] + static_cast<size_t>(gy) * P.nx + gx);
+    tile_sm[TileGather<R>::pos(c, r)] = __ldg(P.yee[c] + static_cast<size_t>(gy) * P.nx + gx);
   }
   __syncthreads();
   PhotonStageSoA& stage = stage_all[threadIdx.x >> 5];

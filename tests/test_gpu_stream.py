@@ -115,3 +115,47 @@ def test_one_step_tiny_counts():
     for n in (1, 31, 255, 257):
         wl = W.plane_wave(a0=500.0, n=n, seed=16)
         _same(_run(wl, 5, steps_per_launch=1), _run(wl, 5, steps_per_launch=5))
+
+
+@pytest.fixture(scope="module")
+def mlp_params():
+    """A trained learned sampler (10^7 device samples: enough for valid
+    outputs; the equality below does not depend on its accuracy)."""
+    wl = W.plane_wave(a0=300.0, n=16, seed=1)
+    ctx = prad.Context(wl.problem_kwargs(), precision=prad.PRAD_FP32,
+                       photon_capacity=1 << 10, max_particles=16)
+    ctx.mlp_train(160, 65536, 3e-3, seed=3)
+    p = ctx.mlp_weights()
+    ctx.close()
+    return p
+
+
+@pytest.mark.parametrize("n", [256 * 37, 256 * 41 + 129])
+def test_one_step_launches_equal_fused_launch_learned_sampler(mlp_params, n):
+    """The learned sampler's step kernel (records staged as vectors with the
+    network payload) in one-step and multi-step launches: the same state,
+    counters and photon multiset (energies from the finishing kernel after
+    each call), ledgers to FP64 rounding."""
+    wl = W.plane_wave(a0=500.0, n=n, seed=21)
+    out = []
+    for spl in (1, 12):
+        ctx = prad.Context(wl.problem_kwargs(), precision=prad.PRAD_FP32,
+                           sampler=prad.PRAD_SAMPLER_MLP_FALLBACK, photon_capacity=1 << 20,
+                           max_particles=wl.n, steps_per_launch=spl)
+        ctx.mlp_set_weights(mlp_params)
+        st = ctx.to_device(wl.state)
+        ctx.push_emit(st, 12, t0=3)
+        torch.cuda.synchronize()
+        ph = ctx.photons(on_device=False)
+        e, l, stats = ctx.energy_budget()
+        le, ll = ctx.ledger()
+        out.append(dict(state={k: v.cpu().numpy().copy() for k, v in st.items() if k != "pid"},
+                        ph={k: (v.numpy().copy() if hasattr(v, "numpy") else v)
+                            for k, v in ph.items()},
+                        e=e, l=l, stats=stats, le=le.cpu().numpy(), ll=ll.cpu().numpy()))
+        ctx.close()
+    a, b = out
+    assert a["stats"]["records"] > 0
+    for k in ("records", "dropped", "dn_gt1", "clamped", "chi_gt1", "nan_frozen", "status"):
+        assert a["stats"][k] == b["stats"][k], k
+    _same(a, b)

@@ -143,6 +143,31 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(seconds: float, device) -> float:
+    """The largest of every rank's `seconds` (one all-reduce over the process
+    group on `device`); `seconds` itself when no group of more than one rank
+    is initialised."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return seconds
+    t = torch.tensor([seconds], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, seconds: float, world_size: int) -> float:
+    """Whole-job throughput of identical per-rank work timed by the slowest
+    rank."""
+    return world_size * units_per_rank / seconds
+
+
+def rank_inputs(rank: int, n: int) -> dict:
+    """Seeds and particle-id offset of a rank's replica (independent
+    particles: no two ranks share ids or random streams)."""
+    return {"seed": 1 + 97 * rank, "pid0": rank * n}
+
+
 def a0_list(s: str):
     return [float(v) for v in s.split(",") if v.strip()]
 
@@ -364,7 +389,8 @@ def run_prad(args):
     bps = args.bps if args.bps > 0 else 0
 
     # inputs: seeded synthetic states, one per a0, resident in HBM
-    wls = [W.plane_wave(a0=a0, n=n, periods=args.periods, seed=1 + 97 * rank) for a0 in a0s]
+    ri = rank_inputs(rank, n)
+    wls = [W.plane_wave(a0=a0, n=n, periods=args.periods, seed=ri["seed"]) for a0 in a0s]
     cap = int(0.12 * n * nsteps) + (1 << 20)
     ctx = prad.Context(wls[0].problem_kwargs(), precision=prad.PRAD_FP32,
                        photon_capacity=cap, max_particles=n, steps_per_launch=nsub,
@@ -372,7 +398,7 @@ def run_prad(args):
     init = [ctx.to_device(w.state) for w in wls]
     work = {k: torch.empty_like(v) for k, v in init[0].items()}
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    pid0 = rank * n
+    pid0 = ri["pid0"]
     launches_per_run = math.ceil(nsteps / nsub)
 
     def one_step():
@@ -409,13 +435,9 @@ def run_prad(args):
     if ws > 1:
         dist.barrier()
     ck = clocks.stop()
-    t_total = sum(times)
-    if ws > 1:
-        tt = torch.tensor([t_total], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_total = float(tt.item())
+    t_total = max_over_ranks(sum(times), "cuda")
     ps_per_step = len(a0s) * n * nsteps
-    value = ws * ps_per_step * args.steps / t_total
+    value = job_rate(ps_per_step * args.steps, t_total, ws)
 
     # dominant kernel: average launch duration of the fused push kernel, from
     # events around one run's push_emit only (same stream, same launches)
@@ -519,12 +541,8 @@ def run_prad(args):
         for _ in range(args.steps):
             e2e_step()
         torch.cuda.synchronize()
-        te = time.perf_counter() - t0
-        if ws > 1:
-            tt = torch.tensor([te], device="cuda", dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            te = float(tt.item())
-        e2e = {"value": ws * ps_per_step * args.steps / te, "unit": UNIT,
+        te = max_over_ranks(time.perf_counter() - t0, "cuda")
+        e2e = {"value": job_rate(ps_per_step * args.steps, te, ws), "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     # The metric's other arm: the learned sampler (trained here on 10^8
@@ -571,9 +589,9 @@ def run_prad(args):
             m1.synchronize()
             tm += m0.elapsed_time(m1) / 1e3
         _, _, mst = ctx_m.energy_budget()
-        v_mlp = ps_per_step * args.steps / tm
-        mlp = {"value": v_mlp, "unit": UNIT, "vs_table": v_mlp / (ps_per_step * args.steps
-                                                                  / t_total * 1.0),
+        tm = max_over_ranks(tm, "cuda")
+        v_mlp = job_rate(ps_per_step * args.steps, tm, ws)
+        mlp = {"value": v_mlp, "unit": UNIT, "vs_table": v_mlp / value,
                "spectral_error": bound,
                "spectral_error_how": "first order from the device G^-1 table at gamma=1e3, "
                                      "omega_c dt=1e3 (tests check the exact error against "

@@ -276,8 +276,8 @@ def other_workloads(prad, W, torch, params, rank):
     # 1000 steps, sorted by 32 x 32-cell tile every 8 steps
     wl = W.yee2d(nsteps=1000, seed=1 + rank)
     ctx = prad.Context(wl.problem_kwargs(), precision=prad.PRAD_FP32,
-                       photon_capacity=1 << 28, max_particles=wl.n, sort_interval=8,
-                       steps_per_launch=8)
+                       photon_capacity=1 << 28, max_particles=wl.n, sort_interval=16,
+                       steps_per_launch=16)
     st = ctx.to_device(wl.state, with_pid=True)
     ctx.push_emit({k: v[:4096].clone() for k, v in st.items()}, 8)   # warm-up
     ctx.reset()
@@ -289,7 +289,7 @@ def other_workloads(prad, W, torch, params, rank):
     out["yee2d"] = {"value": wl.n * 1000 / secs, "unit": UNIT,
                     "workload": "2D Yee 4096^2 FP32 planes, a0=300 standing wave + 1% noise, "
                                 "16777216 electrons in the central 1024^2 cells, 1000 steps, "
-                                "tile sort every 8 steps, table sampler"}
+                                "tile sort every 16 steps, table sampler"}
     ctx.close()
     del st, wl
 

@@ -273,7 +273,7 @@ def other_workloads(prad, W, torch, params, rank):
         return a.elapsed_time(b) / 1e3
 
     # 2D Yee grid 4096^2 (standing wave a0 = 300 + 1% noise), 16M electrons,
-    # 1000 steps, sorted by 32 x 32-cell tile every 8 steps
+    # 1000 steps, sorted by 32 x 32-cell tile every 16 steps
     wl = W.yee2d(nsteps=1000, seed=1 + rank)
     ctx = prad.Context(wl.problem_kwargs(), precision=prad.PRAD_FP32,
                        photon_capacity=1 << 28, max_particles=wl.n, sort_interval=16,

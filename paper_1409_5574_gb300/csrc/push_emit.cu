@@ -41,12 +41,19 @@ __device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
 // with rk in the kernel's parameter space each round's XOR with the key
 // reads it from there instead of carrying the key schedule in registers, and
 // each product is one 32 x 32 -> 64-bit multiply (hi and lo words at once).
+// ZeroTag: counter word 2 is 0, and so is word 2 after the first round; the
+// products of those words are left to the compiler, which folds them (the
+// table-sampler kernels gain from it, the learned sampler's does not).
+template <bool ZeroTag = false>
 __device__ __forceinline__ uint4 philox10_rk(uint4 c, const uint32_t* rk) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
     uint64_t p0, p1;
     asm("mul.wide.u32 %0, %1, %2;" : "=l"(p0) : "r"(c.x), "r"(0xD2511F53u));
-    asm("mul.wide.u32 %0, %1, %2;" : "=l"(p1) : "r"(c.z), "r"(0xCD9E8D57u));
+    if (ZeroTag && r < 2)
+      p1 = static_cast<uint64_t>(c.z) * 0xCD9E8D57ull;
+    else
+      asm("mul.wide.u32 %0, %1, %2;" : "=l"(p1) : "r"(c.z), "r"(0xCD9E8D57u));
     const uint32_t lo0 = static_cast<uint32_t>(p0), hi0 = static_cast<uint32_t>(p0 >> 32);
     const uint32_t lo1 = static_cast<uint32_t>(p1), hi1 = static_cast<uint32_t>(p1 >> 32);
     c = make_uint4(hi1 ^ c.y ^ rk[2 * r], lo1, hi0 ^ c.w ^ rk[2 * r + 1], lo0);
@@ -776,7 +783,7 @@ __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const u
       yn -= P.Ly * flr((yn - P.y0) * (R(1) / P.Ly));
     }
     const uint4 ctr = make_uint4(pid, step, 0u, P.ensemble);
-    const uint4 rnd = philox10_rk(ctr, rk);
+    const uint4 rnd = philox10_rk<SAMP == PRAD_SAMPLER_TABLE>(ctr, rk);
     const R Rr = unit_uniform<R>(rnd.z);
     if constexpr (SAMP == PRAD_SAMPLER_TABLE) {
       // 8. Monte Carlo emission: proposal x = P^-1(R'), dN of Eq. (13);

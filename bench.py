@@ -39,9 +39,9 @@ KERNEL_SOURCES = ["paper_1409_5574_gb300/csrc/push_emit.cu",
                   "paper_1409_5574_gb300/csrc/prad_internal.h",
                   "paper_1409_5574_gb300/csrc/mlp_device.cuh"]
 NCU_TRAFFIC = {
-    "src_sha256": "094618bc5645be38428743b673ad2a1364c173993e40761e3e292ce7b64e9e38",
-    "fused": 256139639,   # mean bytes per launch over the 30 fused launches of one bench step
-    "stream": 1333899520, # bytes per launch, 2^24 particles x 1 step, a0 = 500
+    "src_sha256": "1c4a13b70083323474166b6da22630af05b4e4098bb8465b3415fe99a09e0caf",
+    "fused": 256023083,   # mean bytes per launch over the 30 fused launches of one bench step
+    "stream": 1334459904, # bytes per launch, 2^24 particles x 1 step, a0 = 500
 }
 
 
@@ -297,7 +297,7 @@ def other_workloads(prad, W, torch, params, rank):
     # 400 steps from the initial state (the emission-heavy first periods)
     n4 = 1 << 26
     wl = W.plane_wave(a0=500.0, n=n4, periods=2, seed=41 + rank)
-    res = {}
+    res, bal = {}, {}
     for name, smp in (("table", prad.PRAD_SAMPLER_TABLE),
                       ("mlp", prad.PRAD_SAMPLER_MLP_FALLBACK)):
         if smp != prad.PRAD_SAMPLER_TABLE and params is None:
@@ -328,7 +328,7 @@ def other_workloads(prad, W, torch, params, rank):
     # captured graph, autotuned launch shape
     es = W.ensembles(count=256, nsteps=500, seed=1 + rank)
     total = int(sum(w.n for w in es.workloads))
-    res = {}
+    res, bal = {}, {}
     for name, smp in (("table", prad.PRAD_SAMPLER_TABLE),
                       ("mlp", prad.PRAD_SAMPLER_MLP_FALLBACK)):
         if smp != prad.PRAD_SAMPLER_TABLE and params is None:
@@ -343,7 +343,7 @@ def other_workloads(prad, W, torch, params, rank):
             sts = [ctx.to_device(w.state) for w in es.workloads]
             probs = [w.problem_kwargs() for w in es.workloads]
             ctx.autotune_batch(ctx.ensembles(sts, probs), probe_steps=10, sample=4096)
-            secs = 0.0
+            secs, effs = 0.0, []
             for c in range(5):
                 ens = ctx.ensembles(sts, probs, t0=100 * c)
                 a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -352,13 +352,18 @@ def other_workloads(prad, W, torch, params, rank):
                 b.record(s2)
                 b.synchronize()
                 secs += a.elapsed_time(b) / 1e3
+                effs.append(ctx.batch_balance())  # outside the events
                 ctx.drain()
             res[name] = total * 500 / secs
+            # mean over maximum of the CTAs' busy clocks, per call
+            bal[name] = {"efficiency": sum(e for e, _ in effs) / len(effs),
+                         "min_efficiency": min(e for e, _ in effs), "ctas": effs[0][1]}
             ctx.close()
             del sts
     out["batched_256"] = {
         "table": res.get("table"), "mlp": res.get("mlp"), "unit": UNIT,
         "mlp_vs_table": (res["mlp"] / res["table"]) if "mlp" in res else None,
+        "load_balance": bal,
         "workload": f"256 ensembles, {total} electrons, 500 steps in 5 graph-replayed calls, "
                     "autotuned persistent kernel"}
     return out

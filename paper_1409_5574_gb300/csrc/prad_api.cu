@@ -83,6 +83,9 @@ struct prad_ctx {
   StepParams<float>* d_batch = nullptr;
   int64_t* d_batch_off = nullptr;
   unsigned long long* d_batch_next = nullptr;
+  unsigned long long* d_batch_busy = nullptr;  // per-CTA busy clocks of the last call
+  int batch_busy_n = 0;                        // its entries
+  int batch_grid = 0;                          // CTAs of the last call's launches
   int batch_cap = 0;
   std::vector<StepParams<float>> h_batch;
   std::vector<int64_t> h_batch_off;
@@ -681,6 +684,10 @@ int prad_init(prad_ctx** out, const prad_config* cfg) {
     CKI(cudaMalloc(&c->d_pend, cap * sizeof(float4)));
     c->finish_grid = c->num_sms * mlp_finish_blocks_per_sm();
   }
+  // per-CTA busy clocks of batched calls: at most 2048 threads per SM in
+  // CTAs of at least 32 threads
+  c->batch_busy_n = c->num_sms * 64;
+  CKI(cudaMalloc(&c->d_batch_busy, sizeof(unsigned long long) * c->batch_busy_n));
   CKI(cudaMalloc(&c->d_cnt, kNumCounters * sizeof(unsigned long long)));
   CKI(cudaMemset(c->d_cnt, 0, kNumCounters * sizeof(unsigned long long)));
   const size_t np = static_cast<size_t>(cfg->max_particles);
@@ -718,6 +725,7 @@ int prad_destroy(prad_ctx* c) {
   cudaFree(c->d_batch);
   cudaFree(c->d_batch_off);
   cudaFree(c->d_batch_next);
+  cudaFree(c->d_batch_busy);
   cudaFree(c->d_tab32);
   cudaFree(c->d_tab64);
   for (int k = 0; k < 8; ++k) cudaFree(c->d_ph[k]);
@@ -1046,6 +1054,16 @@ int issue_batch(prad_ctx* c, int n_ens, int64_t items, int32_t nsteps, int chunk
   const int cap = batch_max_blocks_per_sm(block, c->cfg.sampler, ctrl_of(c));
   const int64_t g = static_cast<int64_t>(c->num_sms) * (bps < cap ? bps : cap);
   const int grid = static_cast<int>(g < items ? g : (items > 0 ? items : 1));
+  // per-CTA busy clocks of this call (load balance), zeroed per call; the
+  // array is allocated at init for the largest possible grid, so nothing
+  // is allocated here (this may run inside a graph capture)
+  bp.busy = nullptr;
+  c->batch_grid = 0;
+  if (c->d_batch_busy && grid <= c->batch_busy_n) {
+    CK(c, cudaMemsetAsync(c->d_batch_busy, 0, sizeof(unsigned long long) * grid, c->stream));
+    bp.busy = c->d_batch_busy;
+    c->batch_grid = grid;
+  }
   for (int32_t done = 0; done < nsteps;) {
     const int32_t m = (nsteps - done) < nsub ? (nsteps - done) : nsub;
     bp.step_base = done;
@@ -1406,6 +1424,24 @@ int prad_mlp_wait_selftest(prad_ctx* c) {
   if (e != cudaSuccess) return fail(c, PRAD_ERR_CUDA, cudaGetErrorString(e));
   if (st & 4ull) return fail(c, PRAD_ERR_TIMEOUT, "mlp_wait_selftest: the bounded waits ran out");
   return fail(c, PRAD_ERR_STATE, "mlp_wait_selftest: the withheld waits did not report");
+}
+
+int prad_batch_balance(prad_ctx* c, double* efficiency, int32_t* ctas) {
+  if (!c || !efficiency) return fail(c, PRAD_ERR_ARG, "batch_balance: null argument");
+  if (c->batch_grid < 1 || !c->d_batch_busy)
+    return fail(c, PRAD_ERR_STATE, "batch_balance: no batched call yet");
+  std::vector<unsigned long long> busy(static_cast<size_t>(c->batch_grid));
+  CK(c, cudaMemcpyAsync(busy.data(), c->d_batch_busy, sizeof(unsigned long long) * busy.size(),
+                        cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  double sum = 0.0, mx = 0.0;
+  for (unsigned long long b : busy) {
+    sum += static_cast<double>(b);
+    mx = static_cast<double>(b) > mx ? static_cast<double>(b) : mx;
+  }
+  *efficiency = mx > 0.0 ? sum / (mx * static_cast<double>(busy.size())) : 0.0;
+  if (ctas) *ctas = c->batch_grid;
+  return PRAD_OK;
 }
 
 int prad_ginv_eval(prad_ctx* c, const float* r, float* lnx, int64_t n) {

@@ -144,6 +144,9 @@ struct BatchParams {
   int32_t nsub;                // steps of this launch
   int32_t pad;
   uint32_t rkey[20];           // Philox round keys of the context's seed
+  // per-CTA busy SM clocks, accumulated over a call's launches (load
+  // balance); may be null
+  unsigned long long* busy;
 };
 
 // Philox4x32-10 round keys of a 64-bit seed: (key0 + r 0x9E3779B9,

@@ -1008,6 +1008,7 @@ __global__ void __launch_bounds__(256, (PF ? PRAD_PF_MINB : MinBlocks<R, FIELD, 
 template <int SAMP, bool CTRL>
 __global__ void __launch_bounds__(256, PRAD_BATCH_MINB)
     k_push_emit_batch(const BatchParams bp) {
+  const long long t_begin = clock64();
   __shared__ PhotonStageSoA stage_all[kMaxWarps];
   __shared__ StepParams<float> Ps;
   __shared__ long long s_item;
@@ -1081,6 +1082,8 @@ __global__ void __launch_bounds__(256, PRAD_BATCH_MINB)
   if (cur >= 0 && fill > 0) flush_stage<SAMP != PRAD_SAMPLER_TABLE>(stage, fill, pout);
   // counters: any ensemble's pointer to the shared counter array will do
   flush_counts(cnt, bp.ens[0].counters);
+  if (threadIdx.x == 0 && bp.busy)  // after the block's last barrier: its busy time
+    atomicAdd(bp.busy + blockIdx.x, static_cast<unsigned long long>(clock64() - t_begin));
 }
 
 template <int SAMP>

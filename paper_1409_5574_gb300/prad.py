@@ -107,6 +107,7 @@ SIGNATURES = {
     "prad_mlp_grad": (_i32, [_vp, _vp, _i64, _vp, ctypes.POINTER(_dbl)]),
     "prad_mlp_eval": (_i32, [_vp, _vp, _vp, _i64]),
     "prad_mlp_wait_selftest": (_i32, [_vp]),
+    "prad_batch_balance": (_i32, [_vp, ctypes.POINTER(_dbl), ctypes.POINTER(_i32)]),
     "prad_ginv_eval": (_i32, [_vp, _vp, _vp, _i64]),
     "prad_ledger_totals_noalloc": (_i32, [_vp, _vp, _i64, _vp, _vp]),
     "prad_ledger_totals_noalloc_error": (ctypes.c_char_p, []),
@@ -256,6 +257,13 @@ def prad_mlp_grad(h, samples_ptr, n: int):
 
 def prad_mlp_eval(h, in_ptr, out_ptr, n: int) -> None:
     _check(load_library().prad_mlp_eval(h, in_ptr, out_ptr, n), h)
+
+
+def prad_batch_balance(h):
+    """(load-balance efficiency, CTA count) of the last batched call."""
+    eff, n = _dbl(), _i32()
+    _check(load_library().prad_batch_balance(h, ctypes.byref(eff), ctypes.byref(n)), h)
+    return eff.value, n.value
 
 
 def prad_mlp_wait_selftest(h) -> int:
@@ -466,6 +474,10 @@ class Context:
         held, dropped = prad_get_photons(self.h, ph if m else None, m, drain, on_device)
         out["dropped"] = dropped
         return out
+
+    def batch_balance(self):
+        """Load balance (mean / max CTA busy time) of the last batched call."""
+        return prad_batch_balance(self.h)
 
     def drain(self):
         return prad_get_photons(self.h, None, 0, True, True)

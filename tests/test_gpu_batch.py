@@ -198,6 +198,9 @@ def test_graph_replay_equals_direct_launches():
             ens2 = ctx.ensembles(sts, [w.problem_kwargs() for w in wls], t0=12)
             ctx.push_emit_batch(ens2, 12)
             stream.synchronize()
+            # the busy-clock array is zeroed and filled inside the graph too
+            eff, ctas = ctx.batch_balance()
+            assert 0.0 < eff <= 1.0 and ctas >= 1
             res.append(_collect(ctx, sts))
             ctx.close()
     for k in range(len(wls)):
@@ -206,6 +209,21 @@ def test_graph_replay_equals_direct_launches():
             np.testing.assert_array_equal(res[0][0][k][c], res[2][0][k][c])
     np.testing.assert_array_equal(_keys(res[0][1]), _keys(res[1][1]))
     assert res[0][3] == res[1][3]
+
+
+def test_batch_balance_needs_a_batched_call():
+    wls = _small_set(seed=5)
+    ctx = _ctx(wls)
+    with pytest.raises(prad.PradError) as ei:
+        ctx.batch_balance()
+    assert ei.value.code == prad.PRAD_ERR_STATE
+    sts = [ctx.to_device(w.state) for w in wls]
+    ctx.push_emit_batch(ctx.ensembles(sts, [w.problem_kwargs() for w in wls]), 4)
+    eff, ctas = ctx.batch_balance()
+    # a persistent launch: at most one CTA per resident slot of every SM
+    assert 0.0 < eff <= 1.0
+    assert 1 <= ctas <= torch.cuda.get_device_properties(0).multi_processor_count * 64
+    ctx.close()
 
 
 def test_autotune_leaves_state_and_caches():
@@ -255,8 +273,13 @@ def test_full_size_uneven_ensembles_graph_autotuned(sampler, trained_params):
         ev1.record(stream)
         stream.synchronize()
     secs = ev0.elapsed_time(ev1) / 1e3
+    eff, ctas = ctx.batch_balance()
     print(f"\nbatched ({sampler}): {total} particles x 500 steps in {secs * 1e3:.1f} ms = "
-          f"{total * 500 / secs:.3e} particle-steps/s, tuning {tune}")
+          f"{total * 500 / secs:.3e} particle-steps/s, tuning {tune}, "
+          f"load balance {eff:.3f} over {ctas} CTAs")
+    # work items of at most batch_chunk particles handed out by an atomic
+    # counter keep the CTAs' busy times within a few items of each other
+    assert 0.5 < eff <= 1.0
     e, l, s = ctx.energy_budget()
     assert s["dropped"] == 0 and s["status"] == 0
     off = 0

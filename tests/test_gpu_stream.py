@@ -117,6 +117,56 @@ def test_one_step_tiny_counts():
         _same(_run(wl, 5, steps_per_launch=1), _run(wl, 5, steps_per_launch=5))
 
 
+def _run_layout(wl, nsteps, with_pid=False, offset=0, ledger_offset=0):
+    """One step per launch with the arrays optionally viewed `offset`
+    elements into a larger buffer and the ledger entries at ledger_offset."""
+    ctx = prad.Context(wl.problem_kwargs(), precision=prad.PRAD_FP32,
+                       photon_capacity=1 << 20, max_particles=wl.n + ledger_offset,
+                       steps_per_launch=1)
+    st = ctx.to_device(wl.state, with_pid=with_pid)
+    if offset:
+        views = {}
+        for k, v in st.items():
+            buf = torch.zeros(v.numel() + offset, dtype=v.dtype, device=v.device)
+            buf[offset:] = v
+            views[k] = buf[offset:]
+        st = views
+    ctx.push_emit(st, nsteps, t0=3, ledger_offset=ledger_offset)
+    torch.cuda.synchronize()
+    ph = ctx.photons(on_device=False)
+    e, l, stats = ctx.energy_budget()
+    le, ll = ctx.ledger()
+    sl = slice(ledger_offset, ledger_offset + wl.n)
+    out = dict(state={k: v.cpu().numpy().copy() for k, v in st.items() if k != "pid"},
+               ph={k: (v.numpy().copy() if hasattr(v, "numpy") else v) for k, v in ph.items()},
+               e=e, l=l, stats=stats, le=le.cpu().numpy()[sl], ll=ll.cpu().numpy()[sl])
+    ctx.close()
+    return out
+
+
+@pytest.mark.parametrize("n", [255, 256 * 41 + 129, (1 << 16) + 77])
+def test_one_step_results_do_not_depend_on_layout(n):
+    """One step per launch with implicit ids, with an explicit id array, with
+    every array one element off a 16-byte boundary (views into larger
+    buffers) and with an odd ledger offset: state, ledgers, counters and
+    photons agree bit for bit."""
+    wl = W.plane_wave(a0=500.0, n=n, seed=31)
+    ref = _run_layout(wl, 6)
+    assert ref["stats"]["records"] > 0 and ref["stats"]["status"] == 0
+    for kw in (dict(with_pid=True), dict(offset=1), dict(ledger_offset=1)):
+        other = _run_layout(wl, 6, **kw)
+        for k in ref["state"]:
+            np.testing.assert_array_equal(ref["state"][k], other["state"][k], err_msg=f"{kw} {k}")
+        np.testing.assert_array_equal(ref["le"], other["le"])
+        np.testing.assert_array_equal(ref["ll"], other["ll"])
+        ka, ta = _photon_table(ref["ph"])
+        kb, tb = _photon_table(other["ph"])
+        np.testing.assert_array_equal(ka, kb)
+        np.testing.assert_array_equal(ta, tb)
+        for k in ("records", "dropped", "dn_gt1", "clamped", "chi_gt1", "nan_frozen", "status"):
+            assert ref["stats"][k] == other["stats"][k], (kw, k)
+
+
 @pytest.fixture(scope="module")
 def mlp_params():
     """A trained learned sampler (10^7 device samples: enough for valid

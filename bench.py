@@ -218,9 +218,24 @@ def cpu_baseline(args, budget_s: float) -> dict:
     t = time.perf_counter()
     ps = _oracle_step(subs, nsteps)
     dt = time.perf_counter() - t
-    return {"value": ps / dt, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
-            "sample": f"first {n} of {args.particles} electrons x {nsteps} steps for each "
-                      f"a0 in {{{args.a0}}} ({ps:.3g} particle-steps, {dt:.1f} s)"}
+    cores = O.num_threads()
+    out = {"value": ps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"first {n} of {args.particles} electrons x {nsteps} steps for each "
+                     f"a0 in {{{args.a0}}} ({ps:.3g} particle-steps, {dt:.1f} s)"}
+    # the same oracle on one core, on a sample a quarter of the time long
+    n1 = max(16, min(n, int(n * 0.25 / max(1, cores))))
+    subs1 = [s.subset(slice(0, n1)) for s in subs]
+    O.set_num_threads(1)
+    try:
+        t = time.perf_counter()
+        ps1 = _oracle_step(subs1, nsteps)
+        dt1 = time.perf_counter() - t
+    finally:
+        O.set_num_threads(cores)
+    out["single_core"] = {"value": ps1 / dt1, "unit": UNIT,
+                          "sample": f"first {n1} electrons of the same sample "
+                                    f"({ps1:.3g} particle-steps, {dt1:.1f} s)"}
+    return out
 
 
 # ---------------------------------------------------------------- reference arm

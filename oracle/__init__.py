@@ -73,6 +73,7 @@ def lib() -> ctypes.CDLL:
             L.orc_alpha.restype = d
             L.orc_branch_threshold.restype = u64
             L.orc_num_threads.restype = ctypes.c_int
+            L.orc_set_num_threads.argtypes = [ctypes.c_int]
             L.orc_sample_x.restype = d
             L.orc_sample_x.argtypes = [P, P]
             L.orc_S_of_words.restype = d
@@ -164,6 +165,11 @@ def int_F_over_x(x: float) -> float:
 
 def num_threads() -> int:
     return lib().orc_num_threads()
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the oracle's later parallel loops."""
+    lib().orc_set_num_threads(int(n))
 
 
 def philox(ctr, key) -> np.ndarray:

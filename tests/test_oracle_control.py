@@ -93,3 +93,29 @@ def test_wiggler_counter_limits():
     assert _run(wl, 20)["stats"]["wiggler_invalid"] == 0
     wl = W.const_b(n=200, nsteps=20, seed=9)
     assert _run(wl, 20)["stats"]["wiggler_invalid"] == 0
+
+
+def test_oracle_result_does_not_depend_on_thread_count():
+    """The oracle's particles are independent and its photon records are
+    returned sorted by (pid, step): one thread and all threads give the same
+    state, ledger and records (what the single-core timing relies on)."""
+    wl = W.plane_wave(a0=500.0, n=300, periods=1, seed=8)
+    cores = O.num_threads()
+    out = []
+    for nt in (1, cores):
+        O.set_num_threads(nt)
+        try:
+            assert O.num_threads() == nt
+            st = wl.copy_state()
+            r = O.run(O.Problem(**wl.problem_kwargs()), st, 40, capacity=1 << 16)
+        finally:
+            O.set_num_threads(cores)
+        out.append((st, r))
+    (s1, r1), (s2, r2) = out
+    for k in s1:
+        np.testing.assert_array_equal(s1[k], s2[k])
+    assert len(r1["photons"]["x"]) > 0
+    for k in r1["photons"]:
+        np.testing.assert_array_equal(r1["photons"][k], r2["photons"][k])
+    for k in r1["ledger"]:
+        np.testing.assert_array_equal(r1["ledger"][k], r2["ledger"][k])

@@ -851,10 +851,11 @@ __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const u
         stage_photon_mask<true>(stage, fill, pout, want, wmask, rec, pid, step, pend);
       }
     }
-    if (live) {
-      x = xn; y = yn; z = zn;
-      ux = nux; uy = nuy; uz = nuz;
-    }
+    // a particle that is not live (inactive lane or non-finite state) is
+    // never stored, emits nothing and counts nothing, so its registers may
+    // advance like the others' (no select per step)
+    x = xn; y = yn; z = zn;
+    ux = nux; uy = nuy; uz = nuz;
   }
   if (live) {
     P.x[i] = x; P.y[i] = y;

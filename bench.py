@@ -39,9 +39,9 @@ KERNEL_SOURCES = ["paper_1409_5574_gb300/csrc/push_emit.cu",
                   "paper_1409_5574_gb300/csrc/prad_internal.h",
                   "paper_1409_5574_gb300/csrc/mlp_device.cuh"]
 NCU_TRAFFIC = {
-    "src_sha256": "f0f1d1a76f104004435f3718b230401fa6649feee01f325718446ba0df1d6cc7",
-    "fused": 253793698,   # mean bytes per launch over the 30 fused launches of one bench step
-    "stream": 1333788928, # bytes per launch, 2^24 particles x 1 step, a0 = 500
+    "src_sha256": "1bf37ba5ffe15fe02b3c125834c5bbe6b109a921169c35cd16ffd5a8bbd1f5a1",
+    "fused": 253695573,   # mean bytes per launch over the 30 fused launches of one bench step
+    "stream": 1333914368, # bytes per launch, 2^24 particles x 1 step, a0 = 500
 }
 
 
@@ -494,7 +494,7 @@ def run_prad(args):
     achieved = alg_ops * n * nsub / per_launch_s / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
                 "frac": achieved / alu_peak, "traffic": ncu_traffic("fused"),
-                "kernel": "k_push_emit<float, PLANE_WAVE>",
+                "kernel": "k_push_emit<float, PLANE_WAVE, TABLE, STD>",
                 "launch": f"{n} particles x {nsub} steps",
                 "ops_per_particle_step": alg_ops,
                 "peak_source": f"{nsm} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz (sm_max_mhz of "

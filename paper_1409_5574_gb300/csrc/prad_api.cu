@@ -323,6 +323,12 @@ bool ctrl_of(const prad_ctx* c) {
          c->cfg.diagnostics != 0;
 }
 
+// The standard configuration of the batched kernel's ensembles (constant or
+// plane-wave fields, so three dimensions): LL kick applied, field-form H_eff.
+bool std_of(const prad_ctx* c) {
+  return c->cfg.rr_mode == PRAD_RR_APPLY && c->cfg.heff_form == PRAD_HEFF_FIELD;
+}
+
 MlpDev mlp_dev(const prad_ctx* c) {
   MlpDev d;
   d.params = c->d_mlp;
@@ -581,7 +587,7 @@ int push_emit_t(prad_ctx* c, const prad_particles* pp, int64_t n,
   const int sub_eff = sub < nsteps ? sub : nsteps;
   // persistent grid: at most the resident blocks of the kernel variant, so
   // no block waits for a second wave (blocks_per_sm = 0: all of them)
-  const int occ = push_emit_occupancy<R>(c->fields.kind, c->cfg.sampler, sub_eff, block,
+  const int occ = push_emit_occupancy<R>(p, c->fields.kind, c->cfg.sampler, sub_eff, block,
                                          ctrl_of(c));
   const int bps = c->cfg.blocks_per_sm > 0 && c->cfg.blocks_per_sm < occ ? c->cfg.blocks_per_sm
                                                                          : occ;
@@ -1051,7 +1057,7 @@ int issue_batch(prad_ctx* c, int n_ens, int64_t items, int32_t nsteps, int chunk
   bp.chunk = chunk;
   bp.pad = 0;
   philox_round_keys(c->cfg.seed, bp.rkey);
-  const int cap = batch_max_blocks_per_sm(block, c->cfg.sampler, ctrl_of(c));
+  const int cap = batch_max_blocks_per_sm(block, c->cfg.sampler, ctrl_of(c), std_of(c));
   const int64_t g = static_cast<int64_t>(c->num_sms) * (bps < cap ? bps : cap);
   const int grid = static_cast<int>(g < items ? g : (items > 0 ? items : 1));
   // per-CTA busy clocks of this call (load balance), zeroed per call; the
@@ -1069,7 +1075,8 @@ int issue_batch(prad_ctx* c, int n_ens, int64_t items, int32_t nsteps, int chunk
     bp.step_base = done;
     bp.nsub = m;
     CK(c, cudaMemsetAsync(c->d_batch_next, 0, sizeof(unsigned long long), c->stream));
-    CK(c, launch_push_emit_batch(bp, c->cfg.sampler, ctrl_of(c), grid, block, c->stream));
+    CK(c, launch_push_emit_batch(bp, c->cfg.sampler, ctrl_of(c), std_of(c), grid, block,
+                                 c->stream));
     done += m;
   }
   return mlp_finish(c, c->h_batch.empty() ? c->d_led_emit : c->h_batch[0].led_base);
@@ -1232,7 +1239,7 @@ int prad_autotune_batch(prad_ctx* c, const prad_ensemble* ens, int32_t n_ens, in
   int rc_all = PRAD_OK;
   for (int bi = 0; bi < 2 && rc_all == PRAD_OK; ++bi) {
     const int block = blocks[bi];
-    const int cap = batch_max_blocks_per_sm(block, c->cfg.sampler, ctrl_of(c));
+    const int cap = batch_max_blocks_per_sm(block, c->cfg.sampler, ctrl_of(c), std_of(c));
     for (int bps = 2; bps <= cap && bps <= 2 * (256 / block) * 3 && rc_all == PRAD_OK; ++bps) {
       for (int ci = 0; ci < 4 && rc_all == PRAD_OK; ++ci) {
         const int chunk = chunks[ci];

@@ -161,11 +161,15 @@ inline void philox_round_keys(uint64_t seed, uint32_t* rk) {
 }
 
 // Launchers (defined in the kernel translation units).
-cudaError_t launch_push_emit_batch(const BatchParams& bp, int sampler, bool ctrl, int grid,
-                                   int block, cudaStream_t s);
+// std_cfg: the standard configuration (LL kick applied, field form of H_eff)
+// in every ensemble, which selects the variant with those modes fixed at
+// compile time (as for k_push_emit)
+cudaError_t launch_push_emit_batch(const BatchParams& bp, int sampler, bool ctrl, bool std_cfg,
+                                   int grid, int block, cudaStream_t s);
 template <typename R>
-int push_emit_occupancy(int field_kind, int sampler, int nsub, int block, bool ctrl);
-int batch_max_blocks_per_sm(int block, int sampler, bool ctrl);
+int push_emit_occupancy(const StepParams<R>& p, int field_kind, int sampler, int nsub, int block,
+                        bool ctrl);
+int batch_max_blocks_per_sm(int block, int sampler, bool ctrl, bool std_cfg);
 template <typename R>
 cudaError_t launch_push_emit(const StepParams<R>& p, int field_kind, int sampler, int grid,
                              int block, cudaStream_t s);

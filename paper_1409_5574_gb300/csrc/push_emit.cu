@@ -659,8 +659,10 @@ __device__ __forceinline__ void load_state(const StepParams<R>& P, int64_t i, bo
 // CTRL: super-photon control or diagnostics are enabled (the plain method
 // compiles without their per-step work).
 // rk: the Philox round keys, in the kernel's parameter space.
-template <typename R, int FIELD, int SAMP, bool ONE = false, bool CTRL = false, class G,
-          class ST>
+// STD: the standard configuration (LL kick applied, field form of H_eff,
+// three dimensions) fixed at compile time, so the step tests no mode.
+template <typename R, int FIELD, int SAMP, bool ONE = false, bool CTRL = false,
+          bool STD = false, class G, class ST>
 __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const uint32_t (&rk)[20],
                                                  const G& gat,
                                                  int64_t i, const PState<R>& st,
@@ -681,6 +683,9 @@ __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const u
   (void)li_abs;
 
   const int nsub = ONE ? 1 : P.nsub;
+  const int rr_mode = STD ? PRAD_RR_APPLY : P.rr_mode;
+  const int heff_form = STD ? PRAD_HEFF_FIELD : P.heff_form;
+  const int dims = STD ? 3 : P.dims;
   for (int s = 0; s < nsub; ++s) {
     const uint32_t step = static_cast<uint32_t>(P.t0 + s);
     // 1. field at x^n, t^n
@@ -722,7 +727,7 @@ __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const u
     const R ga = (R(1) + ua2) * iga;
     // 4. effective field, limited by dp_perp/p <= 1 (Omega dt <= gamma)
     R Om;
-    if (P.heff_form == PRAD_HEFF_FIELD) {
+    if (heff_form == PRAD_HEFF_FIELD) {
       const R bx = ax * iga, by = ay * iga, bz = az * iga;
       R fx, fy, fz, eb;
       if constexpr (FIELD == PRAD_FIELD_PLANE_WAVE) {
@@ -765,9 +770,9 @@ __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const u
     if (live && P.eps_r * Om * ga > R(1)) ++cnt.chi;
     // 6. Landau-Lifshitz loss (Eq. (4)): ledger and optional kick
     const R om2 = Om * Om;
-    if (P.rr_mode >= PRAD_RR_LEDGER) ll.add(w * P.ll_coef * om2 * ua2);
+    if (rr_mode >= PRAD_RR_LEDGER) ll.add(w * P.ll_coef * om2 * ua2);
     R n2 = nux * nux + nuy * nuy + nuz * nuz;
-    if (P.rr_mode == PRAD_RR_APPLY) {
+    if (rr_mode == PRAD_RR_APPLY) {
       const R gL = sqr(R(1) + n2);
       const R fk = rcp(R(1) + P.ll_coef * om2 * gL);
       nux *= fk; nuy *= fk; nuz *= fk;
@@ -777,7 +782,7 @@ __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const u
     const R ign = rsq(R(1) + n2);
     const R dtg = P.dtn * ign;
     R xn = x + dtg * nux, yn = y + dtg * nuy, zn = z;
-    if (P.dims == 3) zn = z + dtg * nuz;
+    if (dims == 3) zn = z + dtg * nuz;
     if constexpr (FIELD == PRAD_FIELD_YEE2D) {
       xn -= P.Lx * flr((xn - P.x0) * (R(1) / P.Lx));
       yn -= P.Ly * flr((yn - P.y0) * (R(1) / P.Ly));
@@ -863,7 +868,7 @@ __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const u
     P.ux[i] = ux; P.uy[i] = uy; P.uz[i] = uz;
     const int64_t li = static_cast<int64_t>(pid - P.pid0);
     if (li < P.led_n) {
-      if (P.rr_mode >= PRAD_RR_LEDGER) {
+      if (rr_mode >= PRAD_RR_LEDGER) {
         if constexpr (ONE)
           P.led_ll[li] = st.ll_old + ll.value_one();
         else
@@ -960,7 +965,7 @@ int occupancy_of(K kernel, int block, size_t dyn) {
 #ifndef PRAD_PF_MINB
 #define PRAD_PF_MINB 4
 #endif
-template <typename R, int FIELD, int SAMP, bool PF, bool CTRL>
+template <typename R, int FIELD, int SAMP, bool PF, bool CTRL, bool STD = false>
 __global__ void __launch_bounds__(256, (PF ? PRAD_PF_MINB : MinBlocks<R, FIELD, SAMP>::value))
     k_push_emit(const StepParams<R> P) {
   using Stage = PhotonStageT<SAMP != PRAD_SAMPLER_TABLE>;
@@ -983,14 +988,16 @@ __global__ void __launch_bounds__(256, (PF ? PRAD_PF_MINB : MinBlocks<R, FIELD, 
       const PState<R> cur = nxt;
       const int64_t j = i + stride;
       load_state<R, true>(P, j, j < P.n, nxt);
-      advance_particle<R, FIELD, SAMP, true, CTRL>(P, P.rkey, gat, i, cur, stage, fill, pout, cnt);
+      advance_particle<R, FIELD, SAMP, true, CTRL, STD>(P, P.rkey, gat, i, cur, stage, fill, pout,
+                                                        cnt);
     }
   } else {
     for (int64_t base = first; base < P.n; base += stride) {
       const int64_t i = base + threadIdx.x;
       PState<R> cur;
       load_state(P, i, i < P.n, cur);
-      advance_particle<R, FIELD, SAMP, false, CTRL>(P, P.rkey, gat, i, cur, stage, fill, pout, cnt);
+      advance_particle<R, FIELD, SAMP, false, CTRL, STD>(P, P.rkey, gat, i, cur, stage, fill, pout,
+                                                         cnt);
     }
   }
   if (fill > 0) flush_stage<SAMP != PRAD_SAMPLER_TABLE>(stage, fill, pout);
@@ -1006,7 +1013,7 @@ __global__ void __launch_bounds__(256, (PF ? PRAD_PF_MINB : MinBlocks<R, FIELD, 
 #ifndef PRAD_BATCH_MINB
 #define PRAD_BATCH_MINB 3
 #endif
-template <int SAMP, bool CTRL>
+template <int SAMP, bool CTRL, bool STD = false>
 __global__ void __launch_bounds__(256, PRAD_BATCH_MINB)
     k_push_emit_batch(const BatchParams bp) {
   const long long t_begin = clock64();
@@ -1064,8 +1071,8 @@ __global__ void __launch_bounds__(256, PRAD_BATCH_MINB)
         const int64_t i = base + threadIdx.x;
         PState<float> st;
         load_state(Ps, i, i < last, st);
-        advance_particle<float, PRAD_FIELD_CONST, SAMP, false, CTRL>(Ps, bp.rkey, gat, i, st, stage,
-                                                                     fill, pout, cnt);
+        advance_particle<float, PRAD_FIELD_CONST, SAMP, false, CTRL, STD>(Ps, bp.rkey, gat, i, st,
+                                                                          stage, fill, pout, cnt);
       }
     } else {
       const FieldGather<float, PRAD_FIELD_PLANE_WAVE> gat{Ps};
@@ -1073,9 +1080,8 @@ __global__ void __launch_bounds__(256, PRAD_BATCH_MINB)
         const int64_t i = base + threadIdx.x;
         PState<float> st;
         load_state(Ps, i, i < last, st);
-        advance_particle<float, PRAD_FIELD_PLANE_WAVE, SAMP, false, CTRL>(Ps, bp.rkey, gat, i, st,
-                                                                          stage, fill, pout,
-                                                                          cnt);
+        advance_particle<float, PRAD_FIELD_PLANE_WAVE, SAMP, false, CTRL, STD>(
+            Ps, bp.rkey, gat, i, st, stage, fill, pout, cnt);
       }
     }
     __syncthreads();
@@ -1087,40 +1093,46 @@ __global__ void __launch_bounds__(256, PRAD_BATCH_MINB)
     atomicAdd(bp.busy + blockIdx.x, static_cast<unsigned long long>(clock64() - t_begin));
 }
 
+// std_cfg: every ensemble runs the standard configuration (STD variant, the
+// same per-step code as the standard k_push_emit variants)
 template <int SAMP>
-cudaError_t launch_batch_samp(const BatchParams& bp, bool ctrl, int grid, int block,
-                              cudaStream_t s) {
+cudaError_t launch_batch_samp(const BatchParams& bp, bool ctrl, bool std_cfg, int grid,
+                              int block, cudaStream_t s) {
   if (ctrl)
     k_push_emit_batch<SAMP, true><<<grid, block, 0, s>>>(bp);
+  else if (std_cfg)
+    k_push_emit_batch<SAMP, false, true><<<grid, block, 0, s>>>(bp);
   else
     k_push_emit_batch<SAMP, false><<<grid, block, 0, s>>>(bp);
   return cudaGetLastError();
 }
 
-cudaError_t launch_push_emit_batch(const BatchParams& bp, int sampler, bool ctrl, int grid,
-                                   int block, cudaStream_t s) {
+cudaError_t launch_push_emit_batch(const BatchParams& bp, int sampler, bool ctrl, bool std_cfg,
+                                   int grid, int block, cudaStream_t s) {
   switch (sampler) {
     case PRAD_SAMPLER_TABLE:
-      return launch_batch_samp<PRAD_SAMPLER_TABLE>(bp, ctrl, grid, block, s);
-    case PRAD_SAMPLER_MLP: return launch_batch_samp<PRAD_SAMPLER_MLP>(bp, ctrl, grid, block, s);
+      return launch_batch_samp<PRAD_SAMPLER_TABLE>(bp, ctrl, std_cfg, grid, block, s);
+    case PRAD_SAMPLER_MLP:
+      return launch_batch_samp<PRAD_SAMPLER_MLP>(bp, ctrl, std_cfg, grid, block, s);
     case PRAD_SAMPLER_MLP_FALLBACK:
-      return launch_batch_samp<PRAD_SAMPLER_MLP_FALLBACK>(bp, ctrl, grid, block, s);
+      return launch_batch_samp<PRAD_SAMPLER_MLP_FALLBACK>(bp, ctrl, std_cfg, grid, block, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
 template <int SAMP>
-int batch_occupancy_samp(int block, bool ctrl) {
-  return ctrl ? occupancy_of(k_push_emit_batch<SAMP, true>, block, 0)
-              : occupancy_of(k_push_emit_batch<SAMP, false>, block, 0);
+int batch_occupancy_samp(int block, bool ctrl, bool std_cfg) {
+  if (ctrl) return occupancy_of(k_push_emit_batch<SAMP, true>, block, 0);
+  if (std_cfg) return occupancy_of(k_push_emit_batch<SAMP, false, true>, block, 0);
+  return occupancy_of(k_push_emit_batch<SAMP, false>, block, 0);
 }
 
-int batch_max_blocks_per_sm(int block, int sampler, bool ctrl) {
+int batch_max_blocks_per_sm(int block, int sampler, bool ctrl, bool std_cfg) {
   switch (sampler) {
-    case PRAD_SAMPLER_MLP: return batch_occupancy_samp<PRAD_SAMPLER_MLP>(block, ctrl);
+    case PRAD_SAMPLER_MLP: return batch_occupancy_samp<PRAD_SAMPLER_MLP>(block, ctrl, std_cfg);
     case PRAD_SAMPLER_MLP_FALLBACK:
-      return batch_occupancy_samp<PRAD_SAMPLER_MLP_FALLBACK>(block, ctrl);
-    default: return batch_occupancy_samp<PRAD_SAMPLER_TABLE>(block, ctrl);
+      return batch_occupancy_samp<PRAD_SAMPLER_MLP_FALLBACK>(block, ctrl, std_cfg);
+    default: return batch_occupancy_samp<PRAD_SAMPLER_TABLE>(block, ctrl, std_cfg);
   }
 }
 
@@ -1193,6 +1205,34 @@ cudaError_t launch_push_emit_tiled(const StepParams<R>& p, int max_work, int blo
   return cudaGetLastError();
 }
 
+// The standard-configuration variant (STD) exists for FP32 analytic fields
+// without control or diagnostics.
+template <typename R, int FIELD, bool CTRL>
+constexpr bool kHasStd = sizeof(R) == 4 && FIELD != PRAD_FIELD_YEE2D && !CTRL;
+
+template <typename R>
+bool std_config(const StepParams<R>& p) {
+  return p.rr_mode == PRAD_RR_APPLY && p.heff_form == PRAD_HEFF_FIELD && p.dims == 3;
+}
+
+template <typename R, int FIELD, int SAMP, bool PF, bool CTRL>
+void launch_k(const StepParams<R>& p, int grid, int block, cudaStream_t s) {
+  if constexpr (kHasStd<R, FIELD, CTRL>) {
+    if (std_config(p)) {
+      k_push_emit<R, FIELD, SAMP, PF, CTRL, true><<<grid, block, 0, s>>>(p);
+      return;
+    }
+  }
+  k_push_emit<R, FIELD, SAMP, PF, CTRL, false><<<grid, block, 0, s>>>(p);
+}
+
+template <typename R, int FIELD, int SAMP, bool PF, bool CTRL>
+int occupancy_k(int block, bool std_cfg) {
+  if constexpr (kHasStd<R, FIELD, CTRL>)
+    if (std_cfg) return occupancy_of(k_push_emit<R, FIELD, SAMP, PF, CTRL, true>, block, 0);
+  return occupancy_of(k_push_emit<R, FIELD, SAMP, PF, CTRL, false>, block, 0);
+}
+
 template <typename R, int FIELD, bool CTRL>
 cudaError_t launch_field_c(const StepParams<R>& p, int sampler, int grid, int block,
                            cudaStream_t s) {
@@ -1202,15 +1242,15 @@ cudaError_t launch_field_c(const StepParams<R>& p, int sampler, int grid, int bl
     bool pf = false;
     if constexpr (sizeof(R) == 4) pf = p.nsub == 1;
     if constexpr (sizeof(R) == 4)
-      if (pf) k_push_emit<R, FIELD, PRAD_SAMPLER_TABLE, true, CTRL><<<grid, block, 0, s>>>(p);
-    if (!pf) k_push_emit<R, FIELD, PRAD_SAMPLER_TABLE, false, CTRL><<<grid, block, 0, s>>>(p);
+      if (pf) launch_k<R, FIELD, PRAD_SAMPLER_TABLE, true, CTRL>(p, grid, block, s);
+    if (!pf) launch_k<R, FIELD, PRAD_SAMPLER_TABLE, false, CTRL>(p, grid, block, s);
     return cudaGetLastError();
   }
   if constexpr (sizeof(R) == 4) {
     if (sampler == PRAD_SAMPLER_MLP)
-      k_push_emit<R, FIELD, PRAD_SAMPLER_MLP, false, CTRL><<<grid, block, 0, s>>>(p);
+      launch_k<R, FIELD, PRAD_SAMPLER_MLP, false, CTRL>(p, grid, block, s);
     else
-      k_push_emit<R, FIELD, PRAD_SAMPLER_MLP_FALLBACK, false, CTRL><<<grid, block, 0, s>>>(p);
+      launch_k<R, FIELD, PRAD_SAMPLER_MLP_FALLBACK, false, CTRL>(p, grid, block, s);
     return cudaGetLastError();
   }
   return cudaErrorInvalidValue;
@@ -1225,42 +1265,42 @@ cudaError_t launch_field(const StepParams<R>& p, int sampler, int grid, int bloc
 }
 
 template <typename R, int FIELD, bool CTRL>
-int field_occupancy_c(int sampler, bool pf, int block) {
+int field_occupancy_c(int sampler, bool pf, int block, bool std_cfg) {
   if (sampler == PRAD_SAMPLER_TABLE) {
     if constexpr (sizeof(R) == 4)
-      if (pf)
-        return occupancy_of(k_push_emit<R, FIELD, PRAD_SAMPLER_TABLE, true, CTRL>, block, 0);
-    return occupancy_of(k_push_emit<R, FIELD, PRAD_SAMPLER_TABLE, false, CTRL>, block, 0);
+      if (pf) return occupancy_k<R, FIELD, PRAD_SAMPLER_TABLE, true, CTRL>(block, std_cfg);
+    return occupancy_k<R, FIELD, PRAD_SAMPLER_TABLE, false, CTRL>(block, std_cfg);
   }
   if constexpr (sizeof(R) == 4) {
     if (sampler == PRAD_SAMPLER_MLP)
-      return occupancy_of(k_push_emit<R, FIELD, PRAD_SAMPLER_MLP, false, CTRL>, block, 0);
-    return occupancy_of(k_push_emit<R, FIELD, PRAD_SAMPLER_MLP_FALLBACK, false, CTRL>, block,
-                        0);
+      return occupancy_k<R, FIELD, PRAD_SAMPLER_MLP, false, CTRL>(block, std_cfg);
+    return occupancy_k<R, FIELD, PRAD_SAMPLER_MLP_FALLBACK, false, CTRL>(block, std_cfg);
   }
   return 1;
 }
 
 template <typename R, int FIELD>
-int field_occupancy(int sampler, bool pf, int block, bool ctrl) {
-  return ctrl ? field_occupancy_c<R, FIELD, true>(sampler, pf, block)
-              : field_occupancy_c<R, FIELD, false>(sampler, pf, block);
+int field_occupancy(int sampler, bool pf, int block, bool ctrl, bool std_cfg) {
+  return ctrl ? field_occupancy_c<R, FIELD, true>(sampler, pf, block, std_cfg)
+              : field_occupancy_c<R, FIELD, false>(sampler, pf, block, std_cfg);
 }
 
 // Resident blocks per SM of the kernel variant a launch would use.
 template <typename R>
-int push_emit_occupancy(int field_kind, int sampler, int nsub, int block, bool ctrl) {
+int push_emit_occupancy(const StepParams<R>& p, int field_kind, int sampler, int nsub, int block,
+                        bool ctrl) {
   const bool pf = nsub == 1;
+  const bool sc = std_config(p);
   switch (field_kind) {
     case PRAD_FIELD_CONST:
-      return field_occupancy<R, PRAD_FIELD_CONST>(sampler, pf, block, ctrl);
+      return field_occupancy<R, PRAD_FIELD_CONST>(sampler, pf, block, ctrl, sc);
     case PRAD_FIELD_PLANE_WAVE:
-      return field_occupancy<R, PRAD_FIELD_PLANE_WAVE>(sampler, pf, block, ctrl);
-    default: return field_occupancy<R, PRAD_FIELD_YEE2D>(sampler, pf, block, ctrl);
+      return field_occupancy<R, PRAD_FIELD_PLANE_WAVE>(sampler, pf, block, ctrl, sc);
+    default: return field_occupancy<R, PRAD_FIELD_YEE2D>(sampler, pf, block, ctrl, sc);
   }
 }
-template int push_emit_occupancy<float>(int, int, int, int, bool);
-template int push_emit_occupancy<double>(int, int, int, int, bool);
+template int push_emit_occupancy<float>(const StepParams<float>&, int, int, int, int, bool);
+template int push_emit_occupancy<double>(const StepParams<double>&, int, int, int, int, bool);
 
 template <typename R>
 cudaError_t launch_push_emit(const StepParams<R>& p, int field_kind, int sampler, int grid,

@@ -660,7 +660,8 @@ __device__ __forceinline__ void load_state(const StepParams<R>& P, int64_t i, bo
 // compiles without their per-step work).
 // rk: the Philox round keys, in the kernel's parameter space.
 // STD: the standard configuration (LL kick applied, field form of H_eff,
-// three dimensions) fixed at compile time, so the step tests no mode.
+// three dimensions, two for the Yee grid) fixed at compile time, so the step
+// tests no mode.
 template <typename R, int FIELD, int SAMP, bool ONE = false, bool CTRL = false,
           bool STD = false, class G, class ST>
 __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const uint32_t (&rk)[20],
@@ -685,7 +686,7 @@ __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const u
   const int nsub = ONE ? 1 : P.nsub;
   const int rr_mode = STD ? PRAD_RR_APPLY : P.rr_mode;
   const int heff_form = STD ? PRAD_HEFF_FIELD : P.heff_form;
-  const int dims = STD ? 3 : P.dims;
+  const int dims = STD ? (FIELD == PRAD_FIELD_YEE2D ? 2 : 3) : P.dims;
   for (int s = 0; s < nsub; ++s) {
     const uint32_t step = static_cast<uint32_t>(P.t0 + s);
     // 1. field at x^n, t^n
@@ -1142,7 +1143,7 @@ int batch_max_blocks_per_sm(int block, int sampler, bool ctrl, bool std_cfg) {
 // (+ halo, periodic) in shared memory with coalesced row loads, then runs the
 // same per-particle path with the shared-memory gather.
 // ---------------------------------------------------------------------------
-template <typename R, bool CTRL>
+template <typename R, bool CTRL, bool STD = false>
 __global__ void __launch_bounds__(256, 3) k_push_emit_tiled(const StepParams<R> P) {
   if (blockIdx.x >= *P.work_count) return;
   extern __shared__ __align__(16) float tile_sm[];
@@ -1182,43 +1183,49 @@ __global__ void __launch_bounds__(256, 3) k_push_emit_tiled(const StepParams<R> 
     const int64_t i = base + threadIdx.x;
     PState<R> st;
     load_state(P, i, i < wk.z, st);
-    advance_particle<R, PRAD_FIELD_YEE2D, PRAD_SAMPLER_TABLE, false, CTRL>(P, P.rkey, gat, i, st, stage,
-                                                                           fill, pout, cnt);
+    advance_particle<R, PRAD_FIELD_YEE2D, PRAD_SAMPLER_TABLE, false, CTRL, STD>(
+        P, P.rkey, gat, i, st, stage, fill, pout, cnt);
   }
   if (fill > 0) flush_stage(stage, fill, pout);
   flush_counts(cnt, P.counters);
 }
 
+// The standard-configuration variant (STD) exists for FP32 without control
+// or diagnostics.
+template <typename R, int FIELD, bool CTRL>
+constexpr bool kHasStd = sizeof(R) == 4 && !CTRL;
+
+// LL kick applied, field-form H_eff, and the field's usual dimensions
 template <typename R>
-cudaError_t launch_push_emit_tiled(const StepParams<R>& p, int max_work, int block,
-                                   cudaStream_t s) {
+bool std_config(const StepParams<R>& p, int dims) {
+  return p.rr_mode == PRAD_RR_APPLY && p.heff_form == PRAD_HEFF_FIELD && p.dims == dims;
+}
+
+template <typename R, bool CTRL, bool STD>
+cudaError_t launch_tiled_v(const StepParams<R>& p, int max_work, int block, cudaStream_t s) {
   // dynamic tile (38.4 KB) + static photon staging exceed the 48 KB default
-  const bool ctrl = p.ntry > 1 || p.sel_q < R(1) || p.diag != 0;
-  cudaError_t e = cudaFuncSetAttribute(ctrl ? k_push_emit_tiled<R, true> : k_push_emit_tiled<R, false>,
+  cudaError_t e = cudaFuncSetAttribute(k_push_emit_tiled<R, CTRL, STD>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        kTileSmemBytes);
   if (e != cudaSuccess) return e;
-  if (ctrl)
-    k_push_emit_tiled<R, true><<<max_work, block, kTileSmemBytes, s>>>(p);
-  else
-    k_push_emit_tiled<R, false><<<max_work, block, kTileSmemBytes, s>>>(p);
+  k_push_emit_tiled<R, CTRL, STD><<<max_work, block, kTileSmemBytes, s>>>(p);
   return cudaGetLastError();
 }
 
-// The standard-configuration variant (STD) exists for FP32 analytic fields
-// without control or diagnostics.
-template <typename R, int FIELD, bool CTRL>
-constexpr bool kHasStd = sizeof(R) == 4 && FIELD != PRAD_FIELD_YEE2D && !CTRL;
-
 template <typename R>
-bool std_config(const StepParams<R>& p) {
-  return p.rr_mode == PRAD_RR_APPLY && p.heff_form == PRAD_HEFF_FIELD && p.dims == 3;
+cudaError_t launch_push_emit_tiled(const StepParams<R>& p, int max_work, int block,
+                                   cudaStream_t s) {
+  const bool ctrl = p.ntry > 1 || p.sel_q < R(1) || p.diag != 0;
+  if (ctrl) return launch_tiled_v<R, true, false>(p, max_work, block, s);
+  if constexpr (kHasStd<R, PRAD_FIELD_YEE2D, false>)
+    if (std_config(p, 2)) return launch_tiled_v<R, false, true>(p, max_work, block, s);
+  return launch_tiled_v<R, false, false>(p, max_work, block, s);
 }
 
 template <typename R, int FIELD, int SAMP, bool PF, bool CTRL>
 void launch_k(const StepParams<R>& p, int grid, int block, cudaStream_t s) {
   if constexpr (kHasStd<R, FIELD, CTRL>) {
-    if (std_config(p)) {
+    if (std_config(p, FIELD == PRAD_FIELD_YEE2D ? 2 : 3)) {
       k_push_emit<R, FIELD, SAMP, PF, CTRL, true><<<grid, block, 0, s>>>(p);
       return;
     }
@@ -1290,7 +1297,7 @@ template <typename R>
 int push_emit_occupancy(const StepParams<R>& p, int field_kind, int sampler, int nsub, int block,
                         bool ctrl) {
   const bool pf = nsub == 1;
-  const bool sc = std_config(p);
+  const bool sc = std_config(p, field_kind == PRAD_FIELD_YEE2D ? 2 : 3);
   switch (field_kind) {
     case PRAD_FIELD_CONST:
       return field_occupancy<R, PRAD_FIELD_CONST>(sampler, pf, block, ctrl, sc);

@@ -145,7 +145,8 @@ def test_trained_spectral_error_below_one_percent(trained, gamma, wdt):
 
 
 def test_direct_scheme_spectrum_and_power(trained):
-    """Constant B (the configs[0] physics in FP32, no LL kick): the direct
+    """Constant B (10^4 T, isotropic electrons, gamma in [100, 1000]; FP32,
+    no LL kick): the direct
     scheme with the trained net emits the number spectrum G and, on average,
     the synchrotron power; the table scheme on the same GPU agrees."""
     params, _, _ = trained

@@ -375,12 +375,12 @@ constexpr int kStage = 64;
 constexpr int kMaxWarps = 8;  // 256 threads per block at most
 
 // Two layouts of the staging buffer.  Fields (SoA): one 32-bit store per
-// field and record; it keeps the fewest registers live, which the table
-// and batched kernels need.  Records (AoS): record r in three 16-byte
+// field and record; it keeps the fewest registers live, which the batched,
+// tiled and control kernels need.  Records (AoS): record r in three 16-byte
 // vectors, (x, y, z, u_x), (u_y, u_z, eps, weight), (pid, step, -, -) as
 // bits, and the learned sampler's payload (r, gamma, eps_c, ledger index)
-// in a fourth: three or four vector stores per record, which the learned
-// sampler's step kernel (14 words per record) gains from; the 48-byte record
+// in a fourth: three or four vector stores per record, which the plain
+// step kernels use (the learned sampler's has 14 words per record); the 48-byte record
 // stride keeps the 8 lanes of each quarter-warp on distinct banks.  u is the
 // raw mean momentum, normalised at the flush.
 struct PhotonStageSoA {
@@ -427,8 +427,7 @@ __device__ __forceinline__ float stage_weight(const PhotonStageAoS& st, int r) {
   return st.q[r][1].w;
 }
 
-// The layout a kernel stages in: records for the learned sampler's step
-// kernel (Pend), fields otherwise.
+// The layout a kernel stages in: records or fields.
 template <bool Aos>
 using PhotonStageT = typename std::conditional<Aos, PhotonStageAoS, PhotonStageSoA>::type;
 
@@ -969,7 +968,7 @@ int occupancy_of(K kernel, int block, size_t dyn) {
 template <typename R, int FIELD, int SAMP, bool PF, bool CTRL, bool STD = false>
 __global__ void __launch_bounds__(256, (PF ? PRAD_PF_MINB : MinBlocks<R, FIELD, SAMP>::value))
     k_push_emit(const StepParams<R> P) {
-  using Stage = PhotonStageT<SAMP != PRAD_SAMPLER_TABLE>;
+  using Stage = PhotonStageT<SAMP != PRAD_SAMPLER_TABLE || !CTRL>;
   __shared__ Stage stage_all[kMaxWarps];
   Stage& stage = stage_all[threadIdx.x >> 5];
   int fill = 0;  // warp-uniform

@@ -54,8 +54,10 @@ def kernel_sha() -> str:
     return h.hexdigest()
 
 
-def ncu_traffic(kind: str):
-    if NCU_TRAFFIC["src_sha256"] and NCU_TRAFFIC["src_sha256"] == kernel_sha():
+def ncu_traffic(kind: str, same_workload: bool = True):
+    """The captured DRAM bytes per launch, if the kernel sources are the ones
+    captured and the launch is the captured workload's."""
+    if same_workload and NCU_TRAFFIC["src_sha256"] and NCU_TRAFFIC["src_sha256"] == kernel_sha():
         return NCU_TRAFFIC[kind]
     return None
 UNIT = "particle-steps/s"
@@ -493,7 +495,9 @@ def run_prad(args):
     alu_peak = nsm * 128 * sm_mhz * 1e6 / 1e12
     achieved = alg_ops * n * nsub / per_launch_s / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
-                "frac": achieved / alu_peak, "traffic": ncu_traffic("fused"),
+                "frac": achieved / alu_peak,
+                "traffic": ncu_traffic("fused", n == 1 << 20 and nsub == 400 and nsteps == 4000
+                                       and a0s == [100.0, 300.0, 500.0]),
                 "kernel": "k_push_emit<float, PLANE_WAVE, TABLE, STD>",
                 "launch": f"{n} particles x {nsub} steps",
                 "ops_per_particle_step": alg_ops,
@@ -525,7 +529,8 @@ def run_prad(args):
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     ach_s = bytes_s / t_s / 1e9
     roofline_stream = {"bound": "hbm", "achieved": ach_s, "peak": hbm_peak, "unit": "GB/s",
-                       "frac": ach_s / hbm_peak, "traffic": ncu_traffic("stream"),
+                       "frac": ach_s / hbm_peak,
+                       "traffic": ncu_traffic("stream", a0s[-1] == 500.0),
                        "algorithmic_bytes": bytes_s,
                        "kernel": "k_push_emit<float, PLANE_WAVE, one-step> (next particle "
                                  "prefetched), 1 step per launch",

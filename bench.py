@@ -80,7 +80,7 @@ def parse():
     ap.add_argument("--no-mlp", action="store_true")
     ap.add_argument("--no-other", action="store_true",
                     help="skip the Yee, a0=500 2^26-electron and batched workloads")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
     return ap.parse_args()
 
 

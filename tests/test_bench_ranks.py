@@ -60,3 +60,16 @@ def test_two_rank_reduction_and_replica_inputs():
 def test_single_process_needs_no_group():
     assert bench.max_over_ranks(2.5, "cpu") == 2.5
     assert bench.job_rate(10.0, 2.0, 1) == 5.0
+
+
+def test_captured_traffic_reported_only_for_its_sources_and_workload(monkeypatch):
+    """The bench attaches the ncu-captured DRAM bytes to its roofline objects
+    only while the kernel sources are the captured ones and the launch is the
+    captured workload; otherwise the field is null."""
+    sha = bench.kernel_sha()
+    monkeypatch.setitem(bench.NCU_TRAFFIC, "src_sha256", sha)
+    monkeypatch.setitem(bench.NCU_TRAFFIC, "fused", 123)
+    assert bench.ncu_traffic("fused") == 123
+    assert bench.ncu_traffic("fused", same_workload=False) is None
+    monkeypatch.setitem(bench.NCU_TRAFFIC, "src_sha256", "0" * 64)
+    assert bench.ncu_traffic("fused") is None

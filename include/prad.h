@@ -296,12 +296,14 @@ int prad_autotune_batch(prad_ctx* ctx, const prad_ensemble* ens, int32_t n_ens,
  * PRAD_ERR_ARG (null arrays, no pid array, n > max_particles). */
 int prad_sort_by_tile(prad_ctx* ctx, const prad_particles* p, int64_t n);
 
-/* Load balance of the last prad_push_emit_batch call: each CTA of its
+/* Load balance of the last prad_push_emit_batch call (a measurement of the
+ * batched form; the paper defines no such quantity): each CTA of its
  * persistent launches accumulates the SM clocks from its start to its exit
  * (summed over the call's launches); *efficiency (host) = mean / max over
  * the CTAs, 1 when every CTA was busy as long as the slowest.  *ctas (host,
- * may be NULL) receives the CTA count.  PRAD_ERR_STATE before the first
- * batched call.  Synchronises. */
+ * may be NULL) receives the CTA count.  PRAD_ERR_ARG for a null context or
+ * efficiency pointer, PRAD_ERR_STATE before the first batched call,
+ * PRAD_ERR_CUDA if the copy fails.  Synchronises. */
 int prad_batch_balance(prad_ctx* ctx, double* efficiency, int32_t* ctas);
 
 /* Copy up to `cap` photon records into `out` (device arrays if

@@ -321,9 +321,11 @@ double orc_Ginv(double r) {
 }
 
 void orc_G_batch(const double* x, double* out, int64_t n) {
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i) out[i] = orc_G(x[i]);
 }
 void orc_Q_batch(const double* x, double* out, int64_t n) {
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i) out[i] = orc_Q(x[i]);
 }
 void orc_Ginv_batch(const double* r, double* out, int64_t n) {
@@ -331,9 +333,11 @@ void orc_Ginv_batch(const double* r, double* out, int64_t n) {
   for (int64_t i = 0; i < n; ++i) out[i] = orc_Ginv(r[i]);
 }
 void orc_F_batch(const double* x, double* out, int64_t n) {
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i) out[i] = orc_F(x[i]);
 }
 void orc_F_exact_batch(const double* x, double* out, int64_t n) {
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i) out[i] = orc_F_exact(x[i]);
 }
 

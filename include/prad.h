@@ -430,10 +430,12 @@ int prad_angular_histogram(prad_ctx* ctx, const double axis[3], const double ref
  * before any stream capture.  All calls share the array and it keeps the
  * last call's contents (each call writes every partial it reads), so calls
  * that overlap on the GPU race: order them on one stream or synchronise.
- * n == 0 writes zeros (emit and rr may then be NULL).
+ * n == 0 writes zeros (emit and rr may then be NULL).  The device address
+ * looked up by the first call stays in use for the life of the process:
+ * calls after a cudaDeviceReset of that device are not supported.
  * Errors: PRAD_ERR_ARG (null pointer, n < 0, n too large), PRAD_ERR_CUDA;
  * prad_ledger_totals_noalloc_error() returns the message of this thread's
- * last failure. */
+ * last call if it failed, and an empty string after a call that succeeded. */
 int prad_ledger_totals_noalloc(const double* emit, const double* rr, int64_t n, double* out,
                                void* stream);
 const char* prad_ledger_totals_noalloc_error(void);

@@ -126,7 +126,10 @@ constexpr int kStaticBlocks = 4096;
 __device__ __align__(256) double g_static_partials[4 * kStaticBlocks];
 
 // Device address of g_static_partials per device, looked up once per device
-// (host code must not pass the array's host-side name to a kernel).
+// (host code must not pass the array's host-side name to a kernel).  The
+// address belongs to the device's primary context at the first call; a
+// cudaDeviceReset later in the process invalidates it (calls after a reset
+// are not supported).
 constexpr int kMaxDevices = 64;
 std::mutex g_static_mu;
 double* g_static_addr[kMaxDevices] = {nullptr};
@@ -144,6 +147,7 @@ extern "C" const char* prad_ledger_totals_noalloc_error(void) { return g_static_
 
 extern "C" int prad_ledger_totals_noalloc(const double* emit, const double* rr, int64_t n,
                                           double* out, void* stream) {
+  g_static_err[0] = '\0';  // the message describes this call's failure only
   if (!out || n < 0 || (n > 0 && (!emit || !rr)))
     return static_fail(PRAD_ERR_ARG, "ledger_totals_noalloc: null pointer or n < 0");
   if (n > kStaticChunk * kStaticBlocks)

@@ -71,3 +71,8 @@ def test_noalloc_rejects_sizes_beyond_the_static_limit():
         prad.prad_ledger_totals_noalloc(a.data_ptr(), a.data_ptr(), (1 << 28) + 1,
                                         out.data_ptr(), None)
     assert ei.value.code == prad.PRAD_ERR_ARG and "268435456" in str(ei.value)
+    # the message describes the last call only: empty after a call that succeeds
+    prad.prad_ledger_totals_noalloc(a.data_ptr(), a.data_ptr(), a.numel(), out.data_ptr(), None)
+    torch.cuda.synchronize()
+    assert prad.load_library().prad_ledger_totals_noalloc_error() == b""
+    assert np.array_equal(out.cpu().numpy(), [0.0, 0.0])

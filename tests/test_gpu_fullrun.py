@@ -1,0 +1,119 @@
+"""Full-length parity of the benchmarked workloads, GPU through the C ABI vs
+the FP64 oracle.
+
+* The counter-propagating CP plane wave (lambda = 0.8 um, 2^20 electrons with
+  gamma = 1000 along -x plus 1% spread, LL kick, 20 periods at 200 steps per
+  period) for a0 = 100, 300 and 500, in the launch shape the benchmark times
+  (400 fused steps per launch, ten launches).  The oracle follows every 256th
+  electron (4096 of them) through all 4000 steps.
+  - each followed electron's momentum within max(1e-5, its float32 envelope)
+    (tests/fp32_envelope.py; the envelope is pinned by
+    test_oracle_fp32_envelope.py: over 4000 steps the oracle's own
+    float32-held runs depart by more than 1e-4);
+  - their photons matched on (pid, step) >= 99.99%;
+  - their emitted-energy and LL totals within 1e-4 (the Fig. 3 comparison
+    of emitted energy with radiation-reaction losses);
+  - GPU vs oracle two-sample KS test of the photon energies, p > 0.01.
+* The constant-B check (10^4 electrons, 1000 steps, FP64, one fused launch)
+  at full size: per particle |du|/|u| <= 1e-12, photons matched, per-particle
+  ledgers <= 1e-10.
+"""
+import numpy as np
+import pytest
+from scipy import stats
+
+import fp32_envelope as FE
+import oracle as O
+from paper_1409_5574_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if torch.cuda.is_available():
+    from paper_1409_5574_gb300 import prad
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    prad.load_library()
+
+
+def _keys(pid, step):
+    return np.asarray(pid).astype(np.int64) * 2 ** 32 + np.asarray(step).astype(np.int64)
+
+
+def _match(gk, rk):
+    common = np.intersect1d(gk, rk)
+    return common.size / max(1, gk.size, rk.size)
+
+
+@pytest.mark.parametrize("a0", [100.0, 300.0, 500.0])
+def test_planewave_full_length_parity(a0):
+    n, nsteps, stride = 1 << 20, 4000, 256
+    wl = W.plane_wave(a0=a0, n=n, periods=20, seed=1)
+    # the FP32 path's inputs exactly (float32 values) on both sides
+    wl.state = {k: v.astype(np.float32).astype(np.float64) for k, v in wl.state.items()}
+    ctx = prad.Context(wl.problem_kwargs(), precision=prad.PRAD_FP32,
+                       photon_capacity=int(0.12 * n * nsteps) + (1 << 20), max_particles=n,
+                       steps_per_launch=400)
+    st = ctx.to_device(wl.state)
+    ctx.push_emit(st, nsteps)
+    torch.cuda.synchronize()
+    _, _, stats_ = ctx.energy_budget()
+    assert stats_["dropped"] == 0 and stats_["status"] == 0 and stats_["nan_frozen"] == 0
+    sel = np.arange(0, n, stride)
+    idx = torch.from_numpy(sel).cuda()
+    gs = {k: st[k][idx].double().cpu().numpy() for k in ("x", "ux", "uy", "uz")}
+    le, ll = ctx.ledger()
+    g_emit, g_ll = le[idx].cpu().numpy(), ll[idx].cpu().numpy()
+    ph = ctx.photons(on_device=True)
+    keep = (ph["pid"] % stride) == 0
+    gp = {k: ph[k][keep].cpu().numpy() for k in ("pid", "step", "eps", "weight")}
+    ctx.close()
+    del st, ph
+
+    sub = wl.subset(sel)
+    pid = sel.astype(np.uint32)
+    prob = O.Problem(**sub.problem_kwargs())
+    ref = sub.copy_state()
+    r = O.run(prob, ref, nsteps, pid=pid, capacity=1 << 22)
+    assert r["stats"]["dropped"] == 0
+
+    env = FE.envelope(prob, sub.copy_state(), nsteps, ref, pid=pid)
+    FE.assert_within(FE.momentum_rel(gs, ref), env)
+    rp = r["photons"]
+    assert rp["pid"].size > 20_000
+    assert _match(_keys(gp["pid"], gp["step"]), _keys(rp["pid"], rp["step"])) >= 0.9999
+    assert g_emit.sum() == pytest.approx(r["ledger"]["emit"].sum(), rel=1e-4)
+    assert g_ll.sum() == pytest.approx(r["ledger"]["ll"].sum(), rel=1e-4)
+    ks = stats.ks_2samp(gp["eps"].astype(np.float64), rp["eps"])
+    assert ks.pvalue > 0.01, ks
+    # photon number (records x multiplicity) and the mean energy per photon
+    assert gp["weight"].astype(np.float64).sum() == pytest.approx(rp["weight"].sum(), rel=1e-4)
+
+
+def test_constant_b_fp64_full_size():
+    """10^4 electrons, gamma ~ U[100, 1000], isotropic, B = 10^4 T, 1000
+    steps in one fused FP64 launch, LL ledger (the paper's constant-field
+    check, Comparison section)."""
+    wl = W.const_b()
+    ctx = prad.Context(wl.problem_kwargs(), precision=prad.PRAD_FP64, photon_capacity=1 << 20,
+                       max_particles=wl.n, steps_per_launch=1000)
+    st = ctx.to_device(wl.state)
+    ctx.push_emit(st, 1000)
+    torch.cuda.synchronize()
+    ph = ctx.photons(on_device=False)
+    le, ll = ctx.ledger()
+    g = {k: v.cpu().numpy() for k, v in st.items()}
+    ctx.close()
+    ref = wl.copy_state()
+    r = O.run(O.Problem(**wl.problem_kwargs()), ref, 1000, capacity=1 << 20)
+    assert FE.momentum_rel(g, ref).max() <= 1e-12
+    rp = r["photons"]
+    assert rp["pid"].size > 40_000
+    assert _match(_keys(ph["pid"].numpy(), ph["step"].numpy()),
+                  _keys(rp["pid"], rp["step"])) >= 0.9999
+    np.testing.assert_allclose(ll.cpu().numpy(), r["ledger"]["ll"], rtol=1e-10, atol=0)
+    np.testing.assert_allclose(le.cpu().numpy(), r["ledger"]["emit"], rtol=1e-10, atol=1e-300)

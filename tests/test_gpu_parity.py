@@ -13,6 +13,7 @@ import math
 import numpy as np
 import pytest
 
+import fp32_envelope as FE
 import oracle as O
 from paper_1409_5574_gb300 import workloads as W
 
@@ -171,6 +172,54 @@ def test_planewave_fp32_parity(a0):
     assert gpu["ll"] == pytest.approx(ref["ledger"]["ll"].sum(), rel=1e-4)
     assert gpu["emitted"] == pytest.approx(ref["ledger"]["emit"].sum(), rel=1e-4)
     assert gpu["stats"]["chi_gt1"] == pytest.approx(ref["stats"]["chi_gt1"], rel=1e-3, abs=2)
+
+
+def _strong_constant_b(n=4096, a0=500.0, seed=2):
+    """Isotropic electrons, gamma ~ U[100, 1000], in B = a0 m omega_L / e with
+    the LL kick (the strongest constant-B ensembles of the batched mix)."""
+    omega = 2 * math.pi * W.C_LIGHT / 0.8e-6
+    rng = np.random.default_rng(seed)
+    gamma = rng.uniform(100.0, 1000.0, n)
+    u = rng.standard_normal((n, 3))
+    u *= (np.sqrt(gamma ** 2 - 1) / np.linalg.norm(u, axis=1))[:, None]
+    return W.Workload(name="strong constant B", omega_ref=omega,
+                      dt=(2 * math.pi / omega) / 200, nsteps=1, rr_mode=W.RR_APPLY,
+                      field_kind=W.FIELD_CONST, B=(0.0, 0.0, a0 * W.M_E * omega / W.Q_E),
+                      state=dict(x=np.zeros(n), y=np.zeros(n), z=np.zeros(n), ux=u[:, 0].copy(),
+                                 uy=u[:, 1].copy(), uz=u[:, 2].copy(), w=np.ones(n)))
+
+
+def _small_yee_case(nx=130, ny=100, n=6000 + 13, seed=3):
+    rng = np.random.default_rng(seed)
+    dxn = 2 * np.pi / 32
+    planes = W.yee_planes(nx, ny, 300.0, dxn, rng)
+    wl = W.yee2d(n_grid=64, slab=32, n_particles=n, seed=seed, with_grid=False)
+    wl.yee = planes
+    wl.state["x"] = rng.uniform(-0.5, nx + 0.5, n) * dxn
+    wl.state["y"] = rng.uniform(-0.5, ny + 0.5, n) * dxn
+    return wl
+
+
+@pytest.mark.parametrize("case", ["yee", "constant_b", "pw100", "pw300", "pw500"])
+def test_one_step_departure_in_float32_units(case):
+    """One FP32 step from identical float32 inputs departs from the oracle by
+    at most FE.FACTOR (= 3) float32 units of |u| on every field kind: the
+    kernel's own rounding per step, the factor the multi-step float32
+    envelope bar allows over the envelope's one unit per step."""
+    if case == "yee":
+        wl = _small_yee_case()
+    elif case == "constant_b":
+        wl = _strong_constant_b()
+    else:
+        wl = W.plane_wave(a0=float(case[2:]), n=4096, seed=3)
+    wl = _f32_inputs(wl)
+    for t0 in (0, 1000):
+        gpu = _run_gpu(wl, 1, prad.PRAD_FP32, t0=t0)
+        ref = wl.copy_state()
+        O.run(O.Problem(**wl.problem_kwargs()), ref, 1, t0=t0, capacity=1 << 16)
+        units = FE.float32_units(gpu["state"], ref)
+        assert units.max() <= FE.FACTOR, (case, t0, units.max())
+        assert np.median(units) <= 1.0
 
 
 def test_substeps_and_split_calls_are_bit_identical():

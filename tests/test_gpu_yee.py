@@ -6,10 +6,18 @@ Small grids that are not multiples of the 32-cell tile, particles everywhere
 tile-sorted shared-memory gather; then the 4096^2 standing-wave workload at
 full size in the sorted launch configuration, checked on a pid-strided
 10^4-particle subset.
+
+Bars: one FP32 step from identical inputs |du|/|u| <= 1e-5 per particle; FP64
+<= 1e-12 per particle; over several FP32 steps every particle within
+max(1e-5, its float32 envelope) (tests/fp32_envelope.py: the oracle's own
+departure when its state is held in float32, pinned by
+test_oracle_fp32_envelope.py); photons matched on (pid, step) >= 99.99%;
+emitted and LL totals within 1e-4 (FP32) / 1e-10 (FP64).
 """
 import numpy as np
 import pytest
 
+import fp32_envelope as FE
 import oracle as O
 from paper_1409_5574_gb300 import workloads as W
 
@@ -81,13 +89,14 @@ def _urel(a, b):
     return np.abs(ua - ub).max(1) / np.linalg.norm(ub, axis=1)
 
 
-def _fp32_multistep_ok(rel):
-    """Multi-step FP32 bound: the float32 state (positions rounded every
-    step) meets steep, noisy fields, and a few low-gamma trajectories
-    diverge chaotically from the FP64 oracle; the bulk stays at the
-    per-step rounding level."""
-    q50, q99 = np.quantile(rel, [0.5, 0.99])
-    assert q50 <= 2e-5 and q99 <= 2e-3 and rel.max() <= 5e-2, (q50, q99, rel.max())
+def _fp32_multistep_ok(wl, nsteps, ref_state, gpu_state, pid=None):
+    """Multi-step FP32 bound: every particle within max(1e-5, its float32
+    envelope), the oracle's own departure from `ref_state` when its state is
+    held in float32 (low-gamma electrons in the steep, noisy standing wave
+    amplify the state's rounding past 1e-5 within a few tens of steps)."""
+    env = FE.envelope(O.Problem(**wl.problem_kwargs()), wl.copy_state(), nsteps, ref_state,
+                      pid=pid)
+    FE.assert_within(_urel(gpu_state, ref_state), env)
 
 
 def _pos_err(a, b, L):
@@ -111,28 +120,28 @@ def test_yee_fp32_one_step_parity():
         assert _urel(g["state"], r["state"]).max() <= 1e-5
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("fp32", 1e-3)])
-def test_yee_plain_gather_parity(precision, tol):
-    """25 steps.  FP32 tolerance: the float32 state (positions ~1e-5 cell)
-    meets field gradients of E0 k dx ~ 60 per cell, so low-gamma electrons
-    accumulate ~3e-6 per step; the median stays at the 1e-6 level."""
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_yee_plain_gather_parity(precision):
+    """25 steps, FP64 per particle <= 1e-12; FP32 per particle within the
+    float32 envelope (low-gamma electrons meet field gradients of E0 k dx ~ 60
+    per cell, so the state's rounding grows past 1e-5 for some of them)."""
     wl = _small_yee()
     p = prad.PRAD_FP64 if precision == "fp64" else prad.PRAD_FP32
     if p == prad.PRAD_FP32:
         wl = _f32_inputs(wl)
     g = _gpu_run(wl, 25, p)
     r = _oracle(wl, 25)
-    rel = _urel(g["state"], r["state"])
     if p == prad.PRAD_FP32:
-        _fp32_multistep_ok(rel)
+        _fp32_multistep_ok(wl, 25, r["state"], g["state"])
     else:
-        assert rel.max() <= tol
+        assert _urel(g["state"], r["state"]).max() <= 1e-12
     Lx = wl.yee[0].shape[1] * wl.dx
     assert _pos_err(g["state"]["x"], r["state"]["x"], Lx).max() < 1e-4
     frac, ng, nr = _photon_match(g["photons"], r["photons"])
-    assert frac >= (0.995 if p == prad.PRAD_FP32 else 0.999) and nr > 500
-    assert g["ll"] == pytest.approx(r["ledger"]["ll"].sum(), rel=1e-4 if p == prad.PRAD_FP32 else 1e-10)
-    assert g["emitted"] == pytest.approx(r["ledger"]["emit"].sum(), rel=2e-3)
+    assert frac >= 0.9999 and nr > 500
+    tot = 1e-4 if p == prad.PRAD_FP32 else 1e-10
+    assert g["ll"] == pytest.approx(r["ledger"]["ll"].sum(), rel=tot)
+    assert g["emitted"] == pytest.approx(r["ledger"]["emit"].sum(), rel=tot)
 
 
 def test_tile_sort_is_a_tile_ordered_permutation():
@@ -157,8 +166,8 @@ def test_tile_sort_is_a_tile_ordered_permutation():
     ctx.close()
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("fp32", 1e-3)])
-def test_yee_tiled_gather_parity(precision, tol):
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_yee_tiled_gather_parity(precision):
     """sort_interval > 0: particles reordered by tile every 6 steps, fields
     gathered from shared-memory tiles (global fallback near tile edges)."""
     wl = _small_yee(nx=160, ny=96, n=20_000 + 5)
@@ -167,14 +176,15 @@ def test_yee_tiled_gather_parity(precision, tol):
         wl = _f32_inputs(wl)
     g = _gpu_run(wl, 25, p, sort_interval=6, with_pid=True)
     r = _oracle(wl, 25)
-    rel = _urel(g["state"], r["state"])
     if p == prad.PRAD_FP32:
-        _fp32_multistep_ok(rel)
+        _fp32_multistep_ok(wl, 25, r["state"], g["state"])
     else:
-        assert rel.max() <= tol
+        assert _urel(g["state"], r["state"]).max() <= 1e-12
     frac, ng, nr = _photon_match(g["photons"], r["photons"])
-    assert frac >= (0.995 if p == prad.PRAD_FP32 else 0.999) and nr > 1000
-    assert g["ll"] == pytest.approx(r["ledger"]["ll"].sum(), rel=1e-4 if p == prad.PRAD_FP32 else 1e-10)
+    assert frac >= 0.9999 and nr > 1000
+    tot = 1e-4 if p == prad.PRAD_FP32 else 1e-10
+    assert g["ll"] == pytest.approx(r["ledger"]["ll"].sum(), rel=tot)
+    assert g["emitted"] == pytest.approx(r["ledger"]["emit"].sum(), rel=tot)
     # ledger entries follow the ids through the sorts
     if p == prad.PRAD_FP64:
         np.testing.assert_allclose(g["led_ll"], r["ledger"]["ll"], rtol=1e-10, atol=1e-30)
@@ -194,12 +204,12 @@ def test_yee_tiled_equals_plain_fp32():
 
 def test_yee_full_size_subset_parity():
     """The 4096^2 standing wave (a0 = 300, 1% noise), 16M electrons in the
-    central 1024^2 cells, sorted every 8 steps (the benchmarked launch shape),
-    40 steps; the oracle follows every 1600th electron."""
+    central 1024^2 cells, sorted every 16 steps (the benchmarked launch
+    shape), 40 steps; the oracle follows every 1600th electron."""
     wl = _f32_inputs(W.yee2d(nsteps=40, seed=1))
     ctx = prad.Context(wl.problem_kwargs(), precision=prad.PRAD_FP32,
-                       photon_capacity=1 << 26, max_particles=wl.n, sort_interval=8,
-                       steps_per_launch=8)
+                       photon_capacity=1 << 26, max_particles=wl.n, sort_interval=16,
+                       steps_per_launch=16)
     st = ctx.to_device(wl.state, with_pid=True)
     sel = np.arange(0, wl.n, 1600)
     sub = wl.subset(sel)
@@ -222,7 +232,7 @@ def test_yee_full_size_subset_parity():
     gstate = {k: st[k][torch.from_numpy(inv[sel]).cuda()].double().cpu().numpy()
               for k in ("x", "y", "ux", "uy", "uz")}
     r = _oracle(sub, 40, pid=sel.astype(np.uint32))
-    _fp32_multistep_ok(_urel(gstate, r["state"]))
+    _fp32_multistep_ok(sub, 40, r["state"], gstate, pid=sel.astype(np.uint32))
     le, ll = ctx.ledger()
     lr = np.abs(ll.cpu().numpy()[sel] / r["ledger"]["ll"] - 1)
     assert np.median(lr) < 1e-4 and np.quantile(lr, 0.99) < 5e-3
@@ -231,5 +241,7 @@ def test_yee_full_size_subset_parity():
     keep = np.isin(ph["pid"].numpy(), sel)
     gp = {k: ph[k].numpy()[keep] for k in ("pid", "step")}
     frac, ng, nr = _photon_match(gp, r["photons"])
-    assert frac >= 0.995 and nr > 1000
+    assert frac >= 0.9999 and nr > 1000
+    e_sub = le.cpu().numpy()[sel].sum()
+    assert e_sub == pytest.approx(r["ledger"]["emit"].sum(), rel=1e-4)
     ctx.close()

@@ -373,7 +373,9 @@ struct FinishSrc {
     const float eps = x * pd.z;
     a.eps[row] = eps;
     const int li = __float_as_int(pd.w);
-    if (li >= 0) atomicAdd(a.led_emit + li, static_cast<double>(w) * static_cast<double>(eps));
+    // the increment rounded to float as in the table sampler's ledger sums,
+    // converted without the FP64 pipe
+    if (li >= 0) atomicAdd(a.led_emit + li, f32_to_f64(w * eps));
   }
 };
 

@@ -84,13 +84,13 @@ struct Acc<float> {
   // FP64 value; a single add (one step per launch) leaves lo == 0 and costs
   // one conversion on the slow FP64 pipe instead of two plus an add
   __device__ __forceinline__ double value() const {
-    double v = static_cast<double>(hi);
-    if (lo != 0.0f) v += static_cast<double>(lo);
+    double v = f32_to_f64(hi);
+    if (lo != 0.0f) v += f32_to_f64(lo);
     return v;
   }
   __device__ __forceinline__ bool nonzero() const { return hi != 0.0f; }
   // after exactly one add, TwoSum leaves lo == 0: one conversion
-  __device__ __forceinline__ double value_one() const { return static_cast<double>(hi); }
+  __device__ __forceinline__ double value_one() const { return f32_to_f64(hi); }
 };
 template <>
 struct Acc<double> {
@@ -482,8 +482,7 @@ __device__ __forceinline__ void flush_stage(ST& st, int fill, const PhotonOut& o
       const float x = __expf(ginv_ln(o.ginv, pd.x));
       const int li = __float_as_int(pd.w);
       if (li >= 0)
-        atomicAdd(o.led_base + li,
-                  static_cast<double>(stage_weight(st, r)) * static_cast<double>(x * pd.z));
+        atomicAdd(o.led_base + li, f32_to_f64(stage_weight(st, r) * (x * pd.z)));
       atomicAdd(o.fallback, 1ull);
     }
   }
@@ -683,6 +682,13 @@ __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const u
   (void)li_abs;
 
   const int nsub = ONE ? 1 : P.nsub;
+  // The learned sampler without control draws two uniforms per step (the
+  // network's r and the emission decision's R), so one Philox block, counter
+  // (pid, step / 2, tag 4, ensemble), serves an even step (words 0, 1) and
+  // the odd step after it (words 2, 3); the table sampler and the control
+  // variants draw one block per step, counter (pid, step, 0, ensemble).
+  constexpr bool kPairDraws = SAMP != PRAD_SAMPLER_TABLE && !CTRL;
+  uint4 pair_blk = make_uint4(0u, 0u, 0u, 0u);
   const int rr_mode = STD ? PRAD_RR_APPLY : P.rr_mode;
   const int heff_form = STD ? PRAD_HEFF_FIELD : P.heff_form;
   const int dims = STD ? (FIELD == PRAD_FIELD_YEE2D ? 2 : 3) : P.dims;
@@ -787,8 +793,17 @@ __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const u
       xn -= P.Lx * flr((xn - P.x0) * (R(1) / P.Lx));
       yn -= P.Ly * flr((yn - P.y0) * (R(1) / P.Ly));
     }
-    const uint4 ctr = make_uint4(pid, step, 0u, P.ensemble);
-    const uint4 rnd = philox10_rk<SAMP == PRAD_SAMPLER_TABLE>(ctr, rk);
+    uint4 rnd;
+    if constexpr (kPairDraws) {
+      // (step & 1) is the same in every lane: no divergence
+      if (s == 0 || (step & 1u) == 0u)
+        pair_blk = philox10_rk(make_uint4(pid, step >> 1, 4u, P.ensemble), rk);
+      // r in word 0 and R in word 2 of rnd, as in the one-block-per-step layout
+      rnd = (step & 1u) ? make_uint4(pair_blk.z, 0u, pair_blk.w, 0u)
+                        : make_uint4(pair_blk.x, 0u, pair_blk.y, 0u);
+    } else {
+      rnd = philox10_rk<SAMP == PRAD_SAMPLER_TABLE>(make_uint4(pid, step, 0u, P.ensemble), rk);
+    }
     const R Rr = unit_uniform<R>(rnd.z);
     if constexpr (SAMP == PRAD_SAMPLER_TABLE) {
       // 8. Monte Carlo emission: proposal x = P^-1(R'), dN of Eq. (13);

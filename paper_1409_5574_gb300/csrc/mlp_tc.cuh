@@ -117,30 +117,22 @@ __device__ __forceinline__ void tc_fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-// tcgen05.ld / wait::ld wrappers (generated: long operand lists)
-__device__ __forceinline__ void tmem_ld_32x32b_x32(uint32_t taddr, uint32_t* v) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+// tcgen05.ld wrappers (generated: long operand lists).  Load and wait in one
+// statement: the outputs are complete when it returns, so no separate wait
+// has to carry them as operands.
+__device__ __forceinline__ void tmem_ld_wait_32x32b_x32(uint32_t taddr, uint32_t* v) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n\t"
+               "tcgen05.wait::ld.sync.aligned;"
                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-               : "r"(taddr));
-}
-
-__device__ __forceinline__ void tmem_ld_32x32b_x1(uint32_t taddr, uint32_t* v) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];"
-               : "=r"(v[0])
-               : "r"(taddr));
-}
-
-__device__ __forceinline__ void tmem_wait_ld_x32(uint32_t* v) {
-  asm volatile("tcgen05.wait::ld.sync.aligned;"
-               : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7]), "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]), "+r"(v[13]), "+r"(v[14]), "+r"(v[15]), "+r"(v[16]), "+r"(v[17]), "+r"(v[18]), "+r"(v[19]), "+r"(v[20]), "+r"(v[21]), "+r"(v[22]), "+r"(v[23]), "+r"(v[24]), "+r"(v[25]), "+r"(v[26]), "+r"(v[27]), "+r"(v[28]), "+r"(v[29]), "+r"(v[30]), "+r"(v[31])
-               :
+               : "r"(taddr)
                : "memory");
 }
 
-__device__ __forceinline__ void tmem_wait_ld_x1(uint32_t* v) {
-  asm volatile("tcgen05.wait::ld.sync.aligned;"
-               : "+r"(v[0])
-               :
+__device__ __forceinline__ void tmem_ld_wait_32x32b_x1(uint32_t taddr, uint32_t* v) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];\n\t"
+               "tcgen05.wait::ld.sync.aligned;"
+               : "=r"(v[0])
+               : "r"(taddr)
                : "memory");
 }
 
@@ -311,8 +303,7 @@ __device__ __forceinline__ void tc_silu_to_a2(uint16_t* a2, int row, uint32_t ta
 #pragma unroll
   for (int half = 0; half < 2; ++half) {
     uint32_t z[32];
-    tmem_ld_32x32b_x32(taddr + 32 * half, z);
-    tmem_wait_ld_x32(z);
+    tmem_ld_wait_32x32b_x32(taddr + 32 * half, z);
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       uint4 q;
@@ -427,8 +418,7 @@ __device__ __forceinline__ bool tc_run(TcSmem& S, Src& src) {
       if (!live || stop) continue;
       tc_wait(S, t, sl);
       uint32_t o[1];
-      tmem_ld_32x32b_x1(lanes + sl * kHid, o);
-      tmem_wait_ld_x1(o);
+      tmem_ld_wait_32x32b_x1(lanes + sl * kHid, o);
       if (!t.bad) src.finish(sl, k0 + sl, kOutScale * (__uint_as_float(o[0]) + S.b3s));
       const long long kn = k0 + sl + kTcSlots;
       const bool next = src.has(kn);

@@ -582,7 +582,17 @@ int push_emit_t(prad_ctx* c, const prad_particles* pp, int64_t n,
     }
     return PRAD_OK;
   }
-  const int block = c->cfg.block_size > 0 ? c->cfg.block_size : 256;
+  // default block: 256 threads, or, when that leaves SMs without a block
+  // (n < 256 x SMs), the smallest multiple of 32 that spreads the particles
+  // over every SM (FP64 on GB300 runs at a small fraction of the FP32 rate
+  // per SM: 10^4 particles take half the time on 105 blocks of 96 threads
+  // as on 40 of 256)
+  int block = c->cfg.block_size > 0 ? c->cfg.block_size : 256;
+  if (c->cfg.block_size <= 0 && n < static_cast<int64_t>(256) * c->num_sms) {
+    const int64_t per_sm = (n + c->num_sms - 1) / c->num_sms;
+    const int64_t b = (per_sm + 31) / 32 * 32;
+    block = static_cast<int>(b < 32 ? 32 : (b > 256 ? 256 : b));
+  }
   const int sub = c->cfg.steps_per_launch > 0 ? c->cfg.steps_per_launch : 1;
   const int sub_eff = sub < nsteps ? sub : nsteps;
   // persistent grid: at most the resident blocks of the kernel variant, so

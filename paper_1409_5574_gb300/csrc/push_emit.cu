@@ -84,13 +84,13 @@ struct Acc<float> {
   // FP64 value; a single add (one step per launch) leaves lo == 0 and costs
   // one conversion on the slow FP64 pipe instead of two plus an add
   __device__ __forceinline__ double value() const {
-    double v = f32_to_f64(hi);
-    if (lo != 0.0f) v += f32_to_f64(lo);
+    double v = static_cast<double>(hi);
+    if (lo != 0.0f) v += static_cast<double>(lo);
     return v;
   }
   __device__ __forceinline__ bool nonzero() const { return hi != 0.0f; }
   // after exactly one add, TwoSum leaves lo == 0: one conversion
-  __device__ __forceinline__ double value_one() const { return f32_to_f64(hi); }
+  __device__ __forceinline__ double value_one() const { return static_cast<double>(hi); }
 };
 template <>
 struct Acc<double> {

@@ -317,15 +317,16 @@ __global__ void k_mlp_reduce_adam(const float* __restrict__ partial, int nblocks
 }
 
 // The finishing kernel on the tcgen05 tensor cores (mlp_tc.cuh): tiles of
-// 128 consecutive records, one per thread, kTcSlots tiles in flight per CTA.
-// A slot's payload (r, gamma, eps_c, ledger index) and weight are loaded one
-// tile of that slot ahead.  A tensor-core wait that runs out stops the block and sets
-// status bit 2.
+// 128 consecutive records, one per thread of a warpgroup, each warpgroup on
+// its own tiles (tile (blockIdx.x * kTcGroups + g) + k * gridDim.x *
+// kTcGroups).  A tile's payload (r, gamma, eps_c, ledger index) and weights
+// are loaded one tile ahead.  A tensor-core wait that runs out stops the
+// warpgroup and sets status bit 2.
 struct FinishSrc {
   const MlpFinishArgs& a;
   unsigned long long first, stride, end;
-  float4 pd0, pd1, nx0, nx1;  // slot payloads: current tile and the next
-  float w0, w1, nw0, nw1;
+  float4 pd, nx;  // payload of the current tile and of the next
+  float w, nw;
   uint32_t fb = 0;
 
   __device__ FinishSrc(const MlpFinishArgs& args, unsigned long long beg)
@@ -333,31 +334,25 @@ struct FinishSrc {
     const unsigned long long cur = a.counters[kCursor];
     const unsigned long long cap = static_cast<unsigned long long>(a.cap);
     end = cur < cap ? cur : cap;
-    first = beg + static_cast<unsigned long long>(blockIdx.x) * kTcRows + threadIdx.x;
-    stride = static_cast<unsigned long long>(gridDim.x) * kTcRows;
-    load(first, nx0, nw0);
-    if (kTcSlots > 1) load(first + stride, nx1, nw1);
+    const unsigned long long tile =
+        static_cast<unsigned long long>(blockIdx.x) * kTcGroups + tc_group();
+    first = beg + tile * kTcRows + tc_row();
+    stride = static_cast<unsigned long long>(gridDim.x) * kTcGroups * kTcRows;
+    load(first, nx, nw);
   }
-  __device__ void load(unsigned long long row, float4& pd, float& w) const {
+  __device__ void load(unsigned long long row, float4& p, float& wt) const {
     // past the end: a harmless payload that books nothing (ledger index -1)
-    pd = row < end ? a.pend[row] : make_float4(0.5f, 1.0f, 0.0f, __int_as_float(-1));
-    w = row < end ? a.weight[row] : 0.0f;
+    p = row < end ? a.pend[row] : make_float4(0.5f, 1.0f, 0.0f, __int_as_float(-1));
+    wt = row < end ? a.weight[row] : 0.0f;
   }
-  __device__ bool has(long long k) const { return first - threadIdx.x + k * stride < end; }
-  __device__ float3 features(int sl, long long k) {
-    const unsigned long long ahead = first + (k + kTcSlots) * stride;
-    float4& pd = sl == 0 ? pd0 : pd1;
-    float4& nx = sl == 0 ? nx0 : nx1;
-    float& w = sl == 0 ? w0 : w1;
-    float& nw = sl == 0 ? nw0 : nw1;
+  __device__ bool has(long long k) const { return first - tc_row() + k * stride < end; }
+  __device__ float3 features(long long k) {
     pd = nx;
     w = nw;
-    load(ahead, nx, nw);
+    load(first + (k + 1) * stride, nx, nw);
     return mlp_features(pd.x, pd.y, pd.z * a.wdt_per_eps);
   }
-  __device__ void finish(int sl, long long k, float o) {
-    const float4 pd = sl == 0 ? pd0 : pd1;
-    const float w = sl == 0 ? w0 : w1;
+  __device__ void finish(long long k, float o) {
     const unsigned long long row = first + k * stride;
     if (row >= end) return;
     float x = __expf(o + mlp_prior(pd.x));
@@ -379,10 +374,12 @@ struct FinishSrc {
   }
 };
 
+// Resident CTAs per SM the finishing kernel is compiled for: shared memory
+// holds four CTAs of two warpgroups (54 KB each), or six of one (34 KB).
 #ifndef PRAD_TC_MINB
-#define PRAD_TC_MINB (kTcSlots == 1 ? 6 : 4)
+#define PRAD_TC_MINB (kTcGroups == 2 ? 4 : 6)
 #endif
-__global__ void __launch_bounds__(kTcRows, PRAD_TC_MINB) k_mlp_finish_tc(const MlpFinishArgs a) {
+__global__ void __launch_bounds__(kTcThreads, PRAD_TC_MINB) k_mlp_finish_tc(const MlpFinishArgs a) {
   extern __shared__ unsigned char tc_raw[];
   TcSmem& S = tc_smem(tc_raw);
   tc_setup(S, a.mlp);
@@ -409,36 +406,35 @@ struct EvalSrc {
   const float* in;
   float* out;
   int64_t n, first, stride;
-  float3 v0, v1, nx0, nx1;
+  float3 v, nx;
 
   __device__ EvalSrc(const float* i, float* o, int64_t count) : in(i), out(o), n(count) {
-    first = static_cast<int64_t>(blockIdx.x) * kTcRows + threadIdx.x;
-    stride = static_cast<int64_t>(gridDim.x) * kTcRows;
-    nx0 = load(first);
-    if (kTcSlots > 1) nx1 = load(first + stride);
+    const int64_t tile = static_cast<int64_t>(blockIdx.x) * kTcGroups + tc_group();
+    first = tile * kTcRows + tc_row();
+    stride = static_cast<int64_t>(gridDim.x) * kTcGroups * kTcRows;
+    nx = load(first);
   }
   __device__ float3 load(int64_t i) const {
     return i < n ? make_float3(in[3 * i], in[3 * i + 1], in[3 * i + 2])
                  : make_float3(0.5f, 1.0f, 1.0f);
   }
-  __device__ bool has(long long k) const { return first - threadIdx.x + k * stride < n; }
-  __device__ float3 features(int sl, long long k) {
-    float3& v = sl == 0 ? v0 : v1;
-    float3& nx = sl == 0 ? nx0 : nx1;
+  __device__ bool has(long long k) const { return first - tc_row() + k * stride < n; }
+  __device__ float3 features(long long k) {
     v = nx;
-    nx = load(first + (k + kTcSlots) * stride);
+    nx = load(first + (k + 1) * stride);
     return mlp_features(v.x, v.y, v.z);
   }
-  __device__ void finish(int sl, long long k, float o) {
+  __device__ void finish(long long k, float o) {
     const int64_t i = first + k * stride;
-    if (i < n) out[i] = o + mlp_prior(sl == 0 ? v0.x : v1.x);
+    if (i < n) out[i] = o + mlp_prior(v.x);
   }
 };
 
-__global__ void __launch_bounds__(kTcRows) k_mlp_eval_tc(MlpDev dev, const float* __restrict__ in,
-                                                         float* __restrict__ out, int64_t n,
-                                                         unsigned long long* status,
-                                                         int withhold) {
+__global__ void __launch_bounds__(kTcThreads) k_mlp_eval_tc(MlpDev dev,
+                                                            const float* __restrict__ in,
+                                                            float* __restrict__ out, int64_t n,
+                                                            unsigned long long* status,
+                                                            int withhold) {
   extern __shared__ unsigned char tc_raw[];
   TcSmem& S = tc_smem(tc_raw);
   tc_setup(S, dev, withhold != 0);
@@ -501,23 +497,23 @@ cudaError_t launch_mlp_eval(const MlpDev& dev, const float* in, float* out, int6
   cudaError_t e = tc_allow_smem(reinterpret_cast<const void*>(k_mlp_eval_tc));
   if (e != cudaSuccess) return e;
   const int64_t tiles = (n + kTcRows - 1) / kTcRows;
-  const int64_t want = (tiles + kTcSlots - 1) / kTcSlots;
+  const int64_t want = (tiles + kTcGroups - 1) / kTcGroups;
   const int grid = static_cast<int>(want < 1024 ? (want > 0 ? want : 1) : 1024);
-  k_mlp_eval_tc<<<grid, kTcRows, kTcSmemBytes, s>>>(dev, in, out, n, status, withhold);
+  k_mlp_eval_tc<<<grid, kTcThreads, kTcSmemBytes, s>>>(dev, in, out, n, status, withhold);
   return cudaGetLastError();
 }
 
 cudaError_t launch_mlp_finish(const MlpFinishArgs& a, int grid, cudaStream_t s) {
   cudaError_t e = tc_allow_smem(reinterpret_cast<const void*>(k_mlp_finish_tc));
   if (e != cudaSuccess) return e;
-  k_mlp_finish_tc<<<grid, kTcRows, kTcSmemBytes, s>>>(a);
+  k_mlp_finish_tc<<<grid, kTcThreads, kTcSmemBytes, s>>>(a);
   return cudaGetLastError();
 }
 
 // Resident CTAs per SM, from the kernel's registers and shared memory and
-// the SM's limits (6 on GB300 with one slot: shared memory); every resident CTA holds
-// kTcCols of the SM's 512 TMEM columns, so the allocations never wait on
-// one another.
+// the SM's limits (4 on GB300 with two warpgroups per CTA: shared memory);
+// every resident CTA holds kTcCols of the SM's 512 TMEM columns, so the
+// allocations never wait on one another.
 int mlp_finish_blocks_per_sm() {
   int dev = 0, smem_sm = 0, smem_rsv = 0, regs_sm = 0, thr_sm = 0;
   cudaFuncAttributes fa;
@@ -535,8 +531,8 @@ int mlp_finish_blocks_per_sm() {
   int nb = smem_sm / per_cta_smem;
   // registers are allocated per warp in units of 256
   const int regs_warp = ((fa.numRegs > 0 ? fa.numRegs : 1) * 32 + 255) / 256 * 256;
-  nb = min(nb, regs_sm / (regs_warp * (kTcRows / 32)));
-  nb = min(nb, thr_sm / kTcRows);
+  nb = min(nb, regs_sm / (regs_warp * (kTcThreads / 32)));
+  nb = min(nb, thr_sm / kTcThreads);
   nb = min(nb, 512 / static_cast<int>(kTcCols));
   return nb > 0 ? nb : 1;
 }

@@ -16,10 +16,9 @@
 // tanh form; halving is exact), the numerics of mlp_device.cuh; features
 // and biases enter as sums of two parts (BF16 or f16 high part + rounded
 // remainder), so z agrees with the FP32 form to ~1e-6, and the BF16 weights
-// are exact in f16.  A CTA keeps kTcSlots tiles in flight (with two, the
-// tensor cores work on one while the threads run the other's SiLU); a
-// slot's three accumulators share its 64 TMEM columns, each read out before
-// the slot's next MMA is issued.
+// are exact in f16.  A CTA runs kTcGroups warpgroups, each on its own tiles;
+// a tile's three accumulators share the group's 64 TMEM columns, each read
+// out before the group's next MMA is issued.
 //
 // Every wait on the tensor cores is bounded.  A wait that runs out marks
 // the thread bad; the block agrees on it at its next barrier and stops.
@@ -153,19 +152,22 @@ __host__ __device__ constexpr uint32_t tc_idesc(bool bf16, int m, int n) {
          (static_cast<uint32_t>(n >> 3) << 17) | (static_cast<uint32_t>(m >> 4) << 24);
 }
 
-// ---- 128-row tiles, two in flight per CTA --------------------------------
-constexpr int kTcRows = 128;          // rows per tile = threads per CTA
-// Tiles in flight per CTA.  Two overlap one tile's MMAs with the other's
-// activations; with SiLU the kernel is bound by the MUFU tanh instead, and
-// one slot, which fits six CTAs per SM (24 warps) instead of four, is
-// faster (1.28 against 1.43 ms for 29M records).
-#ifndef PRAD_TC_SLOTS
-#define PRAD_TC_SLOTS 1
+// ---- 128-row tiles, one warpgroup per tile ----------------------------------
+constexpr int kTcRows = 128;          // rows per tile = threads per warpgroup
+// Warpgroups per CTA.  Each runs its own sequence of tiles (its A tile, its
+// mbarrier, its 64 TMEM columns) and the weight images are shared by the
+// CTA, so two warpgroups take 54 KB of shared memory where two one-warpgroup
+// CTAs take 68 KB: eight tiles in flight per SM instead of six.  (A tile's
+// three MMA rounds, each waited for, set the pace: with the arithmetic taken
+// out the kernel still needs 72% of its time.)
+#ifndef PRAD_TC_GROUPS
+#define PRAD_TC_GROUPS 2
 #endif
-constexpr int kTcSlots = PRAD_TC_SLOTS;  // 1 or 2
-static_assert(kTcSlots == 1 || kTcSlots == 2, "one or two slots");
+constexpr int kTcGroups = PRAD_TC_GROUPS;
+static_assert(kTcGroups == 1 || kTcGroups == 2, "one or two warpgroups");
+constexpr int kTcThreads = kTcRows * kTcGroups;  // threads per CTA
 constexpr int kTcK2 = 80;             // layer-2 K: 64 units, 2 bias columns, zeros
-constexpr uint32_t kTcCols = 64 * kTcSlots;  // TMEM columns held per CTA: 64 per slot
+constexpr uint32_t kTcCols = 64 * kTcGroups;     // TMEM columns per CTA: 64 per warpgroup
 constexpr uint32_t kTcLbo = 128;      // core matrix: 8 rows x 16 B
 constexpr uint32_t kTcSbo1 = 2 * 128;            // K = 16
 constexpr uint32_t kTcSbo2 = (kTcK2 / 8) * 128;  // K = 80
@@ -173,16 +175,16 @@ constexpr uint32_t kTcSbo3 = (kHid / 8) * 128;   // K = 64
 constexpr uint32_t kTcKStep = 2 * 128;           // bytes per K = 16 step
 constexpr long long kTcWaitCycles = 1ll << 31;   // ~1 s at the SM clock
 
-// A slot's A1 tile lives in the first 16 columns of its A2 tile (same
-// canonical layout, SBO of K = 80): layer 1 has read it before the slot's
-// activations overwrite those columns, and the slot's layer 3 has read h2
-// before the next tile's features are written there.
+// A warpgroup's A1 tile lives in the first 16 columns of its A2 tile (same
+// canonical layout, SBO of K = 80): layer 1 has read it before the
+// activations overwrite those columns, and layer 3 has read h2 before the
+// next tile's features are written there.
 struct alignas(128) TcSmem {
-  uint16_t a2[kTcSlots][kTcRows * kTcK2];
+  uint16_t a2[kTcGroups][kTcRows * kTcK2];
   uint16_t b1[kHid * 16];
   uint16_t b2[kHid * kTcK2];
   uint16_t b3[16 * kHid];
-  uint64_t bar[kTcSlots];
+  uint64_t bar[kTcGroups];
   uint32_t tmem;
   float b3s;
   uint32_t withhold;  // self-test: commit no MMA group (every wait runs out)
@@ -220,6 +222,25 @@ __device__ __forceinline__ TcSmem& tc_smem(unsigned char* raw) {
   return *reinterpret_cast<TcSmem*>(p);
 }
 
+// The thread's warpgroup and its row in the group's tiles.
+__device__ __forceinline__ int tc_group() { return static_cast<int>(threadIdx.x) / kTcRows; }
+__device__ __forceinline__ int tc_row() { return static_cast<int>(threadIdx.x) % kTcRows; }
+
+// Barrier of warpgroup g alone (named barrier 1 + g, its 128 threads); true
+// if any of them passes bad.
+__device__ __forceinline__ bool tc_group_sync_or(int g, bool bad) {
+  uint32_t any;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 p, %1, 0;\n\t"
+      "bar.red.or.pred q, %2, %3, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(any)
+      : "r"(bad ? 1u : 0u), "r"(1 + g), "r"(kTcRows)
+      : "memory");
+  return any != 0;
+}
+
 // Block-collective set-up: the weight images, the constant columns of the
 // A tiles, the mbarriers and the TMEM allocation (warp 0).  withhold: the
 // self-test of the bounded waits, in which no MMA completion is signalled.
@@ -252,17 +273,15 @@ __device__ __forceinline__ void tc_setup(TcSmem& S, const MlpDev& d, bool withho
     const int n = e / kHid, k = e - n * kHid;
     S.b3[tc_off(n, k, kTcSbo3)] = tc_f16_bits(n == 0 ? bf16_round(d.params[kOffW3 + k]) : 0.0f);
   }
-#pragma unroll
-  for (int sl = 0; sl < kTcSlots; ++sl) {
-    for (int e = threadIdx.x; e < kTcRows * 16; e += nt) {  // A2 columns 64..79: 1 1 0..
-      const int m = e >> 4, k = kHid + (e & 15);
-      S.a2[sl][tc_off(m, k, kTcSbo2)] = k < kHid + 2 ? static_cast<uint16_t>(0x3C00u) : 0;
-    }
+  for (int e = threadIdx.x; e < kTcGroups * kTcRows * 16; e += nt) {  // A2 cols 64..79: 1 1 0..
+    const int g = e / (kTcRows * 16), r = e - g * kTcRows * 16;
+    const int m = r >> 4, k = kHid + (r & 15);
+    S.a2[g][tc_off(m, k, kTcSbo2)] = k < kHid + 2 ? static_cast<uint16_t>(0x3C00u) : 0;
   }
   if (threadIdx.x == 0) {
     S.b3s = d.params[kOffB3];
     S.withhold = withhold ? 1u : 0u;
-    for (int sl = 0; sl < kTcSlots; ++sl) tc_mbar_init(&S.bar[sl]);
+    for (int g = 0; g < kTcGroups; ++g) tc_mbar_init(&S.bar[g]);
   }
   __syncwarp();
   if (threadIdx.x < 32) tc_tmem_alloc(&S.tmem, kTcCols);
@@ -272,19 +291,19 @@ __device__ __forceinline__ void tc_setup(TcSmem& S, const MlpDev& d, bool withho
   tc_fence_after_sync();
 }
 
-// Barrier that orders this thread's shared-memory writes and TMEM reads
-// before the tensor-core work the next MMA issues; true if any thread of
-// the block is bad.
-__device__ __forceinline__ bool tc_sync_bad(bool bad) {
+// Warpgroup barrier that orders this thread's shared-memory writes and TMEM
+// reads before the tensor-core work the next MMA issues; true if any thread
+// of the group is bad.
+__device__ __forceinline__ bool tc_sync_bad(int g, bool bad) {
   tc_fence_proxy_async();
   tc_fence_before_sync();
-  const bool any = __syncthreads_or(bad) != 0;
+  const bool any = tc_group_sync_or(g, bad);
   tc_fence_after_sync();
   return any;
 }
 
 // Writes this thread's A1 row [f0h f1h f2h f0l f1l f2l 1 1 0 0 0 0 0 0 0 0]
-// into columns 0..15 of its slot's A2 tile.
+// into columns 0..15 of its group's A2 tile.
 __device__ __forceinline__ void tc_put_a1(uint16_t* a2, int row, float3 f) {
   const float h0 = bf16_round(f.x), h1 = bf16_round(f.y), h2 = bf16_round(f.z);
   uint4 q;
@@ -316,134 +335,120 @@ __device__ __forceinline__ void tc_silu_to_a2(uint16_t* a2, int row, uint32_t ta
   }
 }
 
-// MMA groups of one layer for slot sl (one thread), committed to the slot's
-// mbarrier.  Layer 1: D = A1 B1^T (BF16, K = 16, A1 = A2[:, 0..15]); layer
-// 2: D = A2 B2^T (f16, K = 80); layer 3: D[:, 0..15] = A2[:, 0..63] B3^T
-// (f16, K = 64).
-__device__ __forceinline__ void tc_issue(TcSmem& S, int sl, int layer) {
-  const uint32_t d = S.tmem + static_cast<uint32_t>(sl) * kHid;
+// MMA groups of one layer for warpgroup g (one thread), committed to the
+// group's mbarrier.  Layer 1: D = A1 B1^T (BF16, K = 16, A1 = A2[:, 0..15]);
+// layer 2: D = A2 B2^T (f16, K = 80); layer 3: D[:, 0..15] = A2[:, 0..63]
+// B3^T (f16, K = 64).  D: the group's 64 TMEM columns.
+__device__ __forceinline__ void tc_issue(TcSmem& S, int g, int layer) {
+  const uint32_t d = S.tmem + static_cast<uint32_t>(g) * kHid;
   if (layer == 1) {
-    tc_mma_f16(d, tc_desc(S.a2[sl], kTcLbo, kTcSbo2), tc_desc(S.b1, kTcLbo, kTcSbo1),
+    tc_mma_f16(d, tc_desc(S.a2[g], kTcLbo, kTcSbo2), tc_desc(S.b1, kTcLbo, kTcSbo1),
                tc_idesc(true, kTcRows, kHid), 0u);
   } else if (layer == 2) {
-    const uint64_t ad = tc_desc(S.a2[sl], kTcLbo, kTcSbo2), bd = tc_desc(S.b2, kTcLbo, kTcSbo2);
+    const uint64_t ad = tc_desc(S.a2[g], kTcLbo, kTcSbo2), bd = tc_desc(S.b2, kTcLbo, kTcSbo2);
 #pragma unroll
     for (int k = 0; k < kTcK2 / 16; ++k)
       tc_mma_f16(d, ad + k * (kTcKStep >> 4), bd + k * (kTcKStep >> 4),
                  tc_idesc(false, kTcRows, kHid), k > 0 ? 1u : 0u);
   } else {
-    const uint64_t ad = tc_desc(S.a2[sl], kTcLbo, kTcSbo2), bd = tc_desc(S.b3, kTcLbo, kTcSbo3);
+    const uint64_t ad = tc_desc(S.a2[g], kTcLbo, kTcSbo2), bd = tc_desc(S.b3, kTcLbo, kTcSbo3);
 #pragma unroll
     for (int k = 0; k < kHid / 16; ++k)
       tc_mma_f16(d, ad + k * (kTcKStep >> 4), bd + k * (kTcKStep >> 4),
                  tc_idesc(false, kTcRows, 16), k > 0 ? 1u : 0u);
   }
-  if (!S.withhold) tc_commit(&S.bar[sl]);
+  if (!S.withhold) tc_commit(&S.bar[g]);
 }
 
-// Per-thread bookkeeping of the MMA groups in flight on each slot's
+// Per-thread bookkeeping of the MMA group in flight on its warpgroup's
 // mbarrier: the parity of the next phase, and whether a committed group has
 // not been seen complete (with the parity it completes).
-struct TcSlots {
-  uint32_t phase[kTcSlots] = {};
-  uint32_t pend_par[kTcSlots] = {};
-  bool pend[kTcSlots] = {};
-  bool bad = false;  // a wait of this thread ran out
+struct TcState {
+  uint32_t phase = 0;
+  uint32_t pend_par = 0;
+  bool pend = false;
+  bool bad = false;  // a wait of the group ran out
 };
 
-__device__ __forceinline__ void tc_note_issue(TcSlots& t, int sl) {
-  t.pend[sl] = true;
-  t.pend_par[sl] = t.phase[sl];
+__device__ __forceinline__ void tc_note_issue(TcState& t) {
+  t.pend = true;
+  t.pend_par = t.phase;
 }
 
-// Waits for slot sl's last committed MMA group; marks the thread bad if the
-// wait runs out.
-__device__ __forceinline__ void tc_wait(TcSmem& S, TcSlots& t, int sl) {
-  if (tc_mbar_wait(&S.bar[sl], t.phase[sl], kTcWaitCycles)) t.pend[sl] = false;
+// Waits for warpgroup g's last committed MMA group; marks every thread of
+// the group bad if the wait runs out.  Group-collective: its warp 0 polls
+// the mbarrier and its other warps wait at the group barrier, where they
+// take no issue slots.
+__device__ __forceinline__ void tc_wait(TcSmem& S, TcState& t, int g) {
+  bool ok = true;
+  if (tc_row() < 32) ok = tc_mbar_wait(&S.bar[g], t.phase, kTcWaitCycles);
+  if (!tc_group_sync_or(g, !ok)) t.pend = false;
   else t.bad = true;
-  t.phase[sl] ^= 1u;
-  __syncwarp();  // the TMEM loads that follow are warp-collective
+  t.phase ^= 1u;
   tc_fence_after_sync();
 }
 
-// The network over a sequence of 128-row tiles k = 0, 1, 2, ... (one row per
-// thread; tile k in slot k % kTcSlots; with two slots the tensor cores work
-// on one while the threads run the other's SiLU).  Src supplies,
-// block-uniformly, whether tile k exists (has(k)), this thread's features of
-// tile k in slot sl (features(sl, k): called once per tile, in order of k),
-// and takes kOutScale * o of the thread's row (finish(sl, k, o): not called
-// for a tile whose waits ran out).  Block-collective.  Returns true if a
-// tensor-core wait ran out in any thread (the block then stopped early).
+// The network over a sequence of 128-row tiles k = 0, 1, 2, ... of the
+// thread's warpgroup (one row per thread).  Src supplies, uniformly over
+// the group, whether tile k exists (has(k)), this thread's features of tile
+// k (features(k): called once per tile, in order of k), and takes
+// kOutScale * o of the thread's row (finish(k, o): not called for a tile
+// whose waits ran out).  Block-collective (every warpgroup of the CTA runs
+// its own tiles).  Returns true if a tensor-core wait ran out in any thread
+// of the CTA (its warpgroup then stopped early).
 template <class Src>
 __device__ __forceinline__ bool tc_run(TcSmem& S, Src& src) {
-  const int row = threadIdx.x;
-  const uint32_t lanes = S.tmem + (static_cast<uint32_t>(row & ~31) << 16);  // warp's TMEM lanes
-  TcSlots t;
-  long long k0 = 0;  // tile of slot 0; a second slot holds k0 + 1
-  bool live0 = src.has(0), live1 = kTcSlots > 1 && src.has(1);
+  const int g = tc_group(), row = tc_row();
+  // the warp's TMEM lanes (warp w of a warpgroup reads lanes 32w..32w+31),
+  // the group's columns
+  const uint32_t lanes = S.tmem + (static_cast<uint32_t>(row & ~31) << 16) +
+                         static_cast<uint32_t>(g) * kHid;
+  uint16_t* a2 = S.a2[g];
+  TcState t;
+  bool live = src.has(0);
   bool stop = false;
-  if (live0) tc_put_a1(S.a2[0], row, src.features(0, 0));
-  if (live1) tc_put_a1(S.a2[kTcSlots - 1], row, src.features(kTcSlots - 1, 1));
-  tc_sync_bad(false);
-  if (live0) {
-    if (row == 0) tc_issue(S, 0, 1);
-    tc_note_issue(t, 0);
+  if (live) tc_put_a1(a2, row, src.features(0));
+  tc_sync_bad(g, false);
+  if (live) {
+    if (row == 0) tc_issue(S, g, 1);
+    tc_note_issue(t);
   }
-  if (live1) {
-    if (row == 0) tc_issue(S, kTcSlots - 1, 1);
-    tc_note_issue(t, kTcSlots - 1);
-  }
-  while (live0 && !stop) {
-    // layers 2 and 3: SiLU of slot sl's accumulators, then its next layer
+  for (long long k = 0; live && !stop; ++k) {
+    // layers 2 and 3: SiLU of the accumulators, then the next layer
 #pragma unroll
     for (int layer = 2; layer <= 3; ++layer) {
-#pragma unroll
-      for (int sl = 0; sl < kTcSlots; ++sl) {
-        const bool live = sl == 0 ? live0 : live1;
-        if (!live || stop) continue;
-        tc_wait(S, t, sl);
-        tc_silu_to_a2(S.a2[sl], row, lanes + sl * kHid);
-        if (tc_sync_bad(t.bad)) {
-          stop = true;
-          continue;
-        }
-        if (row == 0) tc_issue(S, sl, layer);
-        tc_note_issue(t, sl);
-      }
-    }
-    // outputs, then the slot's next tile
-#pragma unroll
-    for (int sl = 0; sl < kTcSlots; ++sl) {
-      const bool live = sl == 0 ? live0 : live1;
-      if (!live || stop) continue;
-      tc_wait(S, t, sl);
-      uint32_t o[1];
-      tmem_ld_wait_32x32b_x1(lanes + sl * kHid, o);
-      if (!t.bad) src.finish(sl, k0 + sl, kOutScale * (__uint_as_float(o[0]) + S.b3s));
-      const long long kn = k0 + sl + kTcSlots;
-      const bool next = src.has(kn);
-      if (next) tc_put_a1(S.a2[sl], row, src.features(sl, kn));
-      if (tc_sync_bad(t.bad)) {
+      if (stop) continue;
+      tc_wait(S, t, g);
+      tc_silu_to_a2(a2, row, lanes);
+      if (tc_sync_bad(g, t.bad)) {
         stop = true;
         continue;
       }
-      if (next) {
-        if (row == 0) tc_issue(S, sl, 1);
-        tc_note_issue(t, sl);
-      }
-      if (sl == 0) live0 = next;
-      else live1 = next;
+      if (row == 0) tc_issue(S, g, layer);
+      tc_note_issue(t);
     }
-    k0 += kTcSlots;
+    if (stop) break;
+    // output, then the next tile
+    tc_wait(S, t, g);
+    uint32_t o[1];
+    tmem_ld_wait_32x32b_x1(lanes, o);
+    if (!t.bad) src.finish(k, kOutScale * (__uint_as_float(o[0]) + S.b3s));
+    const bool next = src.has(k + 1);
+    if (next) tc_put_a1(a2, row, src.features(k + 1));
+    if (tc_sync_bad(g, t.bad)) {
+      stop = true;
+      break;
+    }
+    if (next) {
+      if (row == 0) tc_issue(S, g, 1);
+      tc_note_issue(t);
+    }
+    live = next;
   }
   // tear-down: agree on a timeout; if there was one, wait (bounded) for
-  // the groups still in flight before the TMEM is released
+  // the group still in flight before the TMEM is released
   const bool any_bad = __syncthreads_or(t.bad) != 0;
-  if (any_bad) {
-#pragma unroll
-    for (int sl = 0; sl < kTcSlots; ++sl)
-      if (t.pend[sl]) tc_mbar_wait(&S.bar[sl], t.pend_par[sl], kTcWaitCycles);
-  }
+  if (any_bad && t.pend) tc_mbar_wait(&S.bar[g], t.pend_par, kTcWaitCycles);
   tc_fence_before_sync();
   __syncthreads();
   tc_fence_after_sync();

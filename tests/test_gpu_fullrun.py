@@ -17,6 +17,10 @@ the FP64 oracle.
 * The constant-B check (10^4 electrons, 1000 steps, FP64, one fused launch)
   at full size: per particle |du|/|u| <= 1e-12, photons matched, per-particle
   ledgers <= 1e-10.
+* The benchmark's own workload (a0 = 500, 2^26 electrons, 400 steps, 100
+  per launch, the buffer drained between launches): the table sampler against
+  the oracle on every 16384th electron (the same bars as above), and the
+  learned sampler against the table sampler on the same run.
 """
 import numpy as np
 import pytest
@@ -117,3 +121,99 @@ def test_constant_b_fp64_full_size():
                   _keys(rp["pid"], rp["step"])) >= 0.9999
     np.testing.assert_allclose(ll.cpu().numpy(), r["ledger"]["ll"], rtol=1e-10, atol=0)
     np.testing.assert_allclose(le.cpu().numpy(), r["ledger"]["emit"], rtol=1e-10, atol=1e-300)
+
+
+def _headline(n=1 << 26, a0=500.0):
+    """The benchmarked workload: CP plane wave, a0 = 500, 2^26 electrons,
+    400 steps (float32 inputs on both sides)."""
+    wl = W.plane_wave(a0=a0, n=n, periods=2, seed=1)
+    wl.state = {k: v.astype(np.float32).astype(np.float64) for k, v in wl.state.items()}
+    return wl
+
+
+def _run_headline(wl, sampler, stride, params=None):
+    """400 steps in the bench's launch shape (100 per launch, the buffer
+    drained after each launch); returns the state and ledgers of every
+    stride-th electron, their photons, the totals and the counters."""
+    n, chunk = wl.n, 100
+    ctx = prad.Context(wl.problem_kwargs(), precision=prad.PRAD_FP32, sampler=sampler,
+                       photon_capacity=int(0.14 * n * chunk) + (1 << 20), max_particles=n,
+                       steps_per_launch=chunk)
+    if params is not None:
+        ctx.mlp_set_weights(params)
+    st = ctx.to_device(wl.state)
+    keep = {k: [] for k in ("pid", "step", "eps", "weight")}
+    tot_w = tot_we = 0.0
+    for c in range(4):
+        ctx.push_emit(st, chunk, t0=chunk * c)
+        ph = ctx.photons(on_device=True)
+        sel = (ph["pid"] % stride) == 0
+        for k in keep:
+            keep[k].append(ph[k][sel].cpu().numpy())
+        w = ph["weight"].double()
+        tot_w += float(w.sum())
+        tot_we += float((w * ph["eps"].double()).sum())
+        assert ph["dropped"] == 0
+        del ph
+        ctx.drain()
+    torch.cuda.synchronize()
+    emitted, ll, stats = ctx.energy_budget()
+    idx = torch.arange(0, n, stride, device="cuda")
+    le, lr = ctx.ledger()
+    out = dict(state={k: st[k][idx].double().cpu().numpy() for k in ("x", "ux", "uy", "uz")},
+               full_state={k: st[k].clone() for k in ("x", "y", "z", "ux", "uy", "uz")},
+               led_emit=le[idx].cpu().numpy(), led_ll=lr[idx].cpu().numpy(),
+               full_ll=lr.clone(),
+               photons={k: np.concatenate(v) for k, v in keep.items()},
+               emitted=emitted, ll=ll, stats=stats, mean_eps=tot_we / tot_w)
+    ctx.close()
+    return out
+
+
+def test_headline_full_size_parity():
+    """The bench's workload at full size and launch shape, table sampler;
+    the oracle follows every 16384th electron (4096) through all 400 steps."""
+    wl, stride = _headline(), 16384
+    g = _run_headline(wl, prad.PRAD_SAMPLER_TABLE, stride)
+    assert g["stats"]["status"] == 0 and g["stats"]["nan_frozen"] == 0
+    sel = np.arange(0, wl.n, stride)
+    sub = wl.subset(sel)
+    pid = sel.astype(np.uint32)
+    prob = O.Problem(**sub.problem_kwargs())
+    ref = sub.copy_state()
+    r = O.run(prob, ref, 400, pid=pid, capacity=1 << 22)
+    env = FE.envelope(prob, sub.copy_state(), 400, ref, pid=pid)
+    FE.assert_within(FE.momentum_rel(g["state"], ref), env)
+    rp, gp = r["photons"], g["photons"]
+    assert rp["pid"].size > 20_000
+    assert _match(_keys(gp["pid"], gp["step"]), _keys(rp["pid"], rp["step"])) >= 0.9999
+    assert g["led_emit"].sum() == pytest.approx(r["ledger"]["emit"].sum(), rel=1e-4)
+    assert g["led_ll"].sum() == pytest.approx(r["ledger"]["ll"].sum(), rel=1e-4)
+    assert stats.ks_2samp(gp["eps"].astype(np.float64), rp["eps"]).pvalue > 0.01
+
+
+def test_headline_full_size_learned_sampler():
+    """The same workload with the learned sampler (trained here): the
+    electrons' trajectories and LL ledgers do not depend on the sampler (no
+    photon recoil; the LL kick acts either way), so they equal the table
+    run's bit for bit; the emitted energy and the mean photon energy agree
+    with the table sampler's within 1% (both estimate the same spectrum;
+    statistical spread at this size ~1e-4), and the network's fallback to
+    the G^-1 table stays rare."""
+    wl = _headline()
+    stride = 16384
+    t = _run_headline(wl, prad.PRAD_SAMPLER_TABLE, stride)
+    trainer = prad.Context(wl.problem_kwargs(), precision=prad.PRAD_FP32, max_particles=16,
+                           photon_capacity=16)
+    trainer.mlp_train(1526, 65536, 3e-3, seed=7)
+    params = trainer.mlp_weights()
+    trainer.close()
+    m = _run_headline(wl, prad.PRAD_SAMPLER_MLP_FALLBACK, stride, params=params)
+    for k in t["full_state"]:
+        assert torch.equal(t["full_state"][k], m["full_state"][k]), k
+    assert torch.equal(t["full_ll"], m["full_ll"])
+    assert m["ll"] == t["ll"]
+    assert m["emitted"] == pytest.approx(t["emitted"], rel=1e-2)
+    assert m["mean_eps"] == pytest.approx(t["mean_eps"], rel=1e-2)
+    assert m["stats"]["status"] == 0
+    assert m["stats"]["mlp_fallback"] < 1e-5 * m["stats"]["records"]

@@ -1,10 +1,10 @@
 // Training and evaluation kernels of the learned inverse-CDF sampler
 // (mlp_device.cuh): sample generation with the device G^-1 table, a fused
-// forward + backward pass per block of 128 samples (m16n8k16 MMAs for the
-// 64 x 64 layer: f16 forward, BF16 gradient products), per-block partial
-// gradients, and a deterministic reduction + Adam update; the evaluators
-// (the learned sampler's finishing kernel and prad_mlp_eval) run the
-// network on the tcgen05 tensor cores (mlp_tc.cuh).
+// forward + backward pass per block of 128 samples on the tcgen05 tensor
+// cores (f16 forward, BF16 gradient products, accumulators in TMEM),
+// per-block partial gradients, and a deterministic reduction + Adam update;
+// the evaluators (the learned sampler's finishing kernel and prad_mlp_eval)
+// run the network on the tcgen05 tensor cores too (mlp_tc.cuh).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -31,24 +31,47 @@ __device__ __forceinline__ uint4 philox10_mlp(uint4 c, uint32_t k0, uint32_t k1)
 
 namespace {
 
-constexpr int kTB = 128;  // samples per block
-constexpr int kTThreads = 256;
-constexpr int kLdT = kTB + 8;  // transposed [unit][sample] rows, bf16
+constexpr int kTB = 128;  // samples per block (one tile: one sample per thread)
+constexpr int kTZ = kHid + 1;  // padded FP32 rows: column sums without bank conflicts
 
-struct TrainSmem {
-  MlpSmem net;
-  __nv_bfloat16 w2t[kHid * kW2Ld];    // W2 transposed [i][j]
-  float x[kTB][4];                    // features
-  float tgt[kTB];                     // target (ln x - prior) / kOutScale
-  float wgt[kTB];                     // loss weight
-  float dout[kTB];                    // dL/do per sample
+// Canonical K-major strides (bytes per 8-row group) of the training tiles:
+// K = 64 (delta2 [s][j], W2^T [i][j]) and K = 128 (delta2^T [j][s], h1^T [i][s]).
+constexpr uint32_t kTrSbo64 = (kHid / 8) * 128;
+constexpr uint32_t kTrSbo128 = (kTB / 8) * 128;
+
+// Shared memory of the training kernel.  The operand tiles are in the
+// canonical K-major layout of the tensor cores (no swizzle, mlp_tc.cuh).
+struct alignas(128) TrainTcSmem {
+  uint16_t a2[kTB * kTcK2];      // [h1 f16 | 1 1 0..] (forward layer 2, A)
+  uint16_t b2[kHid * kTcK2];     // halved W2 | split b2, f16 (forward layer 2, B)
+  uint16_t d2t[kTB * kTB];       // rows j < 64: bf16 delta2^T [j][s] (dW2, A; rows >= 64 zero)
+  uint16_t h1t[kHid * kTB];      // bf16(silu(z1))^T [i][s] (dW2, B)
+  uint16_t d2[kTB * kHid];       // bf16 delta2 [s][j] (delta1, A)
+  uint16_t w2t[kHid * kHid];     // BF16 W2^T [i][j] (delta1, B)
+  float z1[kTB][kTZ];            // z1, then delta1
+  float z2[kTB][kTZ];
+  float4 w1b1[kHid];             // (BF16 W1 row j, b1 j)
+  float w3[kHid];
+  float x[kTB][4];               // features; x[s][3] = 0 valid, -1 padding
+  float tgt[kTB];
+  float wgt[kTB];
+  float dout[kTB];
   float loss[kTB];
-  float z1[kTB][kHid];
-  float z2[kTB][kHid];                // later: delta1
-  __nv_bfloat16 h1t[kHid * kLdT];     // h1 transposed [i][s]
-  __nv_bfloat16 d2[kTB * kW2Ld];      // delta2 [s][j]
-  __nv_bfloat16 d2t[kHid * kLdT];     // delta2 transposed [j][s]
+  float b3;
+  uint32_t tmem;
+  uint32_t bad;
+  uint64_t bar;
 };
+static_assert(offsetof(TrainTcSmem, a2) % 128 == 0 && offsetof(TrainTcSmem, b2) % 128 == 0 &&
+                  offsetof(TrainTcSmem, d2t) % 128 == 0 && offsetof(TrainTcSmem, h1t) % 128 == 0 &&
+                  offsetof(TrainTcSmem, d2) % 128 == 0 && offsetof(TrainTcSmem, w2t) % 128 == 0 &&
+                  offsetof(TrainTcSmem, bar) % 8 == 0,
+              "operand and mbarrier alignment");
+static_assert(tc_off(kTB - 1, kTB - 1, kTrSbo128) < kTB * kTB &&
+                  tc_off(kHid - 1, kTB - 1, kTrSbo128) < kHid * kTB &&
+                  tc_off(kTB - 1, kHid - 1, kTrSbo64) < kTB * kHid &&
+                  tc_off(kHid - 1, kHid - 1, kTrSbo64) < kHid * kHid,
+              "training tiles stay inside their arrays");
 
 // Training samples: r from a Philox uniform (tag 3), gamma log-uniform in
 // [g_lo, g_hi], H log-uniform in [h_lo, h_hi] T, omega_c dt = 1.5 e H / m
@@ -94,196 +117,259 @@ __device__ void make_sample(const SampleSpec& sp, int64_t idx, float* f, float* 
   *wgt = (1.0f + __expf(lnx)) * (1.0f / 1.308f);
 }
 
-// One block: 128 samples, forward + backward; writes the block's partial
-// gradient (kNumParams floats) and partial loss sum.
-__global__ void __launch_bounds__(kTThreads)
-    k_mlp_train_block(MlpDev dev, SampleSpec sp, float* __restrict__ partial,
-                      float* __restrict__ loss_part) {
-  extern __shared__ __align__(16) unsigned char raw[];
-  TrainSmem& S = *reinterpret_cast<TrainSmem*>(raw);
-  mlp_load_smem(S.net, dev);
-  for (int e = threadIdx.x; e < kHid * kHid; e += blockDim.x) {
+// Block-wide wait for the MMA group committed to the block's mbarrier: warp
+// 0 polls (bounded), the block agrees at a barrier; true if it ran out.
+__device__ __forceinline__ bool train_wait(TrainTcSmem& S, uint32_t parity) {
+  bool ok = true;
+  if (threadIdx.x < 32) ok = tc_mbar_wait(&S.bar, parity, kTcWaitCycles);
+  const bool bad = __syncthreads_or(!ok) != 0;
+  tc_fence_after_sync();
+  return bad;
+}
+
+// One block: 128 samples (one per thread), forward and backward on the
+// tcgen05 tensor cores; writes the block's partial gradient (kNumParams
+// floats) and partial loss sum.  The three products:
+//   forward  z2 / 2 = [h1 | 1 1] [W2 / 2 | b2]^T   M 128, N 64, K 80 (f16)
+//   dW2      = delta2^T h1                          M 128 (64 used), N 64, K 128 (BF16)
+//   dh1      = delta2 W2                            M 128, N 64, K 64 (BF16)
+// with accumulators in TMEM (128 columns: the forward result, then dW2 in
+// columns 0..63 and dh1 in 64..127).  Numerics: h1 = f16(silu(z1)) in
+// packed f16 arithmetic forward (as in the evaluator), BF16 copies of
+// delta2, bf16(silu(z1)) and W2 in the gradient products, FP32 elsewhere.
+// A tensor-core wait that runs out zeroes the block's partials and sets
+// status bit 2.
+__global__ void __launch_bounds__(kTB)
+    k_mlp_train_tc(MlpDev dev, SampleSpec sp, float* __restrict__ partial,
+                   float* __restrict__ loss_part, unsigned long long* status) {
+  extern __shared__ unsigned char raw[];
+  TrainTcSmem& S = *reinterpret_cast<TrainTcSmem*>(
+      (reinterpret_cast<uintptr_t>(raw) + 127) & ~static_cast<uintptr_t>(127));
+  const int s = threadIdx.x;
+  // ---- set-up: weight images, constant columns, mbarrier, TMEM
+  for (int e = s; e < kHid * kTcK2; e += kTB) {  // forward B (unit n, k)
+    const int n = e / kTcK2, k = e - n * kTcK2;
+    float v = 0.0f;
+    if (k < kHid) {
+      v = 0.5f * __bfloat162float(dev.w2[n * kHid + k]);
+    } else if (k < kHid + 2) {
+      const float hb = 0.5f * dev.params[kOffB2 + n];
+      const float hi = __half2float(__float2half_rn(hb));
+      v = k == kHid ? hi : hb - hi;
+    }
+    S.b2[tc_off(n, k, kTcSbo2)] = tc_f16_bits(v);
+  }
+  for (int e = s; e < kHid * kHid; e += kTB) {  // W2^T [i][j] = W2[j][i]
     const int j = e / kHid, i = e - j * kHid;
-    S.w2t[i * kW2Ld + j] = dev.w2[e];
+    S.w2t[tc_off(i, j, kTrSbo64)] = *reinterpret_cast<const uint16_t*>(dev.w2 + e);
   }
-  const int64_t base = static_cast<int64_t>(blockIdx.x) * kTB;
-  if (threadIdx.x < kTB) {
-    const int64_t idx = base + threadIdx.x;
-    if (idx < sp.n_valid) {
-      make_sample(sp, idx, S.x[threadIdx.x], &S.tgt[threadIdx.x], &S.wgt[threadIdx.x]);
-    } else {  // padding rows contribute nothing
-      S.x[threadIdx.x][0] = S.x[threadIdx.x][1] = S.x[threadIdx.x][2] = 0.0f;
-      S.x[threadIdx.x][3] = -1.0f;  // marker
-      S.tgt[threadIdx.x] = 0.0f;
-      S.wgt[threadIdx.x] = 0.0f;
-    }
+  for (int e = s; e < kTB * 16; e += kTB) {  // forward A columns 64..79: 1 1 0..
+    const int m = e >> 4, k = kHid + (e & 15);
+    S.a2[tc_off(m, k, kTcSbo2)] = k < kHid + 2 ? static_cast<uint16_t>(0x3C00u) : 0;
+  }
+  for (int e = s; e < (kTB - kHid) * kTB; e += kTB) {  // dW2 A rows 64..127: zero
+    const int m = kHid + e / kTB, k = e % kTB;
+    S.d2t[tc_off(m, k, kTrSbo128)] = 0;
+  }
+  if (s < kHid) {
+    S.w1b1[s] = make_float4(bf16_round(dev.params[kOffW1 + 3 * s]),
+                            bf16_round(dev.params[kOffW1 + 3 * s + 1]),
+                            bf16_round(dev.params[kOffW1 + 3 * s + 2]), dev.params[kOffB1 + s]);
+    S.w3[s] = bf16_round(dev.params[kOffW3 + s]);
+  }
+  if (s == 0) {
+    S.b3 = dev.params[kOffB3];
+    S.bad = 0u;
+    tc_mbar_init(&S.bar);
+  }
+  __syncwarp();
+  if (s < 32) tc_tmem_alloc(&S.tmem, 128);
+  // ---- the block's samples and layer 1 (FP32, BF16 weights)
+  const int64_t idx = static_cast<int64_t>(blockIdx.x) * kTB + s;
+  if (idx < sp.n_valid) {
+    make_sample(sp, idx, S.x[s], &S.tgt[s], &S.wgt[s]);
+  } else {  // padding rows contribute nothing
+    S.x[s][0] = S.x[s][1] = S.x[s][2] = 0.0f;
+    S.x[s][3] = -1.0f;
+    S.tgt[s] = 0.0f;
+    S.wgt[s] = 0.0f;
   }
   __syncthreads();
-  // layer 1 (FP32, BF16 weights): z1 and bf16(silu(z1)) transposed
-  for (int e = threadIdx.x; e < kTB * kHid; e += blockDim.x) {
-    const int s = e / kHid, j = e - s * kHid;
-    const float4 w = S.net.w1b1[j];
-    const float z = fmaf(w.x, S.x[s][0], fmaf(w.y, S.x[s][1], fmaf(w.z, S.x[s][2], w.w)));
-    S.z1[s][j] = z;
-    S.h1t[j * kLdT + s] = __float2bfloat16(silu(z));
-  }
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int g = lane >> 2, t = lane & 3;
-  // layer 2 forward, warp w: samples 16w .. 16w + 15
   {
-    const int s0 = 16 * warp;
-    // h1 = f16(silu(z1)) in packed f16 arithmetic, as in the evaluator
-    uint32_t a[4][4];
+    const float f0 = S.x[s][0], f1 = S.x[s][1], f2 = S.x[s][2];
+#pragma unroll 4
+    for (int c = 0; c < kHid / 8; ++c) {
+      float z[8];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int j = 16 * q + 2 * t;
-      a[q][0] = silu_f16x2(S.z1[s0 + g][j], S.z1[s0 + g][j + 1]);
-      a[q][1] = silu_f16x2(S.z1[s0 + g + 8][j], S.z1[s0 + g + 8][j + 1]);
-      a[q][2] = silu_f16x2(S.z1[s0 + g][j + 8], S.z1[s0 + g][j + 9]);
-      a[q][3] = silu_f16x2(S.z1[s0 + g + 8][j + 8], S.z1[s0 + g + 8][j + 9]);
-    }
-    // the network image holds W2 / 2 and b2 / 2 (exact): z2 = 2 c
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-      const int j0 = 8 * nt + 2 * t;
-      float c[4] = {S.net.b2h[j0], S.net.b2h[j0 + 1], S.net.b2h[j0], S.net.b2h[j0 + 1]};
-      const __half* wrow = S.net.w2h + (8 * nt + g) * kW2Ld + 2 * t;
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-        mma_f16_16816(c, a[q][0], a[q][1], a[q][2], a[q][3],
-                      *reinterpret_cast<const uint32_t*>(wrow + 16 * q),
-                      *reinterpret_cast<const uint32_t*>(wrow + 16 * q + 8));
-      S.z2[s0 + g][j0] = 2.0f * c[0];
-      S.z2[s0 + g][j0 + 1] = 2.0f * c[1];
-      S.z2[s0 + g + 8][j0] = 2.0f * c[2];
-      S.z2[s0 + g + 8][j0 + 1] = 2.0f * c[3];
+      for (int q = 0; q < 8; ++q) {
+        const int j = 8 * c + q;
+        const float4 w = S.w1b1[j];
+        z[q] = fmaf(w.x, f0, fmaf(w.y, f1, fmaf(w.z, f2, w.w)));
+        S.z1[s][j] = z[q];
+        S.h1t[tc_off(j, s, kTrSbo128)] = tc_bf16_bits(silu(z[q]));
+      }
+      uint4 q4;
+      q4.x = silu_f16x2(z[0], z[1]);
+      q4.y = silu_f16x2(z[2], z[3]);
+      q4.z = silu_f16x2(z[4], z[5]);
+      q4.w = silu_f16x2(z[6], z[7]);
+      *reinterpret_cast<uint4*>(&S.a2[tc_off(s, 8 * c, kTcSbo2)]) = q4;
     }
   }
+  tc_fence_proxy_async();
+  tc_fence_before_sync();
   __syncthreads();
-  // output (h2 = f16(silu(z2)) as in the evaluator), loss and dL/do per sample
-  if (threadIdx.x < kTB) {
-    const int s = threadIdx.x;
-    float o = S.net.b3;
+  tc_fence_after_sync();
+  const uint32_t tmem = S.tmem;
+  const uint32_t lanes = tmem + (static_cast<uint32_t>(s & ~31) << 16);
+  // ---- forward layer 2 on the tensor cores
+  if (s == 0) {
+    const uint64_t ad = tc_desc(S.a2, kTcLbo, kTcSbo2), bd = tc_desc(S.b2, kTcLbo, kTcSbo2);
+#pragma unroll
+    for (int k = 0; k < kTcK2 / 16; ++k)
+      tc_mma_f16(tmem, ad + k * (kTcKStep >> 4), bd + k * (kTcKStep >> 4),
+                 tc_idesc(false, kTB, kHid), k > 0 ? 1u : 0u);
+    tc_commit(&S.bar);
+  }
+  uint32_t pend_par = 0u;  // parity of the MMA group last committed
+  bool bad = train_wait(S, 0u);
+  if (!bad) {
+    // z2 = 2 c; output o = W3 h2 + b3 with h2 = f16(silu(z2)); loss, dL/do,
+    // delta2 = dL/do W3 silu'(z2)
+    float o = S.b3;
+    float c2[kHid];
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      uint32_t v[32];
+      tmem_ld_wait_32x32b_x32(lanes + 32 * half, v);
+#pragma unroll
+      for (int q = 0; q < 32; ++q) c2[32 * half + q] = __uint_as_float(v[q]);
+    }
+#pragma unroll
     for (int j = 0; j < kHid; j += 2) {
-      const uint32_t hh = silu_f16x2(S.z2[s][j], S.z2[s][j + 1]);
+      const uint32_t hh = silu_half_f16x2(c2[j], c2[j + 1]);
       const float2 h2 = __half22float2(*reinterpret_cast<const __half2*>(&hh));
-      o = fmaf(S.net.w3[j], h2.x, o);
-      o = fmaf(S.net.w3[j + 1], h2.y, o);
+      o = fmaf(S.w3[j], h2.x, o);
+      o = fmaf(S.w3[j + 1], h2.y, o);
     }
     const bool valid = S.x[s][3] == 0.0f;
     const float diff = o - S.tgt[s];
-    const float wgt = S.wgt[s];
-    S.loss[s] = valid ? wgt * diff * diff : 0.0f;
-    S.dout[s] = valid ? 2.0f * wgt * diff / static_cast<float>(sp.n_total) : 0.0f;
+    const float wg = S.wgt[s];
+    S.loss[s] = valid ? wg * diff * diff : 0.0f;
+    const float dout = valid ? 2.0f * wg * diff / static_cast<float>(sp.n_total) : 0.0f;
+    S.dout[s] = dout;
+#pragma unroll
+    for (int c = 0; c < kHid / 8; ++c) {
+      uint32_t pk[4];
+#pragma unroll
+      for (int q = 0; q < 8; q += 2) {
+        const int j = 8 * c + q;
+        const float za = 2.0f * c2[j], zb = 2.0f * c2[j + 1];
+        S.z2[s][j] = za;
+        S.z2[s][j + 1] = zb;
+        const float da = dout * S.w3[j] * silu_grad(za);
+        const float db = dout * S.w3[j + 1] * silu_grad(zb);
+        pk[q / 2] = pack_bf16x2(da, db);
+        S.d2t[tc_off(j, s, kTrSbo128)] = static_cast<uint16_t>(pk[q / 2] & 0xffffu);
+        S.d2t[tc_off(j + 1, s, kTrSbo128)] = static_cast<uint16_t>(pk[q / 2] >> 16);
+      }
+      *reinterpret_cast<uint4*>(&S.d2[tc_off(s, 8 * c, kTrSbo64)]) =
+          make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    }
   }
+  // ---- backward products on the tensor cores
+  tc_fence_proxy_async();
+  tc_fence_before_sync();
   __syncthreads();
-  // delta2 = dout W3 silu'(z2): BF16 copies for the two tensor-core products
-  for (int e = threadIdx.x; e < kTB * kHid; e += blockDim.x) {
-    const int s = e / kHid, j = e - s * kHid;
-    const __nv_bfloat16 d =
-        __float2bfloat16(S.dout[s] * S.net.w3[j] * silu_grad(S.z2[s][j]));
-    S.d2[s * kW2Ld + j] = d;
-    S.d2t[j * kLdT + s] = d;
+  tc_fence_after_sync();
+  if (!bad && s == 0) {
+    const uint64_t ad = tc_desc(S.d2t, kTcLbo, kTrSbo128), bd = tc_desc(S.h1t, kTcLbo, kTrSbo128);
+#pragma unroll
+    for (int k = 0; k < kTB / 16; ++k)
+      tc_mma_f16(tmem, ad + k * (kTcKStep >> 4), bd + k * (kTcKStep >> 4),
+                 tc_idesc(true, kTB, kHid), k > 0 ? 1u : 0u);
+    const uint64_t ad3 = tc_desc(S.d2, kTcLbo, kTrSbo64), bd3 = tc_desc(S.w2t, kTcLbo, kTrSbo64);
+#pragma unroll
+    for (int k = 0; k < kHid / 16; ++k)
+      tc_mma_f16(tmem + kHid, ad3 + k * (kTcKStep >> 4), bd3 + k * (kTcKStep >> 4),
+                 tc_idesc(true, kTB, kHid), k > 0 ? 1u : 0u);
+    tc_commit(&S.bar);
   }
-  __syncthreads();
+  if (!bad) {
+    pend_par = 1u;
+    bad = train_wait(S, 1u);
+  }
   float* gp = partial + static_cast<size_t>(blockIdx.x) * kNumParams;
-  // per-unit sums: dW3, db2 (FP32 from z2), loss
-  if (threadIdx.x < kHid) {
-    const int j = threadIdx.x;
-    float dw3 = 0.0f, db2 = 0.0f;
-    for (int s = 0; s < kTB; ++s) {
-      dw3 = fmaf(S.dout[s], silu(S.z2[s][j]), dw3);
-      db2 = fmaf(S.dout[s] * S.net.w3[j], silu_grad(S.z2[s][j]), db2);
-    }
-    gp[kOffW3 + j] = dw3;
-    gp[kOffB2 + j] = db2;
-  }
-  if (threadIdx.x == kHid) {
-    float db3 = 0.0f, ls = 0.0f;
-    for (int s = 0; s < kTB; ++s) {
-      db3 += S.dout[s];
-      ls += S.loss[s];
-    }
-    gp[kOffB3] = db3;
-    loss_part[blockIdx.x] = ls;
-  }
-  __syncthreads();  // z2 is overwritten by delta1 below
-  // delta1 = (delta2 W2) * silu'(z1), warp w: samples 16w .. 16w + 15
-  {
-    const int s0 = 16 * warp;
-    uint32_t a[4][4];
+  if (!bad) {
+    // dW2 row j = s (TMEM lanes 0..63: warps 0 and 1)
+    if (s < kHid) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const __nv_bfloat16* r0 = S.d2 + (s0 + g) * kW2Ld + 16 * q + 2 * t;
-      const __nv_bfloat16* r1 = S.d2 + (s0 + g + 8) * kW2Ld + 16 * q + 2 * t;
-      a[q][0] = *reinterpret_cast<const uint32_t*>(r0);
-      a[q][1] = *reinterpret_cast<const uint32_t*>(r1);
-      a[q][2] = *reinterpret_cast<const uint32_t*>(r0 + 8);
-      a[q][3] = *reinterpret_cast<const uint32_t*>(r1 + 8);
-    }
+      for (int half = 0; half < 2; ++half) {
+        uint32_t v[32];
+        tmem_ld_wait_32x32b_x32(lanes + 32 * half, v);
+        // (scalar stores: a block's partials start at a multiple of
+        // kNumParams = 4481 floats, only 4-byte aligned)
 #pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-      float c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-      const __nv_bfloat16* brow = S.w2t + (8 * nt + g) * kW2Ld + 2 * t;
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-        mma_bf16_16816(c, a[q][0], a[q][1], a[q][2], a[q][3],
-                       *reinterpret_cast<const uint32_t*>(brow + 16 * q),
-                       *reinterpret_cast<const uint32_t*>(brow + 16 * q + 8));
-      const int i0 = 8 * nt + 2 * t;
-      S.z2[s0 + g][i0] = c[0] * silu_grad(S.z1[s0 + g][i0]);
-      S.z2[s0 + g][i0 + 1] = c[1] * silu_grad(S.z1[s0 + g][i0 + 1]);
-      S.z2[s0 + g + 8][i0] = c[2] * silu_grad(S.z1[s0 + g + 8][i0]);
-      S.z2[s0 + g + 8][i0 + 1] = c[3] * silu_grad(S.z1[s0 + g + 8][i0 + 1]);
-    }
-  }
-  // dW2 = delta2^T h1 over the block's 128 samples: output [j][i];
-  // warp w: rows j in 16 (w % 4) .., columns i in 32 (w / 4) .. (4 tiles)
-  {
-    const int mt = warp & 3, nb = (warp >> 2) * 4;
-    float c[4][4] = {};
-#pragma unroll
-    for (int kt = 0; kt < kTB / 16; ++kt) {
-      const __nv_bfloat16* ar0 = S.d2t + (16 * mt + g) * kLdT + 16 * kt + 2 * t;
-      const __nv_bfloat16* ar1 = S.d2t + (16 * mt + g + 8) * kLdT + 16 * kt + 2 * t;
-      const uint32_t a0 = *reinterpret_cast<const uint32_t*>(ar0);
-      const uint32_t a1 = *reinterpret_cast<const uint32_t*>(ar1);
-      const uint32_t a2 = *reinterpret_cast<const uint32_t*>(ar0 + 8);
-      const uint32_t a3 = *reinterpret_cast<const uint32_t*>(ar1 + 8);
-#pragma unroll
-      for (int n = 0; n < 4; ++n) {
-        const __nv_bfloat16* br = S.h1t + (8 * (nb + n) + g) * kLdT + 16 * kt + 2 * t;
-        mma_bf16_16816(c[n], a0, a1, a2, a3, *reinterpret_cast<const uint32_t*>(br),
-                       *reinterpret_cast<const uint32_t*>(br + 8));
+        for (int q = 0; q < 32; ++q) gp[kOffW2 + s * kHid + 32 * half + q] = __uint_as_float(v[q]);
       }
     }
+    // delta1 = dh1 silu'(z1), in place of z1
 #pragma unroll
-    for (int n = 0; n < 4; ++n) {
-      const int j = 16 * mt + g, i = 8 * (nb + n) + 2 * t;
-      gp[kOffW2 + j * kHid + i] = c[n][0];
-      gp[kOffW2 + j * kHid + i + 1] = c[n][1];
-      gp[kOffW2 + (j + 8) * kHid + i] = c[n][2];
-      gp[kOffW2 + (j + 8) * kHid + i + 1] = c[n][3];
+    for (int half = 0; half < 2; ++half) {
+      uint32_t v[32];
+      tmem_ld_wait_32x32b_x32(lanes + kHid + 32 * half, v);
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        const int i = 32 * half + q;
+        S.z1[s][i] = __uint_as_float(v[q]) * silu_grad(S.z1[s][i]);
+      }
     }
   }
+  tc_fence_before_sync();
   __syncthreads();
-  // dW1, db1 from delta1 (held in z2)
-  if (threadIdx.x < kHid) {
-    const int j = threadIdx.x;
-    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, b = 0.0f;
-    for (int s = 0; s < kTB; ++s) {
-      const float d = S.z2[s][j];
-      a0 = fmaf(d, S.x[s][0], a0);
-      a1 = fmaf(d, S.x[s][1], a1);
-      a2 = fmaf(d, S.x[s][2], a2);
-      b += d;
+  if (bad) {
+    // tensor-core wait ran out: this block contributes nothing
+    for (int p = s; p < kNumParams; p += kTB) gp[p] = 0.0f;
+    if (s == 0) {
+      loss_part[blockIdx.x] = 0.0f;
+      atomicOr(status, 4ull);
     }
-    gp[kOffW1 + 3 * j] = a0;
-    gp[kOffW1 + 3 * j + 1] = a1;
-    gp[kOffW1 + 3 * j + 2] = a2;
-    gp[kOffB1 + j] = b;
+  } else {
+    // per-unit sums over the block's samples (FP32)
+    if (s < kHid) {
+      const int j = s;
+      float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, b1 = 0.0f, dw3 = 0.0f, db2 = 0.0f;
+      for (int r = 0; r < kTB; ++r) {
+        const float d = S.z1[r][j];
+        a0 = fmaf(d, S.x[r][0], a0);
+        a1 = fmaf(d, S.x[r][1], a1);
+        a2 = fmaf(d, S.x[r][2], a2);
+        b1 += d;
+        dw3 = fmaf(S.dout[r], silu(S.z2[r][j]), dw3);
+        db2 = fmaf(S.dout[r] * S.w3[j], silu_grad(S.z2[r][j]), db2);
+      }
+      gp[kOffW1 + 3 * j] = a0;
+      gp[kOffW1 + 3 * j + 1] = a1;
+      gp[kOffW1 + 3 * j + 2] = a2;
+      gp[kOffB1 + j] = b1;
+      gp[kOffW3 + j] = dw3;
+      gp[kOffB2 + j] = db2;
+    }
+    if (s == kHid) {
+      float db3 = 0.0f, ls = 0.0f;
+      for (int r = 0; r < kTB; ++r) {
+        db3 += S.dout[r];
+        ls += S.loss[r];
+      }
+      gp[kOffB3] = db3;
+      loss_part[blockIdx.x] = ls;
+    }
   }
+  // tear-down: after a timeout, wait (bounded) for the MMAs in flight
+  if (bad && threadIdx.x < 32) tc_mbar_wait(&S.bar, pend_par, kTcWaitCycles);
+  __syncthreads();
+  tc_fence_after_sync();
+  if (s < 32) tc_tmem_dealloc(tmem, 128);
 }
 
 // Sum the block partials in a fixed order; optionally Adam-update the FP32
@@ -451,24 +537,25 @@ __global__ void k_ginv_eval(const float* __restrict__ tab, const float* __restri
 
 }  // namespace
 
-size_t mlp_train_smem_bytes() { return sizeof(TrainSmem); }
+size_t mlp_train_smem_bytes() { return sizeof(TrainTcSmem) + 128; }
 
 cudaError_t launch_mlp_train_block(const MlpDev& dev, uint32_t key0, uint32_t key1,
                                    uint64_t first, int64_t n_valid, int64_t n_total,
                                    const float4* explicit_samples, const float* ginv,
                                    float lng_lo, float lng_span, float lnh_lo,
                                    float lnh_span, float wdt_per_H_g2, float* partial,
-                                   float* loss_part, int nblocks, cudaStream_t s) {
+                                   float* loss_part, int nblocks, unsigned long long* status,
+                                   cudaStream_t s) {
   SampleSpec sp;
   sp.key0 = key0; sp.key1 = key1; sp.first = first;
   sp.lng_lo = lng_lo; sp.lng_span = lng_span; sp.lnh_lo = lnh_lo; sp.lnh_span = lnh_span;
   sp.wdt_per_H_g2 = wdt_per_H_g2; sp.ginv = ginv; sp.explicit_samples = explicit_samples;
   sp.n_total = n_total; sp.n_valid = n_valid;
-  const int bytes = static_cast<int>(sizeof(TrainSmem));
-  cudaError_t e = cudaFuncSetAttribute(k_mlp_train_block,
+  const int bytes = static_cast<int>(mlp_train_smem_bytes());
+  cudaError_t e = cudaFuncSetAttribute(k_mlp_train_tc,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e != cudaSuccess) return e;
-  k_mlp_train_block<<<nblocks, kTThreads, bytes, s>>>(dev, sp, partial, loss_part);
+  k_mlp_train_tc<<<nblocks, kTB, bytes, s>>>(dev, sp, partial, loss_part, status);
   return cudaGetLastError();
 }
 

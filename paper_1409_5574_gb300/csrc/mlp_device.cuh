@@ -53,24 +53,6 @@ constexpr float kOutScale = 1.0f;
 constexpr float kRMin = 1.0e-7f;
 constexpr float kRMax = 1.0f - 1.0e-7f;
 
-// Shared-memory image of the network used by the training kernel.
-constexpr int kW2Ld = kHid + 8;  // padded row (bank-conflict free B loads)
-struct MlpSmem {
-  float4 w1b1[kHid];                       // (W1 row j, b1 j)
-  float b2[kHid];
-  float w3[kHid];
-  float b3;
-  float pad[3];
-  // layer 2 in f16, halved (exact): W2 / 2 row-major [j][i] and b2 / 2, so
-  // the accumulators hold z2 / 2, the argument of SiLU's tanh form
-  __half w2h[kHid * kW2Ld];
-  float b2h[kHid];
-};
-
-static_assert(sizeof(MlpSmem) % 16 == 0 && offsetof(MlpSmem, w2h) % 16 == 0 &&
-                  offsetof(MlpSmem, b2h) % 8 == 0,
-              "16-byte alignment of the network image");
-
 // Device copy of the network: FP32 master parameters and the BF16 W2.
 struct MlpDev {
   const float* params;                 // kNumParams FP32
@@ -84,23 +66,6 @@ __device__ __forceinline__ float bf16_round(float v) {
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<const uint32_t*>(&v);
-}
-
-// Weights enter as BF16 (rounded from the FP32 master), biases as FP32.
-__device__ __forceinline__ void mlp_load_smem(MlpSmem& s, const MlpDev& d) {
-  for (int j = threadIdx.x; j < kHid; j += blockDim.x) {
-    s.w1b1[j] = make_float4(bf16_round(d.params[kOffW1 + 3 * j]),
-                            bf16_round(d.params[kOffW1 + 3 * j + 1]),
-                            bf16_round(d.params[kOffW1 + 3 * j + 2]), d.params[kOffB1 + j]);
-    s.b2[j] = d.params[kOffB2 + j];
-    s.w3[j] = bf16_round(d.params[kOffW3 + j]);
-  }
-  if (threadIdx.x == 0) s.b3 = d.params[kOffB3];
-  for (int e = threadIdx.x; e < kHid * kHid; e += blockDim.x) {
-    const int j = e / kHid, i = e - j * kHid;
-    s.w2h[j * kW2Ld + i] = __float2half_rn(0.5f * __bfloat162float(d.w2[e]));
-  }
-  for (int j = threadIdx.x; j < kHid; j += blockDim.x) s.b2h[j] = 0.5f * d.params[kOffB2 + j];
 }
 
 // SiLU from half arguments: h = hz + hz tanh(hz) with hz = z / 2 given
@@ -140,33 +105,6 @@ __device__ __forceinline__ float silu_grad(float z) {
   asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(0.5f * z));
   const float s = 0.5f * (1.0f + t);
   return s + z * s * (1.0f - s);
-}
-
-// D = A(16x16, row) * B(16x8, col) + C, BF16 inputs, FP32 accumulate.
-// Fragment ownership (g = lane / 4, t = lane % 4):
-//   a0: A[g][2t..2t+1]   a1: A[g+8][2t..]   a2: A[g][2t+8..]   a3: A[g+8][2t+8..]
-//   b0: B[2t..2t+1][g]   b1: B[2t+8..2t+9][g]
-//   c0,c1: C[g][2t..2t+1]   c2,c3: C[g+8][2t..2t+1]
-__device__ __forceinline__ void mma_bf16_16816(float c[4], uint32_t a0, uint32_t a1,
-                                               uint32_t a2, uint32_t a3, uint32_t b0,
-                                               uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
-      "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
-// D = A(16x16, row) * B(16x8, col) + C, f16 inputs, FP32 accumulate (the
-// fragment layout of mma_bf16_16816).
-__device__ __forceinline__ void mma_f16_16816(float c[4], uint32_t a0, uint32_t a1,
-                                              uint32_t a2, uint32_t a3, uint32_t b0,
-                                              uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 "
-      "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
 // -ln(1 - r) for r in (0, 1): below r = 1/64 the series r (1 + r/2 + r^2/3 +

@@ -1357,7 +1357,8 @@ int prad_mlp_train(prad_ctx* c, int64_t steps, int32_t batch, float lr, uint64_t
     CK(c, launch_mlp_train_block(dev, static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32),
                                  static_cast<uint64_t>(s) * batch, batch, batch, nullptr,
                                  c->d_ginv, lng_lo, lng_span, lnh_lo, lnh_span, wdt,
-                                 c->d_mlp_partial, c->d_mlp_loss_part, nblocks, c->stream));
+                                 c->d_mlp_partial, c->d_mlp_loss_part, nblocks,
+                                 c->d_cnt + kStatus, c->stream));
     c->mlp_t += 1;
     const double lr_s = lr * 0.5 * (1.0 + std::cos(kPi * static_cast<double>(s) / steps));
     const float b1t = static_cast<float>(std::pow(0.9, static_cast<double>(c->mlp_t)));
@@ -1368,10 +1369,13 @@ int prad_mlp_train(prad_ctx* c, int64_t steps, int32_t batch, float lr, uint64_t
                                  1.0f / static_cast<float>(batch), c->stream));
   }
   float loss = 0.0f;
+  unsigned long long st = 0;
   CK(c, cudaMemcpyAsync(&loss, c->d_mlp_loss, sizeof(float), cudaMemcpyDeviceToHost,
                         c->stream));
+  CK(c, cudaMemcpyAsync(&st, c->d_cnt + kStatus, sizeof(st), cudaMemcpyDeviceToHost, c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
   if (final_loss) *final_loss = loss;
+  if (st & 4ull) return fail(c, PRAD_ERR_TIMEOUT, "mlp_train: a tensor-core wait timed out");
   return PRAD_OK;
 }
 
@@ -1386,16 +1390,20 @@ int prad_mlp_grad(prad_ctx* c, const float* samples, int64_t n, float* grad, dou
   mlp_ranges(c, &lng_lo, &lng_span, &lnh_lo, &lnh_span, &wdt);
   CK(c, launch_mlp_train_block(mlp_dev(c), 0, 0, 0, n, n, reinterpret_cast<const float4*>(samples),
                                c->d_ginv, lng_lo, lng_span, lnh_lo, lnh_span, wdt,
-                               c->d_mlp_partial, c->d_mlp_loss_part, nblocks, c->stream));
+                               c->d_mlp_partial, c->d_mlp_loss_part, nblocks,
+                               c->d_cnt + kStatus, c->stream));
   CK(c, launch_mlp_reduce_adam(c->d_mlp_partial, nblocks, c->d_mlp_loss_part, c->d_mlp_grad,
                                c->d_mlp, c->d_mlp_m, c->d_mlp_v, c->d_mlp_w2, 0.0f, 0.0f, 0.0f,
                                0, c->d_mlp_loss, 1.0f / static_cast<float>(n), c->stream));
   float l = 0.0f;
+  unsigned long long st = 0;
   CK(c, cudaMemcpyAsync(grad, c->d_mlp_grad, sizeof(float) * kNumParams,
                         cudaMemcpyDeviceToHost, c->stream));
   CK(c, cudaMemcpyAsync(&l, c->d_mlp_loss, sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaMemcpyAsync(&st, c->d_cnt + kStatus, sizeof(st), cudaMemcpyDeviceToHost, c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
   if (loss) *loss = l;
+  if (st & 4ull) return fail(c, PRAD_ERR_TIMEOUT, "mlp_grad: a tensor-core wait timed out");
   return PRAD_OK;
 }
 

@@ -207,7 +207,8 @@ cudaError_t launch_mlp_train_block(const MlpDev& dev, uint32_t key0, uint32_t ke
                                    const float4* explicit_samples, const float* ginv,
                                    float lng_lo, float lng_span, float lnh_lo,
                                    float lnh_span, float wdt_per_H_g2, float* partial,
-                                   float* loss_part, int nblocks, cudaStream_t s);
+                                   float* loss_part, int nblocks, unsigned long long* status,
+                                   cudaStream_t s);
 cudaError_t launch_mlp_reduce_adam(const float* partial, int nblocks, const float* loss_part,
                                    float* grad, float* params, float* m, float* v,
                                    __nv_bfloat16* w2, float lr, float b1t, float b2t,

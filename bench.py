@@ -669,7 +669,7 @@ def run_prad(args):
                            "buffers (40 B per record), timed on the host"}
     del hb
 
-    # The metric's other arm: the learned sampler (trained here on 10^8
+    # The metric's other arm: the learned sampler (trained here on 2 x 10^8
     # device-generated samples) on the same workload and launch shape.
     mlp = None
     grid = None
@@ -677,7 +677,7 @@ def run_prad(args):
     if not args.no_mlp:
         torch.cuda.synchronize()
         t_tr = time.perf_counter()
-        train_loss = ctx.mlp_train(1526, 65536, 3e-3, seed=7)
+        train_loss = ctx.mlp_train(3052, 65536, 3e-3, seed=7)
         torch.cuda.synchronize()
         t_tr = time.perf_counter() - t_tr
         params = ctx.mlp_weights()
@@ -724,7 +724,7 @@ def run_prad(args):
                "ms_per_step": 1e3 * tm / args.steps,
                "photon_records_per_step": mrec / args.steps, "dropped": mdrop,
                "train_seconds": t_tr,
-               "train_samples": 1526 * 65536, "train_loss": train_loss,
+               "train_samples": 3052 * 65536, "train_loss": train_loss,
                "mlp_fallback": mst["mlp_fallback"], "sampler": "MLP_FALLBACK (direct scheme)"}
         ctx_m.close()
     else:

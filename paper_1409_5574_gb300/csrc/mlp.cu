@@ -39,39 +39,67 @@ constexpr int kTZ = kHid + 1;  // padded FP32 rows: column sums without bank con
 constexpr uint32_t kTrSbo64 = (kHid / 8) * 128;
 constexpr uint32_t kTrSbo128 = (kTB / 8) * 128;
 
-// Shared memory of the training kernel.  The operand tiles are in the
-// canonical K-major layout of the tensor cores (no swizzle, mlp_tc.cuh).
+// Shared memory of the training kernel (~104 KB: two CTAs per SM).  The
+// operand tiles are in the canonical K-major layout of the tensor cores (no
+// swizzle, mlp_tc.cuh).  The forward operands are dead once the forward MMA
+// has completed, and the backward operands take their place.  The dW2 product
+// reads its A operand as 128 rows from d2t: rows 64..127 are h1t's bytes
+// (d2t is followed by h1t), and give TMEM lanes 64..127 that are never read.
 struct alignas(128) TrainTcSmem {
-  uint16_t a2[kTB * kTcK2];      // [h1 f16 | 1 1 0..] (forward layer 2, A)
-  uint16_t b2[kHid * kTcK2];     // halved W2 | split b2, f16 (forward layer 2, B)
-  uint16_t d2t[kTB * kTB];       // rows j < 64: bf16 delta2^T [j][s] (dW2, A; rows >= 64 zero)
-  uint16_t h1t[kHid * kTB];      // bf16(silu(z1))^T [i][s] (dW2, B)
-  uint16_t d2[kTB * kHid];       // bf16 delta2 [s][j] (delta1, A)
-  uint16_t w2t[kHid * kHid];     // BF16 W2^T [i][j] (delta1, B)
-  float z1[kTB][kTZ];            // z1, then delta1
-  float z2[kTB][kTZ];
-  float4 w1b1[kHid];             // (BF16 W1 row j, b1 j)
+  union {
+    struct {
+      uint16_t a2[kTB * kTcK2];    // [h1 f16 | 1 1 0..] (forward layer 2, A)
+      uint16_t b2[kHid * kTcK2];   // halved W2 | split b2, f16 (forward layer 2, B)
+    } fwd;
+    struct {
+      uint16_t d2[kTB * kHid];     // bf16 delta2 [s][j] (delta1, A)
+      uint16_t w2t[kHid * kHid];   // BF16 W2^T [i][j] (delta1, B)
+    } bwd;
+  } u;
+  uint16_t d2t[kHid * kTB];        // bf16 delta2^T [j][s] (dW2, A rows 0..63)
+  uint16_t h1t[kHid * kTB];        // bf16(silu(z1))^T [i][s] (dW2, B)
+  float z1[kTB][kTZ];              // z1, then delta1
+  float wsum[kTB / 32][2 * kHid];  // per-warp sums of dL/dW3 and dL/db2
+  float4 w1b1[kHid];               // (BF16 W1 row j, b1 j)
   float w3[kHid];
-  float x[kTB][4];               // features; x[s][3] = 0 valid, -1 padding
+  float x[kTB][4];                 // features; x[s][3] = 0 valid, -1 padding
   float tgt[kTB];
   float wgt[kTB];
-  float dout[kTB];
   float loss[kTB];
+  float dout[kTB];
   float b3;
   uint32_t tmem;
-  uint32_t bad;
   uint64_t bar;
 };
-static_assert(offsetof(TrainTcSmem, a2) % 128 == 0 && offsetof(TrainTcSmem, b2) % 128 == 0 &&
-                  offsetof(TrainTcSmem, d2t) % 128 == 0 && offsetof(TrainTcSmem, h1t) % 128 == 0 &&
-                  offsetof(TrainTcSmem, d2) % 128 == 0 && offsetof(TrainTcSmem, w2t) % 128 == 0 &&
+static_assert(offsetof(TrainTcSmem, u.fwd.b2) % 128 == 0 &&
+                  offsetof(TrainTcSmem, u.bwd.w2t) % 128 == 0 &&
+                  offsetof(TrainTcSmem, d2t) % 128 == 0 &&
+                  offsetof(TrainTcSmem, h1t) == offsetof(TrainTcSmem, d2t) + kHid * kTB * 2 &&
                   offsetof(TrainTcSmem, bar) % 8 == 0,
-              "operand and mbarrier alignment");
-static_assert(tc_off(kTB - 1, kTB - 1, kTrSbo128) < kTB * kTB &&
+              "operand and mbarrier alignment; h1t directly after d2t");
+static_assert(tc_off(kTB - 1, kTB - 1, kTrSbo128) < 2 * kHid * kTB &&
                   tc_off(kHid - 1, kTB - 1, kTrSbo128) < kHid * kTB &&
                   tc_off(kTB - 1, kHid - 1, kTrSbo64) < kTB * kHid &&
                   tc_off(kHid - 1, kHid - 1, kTrSbo64) < kHid * kHid,
-              "training tiles stay inside their arrays");
+              "training tiles stay inside their arrays (dW2's A: d2t and h1t)");
+
+// Warp sums of 64 per-lane values v[0..63] (recursive halving: each round a
+// lane keeps one half of its range and adds its partner's copy of it); lane l
+// ends with the sums of entries 2l and 2l + 1 in v[0] and v[1].
+__device__ __forceinline__ void warp_sum64(float (&v)[kHid], int lane) {
+#pragma unroll
+  for (int r = 0; r < 5; ++r) {
+    const int half = 32 >> r;           // entries kept after this round
+    const int bit = 16 >> r;            // partner lane distance
+    const bool upper = (lane & bit) != 0;
+#pragma unroll
+    for (int k = 0; k < half; ++k) {
+      const float keep = upper ? v[k + half] : v[k];
+      const float send = upper ? v[k] : v[k + half];
+      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, bit);
+    }
+  }
+}
 
 // Training samples: r from a Philox uniform (tag 3), gamma log-uniform in
 // [g_lo, g_hi], H log-uniform in [h_lo, h_hi] T, omega_c dt = 1.5 e H / m
@@ -139,14 +167,14 @@ __device__ __forceinline__ bool train_wait(TrainTcSmem& S, uint32_t parity) {
 // delta2, bf16(silu(z1)) and W2 in the gradient products, FP32 elsewhere.
 // A tensor-core wait that runs out zeroes the block's partials and sets
 // status bit 2.
-__global__ void __launch_bounds__(kTB)
+__global__ void __launch_bounds__(kTB, 2)
     k_mlp_train_tc(MlpDev dev, SampleSpec sp, float* __restrict__ partial,
                    float* __restrict__ loss_part, unsigned long long* status) {
   extern __shared__ unsigned char raw[];
   TrainTcSmem& S = *reinterpret_cast<TrainTcSmem*>(
       (reinterpret_cast<uintptr_t>(raw) + 127) & ~static_cast<uintptr_t>(127));
-  const int s = threadIdx.x;
-  // ---- set-up: weight images, constant columns, mbarrier, TMEM
+  const int s = threadIdx.x, lane = s & 31, warp = s >> 5;
+  // ---- set-up: the forward weight image, constant columns, mbarrier, TMEM
   for (int e = s; e < kHid * kTcK2; e += kTB) {  // forward B (unit n, k)
     const int n = e / kTcK2, k = e - n * kTcK2;
     float v = 0.0f;
@@ -157,19 +185,11 @@ __global__ void __launch_bounds__(kTB)
       const float hi = __half2float(__float2half_rn(hb));
       v = k == kHid ? hi : hb - hi;
     }
-    S.b2[tc_off(n, k, kTcSbo2)] = tc_f16_bits(v);
-  }
-  for (int e = s; e < kHid * kHid; e += kTB) {  // W2^T [i][j] = W2[j][i]
-    const int j = e / kHid, i = e - j * kHid;
-    S.w2t[tc_off(i, j, kTrSbo64)] = *reinterpret_cast<const uint16_t*>(dev.w2 + e);
+    S.u.fwd.b2[tc_off(n, k, kTcSbo2)] = tc_f16_bits(v);
   }
   for (int e = s; e < kTB * 16; e += kTB) {  // forward A columns 64..79: 1 1 0..
     const int m = e >> 4, k = kHid + (e & 15);
-    S.a2[tc_off(m, k, kTcSbo2)] = k < kHid + 2 ? static_cast<uint16_t>(0x3C00u) : 0;
-  }
-  for (int e = s; e < (kTB - kHid) * kTB; e += kTB) {  // dW2 A rows 64..127: zero
-    const int m = kHid + e / kTB, k = e % kTB;
-    S.d2t[tc_off(m, k, kTrSbo128)] = 0;
+    S.u.fwd.a2[tc_off(m, k, kTcSbo2)] = k < kHid + 2 ? static_cast<uint16_t>(0x3C00u) : 0;
   }
   if (s < kHid) {
     S.w1b1[s] = make_float4(bf16_round(dev.params[kOffW1 + 3 * s]),
@@ -179,7 +199,6 @@ __global__ void __launch_bounds__(kTB)
   }
   if (s == 0) {
     S.b3 = dev.params[kOffB3];
-    S.bad = 0u;
     tc_mbar_init(&S.bar);
   }
   __syncwarp();
@@ -213,7 +232,7 @@ __global__ void __launch_bounds__(kTB)
       q4.y = silu_f16x2(z[2], z[3]);
       q4.z = silu_f16x2(z[4], z[5]);
       q4.w = silu_f16x2(z[6], z[7]);
-      *reinterpret_cast<uint4*>(&S.a2[tc_off(s, 8 * c, kTcSbo2)]) = q4;
+      *reinterpret_cast<uint4*>(&S.u.fwd.a2[tc_off(s, 8 * c, kTcSbo2)]) = q4;
     }
   }
   tc_fence_proxy_async();
@@ -224,7 +243,8 @@ __global__ void __launch_bounds__(kTB)
   const uint32_t lanes = tmem + (static_cast<uint32_t>(s & ~31) << 16);
   // ---- forward layer 2 on the tensor cores
   if (s == 0) {
-    const uint64_t ad = tc_desc(S.a2, kTcLbo, kTcSbo2), bd = tc_desc(S.b2, kTcLbo, kTcSbo2);
+    const uint64_t ad = tc_desc(S.u.fwd.a2, kTcLbo, kTcSbo2);
+    const uint64_t bd = tc_desc(S.u.fwd.b2, kTcLbo, kTcSbo2);
 #pragma unroll
     for (int k = 0; k < kTcK2 / 16; ++k)
       tc_mma_f16(tmem, ad + k * (kTcKStep >> 4), bd + k * (kTcKStep >> 4),
@@ -234,9 +254,14 @@ __global__ void __launch_bounds__(kTB)
   uint32_t pend_par = 0u;  // parity of the MMA group last committed
   bool bad = train_wait(S, 0u);
   if (!bad) {
+    // the forward operands are dead: W2^T for the delta1 product takes
+    // their place
+    for (int e = s; e < kHid * kHid; e += kTB) {  // W2^T [i][j] = W2[j][i]
+      const int j = e / kHid, i = e - j * kHid;
+      S.u.bwd.w2t[tc_off(i, j, kTrSbo64)] = *reinterpret_cast<const uint16_t*>(dev.w2 + e);
+    }
     // z2 = 2 c; output o = W3 h2 + b3 with h2 = f16(silu(z2)); loss, dL/do,
     // delta2 = dL/do W3 silu'(z2)
-    float o = S.b3;
     float c2[kHid];
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
@@ -245,6 +270,7 @@ __global__ void __launch_bounds__(kTB)
 #pragma unroll
       for (int q = 0; q < 32; ++q) c2[32 * half + q] = __uint_as_float(v[q]);
     }
+    float o = S.b3;
 #pragma unroll
     for (int j = 0; j < kHid; j += 2) {
       const uint32_t hh = silu_half_f16x2(c2[j], c2[j + 1]);
@@ -258,22 +284,34 @@ __global__ void __launch_bounds__(kTB)
     S.loss[s] = valid ? wg * diff * diff : 0.0f;
     const float dout = valid ? 2.0f * wg * diff / static_cast<float>(sp.n_total) : 0.0f;
     S.dout[s] = dout;
+    // dL/dW3_j = sum_s dout silu(z2), dL/db2_j = sum_s dout W3_j silu'(z2):
+    // per-warp sums in FP32, then over the warps
+    {
+      float v[kHid];
+#pragma unroll
+      for (int j = 0; j < kHid; ++j) v[j] = dout * silu(2.0f * c2[j]);
+      warp_sum64(v, lane);
+      S.wsum[warp][2 * lane] = v[0];
+      S.wsum[warp][2 * lane + 1] = v[1];
+#pragma unroll
+      for (int j = 0; j < kHid; ++j) v[j] = dout * S.w3[j] * silu_grad(2.0f * c2[j]);
+      warp_sum64(v, lane);
+      S.wsum[warp][kHid + 2 * lane] = v[0];
+      S.wsum[warp][kHid + 2 * lane + 1] = v[1];
+    }
 #pragma unroll
     for (int c = 0; c < kHid / 8; ++c) {
       uint32_t pk[4];
 #pragma unroll
       for (int q = 0; q < 8; q += 2) {
         const int j = 8 * c + q;
-        const float za = 2.0f * c2[j], zb = 2.0f * c2[j + 1];
-        S.z2[s][j] = za;
-        S.z2[s][j + 1] = zb;
-        const float da = dout * S.w3[j] * silu_grad(za);
-        const float db = dout * S.w3[j + 1] * silu_grad(zb);
+        const float da = dout * S.w3[j] * silu_grad(2.0f * c2[j]);
+        const float db = dout * S.w3[j + 1] * silu_grad(2.0f * c2[j + 1]);
         pk[q / 2] = pack_bf16x2(da, db);
         S.d2t[tc_off(j, s, kTrSbo128)] = static_cast<uint16_t>(pk[q / 2] & 0xffffu);
         S.d2t[tc_off(j + 1, s, kTrSbo128)] = static_cast<uint16_t>(pk[q / 2] >> 16);
       }
-      *reinterpret_cast<uint4*>(&S.d2[tc_off(s, 8 * c, kTrSbo64)]) =
+      *reinterpret_cast<uint4*>(&S.u.bwd.d2[tc_off(s, 8 * c, kTrSbo64)]) =
           make_uint4(pk[0], pk[1], pk[2], pk[3]);
     }
   }
@@ -288,7 +326,8 @@ __global__ void __launch_bounds__(kTB)
     for (int k = 0; k < kTB / 16; ++k)
       tc_mma_f16(tmem, ad + k * (kTcKStep >> 4), bd + k * (kTcKStep >> 4),
                  tc_idesc(true, kTB, kHid), k > 0 ? 1u : 0u);
-    const uint64_t ad3 = tc_desc(S.d2, kTcLbo, kTrSbo64), bd3 = tc_desc(S.w2t, kTcLbo, kTrSbo64);
+    const uint64_t ad3 = tc_desc(S.u.bwd.d2, kTcLbo, kTrSbo64);
+    const uint64_t bd3 = tc_desc(S.u.bwd.w2t, kTcLbo, kTrSbo64);
 #pragma unroll
     for (int k = 0; k < kHid / 16; ++k)
       tc_mma_f16(tmem + kHid, ad3 + k * (kTcKStep >> 4), bd3 + k * (kTcKStep >> 4),
@@ -338,20 +377,24 @@ __global__ void __launch_bounds__(kTB)
     // per-unit sums over the block's samples (FP32)
     if (s < kHid) {
       const int j = s;
-      float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, b1 = 0.0f, dw3 = 0.0f, db2 = 0.0f;
+      float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, b1 = 0.0f;
       for (int r = 0; r < kTB; ++r) {
         const float d = S.z1[r][j];
         a0 = fmaf(d, S.x[r][0], a0);
         a1 = fmaf(d, S.x[r][1], a1);
         a2 = fmaf(d, S.x[r][2], a2);
         b1 += d;
-        dw3 = fmaf(S.dout[r], silu(S.z2[r][j]), dw3);
-        db2 = fmaf(S.dout[r] * S.w3[j], silu_grad(S.z2[r][j]), db2);
       }
       gp[kOffW1 + 3 * j] = a0;
       gp[kOffW1 + 3 * j + 1] = a1;
       gp[kOffW1 + 3 * j + 2] = a2;
       gp[kOffB1 + j] = b1;
+      float dw3 = 0.0f, db2 = 0.0f;
+#pragma unroll
+      for (int w = 0; w < kTB / 32; ++w) {
+        dw3 += S.wsum[w][j];
+        db2 += S.wsum[w][kHid + j];
+      }
       gp[kOffW3 + j] = dw3;
       gp[kOffB2 + j] = db2;
     }

@@ -98,11 +98,11 @@ def test_batch_equals_individual_launches():
 
 @pytest.fixture(scope="module")
 def trained_params():
-    """The learned sampler trained on 10^8 device-generated samples."""
+    """The learned sampler trained on 2 x 10^8 device-generated samples."""
     wl = W.plane_wave(a0=300.0, n=16)
     ctx = prad.Context(wl.problem_kwargs(), precision=prad.PRAD_FP32,
                        photon_capacity=1 << 10, max_particles=16)
-    ctx.mlp_train(1526, 65536, 3e-3, seed=7)
+    ctx.mlp_train(3052, 65536, 3e-3, seed=7)
     p = ctx.mlp_weights()
     ctx.close()
     return p

@@ -205,7 +205,7 @@ def test_headline_full_size_learned_sampler():
     t = _run_headline(wl, prad.PRAD_SAMPLER_TABLE, stride)
     trainer = prad.Context(wl.problem_kwargs(), precision=prad.PRAD_FP32, max_particles=16,
                            photon_capacity=16)
-    trainer.mlp_train(1526, 65536, 3e-3, seed=7)
+    trainer.mlp_train(3052, 65536, 3e-3, seed=7)
     params = trainer.mlp_weights()
     trainer.close()
     m = _run_headline(wl, prad.PRAD_SAMPLER_MLP_FALLBACK, stride, params=params)

@@ -4,8 +4,8 @@
 * the tensor-core tile evaluator against the FP64 numpy net (same weights),
   and its bounded waits: a withheld MMA completion is reported, not hung on;
 * the training kernels' gradient against the FP64 numpy backward;
-* training on 10^8 device-generated samples reaches a spectral error
-  sup_r |G(g(r)) - r| <= 1% (G from the oracle) from ~100% untrained, for
+* training on 2 x 10^8 device-generated samples reaches a spectral error
+  sup_r |G(g(r)) - r| <= 0.5% (G from the oracle) from ~100% untrained, for
   gamma and omega_c dt inside and outside the trained range;
 * the direct-scheme emission with the trained net reproduces the number
   spectrum (KS vs the oracle's G) and the synchrotron power in a constant B.
@@ -117,10 +117,10 @@ def test_training_gradient_matches_fp64_backward():
 
 @pytest.fixture(scope="module")
 def trained():
-    """Train once on 10^8 device-generated samples (1526 x 65536)."""
+    """Train once on 2 x 10^8 device-generated samples (3052 x 65536)."""
     ctx = _ctx()
     before = _spectral_error(ctx, 1000.0, 1e3, n=100_000)
-    loss = ctx.mlp_train(1526, 65536, 3e-3, seed=7)
+    loss = ctx.mlp_train(3052, 65536, 3e-3, seed=7)
     params = ctx.mlp_weights()
     ctx.close()
     return params, before, loss
@@ -128,13 +128,13 @@ def trained():
 
 @pytest.mark.parametrize("gamma,wdt", [(1000.0, 1e3), (10.0, 0.1), (1e4, 1e8),
                                        (1e5, 1e12), (3.0, 1e-4)])
-def test_trained_spectral_error_below_one_percent(trained, gamma, wdt):
+def test_trained_spectral_error_below_half_percent(trained, gamma, wdt):
     params, before, loss = trained
     ctx = _ctx()
     ctx.mlp_set_weights(params)
     err = _spectral_error(ctx, gamma, wdt)
     assert before > 0.05          # what training gains: from a useless sampler
-    assert err <= 0.01, (gamma, wdt, err, loss)
+    assert err <= 0.005, (gamma, wdt, err, loss)
     # mean photon energy E[x] = int_0^1 G^-1(r) dr = (8 pi/9 sqrt3)/(5 pi/3)
     n = 200_000
     r = (np.arange(n) + 0.5) / n

@@ -622,10 +622,26 @@ struct PState {
   bool act;
 };
 
-template <typename R, bool LL = false>
+// LL: 0 state and id only; 1 with the ledger entries (one-step launches);
+// 2 the same for a dense launch (implicit ids pid0 + i, every particle inside
+// the ledger, n >= 1; checked on the host): loads at a valid index for
+// every lane, i or, for an inactive lane, 0 (its values are never stored),
+// instead of zeroed registers and a branch, and ledger entry i directly.
+template <typename R, int LL = 0>
 __device__ __forceinline__ void load_state(const StepParams<R>& P, int64_t i, bool act,
                                            PState<R>& s) {
   s.act = act;
+  if constexpr (LL == 2) {
+    const int64_t k = act ? i : 0;
+    s.x = P.x[k]; s.y = P.y[k];
+    s.z = P.z ? P.z[k] : R(0);
+    s.ux = P.ux[k]; s.uy = P.uy[k]; s.uz = P.uz[k];
+    s.w = P.w[k];
+    s.pid = P.pid0 + static_cast<uint32_t>(i);
+    s.ll_old = P.rr_mode >= PRAD_RR_LEDGER ? P.led_ll[k] : 0.0;
+    s.emit_old = P.led_emit[k];
+    return;
+  }
   s.x = s.y = s.z = s.ux = s.uy = s.uz = s.w = R(0);
   s.pid = 0;
   s.ll_old = s.emit_old = 0.0;
@@ -653,14 +669,15 @@ __device__ __forceinline__ void load_state(const StepParams<R>& P, int64_t i, bo
 // increment instead, both entries prefetched with the state: there an
 // atomic per particle per launch would keep L2's atomic units busy, and the
 // photon cursor's atomic waits behind them.
-// ONE: the launch is known to advance exactly one step (P.nsub == 1).
+// ONE: the launch is known to advance exactly one step (P.nsub == 1); 2: a
+// dense one (implicit ids, every particle inside the ledger: entry i).
 // CTRL: super-photon control or diagnostics are enabled (the plain method
 // compiles without their per-step work).
 // rk: the Philox round keys, in the kernel's parameter space.
 // STD: the standard configuration (LL kick applied, field form of H_eff,
 // three dimensions, two for the Yee grid) fixed at compile time, so the step
 // tests no mode.
-template <typename R, int FIELD, int SAMP, bool ONE = false, bool CTRL = false,
+template <typename R, int FIELD, int SAMP, int ONE = 0, bool CTRL = false,
           bool STD = false, class G, class ST>
 __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const uint32_t (&rk)[20],
                                                  const G& gat,
@@ -881,6 +898,11 @@ __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const u
     P.x[i] = x; P.y[i] = y;
     if (P.z) P.z[i] = z;
     P.ux[i] = ux; P.uy[i] = uy; P.uz[i] = uz;
+    if constexpr (ONE == 2) {
+      if (rr_mode >= PRAD_RR_LEDGER) P.led_ll[i] = st.ll_old + ll.value_one();
+      if (le.nonzero()) P.led_emit[i] = st.emit_old + le.value_one();
+      return;
+    }
     const int64_t li = static_cast<int64_t>(pid - P.pid0);
     if (li < P.led_n) {
       if (rr_mode >= PRAD_RR_LEDGER) {
@@ -980,7 +1002,9 @@ int occupancy_of(K kernel, int block, size_t dyn) {
 #ifndef PRAD_PF_MINB
 #define PRAD_PF_MINB 4
 #endif
-template <typename R, int FIELD, int SAMP, bool PF, bool CTRL, bool STD = false>
+// PF: 0 no prefetch (multi-step launches); 1 one step per launch, the next
+// particle prefetched; 2 the same for a dense launch (see dense_launch).
+template <typename R, int FIELD, int SAMP, int PF, bool CTRL, bool STD = false>
 __global__ void __launch_bounds__(256, (PF ? PRAD_PF_MINB : MinBlocks<R, FIELD, SAMP>::value))
     k_push_emit(const StepParams<R> P) {
   using Stage = PhotonStageT<SAMP != PRAD_SAMPLER_TABLE || !CTRL>;
@@ -997,22 +1021,22 @@ __global__ void __launch_bounds__(256, (PF ? PRAD_PF_MINB : MinBlocks<R, FIELD, 
     // pipeline issues the loads of the thread's next particle before the
     // current one is advanced, so DRAM latency overlaps compute
     PState<R> nxt;
-    load_state<R, true>(P, first + threadIdx.x, first + threadIdx.x < P.n, nxt);
+    load_state<R, PF>(P, first + threadIdx.x, first + threadIdx.x < P.n, nxt);
     for (int64_t base = first; base < P.n; base += stride) {
       const int64_t i = base + threadIdx.x;
       const PState<R> cur = nxt;
       const int64_t j = i + stride;
-      load_state<R, true>(P, j, j < P.n, nxt);
-      advance_particle<R, FIELD, SAMP, true, CTRL, STD>(P, P.rkey, gat, i, cur, stage, fill, pout,
-                                                        cnt);
+      load_state<R, PF>(P, j, j < P.n, nxt);
+      advance_particle<R, FIELD, SAMP, PF, CTRL, STD>(P, P.rkey, gat, i, cur, stage, fill, pout,
+                                                      cnt);
     }
   } else {
     for (int64_t base = first; base < P.n; base += stride) {
       const int64_t i = base + threadIdx.x;
       PState<R> cur;
       load_state(P, i, i < P.n, cur);
-      advance_particle<R, FIELD, SAMP, false, CTRL, STD>(P, P.rkey, gat, i, cur, stage, fill, pout,
-                                                         cnt);
+      advance_particle<R, FIELD, SAMP, 0, CTRL, STD>(P, P.rkey, gat, i, cur, stage, fill, pout,
+                                                     cnt);
     }
   }
   if (fill > 0) flush_stage<SAMP != PRAD_SAMPLER_TABLE>(stage, fill, pout);
@@ -1086,7 +1110,7 @@ __global__ void __launch_bounds__(256, PRAD_BATCH_MINB)
         const int64_t i = base + threadIdx.x;
         PState<float> st;
         load_state(Ps, i, i < last, st);
-        advance_particle<float, PRAD_FIELD_CONST, SAMP, false, CTRL, STD>(Ps, bp.rkey, gat, i, st,
+        advance_particle<float, PRAD_FIELD_CONST, SAMP, 0, CTRL, STD>(Ps, bp.rkey, gat, i, st,
                                                                           stage, fill, pout, cnt);
       }
     } else {
@@ -1095,7 +1119,7 @@ __global__ void __launch_bounds__(256, PRAD_BATCH_MINB)
         const int64_t i = base + threadIdx.x;
         PState<float> st;
         load_state(Ps, i, i < last, st);
-        advance_particle<float, PRAD_FIELD_PLANE_WAVE, SAMP, false, CTRL, STD>(
+        advance_particle<float, PRAD_FIELD_PLANE_WAVE, SAMP, 0, CTRL, STD>(
             Ps, bp.rkey, gat, i, st, stage, fill, pout, cnt);
       }
     }
@@ -1197,7 +1221,7 @@ __global__ void __launch_bounds__(256, 3) k_push_emit_tiled(const StepParams<R> 
     const int64_t i = base + threadIdx.x;
     PState<R> st;
     load_state(P, i, i < wk.z, st);
-    advance_particle<R, PRAD_FIELD_YEE2D, PRAD_SAMPLER_TABLE, false, CTRL, STD>(
+    advance_particle<R, PRAD_FIELD_YEE2D, PRAD_SAMPLER_TABLE, 0, CTRL, STD>(
         P, P.rkey, gat, i, st, stage, fill, pout, cnt);
   }
   if (fill > 0) flush_stage(stage, fill, pout);
@@ -1236,7 +1260,7 @@ cudaError_t launch_push_emit_tiled(const StepParams<R>& p, int max_work, int blo
   return launch_tiled_v<R, false, false>(p, max_work, block, s);
 }
 
-template <typename R, int FIELD, int SAMP, bool PF, bool CTRL>
+template <typename R, int FIELD, int SAMP, int PF, bool CTRL>
 void launch_k(const StepParams<R>& p, int grid, int block, cudaStream_t s) {
   if constexpr (kHasStd<R, FIELD, CTRL>) {
     if (std_config(p, FIELD == PRAD_FIELD_YEE2D ? 2 : 3)) {
@@ -1247,11 +1271,20 @@ void launch_k(const StepParams<R>& p, int grid, int block, cudaStream_t s) {
   k_push_emit<R, FIELD, SAMP, PF, CTRL, false><<<grid, block, 0, s>>>(p);
 }
 
-template <typename R, int FIELD, int SAMP, bool PF, bool CTRL>
+template <typename R, int FIELD, int SAMP, int PF, bool CTRL>
 int occupancy_k(int block, bool std_cfg) {
   if constexpr (kHasStd<R, FIELD, CTRL>)
     if (std_cfg) return occupancy_of(k_push_emit<R, FIELD, SAMP, PF, CTRL, true>, block, 0);
   return occupancy_of(k_push_emit<R, FIELD, SAMP, PF, CTRL, false>, block, 0);
+}
+
+// A one-step launch is dense when ids are implicit (pid0 + i) and every
+// particle has a ledger entry: its kernel indexes the ledgers by i and loads
+// without per-particle range checks.
+template <typename R>
+bool dense_launch(const StepParams<R>& p) {
+  return p.pid == nullptr && p.n >= 1 && p.led_n >= p.n && p.led_emit != nullptr &&
+         (p.rr_mode < PRAD_RR_LEDGER || p.led_ll != nullptr);
 }
 
 template <typename R, int FIELD, bool CTRL>
@@ -1262,16 +1295,22 @@ cudaError_t launch_field_c(const StepParams<R>& p, int sampler, int grid, int bl
     // launch); for long fused launches it only costs registers
     bool pf = false;
     if constexpr (sizeof(R) == 4) pf = p.nsub == 1;
-    if constexpr (sizeof(R) == 4)
-      if (pf) launch_k<R, FIELD, PRAD_SAMPLER_TABLE, true, CTRL>(p, grid, block, s);
-    if (!pf) launch_k<R, FIELD, PRAD_SAMPLER_TABLE, false, CTRL>(p, grid, block, s);
+    if constexpr (sizeof(R) == 4) {
+      if (pf) {
+        if (dense_launch(p))
+          launch_k<R, FIELD, PRAD_SAMPLER_TABLE, 2, CTRL>(p, grid, block, s);
+        else
+          launch_k<R, FIELD, PRAD_SAMPLER_TABLE, 1, CTRL>(p, grid, block, s);
+      }
+    }
+    if (!pf) launch_k<R, FIELD, PRAD_SAMPLER_TABLE, 0, CTRL>(p, grid, block, s);
     return cudaGetLastError();
   }
   if constexpr (sizeof(R) == 4) {
     if (sampler == PRAD_SAMPLER_MLP)
-      launch_k<R, FIELD, PRAD_SAMPLER_MLP, false, CTRL>(p, grid, block, s);
+      launch_k<R, FIELD, PRAD_SAMPLER_MLP, 0, CTRL>(p, grid, block, s);
     else
-      launch_k<R, FIELD, PRAD_SAMPLER_MLP_FALLBACK, false, CTRL>(p, grid, block, s);
+      launch_k<R, FIELD, PRAD_SAMPLER_MLP_FALLBACK, 0, CTRL>(p, grid, block, s);
     return cudaGetLastError();
   }
   return cudaErrorInvalidValue;
@@ -1286,22 +1325,24 @@ cudaError_t launch_field(const StepParams<R>& p, int sampler, int grid, int bloc
 }
 
 template <typename R, int FIELD, bool CTRL>
-int field_occupancy_c(int sampler, bool pf, int block, bool std_cfg) {
+int field_occupancy_c(int sampler, int pf, int block, bool std_cfg) {
   if (sampler == PRAD_SAMPLER_TABLE) {
-    if constexpr (sizeof(R) == 4)
-      if (pf) return occupancy_k<R, FIELD, PRAD_SAMPLER_TABLE, true, CTRL>(block, std_cfg);
-    return occupancy_k<R, FIELD, PRAD_SAMPLER_TABLE, false, CTRL>(block, std_cfg);
+    if constexpr (sizeof(R) == 4) {
+      if (pf == 2) return occupancy_k<R, FIELD, PRAD_SAMPLER_TABLE, 2, CTRL>(block, std_cfg);
+      if (pf == 1) return occupancy_k<R, FIELD, PRAD_SAMPLER_TABLE, 1, CTRL>(block, std_cfg);
+    }
+    return occupancy_k<R, FIELD, PRAD_SAMPLER_TABLE, 0, CTRL>(block, std_cfg);
   }
   if constexpr (sizeof(R) == 4) {
     if (sampler == PRAD_SAMPLER_MLP)
-      return occupancy_k<R, FIELD, PRAD_SAMPLER_MLP, false, CTRL>(block, std_cfg);
-    return occupancy_k<R, FIELD, PRAD_SAMPLER_MLP_FALLBACK, false, CTRL>(block, std_cfg);
+      return occupancy_k<R, FIELD, PRAD_SAMPLER_MLP, 0, CTRL>(block, std_cfg);
+    return occupancy_k<R, FIELD, PRAD_SAMPLER_MLP_FALLBACK, 0, CTRL>(block, std_cfg);
   }
   return 1;
 }
 
 template <typename R, int FIELD>
-int field_occupancy(int sampler, bool pf, int block, bool ctrl, bool std_cfg) {
+int field_occupancy(int sampler, int pf, int block, bool ctrl, bool std_cfg) {
   return ctrl ? field_occupancy_c<R, FIELD, true>(sampler, pf, block, std_cfg)
               : field_occupancy_c<R, FIELD, false>(sampler, pf, block, std_cfg);
 }
@@ -1310,7 +1351,7 @@ int field_occupancy(int sampler, bool pf, int block, bool ctrl, bool std_cfg) {
 template <typename R>
 int push_emit_occupancy(const StepParams<R>& p, int field_kind, int sampler, int nsub, int block,
                         bool ctrl) {
-  const bool pf = nsub == 1;
+  const int pf = nsub == 1 ? (dense_launch(p) ? 2 : 1) : 0;
   const bool sc = std_config(p, field_kind == PRAD_FIELD_YEE2D ? 2 : 3);
   switch (field_kind) {
     case PRAD_FIELD_CONST:

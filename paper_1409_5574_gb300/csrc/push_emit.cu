@@ -143,9 +143,12 @@ __device__ __forceinline__ void sincos_pi(double v, double* s, double* c) {
 // The branch is an integer compare, identical in every precision.  Both
 // branches share one log2, so the warp does not diverge.
 // ---------------------------------------------------------------------------
+// STAB: the table is read from a copy in shared memory (stab) instead of
+// through L1 from global memory.
+template <bool STAB = false>
 __device__ __forceinline__ void sample_x_g(const StepParams<float>& P,
                                            uint32_t w0, uint32_t w1, float& x,
-                                           float& g) {
+                                           float& g, const float4* stab = nullptr) {
   const uint64_t W = (static_cast<uint64_t>(w1) << 32) | w0;
   const bool low = W < P.thr;
   const uint32_t h = low ? w1 : ~w1;
@@ -166,13 +169,17 @@ __device__ __forceinline__ void sample_x_g(const StepParams<float>& P,
   const int nmax = low ? kN1 - 1 : kN2 - 1;
   i = min(i, nmax);
   const float s = u - static_cast<float>(i);
-  const float4 c = __ldg(P.tab + (low ? i : kN1 + i));
+  const int ti = low ? i : kN1 + i;
+  float4 c;
+  if constexpr (STAB) c = stab[ti]; else c = __ldg(P.tab + ti);
   g = fmaf(s, fmaf(s, fmaf(s, c.w, c.z), c.y), c.x);
 }
 
+template <bool STAB = false>
 __device__ __forceinline__ void sample_x_g(const StepParams<double>& P,
                                            uint32_t w0, uint32_t w1, double& x,
-                                           double& g) {
+                                           double& g, const Coef4d* = nullptr) {
+  static_assert(!STAB, "the FP64 table is read from global memory");
   const uint64_t W = (static_cast<uint64_t>(w1) << 32) | w0;
   const bool low = W < P.thr;
   double u;
@@ -393,6 +400,14 @@ struct PhotonStageAoS {
   float4 q[kStage][3];
   float4 pend[kStage];
 };
+// The record layout without the payload slot (table sampler), for a kernel
+// whose shared memory also holds the sampling table.
+struct PhotonStageRec {
+  float4 q[kStage][3];
+};
+template <class ST>
+constexpr bool kRecordStage =
+    std::is_same<ST, PhotonStageAoS>::value || std::is_same<ST, PhotonStageRec>::value;
 
 template <bool PEND>
 __device__ __forceinline__ void stage_put(PhotonStageSoA& st, int pos, const float rec[8],
@@ -413,6 +428,14 @@ __device__ __forceinline__ void stage_put(PhotonStageAoS& st, int pos, const flo
   st.q[pos][1] = make_float4(rec[4], rec[5], rec[6], rec[7]);
   st.q[pos][2] = make_float4(__uint_as_float(pid), __uint_as_float(step), 0.0f, 0.0f);
   if constexpr (PEND) st.pend[pos] = make_float4(pend[0], pend[1], pend[2], pend[3]);
+}
+template <bool PEND>
+__device__ __forceinline__ void stage_put(PhotonStageRec& st, int pos, const float rec[8],
+                                          uint32_t pid, uint32_t step, const float*) {
+  static_assert(!PEND, "no payload slot");
+  st.q[pos][0] = make_float4(rec[0], rec[1], rec[2], rec[3]);
+  st.q[pos][1] = make_float4(rec[4], rec[5], rec[6], rec[7]);
+  st.q[pos][2] = make_float4(__uint_as_float(pid), __uint_as_float(step), 0.0f, 0.0f);
 }
 __device__ __forceinline__ float4 stage_pend(const PhotonStageSoA& st, int r) {
   return make_float4(st.pend[0][r], st.pend[1][r], st.pend[2][r], st.pend[3][r]);
@@ -456,7 +479,7 @@ __device__ __forceinline__ void flush_stage(ST& st, int fill, const PhotonOut& o
     if (slot < static_cast<unsigned long long>(o.cap)) {
       // the direction is staged as the raw mean momentum: normalise here,
       // once per record, instead of in every lane of every step
-      if constexpr (std::is_same<ST, PhotonStageAoS>::value) {
+      if constexpr (kRecordStage<ST>) {
         const float4 qa = st.q[r][0], qb = st.q[r][1], qc = st.q[r][2];
         const float d2 = qa.w * qa.w + qb.x * qb.x + qb.y * qb.y;
         const float inv = d2 > 0.0f ? rsqrtf(d2) : 0.0f;
@@ -661,6 +684,15 @@ __device__ __forceinline__ void load_state(const StepParams<R>& P, int64_t i, bo
   }
 }
 
+// One-step launches of the FP32 table sampler without control read the
+// sampling table from a copy in shared memory (advance_particle's STAB):
+// there the streamed state passes through L1 and would evict it.  (Fused
+// launches keep it in L1: the copy's 20 KB would cost them a resident block
+// per SM.)
+template <typename R, int SAMP, int ONE, bool CTRL>
+constexpr bool kSharedTab =
+    sizeof(R) == 4 && SAMP == PRAD_SAMPLER_TABLE && ONE != 0 && !CTRL;
+
 // The new state is written back to global memory.  The launch's ledger increments reach the FP64 ledgers as one add
 // per entry per launch, so the sums are sequenced by the launches and
 // bit-reproducible.  Multi-step launches add them with fire-and-forget
@@ -678,12 +710,13 @@ __device__ __forceinline__ void load_state(const StepParams<R>& P, int64_t i, bo
 // three dimensions, two for the Yee grid) fixed at compile time, so the step
 // tests no mode.
 template <typename R, int FIELD, int SAMP, int ONE = 0, bool CTRL = false,
-          bool STD = false, class G, class ST>
+          bool STD = false, bool STAB = false, class G, class ST>
 __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const uint32_t (&rk)[20],
                                                  const G& gat,
                                                  int64_t i, const PState<R>& st,
                                                  ST& stage, int& fill,
-                                                 const PhotonOut& pout, Counts& cnt) {
+                                                 const PhotonOut& pout, Counts& cnt,
+                                                 const typename TabOf<R>::T* stab = nullptr) {
   const bool act = st.act;
   R x = st.x, y = st.y, z = st.z, ux = st.ux, uy = st.uy, uz = st.uz;
   const R w = st.w;
@@ -828,7 +861,7 @@ __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const u
       //    scaled by dn_scale, record weights by wmul, for lanes with part
       auto trial = [&](uint32_t w0, uint32_t w1, R Rd, R dn_scale, R wmul, bool part) {
         R xs, g;
-        sample_x_g(P, w0, w1, xs, g);
+        sample_x_g<STAB>(P, w0, w1, xs, g, stab);
         const R dN = P.cn_dt * Om * g * rcp(xs) * dn_scale;
         const R fl = flr(dN);
         const R k = fl + ((Rd < dN - fl) ? R(1) : R(0));
@@ -1007,8 +1040,15 @@ int occupancy_of(K kernel, int block, size_t dyn) {
 template <typename R, int FIELD, int SAMP, int PF, bool CTRL, bool STD = false>
 __global__ void __launch_bounds__(256, (PF ? PRAD_PF_MINB : MinBlocks<R, FIELD, SAMP>::value))
     k_push_emit(const StepParams<R> P) {
-  using Stage = PhotonStageT<SAMP != PRAD_SAMPLER_TABLE || !CTRL>;
+  constexpr bool kSTab = kSharedTab<R, SAMP, PF, CTRL>;
+  using Stage = typename std::conditional<kSTab, PhotonStageRec,
+                                          PhotonStageT<SAMP != PRAD_SAMPLER_TABLE || !CTRL>>::type;
   __shared__ Stage stage_all[kMaxWarps];
+  __shared__ typename TabOf<R>::T stab[kSTab ? kNTab : 1];
+  if constexpr (kSTab) {
+    for (int k = threadIdx.x; k < kNTab; k += blockDim.x) stab[k] = __ldg(P.tab + k);
+    __syncthreads();
+  }
   Stage& stage = stage_all[threadIdx.x >> 5];
   int fill = 0;  // warp-uniform
   const PhotonOut pout = make_pout(P);
@@ -1027,16 +1067,16 @@ __global__ void __launch_bounds__(256, (PF ? PRAD_PF_MINB : MinBlocks<R, FIELD, 
       const PState<R> cur = nxt;
       const int64_t j = i + stride;
       load_state<R, PF>(P, j, j < P.n, nxt);
-      advance_particle<R, FIELD, SAMP, PF, CTRL, STD>(P, P.rkey, gat, i, cur, stage, fill, pout,
-                                                      cnt);
+      advance_particle<R, FIELD, SAMP, PF, CTRL, STD, kSTab>(P, P.rkey, gat, i, cur, stage, fill,
+                                                             pout, cnt, kSTab ? stab : nullptr);
     }
   } else {
     for (int64_t base = first; base < P.n; base += stride) {
       const int64_t i = base + threadIdx.x;
       PState<R> cur;
       load_state(P, i, i < P.n, cur);
-      advance_particle<R, FIELD, SAMP, 0, CTRL, STD>(P, P.rkey, gat, i, cur, stage, fill, pout,
-                                                     cnt);
+      advance_particle<R, FIELD, SAMP, 0, CTRL, STD, kSTab>(P, P.rkey, gat, i, cur, stage, fill,
+                                                            pout, cnt, kSTab ? stab : nullptr);
     }
   }
   if (fill > 0) flush_stage<SAMP != PRAD_SAMPLER_TABLE>(stage, fill, pout);

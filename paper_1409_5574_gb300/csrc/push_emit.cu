@@ -933,7 +933,8 @@ __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const u
     P.ux[i] = ux; P.uy[i] = uy; P.uz[i] = uz;
     if constexpr (ONE == 2) {
       if (rr_mode >= PRAD_RR_LEDGER) P.led_ll[i] = st.ll_old + ll.value_one();
-      if (le.nonzero()) P.led_emit[i] = st.emit_old + le.value_one();
+      // (with control a step may add several trials: the full value)
+      if (le.nonzero()) P.led_emit[i] = st.emit_old + (CTRL ? le.value() : le.value_one());
       return;
     }
     const int64_t li = static_cast<int64_t>(pid - P.pid0);
@@ -945,8 +946,9 @@ __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const u
           atomicAdd(P.led_ll + li, ll.value());
       }
       if (le.nonzero()) {
+        // (with control a step may add several trials: the full value)
         if constexpr (ONE)
-          P.led_emit[li] = st.emit_old + le.value_one();
+          P.led_emit[li] = st.emit_old + (CTRL ? le.value() : le.value_one());
         else
           atomicAdd(P.led_emit + li, le.value());
       }

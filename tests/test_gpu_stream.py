@@ -41,10 +41,10 @@ def _small_yee(n, seed=4, a0=300.0, nx=96, ny=80):
     return wl
 
 
-def _run(wl, nsteps, steps_per_launch, blocks_per_sm=0, with_pid=False):
+def _run(wl, nsteps, steps_per_launch, blocks_per_sm=0, with_pid=False, **kw):
     ctx = prad.Context(wl.problem_kwargs(), precision=prad.PRAD_FP32,
                        photon_capacity=1 << 20, max_particles=wl.n,
-                       steps_per_launch=steps_per_launch, blocks_per_sm=blocks_per_sm)
+                       steps_per_launch=steps_per_launch, blocks_per_sm=blocks_per_sm, **kw)
     st = ctx.to_device(wl.state, with_pid=with_pid)
     ctx.push_emit(st, nsteps, t0=3)
     torch.cuda.synchronize()
@@ -59,9 +59,12 @@ def _run(wl, nsteps, steps_per_launch, blocks_per_sm=0, with_pid=False):
 
 
 def _photon_table(ph):
+    """Records in a canonical order: by (pid, step), then by their values
+    (with super-photon control a step can write several records)."""
     key = ph["pid"].astype(np.int64) * 2**32 + ph["step"].astype(np.int64)
-    o = np.argsort(key)
-    cols = [ph[k][o] for k in ("x", "y", "z", "nx", "ny", "nz", "eps", "weight")]
+    names = ("x", "y", "z", "nx", "ny", "nz", "eps", "weight")
+    o = np.lexsort(tuple(ph[k] for k in reversed(names)) + (key,))
+    cols = [ph[k][o] for k in names]
     return key[o], np.stack(cols, 1)
 
 
@@ -98,6 +101,21 @@ def test_one_step_launches_equal_fused_launch(case, n):
     assert a["stats"]["records"] > 0
     if case == "planewave_rr_off":
         assert not a["ll"].any()
+    _same(a, b)
+
+
+@pytest.mark.parametrize("with_pid", [False, True])
+def test_one_step_with_super_photon_control_equals_fused(with_pid):
+    """Super-photon control (3 trials per step at 1/3 of dN each, selection
+    probability 1/2): a step can add several records' energies to a
+    particle's emitted-energy ledger; one-step launches (implicit ids, and
+    an id array) still give the state, photons and ledgers of one fused
+    launch."""
+    wl = W.plane_wave(a0=500.0, n=(1 << 16) + 77, seed=23)
+    kw = dict(n_try=3, select_prob=0.5)
+    a = _run(wl, 8, steps_per_launch=1, with_pid=with_pid, **kw)
+    b = _run(wl, 8, steps_per_launch=8, **kw)
+    assert a["stats"]["records"] > 0
     _same(a, b)
 
 

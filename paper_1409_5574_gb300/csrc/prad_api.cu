@@ -426,6 +426,10 @@ void fill_common(const prad_ctx* c, StepParams<R>& p, const prad_fields& f) {
     p.kc_lo = static_cast<R>(kcd - static_cast<double>(p.kc));
     p.hand = static_cast<R>(f.hand);
     p.dir = static_cast<R>(f.dir);
+    // hand, dir = +-1: these products are exact
+    p.pw_ez = p.hand * p.E0;
+    p.pw_by = -p.dir * p.hand * p.E0;
+    p.pw_bz = p.dir * p.E0;
     // fixed-point cycles: phase0 / 2pi and omega_L dt / 2pi, modulo 1
     long double c0 = static_cast<long double>(f.phase0) / (2.0L * kPi);
     c0 -= std::floor(c0);
@@ -435,6 +439,7 @@ void fill_common(const prad_ctx* c, StepParams<R>& p, const prad_fields& f) {
     p.phase_step = static_cast<uint64_t>(std::ldexp(cs, 64));
   } else {
     p.E0 = p.kc = p.kc_lo = p.hand = p.dir = R(0);
+    p.pw_ez = p.pw_by = p.pw_bz = R(0);
     p.phase_t0 = p.phase_step = 0;
   }
   if (f.kind == PRAD_FIELD_YEE2D) {

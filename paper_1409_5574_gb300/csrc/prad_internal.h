@@ -90,6 +90,7 @@ struct StepParams {
   // field
   R E[3], B[3];
   R E0, kc, kc_lo, hand, dir;  // plane wave (kc + kc_lo: k/2pi to ~2^-48)
+  R pw_ez, pw_by, pw_bz;       // plane wave: hand E0, -dir hand E0, dir E0 (exact)
   uint64_t phase_t0, phase_step;  // fixed-point phase (cycles * 2^64)
   const float* yee[6];
   int32_t nx, ny;

@@ -61,6 +61,51 @@ __device__ __forceinline__ uint4 philox10_rk(uint4 c, const uint32_t* rk) {
   return c;
 }
 
+// The same generator for the counter (pid, step, 0, ens) of the table
+// sampler, in two parts.  With word 2 zero, round 0's second product is 0
+// and its first depends on pid only; after round 1, words 0 and 1 depend on
+// (pid, ens) only, and so does round 2's first product.  philox_pre computes
+// those four words once per particle; philox10_pre finishes the block for a
+// step (two products fewer than philox10_rk), with the same result.
+struct PhiloxPre {
+  uint32_t w0, y1, h2, l2;
+};
+__device__ __forceinline__ PhiloxPre philox_pre(uint32_t pid, uint32_t ens, const uint32_t* rk) {
+  uint64_t p;
+  PhiloxPre q;
+  asm("mul.wide.u32 %0, %1, %2;" : "=l"(p) : "r"(pid), "r"(0xD2511F53u));
+  const uint32_t z0 = static_cast<uint32_t>(p >> 32) ^ ens ^ rk[1];  // round 0, word 2
+  q.w0 = static_cast<uint32_t>(p);                                   // round 0, word 3
+  asm("mul.wide.u32 %0, %1, %2;" : "=l"(p) : "r"(z0), "r"(0xCD9E8D57u));
+  const uint32_t x1 = static_cast<uint32_t>(p >> 32) ^ rk[2];        // round 1, word 0
+  q.y1 = static_cast<uint32_t>(p);                                   // round 1, word 1
+  asm("mul.wide.u32 %0, %1, %2;" : "=l"(p) : "r"(x1), "r"(0xD2511F53u));
+  q.h2 = static_cast<uint32_t>(p >> 32);                             // round 2, first product
+  q.l2 = static_cast<uint32_t>(p);
+  return q;
+}
+__device__ __forceinline__ uint4 philox10_pre(const PhiloxPre& q, uint32_t step,
+                                              const uint32_t* rk) {
+  uint64_t a, b;
+  const uint32_t x0 = step ^ rk[0];  // round 0, word 0 (word 1 is 0)
+  asm("mul.wide.u32 %0, %1, %2;" : "=l"(a) : "r"(x0), "r"(0xD2511F53u));
+  const uint32_t z1 = static_cast<uint32_t>(a >> 32) ^ q.w0 ^ rk[3];  // round 1, word 2
+  const uint32_t w1 = static_cast<uint32_t>(a);                       // round 1, word 3
+  asm("mul.wide.u32 %0, %1, %2;" : "=l"(b) : "r"(z1), "r"(0xCD9E8D57u));
+  uint4 c = make_uint4(static_cast<uint32_t>(b >> 32) ^ q.y1 ^ rk[4], static_cast<uint32_t>(b),
+                       q.h2 ^ w1 ^ rk[5], q.l2);  // after round 2
+#pragma unroll
+  for (int r = 3; r < 10; ++r) {
+    uint64_t p0, p1;
+    asm("mul.wide.u32 %0, %1, %2;" : "=l"(p0) : "r"(c.x), "r"(0xD2511F53u));
+    asm("mul.wide.u32 %0, %1, %2;" : "=l"(p1) : "r"(c.z), "r"(0xCD9E8D57u));
+    const uint32_t lo0 = static_cast<uint32_t>(p0), hi0 = static_cast<uint32_t>(p0 >> 32);
+    const uint32_t lo1 = static_cast<uint32_t>(p1), hi1 = static_cast<uint32_t>(p1 >> 32);
+    c = make_uint4(hi1 ^ c.y ^ rk[2 * r], lo1, hi0 ^ c.w ^ rk[2 * r + 1], lo0);
+  }
+  return c;
+}
+
 // ---- compensated accumulators for the per-particle ledgers -----------------
 // The FP32 path sums a launch's ledger increments in a float-float pair
 // (Knuth TwoSum: the rounding error of every add is kept in `lo`), about
@@ -132,6 +177,14 @@ __device__ __forceinline__ void sincos_pi(float v, float* s, float* c) {
 }
 __device__ __forceinline__ void sincos_pi(double v, double* s, double* c) {
   sincospi(v, s, c);
+}
+// sin/cos of 2 pi v: the same values as sincos_pi(v + v) (2 v and the float
+// 2 pi = 2 x the float pi are exact), one instruction fewer
+__device__ __forceinline__ void sincos_2pi(float v, float* s, float* c) {
+  __sincosf((2.0f * 3.14159265358979323846f) * v, s, c);
+}
+__device__ __forceinline__ void sincos_2pi(double v, double* s, double* c) {
+  sincospi(v + v, s, c);
 }
 
 // ---------------------------------------------------------------------------
@@ -230,14 +283,14 @@ __device__ __forceinline__ EB<R> plane_wave(const StepParams<R>& P, R x,
   R psi = (psi_t - (p_hi - rnd_int(p_hi))) - p_lo;
   psi -= rnd_int(psi);
   R s, c;
-  sincos_pi(psi + psi, &s, &c);
+  sincos_2pi(psi, &s, &c);
   EB<R> f;
   f.Ex = R(0);
   f.Ey = P.E0 * c;
-  f.Ez = P.hand * P.E0 * s;
+  f.Ez = P.pw_ez * s;  // hand E0 sin: the signs are exact factors
   f.Bx = R(0);
-  f.By = -P.dir * f.Ez;
-  f.Bz = P.dir * f.Ey;
+  f.By = P.pw_by * s;  // -dir E_z
+  f.Bz = P.pw_bz * c;  // dir E_y
   return f;
 }
 
@@ -739,6 +792,12 @@ __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const u
   // variants draw one block per step, counter (pid, step, 0, ensemble).
   constexpr bool kPairDraws = SAMP != PRAD_SAMPLER_TABLE && !CTRL;
   uint4 pair_blk = make_uint4(0u, 0u, 0u, 0u);
+  // the table sampler's per-particle Philox words (one-step launches and the
+  // Yee grid; the fused analytic-field kernels, at 48 registers, are faster
+  // recomputing them than keeping four more words live)
+  constexpr bool kPre = SAMP == PRAD_SAMPLER_TABLE && (ONE != 0 || FIELD == PRAD_FIELD_YEE2D);
+  PhiloxPre ppre{};
+  if constexpr (kPre) ppre = philox_pre(pid, P.ensemble, rk);
   const int rr_mode = STD ? PRAD_RR_APPLY : P.rr_mode;
   const int heff_form = STD ? PRAD_HEFF_FIELD : P.heff_form;
   const int dims = STD ? (FIELD == PRAD_FIELD_YEE2D ? 2 : 3) : P.dims;
@@ -852,7 +911,10 @@ __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const u
       rnd = (step & 1u) ? make_uint4(pair_blk.z, 0u, pair_blk.w, 0u)
                         : make_uint4(pair_blk.x, 0u, pair_blk.y, 0u);
     } else {
-      rnd = philox10_rk<SAMP == PRAD_SAMPLER_TABLE>(make_uint4(pid, step, 0u, P.ensemble), rk);
+      if constexpr (kPre)
+        rnd = philox10_pre(ppre, step, rk);
+      else
+        rnd = philox10_rk<SAMP == PRAD_SAMPLER_TABLE>(make_uint4(pid, step, 0u, P.ensemble), rk);
     }
     const R Rr = unit_uniform<R>(rnd.z);
     if constexpr (SAMP == PRAD_SAMPLER_TABLE) {

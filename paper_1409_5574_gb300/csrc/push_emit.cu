@@ -166,6 +166,10 @@ __device__ __forceinline__ double rcp(double v) { return 1.0 / v; }
 // sqr(0) = 0
 __device__ __forceinline__ float sqr(float v) { return v > 0.0f ? v * rsqrtf(v) : 0.0f; }
 __device__ __forceinline__ double sqr(double v) { return sqrt(v); }
+// the same for an argument known to be >= 1 (1 + |u|^2): no zero guard (a
+// non-finite argument belongs to a frozen particle, which is never stored)
+__device__ __forceinline__ float sqr_pos(float v) { return v * rsqrtf(v); }
+__device__ __forceinline__ double sqr_pos(double v) { return sqrt(v); }
 __device__ __forceinline__ float flr(float v) { return floorf(v); }
 __device__ __forceinline__ double flr(double v) { return floor(v); }
 __device__ __forceinline__ float rnd_int(float v) { return rintf(v); }
@@ -862,8 +866,8 @@ __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const u
       const R dx_ = nux - ux, dy_ = nuy - uy, dz_ = nuz - uz;
       const R dp2 = dx_ * dx_ + dy_ * dy_ + dz_ * dz_;
       const R pdp = ax * dx_ + ay * dy_ + az * dz_;
-      const R g0 = sqr(R(1) + ux * ux + uy * uy + uz * uz);
-      const R g1 = sqr(R(1) + nux * nux + nuy * nuy + nuz * nuz);
+      const R g0 = sqr_pos(R(1) + ux * ux + uy * uy + uz * uz);
+      const R g1 = sqr_pos(R(1) + nux * nux + nuy * nuy + nuz * nuz);
       R c2 = ua2 * dp2 - pdp * pdp;
       c2 = c2 > R(0) ? c2 : R(0);
       Om = ua2 > R(0) ? R(0.5) * (g0 + g1) * sqr(c2) * rcp(ua2) * P.inv_dtn : R(0);
@@ -888,7 +892,7 @@ __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const u
     if (rr_mode >= PRAD_RR_LEDGER) ll.add(w * P.ll_coef * om2 * ua2);
     R n2 = nux * nux + nuy * nuy + nuz * nuz;
     if (rr_mode == PRAD_RR_APPLY) {
-      const R gL = sqr(R(1) + n2);
+      const R gL = sqr_pos(R(1) + n2);
       const R fk = rcp(R(1) + P.ll_coef * om2 * gL);
       nux *= fk; nuy *= fk; nuz *= fk;
       n2 *= fk * fk;

@@ -41,9 +41,9 @@ def _small_yee(n, seed=4, a0=300.0, nx=96, ny=80):
     return wl
 
 
-def _run(wl, nsteps, steps_per_launch, blocks_per_sm=0, with_pid=False, **kw):
+def _run(wl, nsteps, steps_per_launch, blocks_per_sm=0, with_pid=False, cap=1 << 20, **kw):
     ctx = prad.Context(wl.problem_kwargs(), precision=prad.PRAD_FP32,
-                       photon_capacity=1 << 20, max_particles=wl.n,
+                       photon_capacity=cap, max_particles=wl.n,
                        steps_per_launch=steps_per_launch, blocks_per_sm=blocks_per_sm, **kw)
     st = ctx.to_device(wl.state, with_pid=with_pid)
     ctx.push_emit(st, nsteps, t0=3)
@@ -116,6 +116,17 @@ def test_one_step_with_super_photon_control_equals_fused(with_pid):
     a = _run(wl, 8, steps_per_launch=1, with_pid=with_pid, **kw)
     b = _run(wl, 8, steps_per_launch=8, **kw)
     assert a["stats"]["records"] > 0
+    _same(a, b)
+
+
+def test_one_step_many_particles_per_thread():
+    """2^22 electrons on the default grid (four 256-thread blocks per SM):
+    each thread of the one-step kernel walks ~27 particles through its
+    prefetch pipeline; four one-step launches equal one fused launch."""
+    wl = W.plane_wave(a0=500.0, n=1 << 22, seed=27)
+    a = _run(wl, 4, steps_per_launch=1, cap=1 << 22)
+    b = _run(wl, 4, steps_per_launch=4, cap=1 << 22)
+    assert a["stats"]["records"] > 0 and a["stats"]["dropped"] == 0
     _same(a, b)
 
 

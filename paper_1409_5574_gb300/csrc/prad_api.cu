@@ -25,10 +25,6 @@ constexpr double kMe = 9.1093837015e-31;
 constexpr double kHbar = 1.054571817e-34;
 constexpr double kEps0 = 8.8541878128e-12;
 constexpr double kPi = 3.14159265358979323846;
-// Proposal constant of Eq. (11): root of a^(4/3) + (7/9) e^(-a) = 1.
-constexpr double kA = 0.69020670216845766;
-// round(a^(4/3) 2^64): 64-bit words W below it take the x < a branch.
-constexpr uint64_t kThr = 0x9C26B9CE251FFCB8ull;
 
 thread_local char g_init_err[512];
 
@@ -185,7 +181,7 @@ void build_tables(std::vector<float4>& t32, std::vector<Coef4d>& t64) {
   GaussLegendre gl;
   t32.resize(kNTab);
   t64.resize(kNTab);
-  const double T1 = std::cbrt(kA);
+  const double T1 = kCbrtA;
   for (int i = 0; i < kNTab; ++i) {
     double v[4];
     for (int k = 0; k < 4; ++k) {
@@ -325,8 +321,11 @@ bool ctrl_of(const prad_ctx* c) {
 
 // The standard configuration of the batched kernel's ensembles (constant or
 // plane-wave fields, so three dimensions): LL kick applied, field-form H_eff.
+// the batched kernel's standard variant: as std_config of the step kernels
+// (LL kick applied, field-form H_eff, unit charge)
 bool std_of(const prad_ctx* c) {
-  return c->cfg.rr_mode == PRAD_RR_APPLY && c->cfg.heff_form == PRAD_HEFF_FIELD;
+  return c->cfg.rr_mode == PRAD_RR_APPLY && c->cfg.heff_form == PRAD_HEFF_FIELD &&
+         std::fabs(c->cfg.charge) == 1.0;
 }
 
 MlpDev mlp_dev(const prad_ctx* c) {
@@ -381,8 +380,8 @@ void fill_common(const prad_ctx* c, StepParams<R>& p, const prad_fields& f) {
   p.key0 = static_cast<uint32_t>(c->cfg.seed & 0xffffffffull);
   p.key1 = static_cast<uint32_t>(c->cfg.seed >> 32);
   philox_round_keys(c->cfg.seed, p.rkey);
-  p.t_scale = static_cast<R>(kN1 / std::cbrt(kA));
-  p.x_scale = static_cast<R>(kN2 / (kXmax - kA));
+  p.t_scale = static_cast<R>(kTScale);
+  p.x_scale = static_cast<R>(kXScale);
   p.a = static_cast<R>(kA);
   p.thr = kThr;
   if constexpr (sizeof(R) == 4)

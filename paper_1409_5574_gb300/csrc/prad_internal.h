@@ -19,6 +19,17 @@ constexpr int kN1 = 256;
 constexpr int kN2 = 1024;
 constexpr int kNTab = kN1 + kN2;
 constexpr double kXmax = 45.0;
+// Proposal constant of Eq. (11): root of a^(4/3) + (7/9) e^(-a) = 1, and its
+// cube root (the low branch's end, t = a^(1/3); correctly rounded).
+constexpr double kA = 0.69020670216845766;
+constexpr double kCbrtA = 0x1.c47a11f9c597ep-1;
+// round(a^(4/3) 2^64): 64-bit words W below it take the x < a branch.
+constexpr uint64_t kThr = 0x9C26B9CE251FFCB8ull;
+// Table coordinates: u = t kTScale on the low branch, (x - a) kXScale on the
+// high one.  The step kernels take these (and kA, kThr) as compile-time
+// constants: immediate operands instead of parameter loads in every step.
+constexpr double kTScale = kN1 / kCbrtA;
+constexpr double kXScale = kN2 / (kXmax - kA);
 
 // float -> double by the IEEE-754 formats (normal numbers: the exponent
 // rebiased by 1023 - 127 = 896, the 23 fraction bits moved to the top of

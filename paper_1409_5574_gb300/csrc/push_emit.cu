@@ -207,7 +207,7 @@ __device__ __forceinline__ void sample_x_g(const StepParams<float>& P,
                                            uint32_t w0, uint32_t w1, float& x,
                                            float& g, const float4* stab = nullptr) {
   const uint64_t W = (static_cast<uint64_t>(w1) << 32) | w0;
-  const bool low = W < P.thr;
+  const bool low = W < kThr;
   const uint32_t h = low ? w1 : ~w1;
   const uint32_t l = low ? w0 : ~w0;
   // (h 2^32 + l + 1/2) 2^-64, never zero
@@ -221,7 +221,8 @@ __device__ __forceinline__ void sample_x_g(const StepParams<float>& P,
   const float x_lo = t * t * t;
   const float x_hi = fmaf(-__log2f(arg), 0.69314718055994531f, -0.25131442828090608f);
   x = low ? x_lo : x_hi;
-  const float u = low ? t * P.t_scale : (x_hi - P.a) * P.x_scale;
+  const float u = low ? t * static_cast<float>(kTScale)
+                      : (x_hi - static_cast<float>(kA)) * static_cast<float>(kXScale);
   int i = static_cast<int>(fmaxf(u, 0.0f));
   const int nmax = low ? kN1 - 1 : kN2 - 1;
   i = min(i, nmax);
@@ -238,18 +239,18 @@ __device__ __forceinline__ void sample_x_g(const StepParams<double>& P,
                                            double& g, const Coef4d* = nullptr) {
   static_assert(!STAB, "the FP64 table is read from global memory");
   const uint64_t W = (static_cast<uint64_t>(w1) << 32) | w0;
-  const bool low = W < P.thr;
+  const bool low = W < kThr;
   double u;
   if (low) {
     const double Rp = fma(static_cast<double>(W), 0x1p-64, 0x1p-65);
     const double L = log2(Rp);
     const double t = exp2(0.25 * L);
     x = exp2(0.75 * L);
-    u = t * P.t_scale;
+    u = t * kTScale;
   } else {
     const double om = fma(static_cast<double>(~W), 0x1p-64, 0x1p-65);
     x = -(log(om) + 0.25131442828090608);
-    u = (x - P.a) * P.x_scale;
+    u = (x - kA) * kXScale;
   }
   int i = static_cast<int>(fmax(u, 0.0));
   i = min(i, low ? kN1 - 1 : kN2 - 1);
@@ -861,7 +862,7 @@ __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const u
         eb = f.Ex * bx + f.Ey * by + f.Ez * bz;
       }
       const R h2 = fx * fx + fy * fy + fz * fz - eb * eb;
-      Om = P.abs_q * sqr(h2 > R(0) ? h2 : R(0));
+      Om = (STD ? R(1) : P.abs_q) * sqr(h2 > R(0) ? h2 : R(0));
     } else {  // Eq. (9), gamma = mean of the end-point Lorentz factors
       const R dx_ = nux - ux, dy_ = nuy - uy, dz_ = nuz - uz;
       const R dp2 = dx_ * dx_ + dy_ * dy_ + dz_ * dz_;
@@ -884,9 +885,11 @@ __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const u
       Om = ga * P.inv_dtn;
       if (live) ++cnt.clamp;
     }
-    // 5. omega_c (Eq. (1)) as hbar omega_c / m c^2; chi = eps_r Omega gamma
-    const R epsc = P.eps_r15 * Om * ga * ga;
-    if (live && P.eps_r * Om * ga > R(1)) ++cnt.chi;
+    // 5. omega_c (Eq. (1)) as hbar omega_c / m c^2; chi = eps_r Omega gamma,
+    //    tested as 1.5 chi > 1.5 on the product epsc is formed from
+    const R e1 = P.eps_r15 * Om * ga;
+    const R epsc = e1 * ga;
+    if (live && e1 > R(1.5)) ++cnt.chi;
     // 6. Landau-Lifshitz loss (Eq. (4)): ledger and optional kick
     const R om2 = Om * Om;
     if (rr_mode >= PRAD_RR_LEDGER) ll.add(w * P.ll_coef * om2 * ua2);
@@ -1341,10 +1344,12 @@ __global__ void __launch_bounds__(256, 3) k_push_emit_tiled(const StepParams<R> 
 template <typename R, int FIELD, bool CTRL>
 constexpr bool kHasStd = sizeof(R) == 4 && !CTRL;
 
-// LL kick applied, field-form H_eff, and the field's usual dimensions
+// LL kick applied, field-form H_eff, the field's usual dimensions and unit
+// charge (electrons, positrons)
 template <typename R>
 bool std_config(const StepParams<R>& p, int dims) {
-  return p.rr_mode == PRAD_RR_APPLY && p.heff_form == PRAD_HEFF_FIELD && p.dims == dims;
+  return p.rr_mode == PRAD_RR_APPLY && p.heff_form == PRAD_HEFF_FIELD && p.dims == dims &&
+         p.abs_q == R(1);
 }
 
 template <typename R, bool CTRL, bool STD>

@@ -273,8 +273,8 @@ struct EB {
 // The time part of the phase is a 64-bit fixed-point fraction of a cycle
 // (exact modular arithmetic), so only the x k term carries rounding.
 template <typename R>
-__device__ __forceinline__ EB<R> plane_wave(const StepParams<R>& P, R x,
-                                            uint64_t phase) {
+__device__ __forceinline__ void plane_wave_sc(const StepParams<R>& P, R x, uint64_t phase,
+                                              R* s, R* c) {
   R psi_t;
   if constexpr (sizeof(R) == 4)
     psi_t = static_cast<float>(static_cast<uint32_t>(phase >> 32)) * 0x1p-32f;
@@ -287,8 +287,13 @@ __device__ __forceinline__ EB<R> plane_wave(const StepParams<R>& P, R x,
   const R p_lo = fma(P.kc, x, -p_hi) + P.kc_lo * x;
   R psi = (psi_t - (p_hi - rnd_int(p_hi))) - p_lo;
   psi -= rnd_int(psi);
+  sincos_2pi(psi, s, c);
+}
+template <typename R>
+__device__ __forceinline__ EB<R> plane_wave(const StepParams<R>& P, R x,
+                                            uint64_t phase) {
   R s, c;
-  sincos_2pi(psi, &s, &c);
+  plane_wave_sc(P, x, phase, &s, &c);
   EB<R> f;
   f.Ex = R(0);
   f.Ey = P.E0 * c;
@@ -296,6 +301,30 @@ __device__ __forceinline__ EB<R> plane_wave(const StepParams<R>& P, R x,
   f.Bx = R(0);
   f.By = P.pw_by * s;  // -dir E_z
   f.Bz = P.pw_bz * c;  // dir E_y
+  return f;
+}
+// The sign variant of a plane wave (1..4): 1 + [hand > 0] + 2 [dir > 0].
+template <typename R>
+__host__ __device__ __forceinline__ int pw_signs(const StepParams<R>& p) {
+  return 1 + (p.hand > R(0) ? 1 : 0) + (p.dir > R(0) ? 2 : 0);
+}
+// The same with the handedness and direction known at compile time
+// (PWS = 1 + [hand > 0] + 2 [dir > 0]): E_z, B_y and B_z are sign changes of
+// E0 sin and E_y, the same values from two products instead of four.
+template <int PWS, typename R>
+__device__ __forceinline__ EB<R> plane_wave_signed(const StepParams<R>& P, R x,
+                                                   uint64_t phase) {
+  constexpr bool hpos = ((PWS - 1) & 1) != 0, dpos = ((PWS - 1) & 2) != 0;
+  R s, c;
+  plane_wave_sc(P, x, phase, &s, &c);
+  const R es = P.E0 * s;
+  EB<R> f;
+  f.Ex = R(0);
+  f.Ey = P.E0 * c;
+  f.Ez = hpos ? es : -es;
+  f.Bx = R(0);
+  f.By = dpos ? -f.Ez : f.Ez;
+  f.Bz = dpos ? f.Ey : -f.Ey;
   return f;
 }
 
@@ -768,7 +797,7 @@ constexpr bool kSharedTab =
 // three dimensions, two for the Yee grid) fixed at compile time, so the step
 // tests no mode.
 template <typename R, int FIELD, int SAMP, int ONE = 0, bool CTRL = false,
-          bool STD = false, bool STAB = false, class G, class ST>
+          bool STD = false, bool STAB = false, int PWS = 0, class G, class ST>
 __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const uint32_t (&rk)[20],
                                                  const G& gat,
                                                  int64_t i, const PState<R>& st,
@@ -809,7 +838,11 @@ __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const u
   for (int s = 0; s < nsub; ++s) {
     const uint32_t step = static_cast<uint32_t>(P.t0 + s);
     // 1. field at x^n, t^n
-    const EB<R> f = gat(x, y, phase);
+    EB<R> f;
+    if constexpr (FIELD == PRAD_FIELD_PLANE_WAVE && PWS != 0)
+      f = plane_wave_signed<PWS>(P, x, phase);
+    else
+      f = gat(x, y, phase);
     phase += P.phase_step;
     // 2. Boris: half E kick, rotation, half E kick
     const R hq = P.half_q_dtn;
@@ -1108,7 +1141,8 @@ int occupancy_of(K kernel, int block, size_t dyn) {
 #endif
 // PF: 0 no prefetch (multi-step launches); 1 one step per launch, the next
 // particle prefetched; 2 the same for a dense launch (see dense_launch).
-template <typename R, int FIELD, int SAMP, int PF, bool CTRL, bool STD = false>
+// PWS: the plane wave's signs at compile time (0: from the parameters).
+template <typename R, int FIELD, int SAMP, int PF, bool CTRL, bool STD = false, int PWS = 0>
 __global__ void __launch_bounds__(256, (PF ? PRAD_PF_MINB : MinBlocks<R, FIELD, SAMP>::value))
     k_push_emit(const StepParams<R> P) {
   constexpr bool kSTab = kSharedTab<R, SAMP, PF, CTRL>;
@@ -1138,16 +1172,16 @@ __global__ void __launch_bounds__(256, (PF ? PRAD_PF_MINB : MinBlocks<R, FIELD, 
       const PState<R> cur = nxt;
       const int64_t j = i + stride;
       load_state<R, PF>(P, j, j < P.n, nxt);
-      advance_particle<R, FIELD, SAMP, PF, CTRL, STD, kSTab>(P, P.rkey, gat, i, cur, stage, fill,
-                                                             pout, cnt, kSTab ? stab : nullptr);
+      advance_particle<R, FIELD, SAMP, PF, CTRL, STD, kSTab, PWS>(
+          P, P.rkey, gat, i, cur, stage, fill, pout, cnt, kSTab ? stab : nullptr);
     }
   } else {
     for (int64_t base = first; base < P.n; base += stride) {
       const int64_t i = base + threadIdx.x;
       PState<R> cur;
       load_state(P, i, i < P.n, cur);
-      advance_particle<R, FIELD, SAMP, 0, CTRL, STD, kSTab>(P, P.rkey, gat, i, cur, stage, fill,
-                                                            pout, cnt, kSTab ? stab : nullptr);
+      advance_particle<R, FIELD, SAMP, 0, CTRL, STD, kSTab, PWS>(
+          P, P.rkey, gat, i, cur, stage, fill, pout, cnt, kSTab ? stab : nullptr);
     }
   }
   if (fill > 0) flush_stage<SAMP != PRAD_SAMPLER_TABLE>(stage, fill, pout);
@@ -1226,12 +1260,27 @@ __global__ void __launch_bounds__(256, PRAD_BATCH_MINB)
       }
     } else {
       const FieldGather<float, PRAD_FIELD_PLANE_WAVE> gat{Ps};
-      for (int64_t base = first; base < last; base += blockDim.x) {
-        const int64_t i = base + threadIdx.x;
-        PState<float> st;
-        load_state(Ps, i, i < last, st);
-        advance_particle<float, PRAD_FIELD_PLANE_WAVE, SAMP, 0, CTRL, STD>(
-            Ps, bp.rkey, gat, i, st, stage, fill, pout, cnt);
+      // the standard variant takes the ensemble's wave signs at compile time,
+      // as a single-ensemble launch does (the same code, the same results)
+      auto items = [&](auto pws) {
+        for (int64_t base = first; base < last; base += blockDim.x) {
+          const int64_t i = base + threadIdx.x;
+          PState<float> st;
+          load_state(Ps, i, i < last, st);
+          advance_particle<float, PRAD_FIELD_PLANE_WAVE, SAMP, 0, CTRL, STD, false,
+                           decltype(pws)::value>(Ps, bp.rkey, gat, i, st, stage, fill, pout,
+                                                 cnt);
+        }
+      };
+      if constexpr (STD) {
+        switch (pw_signs(Ps)) {
+          case 1: items(std::integral_constant<int, 1>{}); break;
+          case 2: items(std::integral_constant<int, 2>{}); break;
+          case 3: items(std::integral_constant<int, 3>{}); break;
+          default: items(std::integral_constant<int, 4>{}); break;
+        }
+      } else {
+        items(std::integral_constant<int, 0>{});
       }
     }
     __syncthreads();
@@ -1373,21 +1422,43 @@ cudaError_t launch_push_emit_tiled(const StepParams<R>& p, int max_work, int blo
   return launch_tiled_v<R, false, false>(p, max_work, block, s);
 }
 
+
 template <typename R, int FIELD, int SAMP, int PF, bool CTRL>
 void launch_k(const StepParams<R>& p, int grid, int block, cudaStream_t s) {
   if constexpr (kHasStd<R, FIELD, CTRL>) {
     if (std_config(p, FIELD == PRAD_FIELD_YEE2D ? 2 : 3)) {
-      k_push_emit<R, FIELD, SAMP, PF, CTRL, true><<<grid, block, 0, s>>>(p);
-      return;
+      if constexpr (FIELD == PRAD_FIELD_PLANE_WAVE) {
+        switch (pw_signs(p)) {
+          case 1: k_push_emit<R, FIELD, SAMP, PF, CTRL, true, 1><<<grid, block, 0, s>>>(p); return;
+          case 2: k_push_emit<R, FIELD, SAMP, PF, CTRL, true, 2><<<grid, block, 0, s>>>(p); return;
+          case 3: k_push_emit<R, FIELD, SAMP, PF, CTRL, true, 3><<<grid, block, 0, s>>>(p); return;
+          default: k_push_emit<R, FIELD, SAMP, PF, CTRL, true, 4><<<grid, block, 0, s>>>(p); return;
+        }
+      } else {
+        k_push_emit<R, FIELD, SAMP, PF, CTRL, true><<<grid, block, 0, s>>>(p);
+        return;
+      }
     }
   }
   k_push_emit<R, FIELD, SAMP, PF, CTRL, false><<<grid, block, 0, s>>>(p);
 }
 
 template <typename R, int FIELD, int SAMP, int PF, bool CTRL>
-int occupancy_k(int block, bool std_cfg) {
-  if constexpr (kHasStd<R, FIELD, CTRL>)
-    if (std_cfg) return occupancy_of(k_push_emit<R, FIELD, SAMP, PF, CTRL, true>, block, 0);
+int occupancy_k(int block, bool std_cfg, int pws) {
+  if constexpr (kHasStd<R, FIELD, CTRL>) {
+    if (std_cfg) {
+      if constexpr (FIELD == PRAD_FIELD_PLANE_WAVE) {
+        switch (pws) {
+          case 1: return occupancy_of(k_push_emit<R, FIELD, SAMP, PF, CTRL, true, 1>, block, 0);
+          case 2: return occupancy_of(k_push_emit<R, FIELD, SAMP, PF, CTRL, true, 2>, block, 0);
+          case 3: return occupancy_of(k_push_emit<R, FIELD, SAMP, PF, CTRL, true, 3>, block, 0);
+          default: return occupancy_of(k_push_emit<R, FIELD, SAMP, PF, CTRL, true, 4>, block, 0);
+        }
+      } else {
+        return occupancy_of(k_push_emit<R, FIELD, SAMP, PF, CTRL, true>, block, 0);
+      }
+    }
+  }
   return occupancy_of(k_push_emit<R, FIELD, SAMP, PF, CTRL, false>, block, 0);
 }
 
@@ -1438,26 +1509,26 @@ cudaError_t launch_field(const StepParams<R>& p, int sampler, int grid, int bloc
 }
 
 template <typename R, int FIELD, bool CTRL>
-int field_occupancy_c(int sampler, int pf, int block, bool std_cfg) {
+int field_occupancy_c(int sampler, int pf, int block, bool std_cfg, int pws) {
   if (sampler == PRAD_SAMPLER_TABLE) {
     if constexpr (sizeof(R) == 4) {
-      if (pf == 2) return occupancy_k<R, FIELD, PRAD_SAMPLER_TABLE, 2, CTRL>(block, std_cfg);
-      if (pf == 1) return occupancy_k<R, FIELD, PRAD_SAMPLER_TABLE, 1, CTRL>(block, std_cfg);
+      if (pf == 2) return occupancy_k<R, FIELD, PRAD_SAMPLER_TABLE, 2, CTRL>(block, std_cfg, pws);
+      if (pf == 1) return occupancy_k<R, FIELD, PRAD_SAMPLER_TABLE, 1, CTRL>(block, std_cfg, pws);
     }
-    return occupancy_k<R, FIELD, PRAD_SAMPLER_TABLE, 0, CTRL>(block, std_cfg);
+    return occupancy_k<R, FIELD, PRAD_SAMPLER_TABLE, 0, CTRL>(block, std_cfg, pws);
   }
   if constexpr (sizeof(R) == 4) {
     if (sampler == PRAD_SAMPLER_MLP)
-      return occupancy_k<R, FIELD, PRAD_SAMPLER_MLP, 0, CTRL>(block, std_cfg);
-    return occupancy_k<R, FIELD, PRAD_SAMPLER_MLP_FALLBACK, 0, CTRL>(block, std_cfg);
+      return occupancy_k<R, FIELD, PRAD_SAMPLER_MLP, 0, CTRL>(block, std_cfg, pws);
+    return occupancy_k<R, FIELD, PRAD_SAMPLER_MLP_FALLBACK, 0, CTRL>(block, std_cfg, pws);
   }
   return 1;
 }
 
 template <typename R, int FIELD>
-int field_occupancy(int sampler, int pf, int block, bool ctrl, bool std_cfg) {
-  return ctrl ? field_occupancy_c<R, FIELD, true>(sampler, pf, block, std_cfg)
-              : field_occupancy_c<R, FIELD, false>(sampler, pf, block, std_cfg);
+int field_occupancy(int sampler, int pf, int block, bool ctrl, bool std_cfg, int pws) {
+  return ctrl ? field_occupancy_c<R, FIELD, true>(sampler, pf, block, std_cfg, pws)
+              : field_occupancy_c<R, FIELD, false>(sampler, pf, block, std_cfg, pws);
 }
 
 // Resident blocks per SM of the kernel variant a launch would use.
@@ -1468,10 +1539,10 @@ int push_emit_occupancy(const StepParams<R>& p, int field_kind, int sampler, int
   const bool sc = std_config(p, field_kind == PRAD_FIELD_YEE2D ? 2 : 3);
   switch (field_kind) {
     case PRAD_FIELD_CONST:
-      return field_occupancy<R, PRAD_FIELD_CONST>(sampler, pf, block, ctrl, sc);
+      return field_occupancy<R, PRAD_FIELD_CONST>(sampler, pf, block, ctrl, sc, pw_signs(p));
     case PRAD_FIELD_PLANE_WAVE:
-      return field_occupancy<R, PRAD_FIELD_PLANE_WAVE>(sampler, pf, block, ctrl, sc);
-    default: return field_occupancy<R, PRAD_FIELD_YEE2D>(sampler, pf, block, ctrl, sc);
+      return field_occupancy<R, PRAD_FIELD_PLANE_WAVE>(sampler, pf, block, ctrl, sc, pw_signs(p));
+    default: return field_occupancy<R, PRAD_FIELD_YEE2D>(sampler, pf, block, ctrl, sc, pw_signs(p));
   }
 }
 template int push_emit_occupancy<float>(const StepParams<float>&, int, int, int, int, bool);

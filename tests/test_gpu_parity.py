@@ -174,6 +174,44 @@ def test_planewave_fp32_parity(a0):
     assert gpu["stats"]["chi_gt1"] == pytest.approx(ref["stats"]["chi_gt1"], rel=1e-3, abs=2)
 
 
+@pytest.mark.parametrize("hand", [1, -1])
+@pytest.mark.parametrize("direction", [1, -1])
+def test_planewave_signs_fp32_parity(hand, direction):
+    """The standard kernels take the plane wave's handedness and direction
+    as compile-time signs (four variants).  Each against the oracle (40
+    one-step launches at a0 = 300, the electrons counter-propagating), and
+    against the batched kernel, which reads the signs at run time: the
+    same state and photons bit for bit."""
+    wl = W.plane_wave(a0=300.0, n=4096 + 77, seed=9)
+    wl.hand, wl.direction = hand, direction
+    wl.state["ux"] = wl.state["ux"] * direction  # against the wave's direction
+    wl = _f32_inputs(wl)
+    nsteps = 40
+    gpu = _run_gpu(wl, nsteps, prad.PRAD_FP32)
+    ref = _run_oracle(wl, nsteps)
+    rel = _momentum_rel(gpu["state"], ref["state"])
+    assert rel.max() <= 1e-5, rel.max()
+    m, tot = _check_photons(gpu, ref, 0, eps_rtol=1e-5, flip_tol=2e-5)
+    assert tot > 1000
+    assert gpu["ll"] == pytest.approx(ref["ledger"]["ll"].sum(), rel=1e-4)
+    assert gpu["emitted"] == pytest.approx(ref["ledger"]["emit"].sum(), rel=1e-4)
+    # the batched kernel (one ensemble, the same launch shape)
+    ctx = prad.Context(wl.problem_kwargs(), precision=prad.PRAD_FP32,
+                       photon_capacity=1 << 18, max_particles=wl.n, steps_per_launch=1)
+    st = ctx.to_device(wl.state)
+    ctx.push_emit_batch(ctx.ensembles([st], [wl.problem_kwargs()]), nsteps)
+    torch.cuda.synchronize()
+    ph = ctx.photons(on_device=False)
+    for k in ("x", "y", "z", "ux", "uy", "uz"):
+        np.testing.assert_array_equal(st[k].double().cpu().numpy(), gpu["state"][k], err_msg=k)
+    kb = ph["pid"].numpy().astype(np.int64) * 2**32 + ph["step"].numpy().astype(np.int64)
+    kg = gpu["photons"]["pid"].astype(np.int64) * 2**32 + gpu["photons"]["step"].astype(np.int64)
+    ob, og = np.argsort(kb), np.argsort(kg)
+    np.testing.assert_array_equal(kb[ob], kg[og])
+    np.testing.assert_array_equal(ph["eps"].numpy()[ob], gpu["photons"]["eps"][og])
+    ctx.close()
+
+
 def _strong_constant_b(n=4096, a0=500.0, seed=2):
     """Isotropic electrons, gamma ~ U[100, 1000], in B = a0 m omega_L / e with
     the LL kick (the strongest constant-B ensembles of the batched mix)."""

@@ -53,9 +53,9 @@ KERNEL_SOURCES = ["paper_1409_5574_gb300/csrc/push_emit.cu",
                   "paper_1409_5574_gb300/csrc/prad_internal.h",
                   "paper_1409_5574_gb300/csrc/mlp_device.cuh"]
 NCU_TRAFFIC = {
-    "src_sha256": "ee3ea78401a21d51bf991450d65e70010ce029591c8806237adc4a97e866d549",
-    "fused": 12567056960,  # mean bytes per launch over the 4 launches of one bench step
-    "stream": 1375764574,  # mean bytes per launch, 2^24 particles x 1 step, a0 = 500
+    "src_sha256": "83bbab324b439f0d653bad57a7178609f7f425ef14e6f634bd03dce2339ca4da",
+    "fused": 12565420672,  # mean bytes per launch over the 4 launches of one bench step
+    "stream": 1375735404,  # mean bytes per launch, 2^24 particles x 1 step, a0 = 500
 }
 
 
@@ -625,6 +625,21 @@ def run_prad(args):
         gm = n // groups
         copy_s = torch.cuda.Stream()
         comp = ctx.stream
+        # this machine's host link: one full-state copy each way (outside the
+        # timed region; the e2e figure depends on it)
+        lk = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        torch.cuda.synchronize()
+        lk[0].record(comp)
+        for k in work:
+            work[k].copy_(host[k], non_blocking=True)
+        lk[1].record(comp)
+        lk[2].record(comp)
+        for k in back:
+            back[k].copy_(work[k], non_blocking=True)
+        lk[3].record(comp)
+        lk[3].synchronize()
+        link = {"h2d_gb_per_s": h2d / (lk[0].elapsed_time(lk[1]) / 1e3) / 1e9,
+                "d2h_gb_per_s": (d2h - 96) / (lk[2].elapsed_time(lk[3]) / 1e3) / 1e9}
 
         def e2e_step():
             ins = []
@@ -662,7 +677,7 @@ def run_prad(args):
         torch.cuda.synchronize()
         te = max_over_ranks(time.perf_counter() - t0, "cuda")
         e2e = {"value": job_rate(ps_per_step * args.steps, te, ws), "unit": UNIT,
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "host_link": link,
                "what": "H2D of the initial state (pinned), all launches, D2H of the advanced "
                        "state (x y z ux uy uz, pinned) and of the totals, in "
                        f"{groups} particle groups whose copies overlap the other groups' "

@@ -51,7 +51,8 @@ METRIC = "particle-steps/s with emission (plain table vs MLP sampler) at <=1% sp
 # KERNEL_SOURCES); reported as null once those sources change.
 KERNEL_SOURCES = ["paper_1409_5574_gb300/csrc/push_emit.cu",
                   "paper_1409_5574_gb300/csrc/prad_internal.h",
-                  "paper_1409_5574_gb300/csrc/mlp_device.cuh"]
+                  "paper_1409_5574_gb300/csrc/mlp_device.cuh",
+                  "paper_1409_5574_gb300/csrc/spec.cu"]
 NCU_TRAFFIC = {
     "src_sha256": "83bbab324b439f0d653bad57a7178609f7f425ef14e6f634bd03dce2339ca4da",
     "fused": 12565420672,  # mean bytes per launch over the 4 launches of one bench step
@@ -98,7 +99,36 @@ def parse():
     ap.add_argument("--no-stream", action="store_true",
                     help="skip the one-step launches (roofline_stream)")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--no-specialize", action="store_true",
+                    help="run the compiled-in kernels only (no run-time specialisation)")
     return ap.parse_args()
+
+
+# Run-time specialisation of the standard plane-wave kernels (prad_config.
+# specialize): on unless --no-specialize or NVRTC cannot provide the kernels
+# on this machine (then the compiled-in kernels run and the reason is
+# reported).
+SPEC = {"on": True, "error": None}
+
+
+def spec_probe(prad, W, torch):
+    """Compile and run one specialised launch; on failure turn it off."""
+    if not SPEC["on"]:
+        return
+    wl = W.plane_wave(a0=100.0, n=1024, periods=1, seed=3)
+    try:
+        ctx = prad.Context(wl.problem_kwargs(), precision=prad.PRAD_FP32,
+                           photon_capacity=1 << 16, max_particles=wl.n, steps_per_launch=2,
+                           specialize=True)
+        try:
+            ctx.push_emit(ctx.to_device(wl.state), 2, t0=0)
+            torch.cuda.synchronize()
+            if ctx.energy_budget()[2]["spec_launches"] != 1:
+                raise RuntimeError("the launch did not run the specialised kernel")
+        finally:
+            ctx.close()
+    except (prad.PradError, RuntimeError) as e:
+        SPEC["on"], SPEC["error"] = False, str(e)[:300]
 
 
 # ---------------------------------------------------------------- clocks
@@ -331,7 +361,7 @@ def planewave_20_periods(prad, W, torch, rank, peaks, nsm):
     wls = [W.plane_wave(a0=a0, n=n, periods=20, seed=1 + 97 * rank) for a0 in (100.0, 300.0, 500.0)]
     ctx = prad.Context(wls[0].problem_kwargs(), precision=prad.PRAD_FP32,
                        photon_capacity=int(0.12 * n * nsteps) + (1 << 20), max_particles=n,
-                       steps_per_launch=nsub)
+                       steps_per_launch=nsub, specialize=SPEC["on"])
     init = [ctx.to_device(w.state) for w in wls]
     work = {k: torch.empty_like(v) for k, v in init[0].items()}
 
@@ -465,7 +495,8 @@ def roofline_stream(prad, W, torch, rank, peaks, a0):
     ns = 1 << 24
     wl_s = W.plane_wave(a0=a0, n=ns, periods=1, seed=5 + rank)
     ctx_s = prad.Context(wl_s.problem_kwargs(), precision=prad.PRAD_FP32,
-                         photon_capacity=ns * 4, max_particles=ns, steps_per_launch=1)
+                         photon_capacity=ns * 4, max_particles=ns, steps_per_launch=1,
+                         specialize=SPEC["on"])
     st_s = ctx_s.to_device(wl_s.state)
     ctx_s.push_emit(st_s, 4, t0=0)
     ctx_s.drain()
@@ -522,9 +553,11 @@ def run_prad(args):
     # photon buffer: the records of one launch (at most ~0.07 per particle-step
     # with the table sampler in the first launch at a0 = 500)
     cap = int(0.10 * n * nsub) + (1 << 20)
+    SPEC["on"] = not args.no_specialize
+    spec_probe(prad, W, torch)
     ctx = prad.Context(wl.problem_kwargs(), precision=prad.PRAD_FP32, photon_capacity=cap,
                        max_particles=n, steps_per_launch=nsub, block_size=args.block,
-                       blocks_per_sm=args.bps)
+                       blocks_per_sm=args.bps, specialize=SPEC["on"])
     init = ctx.to_device(wl.state)
     work = {k: torch.empty_like(v) for k, v in init.items()}
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -584,6 +617,7 @@ def run_prad(args):
     lt = []
     run_once(ctx, lt)
     per_launch_s = sum(lt) / len(lt)
+    spec_launches = ctx.energy_budget()[2]["spec_launches"]
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     # The fused kernel keeps the particle in registers for nsub steps, so it
     # is bound by issue of FP32/INT32 arithmetic: peak = SMs x 128 lanes x
@@ -600,7 +634,8 @@ def run_prad(args):
                 "frac": achieved / alu_peak,
                 "traffic": ncu_traffic("fused", n == 1 << 26 and nsub == 100 and nsteps == 400
                                        and args.a0 == 500.0),
-                "kernel": "k_push_emit<float, PLANE_WAVE, TABLE, STD>",
+                "kernel": "k_push_emit<float, PLANE_WAVE, TABLE, STD>"
+                          + (" specialised at run time" if SPEC["on"] else ""),
                 "launch": f"{n} particles x {nsub} steps",
                 "launch_ms": [round(1e3 * v, 3) for v in lt],
                 "ops_per_particle_step": alg_ops,
@@ -800,7 +835,11 @@ def run_prad(args):
                                  f"{n * 28 / 1e9:.1f} GB state is larger than L2",
                            "photon_records_per_step": records / args.steps,
                            "dropped": dropped,
-                           "parallelism": f"independent particles, {ws} GPU(s)"},
+                           "parallelism": f"independent particles, {ws} GPU(s)",
+                           "kernels": ("specialised at run time (NVRTC, the run's constants "
+                                       "compiled in)" if SPEC["on"] else "compiled-in"),
+                           "specialize_error": SPEC["error"],
+                           "spec_launches": spec_launches},
                 "roofline": roofline, "roofline_stream": stream_rl,
                 "mlp_sampler": mlp, "photon_drain": photon_drain,
                 "other_workloads": others, "cpu_baseline": cb, "e2e": e2e,

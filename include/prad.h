@@ -35,7 +35,9 @@
 #ifndef PRAD_H
 #define PRAD_H
 
+#ifndef __CUDACC_RTC__
 #include <stdint.h>
+#endif
 
 #ifdef __cplusplus
 extern "C" {
@@ -109,7 +111,15 @@ typedef struct prad_config {
    * k w / select_prob.  Both keep the expected emission unchanged. */
   int32_t n_try;
   int32_t diagnostics;      /* bit mask of PRAD_DIAG_*                        */
-  int32_t pad0;
+  int32_t specialize;       /* 1 = run the standard FP32 plane-wave step (table
+                               sampler, no control or diagnostics) through
+                               kernels compiled at run time by NVRTC with this
+                               context's constants (time step, wave, Philox
+                               key ...) as literals: the same results, fewer
+                               loads.  Each variant is compiled (~0.3 s) at its
+                               first launch; prad_push_emit fails with
+                               PRAD_ERR_CUDA if NVRTC or the driver cannot
+                               provide it.  0 = compiled-in kernels only.  */
   double select_prob;
 } prad_config;
 
@@ -184,7 +194,8 @@ typedef struct prad_stats {
                          * outside the ledger; bit 2 a bounded tensor-core
                          * wait of the learned sampler ran out (the block
                          * stopped; its remaining records keep energy 0)   */
-  int32_t pad0;
+  int32_t spec_launches; /* launches through run-time specialised kernels
+                          * since init (saturates at INT32_MAX)            */
   int64_t wiggler_invalid; /* PRAD_DIAG_WIGGLER: steps outside the regime  */
 } prad_stats;
 

@@ -3,6 +3,7 @@ parallel, then a shared-library link.  Output: paper_1409_5574_gb300/_build/."""
 from __future__ import annotations
 
 import os
+import shutil
 import subprocess
 import sys
 from concurrent.futures import ThreadPoolExecutor
@@ -23,6 +24,45 @@ NVCC_FLAGS = [
 def _nvcc() -> str:
     cand = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "bin", "nvcc")
     return cand if os.path.exists(cand) else "nvcc"
+
+
+# The kernel translation unit the run-time specialisation compiles with
+# NVRTC (spec.cu), then the headers it includes, by their include names.
+SPEC_SOURCES = [os.path.join(CSRC, "push_emit.cu"), os.path.join(CSRC, "prad_internal.h"),
+                os.path.join(CSRC, "mlp_device.cuh"), os.path.join(CSRC, "rtc_prelude.h"),
+                os.path.join(ROOT, "include", "prad.h")]
+
+
+def _write_spec_sources(out: str) -> str:
+    """Embed SPEC_SOURCES as raw string literals; rewritten only on change."""
+    names, texts = [], []
+    for path in SPEC_SOURCES:
+        with open(path) as f:
+            text = f.read()
+        assert ")PRADSRC" not in text
+        names.append(os.path.basename(path))
+        texts.append(text)
+    body = "static const char* const kSpecSrcName[] = {%s};\n" % ", ".join(
+        '"%s"' % n for n in names)
+    body += "static const char* const kSpecSrc[] = {\n%s};\n" % ",\n".join(
+        'R"PRADSRC(%s)PRADSRC"' % t for t in texts)
+    inc = os.path.join(out, "prad_spec_sources.inc")
+    old = None
+    if os.path.exists(inc):
+        with open(inc) as f:
+            old = f.read()
+    if old != body:
+        with open(inc, "w") as f:
+            f.write(body)
+    return inc
+
+
+def _spec_flags(nvcc: str, out: str) -> list:
+    """spec.cu: the generated sources and where NVRTC and the CUDA headers are."""
+    path = nvcc if os.path.isabs(nvcc) else (shutil.which(nvcc) or nvcc)
+    home = os.path.dirname(os.path.dirname(os.path.realpath(path)))
+    return ["-I", out, '-DPRAD_CUDA_INCLUDE="%s"' % os.path.join(home, "include"),
+            '-DPRAD_CUDA_LIBDIR="%s"' % os.path.join(home, "lib64")]
 
 
 def sources() -> list:
@@ -48,11 +88,15 @@ def build(verbose: bool = False, extra_flags: list | None = None,
     headers.append(os.path.join(ROOT, "include", "prad.h"))
     flags = NVCC_FLAGS + (extra_flags or [])
     nvcc = _nvcc()
+    spec_inc = _write_spec_sources(out)
     jobs = []
     for src in sources():
         obj = os.path.join(out, os.path.basename(src)[:-3] + ".o")
-        if _stale(obj, [src] + headers) or extra_flags:
-            jobs.append([nvcc] + flags + ["-c", src, "-o", obj])
+        deps, f = [src] + headers, flags
+        if os.path.basename(src) == "spec.cu":
+            deps, f = deps + [spec_inc], flags + _spec_flags(nvcc, out)
+        if _stale(obj, deps) or extra_flags:
+            jobs.append([nvcc] + f + ["-c", src, "-o", obj])
 
     def run(cmd):
         if verbose:
@@ -71,7 +115,7 @@ def build(verbose: bool = False, extra_flags: list | None = None,
         # static cudart: the library loads without a CUDA runtime on the
         # loader path and shares the device's primary context with torch
         run([nvcc, "-shared", "-gencode", "arch=compute_103a,code=sm_103a",
-             "-cudart", "static", "-o", tmp] + objs)
+             "-cudart", "static", "-o", tmp] + objs + ["-ldl"])
         os.replace(tmp, lib)
     return lib
 

@@ -21,12 +21,17 @@
 // arithmetic (tanh.approx.f16x2), within ~1 f16 ulp of f16(silu(z)).
 #pragma once
 
+#ifdef __CUDACC_RTC__
+#include "rtc_prelude.h"
+#endif
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#ifndef __CUDACC_RTC__
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include <cstddef>
+#endif
 
 namespace prad {
 

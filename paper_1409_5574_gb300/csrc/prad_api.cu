@@ -5,6 +5,7 @@
 
 #include <cmath>
 #include <cstdarg>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -88,6 +89,9 @@ struct prad_ctx {
   // captured CUDA graph of the last batch call shape
   cudaGraphExec_t graph_exec = nullptr;
   uint64_t graph_key = 0;
+  // run-time specialised step kernels (prad_config.specialize)
+  SpecCache* spec = nullptr;
+  int64_t spec_launches = 0;
 };
 
 namespace {
@@ -536,6 +540,23 @@ int check_sort_args(prad_ctx* c, const prad_particles* pp, int64_t n) {
   return PRAD_OK;
 }
 
+// The run-time specialised kernel a float launch runs (*f = nullptr when the
+// context does not ask for one or the launch is not of the standard
+// plane-wave configuration); PRAD_ERR_CUDA when it cannot be compiled.
+int spec_for(prad_ctx* c, const StepParams<float>& p, const SpecFn** f) {
+  *f = nullptr;
+  int pf = 0, pws = 0;
+  if (!c->cfg.specialize || !push_emit_std_pw(p, c->fields.kind, c->cfg.sampler, &pf, &pws))
+    return PRAD_OK;
+  if (!c->spec) c->spec = spec_create();
+  char msg[448] = {0};
+  const cudaError_t e = spec_get(c->spec, c->device, p, pf, pws, f, msg, sizeof(msg));
+  if (e != cudaSuccess)
+    return fail(c, PRAD_ERR_CUDA, "push_emit: run-time specialisation: %s (%s)", msg,
+                cudaGetErrorString(e));
+  return PRAD_OK;
+}
+
 template <typename R>
 int push_emit_t(prad_ctx* c, const prad_particles* pp, int64_t n,
                 int32_t nsteps) {
@@ -601,8 +622,15 @@ int push_emit_t(prad_ctx* c, const prad_particles* pp, int64_t n,
   const int sub_eff = sub < nsteps ? sub : nsteps;
   // persistent grid: at most the resident blocks of the kernel variant, so
   // no block waits for a second wave (blocks_per_sm = 0: all of them)
-  const int occ = push_emit_occupancy<R>(p, c->fields.kind, c->cfg.sampler, sub_eff, block,
-                                         ctrl_of(c));
+  const SpecFn* spec = nullptr;
+  if constexpr (sizeof(R) == 4) {
+    p.nsub = sub_eff;
+    const int rc = spec_for(c, p, &spec);
+    if (rc != PRAD_OK) return rc;
+  }
+  const int occ = spec ? spec_occupancy(spec, block)
+                       : push_emit_occupancy<R>(p, c->fields.kind, c->cfg.sampler, sub_eff,
+                                                block, ctrl_of(c));
   const int bps = c->cfg.blocks_per_sm > 0 && c->cfg.blocks_per_sm < occ ? c->cfg.blocks_per_sm
                                                                          : occ;
   const int64_t want = (n + block - 1) / block;
@@ -615,6 +643,18 @@ int push_emit_t(prad_ctx* c, const prad_particles* pp, int64_t n,
     p.nsub = m;
     // wave phase at the launch's first step (modulo one cycle)
     p.phase_t0 = phase0 + static_cast<uint64_t>(p.t0) * p.phase_step;
+    if constexpr (sizeof(R) == 4) {
+      if (spec) {
+        const int rc = spec_for(c, p, &spec);  // the variant of this launch's nsub
+        if (rc != PRAD_OK) return rc;
+      }
+      if (spec) {
+        CK(c, spec_launch(spec, p, grid, block, c->stream));
+        ++c->spec_launches;
+        done += m;
+        continue;
+      }
+    }
     CK(c, launch_push_emit<R>(p, c->fields.kind, c->cfg.sampler, grid, block, c->stream));
     done += m;
   }
@@ -649,6 +689,8 @@ int prad_init(prad_ctx** out, const prad_config* cfg) {
     return fail(nullptr, PRAD_ERR_ARG, "prad_init: block_size must be a multiple of 32 <= 256");
   if (cfg->steps_per_launch < 0 || cfg->blocks_per_sm < 0 || cfg->sort_interval < 0)
     return fail(nullptr, PRAD_ERR_ARG, "prad_init: negative launch parameter");
+  if (cfg->specialize != 0 && cfg->specialize != 1)
+    return fail(nullptr, PRAD_ERR_ARG, "prad_init: specialize must be 0 or 1");
   if (cfg->n_try < 0 || cfg->n_try > 65535)
     return fail(nullptr, PRAD_ERR_ARG, "prad_init: n_try outside [0, 65535]");
   if (cfg->n_try > 1 && cfg->sampler != PRAD_SAMPLER_TABLE)
@@ -742,6 +784,7 @@ int prad_destroy(prad_ctx* c) {
   if (!c) return PRAD_OK;
   free_sort(c->sort);
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  spec_destroy(c->spec);
   cudaFree(c->d_batch);
   cudaFree(c->d_batch_off);
   cudaFree(c->d_batch_next);
@@ -918,7 +961,8 @@ int prad_energy_budget(prad_ctx* c, double* emitted, double* rr_loss, prad_stats
     s->mlp_fallback = static_cast<int64_t>(cnt[kMlpFallback]);
     s->wiggler_invalid = static_cast<int64_t>(cnt[kWiggler]);
     s->status = static_cast<int32_t>(cnt[kStatus]);
-    s->pad0 = 0;
+    s->spec_launches = c->spec_launches < INT32_MAX ? static_cast<int32_t>(c->spec_launches)
+                                                    : INT32_MAX;
   }
   return s && s->nan_frozen > 0 ? PRAD_WARN_NAN : PRAD_OK;
 }

@@ -2,8 +2,12 @@
 // translation units.  Nothing here is part of the public C ABI.
 #pragma once
 
+#ifdef __CUDACC_RTC__
+#include "rtc_prelude.h"
+#else
 #include <cuda_runtime.h>
 #include <stdint.h>
+#endif
 
 #include "prad.h"  // include/ is on the include path
 #include "mlp_device.cuh"
@@ -188,6 +192,7 @@ inline void philox_round_keys(uint64_t seed, uint32_t* rk) {
   }
 }
 
+#ifndef __CUDACC_RTC__
 // Launchers (defined in the kernel translation units).
 // std_cfg: the standard configuration (LL kick applied, field form of H_eff)
 // in every ensemble, which selects the variant with those modes fixed at
@@ -264,5 +269,26 @@ cudaError_t launch_ginv_eval(const float* tab, const float* r, float* out, int64
 cudaError_t launch_ledger_reduce(const double* a, const double* b, int64_t n,
                                  double* partials, int nblocks, double* out,
                                  cudaStream_t s);
+
+// Run-time specialised kernels (spec.cu): the standard FP32 plane-wave
+// k_push_emit variants compiled by NVRTC with the context's constants as
+// literals.  spec_get returns the kernel for prefetch mode pf and sign
+// variant pws, compiling it on first use (an error, with a message in msg,
+// when NVRTC or the driver cannot provide it).
+struct SpecFn;
+struct SpecCache;
+SpecCache* spec_create();
+void spec_destroy(SpecCache* c);
+cudaError_t spec_get(SpecCache* c, int device, const StepParams<float>& p, int pf, int pws,
+                     const SpecFn** out, char* msg, size_t msg_len);
+int spec_occupancy(const SpecFn* f, int block);
+cudaError_t spec_launch(const SpecFn* f, const StepParams<float>& p, int grid, int block,
+                        cudaStream_t s);
+// Whether a launch with these parameters runs the standard plane-wave
+// kernel (FP32 push, table sampler, no control or diagnostics), and if so
+// its prefetch mode and sign variant.
+bool push_emit_std_pw(const StepParams<float>& p, int field_kind, int sampler, int* pf, int* pws);
+
+#endif  // __CUDACC_RTC__
 
 }  // namespace prad

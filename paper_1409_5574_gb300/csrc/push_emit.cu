@@ -7,10 +7,12 @@
 // in registers between substeps and is read and written once per launch
 // (SoA, fully coalesced 4- or 8-byte accesses).  The grid is a multiple of the
 // SM count and strides over the particles.
+#ifndef __CUDACC_RTC__
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include <type_traits>
+#endif
 
 
 #include "mlp_device.cuh"
@@ -1126,6 +1128,7 @@ struct MinBlocks {
       sizeof(R) == 8 ? 1 : (FIELD == PRAD_FIELD_YEE2D ? 4 : PRAD_F32_MINB);
 };
 
+#ifndef __CUDACC_RTC__
 // Resident blocks per SM of a kernel at this block size and dynamic shared
 // memory (1 if the query fails).
 template <typename K>
@@ -1135,16 +1138,52 @@ int occupancy_of(K kernel, int block, size_t dyn) {
     return 1;
   return nb > 0 ? nb : 1;
 }
+#endif  // __CUDACC_RTC__
 
 #ifndef PRAD_PF_MINB
 #define PRAD_PF_MINB 4
+#endif
+
+#ifdef PRAD_SPEC
+// Run-time specialisation (a kernel compiled by NVRTC for one context): the
+// per-run constants of the standard plane-wave step -- the normalised time
+// step and charge factors, the radiation coefficients of Eqs. (1), (4) and
+// (7), the wave's amplitude, wavenumber and phase increment, the ensemble and
+// the Philox round keys -- given as literals, so that they fold into the
+// arithmetic instead of being read from the kernel's parameter space.  The
+// values are those the host would pass, so the results are the same bits.
+template <typename R>
+__device__ __forceinline__ StepParams<R> spec_params(const StepParams<R>& in) {
+  static_assert(sizeof(R) == 4, "run-time specialisation: FP32 kernels only");
+  StepParams<R> p = in;
+  p.half_q_dtn = PRAD_SPEC_HALF_Q_DTN;
+  p.dtn = PRAD_SPEC_DTN;
+  p.inv_dtn = PRAD_SPEC_INV_DTN;
+  p.cn_dt = PRAD_SPEC_CN_DT;
+  p.eps_r15 = PRAD_SPEC_EPS_R15;
+  p.ll_coef = PRAD_SPEC_LL_COEF;
+  p.E0 = PRAD_SPEC_E0;
+  p.kc = PRAD_SPEC_KC;
+  p.kc_lo = PRAD_SPEC_KC_LO;
+  p.phase_step = PRAD_SPEC_PHASE_STEP;
+  p.ensemble = PRAD_SPEC_ENSEMBLE;
+  constexpr uint32_t rk[20] = PRAD_SPEC_RKEY;
+#pragma unroll
+  for (int k = 0; k < 20; ++k) p.rkey[k] = rk[k];
+  return p;
+}
 #endif
 // PF: 0 no prefetch (multi-step launches); 1 one step per launch, the next
 // particle prefetched; 2 the same for a dense launch (see dense_launch).
 // PWS: the plane wave's signs at compile time (0: from the parameters).
 template <typename R, int FIELD, int SAMP, int PF, bool CTRL, bool STD = false, int PWS = 0>
 __global__ void __launch_bounds__(256, (PF ? PRAD_PF_MINB : MinBlocks<R, FIELD, SAMP>::value))
-    k_push_emit(const StepParams<R> P) {
+    k_push_emit(const StepParams<R> P_arg) {
+#ifdef PRAD_SPEC
+  const StepParams<R> P = spec_params(P_arg);
+#else
+  const StepParams<R>& P = P_arg;
+#endif
   constexpr bool kSTab = kSharedTab<R, SAMP, PF, CTRL>;
   using Stage = typename std::conditional<kSTab, PhotonStageRec,
                                           PhotonStageT<SAMP != PRAD_SAMPLER_TABLE || !CTRL>>::type;
@@ -1292,6 +1331,7 @@ __global__ void __launch_bounds__(256, PRAD_BATCH_MINB)
     atomicAdd(bp.busy + blockIdx.x, static_cast<unsigned long long>(clock64() - t_begin));
 }
 
+#ifndef __CUDACC_RTC__
 // std_cfg: every ensemble runs the standard configuration (STD variant, the
 // same per-step code as the standard k_push_emit variants)
 template <int SAMP>
@@ -1335,6 +1375,7 @@ int batch_max_blocks_per_sm(int block, int sampler, bool ctrl, bool std_cfg) {
   }
 }
 
+#endif  // __CUDACC_RTC__
 // ---------------------------------------------------------------------------
 // Tile-sorted Yee kernel: one block per work item (a chunk of <= kChunk
 // particles of one tile).  The block stages the tile's six field components
@@ -1388,6 +1429,7 @@ __global__ void __launch_bounds__(256, 3) k_push_emit_tiled(const StepParams<R> 
   flush_counts(cnt, P.counters);
 }
 
+#ifndef __CUDACC_RTC__
 // The standard-configuration variant (STD) exists for FP32 without control
 // or diagnostics.
 template <typename R, int FIELD, bool CTRL>
@@ -1546,6 +1588,17 @@ int push_emit_occupancy(const StepParams<R>& p, int field_kind, int sampler, int
   }
 }
 template int push_emit_occupancy<float>(const StepParams<float>&, int, int, int, int, bool);
+
+bool push_emit_std_pw(const StepParams<float>& p, int field_kind, int sampler, int* pf,
+                      int* pws) {
+  const bool ctrl = p.ntry > 1 || p.sel_q < 1.0f || p.diag != 0;
+  if (field_kind != PRAD_FIELD_PLANE_WAVE || sampler != PRAD_SAMPLER_TABLE || ctrl ||
+      !std_config(p, 3))
+    return false;
+  *pf = p.nsub == 1 ? (dense_launch(p) ? 2 : 1) : 0;
+  *pws = pw_signs(p);
+  return true;
+}
 template int push_emit_occupancy<double>(const StepParams<double>&, int, int, int, int, bool);
 
 template <typename R>
@@ -1614,4 +1667,5 @@ template cudaError_t launch_push_emit_tiled<double>(const StepParams<double>&, i
 template cudaError_t launch_eval_sampler<float>(const StepParams<float>&, const uint32_t*, float*, float*, int64_t, cudaStream_t);
 template cudaError_t launch_eval_sampler<double>(const StepParams<double>&, const uint32_t*, double*, double*, int64_t, cudaStream_t);
 
+#endif  // __CUDACC_RTC__
 }  // namespace prad

@@ -42,7 +42,7 @@ class prad_config(ctypes.Structure):
                 ("max_particles", _i64), ("stream", _vp), ("block_size", _i32),
                 ("blocks_per_sm", _i32), ("sort_interval", _i32), ("batch_chunk", _i32),
                 ("use_graph", _i32), ("n_try", _i32), ("diagnostics", _i32),
-                ("pad0", _i32), ("select_prob", _dbl)]
+                ("specialize", _i32), ("select_prob", _dbl)]
 
 
 class prad_fields(ctypes.Structure):
@@ -77,7 +77,7 @@ class prad_photons(ctypes.Structure):
 class prad_stats(ctypes.Structure):
     _fields_ = [("records", _i64), ("dropped", _i64), ("dn_gt1", _i64),
                 ("clamped", _i64), ("chi_gt1", _i64), ("mlp_fallback", _i64),
-                ("nan_frozen", _i64), ("status", _i32), ("pad0", _i32),
+                ("nan_frozen", _i64), ("status", _i32), ("spec_launches", _i32),
                 ("wiggler_invalid", _i64)]
 
 
@@ -314,7 +314,7 @@ class Context:
                  blocks_per_sm: int = 0, sampler: int = PRAD_SAMPLER_TABLE,
                  ensemble: int = 0, sort_interval: int = 0, batch_chunk: int = 0,
                  use_graph: bool = False, n_try: int = 1, select_prob: float = 1.0,
-                 diagnostics: int = 0):
+                 diagnostics: int = 0, specialize: bool = False):
         torch = _torch()
         if not torch.cuda.is_available():
             raise RuntimeError("prad needs a CUDA device")
@@ -345,6 +345,7 @@ class Context:
         cfg.n_try = n_try
         cfg.select_prob = select_prob
         cfg.diagnostics = diagnostics
+        cfg.specialize = int(specialize)
         self.cfg = cfg
         self.capacity = photon_capacity
         self.max_particles = max_particles

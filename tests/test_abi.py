@@ -45,8 +45,10 @@ def test_ctypes_layout_matches_c():
                "prad_ensemble", "prad_tuning"]
     body = "".join(f'printf("%zu\\n", sizeof({s}));' for s in structs)
     offs = [("prad_config", "stream"), ("prad_config", "blocks_per_sm"),
-            ("prad_config", "use_graph"), ("prad_fields", "yee"), ("prad_fields", "y0"),
+            ("prad_config", "use_graph"), ("prad_config", "specialize"),
+            ("prad_config", "select_prob"), ("prad_fields", "yee"), ("prad_fields", "y0"),
             ("prad_particles", "pid"), ("prad_particles", "t0"), ("prad_stats", "status"),
+            ("prad_stats", "spec_launches"), ("prad_stats", "wiggler_invalid"),
             ("prad_ensemble", "field"), ("prad_ensemble", "ensemble"),
             ("prad_tuning", "particle_steps_per_s")]
     body += "".join(f'printf("%zu\\n", offsetof({s}, {f}));' for s, f in offs)
@@ -84,6 +86,10 @@ def test_argument_errors_without_gpu(lib):
     bad = prad.prad_config.from_buffer_copy(cfg)
     bad.block_size = 100
     assert lib.prad_init(ctypes.byref(h), ctypes.byref(bad)) == prad.PRAD_ERR_ARG
+    bad = prad.prad_config.from_buffer_copy(cfg)
+    bad.specialize = 2
+    assert lib.prad_init(ctypes.byref(h), ctypes.byref(bad)) == prad.PRAD_ERR_ARG
+    assert b"specialize" in lib.prad_last_error(None)
     assert lib.prad_push_emit(None, None, 1, 1) == prad.PRAD_ERR_ARG
     assert lib.prad_destroy(None) == prad.PRAD_OK
     try:

@@ -1,0 +1,118 @@
+"""Run-time specialised step kernels (prad_config.specialize = 1) against
+the ahead-of-time kernels, through the C ABI.
+
+The specialised kernels are the same source compiled by NVRTC with the
+context's constants as literals, so for every launch form they select
+(fused multi-step launches; one-step launches, dense and with explicit
+ids; the four plane-wave sign variants; a different seed, ensemble and
+field amplitude) the particle state, the photon records and the counters
+must be the same bits, and the per-particle ledgers the same up to the
+grouping of the FP64 atomic adds.  Launches outside the standard
+plane-wave configuration (another field, the LL ledger mode, FP64) keep
+the ahead-of-time kernels.
+"""
+import numpy as np
+import pytest
+
+from paper_1409_5574_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if torch.cuda.is_available():
+    from paper_1409_5574_gb300 import prad
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    prad.load_library()
+
+
+def _run(wl, nsteps, steps_per_launch, specialize, with_pid=False, precision=None, **kw):
+    precision = prad.PRAD_FP32 if precision is None else precision
+    ctx = prad.Context(wl.problem_kwargs(), precision=precision, photon_capacity=1 << 20,
+                       max_particles=wl.n, steps_per_launch=steps_per_launch,
+                       specialize=specialize, **kw)
+    st = ctx.to_device(wl.state, with_pid=with_pid)
+    ctx.push_emit(st, nsteps, t0=5)
+    torch.cuda.synchronize()
+    ph = ctx.photons(on_device=False)
+    e, l, stats = ctx.energy_budget()
+    le, ll = ctx.ledger()
+    out = dict(state={k: v.cpu().numpy().copy() for k, v in st.items() if k != "pid"},
+               ph={k: (v.numpy().copy() if hasattr(v, "numpy") else v) for k, v in ph.items()},
+               e=e, l=l, stats=stats, le=le.cpu().numpy(), ll=ll.cpu().numpy())
+    ctx.close()
+    return out
+
+
+def _photon_table(ph):
+    key = ph["pid"].astype(np.int64) * 2**32 + ph["step"].astype(np.int64)
+    names = ("x", "y", "z", "nx", "ny", "nz", "eps", "weight")
+    o = np.lexsort(tuple(ph[k] for k in reversed(names)) + (key,))
+    return key[o], np.stack([ph[k][o] for k in names], 1)
+
+
+def _same(a, b):
+    for k in a["state"]:
+        np.testing.assert_array_equal(a["state"][k], b["state"][k], err_msg=k)
+    np.testing.assert_allclose(a["le"], b["le"], rtol=1e-13, atol=0)
+    np.testing.assert_allclose(a["ll"], b["ll"], rtol=1e-13, atol=0)
+    ka, ta = _photon_table(a["ph"])
+    kb, tb = _photon_table(b["ph"])
+    np.testing.assert_array_equal(ka, kb)
+    np.testing.assert_array_equal(ta, tb)
+    for k in ("records", "dropped", "dn_gt1", "clamped", "chi_gt1", "nan_frozen", "status"):
+        assert a["stats"][k] == b["stats"][k], k
+
+
+def _wave(n=20000 + 37, a0=400.0, seed=11, hand=1, direction=-1):
+    wl = W.plane_wave(a0=a0, n=n, seed=seed)
+    wl.hand, wl.direction = hand, direction
+    wl.state["ux"] = wl.state["ux"] * direction
+    return wl
+
+
+@pytest.mark.parametrize("form", ["fused", "one_step", "one_step_pid"])
+def test_specialised_equals_compiled_in(form):
+    wl = _wave()
+    spl = 8 if form == "fused" else 1
+    pid = form == "one_step_pid"
+    base = _run(wl, 24, spl, False, with_pid=pid)
+    spec = _run(wl, 24, spl, True, with_pid=pid)
+    _same(base, spec)
+    assert base["stats"]["records"] > 1000
+    assert base["stats"]["spec_launches"] == 0
+    assert spec["stats"]["spec_launches"] == (3 if form == "fused" else 24)
+
+
+@pytest.mark.parametrize("hand,direction", [(1, 1), (-1, 1), (-1, -1)])
+def test_specialised_sign_variants(hand, direction):
+    wl = _wave(n=4096 + 5, a0=250.0, seed=3, hand=hand, direction=direction)
+    for spl in (1, 6):
+        _same(_run(wl, 12, spl, False), _run(wl, 12, spl, True))
+
+
+def test_specialised_other_constants():
+    """Another seed, ensemble and amplitude compile other literals; the
+    tail launch of 10 steps in launches of 4 (4, 4, 2) uses the fused form
+    throughout, and 9 steps in launches of 4 end with a one-step launch."""
+    wl = _wave(n=3000, a0=120.0, seed=77)
+    wl.seed = 987654321
+    for nsteps in (10, 9):
+        a = _run(wl, nsteps, 4, False, ensemble=5)
+        b = _run(wl, nsteps, 4, True, ensemble=5)
+        _same(a, b)
+        assert b["stats"]["spec_launches"] == 3
+
+
+def test_outside_the_standard_configuration_keeps_compiled_in_kernels():
+    wl = _wave(n=2048)
+    wl.rr_mode = W.RR_LEDGER  # LL kick booked, not applied: not the standard form
+    a = _run(wl, 6, 3, True)
+    assert a["stats"]["spec_launches"] == 0
+    _same(_run(wl, 6, 3, False), a)
+    b = _run(_wave(n=2048), 4, 1, True, precision=prad.PRAD_FP64)
+    assert b["stats"]["spec_launches"] == 0

@@ -111,7 +111,7 @@ typedef struct prad_config {
    * k w / select_prob.  Both keep the expected emission unchanged. */
   int32_t n_try;
   int32_t diagnostics;      /* bit mask of PRAD_DIAG_*                        */
-  int32_t specialize;       /* 1 = run the standard FP32 plane-wave step (table
+  int32_t specialize;       /* 1 = run the standard FP32 plane-wave step (any
                                sampler, no control or diagnostics) through
                                kernels compiled at run time by NVRTC with this
                                context's constants (time step, wave, Philox

@@ -550,7 +550,8 @@ int spec_for(prad_ctx* c, const StepParams<float>& p, const SpecFn** f) {
     return PRAD_OK;
   if (!c->spec) c->spec = spec_create();
   char msg[448] = {0};
-  const cudaError_t e = spec_get(c->spec, c->device, p, pf, pws, f, msg, sizeof(msg));
+  const cudaError_t e =
+      spec_get(c->spec, c->device, p, c->cfg.sampler, pf, pws, f, msg, sizeof(msg));
   if (e != cudaSuccess)
     return fail(c, PRAD_ERR_CUDA, "push_emit: run-time specialisation: %s (%s)", msg,
                 cudaGetErrorString(e));

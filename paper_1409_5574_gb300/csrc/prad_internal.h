@@ -272,21 +272,21 @@ cudaError_t launch_ledger_reduce(const double* a, const double* b, int64_t n,
 
 // Run-time specialised kernels (spec.cu): the standard FP32 plane-wave
 // k_push_emit variants compiled by NVRTC with the context's constants as
-// literals.  spec_get returns the kernel for prefetch mode pf and sign
-// variant pws, compiling it on first use (an error, with a message in msg,
-// when NVRTC or the driver cannot provide it).
+// literals.  spec_get returns the kernel for sampler samp, prefetch mode pf
+// and sign variant pws, compiling it on first use (an error, with a message
+// in msg, when NVRTC or the driver cannot provide it).
 struct SpecFn;
 struct SpecCache;
 SpecCache* spec_create();
 void spec_destroy(SpecCache* c);
-cudaError_t spec_get(SpecCache* c, int device, const StepParams<float>& p, int pf, int pws,
-                     const SpecFn** out, char* msg, size_t msg_len);
+cudaError_t spec_get(SpecCache* c, int device, const StepParams<float>& p, int samp, int pf,
+                     int pws, const SpecFn** out, char* msg, size_t msg_len);
 int spec_occupancy(const SpecFn* f, int block);
 cudaError_t spec_launch(const SpecFn* f, const StepParams<float>& p, int grid, int block,
                         cudaStream_t s);
 // Whether a launch with these parameters runs the standard plane-wave
-// kernel (FP32 push, table sampler, no control or diagnostics), and if so
-// its prefetch mode and sign variant.
+// kernel (FP32 push, no control or diagnostics), and if so its prefetch mode
+// and sign variant.
 bool push_emit_std_pw(const StepParams<float>& p, int field_kind, int sampler, int* pf, int* pws);
 
 #endif  // __CUDACC_RTC__

@@ -1147,8 +1147,8 @@ int occupancy_of(K kernel, int block, size_t dyn) {
 #ifdef PRAD_SPEC
 // Run-time specialisation (a kernel compiled by NVRTC for one context): the
 // per-run constants of the standard plane-wave step -- the normalised time
-// step and charge factors, the radiation coefficients of Eqs. (1), (4) and
-// (7), the wave's amplitude, wavenumber and phase increment, the ensemble and
+// step and charge factors, the radiation coefficients of Eqs. (1), (4), (7)
+// and (13), the wave's amplitude, wavenumber and phase increment, the ensemble and
 // the Philox round keys -- given as literals, so that they fold into the
 // arithmetic instead of being read from the kernel's parameter space.  The
 // values are those the host would pass, so the results are the same bits.
@@ -1165,6 +1165,7 @@ __device__ __forceinline__ StepParams<R> spec_params(const StepParams<R>& in) {
   p.E0 = PRAD_SPEC_E0;
   p.kc = PRAD_SPEC_KC;
   p.kc_lo = PRAD_SPEC_KC_LO;
+  p.cp_dt = PRAD_SPEC_CP_DT;
   p.phase_step = PRAD_SPEC_PHASE_STEP;
   p.ensemble = PRAD_SPEC_ENSEMBLE;
   constexpr uint32_t rk[20] = PRAD_SPEC_RKEY;
@@ -1592,10 +1593,9 @@ template int push_emit_occupancy<float>(const StepParams<float>&, int, int, int,
 bool push_emit_std_pw(const StepParams<float>& p, int field_kind, int sampler, int* pf,
                       int* pws) {
   const bool ctrl = p.ntry > 1 || p.sel_q < 1.0f || p.diag != 0;
-  if (field_kind != PRAD_FIELD_PLANE_WAVE || sampler != PRAD_SAMPLER_TABLE || ctrl ||
-      !std_config(p, 3))
-    return false;
-  *pf = p.nsub == 1 ? (dense_launch(p) ? 2 : 1) : 0;
+  if (field_kind != PRAD_FIELD_PLANE_WAVE || ctrl || !std_config(p, 3)) return false;
+  // (the learned samplers have no prefetching variant)
+  *pf = sampler != PRAD_SAMPLER_TABLE ? 0 : p.nsub == 1 ? (dense_launch(p) ? 2 : 1) : 0;
   *pws = pw_signs(p);
   return true;
 }

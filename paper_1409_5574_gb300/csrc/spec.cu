@@ -1,4 +1,5 @@
-// Run-time specialisation of the standard FP32 plane-wave step kernels.
+// Run-time specialisation of the standard FP32 plane-wave step kernels
+// (the table sampler and the learned samplers).
 //
 // The kernel source of push_emit.cu (embedded in the library at build time)
 // is compiled by NVRTC with -DPRAD_SPEC and the context's per-run constants
@@ -126,14 +127,14 @@ const Driver& driver() {
 
 // The constants a specialised kernel has compiled in, with its variant.
 struct SpecKey {
-  float half_q_dtn, dtn, inv_dtn, cn_dt, eps_r15, ll_coef, E0, kc, kc_lo;
+  float half_q_dtn, dtn, inv_dtn, cn_dt, eps_r15, ll_coef, E0, kc, kc_lo, cp_dt;
   uint64_t phase_step;
   uint32_t ensemble;
   uint32_t rkey[20];
-  int32_t pf, pws;
+  int32_t samp, pf, pws;
 };
 
-SpecKey key_of(const StepParams<float>& p, int pf, int pws) {
+SpecKey key_of(const StepParams<float>& p, int samp, int pf, int pws) {
   SpecKey k;
   std::memset(&k, 0, sizeof(k));
   k.half_q_dtn = p.half_q_dtn;
@@ -145,9 +146,11 @@ SpecKey key_of(const StepParams<float>& p, int pf, int pws) {
   k.E0 = p.E0;
   k.kc = p.kc;
   k.kc_lo = p.kc_lo;
+  k.cp_dt = p.cp_dt;
   k.phase_step = p.phase_step;
   k.ensemble = p.ensemble;
   std::memcpy(k.rkey, p.rkey, sizeof(k.rkey));
+  k.samp = samp;
   k.pf = pf;
   k.pws = pws;
   return k;
@@ -157,12 +160,12 @@ bool same(const SpecKey& a, const SpecKey& b) { return std::memcmp(&a, &b, sizeo
 
 // -D options carrying the constants: floats as exact hexadecimal literals
 bool spec_defines(const SpecKey& k, std::vector<std::string>& out) {
-  const float v[9] = {k.half_q_dtn, k.dtn, k.inv_dtn, k.cn_dt, k.eps_r15,
-                      k.ll_coef,    k.E0,  k.kc,      k.kc_lo};
-  const char* nm[9] = {"HALF_Q_DTN", "DTN", "INV_DTN", "CN_DT", "EPS_R15",
-                       "LL_COEF",    "E0",  "KC",      "KC_LO"};
+  const float v[10] = {k.half_q_dtn, k.dtn, k.inv_dtn, k.cn_dt, k.eps_r15,
+                       k.ll_coef,    k.E0,  k.kc,      k.kc_lo, k.cp_dt};
+  const char* nm[10] = {"HALF_Q_DTN", "DTN", "INV_DTN", "CN_DT", "EPS_R15",
+                        "LL_COEF",    "E0",  "KC",      "KC_LO", "CP_DT"};
   char buf[512];
-  for (int j = 0; j < 9; ++j) {
+  for (int j = 0; j < 10; ++j) {
     if (!std::isfinite(v[j])) return false;
     std::snprintf(buf, sizeof(buf), "-DPRAD_SPEC_%s=(%af)", nm[j], static_cast<double>(v[j]));
     out.emplace_back(buf);
@@ -214,9 +217,9 @@ void spec_destroy(SpecCache* c) {
 }
 
 namespace {
-cudaError_t spec_get_impl(SpecCache* c, int device, const StepParams<float>& p, int pf, int pws,
-                          const SpecFn** out, std::string* msg) {
-  const SpecKey key = key_of(p, pf, pws);
+cudaError_t spec_get_impl(SpecCache* c, int device, const StepParams<float>& p, int samp, int pf,
+                          int pws, const SpecFn** out, std::string* msg) {
+  const SpecKey key = key_of(p, samp, pf, pws);
   for (SpecFn* f : c->fns)
     if (same(f->key, key)) {
       *out = f;
@@ -242,8 +245,7 @@ cudaError_t spec_get_impl(SpecCache* c, int device, const StepParams<float>& p, 
   }
   char name[160];
   std::snprintf(name, sizeof(name), "prad::k_push_emit<float, %d, %d, %d, false, true, %d>",
-                static_cast<int>(PRAD_FIELD_PLANE_WAVE), static_cast<int>(PRAD_SAMPLER_TABLE),
-                pf, pws);
+                static_cast<int>(PRAD_FIELD_PLANE_WAVE), samp, pf, pws);
   constexpr int kNSrc = sizeof(kSpecSrc) / sizeof(kSpecSrc[0]);
   nvrtcProgram prog = nullptr;
   if (nv.create(&prog, kSpecSrc[0], kSpecSrcName[0], kNSrc - 1, kSpecSrc + 1, kSpecSrcName + 1) !=
@@ -296,11 +298,11 @@ cudaError_t spec_get_impl(SpecCache* c, int device, const StepParams<float>& p, 
 }
 }  // namespace
 
-cudaError_t spec_get(SpecCache* c, int device, const StepParams<float>& p, int pf, int pws,
-                     const SpecFn** out, char* msg, size_t msg_len) {
+cudaError_t spec_get(SpecCache* c, int device, const StepParams<float>& p, int samp, int pf,
+                     int pws, const SpecFn** out, char* msg, size_t msg_len) {
   *out = nullptr;
   std::string m;
-  const cudaError_t e = spec_get_impl(c, device, p, pf, pws, out, &m);
+  const cudaError_t e = spec_get_impl(c, device, p, samp, pf, pws, out, &m);
   if (e != cudaSuccess && msg && msg_len) std::snprintf(msg, msg_len, "%s", m.c_str());
   return e;
 }

@@ -5,7 +5,7 @@ The specialised kernels are the same source compiled by NVRTC with the
 context's constants as literals, so for every launch form they select
 (fused multi-step launches; one-step launches, dense and with explicit
 ids; the four plane-wave sign variants; a different seed, ensemble and
-field amplitude) the particle state, the photon records and the counters
+field amplitude; the learned samplers) the particle state, the photon records and the counters
 must be the same bits, and the per-particle ledgers the same up to the
 grouping of the FP64 atomic adds.  Launches outside the standard
 plane-wave configuration (another field, the LL ledger mode, FP64) keep
@@ -30,11 +30,14 @@ def _gpu():
     prad.load_library()
 
 
-def _run(wl, nsteps, steps_per_launch, specialize, with_pid=False, precision=None, **kw):
+def _run(wl, nsteps, steps_per_launch, specialize, with_pid=False, precision=None,
+         weights=None, **kw):
     precision = prad.PRAD_FP32 if precision is None else precision
     ctx = prad.Context(wl.problem_kwargs(), precision=precision, photon_capacity=1 << 20,
                        max_particles=wl.n, steps_per_launch=steps_per_launch,
                        specialize=specialize, **kw)
+    if weights is not None:
+        ctx.mlp_set_weights(weights)
     st = ctx.to_device(wl.state, with_pid=with_pid)
     ctx.push_emit(st, nsteps, t0=5)
     torch.cuda.synchronize()
@@ -106,6 +109,22 @@ def test_specialised_other_constants():
         b = _run(wl, nsteps, 4, True, ensemble=5)
         _same(a, b)
         assert b["stats"]["spec_launches"] == 3
+
+
+@pytest.mark.parametrize("sampler", ["mlp", "mlp_fallback"])
+def test_specialised_learned_sampler(sampler):
+    """The learned samplers' step kernels (records finished by the
+    tensor-core network) with any fixed weights: the same bits."""
+    from oracle import mlp as M
+    wts = M.glorot(11).astype(np.float32)
+    samp = prad.PRAD_SAMPLER_MLP if sampler == "mlp" else prad.PRAD_SAMPLER_MLP_FALLBACK
+    wl = _wave(n=8192 + 3, a0=500.0, seed=21)
+    a = _run(wl, 16, 8, False, sampler=samp, weights=wts)
+    b = _run(wl, 16, 8, True, sampler=samp, weights=wts)
+    _same(a, b)
+    assert a["stats"]["records"] > 1000
+    assert b["stats"]["spec_launches"] == 2
+    assert a["stats"]["mlp_fallback"] == b["stats"]["mlp_fallback"]
 
 
 def test_outside_the_standard_configuration_keeps_compiled_in_kernels():

@@ -1,6 +1,7 @@
 """The kernel source that run-time specialisation compiles with NVRTC
 (push_emit.cu and the headers it includes) compiles under NVRTC with the
-specialised constants, for the three launch forms, without a GPU.  The
+specialised constants, for the table sampler's three launch forms and the
+learned samplers, without a GPU.  The
 library embeds the same files at build time; this keeps them free of host
 code outside the __CUDACC_RTC__ guards."""
 import ctypes
@@ -31,14 +32,14 @@ DEFINES = [
     "-DPRAD_SPEC_INV_DTN=(0x1.fd4bbap+4f)", "-DPRAD_SPEC_CN_DT=(0x1.09113p-14f)",
     "-DPRAD_SPEC_EPS_R15=(0x1.314cecp-18f)", "-DPRAD_SPEC_LL_COEF=(0x1.fda8d4p-32f)",
     "-DPRAD_SPEC_E0=(0x1.f4p+8f)", "-DPRAD_SPEC_KC=(0x1.45f306p-3f)",
-    "-DPRAD_SPEC_KC_LO=(0x1.b9391p-28f)", "-DPRAD_SPEC_PHASE_STEP=92233720368547745ull",
+    "-DPRAD_SPEC_KC_LO=(0x1.b9391p-28f)", "-DPRAD_SPEC_CP_DT=(0x1.2a3b4cp-12f)", "-DPRAD_SPEC_PHASE_STEP=92233720368547745ull",
     "-DPRAD_SPEC_ENSEMBLE=3u",
     "-DPRAD_SPEC_RKEY={" + ",".join("%du" % (1000003 * k + 7) for k in range(20)) + "}",
 ]
 
 
-@pytest.mark.parametrize("pf,pws", [(0, 4), (1, 1), (2, 3)])
-def test_kernel_source_compiles_under_nvrtc(pf, pws):
+@pytest.mark.parametrize("samp,pf,pws", [(0, 0, 4), (0, 1, 1), (0, 2, 3), (1, 0, 2), (2, 0, 4)])
+def test_kernel_source_compiles_under_nvrtc(samp, pf, pws):
     nv = _nvrtc()
     paths = build.SPEC_SOURCES
     texts = [open(p, "rb").read() for p in paths]
@@ -48,7 +49,7 @@ def test_kernel_source_compiles_under_nvrtc(pf, pws):
     inc = (ctypes.c_char_p * nh)(*names[1:])
     prog = ctypes.c_void_p()
     assert nv.nvrtcCreateProgram(ctypes.byref(prog), texts[0], names[0], nh, hdr, inc) == 0
-    expr = b"prad::k_push_emit<float, 1, 0, %d, false, true, %d>" % (pf, pws)
+    expr = b"prad::k_push_emit<float, 1, %d, %d, false, true, %d>" % (samp, pf, pws)
     assert nv.nvrtcAddNameExpression(prog, expr) == 0
     home = os.environ.get("CUDA_HOME", "/usr/local/cuda")
     opts = [b"-arch=sm_103a", b"-std=c++17", b"-default-device",

@@ -430,7 +430,7 @@ def other_workloads(prad, W, torch, params, rank, peaks, nsm):
     wl = W.yee2d(nsteps=1000, seed=1 + rank)
     ctx = prad.Context(wl.problem_kwargs(), precision=prad.PRAD_FP32,
                        photon_capacity=1 << 28, max_particles=wl.n, sort_interval=16,
-                       steps_per_launch=16)
+                       steps_per_launch=16, specialize=SPEC["on"])
     st = ctx.to_device(wl.state, with_pid=True)
     ctx.push_emit({k: v[:4096].clone() for k, v in st.items()}, 8)   # warm-up
     ctx.reset()

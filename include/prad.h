@@ -111,11 +111,13 @@ typedef struct prad_config {
    * k w / select_prob.  Both keep the expected emission unchanged. */
   int32_t n_try;
   int32_t diagnostics;      /* bit mask of PRAD_DIAG_*                        */
-  int32_t specialize;       /* 1 = run the standard FP32 plane-wave step (any
-                               sampler, no control or diagnostics) through
-                               kernels compiled at run time by NVRTC with this
-                               context's constants (time step, wave, Philox
-                               key ...) as literals: the same results, fewer
+  int32_t specialize;       /* 1 = run the standard FP32 step of the plane
+                               wave (any sampler) and of the Yee grid (plain
+                               and tile-staged), without control or
+                               diagnostics, through kernels compiled at run
+                               time by NVRTC with this context's constants
+                               (time step, wave or grid geometry, Philox key
+                               ...) as literals: the same results, fewer
                                loads.  Each variant is compiled (~0.3 s) at its
                                first launch; prad_push_emit fails with
                                PRAD_ERR_CUDA if NVRTC or the driver cannot

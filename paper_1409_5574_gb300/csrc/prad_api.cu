@@ -541,17 +541,17 @@ int check_sort_args(prad_ctx* c, const prad_particles* pp, int64_t n) {
 }
 
 // The run-time specialised kernel a float launch runs (*f = nullptr when the
-// context does not ask for one or the launch is not of the standard
-// plane-wave configuration); PRAD_ERR_CUDA when it cannot be compiled.
-int spec_for(prad_ctx* c, const StepParams<float>& p, const SpecFn** f) {
+// context does not ask for one or the launch is not of a specialisable
+// variant); PRAD_ERR_CUDA when it cannot be compiled.
+int spec_for(prad_ctx* c, const StepParams<float>& p, bool tiled, const SpecFn** f) {
   *f = nullptr;
-  int pf = 0, pws = 0;
-  if (!c->cfg.specialize || !push_emit_std_pw(p, c->fields.kind, c->cfg.sampler, &pf, &pws))
+  SpecVariant v;
+  if (!c->cfg.specialize ||
+      !push_emit_spec_variant(p, c->fields.kind, c->cfg.sampler, tiled, &v))
     return PRAD_OK;
   if (!c->spec) c->spec = spec_create();
   char msg[448] = {0};
-  const cudaError_t e =
-      spec_get(c->spec, c->device, p, c->cfg.sampler, pf, pws, f, msg, sizeof(msg));
+  const cudaError_t e = spec_get(c->spec, c->device, p, v, f, msg, sizeof(msg));
   if (e != cudaSuccess)
     return fail(c, PRAD_ERR_CUDA, "push_emit: run-time specialisation: %s (%s)", msg,
                 cudaGetErrorString(e));
@@ -603,6 +603,17 @@ int push_emit_t(prad_ctx* c, const prad_particles* pp, int64_t n,
       p.t0 = pp->t0 + done;
       p.nsub = m;
       const int64_t mw = max_work_items(n, c->sort.ntiles);
+      if constexpr (sizeof(R) == 4) {
+        const SpecFn* spec = nullptr;
+        rc = spec_for(c, p, true, &spec);
+        if (rc != PRAD_OK) return rc;
+        if (spec) {
+          CK(c, spec_launch(spec, p, static_cast<int>(mw), 256, c->stream));
+          ++c->spec_launches;
+          done += m;
+          continue;
+        }
+      }
       CK(c, launch_push_emit_tiled<R>(p, static_cast<int>(mw), 256, c->stream));
       done += m;
     }
@@ -626,7 +637,7 @@ int push_emit_t(prad_ctx* c, const prad_particles* pp, int64_t n,
   const SpecFn* spec = nullptr;
   if constexpr (sizeof(R) == 4) {
     p.nsub = sub_eff;
-    const int rc = spec_for(c, p, &spec);
+    const int rc = spec_for(c, p, false, &spec);
     if (rc != PRAD_OK) return rc;
   }
   const int occ = spec ? spec_occupancy(spec, block)
@@ -646,7 +657,7 @@ int push_emit_t(prad_ctx* c, const prad_particles* pp, int64_t n,
     p.phase_t0 = phase0 + static_cast<uint64_t>(p.t0) * p.phase_step;
     if constexpr (sizeof(R) == 4) {
       if (spec) {
-        const int rc = spec_for(c, p, &spec);  // the variant of this launch's nsub
+        const int rc = spec_for(c, p, false, &spec);  // the variant of this launch's nsub
         if (rc != PRAD_OK) return rc;
       }
       if (spec) {

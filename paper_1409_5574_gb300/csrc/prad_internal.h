@@ -270,25 +270,32 @@ cudaError_t launch_ledger_reduce(const double* a, const double* b, int64_t n,
                                  double* partials, int nblocks, double* out,
                                  cudaStream_t s);
 
-// Run-time specialised kernels (spec.cu): the standard FP32 plane-wave
-// k_push_emit variants compiled by NVRTC with the context's constants as
-// literals.  spec_get returns the kernel for sampler samp, prefetch mode pf
-// and sign variant pws, compiling it on first use (an error, with a message
-// in msg, when NVRTC or the driver cannot provide it).
+// Run-time specialised kernels (spec.cu): the standard FP32 plane-wave and
+// Yee-grid step kernels compiled by NVRTC with the context's constants as
+// literals.  A variant names the kernel (k_push_emit, or k_push_emit_tiled
+// when tiled), field model, sampler, prefetch mode and plane-wave signs.
+// spec_get returns its kernel for these parameters' constants, compiling it
+// on first use (an error, with a message in msg, when NVRTC or the driver
+// cannot provide it).
+struct SpecVariant {
+  int32_t tiled, field, samp, pf, pws;
+};
 struct SpecFn;
 struct SpecCache;
 SpecCache* spec_create();
 void spec_destroy(SpecCache* c);
-cudaError_t spec_get(SpecCache* c, int device, const StepParams<float>& p, int samp, int pf,
-                     int pws, const SpecFn** out, char* msg, size_t msg_len);
+cudaError_t spec_get(SpecCache* c, int device, const StepParams<float>& p, const SpecVariant& v,
+                     const SpecFn** out, char* msg, size_t msg_len);
 int spec_occupancy(const SpecFn* f, int block);
+// grid blocks of block threads; the tiled kernel gets its tile's dynamic
+// shared memory
 cudaError_t spec_launch(const SpecFn* f, const StepParams<float>& p, int grid, int block,
                         cudaStream_t s);
-// Whether a launch with these parameters runs the standard plane-wave
-// kernel (FP32 push, no control or diagnostics), and if so its prefetch mode
-// and sign variant.
-bool push_emit_std_pw(const StepParams<float>& p, int field_kind, int sampler, int* pf, int* pws);
-
+// Whether a launch with these parameters runs a specialisable variant (FP32
+// standard configuration of the plane wave or the Yee grid, no control or
+// diagnostics; the tiled kernel with the table sampler), and which.
+bool push_emit_spec_variant(const StepParams<float>& p, int field_kind, int sampler, bool tiled,
+                            SpecVariant* v);
 #endif  // __CUDACC_RTC__
 
 }  // namespace prad

@@ -1146,10 +1146,10 @@ int occupancy_of(K kernel, int block, size_t dyn) {
 
 #ifdef PRAD_SPEC
 // Run-time specialisation (a kernel compiled by NVRTC for one context): the
-// per-run constants of the standard plane-wave step -- the normalised time
+// per-run constants of the standard step -- the normalised time
 // step and charge factors, the radiation coefficients of Eqs. (1), (4), (7)
 // and (13), the wave's amplitude, wavenumber and phase increment, the ensemble and
-// the Philox round keys -- given as literals, so that they fold into the
+// the Philox round keys, and on the Yee grid its geometry -- given as literals, so that they fold into the
 // arithmetic instead of being read from the kernel's parameter space.  The
 // values are those the host would pass, so the results are the same bits.
 template <typename R>
@@ -1171,6 +1171,21 @@ __device__ __forceinline__ StepParams<R> spec_params(const StepParams<R>& in) {
   constexpr uint32_t rk[20] = PRAD_SPEC_RKEY;
 #pragma unroll
   for (int k = 0; k < 20; ++k) p.rkey[k] = rk[k];
+#ifdef PRAD_SPEC_YEE
+  // the Yee grid's size, spacing (with the low parts of 1/dx, 1/dy), origin,
+  // periods and tiles per row
+  p.nx = PRAD_SPEC_NX;
+  p.ny = PRAD_SPEC_NY;
+  p.inv_dx = PRAD_SPEC_INV_DX;
+  p.inv_dy = PRAD_SPEC_INV_DY;
+  p.inv_dx_lo = PRAD_SPEC_INV_DX_LO;
+  p.inv_dy_lo = PRAD_SPEC_INV_DY_LO;
+  p.x0 = PRAD_SPEC_X0;
+  p.y0 = PRAD_SPEC_Y0;
+  p.Lx = PRAD_SPEC_LX;
+  p.Ly = PRAD_SPEC_LY;
+  p.ntx = PRAD_SPEC_NTX;
+#endif
   return p;
 }
 #endif
@@ -1384,7 +1399,12 @@ int batch_max_blocks_per_sm(int block, int sampler, bool ctrl, bool std_cfg) {
 // same per-particle path with the shared-memory gather.
 // ---------------------------------------------------------------------------
 template <typename R, bool CTRL, bool STD = false>
-__global__ void __launch_bounds__(256, 3) k_push_emit_tiled(const StepParams<R> P) {
+__global__ void __launch_bounds__(256, 3) k_push_emit_tiled(const StepParams<R> P_arg) {
+#ifdef PRAD_SPEC
+  const StepParams<R> P = spec_params(P_arg);
+#else
+  const StepParams<R>& P = P_arg;
+#endif
   if (blockIdx.x >= *P.work_count) return;
   extern __shared__ __align__(16) float tile_sm[];
   __shared__ PhotonStageSoA stage_all[kMaxWarps];
@@ -1411,7 +1431,10 @@ __global__ void __launch_bounds__(256, 3) k_push_emit_tiled(const StepParams<R> 
       gx += gx < 0 ? P.nx : 0;
       gy += gy < 0 ? P.ny : 0;
     }
-    tile_sm[TileGather<R>::pos(c, r)] = __ldg(P.yee[c] + static_cast<size_t>(gy) * P.nx + gx);
+    // (the plane pointer indexed by a run-time c from the kernel's parameter
+    // space: a specialised kernel's copy of the parameters stays in registers)
+    tile_sm[TileGather<R>::pos(c, r)] =
+        __ldg(P_arg.yee[c] + static_cast<size_t>(gy) * P.nx + gx);
   }
   __syncthreads();
   PhotonStageSoA& stage = stage_all[threadIdx.x >> 5];
@@ -1590,13 +1613,27 @@ int push_emit_occupancy(const StepParams<R>& p, int field_kind, int sampler, int
 }
 template int push_emit_occupancy<float>(const StepParams<float>&, int, int, int, int, bool);
 
-bool push_emit_std_pw(const StepParams<float>& p, int field_kind, int sampler, int* pf,
-                      int* pws) {
+bool push_emit_spec_variant(const StepParams<float>& p, int field_kind, int sampler, bool tiled,
+                            SpecVariant* v) {
   const bool ctrl = p.ntry > 1 || p.sel_q < 1.0f || p.diag != 0;
-  if (field_kind != PRAD_FIELD_PLANE_WAVE || ctrl || !std_config(p, 3)) return false;
+  if (ctrl) return false;
+  v->field = field_kind;
+  v->samp = sampler;
+  v->tiled = tiled ? 1 : 0;
+  v->pf = 0;
+  v->pws = 0;
+  if (tiled) return field_kind == PRAD_FIELD_YEE2D && sampler == PRAD_SAMPLER_TABLE &&
+                    std_config(p, 2);
+  if (field_kind == PRAD_FIELD_PLANE_WAVE) {
+    if (!std_config(p, 3)) return false;
+    v->pws = pw_signs(p);
+  } else if (field_kind == PRAD_FIELD_YEE2D) {
+    if (!std_config(p, 2)) return false;
+  } else {
+    return false;
+  }
   // (the learned samplers have no prefetching variant)
-  *pf = sampler != PRAD_SAMPLER_TABLE ? 0 : p.nsub == 1 ? (dense_launch(p) ? 2 : 1) : 0;
-  *pws = pw_signs(p);
+  v->pf = sampler != PRAD_SAMPLER_TABLE ? 0 : p.nsub == 1 ? (dense_launch(p) ? 2 : 1) : 0;
   return true;
 }
 template int push_emit_occupancy<double>(const StepParams<double>&, int, int, int, int, bool);

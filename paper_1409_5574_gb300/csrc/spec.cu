@@ -1,5 +1,6 @@
-// Run-time specialisation of the standard FP32 plane-wave step kernels
-// (the table sampler and the learned samplers).
+// Run-time specialisation of the standard FP32 step kernels: the plane wave
+// (table and learned samplers) and the Yee grid (plain gather and the
+// tile-staged kernel).
 //
 // The kernel source of push_emit.cu (embedded in the library at build time)
 // is compiled by NVRTC with -DPRAD_SPEC and the context's per-run constants
@@ -68,6 +69,7 @@ struct Driver {
   decltype(&cuLaunchKernel) launch = nullptr;
   decltype(&cuOccupancyMaxActiveBlocksPerMultiprocessor) occupancy = nullptr;
   decltype(&cuCtxGetCurrent) ctx_current = nullptr;
+  decltype(&cuFuncSetAttribute) set_attr = nullptr;
 };
 
 template <class F>
@@ -119,7 +121,8 @@ const Driver& driver() {
     d.ok = entry("cuModuleLoadData", &d.load) && entry("cuModuleUnload", &d.unload) &&
            entry("cuModuleGetFunction", &d.get_function) && entry("cuLaunchKernel", &d.launch) &&
            entry("cuOccupancyMaxActiveBlocksPerMultiprocessor", &d.occupancy) &&
-           entry("cuCtxGetCurrent", &d.ctx_current);
+           entry("cuCtxGetCurrent", &d.ctx_current) &&
+           entry("cuFuncSetAttribute", &d.set_attr);
     if (!d.ok) d.why = "driver entry points unavailable";
   });
   return d;
@@ -128,13 +131,15 @@ const Driver& driver() {
 // The constants a specialised kernel has compiled in, with its variant.
 struct SpecKey {
   float half_q_dtn, dtn, inv_dtn, cn_dt, eps_r15, ll_coef, E0, kc, kc_lo, cp_dt;
+  float inv_dx, inv_dy, inv_dx_lo, inv_dy_lo, x0, y0, Lx, Ly;  // Yee grid
+  int32_t nx, ny, ntx;
   uint64_t phase_step;
   uint32_t ensemble;
   uint32_t rkey[20];
-  int32_t samp, pf, pws;
+  SpecVariant v;
 };
 
-SpecKey key_of(const StepParams<float>& p, int samp, int pf, int pws) {
+SpecKey key_of(const StepParams<float>& p, const SpecVariant& v) {
   SpecKey k;
   std::memset(&k, 0, sizeof(k));
   k.half_q_dtn = p.half_q_dtn;
@@ -147,12 +152,23 @@ SpecKey key_of(const StepParams<float>& p, int samp, int pf, int pws) {
   k.kc = p.kc;
   k.kc_lo = p.kc_lo;
   k.cp_dt = p.cp_dt;
+  if (v.field == PRAD_FIELD_YEE2D) {
+    k.inv_dx = p.inv_dx;
+    k.inv_dy = p.inv_dy;
+    k.inv_dx_lo = p.inv_dx_lo;
+    k.inv_dy_lo = p.inv_dy_lo;
+    k.x0 = p.x0;
+    k.y0 = p.y0;
+    k.Lx = p.Lx;
+    k.Ly = p.Ly;
+    k.nx = p.nx;
+    k.ny = p.ny;
+    k.ntx = v.tiled ? p.ntx : 0;
+  }
   k.phase_step = p.phase_step;
   k.ensemble = p.ensemble;
   std::memcpy(k.rkey, p.rkey, sizeof(k.rkey));
-  k.samp = samp;
-  k.pf = pf;
-  k.pws = pws;
+  k.v = v;
   return k;
 }
 
@@ -181,6 +197,22 @@ bool spec_defines(const SpecKey& k, std::vector<std::string>& out) {
     rk += buf;
   }
   out.push_back(rk);
+  if (k.v.field == PRAD_FIELD_YEE2D) {
+    const float y[8] = {k.inv_dx, k.inv_dy, k.inv_dx_lo, k.inv_dy_lo, k.x0, k.y0, k.Lx, k.Ly};
+    const char* ynm[8] = {"INV_DX", "INV_DY", "INV_DX_LO", "INV_DY_LO", "X0", "Y0", "LX", "LY"};
+    for (int j = 0; j < 8; ++j) {
+      if (!std::isfinite(y[j])) return false;
+      std::snprintf(buf, sizeof(buf), "-DPRAD_SPEC_%s=(%af)", ynm[j], static_cast<double>(y[j]));
+      out.emplace_back(buf);
+    }
+    std::snprintf(buf, sizeof(buf), "-DPRAD_SPEC_NX=%d", k.nx);
+    out.emplace_back(buf);
+    std::snprintf(buf, sizeof(buf), "-DPRAD_SPEC_NY=%d", k.ny);
+    out.emplace_back(buf);
+    std::snprintf(buf, sizeof(buf), "-DPRAD_SPEC_NTX=%d", k.ntx);
+    out.emplace_back(buf);
+    out.emplace_back("-DPRAD_SPEC_YEE");
+  }
   return true;
 }
 
@@ -198,6 +230,7 @@ struct SpecFn {
   CUfunction fn = nullptr;
   CUcontext ctx = nullptr;
   int device = 0;
+  unsigned dyn_smem = 0;  // dynamic shared memory per block
 };
 
 struct SpecCache {
@@ -217,9 +250,9 @@ void spec_destroy(SpecCache* c) {
 }
 
 namespace {
-cudaError_t spec_get_impl(SpecCache* c, int device, const StepParams<float>& p, int samp, int pf,
-                          int pws, const SpecFn** out, std::string* msg) {
-  const SpecKey key = key_of(p, samp, pf, pws);
+cudaError_t spec_get_impl(SpecCache* c, int device, const StepParams<float>& p,
+                          const SpecVariant& v, const SpecFn** out, std::string* msg) {
+  const SpecKey key = key_of(p, v);
   for (SpecFn* f : c->fns)
     if (same(f->key, key)) {
       *out = f;
@@ -244,8 +277,11 @@ cudaError_t spec_get_impl(SpecCache* c, int device, const StepParams<float>& p, 
     return cudaErrorInvalidValue;
   }
   char name[160];
-  std::snprintf(name, sizeof(name), "prad::k_push_emit<float, %d, %d, %d, false, true, %d>",
-                static_cast<int>(PRAD_FIELD_PLANE_WAVE), samp, pf, pws);
+  if (v.tiled)
+    std::snprintf(name, sizeof(name), "prad::k_push_emit_tiled<float, false, true>");
+  else
+    std::snprintf(name, sizeof(name), "prad::k_push_emit<float, %d, %d, %d, false, true, %d>",
+                  v.field, v.samp, v.pf, v.pws);
   constexpr int kNSrc = sizeof(kSpecSrc) / sizeof(kSpecSrc[0]);
   nvrtcProgram prog = nullptr;
   if (nv.create(&prog, kSpecSrc[0], kSpecSrcName[0], kNSrc - 1, kSpecSrc + 1, kSpecSrcName + 1) !=
@@ -283,6 +319,11 @@ cudaError_t spec_get_impl(SpecCache* c, int device, const StepParams<float>& p, 
   CUresult cr = d.ctx_current(&f->ctx);
   if (cr == CUDA_SUCCESS) cr = d.load(&f->mod, bin.data());
   if (cr == CUDA_SUCCESS) cr = d.get_function(&f->fn, f->mod, sym_name.c_str());
+  if (cr == CUDA_SUCCESS && v.tiled) {
+    // the staged field tile (dynamic) and the photon stage exceed 48 KB
+    f->dyn_smem = kTileSmemBytes;
+    cr = d.set_attr(f->fn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, kTileSmemBytes);
+  }
   if (cr != CUDA_SUCCESS) {
     if (f->mod) d.unload(f->mod);
     delete f;
@@ -298,18 +339,18 @@ cudaError_t spec_get_impl(SpecCache* c, int device, const StepParams<float>& p, 
 }
 }  // namespace
 
-cudaError_t spec_get(SpecCache* c, int device, const StepParams<float>& p, int samp, int pf,
-                     int pws, const SpecFn** out, char* msg, size_t msg_len) {
+cudaError_t spec_get(SpecCache* c, int device, const StepParams<float>& p, const SpecVariant& v,
+                     const SpecFn** out, char* msg, size_t msg_len) {
   *out = nullptr;
   std::string m;
-  const cudaError_t e = spec_get_impl(c, device, p, samp, pf, pws, out, &m);
+  const cudaError_t e = spec_get_impl(c, device, p, v, out, &m);
   if (e != cudaSuccess && msg && msg_len) std::snprintf(msg, msg_len, "%s", m.c_str());
   return e;
 }
 
 int spec_occupancy(const SpecFn* f, int block) {
   int nb = 0;
-  if (driver().occupancy(&nb, f->fn, block, 0) != CUDA_SUCCESS) return 1;
+  if (driver().occupancy(&nb, f->fn, block, f->dyn_smem) != CUDA_SUCCESS) return 1;
   return nb > 0 ? nb : 1;
 }
 
@@ -325,7 +366,7 @@ cudaError_t spec_launch(const SpecFn* f, const StepParams<float>& p, int grid, i
   }
   void* args[] = {const_cast<StepParams<float>*>(&p)};
   const CUresult r = d.launch(f->fn, static_cast<unsigned>(grid), 1, 1, static_cast<unsigned>(block),
-                              1, 1, 0, reinterpret_cast<CUstream>(s), args, nullptr);
+                              1, 1, f->dyn_smem, reinterpret_cast<CUstream>(s), args, nullptr);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorLaunchFailure;
 }
 

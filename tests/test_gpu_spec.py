@@ -5,11 +5,11 @@ The specialised kernels are the same source compiled by NVRTC with the
 context's constants as literals, so for every launch form they select
 (fused multi-step launches; one-step launches, dense and with explicit
 ids; the four plane-wave sign variants; a different seed, ensemble and
-field amplitude; the learned samplers) the particle state, the photon records and the counters
+field amplitude; the learned samplers; the Yee grid's plain and tile-staged
+kernels) the particle state, the photon records and the counters
 must be the same bits, and the per-particle ledgers the same up to the
 grouping of the FP64 atomic adds.  Launches outside the standard
-plane-wave configuration (another field, the LL ledger mode, FP64) keep
-the ahead-of-time kernels.
+configuration (the LL ledger mode, FP64) keep the ahead-of-time kernels.
 """
 import numpy as np
 import pytest
@@ -125,6 +125,50 @@ def test_specialised_learned_sampler(sampler):
     assert a["stats"]["records"] > 1000
     assert b["stats"]["spec_launches"] == 2
     assert a["stats"]["mlp_fallback"] == b["stats"]["mlp_fallback"]
+
+
+def _small_yee(n, seed=4, a0=300.0, nx=96, ny=80):
+    rng = np.random.default_rng(seed)
+    dxn = 2 * np.pi / 32
+    wl = W.yee2d(n_grid=64, slab=32, n_particles=n, seed=seed, with_grid=False)
+    wl.yee = W.yee_planes(nx, ny, a0, dxn, rng)
+    wl.state["x"] = rng.uniform(0, nx, n) * dxn
+    wl.state["y"] = rng.uniform(0, ny, n) * dxn
+    return wl
+
+
+def _run_by_id(wl, nsteps, specialize, **kw):
+    """A run whose state is returned in id order (the tile sort reorders the
+    particles, and the order within a tile may differ between runs)."""
+    ctx = prad.Context(wl.problem_kwargs(), precision=prad.PRAD_FP32, photon_capacity=1 << 20,
+                       max_particles=wl.n, specialize=specialize, **kw)
+    st = ctx.to_device(wl.state, with_pid=True)
+    ctx.push_emit(st, nsteps, t0=2)
+    torch.cuda.synchronize()
+    o = np.argsort(st["pid"].cpu().numpy().view(np.uint32))
+    ph = ctx.photons(on_device=False)
+    e, l, stats = ctx.energy_budget()
+    le, ll = ctx.ledger()
+    out = dict(state={k: v.cpu().numpy()[o] for k, v in st.items() if k != "pid"},
+               ph={k: (v.numpy().copy() if hasattr(v, "numpy") else v) for k, v in ph.items()},
+               e=e, l=l, stats=stats, le=le.cpu().numpy(), ll=ll.cpu().numpy())
+    ctx.close()
+    return out
+
+
+@pytest.mark.parametrize("form", ["fused", "one_step", "tiled"])
+def test_specialised_yee(form):
+    """The Yee grid's kernels with the grid's size, spacing, origin and
+    periods compiled in: the plain gather (fused and one-step launches) and
+    the tile-staged kernel behind the tile sort."""
+    wl = _small_yee(n=20000 + 11, nx=160, ny=96)
+    kw = dict(sort_interval=5) if form == "tiled" else \
+        dict(steps_per_launch=5 if form == "fused" else 1)
+    a = _run_by_id(wl, 20, False, **kw)
+    b = _run_by_id(wl, 20, True, **kw)
+    _same(a, b)
+    assert a["stats"]["records"] > 1000
+    assert b["stats"]["spec_launches"] == (20 if form == "one_step" else 4)
 
 
 def test_outside_the_standard_configuration_keeps_compiled_in_kernels():

@@ -1,7 +1,8 @@
 """The kernel source that run-time specialisation compiles with NVRTC
 (push_emit.cu and the headers it includes) compiles under NVRTC with the
-specialised constants, for the table sampler's three launch forms and the
-learned samplers, without a GPU.  The
+specialised constants, for the table sampler's three launch forms, the
+learned samplers and the Yee grid's plain and tile-staged kernels, without a
+GPU.  The
 library embeds the same files at build time; this keeps them free of host
 code outside the __CUDACC_RTC__ guards."""
 import ctypes
@@ -38,8 +39,21 @@ DEFINES = [
 ]
 
 
-@pytest.mark.parametrize("samp,pf,pws", [(0, 0, 4), (0, 1, 1), (0, 2, 3), (1, 0, 2), (2, 0, 4)])
-def test_kernel_source_compiles_under_nvrtc(samp, pf, pws):
+YEE = ["-DPRAD_SPEC_YEE", "-DPRAD_SPEC_NX=4096", "-DPRAD_SPEC_NY=4096", "-DPRAD_SPEC_NTX=128",
+       "-DPRAD_SPEC_INV_DX=(0x1.45f306p+2f)", "-DPRAD_SPEC_INV_DY=(0x1.45f306p+2f)",
+       "-DPRAD_SPEC_INV_DX_LO=(0x1.b9391p-23f)", "-DPRAD_SPEC_INV_DY_LO=(0x1.b9391p-23f)",
+       "-DPRAD_SPEC_X0=(0x0p+0f)", "-DPRAD_SPEC_Y0=(0x0p+0f)",
+       "-DPRAD_SPEC_LX=(0x1.921fb6p+9f)", "-DPRAD_SPEC_LY=(0x1.921fb6p+9f)"]
+
+CASES = [(b"prad::k_push_emit<float, 1, %d, %d, false, true, %d>" % c, []) for c in
+         [(0, 0, 4), (0, 1, 1), (0, 2, 3), (1, 0, 2), (2, 0, 4)]]
+CASES += [(b"prad::k_push_emit<float, 2, 0, %d, false, true, 0>" % pf, YEE) for pf in (0, 2)]
+CASES += [(b"prad::k_push_emit_tiled<float, false, true>", YEE)]
+
+
+@pytest.mark.parametrize("expr,extra", CASES, ids=[c[0].decode().split("<")[0][6:] + "_"
+                                                    + str(i) for i, c in enumerate(CASES)])
+def test_kernel_source_compiles_under_nvrtc(expr, extra):
     nv = _nvrtc()
     paths = build.SPEC_SOURCES
     texts = [open(p, "rb").read() for p in paths]
@@ -49,11 +63,10 @@ def test_kernel_source_compiles_under_nvrtc(samp, pf, pws):
     inc = (ctypes.c_char_p * nh)(*names[1:])
     prog = ctypes.c_void_p()
     assert nv.nvrtcCreateProgram(ctypes.byref(prog), texts[0], names[0], nh, hdr, inc) == 0
-    expr = b"prad::k_push_emit<float, 1, %d, %d, false, true, %d>" % (samp, pf, pws)
     assert nv.nvrtcAddNameExpression(prog, expr) == 0
     home = os.environ.get("CUDA_HOME", "/usr/local/cuda")
     opts = [b"-arch=sm_103a", b"-std=c++17", b"-default-device",
-            ("-I" + os.path.join(home, "include")).encode()] + [d.encode() for d in DEFINES]
+            ("-I" + os.path.join(home, "include")).encode()] + [d.encode() for d in DEFINES + extra]
     argv = (ctypes.c_char_p * len(opts))(*opts)
     rc = nv.nvrtcCompileProgram(prog, len(opts), argv)
     n = ctypes.c_size_t()
@@ -66,5 +79,5 @@ def test_kernel_source_compiles_under_nvrtc(samp, pf, pws):
     assert nbin.value > 1000
     lowered = ctypes.c_char_p()
     assert nv.nvrtcGetLoweredName(prog, expr, ctypes.byref(lowered)) == 0
-    assert lowered.value.startswith(b"_ZN4prad11k_push_emit")
+    assert lowered.value.startswith(b"_ZN4prad")
     nv.nvrtcDestroyProgram(ctypes.byref(prog))

@@ -118,10 +118,17 @@ typedef struct prad_config {
                                time by NVRTC with this context's constants
                                (time step, wave or grid geometry, Philox key
                                ...) as literals: the same results, fewer
-                               loads.  Each variant is compiled (~0.3 s) at its
-                               first launch; prad_push_emit fails with
+                               loads.  Each variant is compiled (~0.3-0.7 s)
+                               at its first launch and kept until
+                               prad_destroy; every distinct set of constants
+                               (prad_set_fields with another wave or grid)
+                               compiles its own, so it suits runs whose
+                               constants stay fixed.  Make the first call of
+                               a variant outside CUDA-graph capture (it loads
+                               a module).  prad_push_emit fails with
                                PRAD_ERR_CUDA if NVRTC or the driver cannot
-                               provide it.  0 = compiled-in kernels only.  */
+                               provide a kernel.  0 = compiled-in kernels
+                               only.  */
   double select_prob;
 } prad_config;
 

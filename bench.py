@@ -644,11 +644,13 @@ def run_prad(args):
 
     # end to end through the public API: the initial state from pinned host
     # memory each step, the advanced state and the totals back to the host.
-    # The particles are independent, so the step runs as four groups of
+    # The particles are independent, so the step runs as eight groups of
     # particles (their own ids and ledger entries, as in one launch over
     # all of them): a copy stream brings every group in up front and takes
     # each group back as soon as its launches are done, so the copies
-    # overlap the other groups' launches.
+    # overlap the other groups' launches.  The photon buffer holds a whole
+    # launch's records, so it is drained once per group (after every launch
+    # when the particles do not split into eight groups).
     e2e = None
     if not args.no_e2e:
         host = {k: v.cpu().pin_memory() for k, v in init.items()}
@@ -656,7 +658,7 @@ def run_prad(args):
                 for k in ("x", "y", "z", "ux", "uy", "uz")}
         h2d = sum(v.numel() * v.element_size() for v in host.values())
         d2h = sum(v.numel() * v.element_size() for v in back.values()) + 2 * 8 + 10 * 8
-        groups = 4 if n % 4 == 0 else 1
+        groups = 8 if n % 8 == 0 else 1
         gm = n // groups
         copy_s = torch.cuda.Stream()
         comp = ctx.stream
@@ -693,8 +695,11 @@ def run_prad(args):
                 done = 0
                 for m in chunks:
                     ctx.push_emit(part, m, t0=done, pid0=pid0 + g * gm, ledger_offset=g * gm)
-                    ctx.drain()
                     done += m
+                    if groups == 1:
+                        ctx.drain()
+                if groups > 1:
+                    ctx.drain()
                 ev = torch.cuda.Event()
                 ev.record(comp)
                 copy_s.wait_event(ev)

@@ -127,8 +127,10 @@ typedef struct prad_config {
                                a variant outside CUDA-graph capture (it loads
                                a module).  prad_push_emit fails with
                                PRAD_ERR_CUDA if NVRTC or the driver cannot
-                               provide a kernel.  0 = compiled-in kernels
-                               only.  */
+                               provide a kernel.  NVRTC is the toolkit's
+                               libnvrtc.so.13, or the library the environment
+                               variable PRAD_NVRTC_LIBRARY names.
+                               0 = compiled-in kernels only.  */
   double select_prob;
 } prad_config;
 

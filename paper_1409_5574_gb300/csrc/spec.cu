@@ -82,9 +82,17 @@ const Nvrtc& nvrtc() {
   static Nvrtc n;
   static std::once_flag once;
   std::call_once(once, [] {
-    void* h = dlopen("libnvrtc.so.13", RTLD_NOW | RTLD_LOCAL);
-    if (!h) h = dlopen(PRAD_CUDA_LIBDIR "/libnvrtc.so.13", RTLD_NOW | RTLD_LOCAL);
-    if (!h) h = dlopen("libnvrtc.so", RTLD_NOW | RTLD_LOCAL);
+    // PRAD_NVRTC_LIBRARY names the NVRTC library to open instead of the
+    // toolkit's (and only it)
+    const char* lib = std::getenv("PRAD_NVRTC_LIBRARY");
+    void* h = nullptr;
+    if (lib && *lib) {
+      h = dlopen(lib, RTLD_NOW | RTLD_LOCAL);
+    } else {
+      h = dlopen("libnvrtc.so.13", RTLD_NOW | RTLD_LOCAL);
+      if (!h) h = dlopen(PRAD_CUDA_LIBDIR "/libnvrtc.so.13", RTLD_NOW | RTLD_LOCAL);
+      if (!h) h = dlopen("libnvrtc.so", RTLD_NOW | RTLD_LOCAL);
+    }
     if (!h) {
       const char* e = dlerror();
       n.why = std::string("cannot open NVRTC: ") + (e ? e : "libnvrtc.so.13 not found");

@@ -11,6 +11,10 @@ must be the same bits, and the per-particle ledgers the same up to the
 grouping of the FP64 atomic adds.  Launches outside the standard
 configuration (the LL ledger mode, FP64) keep the ahead-of-time kernels.
 """
+import os
+import subprocess
+import sys
+
 import numpy as np
 import pytest
 
@@ -179,3 +183,46 @@ def test_outside_the_standard_configuration_keeps_compiled_in_kernels():
     _same(_run(wl, 6, 3, False), a)
     b = _run(_wave(n=2048), 4, 1, True, precision=prad.PRAD_FP64)
     assert b["stats"]["spec_launches"] == 0
+
+
+def test_control_variant_keeps_compiled_in_kernels():
+    wl = _wave(n=2048)
+    a = _run(wl, 6, 3, True, n_try=2)
+    assert a["stats"]["spec_launches"] == 0
+    _same(_run(wl, 6, 3, False, n_try=2), a)
+
+
+def test_missing_nvrtc_fails_loudly_and_the_context_stays_usable():
+    """Without NVRTC a specialised launch is an error with the reason, not a
+    silent fallback; the context keeps working with specialize off (a child
+    process, since NVRTC is opened once per process)."""
+    code = """
+import sys, torch
+from paper_1409_5574_gb300 import prad, workloads as W
+prad.load_library()
+wl = W.plane_wave(a0=200.0, n=1000, seed=2)
+ctx = prad.Context(wl.problem_kwargs(), precision=prad.PRAD_FP32, photon_capacity=1 << 16,
+                   max_particles=wl.n, steps_per_launch=4, specialize=True)
+st = ctx.to_device(wl.state)
+try:
+    ctx.push_emit(st, 4)
+    print("NO ERROR")
+except prad.PradError as e:
+    print("ERROR", e)
+ctx.close()
+ctx = prad.Context(wl.problem_kwargs(), precision=prad.PRAD_FP32, photon_capacity=1 << 16,
+                   max_particles=wl.n, steps_per_launch=4)
+ctx.push_emit(ctx.to_device(wl.state), 4)
+torch.cuda.synchronize()
+print("RECORDS", ctx.energy_budget()[2]["records"])
+ctx.close()
+"""
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, PRAD_NVRTC_LIBRARY="/nonexistent/libnvrtc.so.13")
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True,
+                       text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert "ERROR" in r.stdout and "NO ERROR" not in r.stdout, r.stdout
+    assert "specialisation" in r.stdout and "NVRTC" in r.stdout, r.stdout
+    n = int(r.stdout.split("RECORDS")[1].split()[0])
+    assert n > 0

@@ -318,7 +318,16 @@ cudaError_t spec_get_impl(SpecCache* c, int device, const StepParams<float>& p,
   nv.lowered(prog, name, &lowered);
   const std::string sym_name = lowered ? lowered : "";
   nv.destroy(&prog);
-  // the runtime makes the device's primary context current on this thread
+  // the runtime makes the device's primary context current on this thread;
+  // the thread's current device is put back on return
+  struct DeviceGuard {
+    int prev = -1;
+    ~DeviceGuard() {
+      int now = -1;
+      if (prev >= 0 && cudaGetDevice(&now) == cudaSuccess && now != prev) cudaSetDevice(prev);
+    }
+  } guard;
+  if (cudaGetDevice(&guard.prev) != cudaSuccess) guard.prev = -1;
   cudaError_t e = cudaSetDevice(device);
   if (e != cudaSuccess) return e;
   SpecFn* f = new SpecFn();
@@ -366,8 +375,11 @@ cudaError_t spec_launch(const SpecFn* f, const StepParams<float>& p, int grid, i
                         cudaStream_t s) {
   const Driver& d = driver();
   CUcontext cur = nullptr;
+  int prev = -1;
   if (d.ctx_current(&cur) != CUDA_SUCCESS || cur != f->ctx) {
-    // a thread without the device's primary context current: bind it
+    // another device (or none) current on this thread: bind the kernel's
+    // for the launch and put the thread's device back after it
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
     const cudaError_t e = cudaSetDevice(f->device);
     if (e != cudaSuccess) return e;
     if (d.ctx_current(&cur) != CUDA_SUCCESS || cur != f->ctx) return cudaErrorInvalidResourceHandle;
@@ -375,7 +387,14 @@ cudaError_t spec_launch(const SpecFn* f, const StepParams<float>& p, int grid, i
   void* args[] = {const_cast<StepParams<float>*>(&p)};
   const CUresult r = d.launch(f->fn, static_cast<unsigned>(grid), 1, 1, static_cast<unsigned>(block),
                               1, 1, f->dyn_smem, reinterpret_cast<CUstream>(s), args, nullptr);
-  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorLaunchFailure;
+  if (prev >= 0 && prev != f->device) cudaSetDevice(prev);
+  switch (r) {
+    case CUDA_SUCCESS: return cudaSuccess;
+    case CUDA_ERROR_INVALID_VALUE: return cudaErrorInvalidValue;
+    case CUDA_ERROR_INVALID_HANDLE: return cudaErrorInvalidResourceHandle;
+    case CUDA_ERROR_OUT_OF_RESOURCES: return cudaErrorLaunchOutOfResources;
+    default: return cudaErrorLaunchFailure;
+  }
 }
 
 }  // namespace prad

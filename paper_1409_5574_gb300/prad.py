@@ -306,6 +306,10 @@ class Context:
     """A prad context with torch tensors as the particle and photon storage.
 
     ``problem`` keys follow ``workloads.Workload.problem_kwargs()``.
+    ``specialize=True`` sets ``prad_config.specialize``: the standard FP32
+    plane-wave and Yee steps run through kernels NVRTC compiles for this
+    context's constants (same results; ``energy_budget()[2]["spec_launches"]``
+    counts their launches).
     """
 
     def __init__(self, problem: Dict, precision: int = PRAD_FP32,

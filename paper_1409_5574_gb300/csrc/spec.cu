@@ -392,7 +392,7 @@ cudaError_t spec_launch(const SpecFn* f, const StepParams<float>& p, int grid, i
     case CUDA_SUCCESS: return cudaSuccess;
     case CUDA_ERROR_INVALID_VALUE: return cudaErrorInvalidValue;
     case CUDA_ERROR_INVALID_HANDLE: return cudaErrorInvalidResourceHandle;
-    case CUDA_ERROR_OUT_OF_RESOURCES: return cudaErrorLaunchOutOfResources;
+    case CUDA_ERROR_LAUNCH_OUT_OF_RESOURCES: return cudaErrorLaunchOutOfResources;
     default: return cudaErrorLaunchFailure;
   }
 }

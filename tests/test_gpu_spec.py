@@ -226,3 +226,21 @@ ctx.close()
     assert "specialisation" in r.stdout and "NVRTC" in r.stdout, r.stdout
     n = int(r.stdout.split("RECORDS")[1].split()[0])
     assert n > 0
+
+
+@pytest.mark.parametrize("n", [1, 31, 33])
+def test_specialised_ragged_and_tiny_launches(n):
+    """Launches of fewer particles than a warp or a block (the dense one-step
+    form with one particle included) and an empty launch."""
+    wl = _wave(n=n, a0=500.0, seed=5 + n)
+    for spl in (1, 7):
+        a = _run(wl, 14, spl, False)
+        b = _run(wl, 14, spl, True)
+        _same(a, b)
+        assert b["stats"]["spec_launches"] == (14 if spl == 1 else 2)
+    ctx = prad.Context(wl.problem_kwargs(), precision=prad.PRAD_FP32, photon_capacity=1 << 10,
+                       max_particles=wl.n, specialize=True)
+    st = {k: v[:0] for k, v in ctx.to_device(wl.state).items()}
+    ctx.push_emit(st, 3)
+    assert ctx.energy_budget()[2]["spec_launches"] == 0
+    ctx.close()

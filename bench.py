@@ -54,9 +54,9 @@ KERNEL_SOURCES = ["paper_1409_5574_gb300/csrc/push_emit.cu",
                   "paper_1409_5574_gb300/csrc/mlp_device.cuh",
                   "paper_1409_5574_gb300/csrc/spec.cu"]
 NCU_TRAFFIC = {
-    "src_sha256": "21b7285853304db55bd6ed7d45c935813760bb80422475d2dbda41db9e07ade6",
-    "fused": 12567324480,  # mean bytes per launch over the 4 launches of one bench step
-    "stream": 1375841522,  # mean bytes per launch, 2^24 particles x 1 step, a0 = 500
+    "src_sha256": "065d63a03dec2df4cf34ac996f4ba3af0b952f57113f5b98ae4bf93561f75a2b",
+    "fused": 12564032832,  # mean bytes per launch over the 4 launches of one bench step
+    "stream": 1375847168,  # mean bytes per launch, 2^24 particles x 1 step, a0 = 500
 }
 
 

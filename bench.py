@@ -426,11 +426,12 @@ def other_workloads(prad, W, torch, params, rank, peaks, nsm):
            "constant_b_fp64": constant_b_fp64(prad, W, torch)}
 
     # 2D Yee grid 4096^2 (standing wave a0 = 300 + 1% noise), 16M electrons,
-    # 1000 steps, sorted by 32 x 32-cell tile every 16 steps
+    # 1000 steps, sorted by 32 x 32-cell tile (and by cell inside the tile)
+    # every 50 steps
     wl = W.yee2d(nsteps=1000, seed=1 + rank)
     ctx = prad.Context(wl.problem_kwargs(), precision=prad.PRAD_FP32,
-                       photon_capacity=1 << 28, max_particles=wl.n, sort_interval=16,
-                       steps_per_launch=16, specialize=SPEC["on"])
+                       photon_capacity=1 << 28, max_particles=wl.n, sort_interval=50,
+                       steps_per_launch=50, specialize=SPEC["on"])
     st = ctx.to_device(wl.state, with_pid=True)
     ctx.push_emit({k: v[:4096].clone() for k, v in st.items()}, 8)   # warm-up
     ctx.reset()
@@ -442,7 +443,7 @@ def other_workloads(prad, W, torch, params, rank, peaks, nsm):
     out["yee2d"] = {"value": wl.n * 1000 / secs, "unit": UNIT,
                     "workload": "2D Yee 4096^2 FP32 planes, a0=300 standing wave + 1% noise, "
                                 "16777216 electrons in the central 1024^2 cells, 1000 steps, "
-                                "tile sort every 16 steps, table sampler"}
+                                "tile sort every 50 steps, table sampler"}
     ctx.close()
     del st, wl
 

@@ -93,9 +93,9 @@ typedef struct prad_config {
   int32_t blocks_per_sm;    /* blocks per SM of the persistent grid, capped
                                at the kernel's occupancy (0 = occupancy)   */
   int32_t sort_interval;    /* YEE2D with a pid array: reorder particles by
-                               32 x 32-cell tile every this many steps and
-                               gather from shared-memory field tiles
-                               (0 = never sort; plain gather)             */
+                               32 x 32-cell tile (and cell) every this many
+                               steps and gather from shared-memory field
+                               tiles (0 = never sort; plain gather)       */
   int32_t batch_chunk;      /* push_emit_batch: particles per work item
                                (0 = 2048); multiple of 32                 */
   int32_t use_graph;        /* push_emit_batch: capture the launches of a
@@ -310,9 +310,11 @@ int prad_autotune_batch(prad_ctx* ctx, const prad_ensemble* ens, int32_t n_ens,
 
 /* Reorder n particles in place (x, y, z, ux, uy, uz, w and the pid array,
  * which is required) by the 32 x 32-cell tile of the YEE2D grid that holds
- * them (counting sort: histogram, scan, scatter; order within a tile is not
- * deterministic), and record the tile ranges that push_emit uses to gather
- * from shared-memory field tiles.  push_emit calls it itself every
+ * them and, inside each tile, by cell (row-major in the tile), so that
+ * neighbouring threads read the same staged field values (counting sorts:
+ * histogram, scan, scatter, then a per-tile histogram of cells; the order
+ * within a cell is not deterministic), and record the tile ranges that
+ * push_emit uses to gather from shared-memory field tiles.  push_emit calls it itself every
  * sort_interval steps when sort_interval > 0.  Uses the context's scratch
  * (max_particles x 32 B).  Errors: PRAD_ERR_STATE (fields not YEE2D),
  * PRAD_ERR_ARG (null arrays, no pid array, n > max_particles). */

@@ -1,9 +1,13 @@
 // Counting sort of particles by the 32 x 32-cell tile of the 2D Yee grid that
-// holds them (histogram -> exclusive scan -> scatter -> copy back), and the
-// work list of the tile-staged gather kernel: one item per chunk of at most
-// kChunk particles of one tile.  Particles keep their ids (pid array), so the
-// Philox streams and ledger entries follow them.  The order inside a tile
-// depends on atomic timing; results per particle do not.
+// holds them (histogram -> exclusive scan -> scatter into a scratch copy), then
+// by cell inside each tile (one block per tile, scattering back into the
+// caller's arrays), and the work list of the tile-staged gather kernel: one
+// item per chunk of at most kChunk particles of one tile.  In cell order the
+// lanes of a warp read the same or neighbouring stencil values of the staged
+// tile (broadcasts instead of shared-memory bank conflicts).  Particles keep
+// their ids (pid array), so the Philox streams and ledger entries follow
+// them.  The order inside a cell depends on atomic timing; results per
+// particle do not.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -13,10 +17,11 @@ namespace prad {
 
 namespace {
 
+// The grid cell (ix, iy) that holds (x, y): periodic, clamped (also for NaN)
+// into range.
 template <typename R>
-__device__ __forceinline__ int tile_of(R x, R y, int nx, int ny, int ntx, R x0, R y0,
-                                       R inv_dx, R inv_dy) {
-  // periodic cell coordinate in [0, n), clamped (also for NaN) into range
+__device__ __forceinline__ int2 cell_xy(R x, R y, int nx, int ny, R x0, R y0, R inv_dx,
+                                        R inv_dy) {
   R xi = (x - x0) * inv_dx, yi = (y - y0) * inv_dy;
   const R fx = static_cast<R>(nx), fy = static_cast<R>(ny);
   xi -= fx * floor(xi / fx);
@@ -25,7 +30,22 @@ __device__ __forceinline__ int tile_of(R x, R y, int nx, int ny, int ntx, R x0, 
   int iy = static_cast<int>(fmin(fmax(yi, R(0)), fy - R(1)));
   ix = ix < 0 ? 0 : (ix >= nx ? nx - 1 : ix);
   iy = iy < 0 ? 0 : (iy >= ny ? ny - 1 : iy);
-  return (iy / kTile) * ntx + (ix / kTile);
+  return make_int2(ix, iy);
+}
+
+template <typename R>
+__device__ __forceinline__ int tile_of(R x, R y, int nx, int ny, int ntx, R x0, R y0,
+                                       R inv_dx, R inv_dy) {
+  const int2 c = cell_xy(x, y, nx, ny, x0, y0, inv_dx, inv_dy);
+  return (c.y / kTile) * ntx + (c.x / kTile);
+}
+
+// The cell's index inside its tile, row-major (0 .. kTile^2 - 1).
+template <typename R>
+__device__ __forceinline__ int cell_in_tile(R x, R y, int nx, int ny, R x0, R y0, R inv_dx,
+                                            R inv_dy) {
+  const int2 c = cell_xy(x, y, nx, ny, x0, y0, inv_dx, inv_dy);
+  return (c.y % kTile) * kTile + (c.x % kTile);
 }
 
 // Warp-aggregated increment of counter[t] for every valid lane: lanes of the
@@ -141,6 +161,62 @@ __global__ void k_tile_scatter(const Arrays7<R> src, const Arrays7<R> dst,
   }
 }
 
+// Second pass, one block per tile: the tile's particles (a contiguous range
+// of the tile-sorted scratch copy) are ordered by cell with a shared-memory
+// histogram of the tile's kTile^2 cells, and written back to the caller's
+// arrays.  The cell is computed with the same arithmetic as the tile, so
+// every particle stays inside its tile's range.
+constexpr int kCellThreads = kTile * kTile;
+
+template <typename R>
+__global__ void __launch_bounds__(kCellThreads)
+    k_cell_scatter(const Arrays7<R> src, const Arrays7<R> dst,
+                   const uint32_t* __restrict__ pid_src, uint32_t* __restrict__ pid_dst,
+                   const unsigned int* __restrict__ starts, int nx, int ny, R x0, R y0,
+                   R inv_dx, R inv_dy) {
+  __shared__ unsigned int s_cnt[kCellThreads];
+  __shared__ unsigned int s_warp[kCellThreads / 32];
+  const unsigned int a = starts[blockIdx.x], b = starts[blockIdx.x + 1];
+  if (a == b) return;  // the whole block leaves: no barrier is left waiting
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  s_cnt[tid] = 0u;
+  __syncthreads();
+  for (unsigned int i = a + tid; i < b; i += kCellThreads)
+    atomicAdd(s_cnt + cell_in_tile(src.p[0][i], src.p[1][i], nx, ny, x0, y0, inv_dx, inv_dy),
+              1u);
+  __syncthreads();
+  // exclusive scan of the cell counts: within warps, then over the warp sums
+  const unsigned int c = s_cnt[tid];
+  unsigned int v = c;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const unsigned int u = __shfl_up_sync(0xffffffffu, v, off);
+    if (lane >= off) v += u;
+  }
+  if (lane == 31) s_warp[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    unsigned int w = s_warp[lane];
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const unsigned int u = __shfl_up_sync(0xffffffffu, w, off);
+      if (lane >= off) w += u;
+    }
+    s_warp[lane] = w;
+  }
+  __syncthreads();
+  s_cnt[tid] = (warp > 0 ? s_warp[warp - 1] : 0u) + v - c;  // cursor of cell tid
+  __syncthreads();
+  for (unsigned int i = a + tid; i < b; i += kCellThreads) {
+    const int cl = cell_in_tile(src.p[0][i], src.p[1][i], nx, ny, x0, y0, inv_dx, inv_dy);
+    const unsigned int d = a + atomicAdd(s_cnt + cl, 1u);
+#pragma unroll
+    for (int k = 0; k < 7; ++k)
+      if (src.p[k]) dst.p[k][d] = src.p[k][i];
+    pid_dst[d] = pid_src[i];
+  }
+}
+
 }  // namespace
 
 template <typename R>
@@ -167,12 +243,10 @@ cudaError_t launch_tile_sort(R* arr[7], uint32_t* pid, int64_t n, const SortBuff
   k_tile_scatter<R><<<grid, block, 0, s>>>(srcp, dstp, pid, b.tmp_pid, n, nx, ny, ntx, R(x0),
                                            R(y0), R(inv_dx), R(inv_dy), b.cursor);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  for (int k = 0; k < 7; ++k) {
-    if (!arr[k]) continue;
-    e = cudaMemcpyAsync(arr[k], b.tmp[k], sizeof(R) * n, cudaMemcpyDeviceToDevice, s);
-    if (e != cudaSuccess) return e;
-  }
-  return cudaMemcpyAsync(pid, b.tmp_pid, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s);
+  // back into the caller's arrays, in cell order inside each tile
+  k_cell_scatter<R><<<b.ntiles, kCellThreads, 0, s>>>(dstp, srcp, b.tmp_pid, pid, b.starts, nx,
+                                                      ny, R(x0), R(y0), R(inv_dx), R(inv_dy));
+  return cudaGetLastError();
 }
 
 template cudaError_t launch_tile_sort<float>(float* [7], uint32_t*, int64_t, const SortBuffers&,

@@ -159,10 +159,15 @@ def test_tile_sort_is_a_tile_ordered_permutation():
     dxn = wl.dx
     xi = np.mod(st["x"].double().cpu().numpy() / dxn, 200)
     yi = np.mod(st["y"].double().cpu().numpy() / dxn, 70)
-    tile = (np.clip(yi.astype(int), 0, 69) // 32) * 7 + np.clip(xi.astype(int), 0, 199) // 32
+    ix, iy = np.clip(xi.astype(int), 0, 199), np.clip(yi.astype(int), 0, 69)
+    tile = (iy // 32) * 7 + ix // 32
     # tile index non-decreasing (a particle within float rounding of a tile
     # edge may be counted on either side)
     assert np.mean(np.diff(tile) < 0) < 1e-3
+    # and inside a tile, cell order (row-major in the tile), so that a warp's
+    # lanes read the same staged stencil values
+    key = tile.astype(np.int64) * 1024 + (iy % 32) * 32 + ix % 32
+    assert np.mean(np.diff(key) < 0) < 2e-3
     ctx.close()
 
 
@@ -204,12 +209,13 @@ def test_yee_tiled_equals_plain_fp32():
 
 def test_yee_full_size_subset_parity():
     """The 4096^2 standing wave (a0 = 300, 1% noise), 16M electrons in the
-    central 1024^2 cells, sorted every 16 steps (the benchmarked launch
-    shape), 40 steps; the oracle follows every 1600th electron."""
+    central 1024^2 cells, sorted every 50 steps as in the benchmark (here
+    before launches of 1 and 39 steps), 40 steps; the oracle follows every
+    1600th electron."""
     wl = _f32_inputs(W.yee2d(nsteps=40, seed=1))
     ctx = prad.Context(wl.problem_kwargs(), precision=prad.PRAD_FP32,
-                       photon_capacity=1 << 26, max_particles=wl.n, sort_interval=16,
-                       steps_per_launch=16)
+                       photon_capacity=1 << 26, max_particles=wl.n, sort_interval=50,
+                       steps_per_launch=50)
     st = ctx.to_device(wl.state, with_pid=True)
     sel = np.arange(0, wl.n, 1600)
     sub = wl.subset(sel)

@@ -143,9 +143,9 @@ struct StepParams {
 };
 
 // Tile geometry of the sorted Yee gather: 32 x 32-cell tiles, staged with a
-// 4-cell halo (40 x 40 values per field component) in shared memory.
+// 6-cell halo (44 x 44 values per field component) in shared memory.
 constexpr int kTile = 32;
-constexpr int kHalo = 4;
+constexpr int kHalo = 6;
 constexpr int kStageW = kTile + 2 * kHalo;
 constexpr int kTileSmemBytes = 6 * kStageW * kStageW * 4;
 constexpr int kChunk = 4096;  // particles per work item of the tiled kernel

@@ -645,8 +645,8 @@ struct FieldGather {
   }
 };
 
-// Field values of one 32 x 32-cell tile plus a 4-cell halo, all six
-// components, staged in shared memory ([component][row][column], 40 x 40).
+// Field values of one 32 x 32-cell tile plus a 6-cell halo, all six
+// components, staged in shared memory ([component][row][column], 44 x 44).
 // A particle within 2 cells of the staged edge (it drifted since the last
 // sort) is gathered from global memory instead, so the result never depends
 // on the tile assignment.
@@ -1469,7 +1469,7 @@ bool std_config(const StepParams<R>& p, int dims) {
 
 template <typename R, bool CTRL, bool STD>
 cudaError_t launch_tiled_v(const StepParams<R>& p, int max_work, int block, cudaStream_t s) {
-  // dynamic tile (38.4 KB) + static photon staging exceed the 48 KB default
+  // dynamic tile (46.5 KB) + static photon staging exceed the 48 KB default
   cudaError_t e = cudaFuncSetAttribute(k_push_emit_tiled<R, CTRL, STD>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        kTileSmemBytes);

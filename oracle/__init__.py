@@ -17,6 +17,8 @@ Function map to the paper (arXiv:1409.5574):
 * ``heff_field``, ``heff_momentum`` - H_eff, field form and Eq. (9)
 * ``run``              - the full per-step path with emission and LL ledger
 * ``angular_histogram`` - Fig. 4, emitted energy by direction (FP64 numpy)
+* ``K13``, ``K23``, ``ang_parts``, ``ang_norm``, ``ang_cdf``, ``ang_sample`` -
+  Eqs. (5)-(6), the emission's spread in angle about the velocity
 
 Every function is pinned by a ``-m "not gpu"`` test; see tests/test_oracle_*.
 """
@@ -82,6 +84,11 @@ def lib() -> ctypes.CDLL:
             for name in ("orc_G_batch", "orc_Q_batch", "orc_Ginv_batch",
                          "orc_F_batch", "orc_F_exact_batch"):
                 getattr(L, name).argtypes = [P, P, i64]
+            for name in ("orc_K13_batch", "orc_K23_batch", "orc_ang_norm_batch"):
+                getattr(L, name).argtypes = [P, P, i64]
+            for name in ("orc_ang_cdf_batch", "orc_ang_sample_batch"):
+                getattr(L, name).argtypes = [P, P, P, i64]
+            L.orc_ang_parts_batch.argtypes = [P, P, P, P, i64]
             L.orc_boris.argtypes = [P, P, P, d, d]
             L.orc_heff_field.restype = d
             L.orc_heff_field.argtypes = [P, P, P]
@@ -115,6 +122,52 @@ def F_exact(x):
 def F(x):
     """Eq. (8), log-log cubic Hermite interpolant of F_exact."""
     return _vec("orc_F_batch", x)
+
+
+def K13(z):
+    """Modified Bessel function K_1/3 (cosh-integral trapezoid rule)."""
+    return _vec("orc_K13_batch", z)
+
+
+def K23(z):
+    """Modified Bessel function K_2/3 (cosh-integral trapezoid rule)."""
+    return _vec("orc_K23_batch", z)
+
+
+def _vec2(fn_name: str, a, b) -> np.ndarray:
+    a, b = np.broadcast_arrays(np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64))
+    a = np.ascontiguousarray(a)
+    b = np.ascontiguousarray(b)
+    out = np.empty_like(a)
+    getattr(lib(), fn_name)(_ptr(a), _ptr(b), _ptr(out), ctypes.c_int64(a.size))
+    return out
+
+
+def ang_parts(x, psi):
+    """The two polarisation terms of Eq. (5) at x = omega/omega_c and
+    psi = gamma theta: (sigma, pi) = ((1+psi^2)^2 K_2/3(xi)^2,
+    (1+psi^2) psi^2 K_1/3(xi)^2), xi = (x/2)(1+psi^2)^(3/2) (Eq. (6))."""
+    a, b = np.broadcast_arrays(np.asarray(x, dtype=np.float64), np.asarray(psi, dtype=np.float64))
+    a = np.ascontiguousarray(a)
+    b = np.ascontiguousarray(b)
+    sig, pi = np.empty_like(a), np.empty_like(a)
+    lib().orc_ang_parts_batch(_ptr(a), _ptr(b), _ptr(sig), _ptr(pi), ctypes.c_int64(a.size))
+    return sig, pi
+
+
+def ang_norm(x):
+    """int_0^inf (sigma + pi) dpsi at fixed x (Simpson in asinh psi)."""
+    return _vec("orc_ang_norm_batch", x)
+
+
+def ang_cdf(x, psi):
+    """Fraction of the one-sided psi integral below |psi| at fixed x."""
+    return _vec2("orc_ang_cdf_batch", x, psi)
+
+
+def ang_sample(x, u):
+    """psi >= 0 with ang_cdf(x, psi) = u (the angular spread's inverse CDF)."""
+    return _vec2("orc_ang_sample_batch", x, u)
 
 
 def G(x):
@@ -231,7 +284,7 @@ class _Problem(ctypes.Structure):
         ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
         ("dx", ctypes.c_double), ("dy", ctypes.c_double),
         ("x0", ctypes.c_double), ("y0", ctypes.c_double),
-        ("n_try", ctypes.c_int32), ("pad1", ctypes.c_int32),
+        ("n_try", ctypes.c_int32), ("ang_spread", ctypes.c_int32),
         ("select_prob", ctypes.c_double),
     ]
 
@@ -273,6 +326,7 @@ class Problem:
     y0: float = 0.0
     n_try: int = 1
     select_prob: float = 1.0
+    ang_spread: int = 0
     _keep: list = field(default_factory=list, repr=False)
 
     def to_c(self) -> _Problem:
@@ -293,6 +347,7 @@ class Problem:
             p.ny, p.nx = planes[0].shape
         p.dx, p.dy, p.x0, p.y0 = self.dx, self.dy, self.x0, self.y0
         p.n_try, p.select_prob = int(self.n_try), float(self.select_prob)
+        p.ang_spread = int(self.ang_spread)
         return p
 
 

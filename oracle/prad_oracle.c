@@ -341,6 +341,140 @@ void orc_F_exact_batch(const double* x, double* out, int64_t n) {
   for (int64_t i = 0; i < n; ++i) out[i] = orc_F_exact(x[i]);
 }
 
+/* ======================================================================
+ * Angular spread of the emission about the particle's velocity (Eqs. (5)
+ * and (6), the circular-motion spectrum by angle).  With x = omega/omega_c
+ * (omega_c of Eq. (1), equal to (3/2) gamma^3 c / rho for the orbit radius
+ * rho) and psi = gamma theta, theta the angle out of the plane of the orbit,
+ * Eq. (6) gives xi = (x/2) (1 + psi^2)^(3/2) and Eq. (5)'s prefactor
+ * (omega rho / c)^2 (1/gamma^2 + theta^2)^2 = (9/4) x^2 gamma^2 (1 + psi^2)^2,
+ * so at fixed x the radiated energy per unit psi is proportional to
+ *   sigma(x, psi) + pi(x, psi),
+ *   sigma = (1 + psi^2)^2 K_2/3(xi)^2,  pi = (1 + psi^2) psi^2 K_1/3(xi)^2
+ * (the two polarisation terms of Eq. (5)).  Integrated over all psi this
+ * is (2 pi / sqrt 3) F(x) / x^2, F of Eq. (8); over x and psi the sigma
+ * term carries 7/8 of the energy.  The paper's method emits along the
+ * mean velocity (collinear); the optional spread turns each photon by
+ * theta = psi / gamma out of the plane of the step's orbit, psi drawn
+ * from this density (sign from a second Philox word).
+ * ====================================================================== */
+
+/* K_nu(z) = int_0^inf exp(-z cosh t) cosh(nu t) dt, trapezoid rule in t
+ * (exponentially convergent for this integrand); the step shrinks as
+ * 1/sqrt(z) where the peak at t = 0 narrows. */
+static double orc_Knu(double nu, double z) {
+  if (!(z > 0.0)) return INFINITY;
+  const double h = 0.25 / (z > 5.0 ? sqrt(z / 5.0) : 1.0);
+  double acc = 0.5 * exp(-z);
+  for (int k = 1; k < 100000; ++k) {
+    const double t = k * h;
+    const double arg = z * cosh(t);
+    if (arg > z + 745.0) break;
+    acc += exp(-arg) * cosh(nu * t);
+  }
+  return h * acc;
+}
+double orc_K13(double z) { return orc_Knu(1.0 / 3.0, z); }
+double orc_K23(double z) { return orc_Knu(2.0 / 3.0, z); }
+
+void orc_ang_parts(double x, double psi, double* sig, double* pi) {
+  const double q = 1.0 + psi * psi;
+  const double xi = 0.5 * x * q * sqrt(q);
+  const double k23 = orc_K23(xi), k13 = orc_K13(xi);
+  *sig = q * q * k23 * k23;
+  *pi = q * psi * psi * k13 * k13;
+}
+
+static double orc_ang_density(double x, double psi) {
+  double s, p;
+  orc_ang_parts(x, psi, &s, &p);
+  return s + p;
+}
+
+/* psi where xi = xi(0) + 60: beyond it K^2(xi) has fallen by more than
+ * e^-120 from its value at psi = 0 (K_nu(xi) ~ e^-xi) */
+static double orc_ang_psimax(double x) {
+  const double q = pow((x + 120.0) / x, 2.0 / 3.0);
+  return sqrt(q - 1.0);
+}
+
+/* int_{sinh s0}^{sinh s1} density dpsi by composite Simpson in s = asinh psi
+ * (dpsi = cosh s ds) with m (even) subintervals */
+static double orc_ang_int(double x, double s0, double s1, int m) {
+  const double h = (s1 - s0) / m;
+  double acc = 0.0;
+  for (int k = 0; k <= m; ++k) {
+    const double s = s0 + k * h;
+    const double wk = (k == 0 || k == m) ? 1.0 : ((k & 1) ? 4.0 : 2.0);
+    acc += wk * orc_ang_density(x, sinh(s)) * cosh(s);
+  }
+  return acc * h / 3.0;
+}
+
+#define ORC_ANG_PANELS 256
+#define ORC_ANG_SUB 4
+
+/* int_0^inf density dpsi (one side; the density is even in psi) */
+double orc_ang_norm(double x) {
+  const double smax = asinh(orc_ang_psimax(x));
+  return orc_ang_int(x, 0.0, smax, ORC_ANG_PANELS * ORC_ANG_SUB);
+}
+
+/* fraction of the one-sided integral below psi >= 0 */
+double orc_ang_cdf(double x, double psi) {
+  const double smax = asinh(orc_ang_psimax(x));
+  const double s = asinh(fabs(psi));
+  if (s >= smax) return 1.0;
+  const int m = 2 * (int)ceil(0.5 * ORC_ANG_PANELS * ORC_ANG_SUB * s / smax) + 2;
+  return orc_ang_int(x, 0.0, s, m) / orc_ang_norm(x);
+}
+
+/* psi >= 0 with cdf(psi) = u: cumulative Simpson panels in s, then
+ * bisection on s inside the panel that holds u */
+double orc_ang_sample(double x, double u) {
+  const double smax = asinh(orc_ang_psimax(x));
+  const double h = smax / ORC_ANG_PANELS;
+  double cum[ORC_ANG_PANELS + 1];
+  cum[0] = 0.0;
+  for (int k = 0; k < ORC_ANG_PANELS; ++k)
+    cum[k + 1] = cum[k] + orc_ang_int(x, k * h, (k + 1) * h, ORC_ANG_SUB);
+  const double target = u * cum[ORC_ANG_PANELS];
+  int k = 0;
+  while (k < ORC_ANG_PANELS - 1 && cum[k + 1] < target) ++k;
+  double a = k * h, b = (k + 1) * h;
+  for (int it = 0; it < 60; ++it) {
+    const double m = 0.5 * (a + b);
+    if (cum[k] + orc_ang_int(x, k * h, m, ORC_ANG_SUB) < target) a = m; else b = m;
+  }
+  return sinh(0.5 * (a + b));
+}
+
+void orc_K13_batch(const double* z, double* out, int64_t n) {
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) out[i] = orc_K13(z[i]);
+}
+void orc_K23_batch(const double* z, double* out, int64_t n) {
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) out[i] = orc_K23(z[i]);
+}
+void orc_ang_parts_batch(const double* x, const double* psi, double* sig, double* pi,
+                         int64_t n) {
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) orc_ang_parts(x[i], psi[i], &sig[i], &pi[i]);
+}
+void orc_ang_norm_batch(const double* x, double* out, int64_t n) {
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t i = 0; i < n; ++i) out[i] = orc_ang_norm(x[i]);
+}
+void orc_ang_cdf_batch(const double* x, const double* psi, double* out, int64_t n) {
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t i = 0; i < n; ++i) out[i] = orc_ang_cdf(x[i], psi[i]);
+}
+void orc_ang_sample_batch(const double* x, const double* u, double* out, int64_t n) {
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t i = 0; i < n; ++i) out[i] = orc_ang_sample(x[i], u[i]);
+}
+
 int orc_init(void) {
   if (orc_ready) return 0;
   long double a_ld = orc_solve_a();
@@ -454,7 +588,9 @@ typedef struct orc_problem {
    * 1/n_try of dN each; a particle-step takes part with probability
    * select_prob and then carries weight k w / select_prob */
   int32_t n_try;
-  int32_t pad1;
+  /* 1: turn each photon by theta = psi / gamma out of the plane of the
+   * step's orbit (angular spread of Eqs. (5)-(6); 0: collinear) */
+  int32_t ang_spread;
   double select_prob;
 } orc_problem;
 
@@ -601,6 +737,9 @@ int orc_run(const orc_problem* P, int64_t n, int32_t nsteps, int64_t t0,
       orc_fields(P, x, y, z, step, E, B);
       double uo[3] = {u[0], u[1], u[2]};
       orc_boris(u, E, B, q, dtn);
+      /* momentum change of the push (before any LL kick): its component
+       * across the mean momentum lies in the plane of the step's orbit */
+      double du[3] = {u[0] - uo[0], u[1] - uo[1], u[2] - uo[2]};
       double ua[3] = {0.5 * (uo[0] + u[0]), 0.5 * (uo[1] + u[1]),
                       0.5 * (uo[2] + u[2])};
       double ua2 = ua[0] * ua[0] + ua[1] * ua[1] + ua[2] * ua[2];
@@ -667,9 +806,27 @@ int orc_run(const orc_problem* P, int64_t n, int32_t nsteps, int64_t t0,
           if (slot < ph->capacity) {
             double un = sqrt(ua2);
             double inv = un > 0.0 ? 1.0 / un : 0.0;
+            double dir[3] = {ua[0] * inv, ua[1] * inv, ua[2] * inv};
+            if (P->ang_spread) {
+              /* psi from the angular density at this x (its own Philox
+               * block, tag 0x20000 + trial), theta = psi / gamma, turned
+               * about the orbit normal n = u_avg x du / |u_avg x du| */
+              uint32_t ca[4] = {pid[i], (uint32_t)step, 0x20000u + (uint32_t)j,
+                                P->ensemble}, ra[4];
+              orc_philox4x32_10(ca, key, ra);
+              double psi = orc_ang_sample(xs, ((double)ra[0] + 0.5) * 0x1p-32);
+              if (ra[1] & 0x80000000u) psi = -psi;
+              double th = psi / ga;
+              double c[3] = {ua[1] * du[2] - ua[2] * du[1], ua[2] * du[0] - ua[0] * du[2],
+                             ua[0] * du[1] - ua[1] * du[0]};
+              double cn = sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+              if (cn > 0.0 && un > 0.0) {
+                double ct = cos(th), st = sin(th);
+                for (int a = 0; a < 3; ++a) dir[a] = ct * dir[a] + st * c[a] / cn;
+              }
+            }
             ph->x[slot] = x; ph->y[slot] = y; ph->z[slot] = z;
-            ph->nx[slot] = ua[0] * inv; ph->ny[slot] = ua[1] * inv;
-            ph->nz[slot] = ua[2] * inv;
+            ph->nx[slot] = dir[0]; ph->ny[slot] = dir[1]; ph->nz[slot] = dir[2];
             ph->eps[slot] = eps; ph->weight[slot] = kw;
             ph->pid[slot] = pid[i]; ph->step[slot] = (uint32_t)step;
             s_rec++;

@@ -737,9 +737,6 @@ int orc_run(const orc_problem* P, int64_t n, int32_t nsteps, int64_t t0,
       orc_fields(P, x, y, z, step, E, B);
       double uo[3] = {u[0], u[1], u[2]};
       orc_boris(u, E, B, q, dtn);
-      /* momentum change of the push (before any LL kick): its component
-       * across the mean momentum lies in the plane of the step's orbit */
-      double du[3] = {u[0] - uo[0], u[1] - uo[1], u[2] - uo[2]};
       double ua[3] = {0.5 * (uo[0] + u[0]), 0.5 * (uo[1] + u[1]),
                       0.5 * (uo[2] + u[2])};
       double ua2 = ua[0] * ua[0] + ua[1] * ua[1] + ua[2] * ua[2];
@@ -810,15 +807,17 @@ int orc_run(const orc_problem* P, int64_t n, int32_t nsteps, int64_t t0,
             if (P->ang_spread) {
               /* psi from the angular density at this x (its own Philox
                * block, tag 0x20000 + trial), theta = psi / gamma, turned
-               * about the orbit normal n = u_avg x du / |u_avg x du| */
+               * toward the orbit normal n = u^n x u^(n+1) / |u^n x u^(n+1)|
+               * (the plane of the step's orbit holds both momenta; the LL
+               * kick only rescales u^(n+1)) */
               uint32_t ca[4] = {pid[i], (uint32_t)step, 0x20000u + (uint32_t)j,
                                 P->ensemble}, ra[4];
               orc_philox4x32_10(ca, key, ra);
               double psi = orc_ang_sample(xs, ((double)ra[0] + 0.5) * 0x1p-32);
               if (ra[1] & 0x80000000u) psi = -psi;
               double th = psi / ga;
-              double c[3] = {ua[1] * du[2] - ua[2] * du[1], ua[2] * du[0] - ua[0] * du[2],
-                             ua[0] * du[1] - ua[1] * du[0]};
+              double c[3] = {uo[1] * u[2] - uo[2] * u[1], uo[2] * u[0] - uo[0] * u[2],
+                             uo[0] * u[1] - uo[1] * u[0]};
               double cn = sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
               if (cn > 0.0 && un > 0.0) {
                 double ct = cos(th), st = sin(th);

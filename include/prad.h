@@ -139,6 +139,22 @@ typedef struct prad_config {
                                Omega tau_EM < 1 with tau_EM the field period
                                the particle sees, 1 / (omega_L |1 - dir beta_x|)
                                (Eq. (3) context; PLANE_WAVE fields only)   */
+/* Angular spread of the emission (Eqs. (5)-(6), the circular-motion
+ * spectrum by angle), an option beside the paper's collinear photons:
+ * every record's direction is turned out of the plane of the step's orbit
+ * (the plane of u^n and u^(n+1)) by theta = psi / gamma, gamma of the step's
+ * mean momentum, psi drawn from Eq. (5)'s density at the record's
+ * x = omega / omega_c, proportional to (1 + psi^2)^2 K_2/3(xi)^2 +
+ * (1 + psi^2) psi^2 K_1/3(xi)^2 with xi = (x/2)(1 + psi^2)^(3/2) (Eq. (6)).
+ * The uniform and the sign come from Philox block (pid, step, 0x20000 + j,
+ * ensemble), j the trial; the draw of psi is a table lookup (~2e-4
+ * relative in psi).  Energies, weights, ledgers and counters are those of
+ * the collinear run.  Table sampler only (prad_init fails with
+ * PRAD_ERR_ARG otherwise), not in batched calls (prad_push_emit_batch and
+ * prad_autotune_batch fail with PRAD_ERR_ARG); the context holds a 225 KB
+ * device table, built on the host at the first such prad_init of the
+ * process (~0.3 s). */
+#define PRAD_DIAG_ANGLE_SPREAD 2
 
 /* ---- field description ------------------------------------------------- */
 typedef struct prad_fields {
@@ -416,6 +432,17 @@ int prad_mlp_wait_selftest(prad_ctx* ctx);
 
 /* ln G^-1(r) from the device table for n device uniforms. */
 int prad_ginv_eval(prad_ctx* ctx, const float* r, float* lnx, int64_t n);
+
+/* Angular spread (Eqs. (5)-(6), PRAD_DIAG_ANGLE_SPREAD): psi = gamma theta
+ * as the step kernels draw it, for n photons of device x[i] (omega/omega_c,
+ * float32) and device Philox words words[2i] (the uniform
+ * (w + 1/2) 2^-32 of psi's one-sided CDF) and words[2i + 1] (bit 31: the
+ * sign), into device psi[i].  Asynchronous on the context's stream.
+ * PRAD_ERR_STATE if the context was created without
+ * PRAD_DIAG_ANGLE_SPREAD; PRAD_ERR_ARG for a NULL array with n > 0 or
+ * n < 0. */
+int prad_angle_eval(prad_ctx* ctx, const float* x, const uint32_t* words, float* psi,
+                    int64_t n);
 
 /* ---- angular distribution (Fig. 4) -------------------------------------------
  * Histogram of the emitted energy (record energy x weight) of the photon

@@ -3,6 +3,7 @@
 // sampling table, launches and read-back.  Compute happens only in kernels.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdint>
@@ -71,6 +72,7 @@ struct prad_ctx {
   float* d_mlp_grad = nullptr;
   __nv_bfloat16* d_mlp_w2 = nullptr;
   float* d_ginv = nullptr;       // ln G^-1 on a logit grid
+  float* d_ang = nullptr;        // angular-spread table (PRAD_DIAG_ANGLE_SPREAD)
   float* d_mlp_partial = nullptr;
   float* d_mlp_loss_part = nullptr;
   float* d_mlp_loss = nullptr;
@@ -275,6 +277,133 @@ void build_ginv(std::vector<float>& out) {
   (void)norm;
 }
 
+// ---- angular spread table (Eqs. (5)-(6)) -----------------------------------
+// K_1/3 and K_2/3 on nodes uniform in ln z over [kKz0, kKz0 + (n - 1) kKh]:
+// K_nu(z) = int_0^inf exp(-z cosh t) cosh(nu t) dt and its z-derivative
+// -int_0^inf cosh t exp(-z cosh t) cosh(nu t) dt by 16-point Gauss-Legendre
+// panels (scaled by e^z against underflow); between nodes cubic Hermite in
+// (ln z, ln K).  The density needs z = xi in [x/2, x/2 + 50] for x in the
+// table's range: [5e-9, 70].
+struct BesselThirds {
+  static constexpr double kKz0 = -21.0, kKh = 1.0 / 256.0;
+  static constexpr int kN = 26 * 256 + 1;  // up to ln z = 5
+  std::vector<double> l13, l23, d13, d23;  // ln K, d ln K / d ln z
+  explicit BesselThirds(const GaussLegendre& gl)
+      : l13(kN), l23(kN), d13(kN), d23(kN) {
+    for (int k = 0; k < kN; ++k) {
+      const double z = std::exp(kKz0 + k * kKh);
+      const double tmax = std::acosh(1.0 + 745.0 / z);
+      const double width = 0.5 / std::max(1.0, std::sqrt(z / 5.0));
+      double a1 = 0, a2 = 0, b1 = 0, b2 = 0;
+      for (double a = 0.0; a < tmax; a += width) {
+        const double mid = a + 0.5 * width, half = 0.5 * width;
+        for (int q = 0; q < 16; ++q) {
+          const double t = mid + half * gl.x[q];
+          const double ch = std::cosh(t);
+          const double e = half * gl.w[q] * std::exp(-z * (ch - 1.0));
+          const double c1 = std::cosh(t / 3.0), c2 = 2.0 * c1 * c1 - 1.0;  // cosh(2t/3)
+          a1 += e * c1;
+          a2 += e * c2;
+          b1 += e * c1 * ch;
+          b2 += e * c2 * ch;
+        }
+      }
+      l13[k] = std::log(a1) - z;
+      l23[k] = std::log(a2) - z;
+      d13[k] = -z * b1 / a1;
+      d23[k] = -z * b2 / a2;
+    }
+  }
+  void eval(double z, double* k13, double* k23) const {
+    double u = (std::log(z) - kKz0) / kKh;
+    u = std::min(std::max(u, 0.0), static_cast<double>(kN - 1));
+    const int i = std::min(static_cast<int>(u), kN - 2);
+    const double t = u - i, t2 = t * t, t3 = t2 * t;
+    const double h00 = 2 * t3 - 3 * t2 + 1, h10 = t3 - 2 * t2 + t, h01 = -2 * t3 + 3 * t2,
+                 h11 = t3 - t2;
+    *k13 = std::exp(h00 * l13[i] + h10 * kKh * d13[i] + h01 * l13[i + 1] + h11 * kKh * d13[i + 1]);
+    *k23 = std::exp(h00 * l23[i] + h10 * kKh * d23[i] + h01 * l23[i + 1] + h11 * kKh * d23[i + 1]);
+  }
+};
+
+// The table of y = psi / (v s(x)) (geometry in prad_internal.h): per row x,
+// the one-sided integral of Eq. (5)'s density in psi, (1 + psi^2)^2
+// K_2/3(xi)^2 + (1 + psi^2) psi^2 K_1/3(xi)^2 with xi = (x/2)(1 + psi^2)^(3/2),
+// by 4-point Gauss-Legendre on 1024 equal steps in s = asinh psi up to
+// xi = x/2 + 50; cumulative from below and tail from above (so 1 - u keeps
+// its accuracy); psi for each column's u from the cubic Hermite form of the
+// cumulative over the step that holds it (values and slopes at its ends).
+void build_ang_table(std::vector<float>& out) {
+  GaussLegendre gl16;
+  const BesselThirds kb(gl16);
+  static const double g4x[4] = {-0.8611363115940526, -0.3399810435848563, 0.3399810435848563,
+                                0.8611363115940526};
+  static const double g4w[4] = {0.3478548451374538, 0.6521451548625461, 0.6521451548625461,
+                                0.3478548451374538};
+  const int M = 1024;
+  std::vector<double> seg(M), D(M + 1), lo(M + 1), hi(M + 1);
+  out.assign(static_cast<size_t>(kAngNL) * kAngNV, 0.0f);
+  for (int i = 0; i < kAngNL; ++i) {
+    const double lx = kAngLx0 + i * (kAngLx1 - kAngLx0) / (kAngNL - 1);
+    const double x = std::exp(lx);
+    auto dens_s = [&](double sv) {  // density in s: (sigma + pi) dpsi/ds
+      const double psi = std::sinh(sv), q = 1.0 + psi * psi;
+      double k13, k23;
+      kb.eval(0.5 * x * q * std::sqrt(q), &k13, &k23);
+      return (q * q * k23 * k23 + q * psi * psi * k13 * k13) * std::cosh(sv);
+    };
+    const double qmax = std::pow((x + 100.0) / x, 2.0 / 3.0);
+    const double hs = std::asinh(std::sqrt(qmax - 1.0)) / M;
+    for (int k = 0; k <= M; ++k) D[k] = dens_s(k * hs);
+    for (int k = 0; k < M; ++k) {
+      double acc = 0.0;
+      for (int q = 0; q < 4; ++q) acc += g4w[q] * dens_s((k + 0.5 + 0.5 * g4x[q]) * hs);
+      seg[k] = 0.5 * hs * acc;
+    }
+    lo[0] = 0.0;
+    for (int k = 0; k < M; ++k) lo[k + 1] = lo[k] + seg[k];
+    hi[M] = 0.0;
+    for (int k = M - 1; k >= 0; --k) hi[k] = hi[k + 1] + seg[k];
+    const double total = lo[M];
+    const double sc = std::cbrt(2.0 / x) * std::pow(1.0 + x, -1.0 / 6.0);
+    for (int j = 1; j < kAngNV; ++j) {
+      const double v = j * kAngVmax / (kAngNV - 1), w = v * v;
+      int k;
+      double m;  // mass below the target inside step k
+      if (w <= std::log(2.0)) {  // u <= 1/2
+        const double target = -std::expm1(-w) * total;
+        int a = 0, b = M;
+        while (b - a > 1) {
+          const int mid = (a + b) / 2;
+          (lo[mid] <= target ? a : b) = mid;
+        }
+        k = a;
+        m = target - lo[k];
+      } else {
+        const double tail = std::exp(-w) * total;  // (1 - u) total
+        int a = 0, b = M;
+        while (b - a > 1) {
+          const int mid = (a + b) / 2;
+          (hi[mid] > tail ? a : b) = mid;
+        }
+        k = a;
+        m = seg[k] - (tail - hi[k + 1]);
+      }
+      m = std::min(std::max(m, 0.0), seg[k]);
+      // C(tau) = seg h01 + hs D_k h10 + hs D_k+1 h11 = m, by bisection
+      double ta = 0.0, tb = 1.0;
+      for (int it = 0; it < 60; ++it) {
+        const double t = 0.5 * (ta + tb), t2 = t * t, t3 = t2 * t;
+        const double c = seg[k] * (-2 * t3 + 3 * t2) + hs * D[k] * (t3 - 2 * t2 + t) +
+                         hs * D[k + 1] * (t3 - t2);
+        (c < m ? ta : tb) = t;
+      }
+      const double psi = std::sinh((k + 0.5 * (ta + tb)) * hs);
+      out[static_cast<size_t>(i) * kAngNV + j] = static_cast<float>(psi / (v * sc));
+    }
+  }
+}
+
 uint16_t to_bf16(float f) {  // round to nearest even
   uint32_t u;
   std::memcpy(&u, &f, 4);
@@ -411,6 +540,7 @@ void fill_common(const prad_ctx* c, StepParams<R>& p, const prad_fields& f) {
   p.wl = R(0);
   p.mlp = mlp_dev(c);
   p.ginv = c->d_ginv;
+  p.ang = c->d_ang;
   // field, normalised: E by m c omega_ref / e, B by m omega_ref / e
   const double w = c->cfg.omega_ref;
   p.field_kind = f.kind;
@@ -709,8 +839,11 @@ int prad_init(prad_ctx** out, const prad_config* cfg) {
     return fail(nullptr, PRAD_ERR_ARG, "prad_init: n_try > 1 needs the table sampler");
   if (!(cfg->select_prob >= 0.0 && cfg->select_prob <= 1.0))
     return fail(nullptr, PRAD_ERR_ARG, "prad_init: select_prob outside [0, 1]");
-  if (cfg->diagnostics & ~PRAD_DIAG_WIGGLER)
+  if (cfg->diagnostics & ~(PRAD_DIAG_WIGGLER | PRAD_DIAG_ANGLE_SPREAD))
     return fail(nullptr, PRAD_ERR_ARG, "prad_init: unknown diagnostics bit");
+  if ((cfg->diagnostics & PRAD_DIAG_ANGLE_SPREAD) && cfg->sampler != PRAD_SAMPLER_TABLE)
+    return fail(nullptr, PRAD_ERR_ARG,
+                "prad_init: PRAD_DIAG_ANGLE_SPREAD needs the table sampler");
 
   prad_ctx* c = new (std::nothrow) prad_ctx();
   if (!c) return fail(nullptr, PRAD_ERR_ARG, "prad_init: out of host memory");
@@ -745,6 +878,15 @@ int prad_init(prad_ctx** out, const prad_config* cfg) {
     build_tables(t32, t64);
     build_ginv(ginv_host);
   });
+  if (cfg->diagnostics & PRAD_DIAG_ANGLE_SPREAD) {
+    // built on first use in the process (~0.1 s), like the tables above
+    static std::once_flag ang_once;
+    static std::vector<float> ang_host;
+    std::call_once(ang_once, [] { build_ang_table(ang_host); });
+    CKI(cudaMalloc(&c->d_ang, ang_host.size() * sizeof(float)));
+    CKI(cudaMemcpy(c->d_ang, ang_host.data(), ang_host.size() * sizeof(float),
+                   cudaMemcpyHostToDevice));
+  }
   CKI(cudaMalloc(&c->d_tab32, kNTab * sizeof(float4)));
   CKI(cudaMalloc(&c->d_tab64, kNTab * sizeof(Coef4d)));
   CKI(cudaMemcpy(c->d_tab32, t32.data(), kNTab * sizeof(float4), cudaMemcpyHostToDevice));
@@ -820,6 +962,7 @@ int prad_destroy(prad_ctx* c) {
   cudaFree(c->d_mlp_w2);
   cudaFree(c->d_mlp_loss);
   cudaFree(c->d_ginv);
+  cudaFree(c->d_ang);
   cudaFree(c->d_mlp_partial);
   cudaFree(c->d_mlp_loss_part);
   delete c;
@@ -1169,6 +1312,8 @@ int prad_push_emit_batch(prad_ctx* c, const prad_ensemble* ens, int32_t n_ens, i
     return fail(c, PRAD_ERR_ARG, "push_emit_batch: bad argument");
   if (c->cfg.precision != PRAD_FP32)
     return fail(c, PRAD_ERR_ARG, "push_emit_batch: FP32 only");
+  if (c->d_ang)
+    return fail(c, PRAD_ERR_ARG, "push_emit_batch: no angular spread in batched calls");
   for (int k = 0; k < n_ens; ++k) {
     int rc = check_ensemble(c, ens[k], k);
     if (rc != PRAD_OK) return rc;
@@ -1224,6 +1369,8 @@ int prad_autotune_batch(prad_ctx* c, const prad_ensemble* ens, int32_t n_ens, in
     return fail(c, PRAD_ERR_ARG, "autotune_batch: bad argument");
   if (c->cfg.precision != PRAD_FP32)
     return fail(c, PRAD_ERR_ARG, "autotune_batch: FP32 only");
+  if (c->d_ang)
+    return fail(c, PRAD_ERR_ARG, "autotune_batch: no angular spread in batched calls");
   for (int k = 0; k < n_ens; ++k) {
     int rc = check_ensemble(c, ens[k], k);
     if (rc != PRAD_OK) return rc;
@@ -1526,6 +1673,16 @@ int prad_batch_balance(prad_ctx* c, double* efficiency, int32_t* ctas) {
   }
   *efficiency = mx > 0.0 ? sum / (mx * static_cast<double>(busy.size())) : 0.0;
   if (ctas) *ctas = c->batch_grid;
+  return PRAD_OK;
+}
+
+int prad_angle_eval(prad_ctx* c, const float* x, const uint32_t* words, float* psi, int64_t n) {
+  if (!c || n < 0 || (n > 0 && (!x || !words || !psi)))
+    return fail(c, PRAD_ERR_ARG, "angle_eval: bad argument");
+  if (!c->d_ang)
+    return fail(c, PRAD_ERR_STATE, "angle_eval: context created without PRAD_DIAG_ANGLE_SPREAD");
+  if (n == 0) return PRAD_OK;
+  CK(c, launch_angle_eval(c->d_ang, x, words, psi, n, c->stream));
   return PRAD_OK;
 }
 

@@ -35,6 +35,20 @@ constexpr uint64_t kThr = 0x9C26B9CE251FFCB8ull;
 constexpr double kTScale = kN1 / kCbrtA;
 constexpr double kXScale = kN2 / (kXmax - kA);
 
+// ---- angular spread of the emission (Eqs. (5)-(6), PRAD_DIAG_ANGLE_SPREAD)
+// psi = gamma theta, theta the angle out of the plane of the orbit, is drawn
+// from Eq. (5)'s density at the photon's x = omega / omega_c.  The table
+// holds y = psi / (v s(x)) on kAngNL rows uniform in ln x over
+// [kAngLx0, kAngLx1] and kAngNV columns uniform in v = sqrt(-ln(1 - u))
+// over [0, kAngVmax] (u the uniform, one-sided CDF), with
+// s(x) = (2/x)^(1/3) (1 + x)^(-1/6), psi's scale for small and large x;
+// bilinear interpolation, x clamped into the rows' range.
+constexpr int kAngNL = 225;
+constexpr int kAngNV = 257;
+constexpr double kAngLx0 = -18.420680743952367;  // ln 1e-8
+constexpr double kAngLx1 = 3.6888794541139363;   // ln 40
+constexpr double kAngVmax = 4.8;                 // u <= 1 - 2^-33: v <= 4.79
+
 // float -> double by the IEEE-754 formats (normal numbers: the exponent
 // rebiased by 1023 - 127 = 896, the 23 fraction bits moved to the top of
 // the 52), with integer instructions; zeros, subnormals, infinities and NaNs
@@ -132,6 +146,7 @@ struct StepParams {
   R cp_dt;                    // (5 sqrt3 / 6) alpha dtn
   MlpDev mlp;
   const float* ginv;          // G^-1 table (ln x on a logit(r) grid)
+  const float* ang;           // angular-spread table (PRAD_DIAG_ANGLE_SPREAD), else null
   // tile-sorted Yee gather (k_push_emit_tiled)
   const int4* work;           // (tile, first, end, 0) per work item
   const unsigned int* work_count;
@@ -266,6 +281,10 @@ cudaError_t launch_angular_hist(const AngularArgs& a, int grid, cudaStream_t s);
 int mlp_finish_blocks_per_sm();
 cudaError_t launch_ginv_eval(const float* tab, const float* r, float* out, int64_t n,
                              cudaStream_t s);
+// psi of the angular spread for x[i] and the Philox words words[2i],
+// words[2i + 1] (the table lookup of the step kernels; push_emit.cu)
+cudaError_t launch_angle_eval(const float* tab, const float* x, const uint32_t* words,
+                              float* psi, int64_t n, cudaStream_t s);
 cudaError_t launch_ledger_reduce(const double* a, const double* b, int64_t n,
                                  double* partials, int nblocks, double* out,
                                  cudaStream_t s);

@@ -160,6 +160,64 @@ template <>
 __device__ __forceinline__ double unit_uniform<double>(uint32_t w) {
   return fma(static_cast<double>(w), 0x1p-32, 0x1p-33);
 }
+// psi = gamma theta of the emission's angular spread (Eqs. (5)-(6)) at x,
+// from the table (prad_internal.h): the uniform u = (w0 + 1/2) 2^-32 of the
+// one-sided CDF, the sign from bit 31 of w1.  v = sqrt(-ln(1 - u)) is taken
+// as sqrt(-log1p(-u)) below u = 1/2 and from 1 - u = (~w0 + 1/2) 2^-32
+// (exact) above it.  FP32 throughout (the table's accuracy, ~2e-4 in psi,
+// is the limit).
+template <typename R>
+__device__ __forceinline__ R ang_psi(const float* __restrict__ tab, R x, uint32_t w0,
+                                     uint32_t w1) {
+  const float xf = static_cast<float>(x);
+  const float lx = logf(xf);
+  float fi = (lx - static_cast<float>(kAngLx0)) *
+             static_cast<float>((kAngNL - 1) / (kAngLx1 - kAngLx0));
+  fi = fminf(fmaxf(fi, 0.0f), static_cast<float>(kAngNL - 1));
+  const int i = min(static_cast<int>(fi), kAngNL - 2);
+  const float ti = fi - static_cast<float>(i);
+  const float w = w0 < 0x80000000u
+                      ? -log1pf(-fmaf(static_cast<float>(w0), 0x1p-32f, 0x1p-33f))
+                      : -logf(fmaf(static_cast<float>(~w0), 0x1p-32f, 0x1p-33f));
+  const float v = sqrtf(fmaxf(w, 0.0f));
+  const float fj = fminf(v * static_cast<float>((kAngNV - 1) / kAngVmax),
+                         static_cast<float>(kAngNV - 1));
+  const int j = min(static_cast<int>(fj), kAngNV - 2);
+  const float tj = fj - static_cast<float>(j);
+  const float* r0 = tab + i * kAngNV + j;
+  const float* r1 = r0 + kAngNV;
+  const float y0 = fmaf(tj, __ldg(r0 + 1) - __ldg(r0), __ldg(r0));
+  const float y1 = fmaf(tj, __ldg(r1 + 1) - __ldg(r1), __ldg(r1));
+  const float y = fmaf(ti, y1 - y0, y0);
+  // s(x) = (2/x)^(1/3) (1 + x)^(-1/6)
+  const float sc = expf((0.693147181f - lx) * (1.0f / 3.0f) - log1pf(xf) * (1.0f / 6.0f));
+  const float psi = y * v * sc;
+  return static_cast<R>((w1 & 0x80000000u) ? -psi : psi);
+}
+
+__device__ __forceinline__ void sincos_r(float v, float* s, float* c) { sincosf(v, s, c); }
+__device__ __forceinline__ void sincos_r(double v, double* s, double* c) { sincos(v, s, c); }
+
+// The record direction (dx, dy, dz) = u_avg turned by theta = psi / gamma
+// (iga = 1 / gamma) toward the orbit normal u^n x u^(n+1), keeping |u_avg|
+// (ua2 = |u_avg|^2; the flush normalises).
+template <typename R>
+__device__ __forceinline__ void ang_turn(const float* tab, R xs, uint32_t w0, uint32_t w1, R iga,
+                                      R ua2, R ux, R uy, R uz, R nux, R nuy, R nuz, R& dx,
+                                      R& dy, R& dz) {
+  const R th = ang_psi<R>(tab, xs, w0, w1) * iga;
+  const R cx = uy * nuz - uz * nuy, cy = uz * nux - ux * nuz, cz = ux * nuy - uy * nux;
+  const R c2 = cx * cx + cy * cy + cz * cz;
+  if (c2 > R(0)) {
+    R st, ct;
+    sincos_r(th, &st, &ct);
+    const R f = st * sqrt(ua2 / c2);
+    dx = ct * dx + f * cx;
+    dy = ct * dy + f * cy;
+    dz = ct * dz + f * cz;
+  }
+}
+
 __device__ __forceinline__ float rsq(float v) { return rsqrtf(v); }
 __device__ __forceinline__ double rsq(double v) { return rsqrt(v); }
 __device__ __forceinline__ float rcp(float v) { return __fdividef(1.0f, v); }
@@ -778,7 +836,7 @@ __device__ __forceinline__ void load_state(const StepParams<R>& P, int64_t i, bo
 // there the streamed state passes through L1 and would evict it.  (Fused
 // launches keep it in L1: the copy's 20 KB would cost them a resident block
 // per SM.)
-template <typename R, int SAMP, int ONE, bool CTRL>
+template <typename R, int SAMP, int ONE, int CTRL>
 constexpr bool kSharedTab =
     sizeof(R) == 4 && SAMP == PRAD_SAMPLER_TABLE && ONE != 0 && !CTRL;
 
@@ -798,7 +856,7 @@ constexpr bool kSharedTab =
 // STD: the standard configuration (LL kick applied, field form of H_eff,
 // three dimensions, two for the Yee grid) fixed at compile time, so the step
 // tests no mode.
-template <typename R, int FIELD, int SAMP, int ONE = 0, bool CTRL = false,
+template <typename R, int FIELD, int SAMP, int ONE = 0, int CTRL = 0,
           bool STD = false, bool STAB = false, int PWS = 0, class G, class ST>
 __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const uint32_t (&rk)[20],
                                                  const G& gat,
@@ -963,7 +1021,8 @@ __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const u
       // 8. Monte Carlo emission: proposal x = P^-1(R'), dN of Eq. (13);
       //    one trial with the Philox words (w0, w1) and uniform Rd, dN
       //    scaled by dn_scale, record weights by wmul, for lanes with part
-      auto trial = [&](uint32_t w0, uint32_t w1, R Rd, R dn_scale, R wmul, bool part) {
+      auto trial = [&](uint32_t w0, uint32_t w1, R Rd, R dn_scale, R wmul, bool part,
+                       uint32_t j) {
         R xs, g;
         sample_x_g<STAB>(P, w0, w1, xs, g, stab);
         const R dN = P.cn_dt * Om * g * rcp(xs) * dn_scale;
@@ -978,25 +1037,35 @@ __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const u
           const R eps = xs * epsc;
           const R kw = k * w * wmul;
           if (want) le.add(kw * eps);
+          R dx = ax, dy = ay, dz = az;
+          if constexpr (CTRL == 2) {
+            // angular spread (Eqs. (5)-(6)): the direction turned by
+            // theta = psi / gamma toward the orbit normal u^n x u^(n+1)
+            // (its own Philox block, tag 0x20000 + trial; the record keeps
+            // |u_avg| and is normalised at the flush)
+            const uint4 ra = philox10_rk(make_uint4(pid, step, 0x20000u + j, P.ensemble), rk);
+            ang_turn<R>(P.ang, xs, ra.x, ra.y, iga, ua2, ux, uy, uz, nux, nuy, nuz, dx, dy, dz);
+          }
           const float rec[8] = {static_cast<float>(xn), static_cast<float>(yn),
-                                static_cast<float>(zn), static_cast<float>(ax),
-                                static_cast<float>(ay), static_cast<float>(az),
+                                static_cast<float>(zn), static_cast<float>(dx),
+                                static_cast<float>(dy), static_cast<float>(dz),
                                 static_cast<float>(eps), static_cast<float>(kw)};
           stage_photon_mask(stage, fill, pout, want, mask, rec, pid, step);
         }
       };
       if constexpr (!CTRL) {
-        trial(rnd.x, rnd.y, Rr, R(1), R(1), live);
+        trial(rnd.x, rnd.y, Rr, R(1), R(1), live, 0u);
       } else {
         // super-photon control: a particle takes part with probability
         // sel_q (Philox word 3 of trial 0), with weight 1 / sel_q; ntry
         // trials of 1 / ntry of dN each, trial j >= 1 from its own block
         const bool part = live && unit_uniform<R>(rnd.w) < P.sel_q;
-        trial(rnd.x, rnd.y, Rr, P.inv_ntry, P.inv_sel_q, part);
+        trial(rnd.x, rnd.y, Rr, P.inv_ntry, P.inv_sel_q, part, 0u);
         for (int j = 1; j < P.ntry; ++j) {
           const uint4 cj = make_uint4(pid, step, 0x10000u + static_cast<uint32_t>(j), P.ensemble);
           const uint4 rb = philox10_rk(cj, rk);
-          trial(rb.x, rb.y, unit_uniform<R>(rb.z), P.inv_ntry, P.inv_sel_q, part);
+          trial(rb.x, rb.y, unit_uniform<R>(rb.z), P.inv_ntry, P.inv_sel_q, part,
+                static_cast<uint32_t>(j));
         }
       }
     } else {
@@ -1192,7 +1261,7 @@ __device__ __forceinline__ StepParams<R> spec_params(const StepParams<R>& in) {
 // PF: 0 no prefetch (multi-step launches); 1 one step per launch, the next
 // particle prefetched; 2 the same for a dense launch (see dense_launch).
 // PWS: the plane wave's signs at compile time (0: from the parameters).
-template <typename R, int FIELD, int SAMP, int PF, bool CTRL, bool STD = false, int PWS = 0>
+template <typename R, int FIELD, int SAMP, int PF, int CTRL, bool STD = false, int PWS = 0>
 __global__ void __launch_bounds__(256, (PF ? PRAD_PF_MINB : MinBlocks<R, FIELD, SAMP>::value))
     k_push_emit(const StepParams<R> P_arg) {
 #ifdef PRAD_SPEC
@@ -1398,7 +1467,7 @@ int batch_max_blocks_per_sm(int block, int sampler, bool ctrl, bool std_cfg) {
 // (+ halo, periodic) in shared memory with coalesced row loads, then runs the
 // same per-particle path with the shared-memory gather.
 // ---------------------------------------------------------------------------
-template <typename R, bool CTRL, bool STD = false>
+template <typename R, int CTRL, bool STD = false>
 __global__ void __launch_bounds__(256, 3) k_push_emit_tiled(const StepParams<R> P_arg) {
 #ifdef PRAD_SPEC
   const StepParams<R> P = spec_params(P_arg);
@@ -1456,7 +1525,7 @@ __global__ void __launch_bounds__(256, 3) k_push_emit_tiled(const StepParams<R> 
 #ifndef __CUDACC_RTC__
 // The standard-configuration variant (STD) exists for FP32 without control
 // or diagnostics.
-template <typename R, int FIELD, bool CTRL>
+template <typename R, int FIELD, int CTRL>
 constexpr bool kHasStd = sizeof(R) == 4 && !CTRL;
 
 // LL kick applied, field-form H_eff, the field's usual dimensions and unit
@@ -1467,7 +1536,7 @@ bool std_config(const StepParams<R>& p, int dims) {
          p.abs_q == R(1);
 }
 
-template <typename R, bool CTRL, bool STD>
+template <typename R, int CTRL, bool STD>
 cudaError_t launch_tiled_v(const StepParams<R>& p, int max_work, int block, cudaStream_t s) {
   // dynamic tile (46.5 KB) + static photon staging exceed the 48 KB default
   cudaError_t e = cudaFuncSetAttribute(k_push_emit_tiled<R, CTRL, STD>,
@@ -1481,15 +1550,16 @@ cudaError_t launch_tiled_v(const StepParams<R>& p, int max_work, int block, cuda
 template <typename R>
 cudaError_t launch_push_emit_tiled(const StepParams<R>& p, int max_work, int block,
                                    cudaStream_t s) {
+  if (p.ang != nullptr) return launch_tiled_v<R, 2, false>(p, max_work, block, s);
   const bool ctrl = p.ntry > 1 || p.sel_q < R(1) || p.diag != 0;
-  if (ctrl) return launch_tiled_v<R, true, false>(p, max_work, block, s);
-  if constexpr (kHasStd<R, PRAD_FIELD_YEE2D, false>)
-    if (std_config(p, 2)) return launch_tiled_v<R, false, true>(p, max_work, block, s);
-  return launch_tiled_v<R, false, false>(p, max_work, block, s);
+  if (ctrl) return launch_tiled_v<R, 1, false>(p, max_work, block, s);
+  if constexpr (kHasStd<R, PRAD_FIELD_YEE2D, 0>)
+    if (std_config(p, 2)) return launch_tiled_v<R, 0, true>(p, max_work, block, s);
+  return launch_tiled_v<R, 0, false>(p, max_work, block, s);
 }
 
 
-template <typename R, int FIELD, int SAMP, int PF, bool CTRL>
+template <typename R, int FIELD, int SAMP, int PF, int CTRL>
 void launch_k(const StepParams<R>& p, int grid, int block, cudaStream_t s) {
   if constexpr (kHasStd<R, FIELD, CTRL>) {
     if (std_config(p, FIELD == PRAD_FIELD_YEE2D ? 2 : 3)) {
@@ -1509,7 +1579,7 @@ void launch_k(const StepParams<R>& p, int grid, int block, cudaStream_t s) {
   k_push_emit<R, FIELD, SAMP, PF, CTRL, false><<<grid, block, 0, s>>>(p);
 }
 
-template <typename R, int FIELD, int SAMP, int PF, bool CTRL>
+template <typename R, int FIELD, int SAMP, int PF, int CTRL>
 int occupancy_k(int block, bool std_cfg, int pws) {
   if constexpr (kHasStd<R, FIELD, CTRL>) {
     if (std_cfg) {
@@ -1537,64 +1607,76 @@ bool dense_launch(const StepParams<R>& p) {
          (p.rr_mode < PRAD_RR_LEDGER || p.led_ll != nullptr);
 }
 
-template <typename R, int FIELD, bool CTRL>
+template <typename R, int FIELD, int CTRL>
 cudaError_t launch_field_c(const StepParams<R>& p, int sampler, int grid, int block,
                            cudaStream_t s) {
-  if (sampler == PRAD_SAMPLER_TABLE) {
-    // prefetching pays when the state streams through HBM (one step per
-    // launch); for long fused launches it only costs registers
-    bool pf = false;
-    if constexpr (sizeof(R) == 4) pf = p.nsub == 1;
-    if constexpr (sizeof(R) == 4) {
-      if (pf) {
-        if (dense_launch(p))
-          launch_k<R, FIELD, PRAD_SAMPLER_TABLE, 2, CTRL>(p, grid, block, s);
-        else
-          launch_k<R, FIELD, PRAD_SAMPLER_TABLE, 1, CTRL>(p, grid, block, s);
+  if constexpr (CTRL == 2) {  // angular spread: table sampler, no prefetch variant
+    if (sampler != PRAD_SAMPLER_TABLE) return cudaErrorInvalidValue;
+    launch_k<R, FIELD, PRAD_SAMPLER_TABLE, 0, 2>(p, grid, block, s);
+    return cudaGetLastError();
+  } else {
+    if (sampler == PRAD_SAMPLER_TABLE) {
+      // prefetching pays when the state streams through HBM (one step per
+      // launch); for long fused launches it only costs registers
+      bool pf = false;
+      if constexpr (sizeof(R) == 4) pf = p.nsub == 1;
+      if constexpr (sizeof(R) == 4) {
+        if (pf) {
+          if (dense_launch(p))
+            launch_k<R, FIELD, PRAD_SAMPLER_TABLE, 2, CTRL>(p, grid, block, s);
+          else
+            launch_k<R, FIELD, PRAD_SAMPLER_TABLE, 1, CTRL>(p, grid, block, s);
+        }
       }
+      if (!pf) launch_k<R, FIELD, PRAD_SAMPLER_TABLE, 0, CTRL>(p, grid, block, s);
+      return cudaGetLastError();
     }
-    if (!pf) launch_k<R, FIELD, PRAD_SAMPLER_TABLE, 0, CTRL>(p, grid, block, s);
-    return cudaGetLastError();
+    if constexpr (sizeof(R) == 4) {
+      if (sampler == PRAD_SAMPLER_MLP)
+        launch_k<R, FIELD, PRAD_SAMPLER_MLP, 0, CTRL>(p, grid, block, s);
+      else
+        launch_k<R, FIELD, PRAD_SAMPLER_MLP_FALLBACK, 0, CTRL>(p, grid, block, s);
+      return cudaGetLastError();
+    }
+    return cudaErrorInvalidValue;
   }
-  if constexpr (sizeof(R) == 4) {
-    if (sampler == PRAD_SAMPLER_MLP)
-      launch_k<R, FIELD, PRAD_SAMPLER_MLP, 0, CTRL>(p, grid, block, s);
-    else
-      launch_k<R, FIELD, PRAD_SAMPLER_MLP_FALLBACK, 0, CTRL>(p, grid, block, s);
-    return cudaGetLastError();
-  }
-  return cudaErrorInvalidValue;
 }
 
 template <typename R, int FIELD>
 cudaError_t launch_field(const StepParams<R>& p, int sampler, int grid, int block,
                          cudaStream_t s) {
+  if (p.ang != nullptr) return launch_field_c<R, FIELD, 2>(p, sampler, grid, block, s);
   const bool ctrl = p.ntry > 1 || p.sel_q < R(1) || p.diag != 0;
-  return ctrl ? launch_field_c<R, FIELD, true>(p, sampler, grid, block, s)
-              : launch_field_c<R, FIELD, false>(p, sampler, grid, block, s);
+  return ctrl ? launch_field_c<R, FIELD, 1>(p, sampler, grid, block, s)
+              : launch_field_c<R, FIELD, 0>(p, sampler, grid, block, s);
 }
 
-template <typename R, int FIELD, bool CTRL>
+template <typename R, int FIELD, int CTRL>
 int field_occupancy_c(int sampler, int pf, int block, bool std_cfg, int pws) {
-  if (sampler == PRAD_SAMPLER_TABLE) {
-    if constexpr (sizeof(R) == 4) {
-      if (pf == 2) return occupancy_k<R, FIELD, PRAD_SAMPLER_TABLE, 2, CTRL>(block, std_cfg, pws);
-      if (pf == 1) return occupancy_k<R, FIELD, PRAD_SAMPLER_TABLE, 1, CTRL>(block, std_cfg, pws);
+  if constexpr (CTRL == 2) {
+    return occupancy_k<R, FIELD, PRAD_SAMPLER_TABLE, 0, 2>(block, false, 0);
+  } else {
+    if (sampler == PRAD_SAMPLER_TABLE) {
+      if constexpr (sizeof(R) == 4) {
+        if (pf == 2) return occupancy_k<R, FIELD, PRAD_SAMPLER_TABLE, 2, CTRL>(block, std_cfg, pws);
+        if (pf == 1) return occupancy_k<R, FIELD, PRAD_SAMPLER_TABLE, 1, CTRL>(block, std_cfg, pws);
+      }
+      return occupancy_k<R, FIELD, PRAD_SAMPLER_TABLE, 0, CTRL>(block, std_cfg, pws);
     }
-    return occupancy_k<R, FIELD, PRAD_SAMPLER_TABLE, 0, CTRL>(block, std_cfg, pws);
+    if constexpr (sizeof(R) == 4) {
+      if (sampler == PRAD_SAMPLER_MLP)
+        return occupancy_k<R, FIELD, PRAD_SAMPLER_MLP, 0, CTRL>(block, std_cfg, pws);
+      return occupancy_k<R, FIELD, PRAD_SAMPLER_MLP_FALLBACK, 0, CTRL>(block, std_cfg, pws);
+    }
+    return 1;
   }
-  if constexpr (sizeof(R) == 4) {
-    if (sampler == PRAD_SAMPLER_MLP)
-      return occupancy_k<R, FIELD, PRAD_SAMPLER_MLP, 0, CTRL>(block, std_cfg, pws);
-    return occupancy_k<R, FIELD, PRAD_SAMPLER_MLP_FALLBACK, 0, CTRL>(block, std_cfg, pws);
-  }
-  return 1;
 }
 
 template <typename R, int FIELD>
-int field_occupancy(int sampler, int pf, int block, bool ctrl, bool std_cfg, int pws) {
-  return ctrl ? field_occupancy_c<R, FIELD, true>(sampler, pf, block, std_cfg, pws)
-              : field_occupancy_c<R, FIELD, false>(sampler, pf, block, std_cfg, pws);
+int field_occupancy(int sampler, int pf, int block, int ctrl, bool std_cfg, int pws) {
+  if (ctrl == 2) return field_occupancy_c<R, FIELD, 2>(sampler, pf, block, std_cfg, pws);
+  return ctrl ? field_occupancy_c<R, FIELD, 1>(sampler, pf, block, std_cfg, pws)
+              : field_occupancy_c<R, FIELD, 0>(sampler, pf, block, std_cfg, pws);
 }
 
 // Resident blocks per SM of the kernel variant a launch would use.
@@ -1603,12 +1685,14 @@ int push_emit_occupancy(const StepParams<R>& p, int field_kind, int sampler, int
                         bool ctrl) {
   const int pf = nsub == 1 ? (dense_launch(p) ? 2 : 1) : 0;
   const bool sc = std_config(p, field_kind == PRAD_FIELD_YEE2D ? 2 : 3);
+  // the control variant, or its angular-spread form
+  const int cv = ctrl ? (p.ang != nullptr ? 2 : 1) : 0;
   switch (field_kind) {
     case PRAD_FIELD_CONST:
-      return field_occupancy<R, PRAD_FIELD_CONST>(sampler, pf, block, ctrl, sc, pw_signs(p));
+      return field_occupancy<R, PRAD_FIELD_CONST>(sampler, pf, block, cv, sc, pw_signs(p));
     case PRAD_FIELD_PLANE_WAVE:
-      return field_occupancy<R, PRAD_FIELD_PLANE_WAVE>(sampler, pf, block, ctrl, sc, pw_signs(p));
-    default: return field_occupancy<R, PRAD_FIELD_YEE2D>(sampler, pf, block, ctrl, sc, pw_signs(p));
+      return field_occupancy<R, PRAD_FIELD_PLANE_WAVE>(sampler, pf, block, cv, sc, pw_signs(p));
+    default: return field_occupancy<R, PRAD_FIELD_YEE2D>(sampler, pf, block, cv, sc, pw_signs(p));
   }
 }
 template int push_emit_occupancy<float>(const StepParams<float>&, int, int, int, int, bool);
@@ -1683,6 +1767,23 @@ cudaError_t launch_eval_sampler(const StepParams<R>& p, const uint32_t* words,
   const int64_t want = (n + block - 1) / block;
   const int grid = static_cast<int>(want < 4096 ? (want > 0 ? want : 1) : 4096);
   k_eval_sampler<R><<<grid, block, 0, s>>>(p, words, x_out, g_out, n);
+  return cudaGetLastError();
+}
+
+__global__ void k_angle_eval(const float* __restrict__ tab, const float* __restrict__ x,
+                             const uint32_t* __restrict__ words, float* __restrict__ psi,
+                             int64_t n) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    psi[i] = ang_psi<float>(tab, x[i], words[2 * i], words[2 * i + 1]);
+}
+
+cudaError_t launch_angle_eval(const float* tab, const float* x, const uint32_t* words,
+                              float* psi, int64_t n, cudaStream_t s) {
+  const int block = 256;
+  const int64_t want = (n + block - 1) / block;
+  const int grid = static_cast<int>(want < 4096 ? (want > 0 ? want : 1) : 4096);
+  k_angle_eval<<<grid, block, 0, s>>>(tab, x, words, psi, n);
   return cudaGetLastError();
 }
 

@@ -26,6 +26,7 @@ PRAD_FP32, PRAD_FP64 = 0, 1
 PRAD_SAMPLER_TABLE, PRAD_SAMPLER_MLP, PRAD_SAMPLER_MLP_FALLBACK = 0, 1, 2
 PRAD_RR_OFF, PRAD_RR_LEDGER, PRAD_RR_APPLY = 0, 1, 2
 PRAD_DIAG_WIGGLER = 1
+PRAD_DIAG_ANGLE_SPREAD = 2
 PRAD_HEFF_FIELD, PRAD_HEFF_MOMENTUM = 0, 1
 PRAD_FIELD_CONST, PRAD_FIELD_PLANE_WAVE, PRAD_FIELD_YEE2D = 0, 1, 2
 
@@ -109,6 +110,7 @@ SIGNATURES = {
     "prad_mlp_wait_selftest": (_i32, [_vp]),
     "prad_batch_balance": (_i32, [_vp, ctypes.POINTER(_dbl), ctypes.POINTER(_i32)]),
     "prad_ginv_eval": (_i32, [_vp, _vp, _vp, _i64]),
+    "prad_angle_eval": (_i32, [_vp, _vp, _vp, _vp, _i64]),
     "prad_ledger_totals_noalloc": (_i32, [_vp, _vp, _i64, _vp, _vp]),
     "prad_ledger_totals_noalloc_error": (ctypes.c_char_p, []),
     "prad_philox": (_i32, [_vp, _vp, _u32, _u32, _vp, _i64]),
@@ -273,6 +275,10 @@ def prad_mlp_wait_selftest(h) -> int:
 
 def prad_ginv_eval(h, r_ptr, out_ptr, n: int) -> None:
     _check(load_library().prad_ginv_eval(h, r_ptr, out_ptr, n), h)
+
+
+def prad_angle_eval(h, x_ptr, words_ptr, out_ptr, n: int) -> None:
+    _check(load_library().prad_angle_eval(h, x_ptr, words_ptr, out_ptr, n), h)
 
 
 def prad_ledger_totals_noalloc(emit_ptr, rr_ptr, n: int, out_ptr, stream_ptr=None) -> None:
@@ -536,6 +542,21 @@ class Context:
         rr = torch.as_tensor(r, dtype=torch.float32).flatten().cuda().contiguous()
         out = torch.empty_like(rr)
         prad_ginv_eval(self.h, rr.data_ptr(), out.data_ptr(), rr.numel())
+        return out
+
+    def angle_eval(self, x, words):
+        """psi = gamma theta of the angular spread (PRAD_DIAG_ANGLE_SPREAD)
+        for photon frequencies x (omega/omega_c) and Philox word pairs
+        words (n x 2, uint32)."""
+        import numpy as np
+        torch = self.torch
+        xx = torch.as_tensor(x, dtype=torch.float32).flatten().cuda().contiguous()
+        ww = torch.as_tensor(np.ascontiguousarray(words, dtype=np.uint32).view(np.int32)
+                             ).flatten().cuda().contiguous()
+        if ww.numel() != 2 * xx.numel():
+            raise ValueError("angle_eval: words must hold two words per x")
+        out = torch.empty_like(xx)
+        prad_angle_eval(self.h, xx.data_ptr(), ww.data_ptr(), out.data_ptr(), xx.numel())
         return out
 
     def close(self) -> None:

@@ -54,9 +54,9 @@ KERNEL_SOURCES = ["paper_1409_5574_gb300/csrc/push_emit.cu",
                   "paper_1409_5574_gb300/csrc/mlp_device.cuh",
                   "paper_1409_5574_gb300/csrc/spec.cu"]
 NCU_TRAFFIC = {
-    "src_sha256": "fb4868ecb699fc08e98bca2a7286ee357432e72381132a9e3075abf35ceeb932",
-    "fused": 12566126464,  # mean bytes per launch over the 4 launches of one bench step
-    "stream": 1375824680,  # mean bytes per launch, 2^24 particles x 1 step, a0 = 500
+    "src_sha256": "f1c3891ab9328fa287f1c3cbd28187a4bbf6a24bce980b97c9691f9d65b84e5d",
+    "fused": 12565727872,  # mean bytes per launch over the 4 launches of one bench step
+    "stream": 1375859968,  # mean bytes per launch, 2^24 particles x 1 step, a0 = 500
 }
 
 
@@ -396,6 +396,40 @@ def planewave_20_periods(prad, W, torch, rank, peaks, nsm):
                          "launch": "1048576 particles x 400 steps (a0=500)"}}
 
 
+def planewave_angle_spread(prad, W, torch, rank):
+    """Cost of the emission's angular spread (PRAD_DIAG_ANGLE_SPREAD, Eqs.
+    (5)-(6)): the CP plane wave at a0 = 500, 2^20 electrons, 400 steps (100
+    per launch), table sampler, compiled-in kernels: the plain kernel, the
+    control/diagnostics variant (wiggler counter) and the spread variant."""
+    n, nsteps = 1 << 20, 400
+    wl = W.plane_wave(a0=500.0, n=n, periods=2, seed=5 + rank)
+    out = {"unit": UNIT, "workload": "CP plane wave a0=500, 1048576 electrons, 400 steps, "
+                                     "100 per launch, table sampler"}
+    for name, diag in (("plain", 0), ("control_variant", prad.PRAD_DIAG_WIGGLER),
+                       ("angle_spread", prad.PRAD_DIAG_ANGLE_SPREAD)):
+        ctx = prad.Context(wl.problem_kwargs(), precision=prad.PRAD_FP32,
+                           photon_capacity=int(0.05 * n * nsteps) + (1 << 20), max_particles=n,
+                           steps_per_launch=100, diagnostics=diag)
+        init = ctx.to_device(wl.state)
+        work = {k: torch.empty_like(v) for k, v in init.items()}
+
+        def one():
+            for k in work:
+                work[k].copy_(init[k], non_blocking=True)
+            ctx.push_emit(work, nsteps, t0=0)
+        one()
+        torch.cuda.synchronize()
+        secs = []
+        for _ in range(3):
+            ctx.reset()
+            ctx.drain()
+            secs.append(_timed(torch, one))
+        out[name] = n * nsteps / min(secs)
+        ctx.close()
+    out["spread_vs_plain"] = out["angle_spread"] / out["plain"]
+    return out
+
+
 def constant_b_fp64(prad, W, torch):
     """The constant-field check in FP64: 10^4 electrons, 1000 steps in one
     fused launch, LL ledger."""
@@ -423,6 +457,7 @@ def other_workloads(prad, W, torch, params, rank, peaks, nsm):
     records drained between chunks, drain time excluded).  `params`: trained
     network (None: table only)."""
     out = {"planewave_20_periods": planewave_20_periods(prad, W, torch, rank, peaks, nsm),
+           "planewave_angle_spread": planewave_angle_spread(prad, W, torch, rank),
            "constant_b_fp64": constant_b_fp64(prad, W, torch)}
 
     # 2D Yee grid 4096^2 (standing wave a0 = 300 + 1% noise), 16M electrons,

@@ -168,3 +168,37 @@ def test_spread_directions_match_the_oracle(case):
     tol = 5e-4 * theta + 2.0 * base + (3e-7 if precision == prad.PRAD_FP64 else 2e-6)
     bad = err > tol
     assert bad.sum() <= 1e-3 * len(common), (bad.sum(), err[bad][:5], tol[bad][:5])
+
+
+def test_gpu_spread_follows_the_density_in_a_pure_b_field():
+    """Electrons circling in B = 1e4 T along z (momenta in the x-y plane, LL
+    ledger only, so gamma is conserved): the orbit normal is z, and gamma
+    theta of every GPU record, theta its angle out of the x-y plane, is
+    distributed as Eq. (5)'s density at the record's own x (oracle CDF:
+    probability-integral transform uniform, KS p > 0.01), signs balanced."""
+    from scipy import stats
+    n, nsteps = 4000 + 3, 200
+    wl = W.const_b(n=n, nsteps=1, seed=23)
+    rng = np.random.default_rng(23)
+    g0 = rng.uniform(100.0, 1000.0, n)
+    ph0 = rng.uniform(0.0, 2.0 * math.pi, n)
+    um = np.sqrt(g0 * g0 - 1.0)
+    wl.state.update(ux=um * np.cos(ph0), uy=um * np.sin(ph0), uz=np.zeros(n))
+    wl = _f32(wl)
+    g0 = np.sqrt(1.0 + wl.state["ux"] ** 2 + wl.state["uy"] ** 2)
+    ph, _, _, _ = _gpu_run(wl, prad.PRAD_FP32, nsteps, diagnostics=SPREAD)
+    m = ph["pid"].size
+    assert m > 4000
+    d = np.stack([ph["nx"], ph["ny"], ph["nz"]], 1).astype(np.float64)
+    Bn = 1.0e4 * W.Q_E / (W.M_E * wl.omega_ref)
+    dtn = wl.dt * wl.omega_ref
+    g = g0[ph["pid"]]
+    rot = 2.0 * np.arctan(Bn * dtn / (2.0 * g))
+    ua = np.sqrt(g * g - 1.0) * np.cos(rot / 2.0)
+    ga = np.sqrt(1.0 + ua * ua)
+    eps_r = 1.054571817e-34 * wl.omega_ref / (9.1093837015e-31 * 299792458.0 ** 2)
+    x = ph["eps"].astype(np.float64) / (1.5 * eps_r * (Bn * ua / ga) * ga * ga)
+    psi = np.arcsin(np.clip(d[:, 2], -1.0, 1.0)) * ga
+    U = O.ang_cdf(x, np.abs(psi))
+    assert stats.kstest(U, "uniform").pvalue > 0.01
+    assert abs(np.mean(psi > 0) - 0.5) < 4.0 * 0.5 / math.sqrt(m)

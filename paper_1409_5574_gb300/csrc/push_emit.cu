@@ -198,26 +198,6 @@ __device__ __forceinline__ R ang_psi(const float* __restrict__ tab, R x, uint32_
 __device__ __forceinline__ void sincos_r(float v, float* s, float* c) { sincosf(v, s, c); }
 __device__ __forceinline__ void sincos_r(double v, double* s, double* c) { sincos(v, s, c); }
 
-// The record direction (dx, dy, dz) = u_avg turned by theta = psi / gamma
-// (iga = 1 / gamma) toward the orbit normal u^n x u^(n+1), keeping |u_avg|
-// (ua2 = |u_avg|^2; the flush normalises).
-template <typename R>
-__device__ __forceinline__ void ang_turn(const float* tab, R xs, uint32_t w0, uint32_t w1, R iga,
-                                      R ua2, R ux, R uy, R uz, R nux, R nuy, R nuz, R& dx,
-                                      R& dy, R& dz) {
-  const R th = ang_psi<R>(tab, xs, w0, w1) * iga;
-  const R cx = uy * nuz - uz * nuy, cy = uz * nux - ux * nuz, cz = ux * nuy - uy * nux;
-  const R c2 = cx * cx + cy * cy + cz * cz;
-  if (c2 > R(0)) {
-    R st, ct;
-    sincos_r(th, &st, &ct);
-    const R f = st * sqrt(ua2 / c2);
-    dx = ct * dx + f * cx;
-    dy = ct * dy + f * cy;
-    dz = ct * dz + f * cz;
-  }
-}
-
 __device__ __forceinline__ float rsq(float v) { return rsqrtf(v); }
 __device__ __forceinline__ double rsq(double v) { return rsqrt(v); }
 __device__ __forceinline__ float rcp(float v) { return __fdividef(1.0f, v); }
@@ -552,6 +532,18 @@ struct PhotonStageAoS {
 struct PhotonStageRec {
   float4 q[kStage][3];
 };
+// The control kernels' layout with the emission's angular spread (CTRL = 2):
+// the fields, plus per record the inputs of its turn, which the flush
+// evaluates for up to 32 records at a time instead of in every warp-step
+// where some lane emits: x, 1/gamma, |u_avg| times the orbit normal, and
+// the two Philox words of psi.
+struct PhotonStageSpread {
+  float f[8][kStage];
+  uint32_t pid[kStage];
+  uint32_t step[kStage];
+  float ex[7][kStage];  // x, 1/gamma, b_x, b_y, b_z, w0, w1 (words as bits)
+};
+
 template <class ST>
 constexpr bool kRecordStage =
     std::is_same<ST, PhotonStageAoS>::value || std::is_same<ST, PhotonStageRec>::value;
@@ -584,6 +576,17 @@ __device__ __forceinline__ void stage_put(PhotonStageRec& st, int pos, const flo
   st.q[pos][1] = make_float4(rec[4], rec[5], rec[6], rec[7]);
   st.q[pos][2] = make_float4(__uint_as_float(pid), __uint_as_float(step), 0.0f, 0.0f);
 }
+template <bool PEND>
+__device__ __forceinline__ void stage_put(PhotonStageSpread& st, int pos, const float rec[8],
+                                          uint32_t pid, uint32_t step, const float* ex) {
+  static_assert(!PEND, "no payload slot");
+#pragma unroll
+  for (int k = 0; k < 8; ++k) st.f[k][pos] = rec[k];
+  st.pid[pos] = pid;
+  st.step[pos] = step;
+#pragma unroll
+  for (int k = 0; k < 7; ++k) st.ex[k][pos] = ex[k];
+}
 __device__ __forceinline__ float4 stage_pend(const PhotonStageSoA& st, int r) {
   return make_float4(st.pend[0][r], st.pend[1][r], st.pend[2][r], st.pend[3][r]);
 }
@@ -612,6 +615,7 @@ struct PhotonOut {
   const float* ginv;
   double* led_base;
   unsigned long long* fallback;
+  const float* ang;  // angular-spread table (CTRL = 2 kernels)
 };
 
 template <bool PEND = false, class ST>
@@ -626,7 +630,28 @@ __device__ __forceinline__ void flush_stage(ST& st, int fill, const PhotonOut& o
     if (slot < static_cast<unsigned long long>(o.cap)) {
       // the direction is staged as the raw mean momentum: normalise here,
       // once per record, instead of in every lane of every step
-      if constexpr (kRecordStage<ST>) {
+      if constexpr (std::is_same<ST, PhotonStageSpread>::value) {
+        // angular spread: u_avg turned by theta = psi / gamma toward b
+        float dx = st.f[3][r], dy = st.f[4][r], dz = st.f[5][r];
+        const float bx = st.ex[2][r], by = st.ex[3][r], bz = st.ex[4][r];
+        if (bx != 0.0f || by != 0.0f || bz != 0.0f) {
+          const float th = ang_psi<float>(o.ang, st.ex[0][r], __float_as_uint(st.ex[5][r]),
+                                          __float_as_uint(st.ex[6][r])) *
+                           st.ex[1][r];
+          float sn, cs;
+          sincosf(th, &sn, &cs);
+          dx = cs * dx + sn * bx;
+          dy = cs * dy + sn * by;
+          dz = cs * dz + sn * bz;
+        }
+        const float d2 = dx * dx + dy * dy + dz * dz;
+        const float inv = d2 > 0.0f ? rsqrtf(d2) : 0.0f;
+        o.f[0][slot] = st.f[0][r]; o.f[1][slot] = st.f[1][r]; o.f[2][slot] = st.f[2][r];
+        o.f[3][slot] = dx * inv; o.f[4][slot] = dy * inv; o.f[5][slot] = dz * inv;
+        o.f[6][slot] = st.f[6][r]; o.f[7][slot] = st.f[7][r];
+        o.pid[slot] = st.pid[r];
+        o.step[slot] = st.step[r];
+      } else if constexpr (kRecordStage<ST>) {
         const float4 qa = st.q[r][0], qb = st.q[r][1], qc = st.q[r][2];
         const float d2 = qa.w * qa.w + qb.x * qb.x + qb.y * qb.y;
         const float inv = d2 > 0.0f ? rsqrtf(d2) : 0.0f;
@@ -1037,20 +1062,28 @@ __device__ __forceinline__ void advance_particle(const StepParams<R>& P, const u
           const R eps = xs * epsc;
           const R kw = k * w * wmul;
           if (want) le.add(kw * eps);
-          R dx = ax, dy = ay, dz = az;
-          if constexpr (CTRL == 2) {
-            // angular spread (Eqs. (5)-(6)): the direction turned by
-            // theta = psi / gamma toward the orbit normal u^n x u^(n+1)
-            // (its own Philox block, tag 0x20000 + trial; the record keeps
-            // |u_avg| and is normalised at the flush)
-            const uint4 ra = philox10_rk(make_uint4(pid, step, 0x20000u + j, P.ensemble), rk);
-            ang_turn<R>(P.ang, xs, ra.x, ra.y, iga, ua2, ux, uy, uz, nux, nuy, nuz, dx, dy, dz);
-          }
           const float rec[8] = {static_cast<float>(xn), static_cast<float>(yn),
-                                static_cast<float>(zn), static_cast<float>(dx),
-                                static_cast<float>(dy), static_cast<float>(dz),
+                                static_cast<float>(zn), static_cast<float>(ax),
+                                static_cast<float>(ay), static_cast<float>(az),
                                 static_cast<float>(eps), static_cast<float>(kw)};
-          stage_photon_mask(stage, fill, pout, want, mask, rec, pid, step);
+          if constexpr (CTRL == 2) {
+            // angular spread (Eqs. (5)-(6)): the record carries what its
+            // turn needs (psi's Philox words, block (pid, step, 0x20000 +
+            // trial, ensemble); x; 1/gamma; b = |u_avg| times the orbit
+            // normal u^n x u^(n+1) / |u^n x u^(n+1)|, zero if there is none)
+            // and the flush turns u_avg by theta = psi / gamma toward b
+            const uint4 ra = philox10_rk(make_uint4(pid, step, 0x20000u + j, P.ensemble), rk);
+            const R cx = uy * nuz - uz * nuy, cy = uz * nux - ux * nuz, cz = ux * nuy - uy * nux;
+            const R c2 = cx * cx + cy * cy + cz * cz;
+            const R fb = c2 > R(0) ? sqrt(ua2 / c2) : R(0);
+            const float ex[7] = {static_cast<float>(xs), static_cast<float>(iga),
+                                 static_cast<float>(fb * cx), static_cast<float>(fb * cy),
+                                 static_cast<float>(fb * cz), __uint_as_float(ra.x),
+                                 __uint_as_float(ra.y)};
+            stage_photon_mask(stage, fill, pout, want, mask, rec, pid, step, ex);
+          } else {
+            stage_photon_mask(stage, fill, pout, want, mask, rec, pid, step);
+          }
         }
       };
       if constexpr (!CTRL) {
@@ -1143,6 +1176,7 @@ __device__ __forceinline__ PhotonOut make_pout(const StepParams<R>& P) {
   o.ginv = P.ginv;
   o.led_base = P.led_base;
   o.fallback = P.counters + kMlpFallback;
+  o.ang = P.ang;
   return o;
 }
 
@@ -1270,8 +1304,10 @@ __global__ void __launch_bounds__(256, (PF ? PRAD_PF_MINB : MinBlocks<R, FIELD, 
   const StepParams<R>& P = P_arg;
 #endif
   constexpr bool kSTab = kSharedTab<R, SAMP, PF, CTRL>;
-  using Stage = typename std::conditional<kSTab, PhotonStageRec,
-                                          PhotonStageT<SAMP != PRAD_SAMPLER_TABLE || !CTRL>>::type;
+  using Stage = typename std::conditional<
+      CTRL == 2, PhotonStageSpread,
+      typename std::conditional<kSTab, PhotonStageRec,
+                                PhotonStageT<SAMP != PRAD_SAMPLER_TABLE || !CTRL>>::type>::type;
   __shared__ Stage stage_all[kMaxWarps];
   __shared__ typename TabOf<R>::T stab[kSTab ? kNTab : 1];
   if constexpr (kSTab) {
@@ -1476,7 +1512,8 @@ __global__ void __launch_bounds__(256, 3) k_push_emit_tiled(const StepParams<R> 
 #endif
   if (blockIdx.x >= *P.work_count) return;
   extern __shared__ __align__(16) float tile_sm[];
-  __shared__ PhotonStageSoA stage_all[kMaxWarps];
+  using Stage = typename std::conditional<CTRL == 2, PhotonStageSpread, PhotonStageSoA>::type;
+  __shared__ Stage stage_all[kMaxWarps];
   const int4 wk = P.work[blockIdx.x];
   const int tx = wk.x % P.ntx, ty = wk.x / P.ntx;
   const int gx0 = tx * kTile - kHalo, gy0 = ty * kTile - kHalo;
@@ -1506,7 +1543,7 @@ __global__ void __launch_bounds__(256, 3) k_push_emit_tiled(const StepParams<R> 
         __ldg(P_arg.yee[c] + static_cast<size_t>(gy) * P.nx + gx);
   }
   __syncthreads();
-  PhotonStageSoA& stage = stage_all[threadIdx.x >> 5];
+  Stage& stage = stage_all[threadIdx.x >> 5];
   int fill = 0;
   const PhotonOut pout = make_pout(P);
   Counts cnt;

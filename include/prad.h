@@ -155,6 +155,16 @@ typedef struct prad_config {
  * device table, built on the host at the first such prad_init of the
  * process (~0.3 s). */
 #define PRAD_DIAG_ANGLE_SPREAD 2
+/* Geometry of the angular spread's table (prad_angle_table): PRAD_ANG_NL
+ * rows uniform in ln x over [PRAD_ANG_LX0, PRAD_ANG_LX1] and PRAD_ANG_NV
+ * columns uniform in v = sqrt(-ln(1 - u)) over [0, PRAD_ANG_VMAX]; entry
+ * (row, column) is psi / (v s(x)) with s(x) = (2/x)^(1/3) (1 + x)^(-1/6)
+ * (0 in column 0). */
+#define PRAD_ANG_NL 225
+#define PRAD_ANG_NV 257
+#define PRAD_ANG_LX0 (-18.420680743952367) /* ln 1e-8 */
+#define PRAD_ANG_LX1 3.6888794541139363    /* ln 40   */
+#define PRAD_ANG_VMAX 4.8
 
 /* ---- field description ------------------------------------------------- */
 typedef struct prad_fields {
@@ -443,6 +453,13 @@ int prad_ginv_eval(prad_ctx* ctx, const float* r, float* lnx, int64_t n);
  * n < 0. */
 int prad_angle_eval(prad_ctx* ctx, const float* x, const uint32_t* words, float* psi,
                     int64_t n);
+
+/* The angular spread's table as the library builds it for
+ * PRAD_DIAG_ANGLE_SPREAD contexts, written to host out (row-major,
+ * PRAD_ANG_NL x PRAD_ANG_NV floats; geometry above).  Host only: needs no
+ * device and no context (built once per process, ~0.3 s on first use).
+ * PRAD_ERR_ARG if out is NULL or n < PRAD_ANG_NL * PRAD_ANG_NV. */
+int prad_angle_table(float* out, int64_t n);
 
 /* ---- angular distribution (Fig. 4) -------------------------------------------
  * Histogram of the emitted energy (record energy x weight) of the photon

@@ -404,6 +404,20 @@ void build_ang_table(std::vector<float>& out) {
   }
 }
 
+static_assert(PRAD_ANG_NL == kAngNL && PRAD_ANG_NV == kAngNV &&
+                  PRAD_ANG_LX0 == kAngLx0 && PRAD_ANG_LX1 == kAngLx1 &&
+                  PRAD_ANG_VMAX == kAngVmax,
+              "public and internal angular-table geometry agree");
+
+// The table, built on first use in the process (~0.3 s), like the tables
+// prad_init builds.
+const std::vector<float>& ang_table_host() {
+  static std::once_flag once;
+  static std::vector<float> t;
+  std::call_once(once, [] { build_ang_table(t); });
+  return t;
+}
+
 uint16_t to_bf16(float f) {  // round to nearest even
   uint32_t u;
   std::memcpy(&u, &f, 4);
@@ -879,10 +893,7 @@ int prad_init(prad_ctx** out, const prad_config* cfg) {
     build_ginv(ginv_host);
   });
   if (cfg->diagnostics & PRAD_DIAG_ANGLE_SPREAD) {
-    // built on first use in the process (~0.1 s), like the tables above
-    static std::once_flag ang_once;
-    static std::vector<float> ang_host;
-    std::call_once(ang_once, [] { build_ang_table(ang_host); });
+    const std::vector<float>& ang_host = ang_table_host();
     CKI(cudaMalloc(&c->d_ang, ang_host.size() * sizeof(float)));
     CKI(cudaMemcpy(c->d_ang, ang_host.data(), ang_host.size() * sizeof(float),
                    cudaMemcpyHostToDevice));
@@ -1683,6 +1694,14 @@ int prad_angle_eval(prad_ctx* c, const float* x, const uint32_t* words, float* p
     return fail(c, PRAD_ERR_STATE, "angle_eval: context created without PRAD_DIAG_ANGLE_SPREAD");
   if (n == 0) return PRAD_OK;
   CK(c, launch_angle_eval(c->d_ang, x, words, psi, n, c->stream));
+  return PRAD_OK;
+}
+
+int prad_angle_table(float* out, int64_t n) {
+  if (!out || n < static_cast<int64_t>(kAngNL) * kAngNV)
+    return fail(nullptr, PRAD_ERR_ARG, "angle_table: need %d floats", kAngNL * kAngNV);
+  const std::vector<float>& t = ang_table_host();
+  std::memcpy(out, t.data(), t.size() * sizeof(float));
   return PRAD_OK;
 }
 

@@ -111,6 +111,7 @@ SIGNATURES = {
     "prad_batch_balance": (_i32, [_vp, ctypes.POINTER(_dbl), ctypes.POINTER(_i32)]),
     "prad_ginv_eval": (_i32, [_vp, _vp, _vp, _i64]),
     "prad_angle_eval": (_i32, [_vp, _vp, _vp, _vp, _i64]),
+    "prad_angle_table": (_i32, [_vp, _i64]),
     "prad_ledger_totals_noalloc": (_i32, [_vp, _vp, _i64, _vp, _vp]),
     "prad_ledger_totals_noalloc_error": (ctypes.c_char_p, []),
     "prad_philox": (_i32, [_vp, _vp, _u32, _u32, _vp, _i64]),
@@ -275,6 +276,19 @@ def prad_mlp_wait_selftest(h) -> int:
 
 def prad_ginv_eval(h, r_ptr, out_ptr, n: int) -> None:
     _check(load_library().prad_ginv_eval(h, r_ptr, out_ptr, n), h)
+
+
+PRAD_ANG_NL, PRAD_ANG_NV = 225, 257
+PRAD_ANG_LX0, PRAD_ANG_LX1, PRAD_ANG_VMAX = -18.420680743952367, 3.6888794541139363, 4.8
+
+
+def prad_angle_table():
+    """The angular spread's table (PRAD_ANG_NL x PRAD_ANG_NV numpy float32),
+    built on the host by the library; no device needed."""
+    import numpy as np
+    out = np.empty((PRAD_ANG_NL, PRAD_ANG_NV), dtype=np.float32)
+    _check(load_library().prad_angle_table(out.ctypes.data_as(ctypes.c_void_p), out.size), None)
+    return out
 
 
 def prad_angle_eval(h, x_ptr, words_ptr, out_ptr, n: int) -> None:
